@@ -1,0 +1,320 @@
+"""CPU oracle for the Schur refinement iteration -- TEST INFRASTRUCTURE ONLY.
+
+Plain numpy (matrix products as library primitives) plus the C routines of
+``schur_oracle.c`` for the triangular solve and double-double residuals. Only
+the tests, the smoke check and the benchmark's CPU-baseline leg may import
+this module; the product path never does.
+
+Every function follows the paper's steps in its order and notation:
+
+* :func:`ns_init`      -- Alg. 4 line "convert Qhat to hp, one Newton-Schulz
+  step", eq. (NS) of Sec. 2.4: Q = 1/2 Qhat (3I - Qhat^H Qhat).
+* :func:`alg2`         -- Alg. 2 (successive substitution) for
+  stril(T L - L T) = -E, eq. (2.5) of Sec. 2.1.
+* :func:`alg3`         -- Alg. 3 (recursive block algorithm), Sec. 2.1.
+* :func:`kron_solve`   -- brute force of the same equation (dense solve of the
+  operator's n(n-1)/2-square matrix in 128-bit arithmetic).
+* :func:`iteration`    -- one pass of the REPEAT loop of Alg. 4 (Sec. 2.4):
+  T^ = Q^H A Q in hp; E = stril(T^), T = T^ - E, to lp; solve in lp; L to
+  hp; W = L - L^H; Y = Q^H Q - I in hp; YW, W^2, W^3 in lp; Sigma in hp;
+  Q <- 1/2 Q Sigma in hp (eq. "NSmerged", truncated as Sec. 2.4 states).
+* :func:`refine`       -- Alg. 4 from Qhat until the stop test holds.
+* :func:`residuals_dd` -- ||stril(Q^H A Q)||_F / ||A||_F and ||Q^H Q - I||_F
+  (the two error measures of Sec. 3) in double-double.
+
+Precision pairs: hp is float64 (complex128); lp is float32 (complex64) for the
+mixed form and float64 (complex128) for the all-FP64 form.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _lib
+
+OK, NONDISTINCT, NONFINITE, NOT_CONVERGED = 0, 2, 3, 4
+
+
+class SolveError(RuntimeError):
+    def __init__(self, code: int):
+        super().__init__({NONDISTINCT: "diagonal entries of T are not pairwise distinct (Theorem 1)",
+                          NONFINITE: "non-finite value in the solution"}.get(code, f"code {code}"))
+        self.code = code
+
+
+def _lp_dtype(lp: str, complex_: bool):
+    if lp == "f32":
+        return np.complex64 if complex_ else np.float32
+    if lp == "f64":
+        return np.complex128 if complex_ else np.float64
+    raise ValueError(lp)
+
+
+def _hp_dtype(complex_: bool):
+    return np.complex128 if complex_ else np.float64
+
+
+def _ctype(a: np.ndarray):
+    return a.dtype
+
+
+# ---------------------------------------------------------------------------
+# Triangular matrix equation stril(T L - L T) = -E  (Sec. 2.1)
+
+def alg2(T: np.ndarray, E: np.ndarray, d_hp: np.ndarray | None = None) -> np.ndarray:
+    """Alg. 2 in the precision of ``T`` (float32/64, complex64/128).
+
+    ``d_hp`` is the diagonal of T in high precision; when given, the divisors
+    t_ii - t_jj are formed from it and then rounded to the precision of T.
+    Raises :class:`SolveError` on a zero divisor (Theorem 1) or a non-finite L.
+    """
+    n = T.shape[0]
+    dt = T.dtype
+    T = _lib.fortran(T, dt)
+    E = _lib.fortran(E, dt)
+    L = np.zeros((n, n), dtype=dt, order="F")
+    L_ = _lib.lib()
+    if np.iscomplexobj(T):
+        dh = None if d_hp is None else np.ascontiguousarray(d_hp, dtype=np.complex128)
+        fn = L_.sro_alg2_c64 if dt == np.complex64 else L_.sro_alg2_c128
+    else:
+        dh = None if d_hp is None else np.ascontiguousarray(d_hp, dtype=np.float64)
+        fn = L_.sro_alg2_f32 if dt == np.float32 else L_.sro_alg2_f64
+    rc = fn(n, _lib.ptr(T), n, _lib.ptr(E), n, None if dh is None else _lib.ptr(dh),
+            _lib.ptr(L), n)
+    if rc:
+        raise SolveError(rc)
+    return L
+
+
+def alg3(T: np.ndarray, E: np.ndarray, nmin: int = 2) -> np.ndarray:
+    """Alg. 3 (recursive blocks, n1 = floor(n/2)) in float64."""
+    n = T.shape[0]
+    T = _lib.fortran(T, np.float64)
+    Ew = _lib.fortran(E, np.float64).copy(order="F")
+    L = np.zeros((n, n), order="F")
+    rc = _lib.lib().sro_alg3_f64(n, _lib.ptr(T), n, _lib.ptr(Ew), n, _lib.ptr(L), n, int(nmin))
+    if rc:
+        raise SolveError(rc)
+    return L
+
+
+def kron_solve(T: np.ndarray, E: np.ndarray):
+    """Brute-force solve in 128-bit arithmetic; returns (hi, lo) float64 planes."""
+    n = T.shape[0]
+    T = _lib.fortran(T, np.float64)
+    E = _lib.fortran(E, np.float64)
+    hi = np.zeros((n, n), order="F")
+    lo = np.zeros((n, n), order="F")
+    rc = _lib.lib().sro_kron_solve(n, _lib.ptr(T), n, _lib.ptr(E), n, _lib.ptr(hi), _lib.ptr(lo), n)
+    if rc:
+        raise SolveError(rc)
+    return hi, lo
+
+
+# ---------------------------------------------------------------------------
+# Alg. 4 (Sec. 2.4)
+
+def ns_init(Qhat: np.ndarray):
+    """Convert Qhat to hp and apply one Newton-Schulz step, eq. (NS).
+
+    Returns (Q, ||Qhat^H Qhat - I||_F), the latter measured in hp.
+    """
+    cplx = np.iscomplexobj(Qhat)
+    Q = np.asfortranarray(Qhat.astype(_hp_dtype(cplx)))
+    n = Q.shape[0]
+    I = np.eye(n, dtype=Q.dtype)
+    G = Q.conj().T @ Q
+    y = float(np.linalg.norm(G - I))
+    return np.asfortranarray(0.5 * (Q @ (3.0 * I - G))), y
+
+
+@dataclass
+class IterInfo:
+    r_T: float                 # ||stril(Q^H A Q)||_F / ||A||_F of the incoming Q (hp)
+    y_norm: float = math.nan   # ||Q^H Q - I||_F of the incoming Q (hp), nan if not formed
+    w_norm: float = math.nan   # ||W||_F
+    updated: bool = False
+
+
+def form_residual(A: np.ndarray, Q: np.ndarray):
+    """T^ = Q^H A Q in hp (two products), split into E = stril(T^) and T = T^ - E."""
+    That = Q.conj().T @ (A @ Q)
+    E = np.tril(That, -1)
+    T = That - E
+    return T, E
+
+
+def iteration(A: np.ndarray, Q: np.ndarray, lp: str = "f32", full_sigma: bool = False,
+              solver: str = "alg2", T_E=None, parts: dict | None = None):
+    """One pass of the REPEAT loop of Alg. 4; returns (Q_new, IterInfo).
+
+    ``full_sigma`` adds the two terms W^2 Y + W^2 Y W that Sec. 2.4 drops.
+    If ``parts`` is a dict, the intermediates T, E, L, W, Y and Sigma are
+    stored in it.
+    """
+    cplx = np.iscomplexobj(A)
+    hp = _hp_dtype(cplx)
+    lpt = _lp_dtype(lp, cplx)
+    n = A.shape[0]
+    I = np.eye(n, dtype=hp)
+    T, E = form_residual(A, Q) if T_E is None else T_E
+    info = IterInfo(r_T=float(np.linalg.norm(E) / np.linalg.norm(A)))
+    # E, T to lp; divisors from the hp diagonal
+    T_lp = np.asfortranarray(T.astype(lpt))
+    E_lp = np.asfortranarray(E.astype(lpt))
+    if solver == "alg2":
+        L_lp = alg2(T_lp, E_lp, np.diagonal(T).copy())
+    elif solver == "alg3":
+        if lpt != np.float64:
+            raise ValueError("alg3 oracle is float64 only")
+        L_lp = alg3(T_lp, E_lp)
+    else:
+        raise ValueError(solver)
+    L = L_lp.astype(hp)
+    W = L - L.conj().T
+    Y = Q.conj().T @ Q - I
+    info.y_norm = float(np.linalg.norm(Y))
+    info.w_norm = float(np.linalg.norm(W))
+    # products in lp
+    Y_l = Y.astype(lpt)
+    W_l = W.astype(lpt)
+    YW = Y_l @ W_l
+    W2 = W_l @ W_l
+    W3 = W_l @ W2
+    Sigma = 2.0 * I + 2.0 * W - Y - YW.astype(hp) + W2.astype(hp) + W3.astype(hp)
+    if full_sigma:
+        W2Y = W2 @ Y_l
+        W2YW = W2Y @ W_l
+        Sigma = Sigma + W2Y.astype(hp) + W2YW.astype(hp)
+    Qn = np.asfortranarray(0.5 * (Q @ Sigma))
+    info.updated = True
+    if parts is not None:
+        parts.update(T=T, E=E, L=L, W=W, Y=Y, Sigma=Sigma)
+    return Qn, info
+
+
+def default_tol(n: int) -> float:
+    """FP64 target: 1e-14 sqrt(n)."""
+    return 1e-14 * math.sqrt(n)
+
+
+@dataclass
+class RefineResult:
+    Q: np.ndarray
+    status: int
+    iters: int                     # number of T^ formations
+    hp_gemms: int                  # high-precision matrix products
+    history: list = field(default_factory=list)
+    y0: float = math.nan
+
+
+def refine(A: np.ndarray, Qhat: np.ndarray, lp: str = "f32", tol: float | None = None,
+           max_iter: int = 10, full_sigma: bool = False, solver: str = "alg2",
+           init_ns: bool = True) -> RefineResult:
+    """Alg. 4 lines "convert Qhat, NS step" and REPEAT ... UNTIL convergence.
+
+    Stop test (the paper only says "when E becomes small enough"): after
+    forming T^ from Q_k, stop if ||E||_F / ||A||_F <= tol and the last
+    measured ||Q^H Q - I||_F <= sqrt(tol). The final pass forms T^ only, so a
+    run of k passes costs 2 + 4(k-1) + 2 = 4k high-precision products when it
+    starts with the Newton-Schulz step.
+    """
+    n = A.shape[0]
+    tol = default_tol(n) if tol is None else tol
+    if init_ns:
+        Q, y = ns_init(Qhat)
+        gemms = 2
+    else:
+        Q = np.asfortranarray(Qhat.astype(_hp_dtype(np.iscomplexobj(A))))
+        y, gemms = math.nan, 0
+    res = RefineResult(Q=Q, status=NOT_CONVERGED, iters=0, hp_gemms=gemms, y0=y)
+    y_last = y
+    prev_rT = math.inf
+    for k in range(1, max_iter + 1):
+        T, E = form_residual(A, Q)
+        res.hp_gemms += 2
+        res.iters = k
+        r_T = float(np.linalg.norm(E) / np.linalg.norm(A))
+        if not math.isfinite(r_T):
+            res.status = NONFINITE
+            res.history.append(IterInfo(r_T=r_T))
+            break
+        ok_y = (not math.isfinite(y_last)) or y_last <= math.sqrt(tol)
+        if r_T <= tol and ok_y:
+            res.status = OK
+            res.history.append(IterInfo(r_T=r_T))
+            break
+        if k >= 3 and r_T > 10.0 * prev_rT:
+            res.status = NOT_CONVERGED
+            res.history.append(IterInfo(r_T=r_T))
+            break
+        prev_rT = r_T
+        try:
+            Q, info = iteration(A, Q, lp=lp, full_sigma=full_sigma, solver=solver, T_E=(T, E))
+        except SolveError as e:
+            res.status = e.code
+            res.history.append(IterInfo(r_T=r_T))
+            break
+        res.hp_gemms += 2
+        res.history.append(info)
+        y_last = info.y_norm
+        res.Q = Q
+        if not np.all(np.isfinite(Q)):
+            res.status = NONFINITE
+            break
+    return res
+
+
+# ---------------------------------------------------------------------------
+# Residuals in double-double (Sec. 3 error measures)
+
+def residuals_dd(A: np.ndarray, Q: np.ndarray, threads: int | None = None):
+    """(r_T, r_Q) = (||stril(Q^H A Q)||_F/||A||_F, ||Q^H Q - I||_F) in double-double."""
+    n = A.shape[0]
+    if threads is not None:
+        _lib.set_threads(threads)
+    rT = np.zeros(1)
+    rQ = np.zeros(1)
+    if np.iscomplexobj(A) or np.iscomplexobj(Q):
+        Af = _lib.fortran(A, np.complex128)
+        Qf = _lib.fortran(Q, np.complex128)
+        _lib.lib().sro_residuals_dd_c(n, _lib.ptr(Af), n, _lib.ptr(Qf), n, _lib.ptr(rT), _lib.ptr(rQ))
+    else:
+        Af = _lib.fortran(A, np.float64)
+        Qf = _lib.fortran(Q, np.float64)
+        _lib.lib().sro_residuals_dd(n, _lib.ptr(Af), n, _lib.ptr(Qf), n, _lib.ptr(rT), _lib.ptr(rQ))
+    return float(rT[0]), float(rQ[0])
+
+
+def sample_entries_dd(A: np.ndarray, Q: np.ndarray, rows, cols):
+    """Entries (Q^T A Q)[rows, cols] and (Q^T Q - I)[rows, cols] in double-double (real)."""
+    n = A.shape[0]
+    Af = _lib.fortran(A, np.float64)
+    Qf = _lib.fortran(Q, np.float64)
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    t = np.zeros(len(r))
+    y = np.zeros(len(r))
+    _lib.lib().sro_sample_entries_dd(n, _lib.ptr(Af), n, _lib.ptr(Qf), n, len(r), _lib.ptr(r),
+                                     _lib.ptr(c), _lib.ptr(t), _lib.ptr(y))
+    return t, y
+
+
+def gemm_dd(A_hi, A_lo, B_hi, B_lo, transA: bool = False):
+    """C = op(A) B with double-double operands (lo planes may be None)."""
+    m = A_hi.shape[1] if transA else A_hi.shape[0]
+    k = A_hi.shape[0] if transA else A_hi.shape[1]
+    n = B_hi.shape[1]
+    Ah = _lib.fortran(A_hi, np.float64)
+    Al = None if A_lo is None else _lib.fortran(A_lo, np.float64)
+    Bh = _lib.fortran(B_hi, np.float64)
+    Bl = None if B_lo is None else _lib.fortran(B_lo, np.float64)
+    Ch = np.zeros((m, n), order="F")
+    Cl = np.zeros((m, n), order="F")
+    _lib.lib().sro_gemm_dd(int(transA), m, n, k, _lib.ptr(Ah), None if Al is None else _lib.ptr(Al),
+                           Ah.shape[0], _lib.ptr(Bh), None if Bl is None else _lib.ptr(Bl),
+                           Bh.shape[0], _lib.ptr(Ch), _lib.ptr(Cl), m)
+    return Ch, Cl
