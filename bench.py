@@ -1,0 +1,345 @@
+"""Benchmark: seconds to an FP64-accurate Schur decomposition by Alg. 4.
+
+One step = one complete refinement (Alg. 4 from the FP32 starting factor to
+the stop test) of a real n = 4096 planted problem (eigenvalues
+k/n + U(0, 0.5/n), strictly upper entries with standard deviation 1/n,
+Qhat = fl32(Q0 expm(1e-6 S))), with A and Qhat resident in HBM. The mixed form
+(FP32 solve and correction products, FP64 or emulated-FP64 products) is timed;
+the all-FP64 form of the same iteration on the same inputs is timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun) every rank refines its own
+copy (replicas only: a single refinement does not shard); the value is the
+slowest rank's time per refinement.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sec to FP64-accurate Schur refinement, mixed vs all-FP64 GPU; % FP64/tensor peak"
+FP64_NOMINAL_TFLOPS = 1.25        # GB300 FP64 (vector and tensor), nominal
+BF16_NOMINAL_TFLOPS = 2250.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _workload_name(n):
+    return (f"real n={n} planted A=Q0 T0 Q0^T, lambda_k=k/n+U(0,0.5/n), upper std 1/n, "
+            f"Qhat=fl32(Q0 expm(1e-6 S)); Alg. 4 to ||stril||/||A||<=1e-14 sqrt(n)")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(n_full: int, n_sample: int):
+    """The oracle's full refinement at n_sample, scaled by (n_full/n_sample)^3."""
+    import oracle
+    from paper_2203_10879_gb300 import inputs
+    p = inputs.jittered_real(n_sample)
+    t0 = time.perf_counter()
+    r = oracle.refine(p.A, p.Qhat, lp="f32")
+    dt = time.perf_counter() - t0
+    scale = (n_full / n_sample) ** 3
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return dt * scale, dt, r, cores
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    n, ns = args.n, args.cpu_sample_n
+    times = []
+    for i in range(args.warmup + args.steps):
+        est, dt, r, cores = cpu_oracle_sample(n, ns)
+        if i >= args.warmup:
+            times.append(est)
+    v = sum(times) / len(times)
+    sample = (f"oracle (numpy FP64 products + C Alg. 2 in FP32) full refinement at n={ns} of the same "
+              f"recipe, scaled by (n/{ns})^3 to n={n}")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": _workload_name(n), "n": n, "form": "mixed FP32->FP64 (oracle)"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2203_10879_gb300 as P
+    from paper_2203_10879_gb300 import _binding as B
+    from paper_2203_10879_gb300 import inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n = args.n
+    p = inputs.jittered_real(n)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+    A = dev(p.A)
+    Qhat = dev(p.Qhat)
+    Q = torch.empty((n, n), dtype=torch.float64, device="cuda").t()
+    stream = torch.cuda.current_stream()
+
+    hp_name = {"fp64": B.SR_HP_FP64, "ozaki": B.SR_HP_OZAKI_BF16}
+    hp = args.hp
+    if hp == "auto":
+        hp = "ozaki"
+        try:
+            probe = P.Refiner(8, hp_gemm=B.SR_HP_OZAKI_BF16)
+            probe.close()
+        except P.SchurRefineError:
+            hp = "fp64"
+
+    def timed(ref, steps, warmup, host=False):
+        for _ in range(warmup):
+            ref.step(A, Q, Qhat, check=False)
+        ref.reset_profile()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = nr = None
+        for _ in range(steps):
+            st, nr = ref.step(A, Q, Qhat, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1) / steps, st, nr
+
+    # ---- mixed form (the measured path) --------------------------------------------
+    mixed = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, profile=1)
+    for _ in range(args.warmup):
+        mixed.step(A, Q, Qhat, check=False)
+    mixed.reset_profile()
+    clocks = Clocks(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        status, nr = mixed.step(A, Q, Qhat, check=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = mixed.profile()
+    rT, rQ = mixed.residuals(A, Q)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = int(sum(v["launches"] for v in prof.values()))
+
+    # ---- end to end through host buffers --------------------------------------------
+    hA = torch.from_numpy(np.ascontiguousarray(p.A.T)).pin_memory()
+    hQh = torch.from_numpy(np.ascontiguousarray(p.Qhat.T)).pin_memory()
+    hQ = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    dA_t = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    dQh_t = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    dQ_t = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    ke = max(1, min(args.steps, 3))
+    for i in range(1 + ke):
+        if i == 1:
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+        dA_t.copy_(hA, non_blocking=True)
+        dQh_t.copy_(hQh, non_blocking=True)
+        mixed.step(dA_t.t(), dQ_t.t(), dQh_t.t(), check=False)
+        hQ.copy_(dQ_t, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    mixed.close()
+
+    # ---- all-FP64 form of the same iteration on the same inputs -----------------------
+    allfp64 = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP64, profile=1)
+    k64 = max(1, min(args.steps, args.fp64_steps))
+    ms64, st64, nr64 = timed(allfp64, k64, 1)
+    prof64 = allfp64.profile()
+    allfp64.close()
+    mixed_native_ms = None
+    if hp != "fp64":
+        mn = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP32)
+        mixed_native_ms, _, _ = timed(mn, k64, 1)
+        mn.close()
+
+    if rank != 0:
+        return 0
+
+    # ---- roofline of the dominant kernel (live CUDA-event timings) --------------------
+    peaks = _peaks()
+    kinds = {k: v for k, v in prof.items() if v["ms"] > 0}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = prof[dom]
+    if dom in ("hp_gemm",):
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        peak = FP64_NOMINAL_TFLOPS
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "gemm_simt_kernel<double> (FP64 DFMA)",
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table; no measured FP64 peak)"}
+    elif dom == "oz_mma":
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "ozaki slice products (tcgen05 kind::f16 bf16)",
+                "peak_source": "of measured bf16 sustained (MEASURED_PEAKS.json)"}
+    else:
+        gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs") or 6800.0
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                "traffic": None, "kernel": dom, "peak_source": "of measured HBM copy"}
+    roof["launch_ms"] = d["ms"] / max(1, d["spans"])
+    roof["share_of_step"] = d["ms"] / (ms * args.steps)
+
+    cpu_val = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        est, dt, r, cores = cpu_oracle_sample(n, args.cpu_sample_n)
+        cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle full refinement at n={args.cpu_sample_n} ({dt:.2f} s measured), "
+                         f"scaled by (n/{args.cpu_sample_n})^3 to n={n}"}
+        cpu_val = est
+
+    tol = 1e-14 * math.sqrt(n)
+    line = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": _workload_name(n), "n": n, "form": "mixed: FP32 solve/products",
+                   "hp_gemm": hp if hp == "fp64" else f"ozaki-bf16-s{args.slices or 7}",
+                   "l2": "inputs larger than L2 (A 128 MiB + Q 128 MiB + workspace)",
+                   "status": status, "iters": nr.iters, "hp_gemms": nr.hp_gemms,
+                   "certified": {"stril_rel": rT, "orth": rQ, "tol": tol, "ok": bool(rT <= tol and rQ <= tol)},
+                   "all_fp64_s": ms64 / 1e3, "all_fp64_iters": nr64.iters, "all_fp64_status": st64,
+                   "mixed_vs_all_fp64_speedup": ms64 / ms,
+                   "mixed_native_fp64_s": None if mixed_native_ms is None else mixed_native_ms / 1e3,
+                   "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
+                   "all_fp64_phase_ms_per_step": {k: v["ms"] / k64 for k, v in prof64.items() if v["ms"] > 0},
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n * n * (8 + 4)),
+                "d2h_bytes_per_step": int(n * n * 8)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--hp", choices=["auto", "fp64", "ozaki"], default="auto")
+    ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-n", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

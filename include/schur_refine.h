@@ -1,0 +1,227 @@
+/*
+ * schur_refine.h -- C ABI of the GB300 Schur-refinement library.
+ *
+ * Problem (Sec. 2, eq. "lowup"; Alg. 1 REQUIRE/ENSURE; Alg. 4): given a square
+ * matrix A and a nearly unitary Qhat for which Qhat^H A Qhat is nearly upper
+ * triangular, compute a unitary Q (to working high precision) with Q^H A Q
+ * upper triangular. The library runs the Newton-like iteration of Alg. 4 on
+ * one GPU: high-precision products form T^ = Q^H A Q and Y = Q^H Q - I, a
+ * low-precision solve of stril(T L - L T) = -stril(T^) (eq. "linearsystem",
+ * Alg. 2/3) gives L, and the merged Newton-Schulz update of eq. "NSmerged"
+ * (Sec. 2.4) moves Q.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are column-major: element (i, j) of an n x n matrix M with
+ *     leading dimension ld >= n lives at M[i + j*ld].
+ *   - "device" pointers must address memory of the current CUDA device;
+ *     "host" pointers address host memory.
+ *   - The caller owns every matrix it passes. The library owns its workspace,
+ *     allocated by schur_refine_create for the handle's maximum order and
+ *     released by schur_refine_destroy.
+ *   - Work is enqueued on the stream given at creation. Calls that return
+ *     host values (norms, residuals, statuses) synchronize that stream before
+ *     returning; the others return once the work is enqueued, except where
+ *     stated.
+ *   - No C++ exception crosses this interface. A null handle, a null required
+ *     pointer, n < 1 or n above the handle's maximum, or ld < n gives
+ *     SR_ERR_INVALID_ARG and changes nothing.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef SCHUR_REFINE_H
+#define SCHUR_REFINE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct schur_refine_ctx *schur_refine_t;
+
+typedef enum {
+    SR_OK = 0,
+    SR_ERR_INVALID_ARG = 1,
+    /* two diagonal entries of T coincide: the triangular equation has no
+       unique solution (Theorem 1, Sec. 2.1) */
+    SR_ERR_NONDISTINCT = 2,
+    /* a NaN or Inf appeared (Example 3 of Sec. 3 ends this way) */
+    SR_ERR_NONFINITE = 3,
+    /* the stop test did not hold within max_iter passes, or the residual grew
+       tenfold (Alg. 1's "until convergence" not reached) */
+    SR_ERR_NOT_CONVERGED = 4,
+    /* a bounded device-side wait ran out */
+    SR_ERR_TIMEOUT = 5,
+    SR_ERR_CUDA = 6,
+    SR_ERR_OOM = 7,
+    /* the option combination is not built */
+    SR_ERR_UNSUPPORTED = 8
+} sr_status;
+
+/* element type of A and Q */
+enum { SR_REAL = 0, SR_COMPLEX = 1 };
+/* working high precision */
+enum { SR_TARGET_FP64 = 0 };
+/* engine of the high-precision products (Sec. 2.4: "hp matrix-matrix
+   multiplications"; the paper uses the Ozaki scheme, Sec. 3) */
+enum {
+    SR_HP_FP64 = 0,       /* native FP64 arithmetic */
+    SR_HP_OZAKI_BF16 = 1  /* FP64 products emulated by splitting into bf16
+                             slices multiplied exactly on tensor cores */
+};
+/* low precision of the solve and of the products YW, W^2, W^3 (Alg. 4) */
+enum { SR_LP_FP32 = 0, SR_LP_FP64 = 1 };
+/* element type of the starting factor Qhat */
+enum { SR_QHAT_FP32 = 0, SR_QHAT_FP64 = 1 };
+
+typedef struct {
+    int dtype;        /* SR_REAL or SR_COMPLEX */
+    int target;       /* SR_TARGET_FP64 */
+    int hp_gemm;      /* SR_HP_FP64 or SR_HP_OZAKI_BF16 */
+    int lp;           /* SR_LP_FP32 (mixed form) or SR_LP_FP64 (all-FP64 form) */
+    int qhat_type;    /* SR_QHAT_FP32 or SR_QHAT_FP64 */
+    int full_sigma;   /* 1: keep W^2 Y + W^2 Y W in Sigma (eq. NSmerged);
+                         0 (default): drop them, as Sec. 2.4 does */
+    int max_iter;     /* passes of the REPEAT loop; <= 0 selects 10 */
+    int ozaki_slices; /* bf16 slices per operand of the emulated products;
+                         <= 0 selects the library default (7) */
+    double tol;       /* stop when ||stril(T^)||_F / ||A||_F <= tol and the
+                         last ||Q^H Q - I||_F <= sqrt(tol); <= 0 selects
+                         1e-14 * sqrt(n) */
+    int profile;      /* 1: time every phase with CUDA events on the handle's
+                         stream (see schur_refine_get_profile) */
+} sr_options;
+
+/* Fills *opt with the defaults: real, FP64 target, native FP64 products,
+   FP32 low precision, FP32 Qhat, truncated Sigma. */
+void schur_refine_default_options(sr_options *opt);
+
+typedef struct {
+    double stril_rel;  /* ||stril(Q^H A Q)||_F / ||A||_F at the last T^ formed */
+    double orth;       /* ||Q^H Q - I||_F at the last Y formed (or of Qhat) */
+    double w_norm;     /* ||W||_F of the last update, W = L - L^H */
+    int iters;         /* passes = number of T^ formed */
+    int hp_gemms;      /* high-precision products issued (4 per pass, Tables 3/4) */
+} sr_norms;
+
+/*
+ * Creates a handle for orders up to n_max with the given options (NULL for
+ * the defaults) and allocates its workspace on the current device. The
+ * handle enqueues all work on cuda_stream (a cudaStream_t; NULL is the legacy
+ * default stream). On failure *h is set to NULL.
+ * Errors: SR_ERR_INVALID_ARG (h NULL, n_max < 1, bad option value),
+ * SR_ERR_UNSUPPORTED (option combination not built), SR_ERR_OOM, SR_ERR_CUDA.
+ */
+sr_status schur_refine_create(schur_refine_t *h, int n_max, const sr_options *opt,
+                              void *cuda_stream);
+
+/*
+ * Runs Alg. 4 (Sec. 2.4) on one matrix of order n <= n_max.
+ *   dA        device, n x n, lda: A in FP64 (interleaved complex128 when
+ *             dtype is SR_COMPLEX). Not modified.
+ *   dQ        device, n x n, ldq, FP64 (complex128). In: the starting factor
+ *             when dQhat is NULL. Out: the refined factor.
+ *   dQhat     device, n x n with leading dimension ldq, element type
+ *             qhat_type (complex64/complex128 when complex), or NULL. When
+ *             given, Q is first set to one Newton-Schulz step of Qhat
+ *             converted to FP64 (Alg. 4, second line; eq. NS), and dQ's input
+ *             value is ignored.
+ *   dT        device, n x n, ld n, FP64, or NULL: receives T^ = Q^H A Q of the
+ *             last pass (its upper triangle is the Schur factor T).
+ *   out       host, or NULL: norms and counters of the run.
+ * Each pass forms T^ (2 products); if the stop test holds the run ends,
+ * otherwise it solves for L, forms Y (1 product) and updates Q (1 product).
+ * Returns SR_OK when the stop test held, SR_ERR_NOT_CONVERGED after max_iter
+ * passes or when the residual grew tenfold after the second pass,
+ * SR_ERR_NONDISTINCT / SR_ERR_NONFINITE when the solve failed (dQ then holds
+ * the factor from before the failed update). Synchronizes the stream once per
+ * pass to read the residual norm.
+ */
+sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, void *dQ, int ldq,
+                            const void *dQhat, void *dT, sr_norms *out);
+
+/*
+ * Refines `batch` independent matrices of orders n[b] <= n_max (host array),
+ * each exactly as schur_refine_step with dQhat given.
+ *   dA[b], dQ[b], dQhat[b]: host arrays of device pointers to column-major
+ *   matrices with leading dimension n[b].
+ *   iters_out[b], status_out[b]: host arrays (may be NULL) receiving each
+ *   matrix's pass count and status.
+ * Returns SR_OK if every matrix converged, else the first non-OK status in
+ * batch order.
+ */
+sr_status schur_refine_batched(schur_refine_t h, int batch, const int *n, const void *const *dA,
+                               void *const *dQ, const void *const *dQhat, int *iters_out,
+                               int *status_out);
+
+/*
+ * The two accuracy measures of Sec. 3 (Examples 2 and 4):
+ *   *stril_rel = ||stril(Q^H A Q)||_F / ||A||_F,  *orth = ||Q^H Q - I||_F,
+ * with every product accumulated in double-double arithmetic (TwoProd/TwoSum)
+ * so that values near 1e-16 are resolved. dA, dQ as in schur_refine_step;
+ * stril_rel, orth: host. Synchronizes the stream.
+ */
+sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int lda, const void *dQ,
+                                 int ldq, double *stril_rel, double *orth);
+
+/*
+ * The low-precision solve alone (Alg. 4, "solve ... in lp, using Alg. 3"):
+ * solves stril(T L - L T) = -E for strictly lower L, order n <= n_max.
+ *   dTE    device, n x n, ld: on entry its upper triangle (with diagonal)
+ *          holds T and its strictly lower triangle holds E, in the handle's
+ *          low precision (float for SR_LP_FP32, double for SR_LP_FP64;
+ *          complex64/complex128 when complex). On exit the strictly lower
+ *          triangle holds L; the upper triangle is unchanged.
+ *   dDiag  device, n entries, FP64 (complex128): the diagonal of T in high
+ *          precision; divisors t_ii - t_jj are formed from it and then
+ *          rounded to the low precision.
+ * Returns SR_ERR_NONDISTINCT on a zero divisor (Theorem 1), SR_ERR_NONFINITE
+ * on a non-finite entry of L. Synchronizes the stream.
+ */
+sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, const void *dDiag);
+
+/*
+ * One high-precision product with the handle's engine, as used for A Q and
+ * Q^H (A Q): C = op(A) B with op(A) = A (transA = 0) or A^H (transA = 1).
+ *   dA  device, FP64 (complex128): m x k (transA = 0) or k x m (transA = 1), lda
+ *   dB  device, k x n, ldb;  dC device, m x n, ldc (overwritten).
+ * Sizes up to n_max in every dimension.
+ */
+sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, const void *dA,
+                            int lda, const void *dB, int ldb, void *dC, int ldc);
+
+/* Phases of the iteration, after the split of Sec. 3, Table 2 ("matrix
+   multiplication" versus "other operations"), refined per kernel family. */
+enum {
+    SR_PROF_HP_GEMM = 0,    /* native FP64 high-precision products */
+    SR_PROF_OZ_SPLIT = 1,   /* emulated products: splitting into bf16 slices */
+    SR_PROF_OZ_MMA = 2,     /* emulated products: tensor-core slice products */
+    SR_PROF_OZ_COMBINE = 3, /* emulated products: FP64 recombination + epilogue */
+    SR_PROF_SOLVE = 4,      /* triangular matrix equation */
+    SR_PROF_LP_GEMM = 5,    /* low-precision products YW, W^2, W^3 */
+    SR_PROF_OTHER = 6,      /* conversions, norms, copies */
+    SR_PROF_KINDS = 8
+};
+
+typedef struct {
+    double ms[SR_PROF_KINDS];        /* device time (CUDA events), 0 unless profile = 1 */
+    long long flops[SR_PROF_KINDS];  /* algorithmic flops: 2mnk per product; for
+                                        SR_PROF_OZ_MMA the bf16 flops issued */
+    long long bytes[SR_PROF_KINDS];  /* algorithmic bytes moved to/from HBM */
+    long long launches[SR_PROF_KINDS]; /* kernels launched by the library */
+    long long spans[SR_PROF_KINDS];  /* timed regions */
+} sr_profile;
+
+/* Accumulated profile since creation or the last reset (synchronizes the
+   stream). out: host. */
+sr_status schur_refine_get_profile(schur_refine_t h, sr_profile *out);
+sr_status schur_refine_reset_profile(schur_refine_t h);
+
+/* Releases the workspace and the handle; NULL is ignored. */
+void schur_refine_destroy(schur_refine_t h);
+
+/* Human-readable name of a status code (static storage). */
+const char *schur_refine_status_string(sr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCHUR_REFINE_H */

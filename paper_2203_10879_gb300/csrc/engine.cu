@@ -1,0 +1,532 @@
+// Host engine and C ABI of the Schur-refinement library: the control flow of
+// Alg. 4 (Sec. 2.4) over the kernels of gemm_simt.cuh, trisolve.cuh,
+// kernels_misc.cuh and the tensor-core products of ozaki.cu.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "gemm_simt.cuh"
+#include "kernels_misc.cuh"
+#include "ozaki.cuh"
+#include "trisolve.cuh"
+
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+void sr_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+struct schur_refine_ctx {
+    int nmax = 0;
+    sr_options opt{};
+    cudaStream_t st = nullptr;
+    int dev = 0;
+    // workspace (ld = nmax)
+    double *AQ = nullptr, *Qw = nullptr, *Y = nullptr, *Delta = nullptr, *diag = nullptr;
+    void *TE = nullptr, *W2 = nullptr, *YW = nullptr, *W2Y = nullptr, *W2YW = nullptr;   // low precision
+    double *partial = nullptr;   // per-block partial sums
+    size_t npartial = 0;
+    double *dnorm = nullptr;     // [0] ||E||^2 [1] ||Y||^2 [2] ||W||^2 [3] ||A||^2 [4..] scratch
+    int *dflags = nullptr;
+    double *hbuf = nullptr;      // pinned host mirror of dnorm (8) + flags
+    sr::OzakiWork oz{};
+    // profiling
+    sr_profile prof{};
+    std::vector<cudaEvent_t> ev_pool;
+    struct Span { int kind; cudaEvent_t a, b; };
+    std::vector<Span> pending;
+    std::vector<cudaEvent_t> open_ev;   // begin events of open phases (stack)
+};
+
+static cudaEvent_t take_event(schur_refine_ctx *h)
+{
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void sr_prof_begin(schur_refine_ctx *h, int kind, long long flops, long long bytes, long long launches)
+{
+    h->prof.flops[kind] += flops;
+    h->prof.bytes[kind] += bytes;
+    h->prof.launches[kind] += launches;
+    if (!h->opt.profile) return;
+    cudaEvent_t a = take_event(h);
+    cudaEventRecord(a, h->st);
+    h->open_ev.push_back(a);
+}
+
+void sr_prof_end(schur_refine_ctx *h, int kind)
+{
+    if (!h->opt.profile || h->open_ev.empty()) return;
+    cudaEvent_t a = h->open_ev.back();
+    h->open_ev.pop_back();
+    cudaEvent_t b = take_event(h);
+    cudaEventRecord(b, h->st);
+    h->pending.push_back({kind, a, b});
+}
+
+// Adds the elapsed times of finished spans (the stream must be idle).
+static void harvest(schur_refine_ctx *h)
+{
+    for (auto &sp : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
+            h->prof.ms[sp.kind] += ms;
+            h->prof.spans[sp.kind] += 1;
+        }
+        h->ev_pool.push_back(sp.a);
+        h->ev_pool.push_back(sp.b);
+    }
+    h->pending.clear();
+    cudaGetLastError();
+}
+
+namespace {
+
+size_t lp_size(const sr_options &o) { return o.lp == SR_LP_FP32 ? sizeof(float) : sizeof(double); }
+
+sr_status check_opts(const sr_options &o)
+{
+    if (o.dtype != SR_REAL && o.dtype != SR_COMPLEX) return SR_ERR_INVALID_ARG;
+    if (o.target != SR_TARGET_FP64) return SR_ERR_INVALID_ARG;
+    if (o.hp_gemm != SR_HP_FP64 && o.hp_gemm != SR_HP_OZAKI_BF16) return SR_ERR_INVALID_ARG;
+    if (o.lp != SR_LP_FP32 && o.lp != SR_LP_FP64) return SR_ERR_INVALID_ARG;
+    if (o.qhat_type != SR_QHAT_FP32 && o.qhat_type != SR_QHAT_FP64) return SR_ERR_INVALID_ARG;
+    if (o.ozaki_slices > sr::kOzakiMaxSlices) return SR_ERR_INVALID_ARG;
+    if (o.dtype == SR_COMPLEX) return SR_ERR_UNSUPPORTED;
+    if (o.hp_gemm == SR_HP_OZAKI_BF16 && !sr::kOzakiBuilt) return SR_ERR_UNSUPPORTED;
+    return SR_OK;
+}
+
+double tol_of(const schur_refine_ctx *h, int n)
+{
+    return h->opt.tol > 0 ? h->opt.tol : 1e-14 * sqrt((double)n);
+}
+
+sr_status reduce_to(schur_refine_ctx *h, int count, int slot)
+{
+    SrPhase ph(h, SR_PROF_OTHER, 0, (long long)count * 8, 1);
+    sr::reduce_partials_kernel<<<1, 256, 0, h->st>>>(h->partial, count, h->dnorm + slot);
+    SR_CUDA_TRY(cudaGetLastError());
+    return SR_OK;
+}
+
+// Frobenius norm^2 of (part of) a matrix into dnorm[slot].
+template <typename T>
+sr_status sumsq(schur_refine_ctx *h, int n, const T *M, int ld, int part, int slot)
+{
+    const int blocks = (int)std::min<size_t>(1024, h->npartial);
+    {
+    SrPhase ph(h, SR_PROF_OTHER, 2LL * n * n, (long long)n * n * (long long)sizeof(T), 1);
+    sr::sumsq_kernel<T><<<blocks, 256, 0, h->st>>>(n, M, ld, part, h->partial);
+    SR_CUDA_TRY(cudaGetLastError());
+    }
+    return reduce_to(h, blocks, slot);
+}
+
+// copy dnorm (and flags) to the pinned host mirror and wait
+sr_status read_back(schur_refine_ctx *h)
+{
+    SR_CUDA_TRY(cudaMemcpyAsync(h->hbuf, h->dnorm, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    SR_CUDA_TRY(cudaMemcpyAsync(h->hbuf + 8, h->dflags, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+    return SR_OK;
+}
+
+int host_flags(const schur_refine_ctx *h)
+{
+    int f;
+    memcpy(&f, h->hbuf + 8, sizeof(int));
+    return f;
+}
+
+// ---- high-precision product with the handle's engine ---------------------------
+// C = op(A) B (m x n, inner k) fed to epilogue ep; when slot >= 0 the epilogue's
+// returned values are summed into dnorm[slot].
+template <class EP>
+sr_status hp_gemm(schur_refine_ctx *h, bool transA, int m, int n, int k, const double *A, int lda,
+                  const double *B, int ldb, EP ep, int slot)
+{
+    double *part = slot >= 0 ? h->partial : nullptr;
+    int blocks = 0;
+    if (h->opt.hp_gemm == SR_HP_OZAKI_BF16) {
+        SR_TRY(sr::ozaki_gemm(h, h->st, h->oz, transA, m, n, k, A, lda, B, ldb, ep, part, &blocks,
+                              h->opt.ozaki_slices));
+    } else {
+        SrPhase ph(h, SR_PROF_HP_GEMM, 2LL * m * n * k, 8LL * ((long long)m * k + (long long)k * n + (long long)m * n), 1);
+        using sr::LoadN;
+        using sr::LoadT;
+        cudaError_t e;
+        if (transA)
+            e = sr::gemm_simt<double>(h->st, m, n, k, LoadT<double, double>{A, lda}, LoadN<double, double>{B, ldb},
+                                      ep, part);
+        else
+            e = sr::gemm_simt<double>(h->st, m, n, k, LoadN<double, double>{A, lda}, LoadN<double, double>{B, ldb},
+                                      ep, part);
+        SR_CUDA_TRY(e);
+        blocks = sr::simt_blocks<double>(m, n);
+    }
+    if (slot >= 0) SR_TRY(reduce_to(h, blocks, slot));
+    return SR_OK;
+}
+
+// ---- one pass pieces -------------------------------------------------------------
+
+// S1 + S2: AQ = A Q, T^ = Q^H (A Q) with the split epilogue, ||E||^2 -> dnorm[0]
+template <typename Tl>
+sr_status form_residual(schur_refine_ctx *h, int n, const double *A, int lda, const double *Q, int ldq,
+                        double *That)
+{
+    const int ld = h->nmax;
+    SR_TRY(hp_gemm(h, false, n, n, n, A, lda, Q, ldq, sr::EpStore{h->AQ, ld}, -1));
+    sr::EpSplit<Tl> ep{(Tl *)h->TE, ld, h->diag, That, n};
+    SR_TRY(hp_gemm(h, true, n, n, n, Q, ldq, h->AQ, ld, ep, 0));
+    return SR_OK;
+}
+
+// S4: solve in low precision; ||L||^2 -> dnorm[2]
+template <typename Tl>
+sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const double *dhp)
+{
+    const int NB = (n + sr::kSolveTile - 1) / sr::kSolveTile;
+    SrPhase ph(h, SR_PROF_SOLVE, 2LL * n * n * n / 3, (long long)n * n * (long long)sizeof(Tl), NB);
+    SR_CUDA_TRY(sr::trisolve_wavefront<Tl>(h->st, n, TE, ld, dhp, h->dflags));
+    return SR_OK;
+}
+
+// S5-S8: Y = Q^H Q - I, products in lp, Delta, Q_new = Q + 1/2 Q Delta
+template <typename Tl>
+sr_status update(schur_refine_ctx *h, int n, const double *Q, int ldq, double *Qn, int ldn)
+{
+    using sr::LoadN;
+    using sr::LoadSkew;
+    const int ld = h->nmax;
+    SR_TRY(hp_gemm(h, true, n, n, n, Q, ldq, Q, ldq, sr::EpMinusI{h->Y, ld}, 1));
+    const Tl *L = (const Tl *)h->TE;
+    Tl *W2 = (Tl *)h->W2, *YW = (Tl *)h->YW;
+    LoadSkew<Tl, Tl> w{L, ld};
+    const long long f1 = 2LL * n * n * n, b1 = 4LL * n * n * (long long)sizeof(Tl);
+    {
+    SrPhase ph(h, SR_PROF_LP_GEMM, f1 * (h->opt.full_sigma ? 5 : 3), b1 * (h->opt.full_sigma ? 5 : 3),
+               h->opt.full_sigma ? 5 : 3);
+    SR_CUDA_TRY(sr::gemm_simt<Tl>(h->st, n, n, n, w, w, sr::EpStoreLp<Tl>{W2, ld}, nullptr));
+    SR_CUDA_TRY(sr::gemm_simt<Tl>(h->st, n, n, n, LoadN<Tl, double>{h->Y, ld}, w, sr::EpStoreLp<Tl>{YW, ld},
+                                  nullptr));
+    Tl *W2Y = nullptr, *W2YW = nullptr;
+    if (h->opt.full_sigma) {
+        W2Y = (Tl *)h->W2Y;
+        W2YW = (Tl *)h->W2YW;
+        SR_CUDA_TRY(sr::gemm_simt<Tl>(h->st, n, n, n, LoadN<Tl, Tl>{W2, ld}, LoadN<Tl, double>{h->Y, ld},
+                                      sr::EpStoreLp<Tl>{W2Y, ld}, nullptr));
+        SR_CUDA_TRY(sr::gemm_simt<Tl>(h->st, n, n, n, LoadN<Tl, Tl>{W2Y, ld}, w, sr::EpStoreLp<Tl>{W2YW, ld},
+                                      nullptr));
+    }
+    sr::EpDelta<Tl> ed{L, ld, h->Y, ld, YW, W2, W2Y, W2YW, ld, h->Delta, ld};
+    SR_CUDA_TRY(sr::gemm_simt<Tl>(h->st, n, n, n, w, LoadN<Tl, Tl>{W2, ld}, ed, nullptr));
+    }
+    SR_TRY(hp_gemm(h, false, n, n, n, Q, ldq, h->Delta, ld, sr::EpUpdate{Q, ldq, Qn, ldn, 0.5}, -1));
+    return SR_OK;
+}
+
+sr_status copy_q(schur_refine_ctx *h, int n, const double *src, int lds, double *dst, int ldd)
+{
+    if (src == dst) return SR_OK;
+    SrPhase ph(h, SR_PROF_OTHER, 0, 16LL * n * n, 1);
+    SR_CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)ldd * sizeof(double), src, (size_t)lds * sizeof(double),
+                                  (size_t)n * sizeof(double), n, cudaMemcpyDeviceToDevice, h->st));
+    return SR_OK;
+}
+
+template <typename Tl>
+sr_status run_step(schur_refine_ctx *h, int n, const double *A, int lda, double *dQ, int ldq, const void *dQhat,
+                   double *dT, sr_norms *out)
+{
+    const int ld = h->nmax;
+    const double tol = tol_of(h, n);
+    const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 10;
+    sr_norms nr{};
+    nr.stril_rel = nr.orth = nr.w_norm = NAN;
+    SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
+    SR_TRY(sumsq<double>(h, n, A, lda, 0, 3));
+
+    // The working factor alternates between the caller's buffer and Qw.
+    double *Qc = dQ, *Qo = h->Qw;
+    int ldc = ldq, ldo = ld;
+    double y_last = NAN;
+    if (dQhat) {
+        // Alg. 4: convert Qhat to hp, then Q <- 1/2 Qhat (3I - Qhat^H Qhat)
+        {
+            dim3 grid((n + 255) / 256, n);
+            SrPhase ph(h, SR_PROF_OTHER, 0, 12LL * n * n, 1);
+            if (h->opt.qhat_type == SR_QHAT_FP32)
+                sr::convert_to_f64_kernel<float><<<grid, 256, 0, h->st>>>(n, (const float *)dQhat, ldq, dQ, ldq);
+            else
+                sr::convert_to_f64_kernel<double><<<grid, 256, 0, h->st>>>(n, (const double *)dQhat, ldq, dQ, ldq);
+            SR_CUDA_TRY(cudaGetLastError());
+        }
+        SR_TRY(hp_gemm(h, true, n, n, n, dQ, ldq, dQ, ldq, sr::EpMinusI{h->Y, ld}, 1));
+        SR_TRY(hp_gemm(h, false, n, n, n, dQ, ldq, h->Y, ld, sr::EpUpdate{dQ, ldq, Qo, ldo, -0.5}, -1));
+        std::swap(Qc, Qo);
+        std::swap(ldc, ldo);
+        nr.hp_gemms += 2;
+        SR_TRY(read_back(h));
+        y_last = sqrt(h->hbuf[1]);
+        nr.orth = y_last;
+    }
+    const double anorm = sqrt(h->hbuf[3] > 0 ? h->hbuf[3] : 1.0);
+    sr_status status = SR_ERR_NOT_CONVERGED;
+    double prev = INFINITY;
+    for (int k = 1; k <= max_iter; ++k) {
+        SR_TRY(form_residual<Tl>(h, n, A, lda, Qc, ldc, dT));
+        nr.hp_gemms += 2;
+        nr.iters = k;
+        SR_TRY(read_back(h));
+        const double anorm2 = sqrt(h->hbuf[3]);
+        const double rT = sqrt(h->hbuf[0]) / (anorm2 > 0 ? anorm2 : anorm);
+        nr.stril_rel = rT;
+        if (!isfinite(rT)) { status = SR_ERR_NONFINITE; break; }
+        const bool ok_y = !(y_last > sqrt(tol));   // NaN (not measured) passes
+        if (rT <= tol && ok_y) { status = SR_OK; break; }
+        if (k >= 3 && rT > 10.0 * prev) { status = SR_ERR_NOT_CONVERGED; break; }
+        prev = rT;
+        SR_TRY(solve<Tl>(h, n, (Tl *)h->TE, ld, h->diag));
+        SR_TRY(sumsq<Tl>(h, n, (const Tl *)h->TE, ld, 1, 2));
+        SR_TRY(read_back(h));
+        const int f = host_flags(h);
+        if (f & SR_FLAG_NONDISTINCT) { status = SR_ERR_NONDISTINCT; break; }
+        if (f & SR_FLAG_NONFINITE) { status = SR_ERR_NONFINITE; break; }
+        nr.w_norm = sqrt(2.0 * h->hbuf[2]);
+        SR_TRY(update<Tl>(h, n, Qc, ldc, Qo, ldo));
+        nr.hp_gemms += 2;
+        std::swap(Qc, Qo);
+        std::swap(ldc, ldo);
+        SR_TRY(read_back(h));
+        y_last = sqrt(h->hbuf[1]);
+        nr.orth = y_last;
+        status = SR_ERR_NOT_CONVERGED;
+    }
+    SR_TRY(copy_q(h, n, Qc, ldc, dQ, ldq));
+    SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+    harvest(h);
+    if (out) *out = nr;
+    return status;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+void schur_refine_default_options(sr_options *opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->dtype = SR_REAL;
+    opt->target = SR_TARGET_FP64;
+    opt->hp_gemm = SR_HP_FP64;
+    opt->lp = SR_LP_FP32;
+    opt->qhat_type = SR_QHAT_FP32;
+    opt->full_sigma = 0;
+    opt->max_iter = 10;
+    opt->ozaki_slices = 0;
+    opt->tol = 0.0;
+}
+
+const char *schur_refine_status_string(sr_status s)
+{
+    switch (s) {
+    case SR_OK: return "ok";
+    case SR_ERR_INVALID_ARG: return "invalid argument";
+    case SR_ERR_NONDISTINCT: return "diagonal entries of T not pairwise distinct";
+    case SR_ERR_NONFINITE: return "non-finite value";
+    case SR_ERR_NOT_CONVERGED: return "not converged";
+    case SR_ERR_TIMEOUT: return "device wait timed out";
+    case SR_ERR_CUDA: return "CUDA error";
+    case SR_ERR_OOM: return "out of device memory";
+    case SR_ERR_UNSUPPORTED: return "unsupported option combination";
+    }
+    return "unknown status";
+}
+
+sr_status schur_refine_get_profile(schur_refine_t h, sr_profile *out)
+{
+    if (!h || !out) return SR_ERR_INVALID_ARG;
+    SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+    harvest(h);
+    *out = h->prof;
+    return SR_OK;
+}
+
+sr_status schur_refine_reset_profile(schur_refine_t h)
+{
+    if (!h) return SR_ERR_INVALID_ARG;
+    SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+    harvest(h);
+    memset(&h->prof, 0, sizeof(h->prof));
+    return SR_OK;
+}
+
+void schur_refine_destroy(schur_refine_t h)
+{
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    harvest(h);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    cudaFree(h->AQ);
+    cudaFree(h->Qw);
+    cudaFree(h->Y);
+    cudaFree(h->Delta);
+    cudaFree(h->diag);
+    cudaFree(h->TE);
+    cudaFree(h->W2);
+    cudaFree(h->YW);
+    cudaFree(h->W2Y);
+    cudaFree(h->W2YW);
+    cudaFree(h->partial);
+    cudaFree(h->dnorm);
+    cudaFree(h->dflags);
+    if (h->hbuf) cudaFreeHost(h->hbuf);
+    sr::ozaki_free(h->oz);
+    delete h;
+}
+
+sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *opt, void *cuda_stream)
+{
+    if (!hp) return SR_ERR_INVALID_ARG;
+    *hp = nullptr;
+    if (n_max < 1 || n_max > 32768) return SR_ERR_INVALID_ARG;
+    sr_options o;
+    schur_refine_default_options(&o);
+    if (opt) o = *opt;
+    SR_TRY(check_opts(o));
+    schur_refine_ctx *h = new schur_refine_ctx();
+    h->nmax = n_max;
+    h->opt = o;
+    h->st = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&h->dev);
+    const size_t nn = (size_t)n_max * (size_t)n_max;
+    const size_t lps = lp_size(o);
+    const size_t tiles16 = ((size_t)(n_max + 15) / 16) * ((size_t)(n_max + 15) / 16);
+    h->npartial = std::max<size_t>(tiles16, 4096);
+    cudaError_t e = cudaSuccess;
+#define SR_ALLOC(ptr, bytes)                                             \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes));
+    SR_ALLOC(h->AQ, nn * sizeof(double));
+    SR_ALLOC(h->Qw, nn * sizeof(double));
+    SR_ALLOC(h->Y, nn * sizeof(double));
+    SR_ALLOC(h->Delta, nn * sizeof(double));
+    SR_ALLOC(h->diag, (size_t)n_max * sizeof(double));
+    SR_ALLOC(h->TE, nn * lps);
+    SR_ALLOC(h->W2, nn * lps);
+    SR_ALLOC(h->YW, nn * lps);
+    if (o.full_sigma) {
+        SR_ALLOC(h->W2Y, nn * lps);
+        SR_ALLOC(h->W2YW, nn * lps);
+    }
+    SR_ALLOC(h->partial, h->npartial * sizeof(double));
+    SR_ALLOC(h->dnorm, 8 * sizeof(double));
+    SR_ALLOC(h->dflags, sizeof(int));
+#undef SR_ALLOC
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hbuf, 16 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(h->dnorm, 0, 8 * sizeof(double));
+    if (e == cudaSuccess && o.hp_gemm == SR_HP_OZAKI_BF16) e = sr::ozaki_alloc(h->oz, n_max, o.ozaki_slices);
+    if (e != cudaSuccess) {
+        sr_set_last_cuda_error(e);
+        schur_refine_destroy(h);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
+    }
+    memset(h->hbuf, 0, 16 * sizeof(double));
+    *hp = h;
+    return SR_OK;
+}
+
+sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, void *dQ, int ldq, const void *dQhat,
+                            void *dT, sr_norms *out)
+{
+    if (!h || !dA || !dQ || n < 1 || n > h->nmax || lda < n || ldq < n) return SR_ERR_INVALID_ARG;
+    if (h->opt.lp == SR_LP_FP32)
+        return run_step<float>(h, n, (const double *)dA, lda, (double *)dQ, ldq, dQhat, (double *)dT, out);
+    return run_step<double>(h, n, (const double *)dA, lda, (double *)dQ, ldq, dQhat, (double *)dT, out);
+}
+
+sr_status schur_refine_batched(schur_refine_t h, int batch, const int *n, const void *const *dA, void *const *dQ,
+                               const void *const *dQhat, int *iters_out, int *status_out)
+{
+    if (!h || batch < 0 || (batch > 0 && (!n || !dA || !dQ))) return SR_ERR_INVALID_ARG;
+    for (int b = 0; b < batch; ++b)
+        if (n[b] < 1 || n[b] > h->nmax || !dA[b] || !dQ[b]) return SR_ERR_INVALID_ARG;
+    sr_status first = SR_OK;
+    for (int b = 0; b < batch; ++b) {
+        sr_norms nr{};
+        sr_status s = schur_refine_step(h, n[b], dA[b], n[b], dQ[b], n[b], dQhat ? dQhat[b] : nullptr, nullptr, &nr);
+        if (iters_out) iters_out[b] = nr.iters;
+        if (status_out) status_out[b] = (int)s;
+        if (s != SR_OK && first == SR_OK) first = s;
+        if (s == SR_ERR_CUDA) return s;
+    }
+    return first;
+}
+
+sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int lda, const void *dQ, int ldq,
+                                 double *stril_rel, double *orth)
+{
+    if (!h || !dA || !dQ || !stril_rel || !orth || n < 1 || n > h->nmax || lda < n || ldq < n)
+        return SR_ERR_INVALID_ARG;
+    const int ld = h->nmax;
+    const double *A = (const double *)dA, *Q = (const double *)dQ;
+    const size_t tiles = (size_t)((n + 15) / 16) * (size_t)((n + 15) / 16);
+    if (tiles > h->npartial) return SR_ERR_INVALID_ARG;
+    dim3 grid((n + 15) / 16, (n + 15) / 16);
+    // M = A Q in double-double: hi in AQ, lo in Delta
+    sr::gemm_dd_kernel<0><<<grid, 256, 0, h->st>>>(n, 0, A, lda, Q, nullptr, ldq, h->AQ, h->Delta, ld, nullptr);
+    SR_CUDA_TRY(cudaGetLastError());
+    sr::gemm_dd_kernel<1><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, h->AQ, h->Delta, ld, nullptr, nullptr, 0,
+                                                   h->partial);
+    SR_CUDA_TRY(cudaGetLastError());
+    SR_TRY(reduce_to(h, (int)tiles, 4));
+    sr::gemm_dd_kernel<2><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, Q, nullptr, ldq, nullptr, nullptr, 0, h->partial);
+    SR_CUDA_TRY(cudaGetLastError());
+    SR_TRY(reduce_to(h, (int)tiles, 5));
+    SR_TRY(sumsq<double>(h, n, A, lda, 0, 6));
+    SR_TRY(read_back(h));
+    *stril_rel = sqrt(h->hbuf[4]) / sqrt(h->hbuf[6]);
+    *orth = sqrt(h->hbuf[5]);
+    return SR_OK;
+}
+
+sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, const void *dDiag)
+{
+    if (!h || !dTE || !dDiag || n < 1 || n > h->nmax || ld < n) return SR_ERR_INVALID_ARG;
+    SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
+    if (h->opt.lp == SR_LP_FP32)
+        SR_TRY(solve<float>(h, n, (float *)dTE, ld, (const double *)dDiag));
+    else
+        SR_TRY(solve<double>(h, n, (double *)dTE, ld, (const double *)dDiag));
+    SR_TRY(read_back(h));
+    const int f = host_flags(h);
+    if (f & SR_FLAG_NONDISTINCT) return SR_ERR_NONDISTINCT;
+    if (f & SR_FLAG_NONFINITE) return SR_ERR_NONFINITE;
+    return SR_OK;
+}
+
+sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, const void *dA, int lda,
+                            const void *dB, int ldb, void *dC, int ldc)
+{
+    if (!h || !dA || !dB || !dC || m < 1 || n < 1 || k < 1) return SR_ERR_INVALID_ARG;
+    if (m > h->nmax || n > h->nmax || k > h->nmax) return SR_ERR_INVALID_ARG;
+    if (lda < (transA ? k : m) || ldb < k || ldc < m) return SR_ERR_INVALID_ARG;
+    SR_TRY(hp_gemm(h, transA != 0, m, n, k, (const double *)dA, lda, (const double *)dB, ldb,
+                   sr::EpStore{(double *)dC, ldc}, -1));
+    SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+    return SR_OK;
+}
+
+}  // extern "C"

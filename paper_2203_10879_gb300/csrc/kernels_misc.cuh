@@ -1,0 +1,230 @@
+// Epilogues of the products of Alg. 4, small elementwise kernels and the
+// double-double residual kernel.
+#pragma once
+#include "common.cuh"
+
+namespace sr {
+
+// ---- epilogues (value v of the finished product entry (i, j)) ---------------
+
+// plain store of a high-precision product (A Q)
+struct EpStore {
+    double *C; int ld;
+    template <typename V>
+    __device__ double operator()(int i, int j, V v) const { C[sr_idx(i, j, ld)] = (double)v; return 0.0; }
+};
+
+// plain store in low precision (W^2, YW, ...)
+template <typename Tl>
+struct EpStoreLp {
+    Tl *C; int ld;
+    template <typename V>
+    __device__ double operator()(int i, int j, V v) const { C[sr_idx(i, j, ld)] = (Tl)v; return 0.0; }
+};
+
+// T^ = Q^H (A Q): the whole T^ goes to the low-precision buffer TE (upper
+// triangle = T, strictly lower = E, Alg. 4 "set E, T and convert to lp"),
+// its diagonal to `diag` in high precision (divisors of the solve), T^ to
+// `That` in high precision when requested; returns e_ij^2 for ||E||_F.
+template <typename Tl>
+struct EpSplit {
+    Tl *TE; int ldte; double *diag; double *That; int ldt;
+    template <typename V>
+    __device__ double operator()(int i, int j, V v) const
+    {
+        const double x = (double)v;
+        TE[sr_idx(i, j, ldte)] = (Tl)x;
+        if (That) That[sr_idx(i, j, ldt)] = x;
+        if (i == j) diag[i] = x;
+        return i > j ? x * x : 0.0;
+    }
+};
+
+// Y = Q^H Q - I; returns y_ij^2 for ||Y||_F.
+struct EpMinusI {
+    double *Y; int ld;
+    template <typename V>
+    __device__ double operator()(int i, int j, V v) const
+    {
+        const double y = (i == j) ? (double)v - 1.0 : (double)v;
+        Y[sr_idx(i, j, ld)] = y;
+        return y * y;
+    }
+};
+
+// Q_new = Q + alpha * (product):  alpha = 1/2 with product Q Delta gives
+// 1/2 Q Sigma (Alg. 4, last step); alpha = -1/2 with Q Y0 gives the initial
+// Newton-Schulz step 1/2 Q (3I - Q^H Q) (eq. NS).
+struct EpUpdate {
+    const double *Q; int ldq; double *Qn; int ldn; double alpha;
+    template <typename V>
+    __device__ double operator()(int i, int j, V v) const
+    {
+        Qn[sr_idx(i, j, ldn)] = Q[sr_idx(i, j, ldq)] + alpha * (double)v;
+        return 0.0;
+    }
+};
+
+// Delta = Sigma - 2I = 2W - Y - YW + W^2 + W^3 (+ W^2 Y + W^2 Y W), summed in
+// high precision (Alg. 4: "compute Sigma ... in hp"); v is the entry of W^3.
+template <typename Tl>
+struct EpDelta {
+    const Tl *L; int ldl;       // W = L - L^H from the strictly lower part
+    const double *Y; int ldy;
+    const Tl *YW, *W2, *W2Y, *W2YW; int ldp;   // W2Y, W2YW may be null
+    double *Delta; int ldd;
+    template <typename V>
+    __device__ double operator()(int i, int j, V v) const
+    {
+        double w = 0.0;
+        if (i > j) w = (double)L[sr_idx(i, j, ldl)];
+        else if (i < j) w = -(double)L[sr_idx(j, i, ldl)];
+        const size_t p = sr_idx(i, j, ldp);
+        double d = 2.0 * w - Y[sr_idx(i, j, ldy)] - (double)YW[p] + (double)W2[p] + (double)v;
+        if (W2Y) d += (double)W2Y[p] + (double)W2YW[p];
+        Delta[sr_idx(i, j, ldd)] = d;
+        return 0.0;
+    }
+};
+
+// ---- small kernels -----------------------------------------------------------
+
+template <typename Tin>
+__global__ void convert_to_f64_kernel(int n, const Tin *__restrict__ src, int lds, double *__restrict__ dst,
+                                      int ldd)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i < n) dst[sr_idx(i, j, ldd)] = (double)src[sr_idx(i, j, lds)];
+}
+
+// partial[block] = sum of squares of the selected part of an n x n matrix
+// (part 0: all, 1: strictly lower).
+template <typename T>
+__global__ void __launch_bounds__(256) sumsq_kernel(int n, const T *__restrict__ M, int ld, int part,
+                                                    double *__restrict__ partial)
+{
+    double s = 0.0;
+    const size_t total = (size_t)n * (size_t)n;
+    for (size_t e = (size_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (size_t)gridDim.x * 256) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        if (part == 1 && i <= j) continue;
+        const double v = (double)M[sr_idx(i, j, ld)];
+        s += v * v;
+    }
+    s = sr_block_sum<256>(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// out[0] = sum of partial[0..count) in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__restrict__ partial, int count,
+                                                             double *__restrict__ out)
+{
+    double s = 0.0;
+    for (int e = threadIdx.x; e < count; e += 256) s += partial[e];
+    s = sr_block_sum<256>(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// ---- double-double residual products -------------------------------------------
+
+struct ddv { double hi, lo; };
+
+__device__ inline ddv dd_two_sum(double a, double b)
+{
+    const double s = a + b;
+    const double z = s - a;
+    return {s, (a - (s - z)) + (b - z)};
+}
+__device__ inline ddv dd_renorm(double a, double b)
+{
+    const double s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ inline ddv dd_plus(ddv a, ddv b)
+{
+    ddv s = dd_two_sum(a.hi, b.hi);
+    const ddv t = dd_two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = dd_renorm(s.hi, s.lo);
+    s.lo += t.lo;
+    return dd_renorm(s.hi, s.lo);
+}
+// exact product a*b as hi + lo, plus a*c folded into the low part
+__device__ inline ddv dd_times(double a, double b, double c)
+{
+    const double p = a * b;
+    double e = fma(a, b, -p);
+    e = fma(a, c, e);
+    return {p, e};
+}
+
+// C = op(A) * (Bhi + Blo) in double-double, 16 x 16 tiles, one entry per thread.
+// mode 0: store C (hi, lo).  mode 1: partial += sum over i > j of (hi + lo)^2.
+// mode 2: partial += sum over all (i, j) of (C - I)^2 (upper tiles only,
+// off-diagonal entries counted twice; C symmetric).
+template <int MODE>
+__global__ void __launch_bounds__(256)
+gemm_dd_kernel(int n, int transA, const double *__restrict__ A, int lda, const double *__restrict__ Bhi,
+               const double *__restrict__ Blo, int ldb, double *__restrict__ Chi, double *__restrict__ Clo,
+               int ldc, double *__restrict__ partial)
+{
+    constexpr int T = 16;
+    __shared__ double As[T][T + 1];
+    __shared__ double Bh[T][T + 1];
+    __shared__ double Bl[T][T + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.x * T, j0 = blockIdx.y * T;
+    const size_t bid = blockIdx.x + (size_t)gridDim.x * blockIdx.y;
+    // tiles that contribute nothing in modes 1 and 2
+    if ((MODE == 1 && i0 + T - 1 <= j0) || (MODE == 2 && i0 > j0 + T - 1)) {
+        if (threadIdx.x == 0) partial[bid] = 0.0;
+        return;
+    }
+    const int i = i0 + tx, j = j0 + ty;
+    ddv acc = {0.0, 0.0};
+    for (int k0 = 0; k0 < n; k0 += T) {
+        // As[kk][ii] = op(A)(i0+ii, k0+kk)
+        {
+            const int ii = transA ? ty : tx, kk = transA ? tx : ty;
+            const int gi = i0 + ii, gk = k0 + kk;
+            double v = 0.0;
+            if (gi < n && gk < n) v = transA ? A[sr_idx(gk, gi, lda)] : A[sr_idx(gi, gk, lda)];
+            As[kk][ii] = v;
+        }
+        {
+            const int gk = k0 + tx, gj = j0 + ty;
+            const bool in = gk < n && gj < n;
+            Bh[tx][ty] = in ? Bhi[sr_idx(gk, gj, ldb)] : 0.0;
+            Bl[tx][ty] = (in && Blo) ? Blo[sr_idx(gk, gj, ldb)] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < T; ++kk) acc = dd_plus(acc, dd_times(As[kk][tx], Bh[kk][ty], Bl[kk][ty]));
+        __syncthreads();
+    }
+    double part = 0.0;
+    if (i < n && j < n) {
+        if (MODE == 0) {
+            Chi[sr_idx(i, j, ldc)] = acc.hi;
+            Clo[sr_idx(i, j, ldc)] = acc.lo;
+        } else if (MODE == 1) {
+            if (i > j) {
+                const double v = acc.hi + acc.lo;
+                part = v * v;
+            }
+        } else {
+            if (i <= j) {
+                if (i == j) acc = dd_plus(acc, {-1.0, 0.0});
+                const double v = acc.hi + acc.lo;
+                part = (i == j ? 1.0 : 2.0) * v * v;
+            }
+        }
+    }
+    if (MODE != 0) {
+        part = sr_block_sum<256>(part);
+        if (threadIdx.x == 0) partial[bid] = part;
+    }
+}
+
+}  // namespace sr
