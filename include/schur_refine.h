@@ -162,6 +162,29 @@ sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int ld
                                  int ldq, double *stril_rel, double *orth);
 
 /*
+ * schur_refine_residuals without a handle and without any device allocation.
+ * The paper has no counterpart; this is a service for callers that cannot
+ * call cudaMalloc -- for example an application whose device memory is owned
+ * by its own pool allocator, or a service that forbids device allocation
+ * after start-up to keep its memory footprint fixed. Creating a handle
+ * allocates a workspace, so those callers use this entry point instead.
+ *   n        order, 1 <= n <= 512; larger orders give SR_ERR_INVALID_ARG
+ *   dA, dQ   device, as in schur_refine_residuals (FP64, real)
+ *   stril_rel, orth   host, as in schur_refine_residuals
+ *   cuda_stream       the cudaStream_t to run on (NULL: legacy default stream)
+ * The scratch (A Q in double-double plus partial sums, about 4 MiB) is a
+ * fixed array inside the library's device image, present on every GPU that
+ * loads the library until the process exits. No cudaMalloc, cudaFree or other
+ * allocating routine is called. All calls on a device share that array:
+ * calls whose GPU work overlaps (other streams or host threads) race and must
+ * be ordered by the caller. The first call on each device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture. Synchronizes cuda_stream.
+ */
+sr_status schur_refine_residuals_noalloc(int n, const void *dA, int lda, const void *dQ, int ldq,
+                                         double *stril_rel, double *orth, void *cuda_stream);
+
+/*
  * The low-precision solve alone (Alg. 4, "solve ... in lp, using Alg. 3"):
  * solves stril(T L - L T) = -E for strictly lower L, order n <= n_max.
  *   dTE    device, n x n, ld: on entry its upper triangle (with diagonal)

@@ -30,7 +30,7 @@ EXPORTS = [
     "schur_refine_default_options", "schur_refine_create", "schur_refine_step",
     "schur_refine_batched", "schur_refine_residuals", "schur_refine_trisolve",
     "schur_refine_gemm", "schur_refine_get_profile", "schur_refine_reset_profile",
-    "schur_refine_destroy", "schur_refine_status_string",
+    "schur_refine_destroy", "schur_refine_status_string", "schur_refine_residuals_noalloc",
 ]
 
 
@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
         L.schur_refine_batched.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(P), ctypes.POINTER(P),
                                            ctypes.POINTER(P), ctypes.POINTER(I), ctypes.POINTER(I)]
         L.schur_refine_residuals.argtypes = [P, I, P, I, P, I, ctypes.POINTER(D), ctypes.POINTER(D)]
+        L.schur_refine_residuals_noalloc.argtypes = [I, P, I, P, I, ctypes.POINTER(D), ctypes.POINTER(D), P]
         L.schur_refine_trisolve.argtypes = [P, I, P, I, P]
         L.schur_refine_gemm.argtypes = [P, I, I, I, I, P, I, P, I, P, I]
         L.schur_refine_get_profile.argtypes = [P, ctypes.POINTER(sr_profile)]
@@ -92,7 +93,8 @@ def lib() -> ctypes.CDLL:
         L.schur_refine_status_string.restype = ctypes.c_char_p
         for f in ("schur_refine_create", "schur_refine_step", "schur_refine_batched",
                   "schur_refine_residuals", "schur_refine_trisolve", "schur_refine_gemm",
-                  "schur_refine_get_profile", "schur_refine_reset_profile"):
+                  "schur_refine_get_profile", "schur_refine_reset_profile",
+                  "schur_refine_residuals_noalloc"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -177,6 +179,21 @@ def schur_refine_residuals(h, n: int, A, Q):
     pq, ldq = _dev(Q, "Q")
     a, b = ctypes.c_double(), ctypes.c_double()
     s = lib().schur_refine_residuals(h, int(n), pa, lda, pq, ldq, ctypes.byref(a), ctypes.byref(b))
+    return s, a.value, b.value
+
+
+def schur_refine_residuals_noalloc(n: int, A, Q, stream=None):
+    """Residuals without a handle or any device allocation (n <= 512).
+
+    For callers that cannot allocate device memory (their memory belongs to a
+    pool allocator, or allocation is forbidden after start-up). Returns
+    (status, stril_rel, orth).
+    """
+    pa, lda = _dev(A, "A")
+    pq, ldq = _dev(Q, "Q")
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = ctypes.c_void_p(int(stream)) if stream is not None else None
+    s = lib().schur_refine_residuals_noalloc(int(n), pa, lda, pq, ldq, ctypes.byref(a), ctypes.byref(b), st)
     return s, a.value, b.value
 
 

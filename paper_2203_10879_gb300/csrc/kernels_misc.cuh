@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) sumsq_kernel(int n, const T *__restrict__
 }
 
 // out[0] = sum of partial[0..count) in a fixed order (deterministic).
-__global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__restrict__ partial, int count,
+static __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__restrict__ partial, int count,
                                                              double *__restrict__ out)
 {
     double s = 0.0;
