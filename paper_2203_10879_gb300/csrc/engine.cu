@@ -147,6 +147,9 @@ int host_flags(const schur_refine_ctx *h)
     return f;
 }
 
+// a bounded device wait ran out somewhere since the flags were cleared
+bool timed_out(const schur_refine_ctx *h) { return (host_flags(h) & SR_FLAG_TIMEOUT) != 0; }
+
 // ---- high-precision product with the handle's engine ---------------------------
 // C = op(A) B (m x n, inner k) fed to epilogue ep; when slot >= 0 the epilogue's
 // returned values are summed into dnorm[slot].
@@ -158,7 +161,7 @@ sr_status hp_gemm(schur_refine_ctx *h, bool transA, int m, int n, int k, const d
     int blocks = 0;
     if (h->opt.hp_gemm == SR_HP_OZAKI_BF16) {
         SR_TRY(sr::ozaki_gemm(h, h->st, h->oz, transA, m, n, k, A, lda, B, ldb, ep, part, &blocks,
-                              h->opt.ozaki_slices));
+                              h->opt.ozaki_slices, h->dflags));
     } else {
         SrPhase ph(h, SR_PROF_HP_GEMM, 2LL * m * n * k, 8LL * ((long long)m * k + (long long)k * n + (long long)m * n), 1);
         using sr::LoadN;
@@ -288,6 +291,7 @@ sr_status run_step(schur_refine_ctx *h, int n, const double *A, int lda, double 
         nr.hp_gemms += 2;
         nr.iters = k;
         SR_TRY(read_back(h));
+        if (timed_out(h)) { status = SR_ERR_TIMEOUT; break; }
         const double anorm2 = sqrt(h->hbuf[3]);
         const double rT = sqrt(h->hbuf[0]) / (anorm2 > 0 ? anorm2 : anorm);
         nr.stril_rel = rT;
@@ -436,7 +440,13 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
 #undef SR_ALLOC
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hbuf, 16 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(h->dnorm, 0, 8 * sizeof(double));
-    if (e == cudaSuccess && o.hp_gemm == SR_HP_OZAKI_BF16) e = sr::ozaki_alloc(h->oz, n_max, o.ozaki_slices);
+    if (e == cudaSuccess && o.hp_gemm == SR_HP_OZAKI_BF16) {
+        if (n_max > sr::kOzakiMaxK) {
+            schur_refine_destroy(h);
+            return SR_ERR_UNSUPPORTED;
+        }
+        e = sr::ozaki_alloc(h->oz, n_max, o.ozaki_slices);
+    }
     if (e != cudaSuccess) {
         sr_set_last_cuda_error(e);
         schur_refine_destroy(h);
@@ -523,9 +533,11 @@ sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, c
     if (!h || !dA || !dB || !dC || m < 1 || n < 1 || k < 1) return SR_ERR_INVALID_ARG;
     if (m > h->nmax || n > h->nmax || k > h->nmax) return SR_ERR_INVALID_ARG;
     if (lda < (transA ? k : m) || ldb < k || ldc < m) return SR_ERR_INVALID_ARG;
+    SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
     SR_TRY(hp_gemm(h, transA != 0, m, n, k, (const double *)dA, lda, (const double *)dB, ldb,
                    sr::EpStore{(double *)dC, ldc}, -1));
-    SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+    SR_TRY(read_back(h));
+    if (timed_out(h)) return SR_ERR_TIMEOUT;
     return SR_OK;
 }
 

@@ -1,0 +1,504 @@
+// Split kernels and the tcgen05 slice-product kernel of the emulated FP64
+// products (see ozaki.cuh for the scheme).
+//
+// Slice-product kernel, one CTA per 128 x 128 output tile, 10 warps:
+//   warp 0      TMA producer: K-blocks of 64 bf16 (128 bytes, 128B swizzle)
+//               of one B digit matrix (MMA "A", 128 rows = output columns j)
+//               and one op(A) digit matrix (MMA "B", 128 rows = output rows i)
+//               into a 4-stage shared-memory ring.
+//   warp 1      allocates 256 TMEM columns (two 128-column FP32 accumulators)
+//               and issues tcgen05.mma (M = N = 128, K = 16) from one thread;
+//               each 256-long K-chunk of one digit pair fills one accumulator.
+//   warps 2..9  drain a full accumulator with tcgen05.ld (warp w reads TMEM
+//               lanes 32*(w%4).., half (w-2)/4 of the columns), convert the
+//               exact FP32 integers to int32 by adding 1.5*2^23 and taking the
+//               bit pattern, and accumulate them per level; at the end of a
+//               level they store the level's int32 plane (column-major).
+// Every wait on an mbarrier is bounded (about 2 s of clock); on expiry the CTA
+// raises SR_FLAG_TIMEOUT, lets every role leave its loop, waits (bounded) for
+// its own TMA loads and MMAs, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "ozaki.cuh"
+
+namespace sr {
+namespace {
+
+constexpr int BM = kOzakiTile;            // MMA M: output columns j (TMEM lanes)
+constexpr int BN = kOzakiTile;            // MMA N: output rows i (TMEM columns)
+constexpr int BK = 64;                    // K per stage: 64 bf16 = 128 bytes
+constexpr int KB_PER_CHUNK = kOzakiKChunk / BK;
+constexpr int STAGES = 4;
+constexpr int TILE_BYTES = BM * BK * 2;   // 16 KiB per operand tile
+constexpr int NUM_THREADS = 320;
+constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+constexpr int SMEM_BYTES = 2 * STAGES * TILE_BYTES + 1024 + 256;
+
+// instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N>>3 at bit 17,
+// M>>4 at bit 24.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.b32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait. Gives up when *abort is set by another role or after
+// WAIT_CYCLES (then sets *abort itself).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+// Bounded wait that ignores the abort flag (used while draining).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *map, uint32_t bar, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct MmaArgs {
+    int s;            // digits per operand
+    int nch;          // K-chunks of 256
+    int Pmax;         // row stride of digit matrices and planes
+    int32_t *planes;  // [s][Pmax][Pmax]
+    int *flags;
+};
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, MmaArgs args)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *tileA = smem;                             // [STAGES][TILE_BYTES]  B digits (rows j)
+    unsigned char *tileB = smem + STAGES * TILE_BYTES;       // [STAGES][TILE_BYTES]  op(A) digits (rows i)
+    uint64_t *bars = (uint64_t *)(smem + 2 * STAGES * TILE_BYTES);
+    uint64_t *full = bars, *empty = bars + STAGES, *accf = bars + 2 * STAGES, *acce = accf + 2, *done = acce + 2;
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    volatile int *abort = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = blockIdx.x * BN, j0 = blockIdx.y * BM;
+    const int s = args.s, nch = args.nch, P = args.Pmax;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < STAGES; ++q) {
+            mbar_init(smem_u32(&full[q]), 1);
+            mbar_init(smem_u32(&empty[q]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&accf[b]), 1);
+            mbar_init(smem_u32(&acce[b]), 8);
+        }
+        mbar_init(smem_u32(done), 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer ----
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t last_phase[STAGES];
+            int issued = 0;
+            bool ok = true;
+            for (int l = 0; l < s && ok; ++l)
+                for (int p = 0; p <= l && ok; ++p) {
+                    const int q = l - p;
+                    for (int c = 0; c < nch && ok; ++c)
+                        for (int kb = 0; kb < KB_PER_CHUNK; ++kb) {
+                            if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1, abort)) { ok = false; break; }
+                            const uint32_t fb = smem_u32(&full[stage]);
+                            mbar_expect_tx(fb, 2 * TILE_BYTES);
+                            const int kc = c * kOzakiKChunk + kb * BK;
+                            tma_load_2d(smem_u32(tileA + stage * TILE_BYTES), &tmB, fb, kc, q * P + j0);
+                            tma_load_2d(smem_u32(tileB + stage * TILE_BYTES), &tmA, fb, kc, p * P + i0);
+                            last_phase[stage] = phase;
+                            ++issued;
+                            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                        }
+                }
+            // wait for the loads still in flight before the CTA may exit
+            const int inflight = issued < STAGES ? issued : STAGES;
+            for (int d = 0; d < inflight; ++d) {
+                stage = (stage + STAGES - 1) % STAGES;
+                mbar_drain(smem_u32(&full[stage]), last_phase[stage]);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            int stage = 0;
+            uint32_t phase = 0;
+            int t = 0;
+            bool ok = true;
+            for (int l = 0; l < s && ok; ++l)
+                for (int p = 0; p <= l && ok; ++p)
+                    for (int c = 0; c < nch && ok; ++c) {
+                        const int b = t & 1;
+                        const uint32_t aph = (t >> 1) & 1;
+                        if (!mbar_wait(smem_u32(&acce[b]), aph ^ 1, abort)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t dt = tmem + (uint32_t)(b * BN);
+                        for (int kb = 0; kb < KB_PER_CHUNK; ++kb) {
+                            if (!mbar_wait(smem_u32(&full[stage]), phase, abort)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint64_t ad = sdesc_sw128(smem_u32(tileA + stage * TILE_BYTES));
+                            const uint64_t bd = sdesc_sw128(smem_u32(tileB + stage * TILE_BYTES));
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; ++kk)
+                                mma_bf16(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb | kk) != 0);
+                            mma_commit(smem_u32(&empty[stage]));
+                            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                        }
+                        if (!ok) break;
+                        mma_commit(smem_u32(&accf[b]));
+                        ++t;
+                    }
+            // all issued MMAs complete before TMEM is released
+            mma_commit(smem_u32(done));
+            mbar_drain(smem_u32(done), 0);
+        }
+    } else {
+        // ---- epilogue: drain accumulators, exact integer sums per level ----
+        const int ew = warp - 2;
+        const int lg = warp & 3;          // TMEM lane group this warp may access
+        const int half = ew >> 2;         // which 64 columns
+        const int j = j0 + lg * 32 + lane;
+        uint32_t acc[64];
+        int t = 0;
+        bool ok = true;
+        for (int l = 0; l < s && ok; ++l) {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) acc[c] = 0u;
+            uint32_t count = 0;
+            for (int p = 0; p <= l && ok; ++p)
+                for (int c = 0; c < nch; ++c) {
+                    const int b = t & 1;
+                    const uint32_t aph = (t >> 1) & 1;
+                    // one lane polls so the whole warp leaves together on a timeout
+                    int got = 0;
+                    if (lane == 0) got = mbar_wait(smem_u32(&accf[b]), aph, abort) ? 1 : 0;
+                    got = __shfl_sync(0xffffffffu, got, 0);
+                    if (!got) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + half * 64);
+                    uint32_t r[32];
+                    tmem_ld32(ta, r);
+#pragma unroll
+                    for (int x = 0; x < 32; ++x)
+                        acc[x] += __float_as_uint(__fadd_rn(__uint_as_float(r[x]), 12582912.0f));
+                    tmem_ld32(ta + 32, r);
+#pragma unroll
+                    for (int x = 0; x < 32; ++x)
+                        acc[32 + x] += __float_as_uint(__fadd_rn(__uint_as_float(r[x]), 12582912.0f));
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&acce[b]));
+                    ++t;
+                    ++count;
+                }
+            if (!ok) break;
+            const uint32_t bias = count * 0x4B400000u;
+            int32_t *dst = args.planes + (size_t)l * P * P + (size_t)j * P + (size_t)(i0 + half * 64);
+#pragma unroll
+            for (int c = 0; c < 64; c += 4) {
+                int4 v = make_int4((int)(acc[c] - bias), (int)(acc[c + 1] - bias), (int)(acc[c + 2] - bias),
+                                   (int)(acc[c + 3] - bias));
+                *reinterpret_cast<int4 *>(dst + c) = v;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    if (threadIdx.x == 0 && *abort) atomicOr(args.flags, SR_FLAG_TIMEOUT);
+}
+
+// ---- split: X(r, kk) -> s bf16 digit matrices [p][r][kk] and exponents -------------
+// contiguous = 1: X(r, kk) = X[kk + r*ld]; contiguous = 0: X(r, kk) = X[r + kk*ld].
+// One CTA per 32 vectors; the vectors' rows are padded to Pmax, K to Kp (zeros).
+__global__ void __launch_bounds__(256)
+ozaki_split_kernel(int R, int K, int Kp, const double *__restrict__ X, int ld, int contiguous, int s, int Pmax,
+                   int Kmax, __nv_bfloat16 *__restrict__ out, int *__restrict__ exps)
+{
+    __shared__ double tile[32][33];
+    __shared__ unsigned long long smax[32];
+    __shared__ int sexp[32];
+    const int r0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (threadIdx.x < 32) smax[threadIdx.x] = 0ull;
+    __syncthreads();
+
+    auto load_tile = [&](int k0) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            int v, kk;
+            if (contiguous) { kk = k0 + tx; v = ty + 8 * w; } else { v = tx; kk = k0 + ty + 8 * w; }
+            const int r = r0 + v;
+            const double x = (r < R && kk < K) ? (contiguous ? X[(size_t)kk + (size_t)r * ld]
+                                                               : X[(size_t)r + (size_t)kk * ld])
+                                               : 0.0;
+            tile[v][kk - k0] = x;
+        }
+    };
+    // pass 1: largest magnitude per vector (bit patterns of |x| order like the values)
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        load_tile(k0);
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int v = ty + 8 * w;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(tile[v][tx]) & 0x7fffffffffffffffull;
+            atomicMax(&smax[v], b);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 32) {
+        const unsigned long long b = smax[threadIdx.x];
+        const int eb = (int)(b >> 52);
+        int e;
+        if (eb == 0x7ff) e = kOzakiExpNonfinite;          // Inf or NaN in the vector
+        else if (eb == 0) e = -1022;                      // zero or subnormal maximum
+        else e = eb - 1022;                               // max < 2^e
+        sexp[threadIdx.x] = e;
+        exps[r0 + threadIdx.x] = (r0 + threadIdx.x < R) ? e : 0;
+    }
+    __syncthreads();
+    // pass 2: fixed point with F = 7 + 8(s-1) fraction bits, signed base-256 digits
+    const int F = 7 + 8 * (s - 1);
+    for (int k0 = 0; k0 < Kp; k0 += 32) {
+        if (k0 < K) load_tile(k0);
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int v = ty + 8 * w;
+            const int r = r0 + v;
+            const int kk = k0 + tx;
+            const double x = (k0 < K) ? tile[v][tx] : 0.0;
+            const int e = sexp[v];
+            long long Xi = 0;
+            if (e != kOzakiExpNonfinite && kk < K && r < R) {
+                const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+                const int eb = (int)((bits >> 52) & 0x7ff);
+                unsigned long long mant = bits & 0xfffffffffffffull;
+                int ex;
+                if (eb == 0) ex = -1074; else { mant |= 1ull << 52; ex = eb - 1075; }
+                const int sh = ex + F - e;                // x * 2^(F-e) = mant * 2^sh
+                unsigned long long mag;
+                if (mant == 0) mag = 0;
+                else if (sh >= 0) mag = mant << sh;       // sh <= F - 52 here, no overflow
+                else if (-sh >= 64) mag = 0;
+                else mag = (mant + (1ull << (-sh - 1))) >> (-sh);
+                Xi = (bits >> 63) ? -(long long)mag : (long long)mag;
+            }
+            // digits from the least significant: d in [-128, 127]; the top one takes the rest
+            __nv_bfloat16 *o = out + (size_t)r * Kmax + (size_t)kk;
+            const size_t pstride = (size_t)Pmax * Kmax;
+            for (int p = s - 1; p >= 1; --p) {
+                const long long d = ((Xi + 128) & 255) - 128;
+                Xi = (Xi - d) >> 8;
+                o[(size_t)p * pstride] = __int2bfloat16_rn((int)d);
+            }
+            o[0] = __int2bfloat16_rn((int)Xi);
+        }
+        __syncthreads();
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t encode_digits_map(void *map, void *base, int rows, int Kmax)
+{
+    if (!g_encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)Kmax, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kmax * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode((CUtensorMap *)map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t ozaki_alloc(OzakiWork &w, int nmax, int slices)
+{
+    static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+    w.nmax = nmax;
+    w.smax = kOzakiMaxSlices;
+    (void)slices;
+    w.Pmax = (nmax + kOzakiTile - 1) / kOzakiTile * kOzakiTile;
+    w.Kmax = (nmax + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const size_t dig = (size_t)w.smax * w.Pmax * w.Kmax * 2;
+    cudaError_t e = cudaMalloc(&w.Asl, dig);
+    if (e == cudaSuccess) e = cudaMalloc(&w.Bsl, dig);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&w.planes, (size_t)w.smax * w.Pmax * w.Pmax * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&w.ea, (size_t)w.Pmax * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&w.fb, (size_t)w.Pmax * sizeof(int));
+    // digit matrices outside the written rows must read as zero
+    if (e == cudaSuccess) e = cudaMemset(w.Asl, 0, dig);
+    if (e == cudaSuccess) e = cudaMemset(w.Bsl, 0, dig);
+    if (e == cudaSuccess) e = encode_digits_map(w.tmA, w.Asl, w.smax * w.Pmax, w.Kmax);
+    if (e == cudaSuccess) e = encode_digits_map(w.tmB, w.Bsl, w.smax * w.Pmax, w.Kmax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ozaki_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    return e;
+}
+
+void ozaki_free(OzakiWork &w)
+{
+    cudaFree(w.Asl);
+    cudaFree(w.Bsl);
+    cudaFree(w.planes);
+    cudaFree(w.ea);
+    cudaFree(w.fb);
+    w.Asl = w.Bsl = nullptr;
+    w.planes = nullptr;
+    w.ea = w.fb = nullptr;
+}
+
+sr_status ozaki_products(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, bool transA, int m, int n, int k,
+                         const double *A, int lda, const double *B, int ldb, int s, int *flags)
+{
+    if (k > kOzakiMaxK) return SR_ERR_UNSUPPORTED;
+    const int Kp = (k + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const int Mp = (m + kOzakiTile - 1) / kOzakiTile * kOzakiTile;
+    const int Np = (n + kOzakiTile - 1) / kOzakiTile * kOzakiTile;
+    {
+        SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, 8LL * k * (m + n) + 2LL * s * Kp * (Mp + Np), 2);
+        // rows of op(A): columns of A when transposed (contiguous), rows of A otherwise
+        ozaki_split_kernel<<<Mp / 32, 256, 0, st>>>(m, k, Kp, A, lda, transA ? 1 : 0, s, w.Pmax, w.Kmax,
+                                                   (__nv_bfloat16 *)w.Asl, w.ea);
+        SR_CUDA_TRY(cudaGetLastError());
+        ozaki_split_kernel<<<Np / 32, 256, 0, st>>>(n, k, Kp, B, ldb, 1, s, w.Pmax, w.Kmax,
+                                                   (__nv_bfloat16 *)w.Bsl, w.fb);
+        SR_CUDA_TRY(cudaGetLastError());
+    }
+    {
+        const long long pairs = (long long)s * (s + 1) / 2;
+        SrPhase ph(h, SR_PROF_OZ_MMA, pairs * 2LL * Mp * Np * Kp,
+                   pairs * 2LL * Kp * (Mp + Np) + 4LL * s * Mp * Np, 1);
+        MmaArgs a{s, Kp / kOzakiKChunk, w.Pmax, w.planes, flags};
+        dim3 grid(Mp / kOzakiTile, Np / kOzakiTile);
+        ozaki_mma_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.tmA,
+                                                                *(const CUtensorMap *)w.tmB, a);
+        SR_CUDA_TRY(cudaGetLastError());
+    }
+    return SR_OK;
+}
+
+}  // namespace sr
