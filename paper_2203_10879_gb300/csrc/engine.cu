@@ -14,6 +14,23 @@
 #include "ozaki.cuh"
 #include "trisolve.cuh"
 
+void sr::trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long long> &offsets)
+{
+    const int NB = (n + kSolveTile - 1) / kSolveTile;
+    tiles.clear();
+    offsets.assign(1, 0);
+    for (int t = NB - 1; t >= 0; --t) {
+        const int d = t + 1;
+        for (int J = 0; J + t < NB; ++J) tiles.push_back((uint32_t)((J + t) << 16 | J));   // D = t: solve
+        for (int D = t - 1; D >= 0; --D)
+            for (int J = 0; J + D < NB; ++J) {
+                const int I = J + D;
+                if (J + d < NB || I - d >= 0) tiles.push_back((uint32_t)(I << 16 | J));
+            }
+        offsets.push_back((long long)tiles.size());
+    }
+}
+
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void sr_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
 
@@ -25,12 +42,23 @@ struct schur_refine_ctx {
     // workspace (ld = nmax)
     double *AQ = nullptr, *Qw = nullptr, *Y = nullptr, *Delta = nullptr, *diag = nullptr;
     void *TE = nullptr, *W2 = nullptr, *YW = nullptr, *W2Y = nullptr, *W2YW = nullptr;   // low precision
+    double *Wd = nullptr, *W2d = nullptr, *W2Yd = nullptr, *W2YWd = nullptr;   // FP64, emulated-product pass
     double *partial = nullptr;   // per-block partial sums
     size_t npartial = 0;
     double *dnorm = nullptr;     // [0] ||E||^2 [1] ||Y||^2 [2] ||W||^2 [3] ||A||^2 [4..] scratch
     int *dflags = nullptr;
     double *hbuf = nullptr;      // pinned host mirror of dnorm (8) + flags
     sr::OzakiWork oz{};
+    // launch plan of the triangular solve for order plan_n
+    int plan_n = 0;
+    uint32_t *plan = nullptr;
+    size_t plan_cap = 0;
+    std::vector<long long> plan_off;
+    // the solve's two streams of work are captured once per (order, buffers)
+    cudaStream_t cap_st = nullptr, aux_st = nullptr;
+    cudaEvent_t sev0 = nullptr, sev1 = nullptr;
+    struct SolveGraph { int n; const void *TE; int ld; const double *dhp; int fp32; cudaGraphExec_t exec; };
+    std::vector<SolveGraph> graphs;
     // profiling
     sr_profile prof{};
     std::vector<cudaEvent_t> ev_pool;
@@ -195,12 +223,74 @@ sr_status form_residual(schur_refine_ctx *h, int n, const double *A, int lda, co
 }
 
 // S4: solve in low precision; ||L||^2 -> dnorm[2]
+void drop_graphs(schur_refine_ctx *h)
+{
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
+sr_status ensure_plan(schur_refine_ctx *h, int n)
+{
+    if (h->plan_n == n) return SR_OK;
+    drop_graphs(h);   // graphs hold the old plan's pointer and contents
+    std::vector<uint32_t> tiles;
+    sr::trisolve_plan(n, tiles, h->plan_off);
+    if (tiles.size() > h->plan_cap) {
+        // the plan is built once per order; its buffer grows only when needed
+        SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+        cudaFree(h->plan);
+        h->plan = nullptr;
+        h->plan_cap = 0;
+        cudaError_t e = cudaMalloc((void **)&h->plan, tiles.size() * sizeof(uint32_t));
+        if (e != cudaSuccess) {
+            sr_set_last_cuda_error(e);
+            return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
+        }
+        h->plan_cap = tiles.size();
+    }
+    SR_CUDA_TRY(cudaMemcpyAsync(h->plan, tiles.data(), tiles.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                h->st));
+    SR_CUDA_TRY(cudaStreamSynchronize(h->st));   // tiles is a temporary
+    h->plan_n = n;
+    return SR_OK;
+}
+
 template <typename Tl>
 sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const double *dhp)
 {
+    SR_TRY(ensure_plan(h, n));
     const int NB = (n + sr::kSolveTile - 1) / sr::kSolveTile;
-    SrPhase ph(h, SR_PROF_SOLVE, 2LL * n * n * n / 3, (long long)n * n * (long long)sizeof(Tl), NB);
-    SR_CUDA_TRY(sr::trisolve_wavefront<Tl>(h->st, n, TE, ld, dhp, h->dflags));
+    const int fp32 = sizeof(Tl) == 4;
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : h->graphs)
+        if (g.n == n && g.TE == TE && g.ld == ld && g.dhp == dhp && g.fp32 == fp32) exec = g.exec;
+    if (!exec) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t el = sr::trisolve_launches<Tl>(h->cap_st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp,
+                                                       h->dflags, h->plan, h->plan_off);
+            e = cudaStreamEndCapture(h->cap_st, &graph);
+            if (el != cudaSuccess) e = el;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e == cudaSuccess) {
+            h->graphs.push_back({n, TE, ld, dhp, fp32, exec});
+        } else {
+            // no graph (for example while the caller captures this stream): the same
+            // launches, issued directly on the two streams
+            cudaGetLastError();
+            exec = nullptr;
+        }
+    }
+    SrPhase ph(h, SR_PROF_SOLVE, 2LL * n * n * n / 3, (long long)n * n * (long long)sizeof(Tl), 2LL * NB);
+    if (exec) {
+        SR_CUDA_TRY(cudaGraphLaunch(exec, h->st));
+    } else {
+        SR_CUDA_TRY(sr::trisolve_launches<Tl>(h->st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp, h->dflags,
+                                              h->plan, h->plan_off));
+    }
     return SR_OK;
 }
 
@@ -238,6 +328,96 @@ sr_status update(schur_refine_ctx *h, int n, const double *Q, int ldq, double *Q
     return SR_OK;
 }
 
+// ---- the pass on the emulated engine ------------------------------------------------
+// Digits are split once and reused: the columns of Q serve A Q, Q^T (A Q) and
+// Q^T Q; the rows of A are split once per call. The low-precision products use
+// kOzakiLpSlices digits (about 24 bits, FP32-class) and only column splits:
+// W^2 = -W^T W, YW = Y^T W (Y symmetric), W^3 = -W^T W^2, W^2 Y = (W^2)^T Y.
+
+bool oz_pass(const schur_refine_ctx *h) { return h->opt.hp_gemm == SR_HP_OZAKI_BF16 && h->opt.lp == SR_LP_FP32; }
+int oz_s(const schur_refine_ctx *h) { return h->opt.ozaki_slices > 0 ? h->opt.ozaki_slices : sr::kOzakiDefaultSlices; }
+
+// Y = Q^T Q - I from the column digits of Q in slot OZS_COLS; ||Y||^2 -> dnorm[1]
+sr_status oz_gram(schur_refine_ctx *h, int n)
+{
+    const int s = oz_s(h);
+    int blocks = 0;
+    SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_COLS, n, n, n, s, true, h->dflags));
+    SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_COLS, n, n, s, 1.0, true,
+                             sr::EpMinusI{h->Y, h->nmax}, h->partial, &blocks));
+    return reduce_to(h, blocks, 1);
+}
+
+// Q_new = Q + alpha * Q X (rows of Q, columns of X)
+sr_status oz_apply(schur_refine_ctx *h, int n, const double *Q, int ldq, const double *X, int ldx, double *Qn,
+                   int ldn, double alpha)
+{
+    const int s = oz_s(h);
+    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_QROWS, n, n, Q, ldq, sr::OZ_ROWS, false, s));
+    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_X, n, n, X, ldx, sr::OZ_COLS, false, s));
+    SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_QROWS, sr::OZS_X, n, n, n, s, false, h->dflags));
+    return sr::ozaki_combine(h, h->st, h->oz, sr::OZS_QROWS, sr::OZS_X, n, n, s, 1.0, false,
+                             sr::EpUpdate{Q, ldq, Qn, ldn, alpha}, nullptr, nullptr);
+}
+
+sr_status oz_ns_init(schur_refine_ctx *h, int n, const double *Q, int ldq, double *Qn, int ldn)
+{
+    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_COLS, n, n, Q, ldq, sr::OZ_COLS, false, oz_s(h)));
+    SR_TRY(oz_gram(h, n));
+    return oz_apply(h, n, Q, ldq, h->Y, h->nmax, Qn, ldn, -0.5);
+}
+
+sr_status oz_form_residual(schur_refine_ctx *h, int n, const double *Q, int ldq, double *That)
+{
+    const int s = oz_s(h), ld = h->nmax;
+    int blocks = 0;
+    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_COLS, n, n, Q, ldq, sr::OZ_COLS, false, s));
+    SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, n, n, n, s, false, h->dflags));
+    SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, n, n, s, 1.0, false,
+                             sr::EpStore{h->AQ, ld}, nullptr, nullptr));
+    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_X, n, n, h->AQ, ld, sr::OZ_COLS, false, s));
+    SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, n, s, false, h->dflags));
+    SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, s, 1.0, false,
+                             sr::EpSplit<float>{(float *)h->TE, ld, h->diag, That, n}, h->partial, &blocks));
+    return reduce_to(h, blocks, 0);
+}
+
+sr_status oz_update(schur_refine_ctx *h, int n, const double *Q, int ldq, double *Qn, int ldn)
+{
+    using namespace sr;
+    const int ld = h->nmax, sl = kOzakiLpSlices;
+    OzakiWork &w = h->oz;
+    cudaStream_t st = h->st;
+    SR_TRY(oz_gram(h, n));   // Q unchanged since oz_form_residual: its column digits are current
+    {
+        SrPhase ph(h, SR_PROF_OTHER, 0, 12LL * n * n, 1);
+        dim3 grid((n + 31) / 32, (n + 31) / 32);
+        form_skew_kernel<float><<<grid, 256, 0, st>>>(n, (const float *)h->TE, ld, h->Wd, ld);
+        SR_CUDA_TRY(cudaGetLastError());
+    }
+    double *YW = h->AQ;   // A Q is dead after the residual
+    SR_TRY(ozaki_split(h, st, w, OZS_W, n, n, h->Wd, ld, OZ_COLS, false, sl));
+    SR_TRY(ozaki_split(h, st, w, OZS_Y, n, n, h->Y, ld, OZ_COLS, false, sl));
+    SR_TRY(ozaki_product(h, st, w, OZS_W, OZS_W, n, n, n, sl, true, h->dflags));
+    SR_TRY(ozaki_combine(h, st, w, OZS_W, OZS_W, n, n, sl, -1.0, true, EpStore{h->W2d, ld}, nullptr, nullptr));
+    SR_TRY(ozaki_product(h, st, w, OZS_Y, OZS_W, n, n, n, sl, false, h->dflags));
+    SR_TRY(ozaki_combine(h, st, w, OZS_Y, OZS_W, n, n, sl, 1.0, false, EpStore{YW, ld}, nullptr, nullptr));
+    SR_TRY(ozaki_split(h, st, w, OZS_W2, n, n, h->W2d, ld, OZ_COLS, false, sl));
+    if (h->opt.full_sigma) {
+        SR_TRY(ozaki_product(h, st, w, OZS_W2, OZS_Y, n, n, n, sl, false, h->dflags));
+        SR_TRY(ozaki_combine(h, st, w, OZS_W2, OZS_Y, n, n, sl, 1.0, false, EpStore{h->W2Yd, ld}, nullptr,
+                             nullptr));
+        SR_TRY(ozaki_split(h, st, w, 7, n, n, h->W2Yd, ld, OZ_ROWS, false, sl));
+        SR_TRY(ozaki_product(h, st, w, 7, OZS_W, n, n, n, sl, false, h->dflags));
+        SR_TRY(ozaki_combine(h, st, w, 7, OZS_W, n, n, sl, 1.0, false, EpStore{h->W2YWd, ld}, nullptr, nullptr));
+    }
+    SR_TRY(ozaki_product(h, st, w, OZS_W, OZS_W2, n, n, n, sl, false, h->dflags));
+    EpDeltaD ed{h->Wd, h->Y, YW, h->W2d, h->opt.full_sigma ? h->W2Yd : nullptr,
+                h->opt.full_sigma ? h->W2YWd : nullptr, ld, h->Delta, ld};
+    SR_TRY(ozaki_combine(h, st, w, OZS_W, OZS_W2, n, n, sl, -1.0, false, ed, nullptr, nullptr));
+    return oz_apply(h, n, Q, ldq, h->Delta, ld, Qn, ldn, 0.5);
+}
+
 sr_status copy_q(schur_refine_ctx *h, int n, const double *src, int lds, double *dst, int ldd)
 {
     if (src == dst) return SR_OK;
@@ -258,6 +438,8 @@ sr_status run_step(schur_refine_ctx *h, int n, const double *A, int lda, double 
     nr.stril_rel = nr.orth = nr.w_norm = NAN;
     SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
     SR_TRY(sumsq<double>(h, n, A, lda, 0, 3));
+    if (oz_pass(h))   // rows of A: split once, used by every A Q of this call
+        SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_ROWS, n, n, A, lda, sr::OZ_ROWS, false, oz_s(h)));
 
     // The working factor alternates between the caller's buffer and Qw.
     double *Qc = dQ, *Qo = h->Qw;
@@ -274,8 +456,12 @@ sr_status run_step(schur_refine_ctx *h, int n, const double *A, int lda, double 
                 sr::convert_to_f64_kernel<double><<<grid, 256, 0, h->st>>>(n, (const double *)dQhat, ldq, dQ, ldq);
             SR_CUDA_TRY(cudaGetLastError());
         }
-        SR_TRY(hp_gemm(h, true, n, n, n, dQ, ldq, dQ, ldq, sr::EpMinusI{h->Y, ld}, 1));
-        SR_TRY(hp_gemm(h, false, n, n, n, dQ, ldq, h->Y, ld, sr::EpUpdate{dQ, ldq, Qo, ldo, -0.5}, -1));
+        if (oz_pass(h)) {
+            SR_TRY(oz_ns_init(h, n, dQ, ldq, Qo, ldo));
+        } else {
+            SR_TRY(hp_gemm(h, true, n, n, n, dQ, ldq, dQ, ldq, sr::EpMinusI{h->Y, ld}, 1));
+            SR_TRY(hp_gemm(h, false, n, n, n, dQ, ldq, h->Y, ld, sr::EpUpdate{dQ, ldq, Qo, ldo, -0.5}, -1));
+        }
         std::swap(Qc, Qo);
         std::swap(ldc, ldo);
         nr.hp_gemms += 2;
@@ -287,7 +473,10 @@ sr_status run_step(schur_refine_ctx *h, int n, const double *A, int lda, double 
     sr_status status = SR_ERR_NOT_CONVERGED;
     double prev = INFINITY;
     for (int k = 1; k <= max_iter; ++k) {
-        SR_TRY(form_residual<Tl>(h, n, A, lda, Qc, ldc, dT));
+        if (oz_pass(h))
+            SR_TRY(oz_form_residual(h, n, Qc, ldc, dT));
+        else
+            SR_TRY(form_residual<Tl>(h, n, A, lda, Qc, ldc, dT));
         nr.hp_gemms += 2;
         nr.iters = k;
         SR_TRY(read_back(h));
@@ -307,7 +496,10 @@ sr_status run_step(schur_refine_ctx *h, int n, const double *A, int lda, double 
         if (f & SR_FLAG_NONDISTINCT) { status = SR_ERR_NONDISTINCT; break; }
         if (f & SR_FLAG_NONFINITE) { status = SR_ERR_NONFINITE; break; }
         nr.w_norm = sqrt(2.0 * h->hbuf[2]);
-        SR_TRY(update<Tl>(h, n, Qc, ldc, Qo, ldo));
+        if (oz_pass(h))
+            SR_TRY(oz_update(h, n, Qc, ldc, Qo, ldo));
+        else
+            SR_TRY(update<Tl>(h, n, Qc, ldc, Qo, ldo));
         nr.hp_gemms += 2;
         std::swap(Qc, Qo);
         std::swap(ldc, ldo);
@@ -393,6 +585,16 @@ void schur_refine_destroy(schur_refine_t h)
     cudaFree(h->YW);
     cudaFree(h->W2Y);
     cudaFree(h->W2YW);
+    cudaFree(h->Wd);
+    cudaFree(h->W2d);
+    cudaFree(h->W2Yd);
+    cudaFree(h->W2YWd);
+    drop_graphs(h);
+    if (h->cap_st) cudaStreamDestroy(h->cap_st);
+    if (h->aux_st) cudaStreamDestroy(h->aux_st);
+    if (h->sev0) cudaEventDestroy(h->sev0);
+    if (h->sev1) cudaEventDestroy(h->sev1);
+    cudaFree(h->plan);
     cudaFree(h->partial);
     cudaFree(h->dnorm);
     cudaFree(h->dflags);
@@ -439,13 +641,28 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     SR_ALLOC(h->dflags, sizeof(int));
 #undef SR_ALLOC
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hbuf, 16 * sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux_st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->sev0, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->sev1, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(h->dnorm, 0, 8 * sizeof(double));
     if (e == cudaSuccess && o.hp_gemm == SR_HP_OZAKI_BF16) {
         if (n_max > sr::kOzakiMaxK) {
             schur_refine_destroy(h);
             return SR_ERR_UNSUPPORTED;
         }
-        e = sr::ozaki_alloc(h->oz, n_max, o.ozaki_slices);
+        const int shp = o.ozaki_slices > 0 ? o.ozaki_slices : sr::kOzakiDefaultSlices;
+        const bool lp_oz = o.lp == SR_LP_FP32;
+        int caps[sr::kOzakiSlots] = {shp, shp, shp, shp, 0, 0, 0, 0};
+        if (lp_oz) {
+            caps[sr::OZS_W] = caps[sr::OZS_Y] = caps[sr::OZS_W2] = sr::kOzakiLpSlices;
+            if (o.full_sigma) caps[7] = sr::kOzakiLpSlices;
+            e = cudaMalloc((void **)&h->Wd, nn * sizeof(double));
+            if (e == cudaSuccess) e = cudaMalloc((void **)&h->W2d, nn * sizeof(double));
+            if (e == cudaSuccess && o.full_sigma) e = cudaMalloc((void **)&h->W2Yd, nn * sizeof(double));
+            if (e == cudaSuccess && o.full_sigma) e = cudaMalloc((void **)&h->W2YWd, nn * sizeof(double));
+        }
+        if (e == cudaSuccess) e = sr::ozaki_alloc(h->oz, n_max, caps);
     }
     if (e != cudaSuccess) {
         sr_set_last_cuda_error(e);

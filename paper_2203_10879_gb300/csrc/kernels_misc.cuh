@@ -87,7 +87,46 @@ struct EpDelta {
     }
 };
 
+// Delta as above with every term already in FP64 (the emulated-product pass):
+// v is the entry of W^3; W2Y, W2YW may be null.
+struct EpDeltaD {
+    const double *W, *Y, *YW, *W2, *W2Y, *W2YW; int ld;
+    double *Delta; int ldd;
+    template <typename V>
+    __device__ double operator()(int i, int j, V v) const
+    {
+        const size_t p = sr_idx(i, j, ld);
+        double d = 2.0 * W[p] - Y[p] - YW[p] + W2[p] + (double)v;
+        if (W2Y) d += W2Y[p] + W2YW[p];
+        Delta[sr_idx(i, j, ldd)] = d;
+        return 0.0;
+    }
+};
+
 // ---- small kernels -----------------------------------------------------------
+
+// W = L - L^H in FP64 from the strictly lower triangle of L (32 x 32 tiles,
+// both the tile and its transpose staged in shared memory).
+template <typename Tl>
+__global__ void __launch_bounds__(256) form_skew_kernel(int n, const Tl *__restrict__ L, int ldl,
+                                                        double *__restrict__ W, int ldw)
+{
+    __shared__ double a[32][33], b[32][33];
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int q = ty; q < 32; q += 8) {
+        const int i = i0 + tx, j = j0 + q;          // tile (I, J), rows i
+        a[tx][q] = (i < n && j < n) ? (double)L[sr_idx(i, j, ldl)] : 0.0;
+        const int i2 = j0 + tx, j2 = i0 + q;        // tile (J, I)
+        b[tx][q] = (i2 < n && j2 < n) ? (double)L[sr_idx(i2, j2, ldl)] : 0.0;
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {
+        const int i = i0 + tx, j = j0 + q;
+        if (i < n && j < n) W[sr_idx(i, j, ldw)] = (i > j) ? a[tx][q] : ((i < j) ? -b[q][tx] : 0.0);
+    }
+}
+
 
 template <typename Tin>
 __global__ void convert_to_f64_kernel(int n, const Tin *__restrict__ src, int lds, double *__restrict__ dst,

@@ -21,21 +21,24 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "ozaki.cuh"
 
 namespace sr {
 namespace {
 
-constexpr int BM = kOzakiTile;            // MMA M: output columns j (TMEM lanes)
-constexpr int BN = kOzakiTile;            // MMA N: output rows i (TMEM columns)
+constexpr int BM = kOzakiTileJ;           // MMA M: output columns j (TMEM lanes)
+constexpr int BN = kOzakiTileI;           // MMA N: output rows i (TMEM columns)
 constexpr int BK = 64;                    // K per stage: 64 bf16 = 128 bytes
 constexpr int KB_PER_CHUNK = kOzakiKChunk / BK;
 constexpr int STAGES = 4;
-constexpr int TILE_BYTES = BM * BK * 2;   // 16 KiB per operand tile
+constexpr int A_BYTES = BM * BK * 2;      // 16 KiB: column-side digits
+constexpr int B_BYTES = BN * BK * 2;      // 32 KiB: row-side digits
 constexpr int NUM_THREADS = 320;
-constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr uint32_t TMEM_COLS = 2 * BN;    // two accumulators of BN columns
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
-constexpr int SMEM_BYTES = 2 * STAGES * TILE_BYTES + 1024 + 256;
+constexpr int SMEM_BYTES = STAGES * (A_BYTES + B_BYTES) + 1024 + 256;
 
 // instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B bf16
 // (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N>>3 at bit 17,
@@ -147,28 +150,51 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 struct MmaArgs {
     int s;            // digits per operand
     int nch;          // K-chunks of 256
     int Pmax;         // row stride of digit matrices and planes
+    int tiles_i;      // row tiles (BN rows of C)
+    int ntiles;       // tiles_i * column tiles
+    int symmetric;    // 1: skip tiles entirely below the diagonal (mirrored by the combine)
     int32_t *planes;  // [s][Pmax][Pmax]
     int *flags;
 };
 
+// tile -> (first row i0, first column j0); false if the tile is skipped
+__device__ __forceinline__ bool tile_coords(const MmaArgs &a, int tile, int &i0, int &j0)
+{
+    i0 = (tile % a.tiles_i) * BN;
+    j0 = (tile / a.tiles_i) * BM;
+    return !(a.symmetric && i0 > j0 + BM - 1);
+}
+
+// Persistent: CTA b takes tiles b, b + gridDim.x, ... Every role walks the same
+// sequence of (tile, level l, pair p, chunk c, K-block kb).
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, MmaArgs args)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *tileA = smem;                             // [STAGES][TILE_BYTES]  B digits (rows j)
-    unsigned char *tileB = smem + STAGES * TILE_BYTES;       // [STAGES][TILE_BYTES]  op(A) digits (rows i)
-    uint64_t *bars = (uint64_t *)(smem + 2 * STAGES * TILE_BYTES);
+    unsigned char *tileA = smem;                             // [STAGES][A_BYTES]  column-side digits (rows j)
+    unsigned char *tileB = smem + STAGES * A_BYTES;          // [STAGES][B_BYTES]  row-side digits (rows i)
+    uint64_t *bars = (uint64_t *)(smem + STAGES * (A_BYTES + B_BYTES));
     uint64_t *full = bars, *empty = bars + STAGES, *accf = bars + 2 * STAGES, *acce = accf + 2, *done = acce + 2;
     uint32_t *tmem_slot = (uint32_t *)(done + 1);
     volatile int *abort = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i0 = blockIdx.x * BN, j0 = blockIdx.y * BM;
     const int s = args.s, nch = args.nch, P = args.Pmax;
 
     if (threadIdx.x == 0) {
@@ -202,30 +228,33 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t last_phase[STAGES];
             int issued = 0;
             bool ok = true;
-            for (int l = 0; l < s && ok; ++l)
-                for (int p = 0; p <= l && ok; ++p) {
-                    const int q = l - p;
-                    for (int c = 0; c < nch && ok; ++c)
-                        for (int kb = 0; kb < KB_PER_CHUNK; ++kb) {
-                            if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1, abort)) { ok = false; break; }
-                            const uint32_t fb = smem_u32(&full[stage]);
-                            mbar_expect_tx(fb, 2 * TILE_BYTES);
-                            const int kc = c * kOzakiKChunk + kb * BK;
-                            tma_load_2d(smem_u32(tileA + stage * TILE_BYTES), &tmB, fb, kc, q * P + j0);
-                            tma_load_2d(smem_u32(tileB + stage * TILE_BYTES), &tmA, fb, kc, p * P + i0);
-                            last_phase[stage] = phase;
-                            ++issued;
-                            if (++stage == STAGES) { stage = 0; phase ^= 1; }
-                        }
-                }
-            // wait for the loads still in flight before the CTA may exit
+            for (int tile = blockIdx.x; tile < args.ntiles && ok; tile += gridDim.x) {
+                int i0, j0;
+                if (!tile_coords(args, tile, i0, j0)) continue;
+                for (int l = 0; l < s && ok; ++l)
+                    for (int p = 0; p <= l && ok; ++p) {
+                        const int q = l - p;
+                        for (int c = 0; c < nch && ok; ++c)
+                            for (int kb = 0; kb < KB_PER_CHUNK; ++kb) {
+                                if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1, abort)) { ok = false; break; }
+                                const uint32_t fb = smem_u32(&full[stage]);
+                                mbar_expect_tx(fb, A_BYTES + B_BYTES);
+                                const int kc = c * kOzakiKChunk + kb * BK;
+                                tma_load_2d(smem_u32(tileA + stage * A_BYTES), &tmB, fb, kc, q * P + j0);
+                                tma_load_2d(smem_u32(tileB + stage * B_BYTES), &tmA, fb, kc, p * P + i0);
+                                ++issued;
+                                if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                            }
+                    }
+            }
+            // wait for the loads still in flight before the CTA may exit: load number
+            // x went to stage x % STAGES in phase (x / STAGES) & 1
             const int inflight = issued < STAGES ? issued : STAGES;
-            for (int d = 0; d < inflight; ++d) {
-                stage = (stage + STAGES - 1) % STAGES;
-                mbar_drain(smem_u32(&full[stage]), last_phase[stage]);
+            for (int d = 1; d <= inflight; ++d) {
+                const int x = issued - d;
+                mbar_drain(smem_u32(&full[x % STAGES]), (uint32_t)((x / STAGES) & 1));
             }
         }
     } else if (warp == 1) {
@@ -235,29 +264,33 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             uint32_t phase = 0;
             int t = 0;
             bool ok = true;
-            for (int l = 0; l < s && ok; ++l)
-                for (int p = 0; p <= l && ok; ++p)
-                    for (int c = 0; c < nch && ok; ++c) {
-                        const int b = t & 1;
-                        const uint32_t aph = (t >> 1) & 1;
-                        if (!mbar_wait(smem_u32(&acce[b]), aph ^ 1, abort)) { ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t dt = tmem + (uint32_t)(b * BN);
-                        for (int kb = 0; kb < KB_PER_CHUNK; ++kb) {
-                            if (!mbar_wait(smem_u32(&full[stage]), phase, abort)) { ok = false; break; }
+            for (int tile = blockIdx.x; tile < args.ntiles && ok; tile += gridDim.x) {
+                int i0, j0;
+                if (!tile_coords(args, tile, i0, j0)) continue;
+                for (int l = 0; l < s && ok; ++l)
+                    for (int p = 0; p <= l && ok; ++p)
+                        for (int c = 0; c < nch && ok; ++c) {
+                            const int b = t & 1;
+                            const uint32_t aph = (t >> 1) & 1;
+                            if (!mbar_wait(smem_u32(&acce[b]), aph ^ 1, abort)) { ok = false; break; }
                             tc_fence_after();
-                            const uint64_t ad = sdesc_sw128(smem_u32(tileA + stage * TILE_BYTES));
-                            const uint64_t bd = sdesc_sw128(smem_u32(tileB + stage * TILE_BYTES));
+                            const uint32_t dt = tmem + (uint32_t)(b * BN);
+                            for (int kb = 0; kb < KB_PER_CHUNK; ++kb) {
+                                if (!mbar_wait(smem_u32(&full[stage]), phase, abort)) { ok = false; break; }
+                                tc_fence_after();
+                                const uint64_t ad = sdesc_sw128(smem_u32(tileA + stage * A_BYTES));
+                                const uint64_t bd = sdesc_sw128(smem_u32(tileB + stage * B_BYTES));
 #pragma unroll
-                            for (int kk = 0; kk < BK / 16; ++kk)
-                                mma_bf16(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb | kk) != 0);
-                            mma_commit(smem_u32(&empty[stage]));
-                            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                                for (int kk = 0; kk < BK / 16; ++kk)
+                                    mma_bf16(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb | kk) != 0);
+                                mma_commit(smem_u32(&empty[stage]));
+                                if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                            }
+                            if (!ok) break;
+                            mma_commit(smem_u32(&accf[b]));
+                            ++t;
                         }
-                        if (!ok) break;
-                        mma_commit(smem_u32(&accf[b]));
-                        ++t;
-                    }
+            }
             // all issued MMAs complete before TMEM is released
             mma_commit(smem_u32(done));
             mbar_drain(smem_u32(done), 0);
@@ -266,49 +299,52 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         // ---- epilogue: drain accumulators, exact integer sums per level ----
         const int ew = warp - 2;
         const int lg = warp & 3;          // TMEM lane group this warp may access
-        const int half = ew >> 2;         // which 64 columns
-        const int j = j0 + lg * 32 + lane;
-        uint32_t acc[64];
+        const int half = ew >> 2;         // which BN/2 columns
+        uint32_t acc[BN / 2];
         int t = 0;
         bool ok = true;
-        for (int l = 0; l < s && ok; ++l) {
+        for (int tile = blockIdx.x; tile < args.ntiles && ok; tile += gridDim.x) {
+            int i0, j0;
+            if (!tile_coords(args, tile, i0, j0)) continue;
+            const int j = j0 + lg * 32 + lane;
+            for (int l = 0; l < s && ok; ++l) {
 #pragma unroll
-            for (int c = 0; c < 64; ++c) acc[c] = 0u;
-            uint32_t count = 0;
-            for (int p = 0; p <= l && ok; ++p)
-                for (int c = 0; c < nch; ++c) {
-                    const int b = t & 1;
-                    const uint32_t aph = (t >> 1) & 1;
-                    // one lane polls so the whole warp leaves together on a timeout
-                    int got = 0;
-                    if (lane == 0) got = mbar_wait(smem_u32(&accf[b]), aph, abort) ? 1 : 0;
-                    got = __shfl_sync(0xffffffffu, got, 0);
-                    if (!got) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + half * 64);
-                    uint32_t r[32];
-                    tmem_ld32(ta, r);
+                for (int c = 0; c < BN / 2; ++c) acc[c] = 0u;
+                uint32_t count = 0;
+                for (int p = 0; p <= l && ok; ++p)
+                    for (int c = 0; c < nch; ++c) {
+                        const int b = t & 1;
+                        const uint32_t aph = (t >> 1) & 1;
+                        // one lane polls so the whole warp leaves together on a timeout
+                        int got = 0;
+                        if (lane == 0) got = mbar_wait(smem_u32(&accf[b]), aph, abort) ? 1 : 0;
+                        got = __shfl_sync(0xffffffffu, got, 0);
+                        if (!got) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + half * (BN / 2));
 #pragma unroll
-                    for (int x = 0; x < 32; ++x)
-                        acc[x] += __float_as_uint(__fadd_rn(__uint_as_float(r[x]), 12582912.0f));
-                    tmem_ld32(ta + 32, r);
+                        for (int g = 0; g < BN / 32; ++g) {
+                            uint32_t r[16];
+                            tmem_ld16(ta + 16 * g, r);
 #pragma unroll
-                    for (int x = 0; x < 32; ++x)
-                        acc[32 + x] += __float_as_uint(__fadd_rn(__uint_as_float(r[x]), 12582912.0f));
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&acce[b]));
-                    ++t;
-                    ++count;
+                            for (int x = 0; x < 16; ++x)
+                                acc[16 * g + x] += __float_as_uint(__fadd_rn(__uint_as_float(r[x]), 12582912.0f));
+                        }
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&acce[b]));
+                        ++t;
+                        ++count;
+                    }
+                if (!ok) break;
+                const uint32_t bias = count * 0x4B400000u;
+                int32_t *dst = args.planes + (size_t)l * P * P + (size_t)j * P + (size_t)(i0 + half * (BN / 2));
+#pragma unroll
+                for (int c = 0; c < BN / 2; c += 4) {
+                    int4 v = make_int4((int)(acc[c] - bias), (int)(acc[c + 1] - bias), (int)(acc[c + 2] - bias),
+                                       (int)(acc[c + 3] - bias));
+                    *reinterpret_cast<int4 *>(dst + c) = v;
                 }
-            if (!ok) break;
-            const uint32_t bias = count * 0x4B400000u;
-            int32_t *dst = args.planes + (size_t)l * P * P + (size_t)j * P + (size_t)(i0 + half * 64);
-#pragma unroll
-            for (int c = 0; c < 64; c += 4) {
-                int4 v = make_int4((int)(acc[c] - bias), (int)(acc[c + 1] - bias), (int)(acc[c + 2] - bias),
-                                   (int)(acc[c + 3] - bias));
-                *reinterpret_cast<int4 *>(dst + c) = v;
             }
         }
     }
@@ -322,59 +358,90 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 }
 
 // ---- split: X(r, kk) -> s bf16 digit matrices [p][r][kk] and exponents -------------
-// contiguous = 1: X(r, kk) = X[kk + r*ld]; contiguous = 0: X(r, kk) = X[r + kk*ld].
-// One CTA per 32 vectors; the vectors' rows are padded to Pmax, K to Kp (zeros).
+// LAYOUT OZ_COLS: X(r, kk) = X[kk + r*ld] (vector r = column r);
+// LAYOUT OZ_ROWS: X(r, kk) = X[r + kk*ld] (vector r = row r).
+// Two kernels, each over a 2-D grid of (32 vectors) x (a stretch of K):
+//   ozaki_absmax_kernel  largest |x| per vector (bit patterns of non-negative
+//                        doubles order like the values), atomicMax per vector;
+//   ozaki_digits_kernel  scale exponent from that maximum, then the fixed-point
+//                        digits of every entry; rows up to the next multiple of
+//                        32 and K up to Kp are written as zero digits.
+constexpr int SPLIT_KT = 256;   // K per absmax CTA
+constexpr int DIGIT_KT = 64;    // K per digits CTA
+
+template <typename Tin, int LAYOUT>
+__device__ __forceinline__ void split_load_tile(double (&tile)[32][33], const Tin *__restrict__ X, int ld, int R,
+                                                int K, int r0, int k0)
+{
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        int v, kk;
+        if (LAYOUT == OZ_COLS) { kk = k0 + tx; v = ty + 8 * w; } else { v = tx; kk = k0 + ty + 8 * w; }
+        const int r = r0 + v;
+        double x = 0.0;
+        if (r < R && kk < K)
+            x = (double)(LAYOUT == OZ_COLS ? X[(size_t)kk + (size_t)r * ld] : X[(size_t)r + (size_t)kk * ld]);
+        tile[v][kk - k0] = x;
+    }
+}
+
+template <typename Tin, int LAYOUT>
 __global__ void __launch_bounds__(256)
-ozaki_split_kernel(int R, int K, int Kp, const double *__restrict__ X, int ld, int contiguous, int s, int Pmax,
-                   int Kmax, __nv_bfloat16 *__restrict__ out, int *__restrict__ exps)
+ozaki_absmax_kernel(int R, int K, const Tin *__restrict__ X, int ld, unsigned long long *__restrict__ vmax)
 {
     __shared__ double tile[32][33];
     __shared__ unsigned long long smax[32];
-    __shared__ int sexp[32];
-    const int r0 = blockIdx.x * 32;
+    const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * SPLIT_KT;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     if (threadIdx.x < 32) smax[threadIdx.x] = 0ull;
+    unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
+    for (int k0 = kbeg; k0 < kbeg + SPLIT_KT && k0 < K; k0 += 32) {
+        __syncthreads();
+        split_load_tile<Tin, LAYOUT>(tile, X, ld, R, K, r0, k0);
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const unsigned long long b =
+                (unsigned long long)__double_as_longlong(tile[ty + 8 * w][tx]) & 0x7fffffffffffffffull;
+            m[w] = b > m[w] ? b : m[w];
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w) atomicMax(&smax[ty + 8 * w], m[w]);
     __syncthreads();
+    if (threadIdx.x < 32 && r0 + threadIdx.x < R) atomicMax(&vmax[r0 + threadIdx.x], smax[threadIdx.x]);
+}
 
-    auto load_tile = [&](int k0) {
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            int v, kk;
-            if (contiguous) { kk = k0 + tx; v = ty + 8 * w; } else { v = tx; kk = k0 + ty + 8 * w; }
-            const int r = r0 + v;
-            const double x = (r < R && kk < K) ? (contiguous ? X[(size_t)kk + (size_t)r * ld]
-                                                               : X[(size_t)r + (size_t)kk * ld])
-                                               : 0.0;
-            tile[v][kk - k0] = x;
-        }
-    };
-    // pass 1: largest magnitude per vector (bit patterns of |x| order like the values)
-    for (int k0 = 0; k0 < K; k0 += 32) {
-        load_tile(k0);
-        __syncthreads();
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const int v = ty + 8 * w;
-            const unsigned long long b = (unsigned long long)__double_as_longlong(tile[v][tx]) & 0x7fffffffffffffffull;
-            atomicMax(&smax[v], b);
-        }
-        __syncthreads();
-    }
+__device__ __forceinline__ int split_exponent(unsigned long long b)
+{
+    const int eb = (int)(b >> 52);
+    if (eb == 0x7ff) return kOzakiExpNonfinite;   // Inf or NaN in the vector
+    if (eb == 0) return -1022;                    // zero or subnormal maximum
+    return eb - 1022;                             // max < 2^e
+}
+
+template <typename Tin, int LAYOUT>
+__global__ void __launch_bounds__(256)
+ozaki_digits_kernel(int R, int K, int Kp, const Tin *__restrict__ X, int ld, int s, int Pmax, int Kmax,
+                    const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
+                    int *__restrict__ exps)
+{
+    __shared__ double tile[32][33];
+    __shared__ int sexp[32];
+    const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * DIGIT_KT;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     if (threadIdx.x < 32) {
-        const unsigned long long b = smax[threadIdx.x];
-        const int eb = (int)(b >> 52);
-        int e;
-        if (eb == 0x7ff) e = kOzakiExpNonfinite;          // Inf or NaN in the vector
-        else if (eb == 0) e = -1022;                      // zero or subnormal maximum
-        else e = eb - 1022;                               // max < 2^e
+        const int r = r0 + threadIdx.x;
+        const int e = (r < R) ? split_exponent(vmax[r]) : 0;
         sexp[threadIdx.x] = e;
-        exps[r0 + threadIdx.x] = (r0 + threadIdx.x < R) ? e : 0;
+        if (blockIdx.y == 0) exps[r] = e;
     }
-    __syncthreads();
-    // pass 2: fixed point with F = 7 + 8(s-1) fraction bits, signed base-256 digits
     const int F = 7 + 8 * (s - 1);
-    for (int k0 = 0; k0 < Kp; k0 += 32) {
-        if (k0 < K) load_tile(k0);
+    const size_t pstride = (size_t)Pmax * Kmax;
+    for (int k0 = kbeg; k0 < kbeg + DIGIT_KT && k0 < Kp; k0 += 32) {
+        __syncthreads();
+        if (k0 < K) split_load_tile<Tin, LAYOUT>(tile, X, ld, R, K, r0, k0);
         __syncthreads();
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
@@ -400,21 +467,19 @@ ozaki_split_kernel(int R, int K, int Kp, const double *__restrict__ X, int ld, i
             }
             // digits from the least significant: d in [-128, 127]; the top one takes the rest
             __nv_bfloat16 *o = out + (size_t)r * Kmax + (size_t)kk;
-            const size_t pstride = (size_t)Pmax * Kmax;
             for (int p = s - 1; p >= 1; --p) {
-                const long long d = ((Xi + 128) & 255) - 128;
-                Xi = (Xi - d) >> 8;
-                o[(size_t)p * pstride] = __int2bfloat16_rn((int)d);
+                const long long dg = ((Xi + 128) & 255) - 128;
+                Xi = (Xi - dg) >> 8;
+                o[(size_t)p * pstride] = __int2bfloat16_rn((int)dg);
             }
             o[0] = __int2bfloat16_rn((int)Xi);
         }
-        __syncthreads();
     }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
-cudaError_t encode_digits_map(void *map, void *base, int rows, int Kmax)
+cudaError_t encode_digits_map(void *map, void *base, int rows, int Kmax, int box_rows)
 {
     if (!g_encode) {
         cudaDriverEntryPointQueryResult q;
@@ -425,7 +490,7 @@ cudaError_t encode_digits_map(void *map, void *base, int rows, int Kmax)
     }
     const cuuint64_t dims[2] = {(cuuint64_t)Kmax, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)Kmax * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode((CUtensorMap *)map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -435,25 +500,26 @@ cudaError_t encode_digits_map(void *map, void *base, int rows, int Kmax)
 
 }  // namespace
 
-cudaError_t ozaki_alloc(OzakiWork &w, int nmax, int slices)
+cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps)
 {
     static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
     w.nmax = nmax;
-    w.smax = kOzakiMaxSlices;
-    (void)slices;
-    w.Pmax = (nmax + kOzakiTile - 1) / kOzakiTile * kOzakiTile;
+    w.Pmax = (nmax + kOzakiTileI - 1) / kOzakiTileI * kOzakiTileI;
     w.Kmax = (nmax + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
-    const size_t dig = (size_t)w.smax * w.Pmax * w.Kmax * 2;
-    cudaError_t e = cudaMalloc(&w.Asl, dig);
-    if (e == cudaSuccess) e = cudaMalloc(&w.Bsl, dig);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&w.planes, (size_t)w.smax * w.Pmax * w.Pmax * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&w.ea, (size_t)w.Pmax * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&w.fb, (size_t)w.Pmax * sizeof(int));
-    // digit matrices outside the written rows must read as zero
-    if (e == cudaSuccess) e = cudaMemset(w.Asl, 0, dig);
-    if (e == cudaSuccess) e = cudaMemset(w.Bsl, 0, dig);
-    if (e == cudaSuccess) e = encode_digits_map(w.tmA, w.Asl, w.smax * w.Pmax, w.Kmax);
-    if (e == cudaSuccess) e = encode_digits_map(w.tmB, w.Bsl, w.smax * w.Pmax, w.Kmax);
+    cudaError_t e = cudaMalloc((void **)&w.planes, (size_t)kOzakiMaxSlices * w.Pmax * w.Pmax * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&w.vmax, (size_t)w.Pmax * sizeof(unsigned long long));
+    for (int i = 0; i < kOzakiSlots && e == cudaSuccess; ++i) {
+        OzakiSlot &sl = w.slot[i];
+        sl.cap = caps[i];
+        if (sl.cap <= 0) continue;
+        const size_t bytes = (size_t)sl.cap * w.Pmax * w.Kmax * 2;
+        e = cudaMalloc(&sl.dig, bytes);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sl.exps, (size_t)w.Pmax * sizeof(int));
+        // digits outside the rows and K a split writes must read as zero
+        if (e == cudaSuccess) e = cudaMemset(sl.dig, 0, bytes);
+        if (e == cudaSuccess) e = encode_digits_map(sl.map_j, sl.dig, sl.cap * w.Pmax, w.Kmax, BM);
+        if (e == cudaSuccess) e = encode_digits_map(sl.map_i, sl.dig, sl.cap * w.Pmax, w.Kmax, BN);
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ozaki_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     return e;
@@ -461,43 +527,72 @@ cudaError_t ozaki_alloc(OzakiWork &w, int nmax, int slices)
 
 void ozaki_free(OzakiWork &w)
 {
-    cudaFree(w.Asl);
-    cudaFree(w.Bsl);
     cudaFree(w.planes);
-    cudaFree(w.ea);
-    cudaFree(w.fb);
-    w.Asl = w.Bsl = nullptr;
+    cudaFree(w.vmax);
     w.planes = nullptr;
-    w.ea = w.fb = nullptr;
+    w.vmax = nullptr;
+    for (int i = 0; i < kOzakiSlots; ++i) {
+        cudaFree(w.slot[i].dig);
+        cudaFree(w.slot[i].exps);
+        w.slot[i].dig = nullptr;
+        w.slot[i].exps = nullptr;
+        w.slot[i].cap = 0;
+    }
 }
 
-sr_status ozaki_products(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, bool transA, int m, int n, int k,
-                         const double *A, int lda, const double *B, int ldb, int s, int *flags)
+sr_status ozaki_split(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K, const void *X,
+                      int ld, int layout, bool is_float, int s)
+{
+    if (slot < 0 || slot >= kOzakiSlots || s < 1 || s > w.slot[slot].cap || R > w.Pmax || K > kOzakiMaxK ||
+        K > w.Kmax)
+        return SR_ERR_INVALID_ARG;
+    const int Kp = (K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const int Rp = (R + 31) / 32 * 32;
+    SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, 2LL * R * K * (is_float ? 4 : 8) + 2LL * s * Kp * Rp, 2);
+    __nv_bfloat16 *out = (__nv_bfloat16 *)w.slot[slot].dig;
+    int *ex = w.slot[slot].exps;
+    SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)Rp * sizeof(unsigned long long), st));
+    const dim3 gmax(Rp / 32, (K + SPLIT_KT - 1) / SPLIT_KT);
+    const dim3 gdig(Rp / 32, (Kp + DIGIT_KT - 1) / DIGIT_KT);
+#define SR_SPLIT_LAUNCH(TIN, LAY)                                                                               \
+    ozaki_absmax_kernel<TIN, LAY><<<gmax, 256, 0, st>>>(R, K, (const TIN *)X, ld, w.vmax);                      \
+    ozaki_digits_kernel<TIN, LAY><<<gdig, 256, 0, st>>>(R, K, Kp, (const TIN *)X, ld, s, w.Pmax, w.Kmax, w.vmax, \
+                                                        out, ex)
+    if (is_float) {
+        if (layout == OZ_COLS) { SR_SPLIT_LAUNCH(float, OZ_COLS); } else { SR_SPLIT_LAUNCH(float, OZ_ROWS); }
+    } else {
+        if (layout == OZ_COLS) { SR_SPLIT_LAUNCH(double, OZ_COLS); } else { SR_SPLIT_LAUNCH(double, OZ_ROWS); }
+    }
+#undef SR_SPLIT_LAUNCH
+    SR_CUDA_TRY(cudaGetLastError());
+    return SR_OK;
+}
+
+sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n, int k,
+                        int s, bool symmetric, int *flags)
 {
     if (k > kOzakiMaxK) return SR_ERR_UNSUPPORTED;
+    if (s < 1 || s > w.slot[rows].cap || s > w.slot[cols].cap || s > kOzakiMaxSlices) return SR_ERR_INVALID_ARG;
     const int Kp = (k + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
-    const int Mp = (m + kOzakiTile - 1) / kOzakiTile * kOzakiTile;
-    const int Np = (n + kOzakiTile - 1) / kOzakiTile * kOzakiTile;
-    {
-        SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, 8LL * k * (m + n) + 2LL * s * Kp * (Mp + Np), 2);
-        // rows of op(A): columns of A when transposed (contiguous), rows of A otherwise
-        ozaki_split_kernel<<<Mp / 32, 256, 0, st>>>(m, k, Kp, A, lda, transA ? 1 : 0, s, w.Pmax, w.Kmax,
-                                                   (__nv_bfloat16 *)w.Asl, w.ea);
-        SR_CUDA_TRY(cudaGetLastError());
-        ozaki_split_kernel<<<Np / 32, 256, 0, st>>>(n, k, Kp, B, ldb, 1, s, w.Pmax, w.Kmax,
-                                                   (__nv_bfloat16 *)w.Bsl, w.fb);
-        SR_CUDA_TRY(cudaGetLastError());
-    }
-    {
-        const long long pairs = (long long)s * (s + 1) / 2;
-        SrPhase ph(h, SR_PROF_OZ_MMA, pairs * 2LL * Mp * Np * Kp,
-                   pairs * 2LL * Kp * (Mp + Np) + 4LL * s * Mp * Np, 1);
-        MmaArgs a{s, Kp / kOzakiKChunk, w.Pmax, w.planes, flags};
-        dim3 grid(Mp / kOzakiTile, Np / kOzakiTile);
-        ozaki_mma_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.tmA,
-                                                                *(const CUtensorMap *)w.tmB, a);
-        SR_CUDA_TRY(cudaGetLastError());
-    }
+    const int Mp = (m + BN - 1) / BN * BN;
+    const int Np = (n + BM - 1) / BM * BM;
+    const long long pairs = (long long)s * (s + 1) / 2;
+    const int tiles_i = Mp / BN, tiles_j = Np / BM;
+    long long active = 0;
+    for (int bj = 0; bj < tiles_j; ++bj)
+        for (int bi = 0; bi < tiles_i; ++bi)
+            if (!(symmetric && bi * BN > bj * BM + BM - 1)) ++active;
+    const long long tile_flops = 2LL * BN * BM * Kp;
+    SrPhase ph(h, SR_PROF_OZ_MMA, pairs * active * tile_flops,
+               pairs * 2LL * Kp * (Mp + Np) + 4LL * s * active * BN * BM, 1);
+    MmaArgs a{s, Kp / kOzakiKChunk, w.Pmax, tiles_i, tiles_i * tiles_j, symmetric ? 1 : 0, w.planes, flags};
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const int grid = (int)std::min<long long>(active, sms > 0 ? sms : 1);
+    // MMA "A" (TMEM lanes) = column-side digits, MMA "B" = row-side digits
+    ozaki_mma_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.slot[rows].map_i,
+                                                            *(const CUtensorMap *)w.slot[cols].map_j, a);
+    SR_CUDA_TRY(cudaGetLastError());
     return SR_OK;
 }
 

@@ -5,9 +5,9 @@
 // FP64 pipe delivers ~1.2 TFLOP/s and tcgen05 has no integer MMA for sm_103a,
 // so the split here targets bf16 operands with FP32 accumulation:
 //
-//  * every row i of op(A) and column j of B gets a power-of-two scale 2^e with
-//    |entries| < 2^e; the scaled entries x in (-1, 1) are written in fixed
-//    point with F = 7 + 8(s-1) fraction bits and cut into s signed digits
+//  * every vector (a row of op(A) or a column of B) gets a power-of-two scale
+//    2^e with |entries| < 2^e; the scaled entries x in (-1, 1) are written in
+//    fixed point with F = 7 + 8(s-1) fraction bits and cut into s signed digits
 //    sigma_p in [-128, 128], x ~ sum_p sigma_p 2^(-7-8p) (p = 0..s-1). The
 //    digits are exact in bf16. The cut is integer arithmetic only.
 //  * digit matrices are multiplied pairwise on tcgen05 (kind::f16, FP32
@@ -17,6 +17,9 @@
 //    Levels l = 0..s-1 are kept (the pairs with p + q <= s - 1).
 //  * a combine kernel rebuilds C(i,j) = 2^(e_i + f_j) sum_l I_l 2^(-14-8l) in
 //    FP64 and hands it to the same fused epilogues as the native FP64 path.
+//
+// Digits live in "slots" so that one split serves several products: the
+// columns of Q feed A Q, Q^T (A Q) and Q^T Q in the same pass.
 #pragma once
 #include <climits>
 
@@ -26,30 +29,49 @@ namespace sr {
 
 constexpr int kOzakiMaxSlices = 7;   // 7 + 8*6 = 55 fraction bits fit a 64-bit integer
 constexpr int kOzakiDefaultSlices = 7;
+constexpr int kOzakiLpSlices = 3;    // 23 fraction bits: the FP32-class products YW, W^2, W^3
 constexpr bool kOzakiBuilt = true;
-constexpr int kOzakiTile = 128;
+constexpr int kOzakiTileI = 256;      // rows of C per slice-product tile (MMA N)
+constexpr int kOzakiTileJ = 128;      // columns of C per slice-product tile (MMA M, TMEM lanes)
 constexpr int kOzakiKChunk = 256;
 constexpr int kOzakiMaxK = 16384;     // keeps every level sum below 2^31
 constexpr int kOzakiExpNonfinite = INT_MIN;
+constexpr int kOzakiSlots = 8;
 
-struct OzakiWork {
-    int nmax = 0, smax = 0, Pmax = 0, Kmax = 0;
-    void *Asl = nullptr, *Bsl = nullptr;   // bf16 digits: [s][Pmax][Kmax]
-    int32_t *planes = nullptr;             // [s][Pmax cols][Pmax rows], column-major per level
-    int *ea = nullptr, *fb = nullptr;      // scale exponents of op(A) rows and B columns
-    alignas(64) unsigned char tmA[128];    // CUtensorMap of the op(A) digits
-    alignas(64) unsigned char tmB[128];    // CUtensorMap of the B digits
+// vectors of a split: columns (contiguous in a column-major matrix) or rows
+enum { OZ_COLS = 0, OZ_ROWS = 1 };
+
+struct OzakiSlot {
+    int cap = 0;                           // digits this slot can hold
+    void *dig = nullptr;                   // bf16 digits [cap][Pmax][Kmax]
+    int *exps = nullptr;                   // [Pmax]
+    alignas(64) unsigned char map_i[128];  // CUtensorMap over the digits, boxes of kOzakiTileI rows
+    alignas(64) unsigned char map_j[128];  // the same with boxes of kOzakiTileJ rows
 };
 
-cudaError_t ozaki_alloc(OzakiWork &w, int nmax, int slices);
+struct OzakiWork {
+    int nmax = 0, Pmax = 0, Kmax = 0;
+    OzakiSlot slot[kOzakiSlots];
+    int32_t *planes = nullptr;             // [kOzakiMaxSlices][Pmax cols][Pmax rows]
+    unsigned long long *vmax = nullptr;    // per-vector largest |x| (bit pattern) during a split
+};
+
+// caps[i] = digits of slot i (0 = unused)
+cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps);
 void ozaki_free(OzakiWork &w);
 
-// Splits op(A) and B and runs the slice products into w.planes. Returns
-// SR_ERR_UNSUPPORTED for k > kOzakiMaxK.
-sr_status ozaki_products(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, bool transA, int m, int n, int k,
-                         const double *A, int lda, const double *B, int ldb, int s, int *flags);
+// Splits the R vectors of length K of X (double or float, column-major with
+// leading dimension ld; vectors = columns or rows) into s digits in `slot`.
+sr_status ozaki_split(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K, const void *X,
+                      int ld, int layout, bool is_float, int s);
 
-// 2^e as a product of two normal doubles (e within +-2044)
+// Level planes of the product of the vectors in slot `rows` (output rows i)
+// with those in slot `cols` (output columns j), inner length k. With
+// symmetric = true only tiles with i-tile <= j-tile are formed.
+sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n, int k,
+                        int s, bool symmetric, int *flags);
+
+// v * 2^e as a product of two normal doubles (e within +-2044)
 __device__ inline double oz_pow2_scale(double v, int e)
 {
     const int e1 = e / 2, e2 = e - e / 2;
@@ -58,23 +80,37 @@ __device__ inline double oz_pow2_scale(double v, int e)
     return (v * p1) * p2;
 }
 
-// C(i,j) from the level planes; ep as in gemm_simt.cuh.
+// v * 2^e by adding to the exponent field when v and the result are normal
+// (integer work only), else through oz_pow2_scale.
+__device__ inline double oz_scale(double v, int e)
+{
+    const long long b = __double_as_longlong(v);
+    const int eb = (int)((b >> 52) & 0x7ff);
+    if (eb > 0 && eb + e > 0 && eb + e < 2047) return __longlong_as_double(b + ((long long)e << 52));
+    if (v == 0.0) return v;
+    return oz_pow2_scale(v, e);
+}
+
+// C(i,j) = sign * (rebuilt product); ep as in gemm_simt.cuh. With mirror, the
+// entries below the diagonal are read from the transposed position.
 template <class EP>
 __global__ void __launch_bounds__(256)
 ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, int ldp, size_t pstride,
-                     const int *__restrict__ ea, const int *__restrict__ fb, EP ep, double *partial)
+                     const int *__restrict__ ea, const int *__restrict__ fb, double sign, int mirror, EP ep,
+                     double *partial)
 {
     const int i = blockIdx.x * 32 + (threadIdx.x & 31);
     const int jb = blockIdx.y * 32 + (threadIdx.x >> 5);
     const int nh = s < 4 ? s : 4;
-    const double sh = __longlong_as_double((long long)(1023 - 14 - 8 * (nh - 1)) << 52);
-    const double sl = __longlong_as_double((long long)(1023 - 14 - 8 * (s - 1)) << 52);
+    const double sh = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (nh - 1)) << 52);
+    const double sl = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (s - 1)) << 52);
     double part = 0.0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
         const int j = jb + 8 * w;
         if (i < m && j < n) {
-            const size_t off = (size_t)i + (size_t)j * (size_t)ldp;
+            const size_t off = (mirror && i > j) ? (size_t)j + (size_t)i * (size_t)ldp
+                                                 : (size_t)i + (size_t)j * (size_t)ldp;
             long long H = 0, Lo = 0;
             for (int l = 0; l < nh; ++l) H = H * 256 + (long long)planes[off + (size_t)l * pstride];
             for (int l = nh; l < s; ++l) Lo = Lo * 256 + (long long)planes[off + (size_t)l * pstride];
@@ -83,7 +119,7 @@ ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, in
             if (e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite)
                 v = __longlong_as_double(0x7ff8000000000000LL);
             else
-                v = oz_pow2_scale(v, e1 + e2);
+                v = oz_scale(v, e1 + e2);
             part += ep(i, j, v);
         }
     }
@@ -96,22 +132,42 @@ ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, in
 inline int ozaki_blocks(int m, int n) { return ((m + 31) / 32) * ((n + 31) / 32); }
 
 template <class EP>
+sr_status ozaki_combine(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n, int s,
+                        double sign, bool mirror, EP ep, double *partial, int *blocks)
+{
+    SrPhase ph(h, SR_PROF_OZ_COMBINE, 8LL * s * m * n, (long long)m * n * (4LL * s + 16), 1);
+    dim3 grid((m + 31) / 32, (n + 31) / 32);
+    ozaki_combine_kernel<EP><<<grid, 256, 0, st>>>(m, n, s, w.planes, w.Pmax, (size_t)w.Pmax * w.Pmax,
+                                                    w.slot[rows].exps, w.slot[cols].exps, sign, mirror ? 1 : 0, ep,
+                                                    partial);
+    SR_CUDA_TRY(cudaGetLastError());
+    if (blocks) *blocks = ozaki_blocks(m, n);
+    return SR_OK;
+}
+
+// slots used by the engine
+enum {
+    OZS_ROWS = 0,   // generic product: op(A) rows; refinement: rows of A (split once per call)
+    OZS_COLS = 1,   // generic product: B columns; refinement: columns of Q
+    OZS_X = 2,      // columns of A Q, then of Delta
+    OZS_QROWS = 3,  // rows of Q (update product)
+    OZS_W = 4,      // columns of W (low-precision digits)
+    OZS_Y = 5,      // columns of Y (low-precision digits)
+    OZS_W2 = 6      // columns of W^2 (low-precision digits)
+};
+
+// One emulated product C = op(A) B with the generic slots, epilogue ep.
+template <class EP>
 sr_status ozaki_gemm(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, bool transA, int m, int n, int k,
                      const double *A, int lda, const double *B, int ldb, EP ep, double *partial, int *blocks,
                      int slices, int *flags)
 {
     const int s = slices > 0 ? slices : kOzakiDefaultSlices;
-    if (s > w.smax || m > w.nmax || n > w.nmax || k > w.nmax) return SR_ERR_INVALID_ARG;
-    SR_TRY(ozaki_products(h, st, w, transA, m, n, k, A, lda, B, ldb, s, flags));
-    {
-        SrPhase ph(h, SR_PROF_OZ_COMBINE, 8LL * s * m * n, (long long)m * n * (4LL * s + 16), 1);
-        dim3 grid((m + 31) / 32, (n + 31) / 32);
-        ozaki_combine_kernel<EP><<<grid, 256, 0, st>>>(m, n, s, w.planes, w.Pmax, (size_t)w.Pmax * w.Pmax,
-                                                        w.ea, w.fb, ep, partial);
-        SR_CUDA_TRY(cudaGetLastError());
-    }
-    *blocks = ozaki_blocks(m, n);
-    return SR_OK;
+    if (s > w.slot[OZS_ROWS].cap || m > w.nmax || n > w.nmax || k > w.nmax) return SR_ERR_INVALID_ARG;
+    SR_TRY(ozaki_split(h, st, w, OZS_ROWS, m, k, A, lda, transA ? OZ_COLS : OZ_ROWS, false, s));
+    SR_TRY(ozaki_split(h, st, w, OZS_COLS, n, k, B, ldb, OZ_COLS, false, s));
+    SR_TRY(ozaki_product(h, st, w, OZS_ROWS, OZS_COLS, m, n, k, s, false, flags));
+    return ozaki_combine(h, st, w, OZS_ROWS, OZS_COLS, m, n, s, 1.0, false, ep, partial, blocks);
 }
 
 }  // namespace sr

@@ -143,3 +143,26 @@ def test_refine_ozaki_jittered(torch, n):
     Tq = np.diagonal(Q.T @ p.A @ Q)
     Tr = np.diagonal(ref.Q.T @ p.A @ ref.Q)
     assert np.max(np.abs(Tq - Tr)) <= 1e-12
+
+
+def test_one_pass_parity_ozaki(torch):
+    # one pass through the emulated engine against the oracle's FP32 pass: the
+    # FP32 solve dominates the difference, O(u32 ||W||) in Q
+    p = inputs.planted(96, inputs.eig_unit_step(96), 5, pert=1e-5)
+    st, nr, Q = _refine(p, lp=B.SR_LP_FP32, max_iter=1)
+    assert st == B.SR_ERR_NOT_CONVERGED and nr.iters == 1
+    Q0, _ = oracle.ns_init(p.Qhat)
+    Q1, info = oracle.iteration(p.A, Q0, lp="f32")
+    assert nr.w_norm == pytest.approx(info.w_norm, rel=1e-5)
+    assert np.max(np.abs(Q - Q1)) <= 50 * 2.0 ** -24 * info.w_norm + 1e-13
+
+
+def test_refine_ozaki_full_sigma(torch):
+    p = inputs.jittered_real(257)
+    st, nr, Q = _refine(p, lp=B.SR_LP_FP32, full_sigma=1)
+    ref = oracle.refine(p.A, p.Qhat, lp="f32", full_sigma=True)
+    assert st == B.SR_OK and abs(nr.iters - ref.iters) <= 1
+    tol = oracle.default_tol(257)
+    cT, cQ = oracle.residuals_dd(p.A, Q)
+    assert cT <= tol and cQ <= tol
+    assert np.max(np.abs(sign_align(Q, ref.Q) - ref.Q)) <= 1e-9
