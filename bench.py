@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 METRIC = "sec to FP64-accurate Schur refinement, mixed vs all-FP64 GPU; % FP64/tensor peak"
 FP64_NOMINAL_TFLOPS = 1.25        # GB300 FP64 (vector and tensor), nominal
 BF16_NOMINAL_TFLOPS = 2250.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one captured launch of the dominant
+# kernel (profiles/ozaki_mma_kernel_n4096.md: the 28-pair T^ product at n = 4096);
+# valid for that kernel version and size only
+OZ_MMA_TRAFFIC_BYTES_N4096 = 4.521404e9 + 0.468546e9
 
 
 def _peaks():
@@ -275,7 +279,9 @@ def run_ours(args):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "ozaki slice products (tcgen05 kind::f16 bf16)",
+                "traffic": OZ_MMA_TRAFFIC_BYTES_N4096 if (n == 4096 and (args.slices or 7) == 7) else None,
+                "traffic_note": "bytes per launch of the captured 28-pair product (ncu)",
+                "kernel": "ozaki slice products (tcgen05 kind::f16 bf16)",
                 "peak_source": "of measured bf16 sustained (MEASURED_PEAKS.json)"}
     else:
         gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9

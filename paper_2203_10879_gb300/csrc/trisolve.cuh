@@ -21,7 +21,7 @@
 // 0) therefore runs two independent kernels:
 //   trisolve_leaf_kernel    one CTA of 1024 threads per tile of subdiagonal t:
 //                           applies subdiagonal t+1's two products, then solves;
-//   trisolve_update_kernel  one CTA of 256 threads per tile with D < t that
+//   trisolve_update_kernel  one CTA of 128 threads per tile with D < t that
 //                           receives a product of subdiagonal t+1, accumulated
 //                           in place in E.
 // The engine captures the 2 NB launches once per order in a CUDA graph with the
@@ -45,12 +45,40 @@ __device__ inline T sr_div_round(double di, double dj) { return (T)(di - dj); }
 void trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long long> &offsets);
 
 // ---- contributions of subdiagonal t+1 to tiles with D < t --------------------
-// 2 x 2 register blocks: thread (tx, ty) owns rows 2tx, 2tx+1 and columns 2ty, 2ty+1.
+// 128 threads; thread (tx, ty) owns the 4 x 2 block rows 4tx.., columns 2ty..,
+// read with vector loads from shared memory.
+template <typename T> struct SolveVec;
+template <> struct SolveVec<float> {
+    __device__ static void ld4(const float *p, float (&v)[4])
+    {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    __device__ static void ld2(const float *p, float (&v)[2])
+    {
+        const float2 q = *reinterpret_cast<const float2 *>(p);
+        v[0] = q.x; v[1] = q.y;
+    }
+};
+template <> struct SolveVec<double> {
+    __device__ static void ld4(const double *p, double (&v)[4])
+    {
+        const double2 q0 = *reinterpret_cast<const double2 *>(p);
+        const double2 q1 = *reinterpret_cast<const double2 *>(p + 2);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+    __device__ static void ld2(const double *p, double (&v)[2])
+    {
+        const double2 q = *reinterpret_cast<const double2 *>(p);
+        v[0] = q.x; v[1] = q.y;
+    }
+};
+
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t *__restrict__ plan)
 {
-    constexpr int B = kSolveTile, S = B + 2;
+    constexpr int B = kSolveTile, SA = B + 4, SB = B + 2;
     const int NB = (n + B - 1) / B;
     const uint32_t tile = plan[blockIdx.x];
     const int I = (int)(tile >> 16), J = (int)(tile & 0xffffu);
@@ -58,50 +86,50 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
     const int r0 = I * B, c0 = J * B;
     const int nr = min(B, n - r0), nc = min(B, n - c0);
     const int d = t + 1;
-    __shared__ __align__(16) T Ta[2][B][S];   // left operands, transposed: Ta[u][k][row]
-    __shared__ __align__(16) T Tb[2][B][S];   // right operands: Tb[u][k][col]
+    __shared__ __align__(16) T Ta[2][B][SA];   // left operands, transposed: Ta[u][k][row]
+    __shared__ __align__(16) T Tb[2][B][SB];   // right operands: Tb[u][k][col]
     const int tid = threadIdx.x;
-    const int lx = tid & 31, ly = tid >> 5;   // load mapping: element (lx, ly + 8q)
-    const int tx = tid & 15, ty = tid >> 4;
+    const int lx = tid & 31, ly = tid >> 5;   // load mapping: element (lx, ly + 4q), q = 0..7
+    const int tx = tid & 7, ty = tid >> 3;    // block rows 4tx.., columns 2ty..
     const bool hasP = J + d < NB, hasM = I - d >= 0;
     const int kP = (J + d) * B, kM = (I - d) * B;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int y = ly + 8 * q;
+    for (int q = 0; q < 8; ++q) {
+        const int y = ly + 4 * q;
         Ta[0][y][lx] = (hasP && r0 + lx < n && kP + y < n) ? TE[sr_idx(r0 + lx, kP + y, ld)] : (T)0;
         Tb[0][lx][y] = (hasP && kP + lx < n && c0 + y < n) ? TE[sr_idx(kP + lx, c0 + y, ld)] : (T)0;
         Ta[1][y][lx] = (hasM && r0 + lx < n && kM + y < n) ? TE[sr_idx(r0 + lx, kM + y, ld)] : (T)0;
         Tb[1][lx][y] = (hasM && kM + lx < n && c0 + y < n) ? TE[sr_idx(kM + lx, c0 + y, ld)] : (T)0;
     }
-    T acc[2][2];
+    T acc[4][2];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const int x = 2 * tx + i, y = 2 * ty + j;
+            const int x = 4 * tx + i, y = 2 * ty + j;
             acc[i][j] = (x < nr && y < nc && (D > 0 || x > y)) ? TE[sr_idx(r0 + x, c0 + y, ld)] : (T)0;
         }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int k = 0; k < B; ++k) {
-        const T a0 = Ta[0][k][2 * tx], a1 = Ta[0][k][2 * tx + 1];
-        const T b0 = Tb[0][k][2 * ty], b1 = Tb[0][k][2 * ty + 1];
-        const T m0 = Ta[1][k][2 * tx], m1 = Ta[1][k][2 * tx + 1];
-        const T n0 = Tb[1][k][2 * ty], n1 = Tb[1][k][2 * ty + 1];
-        acc[0][0] = fma(a0, b0, acc[0][0]);
-        acc[0][1] = fma(a0, b1, acc[0][1]);
-        acc[1][0] = fma(a1, b0, acc[1][0]);
-        acc[1][1] = fma(a1, b1, acc[1][1]);
-        acc[0][0] = fma(-m0, n0, acc[0][0]);
-        acc[0][1] = fma(-m0, n1, acc[0][1]);
-        acc[1][0] = fma(-m1, n0, acc[1][0]);
-        acc[1][1] = fma(-m1, n1, acc[1][1]);
+        T a[4], b[2], m[4], c[2];
+        SolveVec<T>::ld4(&Ta[0][k][4 * tx], a);
+        SolveVec<T>::ld2(&Tb[0][k][2 * ty], b);
+        SolveVec<T>::ld4(&Ta[1][k][4 * tx], m);
+        SolveVec<T>::ld2(&Tb[1][k][2 * ty], c);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                acc[i][j] = fma(-m[i], c[j], acc[i][j]);
+            }
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const int x = 2 * tx + i, y = 2 * ty + j;
+            const int x = 4 * tx + i, y = 2 * ty + j;
             if (x < nr && y < nc && (D > 0 || x > y)) TE[sr_idx(r0 + x, c0 + y, ld)] = acc[i][j];
         }
 }
@@ -150,7 +178,10 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const double *__restrict
             acc = fma(-Ta[1][k][a], Tb[1][k][b], acc);
         }
     }
+    // divisor t_aa - t_bb formed in FP64 and rounded; its reciprocal (one IEEE
+    // division, off the wavefront's critical path) turns each solve into a product
     const T den = own ? sr_div_round<T>(dI[a], dJ[b]) : (T)1;
+    const T rcp = (T)1 / den;
     __syncthreads();
 
     // 2. wavefront over the tile's subdiagonals. When subdiagonal w is final, a
@@ -168,7 +199,7 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const double *__restrict
             if (den == (T)0) {
                 bad |= SR_FLAG_NONDISTINCT;
             } else {
-                xv = -acc / den;
+                xv = -acc * rcp;
                 if (!sr_finite(xv)) bad |= SR_FLAG_NONFINITE;
             }
             X[a][b] = xv;
@@ -203,7 +234,7 @@ inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEven
         const long long nupd = offsets[l + 1] - offsets[l] - nleaf;
         trisolve_leaf_kernel<T><<<(unsigned)nleaf, 1024, 0, st>>>(n, TE, ld, dhp, t, plan + offsets[l], flags);
         if (nupd > 0)
-            trisolve_update_kernel<T><<<(unsigned)nupd, 256, 0, aux>>>(n, TE, ld, t, plan + offsets[l] + nleaf);
+            trisolve_update_kernel<T><<<(unsigned)nupd, 128, 0, aux>>>(n, TE, ld, t, plan + offsets[l] + nleaf);
         e = cudaGetLastError();
         // both kernels of this step finish before either of the next starts
         if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
