@@ -87,6 +87,9 @@ typedef struct {
                          1e-14 * sqrt(n) */
     int profile;      /* 1: time every phase with CUDA events on the handle's
                          stream (see schur_refine_get_profile) */
+    int batch_streams;/* schur_refine_batched: matrices refined concurrently,
+                         each on its own stream and workspace; <= 0 selects 8,
+                         1 refines them one after another on the handle's stream */
 } sr_options;
 
 /* Fills *opt with the defaults: real, FP64 target, native FP64 products,
@@ -139,11 +142,18 @@ sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, vo
 
 /*
  * Refines `batch` independent matrices of orders n[b] <= n_max (host array),
- * each exactly as schur_refine_step with dQhat given.
+ * each exactly as schur_refine_step with dQhat given (dQhat may be NULL: then
+ * dQ[b] holds each starting factor).
  *   dA[b], dQ[b], dQhat[b]: host arrays of device pointers to column-major
  *   matrices with leading dimension n[b].
  *   iters_out[b], status_out[b]: host arrays (may be NULL) receiving each
  *   matrix's pass count and status.
+ * The matrices are distributed over batch_streams workers (host threads),
+ * each with its own stream and workspace (created on first use and kept by the
+ * handle), so the refinements of different matrices overlap on the GPU. The
+ * workers start after the work already enqueued on the handle's stream, and
+ * that stream waits for all of them before the call returns. Each matrix's
+ * result is the same as from schur_refine_step.
  * Returns SR_OK if every matrix converged, else the first non-OK status in
  * batch order.
  */

@@ -6,6 +6,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -59,6 +61,11 @@ struct schur_refine_ctx {
     cudaEvent_t sev0 = nullptr, sev1 = nullptr;
     struct SolveGraph { int n; const void *TE; int ld; const double *dhp; int fp32; cudaGraphExec_t exec; };
     std::vector<SolveGraph> graphs;
+    // workers of schur_refine_batched: sub-handles on their own streams
+    std::vector<schur_refine_ctx *> subs;
+    std::vector<cudaStream_t> sub_streams;
+    cudaEvent_t bfork = nullptr;
+    std::vector<cudaEvent_t> bjoin;
     // profiling
     sr_profile prof{};
     std::vector<cudaEvent_t> ev_pool;
@@ -533,6 +540,8 @@ void schur_refine_default_options(sr_options *opt)
     opt->max_iter = 10;
     opt->ozaki_slices = 0;
     opt->tol = 0.0;
+    opt->profile = 0;
+    opt->batch_streams = 0;
 }
 
 const char *schur_refine_status_string(sr_status s)
@@ -589,6 +598,10 @@ void schur_refine_destroy(schur_refine_t h)
     cudaFree(h->W2d);
     cudaFree(h->W2Yd);
     cudaFree(h->W2YWd);
+    for (auto *sub : h->subs) schur_refine_destroy(sub);
+    for (auto s : h->sub_streams) cudaStreamDestroy(s);
+    for (auto e : h->bjoin) cudaEventDestroy(e);
+    if (h->bfork) cudaEventDestroy(h->bfork);
     drop_graphs(h);
     if (h->cap_st) cudaStreamDestroy(h->cap_st);
     if (h->aux_st) cudaStreamDestroy(h->aux_st);
@@ -690,14 +703,78 @@ sr_status schur_refine_batched(schur_refine_t h, int batch, const int *n, const 
     if (!h || batch < 0 || (batch > 0 && (!n || !dA || !dQ))) return SR_ERR_INVALID_ARG;
     for (int b = 0; b < batch; ++b)
         if (n[b] < 1 || n[b] > h->nmax || !dA[b] || !dQ[b]) return SR_ERR_INVALID_ARG;
+    if (batch == 0) return SR_OK;
+    const int want = h->opt.batch_streams > 0 ? h->opt.batch_streams : 8;
+    const int W = std::min(want, batch);
+    std::vector<int> st(batch, (int)SR_OK), it(batch, 0);
+    if (W <= 1) {
+        for (int b = 0; b < batch; ++b) {
+            sr_norms nr{};
+            st[b] = (int)schur_refine_step(h, n[b], dA[b], n[b], dQ[b], n[b], dQhat ? dQhat[b] : nullptr, nullptr,
+                                           &nr);
+            it[b] = nr.iters;
+            if (st[b] == SR_ERR_CUDA) break;
+        }
+    } else {
+        // worker pool: sub-handles with the same options, each on its own stream
+        while ((int)h->subs.size() < W) {
+            cudaStream_t s = nullptr;
+            SR_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            sr_options o = h->opt;
+            o.batch_streams = 1;
+            schur_refine_t sub = nullptr;
+            sr_status cs = schur_refine_create(&sub, h->nmax, &o, s);
+            if (cs != SR_OK) {
+                cudaStreamDestroy(s);
+                return cs;
+            }
+            cudaEvent_t ev = nullptr;
+            SR_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            h->subs.push_back(sub);
+            h->sub_streams.push_back(s);
+            h->bjoin.push_back(ev);
+        }
+        if (!h->bfork) SR_CUDA_TRY(cudaEventCreateWithFlags(&h->bfork, cudaEventDisableTiming));
+        // the workers start after the work already on the handle's stream
+        SR_CUDA_TRY(cudaEventRecord(h->bfork, h->st));
+        for (int w = 0; w < W; ++w) SR_CUDA_TRY(cudaStreamWaitEvent(h->sub_streams[w], h->bfork, 0));
+        std::atomic<int> next(0);
+        std::vector<std::thread> pool;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        for (int w = 0; w < W; ++w)
+            pool.emplace_back([&, w]() {
+                cudaSetDevice(dev);
+                for (int b = next++; b < batch; b = next++) {
+                    sr_norms nr{};
+                    st[b] = (int)schur_refine_step(h->subs[w], n[b], dA[b], n[b], dQ[b], n[b],
+                                                   dQhat ? dQhat[b] : nullptr, nullptr, &nr);
+                    it[b] = nr.iters;
+                }
+            });
+        for (auto &t : pool) t.join();
+        for (int w = 0; w < W; ++w) {
+            SR_CUDA_TRY(cudaEventRecord(h->bjoin[w], h->sub_streams[w]));
+            SR_CUDA_TRY(cudaStreamWaitEvent(h->st, h->bjoin[w], 0));
+            // the workers' launches and timings count as the handle's
+            sr_profile p{};
+            if (schur_refine_get_profile(h->subs[w], &p) == SR_OK) {
+                for (int k = 0; k < SR_PROF_KINDS; ++k) {
+                    h->prof.ms[k] += p.ms[k];
+                    h->prof.flops[k] += p.flops[k];
+                    h->prof.bytes[k] += p.bytes[k];
+                    h->prof.launches[k] += p.launches[k];
+                    h->prof.spans[k] += p.spans[k];
+                }
+                schur_refine_reset_profile(h->subs[w]);
+            }
+        }
+    }
     sr_status first = SR_OK;
     for (int b = 0; b < batch; ++b) {
-        sr_norms nr{};
-        sr_status s = schur_refine_step(h, n[b], dA[b], n[b], dQ[b], n[b], dQhat ? dQhat[b] : nullptr, nullptr, &nr);
-        if (iters_out) iters_out[b] = nr.iters;
-        if (status_out) status_out[b] = (int)s;
-        if (s != SR_OK && first == SR_OK) first = s;
-        if (s == SR_ERR_CUDA) return s;
+        if (iters_out) iters_out[b] = it[b];
+        if (status_out) status_out[b] = st[b];
+        if (st[b] != SR_OK && first == SR_OK) first = (sr_status)st[b];
     }
     return first;
 }
