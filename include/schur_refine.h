@@ -55,7 +55,9 @@ typedef enum {
     SR_ERR_UNSUPPORTED = 8
 } sr_status;
 
-/* element type of A and Q */
+/* element type of A and Q. SR_COMPLEX (complex128 data, complex64 low
+   precision) is built for hp_gemm = SR_HP_OZAKI_BF16 with lp = SR_LP_FP32 and
+   orders up to 8192; other combinations give SR_ERR_UNSUPPORTED at create. */
 enum { SR_REAL = 0, SR_COMPLEX = 1 };
 /* working high precision */
 enum { SR_TARGET_FP64 = 0 };
@@ -126,7 +128,7 @@ sr_status schur_refine_create(schur_refine_t *h, int n_max, const sr_options *op
  *             given, Q is first set to one Newton-Schulz step of Qhat
  *             converted to FP64 (Alg. 4, second line; eq. NS), and dQ's input
  *             value is ignored.
- *   dT        device, n x n, ld n, FP64, or NULL: receives T^ = Q^H A Q of the
+ *   dT        device, n x n, ld n, FP64 (complex128), or NULL: receives T^ = Q^H A Q of the
  *             last pass (its upper triangle is the Schur factor T).
  *   out       host, or NULL: norms and counters of the run.
  * Each pass forms T^ (2 products); if the stop test holds the run ends,

@@ -290,12 +290,21 @@ def residuals_dd(A: np.ndarray, Q: np.ndarray, threads: int | None = None):
 
 
 def sample_entries_dd(A: np.ndarray, Q: np.ndarray, rows, cols):
-    """Entries (Q^T A Q)[rows, cols] and (Q^T Q - I)[rows, cols] in double-double (real)."""
+    """Entries (Q^H A Q)[rows, cols] and (Q^H Q - I)[rows, cols] in double-double
+    (complex128 results for complex input)."""
     n = A.shape[0]
-    Af = _lib.fortran(A, np.float64)
-    Qf = _lib.fortran(Q, np.float64)
     r = np.ascontiguousarray(rows, dtype=np.int32)
     c = np.ascontiguousarray(cols, dtype=np.int32)
+    if np.iscomplexobj(A) or np.iscomplexobj(Q):
+        Af = _lib.fortran(A, np.complex128)
+        Qf = _lib.fortran(Q, np.complex128)
+        t = np.zeros(len(r), dtype=np.complex128)
+        y = np.zeros(len(r), dtype=np.complex128)
+        _lib.lib().sro_sample_entries_dd_c(n, _lib.ptr(Af), n, _lib.ptr(Qf), n, len(r), _lib.ptr(r),
+                                           _lib.ptr(c), _lib.ptr(t), _lib.ptr(y))
+        return t, y
+    Af = _lib.fortran(A, np.float64)
+    Qf = _lib.fortran(Q, np.float64)
     t = np.zeros(len(r))
     y = np.zeros(len(r))
     _lib.lib().sro_sample_entries_dd(n, _lib.ptr(Af), n, _lib.ptr(Qf), n, len(r), _lib.ptr(r),

@@ -435,6 +435,50 @@ void sro_sample_entries_dd(int n, const double *A, int lda, const double *Q, int
     }
 }
 
+/* Complex form of sro_sample_entries_dd (interleaved complex128 input; tq, yq
+   receive 2 ns doubles, re and im of each sampled entry):
+   (Q^H A Q)(i, j) = sum_l conj(Q(l, i)) sum_k A(l, k) Q(k, j), (Q^H Q - I)(i, j). */
+void sro_sample_entries_dd_c(int n, const double *A, int lda, const double *Q, int ldq,
+                             int ns, const int *rows, const int *cols,
+                             double *tq, double *yq)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int s = 0; s < ns; ++s) {
+        int i = rows[s], j = cols[s];
+        dd_t tr = {0.0, 0.0}, ti = {0.0, 0.0};
+        for (int l = 0; l < n; ++l) {
+            dd_t ar = {0.0, 0.0}, ai = {0.0, 0.0};   /* (A Q)(l, j) */
+            for (int k = 0; k < n; ++k) {
+                double xr = A[2 * IDX(l, k, lda)], xi = A[2 * IDX(l, k, lda) + 1];
+                double qr = Q[2 * IDX(k, j, ldq)], qi = Q[2 * IDX(k, j, ldq) + 1];
+                ar = dd_add(ar, two_prod(xr, qr));
+                ar = dd_add(ar, two_prod(-xi, qi));
+                ai = dd_add(ai, two_prod(xr, qi));
+                ai = dd_add(ai, two_prod(xi, qr));
+            }
+            double cr = Q[2 * IDX(l, i, ldq)], ci = -Q[2 * IDX(l, i, ldq) + 1];   /* conj(Q(l, i)) */
+            tr = dd_add(tr, dd_mul_d(ar, cr));
+            tr = dd_add(tr, dd_mul_d(ai, -ci));
+            ti = dd_add(ti, dd_mul_d(ai, cr));
+            ti = dd_add(ti, dd_mul_d(ar, ci));
+        }
+        tq[2 * s] = tr.hi + tr.lo;
+        tq[2 * s + 1] = ti.hi + ti.lo;
+        dd_t gr = {0.0, 0.0}, gi = {0.0, 0.0};
+        for (int l = 0; l < n; ++l) {
+            double cr = Q[2 * IDX(l, i, ldq)], ci = -Q[2 * IDX(l, i, ldq) + 1];
+            double qr = Q[2 * IDX(l, j, ldq)], qi = Q[2 * IDX(l, j, ldq) + 1];
+            gr = dd_add(gr, two_prod(cr, qr));
+            gr = dd_add(gr, two_prod(-ci, qi));
+            gi = dd_add(gi, two_prod(cr, qi));
+            gi = dd_add(gi, two_prod(ci, qr));
+        }
+        if (i == j) gr = dd_add(gr, (dd_t){-1.0, 0.0});
+        yq[2 * s] = gr.hi + gr.lo;
+        yq[2 * s + 1] = gi.hi + gi.lo;
+    }
+}
+
 /* Complex residuals in double-double (interleaved complex128 input). */
 void sro_residuals_dd_c(int n, const double *A, int lda, const double *Q, int ldq,
                         double *r_T, double *r_Q)

@@ -53,6 +53,105 @@ template <> struct sr_is_double<double> { static constexpr bool value = true; };
 __device__ inline bool sr_finite(float x) { return isfinite(x); }
 __device__ inline bool sr_finite(double x) { return isfinite(x); }
 
+// ---- complex numbers (interleaved re, im; the layout of complex64/complex128) ----
+struct __align__(8) cf { float x, y; };
+struct __align__(16) cd { double x, y; };
+
+__host__ __device__ inline cf operator+(cf a, cf b) { return {a.x + b.x, a.y + b.y}; }
+__host__ __device__ inline cf operator-(cf a, cf b) { return {a.x - b.x, a.y - b.y}; }
+__host__ __device__ inline cf operator-(cf a) { return {-a.x, -a.y}; }
+__host__ __device__ inline cf operator*(cf a, cf b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__host__ __device__ inline cd operator+(cd a, cd b) { return {a.x + b.x, a.y + b.y}; }
+__host__ __device__ inline cd operator-(cd a, cd b) { return {a.x - b.x, a.y - b.y}; }
+__host__ __device__ inline cd operator-(cd a) { return {-a.x, -a.y}; }
+__host__ __device__ inline cd operator*(cd a, cd b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__host__ __device__ inline cd operator*(double s, cd a) { return {s * a.x, s * a.y}; }
+__host__ __device__ inline bool operator==(cf a, cf b) { return a.x == b.x && a.y == b.y; }
+__host__ __device__ inline bool operator==(cd a, cd b) { return a.x == b.x && a.y == b.y; }
+__host__ __device__ inline cd conj(cd a) { return {a.x, -a.y}; }
+__host__ __device__ inline cf conj(cf a) { return {a.x, -a.y}; }
+__device__ inline bool sr_finite(cf a) { return isfinite(a.x) && isfinite(a.y); }
+__device__ inline bool sr_finite(cd a) { return isfinite(a.x) && isfinite(a.y); }
+
+// c + a * b in the working type (one fused operation per real multiply)
+__device__ inline float sr_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ inline double sr_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ inline cf sr_fma(cf a, cf b, cf c)
+{
+    return {fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y))};
+}
+__device__ inline cd sr_fma(cd a, cd b, cd c)
+{
+    return {fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y))};
+}
+__device__ inline float sr_shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ inline double sr_shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ inline cf sr_shfl(cf v, int src) { return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)}; }
+__device__ inline cd sr_shfl(cd v, int src) { return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)}; }
+// 1 / z by Smith's scaling (avoids overflow in |z|^2)
+__device__ inline float sr_recip(float z) { return 1.0f / z; }
+__device__ inline double sr_recip(double z) { return 1.0 / z; }
+__device__ inline cf sr_recip(cf z)
+{
+    if (fabsf(z.x) >= fabsf(z.y)) {
+        const float r = z.y / z.x, d = z.x + z.y * r;
+        return {1.0f / d, -r / d};
+    }
+    const float r = z.x / z.y, d = z.x * r + z.y;
+    return {r / d, -1.0f / d};
+}
+__device__ inline cd sr_recip(cd z)
+{
+    if (fabs(z.x) >= fabs(z.y)) {
+        const double r = z.y / z.x, d = z.x + z.y * r;
+        return {1.0 / d, -r / d};
+    }
+    const double r = z.x / z.y, d = z.x * r + z.y;
+    return {r / d, -1.0 / d};
+}
+
+// types of the high-precision counterpart (diagonals) and zero; kind tells
+// the four number types apart (float, double, complex64, complex128)
+template <typename T> struct SrNum;
+template <> struct SrNum<float> {
+    using hp = double;
+    static constexpr int kind = 0;
+    __host__ __device__ static float zero() { return 0.0f; }
+    __device__ static float from_hp(double v) { return (float)v; }
+};
+template <> struct SrNum<double> {
+    using hp = double;
+    static constexpr int kind = 1;
+    __host__ __device__ static double zero() { return 0.0; }
+    __device__ static double from_hp(double v) { return v; }
+};
+template <> struct SrNum<cf> {
+    using hp = cd;
+    static constexpr int kind = 2;
+    __host__ __device__ static cf zero() { return {0.0f, 0.0f}; }
+    __device__ static cf from_hp(cd v) { return {(float)v.x, (float)v.y}; }
+};
+template <> struct SrNum<cd> {
+    using hp = cd;
+    static constexpr int kind = 3;
+    __host__ __device__ static cd zero() { return {0.0, 0.0}; }
+    __device__ static cd from_hp(cd v) { return v; }
+};
+
+// widening to the high-precision type, |x|^2 in FP64, conjugate (identity for reals)
+__device__ inline double sr_to_hp(float x) { return (double)x; }
+__device__ inline double sr_to_hp(double x) { return x; }
+__device__ inline cd sr_to_hp(cf x) { return {(double)x.x, (double)x.y}; }
+__device__ inline cd sr_to_hp(cd x) { return x; }
+__device__ inline double sr_abs2(float x) { return (double)x * (double)x; }
+__device__ inline double sr_abs2(double x) { return x * x; }
+__device__ inline double sr_abs2(cf x) { return (double)x.x * (double)x.x + (double)x.y * (double)x.y; }
+__device__ inline double sr_abs2(cd x) { return x.x * x.x + x.y * x.y; }
+__device__ inline float sr_conj(float x) { return x; }
+__device__ inline double sr_conj(double x) { return x; }
+__device__ inline cf sr_conj(cf x) { return conj(x); }
+__device__ inline cd sr_conj(cd x) { return conj(x); }
+
 // Block-wide sum of one double per thread; result valid in thread 0.
 template <int NT>
 __device__ inline double sr_block_sum(double v)

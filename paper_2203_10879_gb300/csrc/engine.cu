@@ -59,7 +59,7 @@ struct schur_refine_ctx {
     // the solve's two streams of work are captured once per (order, buffers)
     cudaStream_t cap_st = nullptr, aux_st = nullptr;
     cudaEvent_t sev0 = nullptr, sev1 = nullptr;
-    struct SolveGraph { int n; const void *TE; int ld; const double *dhp; int fp32; cudaGraphExec_t exec; };
+    struct SolveGraph { int n; const void *TE; int ld; const void *dhp; int kind; cudaGraphExec_t exec; };
     std::vector<SolveGraph> graphs;
     // workers of schur_refine_batched: sub-handles on their own streams
     std::vector<schur_refine_ctx *> subs;
@@ -125,7 +125,9 @@ static void harvest(schur_refine_ctx *h)
 
 namespace {
 
-size_t lp_size(const sr_options &o) { return o.lp == SR_LP_FP32 ? sizeof(float) : sizeof(double); }
+bool is_cplx(const sr_options &o) { return o.dtype == SR_COMPLEX; }
+size_t lp_size(const sr_options &o) { return (o.lp == SR_LP_FP32 ? sizeof(float) : sizeof(double)) * (is_cplx(o) ? 2 : 1); }
+size_t hp_size(const sr_options &o) { return sizeof(double) * (is_cplx(o) ? 2 : 1); }
 
 sr_status check_opts(const sr_options &o)
 {
@@ -135,7 +137,8 @@ sr_status check_opts(const sr_options &o)
     if (o.lp != SR_LP_FP32 && o.lp != SR_LP_FP64) return SR_ERR_INVALID_ARG;
     if (o.qhat_type != SR_QHAT_FP32 && o.qhat_type != SR_QHAT_FP64) return SR_ERR_INVALID_ARG;
     if (o.ozaki_slices > sr::kOzakiMaxSlices) return SR_ERR_INVALID_ARG;
-    if (o.dtype == SR_COMPLEX) return SR_ERR_UNSUPPORTED;
+    // complex data: the emulated products with the complex64 correction path
+    if (o.dtype == SR_COMPLEX && (o.hp_gemm != SR_HP_OZAKI_BF16 || o.lp != SR_LP_FP32)) return SR_ERR_UNSUPPORTED;
     if (o.hp_gemm == SR_HP_OZAKI_BF16 && !sr::kOzakiBuilt) return SR_ERR_UNSUPPORTED;
     return SR_OK;
 }
@@ -263,14 +266,14 @@ sr_status ensure_plan(schur_refine_ctx *h, int n)
 }
 
 template <typename Tl>
-sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const double *dhp)
+sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum<Tl>::hp *dhp)
 {
     SR_TRY(ensure_plan(h, n));
     const int NB = (n + sr::kSolveTile - 1) / sr::kSolveTile;
-    const int fp32 = sizeof(Tl) == 4;
+    const int kind = SrNum<Tl>::kind;
     cudaGraphExec_t exec = nullptr;
     for (auto &g : h->graphs)
-        if (g.n == n && g.TE == TE && g.ld == ld && g.dhp == dhp && g.fp32 == fp32) exec = g.exec;
+        if (g.n == n && g.TE == TE && g.ld == ld && g.dhp == dhp && g.kind == kind) exec = g.exec;
     if (!exec) {
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
@@ -283,7 +286,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const double *dhp)
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e == cudaSuccess) {
-            h->graphs.push_back({n, TE, ld, dhp, fp32, exec});
+            h->graphs.push_back({n, TE, ld, dhp, kind, exec});
         } else {
             // no graph (for example while the caller captures this stream): the same
             // launches, issued directly on the two streams
@@ -291,7 +294,8 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const double *dhp)
             exec = nullptr;
         }
     }
-    SrPhase ph(h, SR_PROF_SOLVE, 2LL * n * n * n / 3, (long long)n * n * (long long)sizeof(Tl), 2LL * NB);
+    const long long fl = 2LL * n * n * n / 3 * (SrNum<Tl>::kind >= 2 ? 4 : 1);   // a complex FMA is 4 real ones
+    SrPhase ph(h, SR_PROF_SOLVE, fl, (long long)n * n * (long long)sizeof(Tl), 2LL * NB);
     if (exec) {
         SR_CUDA_TRY(cudaGraphLaunch(exec, h->st));
     } else {
@@ -336,138 +340,182 @@ sr_status update(schur_refine_ctx *h, int n, const double *Q, int ldq, double *Q
 }
 
 // ---- the pass on the emulated engine ------------------------------------------------
-// Digits are split once and reused: the columns of Q serve A Q, Q^T (A Q) and
-// Q^T Q; the rows of A are split once per call. The low-precision products use
+// Digits are split once and reused: the columns of Q serve A Q, Q^H (A Q) and
+// Q^H Q; the rows of A are split once per call. The low-precision products use
 // kOzakiLpSlices digits (about 24 bits, FP32-class) and only column splits:
-// W^2 = -W^T W, YW = Y^T W (Y symmetric), W^3 = -W^T W^2, W^2 Y = (W^2)^T Y.
+// W^2 = -W^H W, YW = Y^H W (Y Hermitian), W^3 = -W^H W^2, W^2 Y = (W^2)^H Y.
+// The same code serves real (C = false) and complex (C = true) data; the
+// types and epilogues come from OzT<C>.
 
 bool oz_pass(const schur_refine_ctx *h) { return h->opt.hp_gemm == SR_HP_OZAKI_BF16 && h->opt.lp == SR_LP_FP32; }
 int oz_s(const schur_refine_ctx *h) { return h->opt.ozaki_slices > 0 ? h->opt.ozaki_slices : sr::kOzakiDefaultSlices; }
 
-// Y = Q^T Q - I from the column digits of Q in slot OZS_COLS; ||Y||^2 -> dnorm[1]
+template <bool C> struct OzT;
+template <> struct OzT<false> {
+    using H = double;
+    using L = float;
+    using Store = sr::EpStore;
+    using Split = sr::EpSplit<float>;
+    using MinusI = sr::EpMinusI;
+    using Update = sr::EpUpdate;
+    using Delta = sr::EpDeltaD;
+};
+template <> struct OzT<true> {
+    using H = cd;
+    using L = cf;
+    using Store = sr::EpStoreC;
+    using Split = sr::EpSplitC;
+    using MinusI = sr::EpMinusIC;
+    using Update = sr::EpUpdateC;
+    using Delta = sr::EpDeltaDC;
+};
+
+// Y = Q^H Q - I from the column digits of Q in slot OZS_COLS; ||Y||^2 -> dnorm[1]
+template <bool C>
 sr_status oz_gram(schur_refine_ctx *h, int n)
 {
+    using H = typename OzT<C>::H;
     const int s = oz_s(h);
     int blocks = 0;
     SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_COLS, n, n, n, s, true, h->dflags));
     SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_COLS, n, n, s, 1.0, true,
-                             sr::EpMinusI{h->Y, h->nmax}, h->partial, &blocks));
+                             typename OzT<C>::MinusI{(H *)h->Y, h->nmax}, h->partial, &blocks));
     return reduce_to(h, blocks, 1);
 }
 
 // Q_new = Q + alpha * Q X (rows of Q, columns of X)
-sr_status oz_apply(schur_refine_ctx *h, int n, const double *Q, int ldq, const double *X, int ldx, double *Qn,
-                   int ldn, double alpha)
+template <bool C>
+sr_status oz_apply(schur_refine_ctx *h, int n, const void *Q, int ldq, const void *X, int ldx, void *Qn, int ldn,
+                   double alpha)
 {
+    using H = typename OzT<C>::H;
     const int s = oz_s(h);
-    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_QROWS, n, n, Q, ldq, sr::OZ_ROWS, false, s));
-    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_X, n, n, X, ldx, sr::OZ_COLS, false, s));
+    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_QROWS, n, n, Q, ldq, sr::OZ_ROWS, s));
+    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_X, n, n, X, ldx, sr::OZ_COLS, s));
     SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_QROWS, sr::OZS_X, n, n, n, s, false, h->dflags));
     return sr::ozaki_combine(h, h->st, h->oz, sr::OZS_QROWS, sr::OZS_X, n, n, s, 1.0, false,
-                             sr::EpUpdate{Q, ldq, Qn, ldn, alpha}, nullptr, nullptr);
+                             typename OzT<C>::Update{(const H *)Q, ldq, (H *)Qn, ldn, alpha}, nullptr, nullptr);
 }
 
-sr_status oz_ns_init(schur_refine_ctx *h, int n, const double *Q, int ldq, double *Qn, int ldn)
+template <bool C>
+sr_status oz_ns_init(schur_refine_ctx *h, int n, const void *Q, int ldq, void *Qn, int ldn)
 {
-    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_COLS, n, n, Q, ldq, sr::OZ_COLS, false, oz_s(h)));
-    SR_TRY(oz_gram(h, n));
-    return oz_apply(h, n, Q, ldq, h->Y, h->nmax, Qn, ldn, -0.5);
+    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_COLS, n, n, Q, ldq, sr::OZ_COLS, oz_s(h)));
+    SR_TRY(oz_gram<C>(h, n));
+    return oz_apply<C>(h, n, Q, ldq, h->Y, h->nmax, Qn, ldn, -0.5);
 }
 
-sr_status oz_form_residual(schur_refine_ctx *h, int n, const double *Q, int ldq, double *That)
+template <bool C>
+sr_status oz_form_residual(schur_refine_ctx *h, int n, const void *Q, int ldq, void *That)
 {
+    using H = typename OzT<C>::H;
+    using L = typename OzT<C>::L;
     const int s = oz_s(h), ld = h->nmax;
     int blocks = 0;
-    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_COLS, n, n, Q, ldq, sr::OZ_COLS, false, s));
+    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_COLS, n, n, Q, ldq, sr::OZ_COLS, s));
     SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, n, n, n, s, false, h->dflags));
     SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, n, n, s, 1.0, false,
-                             sr::EpStore{h->AQ, ld}, nullptr, nullptr));
-    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_X, n, n, h->AQ, ld, sr::OZ_COLS, false, s));
+                             typename OzT<C>::Store{(H *)h->AQ, ld}, nullptr, nullptr));
+    SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_X, n, n, h->AQ, ld, sr::OZ_COLS, s));
     SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, n, s, false, h->dflags));
     SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, s, 1.0, false,
-                             sr::EpSplit<float>{(float *)h->TE, ld, h->diag, That, n}, h->partial, &blocks));
+                             typename OzT<C>::Split{(L *)h->TE, ld, (H *)h->diag, (H *)That, n}, h->partial,
+                             &blocks));
     return reduce_to(h, blocks, 0);
 }
 
-sr_status oz_update(schur_refine_ctx *h, int n, const double *Q, int ldq, double *Qn, int ldn)
+template <bool C>
+sr_status oz_update(schur_refine_ctx *h, int n, const void *Q, int ldq, void *Qn, int ldn)
 {
     using namespace sr;
+    using H = typename OzT<C>::H;
+    using L = typename OzT<C>::L;
+    using Store = typename OzT<C>::Store;
     const int ld = h->nmax, sl = kOzakiLpSlices;
     OzakiWork &w = h->oz;
     cudaStream_t st = h->st;
-    SR_TRY(oz_gram(h, n));   // Q unchanged since oz_form_residual: its column digits are current
+    H *Wd = (H *)h->Wd, *W2d = (H *)h->W2d, *W2Yd = (H *)h->W2Yd, *W2YWd = (H *)h->W2YWd, *Y = (H *)h->Y;
+    SR_TRY(oz_gram<C>(h, n));   // Q unchanged since oz_form_residual: its column digits are current
     {
-        SrPhase ph(h, SR_PROF_OTHER, 0, 12LL * n * n, 1);
+        SrPhase ph(h, SR_PROF_OTHER, 0, (long long)n * n * (long long)(sizeof(L) + sizeof(H)), 1);
         dim3 grid((n + 31) / 32, (n + 31) / 32);
-        form_skew_kernel<float><<<grid, 256, 0, st>>>(n, (const float *)h->TE, ld, h->Wd, ld);
+        form_skew_kernel<L><<<grid, 256, 0, st>>>(n, (const L *)h->TE, ld, Wd, ld);
         SR_CUDA_TRY(cudaGetLastError());
     }
-    double *YW = h->AQ;   // A Q is dead after the residual
-    SR_TRY(ozaki_split(h, st, w, OZS_W, n, n, h->Wd, ld, OZ_COLS, false, sl));
-    SR_TRY(ozaki_split(h, st, w, OZS_Y, n, n, h->Y, ld, OZ_COLS, false, sl));
+    H *YW = (H *)h->AQ;   // A Q is dead after the residual
+    SR_TRY(ozaki_split(h, st, w, OZS_W, n, n, Wd, ld, OZ_COLS, sl));
+    SR_TRY(ozaki_split(h, st, w, OZS_Y, n, n, Y, ld, OZ_COLS, sl));
     SR_TRY(ozaki_product(h, st, w, OZS_W, OZS_W, n, n, n, sl, true, h->dflags));
-    SR_TRY(ozaki_combine(h, st, w, OZS_W, OZS_W, n, n, sl, -1.0, true, EpStore{h->W2d, ld}, nullptr, nullptr));
+    SR_TRY(ozaki_combine(h, st, w, OZS_W, OZS_W, n, n, sl, -1.0, true, Store{W2d, ld}, nullptr, nullptr));
     SR_TRY(ozaki_product(h, st, w, OZS_Y, OZS_W, n, n, n, sl, false, h->dflags));
-    SR_TRY(ozaki_combine(h, st, w, OZS_Y, OZS_W, n, n, sl, 1.0, false, EpStore{YW, ld}, nullptr, nullptr));
-    SR_TRY(ozaki_split(h, st, w, OZS_W2, n, n, h->W2d, ld, OZ_COLS, false, sl));
+    SR_TRY(ozaki_combine(h, st, w, OZS_Y, OZS_W, n, n, sl, 1.0, false, Store{YW, ld}, nullptr, nullptr));
+    SR_TRY(ozaki_split(h, st, w, OZS_W2, n, n, W2d, ld, OZ_COLS, sl));
     if (h->opt.full_sigma) {
         SR_TRY(ozaki_product(h, st, w, OZS_W2, OZS_Y, n, n, n, sl, false, h->dflags));
-        SR_TRY(ozaki_combine(h, st, w, OZS_W2, OZS_Y, n, n, sl, 1.0, false, EpStore{h->W2Yd, ld}, nullptr,
-                             nullptr));
-        SR_TRY(ozaki_split(h, st, w, 7, n, n, h->W2Yd, ld, OZ_ROWS, false, sl));
+        SR_TRY(ozaki_combine(h, st, w, OZS_W2, OZS_Y, n, n, sl, 1.0, false, Store{W2Yd, ld}, nullptr, nullptr));
+        SR_TRY(ozaki_split(h, st, w, 7, n, n, W2Yd, ld, OZ_ROWS, sl));
         SR_TRY(ozaki_product(h, st, w, 7, OZS_W, n, n, n, sl, false, h->dflags));
-        SR_TRY(ozaki_combine(h, st, w, 7, OZS_W, n, n, sl, 1.0, false, EpStore{h->W2YWd, ld}, nullptr, nullptr));
+        SR_TRY(ozaki_combine(h, st, w, 7, OZS_W, n, n, sl, 1.0, false, Store{W2YWd, ld}, nullptr, nullptr));
     }
     SR_TRY(ozaki_product(h, st, w, OZS_W, OZS_W2, n, n, n, sl, false, h->dflags));
-    EpDeltaD ed{h->Wd, h->Y, YW, h->W2d, h->opt.full_sigma ? h->W2Yd : nullptr,
-                h->opt.full_sigma ? h->W2YWd : nullptr, ld, h->Delta, ld};
+    typename OzT<C>::Delta ed{Wd, Y, YW, W2d, h->opt.full_sigma ? W2Yd : nullptr,
+                              h->opt.full_sigma ? W2YWd : nullptr, ld, (H *)h->Delta, ld};
     SR_TRY(ozaki_combine(h, st, w, OZS_W, OZS_W2, n, n, sl, -1.0, false, ed, nullptr, nullptr));
-    return oz_apply(h, n, Q, ldq, h->Delta, ld, Qn, ldn, 0.5);
+    return oz_apply<C>(h, n, Q, ldq, h->Delta, ld, Qn, ldn, 0.5);
 }
 
-sr_status copy_q(schur_refine_ctx *h, int n, const double *src, int lds, double *dst, int ldd)
+sr_status copy_q(schur_refine_ctx *h, int n, const void *src, int lds, void *dst, int ldd)
 {
     if (src == dst) return SR_OK;
-    SrPhase ph(h, SR_PROF_OTHER, 0, 16LL * n * n, 1);
-    SR_CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)ldd * sizeof(double), src, (size_t)lds * sizeof(double),
-                                  (size_t)n * sizeof(double), n, cudaMemcpyDeviceToDevice, h->st));
+    const size_t es = hp_size(h->opt);
+    SrPhase ph(h, SR_PROF_OTHER, 0, 2LL * n * n * (long long)es, 1);
+    SR_CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)ldd * es, src, (size_t)lds * es, (size_t)n * es, n,
+                                  cudaMemcpyDeviceToDevice, h->st));
     return SR_OK;
 }
 
-template <typename Tl>
-sr_status run_step(schur_refine_ctx *h, int n, const double *A, int lda, double *dQ, int ldq, const void *dQhat,
-                   double *dT, sr_norms *out)
+// One call of Alg. 4. Tl: low-precision type of the native path (float or
+// double); C: complex data (emulated products only).
+template <typename Tl, bool C>
+sr_status run_step(schur_refine_ctx *h, int n, const void *A, int lda, void *dQ, int ldq, const void *dQhat,
+                   void *dT, sr_norms *out)
 {
+    using H = typename OzT<C>::H;
     const int ld = h->nmax;
     const double tol = tol_of(h, n);
     const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 10;
+    const bool oz = oz_pass(h);
+    if (C && !oz) return SR_ERR_UNSUPPORTED;
     sr_norms nr{};
     nr.stril_rel = nr.orth = nr.w_norm = NAN;
     SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
-    SR_TRY(sumsq<double>(h, n, A, lda, 0, 3));
-    if (oz_pass(h))   // rows of A: split once, used by every A Q of this call
-        SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_ROWS, n, n, A, lda, sr::OZ_ROWS, false, oz_s(h)));
+    SR_TRY(sumsq<H>(h, n, (const H *)A, lda, 0, 3));
+    if (oz)   // rows of A: split once, used by every A Q of this call
+        SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_ROWS, n, n, A, lda, sr::OZ_ROWS, oz_s(h)));
 
     // The working factor alternates between the caller's buffer and Qw.
-    double *Qc = dQ, *Qo = h->Qw;
+    H *Qc = (H *)dQ, *Qo = (H *)h->Qw;
     int ldc = ldq, ldo = ld;
     double y_last = NAN;
     if (dQhat) {
         // Alg. 4: convert Qhat to hp, then Q <- 1/2 Qhat (3I - Qhat^H Qhat)
         {
             dim3 grid((n + 255) / 256, n);
-            SrPhase ph(h, SR_PROF_OTHER, 0, 12LL * n * n, 1);
+            SrPhase ph(h, SR_PROF_OTHER, 0, 12LL * n * n * (C ? 2 : 1), 1);
+            using Lq = typename OzT<C>::L;
             if (h->opt.qhat_type == SR_QHAT_FP32)
-                sr::convert_to_f64_kernel<float><<<grid, 256, 0, h->st>>>(n, (const float *)dQhat, ldq, dQ, ldq);
+                sr::convert_to_hp_kernel<Lq><<<grid, 256, 0, h->st>>>(n, (const Lq *)dQhat, ldq, (H *)dQ, ldq);
             else
-                sr::convert_to_f64_kernel<double><<<grid, 256, 0, h->st>>>(n, (const double *)dQhat, ldq, dQ, ldq);
+                sr::convert_to_hp_kernel<H><<<grid, 256, 0, h->st>>>(n, (const H *)dQhat, ldq, (H *)dQ, ldq);
             SR_CUDA_TRY(cudaGetLastError());
         }
-        if (oz_pass(h)) {
-            SR_TRY(oz_ns_init(h, n, dQ, ldq, Qo, ldo));
-        } else {
-            SR_TRY(hp_gemm(h, true, n, n, n, dQ, ldq, dQ, ldq, sr::EpMinusI{h->Y, ld}, 1));
-            SR_TRY(hp_gemm(h, false, n, n, n, dQ, ldq, h->Y, ld, sr::EpUpdate{dQ, ldq, Qo, ldo, -0.5}, -1));
+        if (oz) {
+            SR_TRY(oz_ns_init<C>(h, n, dQ, ldq, Qo, ldo));
+        } else if constexpr (!C) {
+            SR_TRY(hp_gemm(h, true, n, n, n, (const double *)dQ, ldq, (const double *)dQ, ldq,
+                           sr::EpMinusI{h->Y, ld}, 1));
+            SR_TRY(hp_gemm(h, false, n, n, n, (const double *)dQ, ldq, h->Y, ld,
+                           sr::EpUpdate{(const double *)dQ, ldq, Qo, ldo, -0.5}, -1));
         }
         std::swap(Qc, Qo);
         std::swap(ldc, ldo);
@@ -480,10 +528,10 @@ sr_status run_step(schur_refine_ctx *h, int n, const double *A, int lda, double 
     sr_status status = SR_ERR_NOT_CONVERGED;
     double prev = INFINITY;
     for (int k = 1; k <= max_iter; ++k) {
-        if (oz_pass(h))
-            SR_TRY(oz_form_residual(h, n, Qc, ldc, dT));
-        else
-            SR_TRY(form_residual<Tl>(h, n, A, lda, Qc, ldc, dT));
+        if (oz)
+            SR_TRY(oz_form_residual<C>(h, n, Qc, ldc, dT));
+        else if constexpr (!C)
+            SR_TRY(form_residual<Tl>(h, n, (const double *)A, lda, Qc, ldc, (double *)dT));
         nr.hp_gemms += 2;
         nr.iters = k;
         SR_TRY(read_back(h));
@@ -496,16 +544,21 @@ sr_status run_step(schur_refine_ctx *h, int n, const double *A, int lda, double 
         if (rT <= tol && ok_y) { status = SR_OK; break; }
         if (k >= 3 && rT > 10.0 * prev) { status = SR_ERR_NOT_CONVERGED; break; }
         prev = rT;
-        SR_TRY(solve<Tl>(h, n, (Tl *)h->TE, ld, h->diag));
-        SR_TRY(sumsq<Tl>(h, n, (const Tl *)h->TE, ld, 1, 2));
+        if constexpr (C) {
+            SR_TRY(solve<cf>(h, n, (cf *)h->TE, ld, (const cd *)h->diag));
+            SR_TRY(sumsq<cf>(h, n, (const cf *)h->TE, ld, 1, 2));
+        } else {
+            SR_TRY(solve<Tl>(h, n, (Tl *)h->TE, ld, h->diag));
+            SR_TRY(sumsq<Tl>(h, n, (const Tl *)h->TE, ld, 1, 2));
+        }
         SR_TRY(read_back(h));
         const int f = host_flags(h);
         if (f & SR_FLAG_NONDISTINCT) { status = SR_ERR_NONDISTINCT; break; }
         if (f & SR_FLAG_NONFINITE) { status = SR_ERR_NONFINITE; break; }
         nr.w_norm = sqrt(2.0 * h->hbuf[2]);
-        if (oz_pass(h))
-            SR_TRY(oz_update(h, n, Qc, ldc, Qo, ldo));
-        else
+        if (oz)
+            SR_TRY(oz_update<C>(h, n, Qc, ldc, Qo, ldo));
+        else if constexpr (!C)
             SR_TRY(update<Tl>(h, n, Qc, ldc, Qo, ldo));
         nr.hp_gemms += 2;
         std::swap(Qc, Qo);
@@ -631,21 +684,25 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     h->st = (cudaStream_t)cuda_stream;
     cudaGetDevice(&h->dev);
     const size_t nn = (size_t)n_max * (size_t)n_max;
-    const size_t lps = lp_size(o);
+    const size_t lps = lp_size(o), hps = hp_size(o);
     const size_t tiles16 = ((size_t)(n_max + 15) / 16) * ((size_t)(n_max + 15) / 16);
     h->npartial = std::max<size_t>(tiles16, 4096);
     cudaError_t e = cudaSuccess;
 #define SR_ALLOC(ptr, bytes)                                             \
     if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes));
-    SR_ALLOC(h->AQ, nn * sizeof(double));
-    SR_ALLOC(h->Qw, nn * sizeof(double));
-    SR_ALLOC(h->Y, nn * sizeof(double));
-    SR_ALLOC(h->Delta, nn * sizeof(double));
-    SR_ALLOC(h->diag, (size_t)n_max * sizeof(double));
+    SR_ALLOC(h->AQ, nn * hps);
+    SR_ALLOC(h->Qw, nn * hps);
+    SR_ALLOC(h->Y, nn * hps);
+    SR_ALLOC(h->Delta, nn * hps);
+    SR_ALLOC(h->diag, (size_t)n_max * hps);
     SR_ALLOC(h->TE, nn * lps);
-    SR_ALLOC(h->W2, nn * lps);
-    SR_ALLOC(h->YW, nn * lps);
-    if (o.full_sigma) {
+    // low-precision products of the native path
+    const bool native_lp = !(o.hp_gemm == SR_HP_OZAKI_BF16 && o.lp == SR_LP_FP32);
+    if (native_lp) {
+        SR_ALLOC(h->W2, nn * lps);
+        SR_ALLOC(h->YW, nn * lps);
+    }
+    if (o.full_sigma && native_lp) {
         SR_ALLOC(h->W2Y, nn * lps);
         SR_ALLOC(h->W2YW, nn * lps);
     }
@@ -660,7 +717,7 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->sev1, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(h->dnorm, 0, 8 * sizeof(double));
     if (e == cudaSuccess && o.hp_gemm == SR_HP_OZAKI_BF16) {
-        if (n_max > sr::kOzakiMaxK) {
+        if (n_max > sr::ozaki_k_limit(is_cplx(o))) {
             schur_refine_destroy(h);
             return SR_ERR_UNSUPPORTED;
         }
@@ -670,12 +727,12 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
         if (lp_oz) {
             caps[sr::OZS_W] = caps[sr::OZS_Y] = caps[sr::OZS_W2] = sr::kOzakiLpSlices;
             if (o.full_sigma) caps[7] = sr::kOzakiLpSlices;
-            e = cudaMalloc((void **)&h->Wd, nn * sizeof(double));
-            if (e == cudaSuccess) e = cudaMalloc((void **)&h->W2d, nn * sizeof(double));
-            if (e == cudaSuccess && o.full_sigma) e = cudaMalloc((void **)&h->W2Yd, nn * sizeof(double));
-            if (e == cudaSuccess && o.full_sigma) e = cudaMalloc((void **)&h->W2YWd, nn * sizeof(double));
+            e = cudaMalloc((void **)&h->Wd, nn * hps);
+            if (e == cudaSuccess) e = cudaMalloc((void **)&h->W2d, nn * hps);
+            if (e == cudaSuccess && o.full_sigma) e = cudaMalloc((void **)&h->W2Yd, nn * hps);
+            if (e == cudaSuccess && o.full_sigma) e = cudaMalloc((void **)&h->W2YWd, nn * hps);
         }
-        if (e == cudaSuccess) e = sr::ozaki_alloc(h->oz, n_max, caps);
+        if (e == cudaSuccess) e = sr::ozaki_alloc(h->oz, n_max, caps, is_cplx(o));
     }
     if (e != cudaSuccess) {
         sr_set_last_cuda_error(e);
@@ -692,9 +749,9 @@ sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, vo
                             void *dT, sr_norms *out)
 {
     if (!h || !dA || !dQ || n < 1 || n > h->nmax || lda < n || ldq < n) return SR_ERR_INVALID_ARG;
-    if (h->opt.lp == SR_LP_FP32)
-        return run_step<float>(h, n, (const double *)dA, lda, (double *)dQ, ldq, dQhat, (double *)dT, out);
-    return run_step<double>(h, n, (const double *)dA, lda, (double *)dQ, ldq, dQhat, (double *)dT, out);
+    if (is_cplx(h->opt)) return run_step<float, true>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
+    if (h->opt.lp == SR_LP_FP32) return run_step<float, false>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
+    return run_step<double, false>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
 }
 
 sr_status schur_refine_batched(schur_refine_t h, int batch, const int *n, const void *const *dA, void *const *dQ,
@@ -785,21 +842,39 @@ sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int ld
     if (!h || !dA || !dQ || !stril_rel || !orth || n < 1 || n > h->nmax || lda < n || ldq < n)
         return SR_ERR_INVALID_ARG;
     const int ld = h->nmax;
-    const double *A = (const double *)dA, *Q = (const double *)dQ;
     const size_t tiles = (size_t)((n + 15) / 16) * (size_t)((n + 15) / 16);
     if (tiles > h->npartial) return SR_ERR_INVALID_ARG;
     dim3 grid((n + 15) / 16, (n + 15) / 16);
-    // M = A Q in double-double: hi in AQ, lo in Delta
-    sr::gemm_dd_kernel<0><<<grid, 256, 0, h->st>>>(n, 0, A, lda, Q, nullptr, ldq, h->AQ, h->Delta, ld, nullptr);
-    SR_CUDA_TRY(cudaGetLastError());
-    sr::gemm_dd_kernel<1><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, h->AQ, h->Delta, ld, nullptr, nullptr, 0,
-                                                   h->partial);
-    SR_CUDA_TRY(cudaGetLastError());
-    SR_TRY(reduce_to(h, (int)tiles, 4));
-    sr::gemm_dd_kernel<2><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, Q, nullptr, ldq, nullptr, nullptr, 0, h->partial);
-    SR_CUDA_TRY(cudaGetLastError());
-    SR_TRY(reduce_to(h, (int)tiles, 5));
-    SR_TRY(sumsq<double>(h, n, A, lda, 0, 6));
+    if (is_cplx(h->opt)) {
+        const cd *A = (const cd *)dA, *Q = (const cd *)dQ;
+        cd *Mhi = (cd *)h->AQ, *Mlo = (cd *)h->Delta;
+        sr::gemm_dd_c_kernel<0><<<grid, 256, 0, h->st>>>(n, 0, A, lda, Q, nullptr, ldq, Mhi, Mlo, ld, nullptr);
+        SR_CUDA_TRY(cudaGetLastError());
+        sr::gemm_dd_c_kernel<1><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, Mhi, Mlo, ld, nullptr, nullptr, 0,
+                                                         h->partial);
+        SR_CUDA_TRY(cudaGetLastError());
+        SR_TRY(reduce_to(h, (int)tiles, 4));
+        sr::gemm_dd_c_kernel<2><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, Q, nullptr, ldq, nullptr, nullptr, 0,
+                                                         h->partial);
+        SR_CUDA_TRY(cudaGetLastError());
+        SR_TRY(reduce_to(h, (int)tiles, 5));
+        SR_TRY(sumsq<cd>(h, n, A, lda, 0, 6));
+    } else {
+        const double *A = (const double *)dA, *Q = (const double *)dQ;
+        // M = A Q in double-double: hi in AQ, lo in Delta
+        sr::gemm_dd_kernel<0><<<grid, 256, 0, h->st>>>(n, 0, A, lda, Q, nullptr, ldq, h->AQ, h->Delta, ld,
+                                                       nullptr);
+        SR_CUDA_TRY(cudaGetLastError());
+        sr::gemm_dd_kernel<1><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, h->AQ, h->Delta, ld, nullptr, nullptr, 0,
+                                                       h->partial);
+        SR_CUDA_TRY(cudaGetLastError());
+        SR_TRY(reduce_to(h, (int)tiles, 4));
+        sr::gemm_dd_kernel<2><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, Q, nullptr, ldq, nullptr, nullptr, 0,
+                                                       h->partial);
+        SR_CUDA_TRY(cudaGetLastError());
+        SR_TRY(reduce_to(h, (int)tiles, 5));
+        SR_TRY(sumsq<double>(h, n, A, lda, 0, 6));
+    }
     SR_TRY(read_back(h));
     *stril_rel = sqrt(h->hbuf[4]) / sqrt(h->hbuf[6]);
     *orth = sqrt(h->hbuf[5]);
@@ -810,7 +885,9 @@ sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, cons
 {
     if (!h || !dTE || !dDiag || n < 1 || n > h->nmax || ld < n) return SR_ERR_INVALID_ARG;
     SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
-    if (h->opt.lp == SR_LP_FP32)
+    if (is_cplx(h->opt))
+        SR_TRY(solve<cf>(h, n, (cf *)dTE, ld, (const cd *)dDiag));
+    else if (h->opt.lp == SR_LP_FP32)
         SR_TRY(solve<float>(h, n, (float *)dTE, ld, (const double *)dDiag));
     else
         SR_TRY(solve<double>(h, n, (double *)dTE, ld, (const double *)dDiag));
@@ -828,8 +905,12 @@ sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, c
     if (m > h->nmax || n > h->nmax || k > h->nmax) return SR_ERR_INVALID_ARG;
     if (lda < (transA ? k : m) || ldb < k || ldc < m) return SR_ERR_INVALID_ARG;
     SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
-    SR_TRY(hp_gemm(h, transA != 0, m, n, k, (const double *)dA, lda, (const double *)dB, ldb,
-                   sr::EpStore{(double *)dC, ldc}, -1));
+    if (is_cplx(h->opt))
+        SR_TRY(sr::ozaki_gemm(h, h->st, h->oz, transA != 0, m, n, k, dA, lda, dB, ldb, sr::EpStoreC{(cd *)dC, ldc},
+                              nullptr, nullptr, h->opt.ozaki_slices, h->dflags));
+    else
+        SR_TRY(hp_gemm(h, transA != 0, m, n, k, (const double *)dA, lda, (const double *)dB, ldb,
+                       sr::EpStore{(double *)dC, ldc}, -1));
     SR_TRY(read_back(h));
     if (timed_out(h)) return SR_ERR_TIMEOUT;
     return SR_OK;

@@ -103,38 +103,99 @@ struct EpDeltaD {
     }
 };
 
+// ---- complex epilogues (v = complex128 value of the entry) ------------------------
+// The same operations on complex data; kComplex marks them for the emulated
+// products' combine step.
+
+struct EpStoreC {
+    static constexpr bool kComplex = true;
+    cd *C; int ld;
+    __device__ double operator()(int i, int j, cd v) const { C[sr_idx(i, j, ld)] = v; return 0.0; }
+};
+
+struct EpSplitC {
+    static constexpr bool kComplex = true;
+    cf *TE; int ldte; cd *diag; cd *That; int ldt;
+    __device__ double operator()(int i, int j, cd v) const
+    {
+        TE[sr_idx(i, j, ldte)] = cf{(float)v.x, (float)v.y};
+        if (That) That[sr_idx(i, j, ldt)] = v;
+        if (i == j) diag[i] = v;
+        return i > j ? v.x * v.x + v.y * v.y : 0.0;
+    }
+};
+
+struct EpMinusIC {
+    static constexpr bool kComplex = true;
+    cd *Y; int ld;
+    __device__ double operator()(int i, int j, cd v) const
+    {
+        if (i == j) v.x -= 1.0;
+        Y[sr_idx(i, j, ld)] = v;
+        return v.x * v.x + v.y * v.y;
+    }
+};
+
+struct EpUpdateC {
+    static constexpr bool kComplex = true;
+    const cd *Q; int ldq; cd *Qn; int ldn; double alpha;
+    __device__ double operator()(int i, int j, cd v) const
+    {
+        const cd q = Q[sr_idx(i, j, ldq)];
+        Qn[sr_idx(i, j, ldn)] = cd{fma(alpha, v.x, q.x), fma(alpha, v.y, q.y)};
+        return 0.0;
+    }
+};
+
+struct EpDeltaDC {
+    static constexpr bool kComplex = true;
+    const cd *W, *Y, *YW, *W2, *W2Y, *W2YW; int ld;
+    cd *Delta; int ldd;
+    __device__ double operator()(int i, int j, cd v) const
+    {
+        const size_t p = sr_idx(i, j, ld);
+        cd d = 2.0 * W[p] - Y[p] - YW[p] + W2[p] + v;
+        if (W2Y) d = d + W2Y[p] + W2YW[p];
+        Delta[sr_idx(i, j, ldd)] = d;
+        return 0.0;
+    }
+};
+
 // ---- small kernels -----------------------------------------------------------
 
-// W = L - L^H in FP64 from the strictly lower triangle of L (32 x 32 tiles,
-// both the tile and its transpose staged in shared memory).
+// W = L - L^H in high precision (FP64 or complex128) from the strictly lower
+// triangle of L (32 x 32 tiles, both the tile and its transpose staged in
+// shared memory).
 template <typename Tl>
 __global__ void __launch_bounds__(256) form_skew_kernel(int n, const Tl *__restrict__ L, int ldl,
-                                                        double *__restrict__ W, int ldw)
+                                                        typename SrNum<Tl>::hp *__restrict__ W, int ldw)
 {
-    __shared__ double a[32][33], b[32][33];
+    using H = typename SrNum<Tl>::hp;
+    __shared__ H a[32][33], b[32][33];
+    const H z = SrNum<H>::zero();
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int q = ty; q < 32; q += 8) {
         const int i = i0 + tx, j = j0 + q;          // tile (I, J), rows i
-        a[tx][q] = (i < n && j < n) ? (double)L[sr_idx(i, j, ldl)] : 0.0;
+        a[tx][q] = (i < n && j < n) ? sr_to_hp(L[sr_idx(i, j, ldl)]) : z;
         const int i2 = j0 + tx, j2 = i0 + q;        // tile (J, I)
-        b[tx][q] = (i2 < n && j2 < n) ? (double)L[sr_idx(i2, j2, ldl)] : 0.0;
+        b[tx][q] = (i2 < n && j2 < n) ? sr_to_hp(L[sr_idx(i2, j2, ldl)]) : z;
     }
     __syncthreads();
     for (int q = ty; q < 32; q += 8) {
         const int i = i0 + tx, j = j0 + q;
-        if (i < n && j < n) W[sr_idx(i, j, ldw)] = (i > j) ? a[tx][q] : ((i < j) ? -b[q][tx] : 0.0);
+        if (i < n && j < n) W[sr_idx(i, j, ldw)] = (i > j) ? a[tx][q] : ((i < j) ? -sr_conj(b[q][tx]) : z);
     }
 }
 
 
 template <typename Tin>
-__global__ void convert_to_f64_kernel(int n, const Tin *__restrict__ src, int lds, double *__restrict__ dst,
-                                      int ldd)
+__global__ void convert_to_hp_kernel(int n, const Tin *__restrict__ src, int lds,
+                                     typename SrNum<Tin>::hp *__restrict__ dst, int ldd)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
-    if (i < n) dst[sr_idx(i, j, ldd)] = (double)src[sr_idx(i, j, lds)];
+    if (i < n) dst[sr_idx(i, j, ldd)] = sr_to_hp(src[sr_idx(i, j, lds)]);
 }
 
 // partial[block] = sum of squares of the selected part of an n x n matrix
@@ -148,8 +209,7 @@ __global__ void __launch_bounds__(256) sumsq_kernel(int n, const T *__restrict__
     for (size_t e = (size_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (size_t)gridDim.x * 256) {
         const int i = (int)(e % n), j = (int)(e / n);
         if (part == 1 && i <= j) continue;
-        const double v = (double)M[sr_idx(i, j, ld)];
-        s += v * v;
+        s += sr_abs2(M[sr_idx(i, j, ld)]);
     }
     s = sr_block_sum<256>(s);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -257,6 +317,78 @@ gemm_dd_kernel(int n, int transA, const double *__restrict__ A, int lda, const d
                 if (i == j) acc = dd_plus(acc, {-1.0, 0.0});
                 const double v = acc.hi + acc.lo;
                 part = (i == j ? 1.0 : 2.0) * v * v;
+            }
+        }
+    }
+    if (MODE != 0) {
+        part = sr_block_sum<256>(part);
+        if (threadIdx.x == 0) partial[bid] = part;
+    }
+}
+
+// Complex form of gemm_dd_kernel (complex128 data; op(A) = A^H when transA):
+// real and imaginary parts each accumulated in double-double.
+template <int MODE>
+__global__ void __launch_bounds__(256)
+gemm_dd_c_kernel(int n, int transA, const cd *__restrict__ A, int lda, const cd *__restrict__ Bhi,
+                 const cd *__restrict__ Blo, int ldb, cd *__restrict__ Chi, cd *__restrict__ Clo, int ldc,
+                 double *__restrict__ partial)
+{
+    constexpr int T = 16;
+    __shared__ cd As[T][T + 1];
+    __shared__ cd Bh[T][T + 1];
+    __shared__ cd Bl[T][T + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.x * T, j0 = blockIdx.y * T;
+    const size_t bid = blockIdx.x + (size_t)gridDim.x * blockIdx.y;
+    if ((MODE == 1 && i0 + T - 1 <= j0) || (MODE == 2 && i0 > j0 + T - 1)) {
+        if (threadIdx.x == 0) partial[bid] = 0.0;
+        return;
+    }
+    const int i = i0 + tx, j = j0 + ty;
+    const cd z = {0.0, 0.0};
+    ddv re = {0.0, 0.0}, im = {0.0, 0.0};
+    for (int k0 = 0; k0 < n; k0 += T) {
+        {
+            const int ii = transA ? ty : tx, kk = transA ? tx : ty;
+            const int gi = i0 + ii, gk = k0 + kk;
+            cd v = z;
+            if (gi < n && gk < n) v = transA ? conj(A[sr_idx(gk, gi, lda)]) : A[sr_idx(gi, gk, lda)];
+            As[kk][ii] = v;
+        }
+        {
+            const int gk = k0 + tx, gj = j0 + ty;
+            const bool in = gk < n && gj < n;
+            Bh[tx][ty] = in ? Bhi[sr_idx(gk, gj, ldb)] : z;
+            Bl[tx][ty] = (in && Blo) ? Blo[sr_idx(gk, gj, ldb)] : z;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < T; ++kk) {
+            const cd a = As[kk][tx], bh = Bh[kk][ty], bl = Bl[kk][ty];
+            // (a.x + i a.y)(b.x + i b.y): four exact products with the low parts folded in
+            re = dd_plus(re, dd_times(a.x, bh.x, bl.x));
+            re = dd_plus(re, dd_times(-a.y, bh.y, bl.y));
+            im = dd_plus(im, dd_times(a.x, bh.y, bl.y));
+            im = dd_plus(im, dd_times(a.y, bh.x, bl.x));
+        }
+        __syncthreads();
+    }
+    double part = 0.0;
+    if (i < n && j < n) {
+        if (MODE == 0) {
+            Chi[sr_idx(i, j, ldc)] = cd{re.hi, im.hi};
+            Clo[sr_idx(i, j, ldc)] = cd{re.lo, im.lo};
+        } else if (MODE == 1) {
+            if (i > j) {
+                const double vr = re.hi + re.lo, vi = im.hi + im.lo;
+                part = vr * vr + vi * vi;
+            }
+        } else {
+            if (i <= j) {
+                if (i == j) re = dd_plus(re, {-1.0, 0.0});
+                const double vr = re.hi + re.lo, vi = im.hi + im.lo;
+                part = (i == j ? 1.0 : 2.0) * (vr * vr + vi * vi);
             }
         }
     }

@@ -1,14 +1,16 @@
 // Split kernels and the tcgen05 slice-product kernel of the emulated FP64
 // products (see ozaki.cuh for the scheme).
 //
-// Slice-product kernel, one CTA per 128 x 128 output tile, 10 warps:
+// Slice-product kernel, persistent (one CTA per SM walks the 128 x 256 output
+// tiles), 10 warps:
 //   warp 0      TMA producer: K-blocks of 64 bf16 (128 bytes, 128B swizzle)
 //               of one B digit matrix (MMA "A", 128 rows = output columns j)
-//               and one op(A) digit matrix (MMA "B", 128 rows = output rows i)
+//               and one op(A) digit matrix (MMA "B", 256 rows = output rows i)
 //               into a 4-stage shared-memory ring.
-//   warp 1      allocates 256 TMEM columns (two 128-column FP32 accumulators)
-//               and issues tcgen05.mma (M = N = 128, K = 16) from one thread;
-//               each 256-long K-chunk of one digit pair fills one accumulator.
+//   warp 1      allocates 512 TMEM columns (two 256-column FP32 accumulators)
+//               and issues tcgen05.mma (M = 128, N = 256, K = 16) from one
+//               thread; each 256-long K-chunk of one digit pair fills one
+//               accumulator.
 //   warps 2..9  drain a full accumulator with tcgen05.ld (warp w reads TMEM
 //               lanes 32*(w%4).., half (w-2)/4 of the columns), convert the
 //               exact FP32 integers to int32 by adding 1.5*2^23 and taking the
@@ -45,6 +47,7 @@ constexpr int SMEM_BYTES = STAGES * (A_BYTES + B_BYTES) + 1024 + 256;
 // M>>4 at bit 24.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t IDESC_NEG_A = 1u << 13;   // negate the A operand (complex products)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -120,7 +123,8 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
     return d;
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t acc)
 {
     asm volatile(
         "{\n"
@@ -128,7 +132,7 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
         "setp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
         "}\n" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar)
@@ -163,21 +167,44 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 
 struct MmaArgs {
     int s;            // digits per operand
-    int nch;          // K-chunks of 256
+    int nch;          // K-chunks of 256 (complex: both halves)
     int Pmax;         // row stride of digit matrices and planes
     int tiles_i;      // row tiles (BN rows of C)
-    int ntiles;       // tiles_i * column tiles
+    int tiles_j;      // column tiles (BM columns of C) per part
+    int ntiles;       // tiles_i * tiles_j (* 2 when complex)
     int symmetric;    // 1: skip tiles entirely below the diagonal (mirrored by the combine)
-    int32_t *planes;  // [s][Pmax][Pmax]
+    int cplx;         // stacked [re; im] vectors; tiles of the second half form imaginary parts
+    int conj;         // complex, row side conjugated (the sign g of the header)
+    int32_t *planes;  // [s][pstride]
+    size_t pstride;   // Pmax * Pmax (2 Pmax * Pmax when complex)
     int *flags;
 };
 
-// tile -> (first row i0, first column j0); false if the tile is skipped
-__device__ __forceinline__ bool tile_coords(const MmaArgs &a, int tile, int &i0, int &j0)
+// tile -> (first row i0, first column j0, imaginary part?); false if skipped
+__device__ __forceinline__ bool tile_coords(const MmaArgs &a, int tile, int &i0, int &j0, int &im)
 {
     i0 = (tile % a.tiles_i) * BN;
-    j0 = (tile / a.tiles_i) * BM;
+    int bj = tile / a.tiles_i;
+    im = bj >= a.tiles_j;
+    if (im) bj -= a.tiles_j;
+    j0 = bj * BM;
     return !(a.symmetric && i0 > j0 + BM - 1);
+}
+
+// column-side K-chunk read for chunk c: the halves are swapped for an imaginary part
+__device__ __forceinline__ int col_chunk(const MmaArgs &a, int c, int im)
+{
+    if (!im) return c;
+    const int hh = a.nch >> 1;
+    return c < hh ? c + hh : c - hh;
+}
+
+// the chunks whose product enters with a minus sign: second half, and
+// re with g = +1 (-r2.c2) or im with g = -1 (-r2.c1)
+__device__ __forceinline__ uint32_t chunk_idesc(const MmaArgs &a, int c, int im)
+{
+    const bool neg = a.cplx && c >= (a.nch >> 1) && (im == a.conj);
+    return neg ? (IDESC | IDESC_NEG_A) : IDESC;
 }
 
 // Persistent: CTA b takes tiles b, b + gridDim.x, ... Every role walks the same
@@ -231,8 +258,8 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             int issued = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < args.ntiles && ok; tile += gridDim.x) {
-                int i0, j0;
-                if (!tile_coords(args, tile, i0, j0)) continue;
+                int i0, j0, im;
+                if (!tile_coords(args, tile, i0, j0, im)) continue;
                 for (int l = 0; l < s && ok; ++l)
                     for (int p = 0; p <= l && ok; ++p) {
                         const int q = l - p;
@@ -242,7 +269,8 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                                 const uint32_t fb = smem_u32(&full[stage]);
                                 mbar_expect_tx(fb, A_BYTES + B_BYTES);
                                 const int kc = c * kOzakiKChunk + kb * BK;
-                                tma_load_2d(smem_u32(tileA + stage * A_BYTES), &tmB, fb, kc, q * P + j0);
+                                const int kcj = col_chunk(args, c, im) * kOzakiKChunk + kb * BK;
+                                tma_load_2d(smem_u32(tileA + stage * A_BYTES), &tmB, fb, kcj, q * P + j0);
                                 tma_load_2d(smem_u32(tileB + stage * B_BYTES), &tmA, fb, kc, p * P + i0);
                                 ++issued;
                                 if (++stage == STAGES) { stage = 0; phase ^= 1; }
@@ -265,11 +293,12 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             int t = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < args.ntiles && ok; tile += gridDim.x) {
-                int i0, j0;
-                if (!tile_coords(args, tile, i0, j0)) continue;
+                int i0, j0, im;
+                if (!tile_coords(args, tile, i0, j0, im)) continue;
                 for (int l = 0; l < s && ok; ++l)
                     for (int p = 0; p <= l && ok; ++p)
                         for (int c = 0; c < nch && ok; ++c) {
+                            const uint32_t idesc = chunk_idesc(args, c, im);
                             const int b = t & 1;
                             const uint32_t aph = (t >> 1) & 1;
                             if (!mbar_wait(smem_u32(&acce[b]), aph ^ 1, abort)) { ok = false; break; }
@@ -282,7 +311,8 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                                 const uint64_t bd = sdesc_sw128(smem_u32(tileB + stage * B_BYTES));
 #pragma unroll
                                 for (int kk = 0; kk < BK / 16; ++kk)
-                                    mma_bf16(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb | kk) != 0);
+                                    mma_bf16(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc,
+                                             (kb | kk) != 0);
                                 mma_commit(smem_u32(&empty[stage]));
                                 if (++stage == STAGES) { stage = 0; phase ^= 1; }
                             }
@@ -304,9 +334,9 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         int t = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < args.ntiles && ok; tile += gridDim.x) {
-            int i0, j0;
-            if (!tile_coords(args, tile, i0, j0)) continue;
-            const int j = j0 + lg * 32 + lane;
+            int i0, j0, im;
+            if (!tile_coords(args, tile, i0, j0, im)) continue;
+            const int j = j0 + lg * 32 + lane + (im ? P : 0);   // plane column
             for (int l = 0; l < s && ok; ++l) {
 #pragma unroll
                 for (int c = 0; c < BN / 2; ++c) acc[c] = 0u;
@@ -338,7 +368,7 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     }
                 if (!ok) break;
                 const uint32_t bias = count * 0x4B400000u;
-                int32_t *dst = args.planes + (size_t)l * P * P + (size_t)j * P + (size_t)(i0 + half * (BN / 2));
+                int32_t *dst = args.planes + (size_t)l * args.pstride + (size_t)j * P + (size_t)(i0 + half * (BN / 2));
 #pragma unroll
                 for (int c = 0; c < BN / 2; c += 4) {
                     int4 v = make_int4((int)(acc[c] - bias), (int)(acc[c + 1] - bias), (int)(acc[c + 2] - bias),
@@ -360,6 +390,8 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 // ---- split: X(r, kk) -> s bf16 digit matrices [p][r][kk] and exponents -------------
 // LAYOUT OZ_COLS: X(r, kk) = X[kk + r*ld] (vector r = column r);
 // LAYOUT OZ_ROWS: X(r, kk) = X[r + kk*ld] (vector r = row r).
+// Complex (Tin = cd): position kk of the stacked vector is the real part of
+// entry kk for kk < Kh and the imaginary part of entry kk - Kh after that.
 // Two kernels, each over a 2-D grid of (32 vectors) x (a stretch of K):
 //   ozaki_absmax_kernel  largest |x| per vector (bit patterns of non-negative
 //                        doubles order like the values), atomicMax per vector;
@@ -369,26 +401,38 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 constexpr int SPLIT_KT = 256;   // K per absmax CTA
 constexpr int DIGIT_KT = 64;    // K per digits CTA
 
+__device__ __forceinline__ double split_part(double v, int) { return v; }
+__device__ __forceinline__ double split_part(cd v, int part) { return part ? v.y : v.x; }
+
+// entry (r, kk) of the (stacked) vectors; Kh = INT_MAX for real input
+template <typename Tin, int LAYOUT>
+__device__ __forceinline__ double split_entry(const Tin *__restrict__ X, int ld, int R, int K, int Kh, int r, int kk)
+{
+    const int part = kk >= Kh ? 1 : 0;
+    const int e = kk - part * Kh;
+    if (r >= R || e >= K) return 0.0;
+    const Tin v = LAYOUT == OZ_COLS ? X[(size_t)e + (size_t)r * ld] : X[(size_t)r + (size_t)e * ld];
+    return split_part(v, part);
+}
+
 template <typename Tin, int LAYOUT>
 __device__ __forceinline__ void split_load_tile(double (&tile)[32][33], const Tin *__restrict__ X, int ld, int R,
-                                                int K, int r0, int k0)
+                                                int K, int Kh, int r0, int k0)
 {
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
         int v, kk;
         if (LAYOUT == OZ_COLS) { kk = k0 + tx; v = ty + 8 * w; } else { v = tx; kk = k0 + ty + 8 * w; }
-        const int r = r0 + v;
-        double x = 0.0;
-        if (r < R && kk < K)
-            x = (double)(LAYOUT == OZ_COLS ? X[(size_t)kk + (size_t)r * ld] : X[(size_t)r + (size_t)kk * ld]);
-        tile[v][kk - k0] = x;
+        tile[v][kk - k0] = split_entry<Tin, LAYOUT>(X, ld, R, K, Kh, r0 + v, kk);
     }
 }
 
+// Kv: length of the (stacked) vectors: K, or 2 Kh when complex
 template <typename Tin, int LAYOUT>
 __global__ void __launch_bounds__(256)
-ozaki_absmax_kernel(int R, int K, const Tin *__restrict__ X, int ld, unsigned long long *__restrict__ vmax)
+ozaki_absmax_kernel(int R, int K, int Kh, int Kv, const Tin *__restrict__ X, int ld,
+                    unsigned long long *__restrict__ vmax)
 {
     __shared__ double tile[32][33];
     __shared__ unsigned long long smax[32];
@@ -396,9 +440,9 @@ ozaki_absmax_kernel(int R, int K, const Tin *__restrict__ X, int ld, unsigned lo
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     if (threadIdx.x < 32) smax[threadIdx.x] = 0ull;
     unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
-    for (int k0 = kbeg; k0 < kbeg + SPLIT_KT && k0 < K; k0 += 32) {
+    for (int k0 = kbeg; k0 < kbeg + SPLIT_KT && k0 < Kv; k0 += 32) {
         __syncthreads();
-        split_load_tile<Tin, LAYOUT>(tile, X, ld, R, K, r0, k0);
+        split_load_tile<Tin, LAYOUT>(tile, X, ld, R, K, Kh, r0, k0);
         __syncthreads();
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
@@ -421,9 +465,10 @@ __device__ __forceinline__ int split_exponent(unsigned long long b)
     return eb - 1022;                             // max < 2^e
 }
 
+// Kp: stacked length written (K rounded up to the chunk, or 2 Kh when complex)
 template <typename Tin, int LAYOUT>
 __global__ void __launch_bounds__(256)
-ozaki_digits_kernel(int R, int K, int Kp, const Tin *__restrict__ X, int ld, int s, int Pmax, int Kmax,
+ozaki_digits_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, int ld, int s, int Pmax, int Kmax,
                     const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
                     int *__restrict__ exps)
 {
@@ -441,17 +486,17 @@ ozaki_digits_kernel(int R, int K, int Kp, const Tin *__restrict__ X, int ld, int
     const size_t pstride = (size_t)Pmax * Kmax;
     for (int k0 = kbeg; k0 < kbeg + DIGIT_KT && k0 < Kp; k0 += 32) {
         __syncthreads();
-        if (k0 < K) split_load_tile<Tin, LAYOUT>(tile, X, ld, R, K, r0, k0);
+        split_load_tile<Tin, LAYOUT>(tile, X, ld, R, K, Kh, r0, k0);
         __syncthreads();
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             const int v = ty + 8 * w;
             const int r = r0 + v;
             const int kk = k0 + tx;
-            const double x = (k0 < K) ? tile[v][tx] : 0.0;
+            const double x = tile[v][tx];   // zero outside the matrix
             const int e = sexp[v];
             long long Xi = 0;
-            if (e != kOzakiExpNonfinite && kk < K && r < R) {
+            if (e != kOzakiExpNonfinite && r < R) {
                 const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
                 const int eb = (int)((bits >> 52) & 0x7ff);
                 unsigned long long mant = bits & 0xfffffffffffffull;
@@ -500,13 +545,15 @@ cudaError_t encode_digits_map(void *map, void *base, int rows, int Kmax, int box
 
 }  // namespace
 
-cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps)
+cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx)
 {
     static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
     w.nmax = nmax;
+    w.cplx = cplx;
     w.Pmax = (nmax + kOzakiTileI - 1) / kOzakiTileI * kOzakiTileI;
-    w.Kmax = (nmax + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
-    cudaError_t e = cudaMalloc((void **)&w.planes, (size_t)kOzakiMaxSlices * w.Pmax * w.Pmax * sizeof(int32_t));
+    w.Kmax = (nmax + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk * (cplx ? 2 : 1);
+    cudaError_t e = cudaMalloc((void **)&w.planes,
+                               (size_t)kOzakiMaxSlices * (cplx ? 2 : 1) * w.Pmax * w.Pmax * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&w.vmax, (size_t)w.Pmax * sizeof(unsigned long long));
     for (int i = 0; i < kOzakiSlots && e == cudaSuccess; ++i) {
         OzakiSlot &sl = w.slot[i];
@@ -541,25 +588,30 @@ void ozaki_free(OzakiWork &w)
 }
 
 sr_status ozaki_split(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K, const void *X,
-                      int ld, int layout, bool is_float, int s)
+                      int ld, int layout, int s)
 {
-    if (slot < 0 || slot >= kOzakiSlots || s < 1 || s > w.slot[slot].cap || R > w.Pmax || K > kOzakiMaxK ||
-        K > w.Kmax)
+    if (slot < 0 || slot >= kOzakiSlots || s < 1 || s > w.slot[slot].cap || R > w.Pmax ||
+        K > ozaki_k_limit(w.cplx) || K > w.nmax)
         return SR_ERR_INVALID_ARG;
-    const int Kp = (K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const int Kc = (K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const int Kh = w.cplx ? Kc : INT_MAX;           // start of the imaginary half (none when real)
+    const int Kv = w.cplx ? 2 * Kc : K;             // stacked length read
+    const int Kp = w.cplx ? 2 * Kc : Kc;            // stacked length written
     const int Rp = (R + 31) / 32 * 32;
-    SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, 2LL * R * K * (is_float ? 4 : 8) + 2LL * s * Kp * Rp, 2);
+    const int esz = w.cplx ? 16 : 8;
+    SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, 2LL * R * K * esz + 2LL * s * Kp * Rp, 2);
+    w.slot[slot].layout = layout;
     __nv_bfloat16 *out = (__nv_bfloat16 *)w.slot[slot].dig;
     int *ex = w.slot[slot].exps;
     SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)Rp * sizeof(unsigned long long), st));
-    const dim3 gmax(Rp / 32, (K + SPLIT_KT - 1) / SPLIT_KT);
+    const dim3 gmax(Rp / 32, (Kv + SPLIT_KT - 1) / SPLIT_KT);
     const dim3 gdig(Rp / 32, (Kp + DIGIT_KT - 1) / DIGIT_KT);
-#define SR_SPLIT_LAUNCH(TIN, LAY)                                                                               \
-    ozaki_absmax_kernel<TIN, LAY><<<gmax, 256, 0, st>>>(R, K, (const TIN *)X, ld, w.vmax);                      \
-    ozaki_digits_kernel<TIN, LAY><<<gdig, 256, 0, st>>>(R, K, Kp, (const TIN *)X, ld, s, w.Pmax, w.Kmax, w.vmax, \
-                                                        out, ex)
-    if (is_float) {
-        if (layout == OZ_COLS) { SR_SPLIT_LAUNCH(float, OZ_COLS); } else { SR_SPLIT_LAUNCH(float, OZ_ROWS); }
+#define SR_SPLIT_LAUNCH(TIN, LAY)                                                                                 \
+    ozaki_absmax_kernel<TIN, LAY><<<gmax, 256, 0, st>>>(R, K, Kh, Kv, (const TIN *)X, ld, w.vmax);                \
+    ozaki_digits_kernel<TIN, LAY><<<gdig, 256, 0, st>>>(R, K, Kh, Kp, (const TIN *)X, ld, s, w.Pmax, w.Kmax,      \
+                                                        w.vmax, out, ex)
+    if (w.cplx) {
+        if (layout == OZ_COLS) { SR_SPLIT_LAUNCH(cd, OZ_COLS); } else { SR_SPLIT_LAUNCH(cd, OZ_ROWS); }
     } else {
         if (layout == OZ_COLS) { SR_SPLIT_LAUNCH(double, OZ_COLS); } else { SR_SPLIT_LAUNCH(double, OZ_ROWS); }
     }
@@ -571,21 +623,36 @@ sr_status ozaki_split(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int sl
 sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n, int k,
                         int s, bool symmetric, int *flags)
 {
-    if (k > kOzakiMaxK) return SR_ERR_UNSUPPORTED;
+    if (k > ozaki_k_limit(w.cplx)) return SR_ERR_UNSUPPORTED;
     if (s < 1 || s > w.slot[rows].cap || s > w.slot[cols].cap || s > kOzakiMaxSlices) return SR_ERR_INVALID_ARG;
-    const int Kp = (k + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const int Kc = (k + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const int Kp = w.cplx ? 2 * Kc : Kc;
     const int Mp = (m + BN - 1) / BN * BN;
     const int Np = (n + BM - 1) / BM * BM;
     const long long pairs = (long long)s * (s + 1) / 2;
     const int tiles_i = Mp / BN, tiles_j = Np / BM;
+    const int parts = w.cplx ? 2 : 1;
     long long active = 0;
     for (int bj = 0; bj < tiles_j; ++bj)
         for (int bi = 0; bi < tiles_i; ++bi)
             if (!(symmetric && bi * BN > bj * BM + BM - 1)) ++active;
+    active *= parts;
     const long long tile_flops = 2LL * BN * BM * Kp;
     SrPhase ph(h, SR_PROF_OZ_MMA, pairs * active * tile_flops,
-               pairs * 2LL * Kp * (Mp + Np) + 4LL * s * active * BN * BM, 1);
-    MmaArgs a{s, Kp / kOzakiKChunk, w.Pmax, tiles_i, tiles_i * tiles_j, symmetric ? 1 : 0, w.planes, flags};
+               pairs * 2LL * Kp * (Mp + parts * Np) + 4LL * s * active * BN * BM, 1);
+    MmaArgs a{};
+    a.s = s;
+    a.nch = Kp / kOzakiKChunk;
+    a.Pmax = w.Pmax;
+    a.tiles_i = tiles_i;
+    a.tiles_j = tiles_j;
+    a.ntiles = tiles_i * tiles_j * parts;
+    a.symmetric = symmetric ? 1 : 0;
+    a.cplx = w.cplx ? 1 : 0;
+    a.conj = (w.cplx && w.slot[rows].layout == OZ_COLS) ? 1 : 0;
+    a.planes = w.planes;
+    a.pstride = (size_t)parts * w.Pmax * w.Pmax;
+    a.flags = flags;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
     const int grid = (int)std::min<long long>(active, sms > 0 ? sms : 1);

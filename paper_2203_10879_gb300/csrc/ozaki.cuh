@@ -20,8 +20,24 @@
 //
 // Digits live in "slots" so that one split serves several products: the
 // columns of Q feed A Q, Q^T (A Q) and Q^T Q in the same pass.
+//
+// Complex operands (a work area made with cplx = true): a vector x = xr + i xi
+// is stored as the real vector [xr; xi] of length 2 Kh (each half padded to
+// Kh, a multiple of the K-chunk) with one scale for both parts. With r_i the
+// stacked row-side vector and c_j the stacked column-side vector, one output
+// entry needs two real dot products over 2 Kh:
+//     re = r1.c1 - g r2.c2,   im = r1.c2 + g r2.c1,
+// g = -1 when the row-side slot holds columns (op = conjugate transpose, the
+// only use of column digits on the row side) and g = +1 when it holds rows.
+// The slice-product kernel forms them as two output columns per j (the real
+// parts in plane columns [0, Pmax), the imaginary ones in [Pmax, 2 Pmax)):
+// for the imaginary half the column-side K-chunks are read with the halves
+// swapped, and the chunks that carry a minus sign are issued with the
+// instruction descriptor's negate-A bit. Every partial sum stays an exact
+// integer, as in the real case.
 #pragma once
 #include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -43,6 +59,7 @@ enum { OZ_COLS = 0, OZ_ROWS = 1 };
 
 struct OzakiSlot {
     int cap = 0;                           // digits this slot can hold
+    int layout = OZ_COLS;                  // vectors of the last split (OZ_COLS or OZ_ROWS)
     void *dig = nullptr;                   // bf16 digits [cap][Pmax][Kmax]
     int *exps = nullptr;                   // [Pmax]
     alignas(64) unsigned char map_i[128];  // CUtensorMap over the digits, boxes of kOzakiTileI rows
@@ -51,23 +68,29 @@ struct OzakiSlot {
 
 struct OzakiWork {
     int nmax = 0, Pmax = 0, Kmax = 0;
+    bool cplx = false;                     // complex128 operands, stacked [re; im] digit vectors
     OzakiSlot slot[kOzakiSlots];
-    int32_t *planes = nullptr;             // [kOzakiMaxSlices][Pmax cols][Pmax rows]
+    int32_t *planes = nullptr;             // [kOzakiMaxSlices][Pmax (2 Pmax if cplx) cols][Pmax rows]
     unsigned long long *vmax = nullptr;    // per-vector largest |x| (bit pattern) during a split
 };
 
-// caps[i] = digits of slot i (0 = unused)
-cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps);
+// caps[i] = digits of slot i (0 = unused); cplx: complex128 operands
+cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx);
 void ozaki_free(OzakiWork &w);
 
-// Splits the R vectors of length K of X (double or float, column-major with
-// leading dimension ld; vectors = columns or rows) into s digits in `slot`.
+// longest inner dimension a work area of order nmax takes
+inline int ozaki_k_limit(bool cplx) { return cplx ? kOzakiMaxK / 2 : kOzakiMaxK; }
+
+// Splits the R vectors of length K of X (double, or complex128 when w.cplx;
+// column-major with leading dimension ld; vectors = columns or rows) into s
+// digits in `slot`.
 sr_status ozaki_split(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K, const void *X,
-                      int ld, int layout, bool is_float, int s);
+                      int ld, int layout, int s);
 
 // Level planes of the product of the vectors in slot `rows` (output rows i)
 // with those in slot `cols` (output columns j), inner length k. With
-// symmetric = true only tiles with i-tile <= j-tile are formed.
+// symmetric = true only tiles with i-tile <= j-tile are formed. Complex: the
+// row side is conjugated when slot `rows` holds columns (op = ^H).
 sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n, int k,
                         int s, bool symmetric, int *flags);
 
@@ -91,11 +114,25 @@ __device__ inline double oz_scale(double v, int e)
     return oz_pow2_scale(v, e);
 }
 
-// C(i,j) = sign * (rebuilt product); ep as in gemm_simt.cuh. With mirror, the
-// entries below the diagonal are read from the transposed position.
-template <class EP>
+// one rebuilt entry: 2^e * sign * sum_l I_l 2^(-14-8l) (levels 0..3 in one
+// 64-bit Horner sum, the rest in a second; exact integers until the two
+// FP64 conversions and the final fused multiply-add)
+__device__ __forceinline__ double oz_rebuild(const int32_t *__restrict__ planes, size_t off, size_t pstride, int s,
+                                             double sh, double sl, int e)
+{
+    const int nh = s < 4 ? s : 4;
+    long long H = 0, Lo = 0;
+    for (int l = 0; l < nh; ++l) H = H * 256 + (long long)planes[off + (size_t)l * pstride];
+    for (int l = nh; l < s; ++l) Lo = Lo * 256 + (long long)planes[off + (size_t)l * pstride];
+    return oz_scale(fma((double)Lo, sl, (double)H * sh), e);
+}
+
+// C(i,j) = sign * (rebuilt product); ep as in gemm_simt.cuh (a complex value
+// cd when CPLX). With mirror, the entries below the diagonal are read from the
+// transposed position (conjugated when CPLX: the product is Hermitian).
+template <class EP, bool CPLX>
 __global__ void __launch_bounds__(256)
-ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, int ldp, size_t pstride,
+ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, int ldp, size_t pstride, size_t imoff,
                      const int *__restrict__ ea, const int *__restrict__ fb, double sign, int mirror, EP ep,
                      double *partial)
 {
@@ -109,18 +146,19 @@ ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, in
     for (int w = 0; w < 4; ++w) {
         const int j = jb + 8 * w;
         if (i < m && j < n) {
-            const size_t off = (mirror && i > j) ? (size_t)j + (size_t)i * (size_t)ldp
-                                                 : (size_t)i + (size_t)j * (size_t)ldp;
-            long long H = 0, Lo = 0;
-            for (int l = 0; l < nh; ++l) H = H * 256 + (long long)planes[off + (size_t)l * pstride];
-            for (int l = nh; l < s; ++l) Lo = Lo * 256 + (long long)planes[off + (size_t)l * pstride];
-            double v = fma((double)Lo, sl, (double)H * sh);
+            const bool mir = mirror && i > j;
+            const size_t off = mir ? (size_t)j + (size_t)i * (size_t)ldp : (size_t)i + (size_t)j * (size_t)ldp;
             const int e1 = ea[i], e2 = fb[j];
-            if (e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite)
-                v = __longlong_as_double(0x7ff8000000000000LL);
-            else
-                v = oz_scale(v, e1 + e2);
-            part += ep(i, j, v);
+            const bool bad = e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite;
+            const double nan = __longlong_as_double(0x7ff8000000000000LL);
+            const double re = bad ? nan : oz_rebuild(planes, off, pstride, s, sh, sl, e1 + e2);
+            if constexpr (CPLX) {
+                double im = bad ? nan : oz_rebuild(planes, off + imoff, pstride, s, sh, sl, e1 + e2);
+                if (mir) im = -im;
+                part += ep(i, j, cd{re, im});
+            } else {
+                part += ep(i, j, re);
+            }
         }
     }
     if (partial) {
@@ -131,15 +169,23 @@ ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, in
 
 inline int ozaki_blocks(int m, int n) { return ((m + 31) / 32) * ((n + 31) / 32); }
 
+// epilogues of complex products carry `static constexpr bool kComplex`
+template <class EP, class = void> struct ep_is_complex : std::false_type {};
+template <class EP> struct ep_is_complex<EP, std::void_t<decltype(EP::kComplex)>> : std::true_type {};
+
 template <class EP>
 sr_status ozaki_combine(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n, int s,
                         double sign, bool mirror, EP ep, double *partial, int *blocks)
 {
-    SrPhase ph(h, SR_PROF_OZ_COMBINE, 8LL * s * m * n, (long long)m * n * (4LL * s + 16), 1);
+    constexpr bool CPLX = ep_is_complex<EP>::value;
+    if (CPLX != w.cplx) return SR_ERR_INVALID_ARG;
+    const int c = CPLX ? 2 : 1;
+    SrPhase ph(h, SR_PROF_OZ_COMBINE, 8LL * c * s * m * n, (long long)m * n * (4LL * c * s + 16 * c), 1);
     dim3 grid((m + 31) / 32, (n + 31) / 32);
-    ozaki_combine_kernel<EP><<<grid, 256, 0, st>>>(m, n, s, w.planes, w.Pmax, (size_t)w.Pmax * w.Pmax,
-                                                    w.slot[rows].exps, w.slot[cols].exps, sign, mirror ? 1 : 0, ep,
-                                                    partial);
+    const size_t pstride = (size_t)c * w.Pmax * w.Pmax, imoff = (size_t)w.Pmax * w.Pmax;
+    ozaki_combine_kernel<EP, CPLX><<<grid, 256, 0, st>>>(m, n, s, w.planes, w.Pmax, pstride, imoff,
+                                                         w.slot[rows].exps, w.slot[cols].exps, sign, mirror ? 1 : 0,
+                                                         ep, partial);
     SR_CUDA_TRY(cudaGetLastError());
     if (blocks) *blocks = ozaki_blocks(m, n);
     return SR_OK;
@@ -156,16 +202,17 @@ enum {
     OZS_W2 = 6      // columns of W^2 (low-precision digits)
 };
 
-// One emulated product C = op(A) B with the generic slots, epilogue ep.
+// One emulated product C = op(A) B with the generic slots, epilogue ep
+// (op(A) = A^H, the conjugate transpose, when transA and w.cplx).
 template <class EP>
 sr_status ozaki_gemm(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, bool transA, int m, int n, int k,
-                     const double *A, int lda, const double *B, int ldb, EP ep, double *partial, int *blocks,
+                     const void *A, int lda, const void *B, int ldb, EP ep, double *partial, int *blocks,
                      int slices, int *flags)
 {
     const int s = slices > 0 ? slices : kOzakiDefaultSlices;
     if (s > w.slot[OZS_ROWS].cap || m > w.nmax || n > w.nmax || k > w.nmax) return SR_ERR_INVALID_ARG;
-    SR_TRY(ozaki_split(h, st, w, OZS_ROWS, m, k, A, lda, transA ? OZ_COLS : OZ_ROWS, false, s));
-    SR_TRY(ozaki_split(h, st, w, OZS_COLS, n, k, B, ldb, OZ_COLS, false, s));
+    SR_TRY(ozaki_split(h, st, w, OZS_ROWS, m, k, A, lda, transA ? OZ_COLS : OZ_ROWS, s));
+    SR_TRY(ozaki_split(h, st, w, OZS_COLS, n, k, B, ldb, OZ_COLS, s));
     SR_TRY(ozaki_product(h, st, w, OZS_ROWS, OZS_COLS, m, n, k, s, false, flags));
     return ozaki_combine(h, st, w, OZS_ROWS, OZS_COLS, m, n, s, 1.0, false, ep, partial, blocks);
 }

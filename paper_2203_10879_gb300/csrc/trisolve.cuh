@@ -37,8 +37,12 @@ namespace sr {
 
 constexpr int kSolveTile = 32;
 
+// divisor t_ii - t_jj formed in high precision and rounded to the working type
 template <typename T>
-__device__ inline T sr_div_round(double di, double dj) { return (T)(di - dj); }
+__device__ inline T sr_div_round(typename SrNum<T>::hp di, typename SrNum<T>::hp dj)
+{
+    return SrNum<T>::from_hp(di - dj);
+}
 
 // Launch plan: for step t, the tiles (I << 16 | J) of subdiagonal t (solved)
 // followed by the tiles with D < t that receive a product of subdiagonal t+1.
@@ -73,6 +77,31 @@ template <> struct SolveVec<double> {
         v[0] = q.x; v[1] = q.y;
     }
 };
+template <> struct SolveVec<cf> {
+    __device__ static void ld4(const cf *p, cf (&v)[4])
+    {
+        const float4 q0 = *reinterpret_cast<const float4 *>(p);
+        const float4 q1 = *reinterpret_cast<const float4 *>(p + 2);
+        v[0] = {q0.x, q0.y}; v[1] = {q0.z, q0.w}; v[2] = {q1.x, q1.y}; v[3] = {q1.z, q1.w};
+    }
+    __device__ static void ld2(const cf *p, cf (&v)[2])
+    {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = {q.x, q.y}; v[1] = {q.z, q.w};
+    }
+};
+template <> struct SolveVec<cd> {
+    __device__ static void ld4(const cd *p, cd (&v)[4])
+    {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = p[i];
+    }
+    __device__ static void ld2(const cd *p, cd (&v)[2])
+    {
+        v[0] = p[0];
+        v[1] = p[1];
+    }
+};
 
 template <typename T>
 __global__ void __launch_bounds__(128)
@@ -91,15 +120,16 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
     const int tid = threadIdx.x;
     const int lx = tid & 31, ly = tid >> 5;   // load mapping: element (lx, ly + 4q), q = 0..7
     const int tx = tid & 7, ty = tid >> 3;    // block rows 4tx.., columns 2ty..
+    const T Z = SrNum<T>::zero();
     const bool hasP = J + d < NB, hasM = I - d >= 0;
     const int kP = (J + d) * B, kM = (I - d) * B;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int y = ly + 4 * q;
-        Ta[0][y][lx] = (hasP && r0 + lx < n && kP + y < n) ? TE[sr_idx(r0 + lx, kP + y, ld)] : (T)0;
-        Tb[0][lx][y] = (hasP && kP + lx < n && c0 + y < n) ? TE[sr_idx(kP + lx, c0 + y, ld)] : (T)0;
-        Ta[1][y][lx] = (hasM && r0 + lx < n && kM + y < n) ? TE[sr_idx(r0 + lx, kM + y, ld)] : (T)0;
-        Tb[1][lx][y] = (hasM && kM + lx < n && c0 + y < n) ? TE[sr_idx(kM + lx, c0 + y, ld)] : (T)0;
+        Ta[0][y][lx] = (hasP && r0 + lx < n && kP + y < n) ? TE[sr_idx(r0 + lx, kP + y, ld)] : Z;
+        Tb[0][lx][y] = (hasP && kP + lx < n && c0 + y < n) ? TE[sr_idx(kP + lx, c0 + y, ld)] : Z;
+        Ta[1][y][lx] = (hasM && r0 + lx < n && kM + y < n) ? TE[sr_idx(r0 + lx, kM + y, ld)] : Z;
+        Tb[1][lx][y] = (hasM && kM + lx < n && c0 + y < n) ? TE[sr_idx(kM + lx, c0 + y, ld)] : Z;
     }
     T acc[4][2];
 #pragma unroll
@@ -107,7 +137,7 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int x = 4 * tx + i, y = 2 * ty + j;
-            acc[i][j] = (x < nr && y < nc && (D > 0 || x > y)) ? TE[sr_idx(r0 + x, c0 + y, ld)] : (T)0;
+            acc[i][j] = (x < nr && y < nc && (D > 0 || x > y)) ? TE[sr_idx(r0 + x, c0 + y, ld)] : Z;
         }
     __syncthreads();
 #pragma unroll 4
@@ -121,8 +151,8 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                acc[i][j] = fma(a[i], b[j], acc[i][j]);
-                acc[i][j] = fma(-m[i], c[j], acc[i][j]);
+                acc[i][j] = sr_fma(a[i], b[j], acc[i][j]);
+                acc[i][j] = sr_fma(-m[i], c[j], acc[i][j]);
             }
     }
 #pragma unroll
@@ -138,10 +168,12 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
 // 1024 threads; thread (lane a, warp b) owns entry (a, b) of the tile.
 template <typename T>
 __global__ void __launch_bounds__(1024)
-trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const double *__restrict__ dhp, int t,
+trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>::hp *__restrict__ dhp, int t,
                      const uint32_t *__restrict__ plan, int *__restrict__ flags)
 {
+    using Hp = typename SrNum<T>::hp;
     constexpr int B = kSolveTile, S = B + 1;
+    const T Z = SrNum<T>::zero();
     const int NB = (n + B - 1) / B;
     const uint32_t tile = plan[blockIdx.x];
     const int I = (int)(tile >> 16), J = (int)(tile & 0xffffu);
@@ -156,61 +188,62 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const double *__restrict
     T (*X)[S] = sm[0];
     T (*Ti)[S] = sm[1];
     T (*Tj)[S] = sm[2];
-    __shared__ double dI[B], dJ[B];
+    __shared__ Hp dI[B], dJ[B];
     const int a = threadIdx.x & 31, b = threadIdx.x >> 5;
     const bool own = a < nr && b < nc && (D > 0 || a > b);
 
     // 1. E plus the two products of subdiagonal t+1
     const bool hasP = d < NB && J + d < NB, hasM = d < NB && I - d >= 0;
     const int kP = (J + d) * B, kM = (I - d) * B;
-    Ta[0][b][a] = (hasP && r0 + a < n && kP + b < n) ? TE[sr_idx(r0 + a, kP + b, ld)] : (T)0;
-    Tb[0][a][b] = (hasP && kP + a < n && c0 + b < n) ? TE[sr_idx(kP + a, c0 + b, ld)] : (T)0;
-    Ta[1][b][a] = (hasM && r0 + a < n && kM + b < n) ? TE[sr_idx(r0 + a, kM + b, ld)] : (T)0;
-    Tb[1][a][b] = (hasM && kM + a < n && c0 + b < n) ? TE[sr_idx(kM + a, c0 + b, ld)] : (T)0;
-    T acc = own ? TE[sr_idx(r0 + a, c0 + b, ld)] : (T)0;
-    if (threadIdx.x < B) dI[threadIdx.x] = (threadIdx.x < nr) ? dhp[r0 + threadIdx.x] : 0.0;
-    else if (threadIdx.x < 2 * B) dJ[threadIdx.x - B] = (threadIdx.x - B < nc) ? dhp[c0 + threadIdx.x - B] : 0.0;
+    Ta[0][b][a] = (hasP && r0 + a < n && kP + b < n) ? TE[sr_idx(r0 + a, kP + b, ld)] : Z;
+    Tb[0][a][b] = (hasP && kP + a < n && c0 + b < n) ? TE[sr_idx(kP + a, c0 + b, ld)] : Z;
+    Ta[1][b][a] = (hasM && r0 + a < n && kM + b < n) ? TE[sr_idx(r0 + a, kM + b, ld)] : Z;
+    Tb[1][a][b] = (hasM && kM + a < n && c0 + b < n) ? TE[sr_idx(kM + a, c0 + b, ld)] : Z;
+    T acc = own ? TE[sr_idx(r0 + a, c0 + b, ld)] : Z;
+    const Hp hz = SrNum<Hp>::zero();
+    if (threadIdx.x < B) dI[threadIdx.x] = (threadIdx.x < nr) ? dhp[r0 + threadIdx.x] : hz;
+    else if (threadIdx.x < 2 * B) dJ[threadIdx.x - B] = (threadIdx.x - B < nc) ? dhp[c0 + threadIdx.x - B] : hz;
     __syncthreads();
     if (hasP || hasM) {
 #pragma unroll 8
         for (int k = 0; k < B; ++k) {
-            acc = fma(Ta[0][k][a], Tb[0][k][b], acc);
-            acc = fma(-Ta[1][k][a], Tb[1][k][b], acc);
+            acc = sr_fma(Ta[0][k][a], Tb[0][k][b], acc);
+            acc = sr_fma(-Ta[1][k][a], Tb[1][k][b], acc);
         }
     }
     // divisor t_aa - t_bb formed in FP64 and rounded; its reciprocal (one IEEE
     // division, off the wavefront's critical path) turns each solve into a product
-    const T den = own ? sr_div_round<T>(dI[a], dJ[b]) : (T)1;
-    const T rcp = (T)1 / den;
+    const T den = own ? sr_div_round<T>(dI[a], dJ[b]) : Z;
+    const T rcp = (own && !(den == Z)) ? sr_recip(den) : Z;
     __syncthreads();
 
     // 2. wavefront over the tile's subdiagonals. When subdiagonal w is final, a
     // pending entry (a, b) adds T_II(a, b+w) X(b+w, b) (from lane b+w of its
     // own warp) and -X(a, a-w) T_JJ(a-w, b) (from shared memory).
-    Ti[a][b] = (a <= b && a < nr && b < nr) ? TE[sr_idx(r0 + a, r0 + b, ld)] : (T)0;
-    Tj[a][b] = (a <= b && a < nc && b < nc) ? TE[sr_idx(c0 + a, c0 + b, ld)] : (T)0;
-    X[a][b] = (T)0;
+    Ti[a][b] = (a <= b && a < nr && b < nr) ? TE[sr_idx(r0 + a, r0 + b, ld)] : Z;
+    Tj[a][b] = (a <= b && a < nc && b < nc) ? TE[sr_idx(c0 + a, c0 + b, ld)] : Z;
+    X[a][b] = Z;
     __syncthreads();
     const int wlo = (D > 0) ? -(B - 1) : 1;
-    T xv = (T)0;
+    T xv = Z;
     int bad = 0;
     for (int w = B - 1; w >= wlo; --w) {
         if (own && a - b == w) {
-            if (den == (T)0) {
+            if (den == Z) {
                 bad |= SR_FLAG_NONDISTINCT;
             } else {
-                xv = -acc * rcp;
+                xv = -(acc * rcp);
                 if (!sr_finite(xv)) bad |= SR_FLAG_NONFINITE;
             }
             X[a][b] = xv;
         }
         __syncthreads();
         const int c = b + w;                         // (c, b): lane c of this warp
-        const T xcol = __shfl_sync(0xffffffffu, xv, c & 31);
+        const T xcol = sr_shfl(xv, c & 31);
         if (own && a - b < w) {
-            if (c < nr) acc = fma(Ti[a][c], xcol, acc);
+            if (c < nr) acc = sr_fma(Ti[a][c], xcol, acc);
             const int c2 = a - w;                    // (a, c2), c2 < b
-            if (c2 >= 0) acc = fma(-X[a][c2], Tj[c2][b], acc);
+            if (c2 >= 0) acc = sr_fma(-X[a][c2], Tj[c2][b], acc);
         }
     }
     if (bad) atomicOr(flags, bad);
@@ -222,8 +255,8 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const double *__restrict
 // plan: device copy of trisolve_plan's tiles; offsets: its host offsets.
 template <typename T>
 inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEvent_t ev0, cudaEvent_t ev1, int n,
-                                     T *TE, int ld, const double *dhp, int *flags, const uint32_t *plan,
-                                     const std::vector<long long> &offsets)
+                                     T *TE, int ld, const typename SrNum<T>::hp *dhp, int *flags,
+                                     const uint32_t *plan, const std::vector<long long> &offsets)
 {
     const int NB = (n + kSolveTile - 1) / kSolveTile;
     cudaError_t e = cudaEventRecord(ev0, st);

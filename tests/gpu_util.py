@@ -27,3 +27,11 @@ def sign_align(Q: np.ndarray, R: np.ndarray) -> np.ndarray:
     s = np.sign(np.sum(Q * R, axis=0))
     s[s == 0] = 1.0
     return Q * s
+
+
+def phase_align(Q: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """Q with each column multiplied by the unit-modulus factor that best matches R."""
+    c = np.sum(np.conj(Q) * R, axis=0)
+    a = np.abs(c)
+    ph = np.where(a > 0, c / np.where(a > 0, a, 1.0), 1.0)
+    return Q * ph

@@ -1,0 +1,235 @@
+"""GPU parity of the complex path (complex128 data, complex64 correction path;
+the ring-spectrum workload of order 8192), through the C ABI, against the oracle.
+
+Tolerances:
+  * complex products of Gaussian integers with parts below 2^7 split exactly
+    into one digit each: the emulated product is bit-exact;
+  * general complex products: each part is a real product of depth 2k over
+    the stacked vectors [re, im], so against the oracle's double-double product
+    of those stacked real operands the error is <= 2k u (|Ar| + |Ai|)(|Br| + |Bi|);
+  * the complex64 solve is compared with the oracle's complex64 Alg. 2 through
+    their distances to the complex128 solution, as in the real FP32 test;
+  * refined factors: residuals certified in double-double <= 1e-14 sqrt(n),
+    columns of Q against the oracle's and the planted Q0 up to a unit phase
+    (ring gaps are >= 0.5 * 2 pi / n; 1e-11 at n <= 300).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_10879_gb300 import _binding as B
+from paper_2203_10879_gb300 import inputs
+from gpu_util import from_dev, phase_align, to_dev
+
+pytestmark = pytest.mark.gpu
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    B.lib()
+    return torch
+
+
+def _opts(**kw):
+    base = dict(dtype=B.SR_COMPLEX, hp_gemm=B.SR_HP_OZAKI_BF16, lp=B.SR_LP_FP32)
+    base.update(kw)
+    return B.default_options(**base)
+
+
+def _handle(n_max, **kw):
+    s, h = B.schur_refine_create(n_max, _opts(**kw), None)
+    assert s == B.SR_OK, B.status_string(s)
+    return h
+
+
+def _cgemm(torch, A, Bm, transA, slices=0):
+    m = A.shape[1] if transA else A.shape[0]
+    k = A.shape[0] if transA else A.shape[1]
+    n = Bm.shape[1]
+    h = _handle(max(m, n, k), ozaki_slices=slices)
+    try:
+        C = torch.zeros((n, m), dtype=torch.complex128, device="cuda").t()
+        st = B.schur_refine_gemm(h, int(transA), m, n, k, to_dev(A), to_dev(Bm), C)
+        assert st == B.SR_OK, B.status_string(st)
+        return from_dev(C)
+    finally:
+        B.schur_refine_destroy(h)
+
+
+def _gauss_int(rng, shape, lim=127):
+    return (rng.integers(-lim, lim + 1, shape) + 1j * rng.integers(-lim, lim + 1, shape)).astype(np.complex128)
+
+
+def test_complex_options_gate(torch):
+    for kw in (dict(hp_gemm=B.SR_HP_FP64), dict(lp=B.SR_LP_FP64)):
+        s, h = B.schur_refine_create(64, _opts(**kw), None)
+        assert s == B.SR_ERR_UNSUPPORTED and not h.value
+    s, h = B.schur_refine_create(8193, _opts(), None)
+    assert s == B.SR_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("m,n,k,transA", [(128, 128, 256, False), (200, 130, 300, False),
+                                          (129, 257, 513, True), (1, 3, 2, True), (300, 300, 300, True)])
+def test_complex_gemm_exact_gaussian_integers(torch, m, n, k, transA):
+    rng = np.random.default_rng(m * 7 + n * 3 + k)
+    A = _gauss_int(rng, (k, m) if transA else (m, k))
+    Bm = _gauss_int(rng, (k, n))
+    C = _cgemm(torch, A, Bm, transA)
+    opA = A.conj().T if transA else A
+    assert np.array_equal(C, opA @ Bm)
+
+
+@pytest.mark.parametrize("m,n,k,transA", [(160, 96, 700, True), (300, 260, 300, False)])
+def test_complex_gemm_fp64_accuracy(torch, m, n, k, transA):
+    rng = np.random.default_rng(11 * m + k)
+    scale = np.exp(rng.uniform(-3, 3, (1, m) if transA else (m, 1)))
+    A = (rng.standard_normal((k, m) if transA else (m, k)) +
+         1j * rng.standard_normal((k, m) if transA else (m, k))) * scale
+    Bm = rng.standard_normal((k, n)) + 1j * rng.standard_normal((k, n))
+    C = _cgemm(torch, A, Bm, transA)
+    opA = A.conj().T if transA else A
+    # reference: the stacked real products in double-double (oracle)
+    Ar, Ai = opA.real, opA.imag
+    re_h, re_l = oracle.gemm_dd(np.hstack([Ar, -Ai]), None, np.vstack([Bm.real, Bm.imag]), None)
+    im_h, im_l = oracle.gemm_dd(np.hstack([Ar, Ai]), None, np.vstack([Bm.imag, Bm.real]), None)
+    mag = (np.abs(Ar) + np.abs(Ai)) @ (np.abs(Bm.real) + np.abs(Bm.imag))
+    bound = 2 * k * U64 * mag
+    assert np.all(np.abs(C.real - re_h - re_l) <= bound)
+    assert np.all(np.abs(C.imag - im_h - im_l) <= bound)
+    err = np.abs(C.real - re_h - re_l) + np.abs(C.imag - im_h - im_l)
+    assert np.median(err / bound) < 0.1
+
+
+def test_complex_gemm_nonfinite_row(torch):
+    A = np.ones((64, 64), dtype=np.complex128)
+    A[5, 7] = complex(0.0, np.inf)
+    C = _cgemm(torch, A, np.ones((64, 64), dtype=np.complex128), False)
+    assert np.all(np.isnan(C[5, :].real))
+    assert np.all(np.isfinite(np.delete(C, 5, axis=0)))
+
+
+def _csolve_problem(n, seed):
+    rng = np.random.default_rng(seed)
+    d = (np.arange(n, dtype=float) / 4.0 + rng.uniform(0, 0.1, n)) * np.exp(1j * rng.uniform(0, 0.3, n))
+    T = np.triu(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)), 1) * 0.05 + np.diag(d)
+    E = np.tril(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)), -1) * 1e-3
+    return T, E
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 100, 257])
+def test_complex_trisolve_parity(torch, n):
+    T, E = _csolve_problem(n, 5 * n + 1)
+    h = _handle(n)
+    try:
+        TE = to_dev((np.triu(T) + E).astype(np.complex64))
+        s = B.schur_refine_trisolve(h, n, TE, to_dev(np.diagonal(T).copy()))
+        assert s == B.SR_OK
+        out = from_dev(TE)
+        assert np.array_equal(np.triu(out), np.triu(T).astype(np.complex64))
+        Lg = np.tril(out, -1).astype(np.complex128)
+        L64 = oracle.alg2(T, E, np.diagonal(T).copy())
+        Lo = oracle.alg2(np.triu(T).astype(np.complex64), E.astype(np.complex64), np.diagonal(T).copy())
+        e_gpu = np.linalg.norm(Lg - L64)
+        e_orc = np.linalg.norm(Lo.astype(np.complex128) - L64)
+        assert e_gpu <= 10 * max(e_orc, U32 * np.linalg.norm(L64))
+    finally:
+        B.schur_refine_destroy(h)
+
+
+def test_complex_trisolve_nondistinct(torch):
+    n = 40
+    T, E = _csolve_problem(n, 9)
+    T[30, 30] = T[3, 3]
+    h = _handle(n)
+    try:
+        s = B.schur_refine_trisolve(h, n, to_dev((np.triu(T) + E).astype(np.complex64)),
+                                    to_dev(np.diagonal(T).copy()))
+        assert s == B.SR_ERR_NONDISTINCT
+    finally:
+        B.schur_refine_destroy(h)
+
+
+def _refine(p, residuals=True, **kw):
+    import torch
+    n = p.n
+    h = _handle(n, **kw)
+    try:
+        A, Qhat = to_dev(p.A), to_dev(p.Qhat)
+        Q = torch.zeros((n, n), dtype=torch.complex128, device="cuda").t()
+        T = torch.zeros((n, n), dtype=torch.complex128, device="cuda").t()
+        st, nr = B.schur_refine_step(h, n, A, Q, Qhat, T)
+        rT = rQ = None
+        if residuals:
+            sr, rT, rQ = B.schur_refine_residuals(h, n, A, Q)
+            assert sr == B.SR_OK
+        return st, nr, from_dev(Q), from_dev(T), (rT, rQ)
+    finally:
+        B.schur_refine_destroy(h)
+
+
+@pytest.mark.parametrize("n", [64, 96, 300])
+def test_complex_refine_matches_oracle(torch, n):
+    p = inputs.ring_complex(n)
+    st, nr, Q, T, (rT, rQ) = _refine(p)
+    ref = oracle.refine(p.A, p.Qhat, lp="f32")
+    assert ref.status == oracle.OK
+    assert st == B.SR_OK and abs(nr.iters - ref.iters) <= 1
+    tol = oracle.default_tol(n)
+    cT, cQ = oracle.residuals_dd(p.A, Q)
+    assert cT <= tol and cQ <= tol
+    # the library's own double-double residuals agree with the oracle's
+    assert rT == pytest.approx(cT, rel=1e-6, abs=1e-30) and rQ == pytest.approx(cQ, rel=1e-6, abs=1e-30)
+    assert np.max(np.abs(phase_align(Q, ref.Q) - ref.Q)) <= 1e-11
+    assert np.max(np.abs(phase_align(Q, p.Q0) - p.Q0)) <= 1e-11
+    # T^ of the last pass: its diagonal carries the planted eigenvalues
+    assert np.max(np.abs(np.diagonal(T) - p.lam)) <= 1e-12
+
+
+def test_complex_one_pass_parity(torch):
+    p = inputs.planted(96, inputs.eig_ring(96, 3), 5, pert=1e-5, complex_=True)
+    st, nr, Q, _, _ = _refine(p, max_iter=1)
+    assert st == B.SR_ERR_NOT_CONVERGED and nr.iters == 1
+    Q0, _ = oracle.ns_init(p.Qhat)
+    Q1, info = oracle.iteration(p.A, Q0, lp="f32")
+    assert nr.w_norm == pytest.approx(info.w_norm, rel=1e-5)
+    assert np.max(np.abs(Q - Q1)) <= 50 * U32 * info.w_norm + 1e-13
+
+
+def test_complex_full_sigma(torch):
+    p = inputs.ring_complex(200)
+    st, nr, Q, _, _ = _refine(p, full_sigma=1)
+    ref = oracle.refine(p.A, p.Qhat, lp="f32", full_sigma=True)
+    assert st == B.SR_OK and abs(nr.iters - ref.iters) <= 1
+    tol = oracle.default_tol(200)
+    cT, cQ = oracle.residuals_dd(p.A, Q)
+    assert cT <= tol and cQ <= tol
+    assert np.max(np.abs(phase_align(Q, ref.Q) - ref.Q)) <= 1e-10
+
+
+def test_complex_workload_full_size(torch):
+    """The ring workload at order 8192 as the benchmark runs it: converged
+    (stop test on the emulated-FP64 residuals), and sampled entries of Q^H A Q
+    and Q^H Q - I recomputed one by one by the oracle in double-double."""
+    n = 8192
+    p = inputs.ring_complex(n)
+    st, nr, Q, T, _ = _refine(p, residuals=False)
+    tol = oracle.default_tol(n)
+    assert st == B.SR_OK, B.status_string(st)
+    assert nr.stril_rel <= tol and nr.orth <= np.sqrt(tol)
+    rng = np.random.default_rng(8192)
+    rows = np.concatenate([rng.integers(1, n, 24), np.arange(0, n, n // 8)])
+    cols = np.concatenate([rng.integers(0, n - 1, 24), np.arange(0, n, n // 8)])
+    rows, cols = np.maximum(rows, cols), np.minimum(rows, cols)   # strictly lower or diagonal
+    t, y = oracle.sample_entries_dd(p.A, Q, rows, cols)
+    anorm = np.linalg.norm(p.A)
+    # the device's T^ at those entries (formed with the factor of the last pass)
+    assert np.max(np.abs(T[rows, cols] - t)) <= 1e-13 * anorm
+    low = rows > cols
+    assert np.max(np.abs(t[low])) <= tol * anorm
+    assert np.max(np.abs(y)) <= tol
+    diag = rows == cols
+    assert np.max(np.abs(t[diag] - p.lam[rows[diag]])) <= 1e-11

@@ -184,6 +184,43 @@ def test_sample_entries_dd_match_exact():
         assert y[s] == pytest.approx(float(yij), rel=1e-12, abs=1e-31)
 
 
+def test_sample_entries_dd_complex_match_exact():
+    # Gaussian-rational arithmetic: each complex entry as a pair of Fractions
+    p = inputs.ring_complex(5)
+    Q, _ = oracle.ns_init(p.Qhat)
+    rows, cols = [4, 2, 0, 3, 1], [0, 1, 0, 3, 4]
+    t, y = oracle.sample_entries_dd(p.A, Q, rows, cols)
+    n = 5
+
+    def fr(z):
+        return (Fraction(float(z.real)), Fraction(float(z.imag)))
+
+    def mul(a, b):
+        return (a[0] * b[0] - a[1] * b[1], a[0] * b[1] + a[1] * b[0])
+
+    def add(a, b):
+        return (a[0] + b[0], a[1] + b[1])
+
+    zero = (Fraction(0), Fraction(0))
+    Af = [[fr(p.A[i, j]) for j in range(n)] for i in range(n)]
+    Qf = [[fr(Q[i, j]) for j in range(n)] for i in range(n)]
+    Qc = [[(q[0], -q[1]) for q in row] for row in Qf]
+    for s, (i, j) in enumerate(zip(rows, cols)):
+        tij = zero
+        for l in range(n):
+            aq = zero
+            for k in range(n):
+                aq = add(aq, mul(Af[l][k], Qf[k][j]))
+            tij = add(tij, mul(Qc[l][i], aq))
+        yij = zero
+        for l in range(n):
+            yij = add(yij, mul(Qc[l][i], Qf[l][j]))
+        if i == j:
+            yij = (yij[0] - 1, yij[1])
+        assert abs(t[s] - complex(float(tij[0]), float(tij[1]))) <= 1e-15 * max(1.0, abs(t[s]))
+        assert abs(y[s] - complex(float(yij[0]), float(yij[1]))) <= 1e-30 + 1e-12 * abs(y[s])
+
+
 def test_gemm_dd_matches_exact(rng):
     n = 7
     A = rng.standard_normal((n, n))
