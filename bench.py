@@ -8,6 +8,12 @@ Qhat = fl32(Q0 expm(1e-6 S))), with A and Qhat resident in HBM. The mixed form
 the all-FP64 form of the same iteration on the same inputs is timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload single|complex|batched]
+
+--workload complex refines the complex n = 8192 ring problem instead
+(eigenvalues 0.5 exp(2 pi i k/n)(1 + U(0, 0.2)), complex64 starting factor,
+complex64 correction path, emulated complex128 products); the library builds no
+all-FP64 complex form, so that line carries no all-FP64 time.
 
 Prints one JSON line (rank 0). With N > 1 (torchrun) every rank refines its own
 copy (replicas only: a single refinement does not shard); the value is the
@@ -45,7 +51,10 @@ def _peaks():
         return {}
 
 
-def _workload_name(n):
+def _workload_name(n, cplx=False):
+    if cplx:
+        return (f"complex n={n} planted A=Q0 T0 Q0^H, lambda_k=0.5 exp(2 pi i k/n)(1+U(0,0.2)), complex upper "
+                f"std 1/n, Qhat=fl_c64(Q0 expm(1e-6 S)), S skew-Hermitian; Alg. 4 to ||stril||/||A||<=1e-14 sqrt(n)")
     return (f"real n={n} planted A=Q0 T0 Q0^T, lambda_k=k/n+U(0,0.5/n), upper std 1/n, "
             f"Qhat=fl32(Q0 expm(1e-6 S)); Alg. 4 to ||stril||/||A||<=1e-14 sqrt(n)")
 
@@ -108,11 +117,11 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_sample(n_full: int, n_sample: int):
+def cpu_oracle_sample(n_full: int, n_sample: int, cplx: bool = False):
     """The oracle's full refinement at n_sample, scaled by (n_full/n_sample)^3."""
     import oracle
     from paper_2203_10879_gb300 import inputs
-    p = inputs.jittered_real(n_sample)
+    p = inputs.ring_complex(n_sample) if cplx else inputs.jittered_real(n_sample)
     t0 = time.perf_counter()
     r = oracle.refine(p.A, p.Qhat, lp="f32")
     dt = time.perf_counter() - t0
@@ -125,10 +134,10 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    n, ns = args.n, args.cpu_sample_n
+    n, ns, cplx = args.n, args.cpu_sample_n, args.workload == "complex"
     times = []
     for i in range(args.warmup + args.steps):
-        est, dt, r, cores = cpu_oracle_sample(n, ns)
+        est, dt, r, cores = cpu_oracle_sample(n, ns, cplx)
         if i >= args.warmup:
             times.append(est)
     v = sum(times) / len(times)
@@ -137,7 +146,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": _workload_name(n), "n": n, "form": "mixed FP32->FP64 (oracle)"},
+            "config": {"workload": _workload_name(n, cplx), "n": n, "form": "mixed FP32->FP64 (oracle)"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -165,15 +174,19 @@ def run_ours(args):
             dist.barrier()
 
     n = args.n
-    p = inputs.jittered_real(n)
+    cplx = args.workload == "complex"
+    p = inputs.ring_complex(n) if cplx else inputs.jittered_real(n)
+    hdt = torch.complex128 if cplx else torch.float64
+    ldt = torch.complex64 if cplx else torch.float32
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
     A = dev(p.A)
     Qhat = dev(p.Qhat)
-    Q = torch.empty((n, n), dtype=torch.float64, device="cuda").t()
+    Q = torch.empty((n, n), dtype=hdt, device="cuda").t()
     stream = torch.cuda.current_stream()
+    dtype_opt = {"dtype": B.SR_COMPLEX} if cplx else {}
 
     hp_name = {"fp64": B.SR_HP_FP64, "ozaki": B.SR_HP_OZAKI_BF16}
-    hp = args.hp
+    hp = "ozaki" if cplx else args.hp
     if hp == "auto":
         hp = "ozaki"
         try:
@@ -199,7 +212,7 @@ def run_ours(args):
         return e0.elapsed_time(e1) / steps, st, nr
 
     # ---- mixed form (the measured path) --------------------------------------------
-    mixed = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, profile=1)
+    mixed = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, profile=1, **dtype_opt)
     for _ in range(args.warmup):
         mixed.step(A, Q, Qhat, check=False)
     mixed.reset_profile()
@@ -217,7 +230,13 @@ def run_ours(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     prof = mixed.profile()
-    rT, rQ = mixed.residuals(A, Q)
+    if cplx:
+        # the double-double residual products at n = 8192 complex take minutes of
+        # FP64 work: report the stop test's emulated-FP64 residuals instead
+        rT, rQ, cert_kind = nr.stril_rel, nr.orth, "stop test (emulated FP64 products)"
+    else:
+        rT, rQ = mixed.residuals(A, Q)
+        cert_kind = "double-double residual products on the device"
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -227,10 +246,10 @@ def run_ours(args):
     # ---- end to end through host buffers --------------------------------------------
     hA = torch.from_numpy(np.ascontiguousarray(p.A.T)).pin_memory()
     hQh = torch.from_numpy(np.ascontiguousarray(p.Qhat.T)).pin_memory()
-    hQ = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    dA_t = torch.empty((n, n), dtype=torch.float64, device="cuda")
-    dQh_t = torch.empty((n, n), dtype=torch.float32, device="cuda")
-    dQ_t = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    hQ = torch.empty((n, n), dtype=hdt).pin_memory()
+    dA_t = torch.empty((n, n), dtype=hdt, device="cuda")
+    dQh_t = torch.empty((n, n), dtype=ldt, device="cuda")
+    dQ_t = torch.empty((n, n), dtype=hdt, device="cuda")
     ke = max(1, min(args.steps, 3))
     for i in range(1 + ke):
         if i == 1:
@@ -250,13 +269,16 @@ def run_ours(args):
     mixed.close()
 
     # ---- all-FP64 form of the same iteration on the same inputs -----------------------
-    allfp64 = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP64, profile=1)
     k64 = max(1, min(args.steps, args.fp64_steps))
-    ms64, st64, nr64 = timed(allfp64, k64, 1)
-    prof64 = allfp64.profile()
-    allfp64.close()
+    ms64 = st64 = nr64 = None
+    prof64 = {}
+    if not cplx:
+        allfp64 = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP64, profile=1)
+        ms64, st64, nr64 = timed(allfp64, k64, 1)
+        prof64 = allfp64.profile()
+        allfp64.close()
     mixed_native_ms = None
-    if hp != "fp64":
+    if hp != "fp64" and not cplx:
         mn = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP32)
         mixed_native_ms, _, _ = timed(mn, k64, 1)
         mn.close()
@@ -279,7 +301,8 @@ def run_ours(args):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": OZ_MMA_TRAFFIC_BYTES_N4096 if (n == 4096 and (args.slices or 7) == 7) else None,
+                "traffic": OZ_MMA_TRAFFIC_BYTES_N4096 if (n == 4096 and not cplx and (args.slices or 7) == 7)
+                else None,
                 "traffic_note": "bytes per launch of the captured 28-pair product (ncu)",
                 "kernel": "ozaki slice products (tcgen05 kind::f16 bf16)",
                 "peak_source": "of measured bf16 sustained (MEASURED_PEAKS.json)"}
@@ -294,7 +317,7 @@ def run_ours(args):
     cpu_val = None
     cpu = None
     if not args.no_cpu_baseline:
-        est, dt, r, cores = cpu_oracle_sample(n, args.cpu_sample_n)
+        est, dt, r, cores = cpu_oracle_sample(n, args.cpu_sample_n, cplx)
         cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle",
                "sample": f"oracle full refinement at n={args.cpu_sample_n} ({dt:.2f} s measured), "
                          f"scaled by (n/{args.cpu_sample_n})^3 to n={n}"}
@@ -304,22 +327,25 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": _workload_name(n), "n": n, "form": "mixed: FP32 solve/products",
+        "vs_baseline": None, "dtype": "c128+c64" if cplx else "f64+f32", "data": "synthetic",
+        "config": {"workload": _workload_name(n, cplx), "n": n,
+                   "form": "mixed: complex64 solve/products" if cplx else "mixed: FP32 solve/products",
                    "hp_gemm": hp if hp == "fp64" else f"ozaki-bf16-s{args.slices or 7}",
-                   "l2": "inputs larger than L2 (A 128 MiB + Q 128 MiB + workspace)",
+                   "l2": f"inputs larger than L2 (A {n * n * (16 if cplx else 8) >> 20} MiB + Q + workspace)",
                    "status": status, "iters": nr.iters, "hp_gemms": nr.hp_gemms,
-                   "certified": {"stril_rel": rT, "orth": rQ, "tol": tol, "ok": bool(rT <= tol and rQ <= tol)},
-                   "all_fp64_s": ms64 / 1e3, "all_fp64_iters": nr64.iters, "all_fp64_status": st64,
-                   "mixed_vs_all_fp64_speedup": ms64 / ms,
+                   "certified": {"stril_rel": rT, "orth": rQ, "tol": tol, "kind": cert_kind,
+                                 "ok": bool(rT <= tol and rQ <= (math.sqrt(tol) if cplx else tol))},
+                   "all_fp64_s": None if ms64 is None else ms64 / 1e3,
+                   "all_fp64_iters": None if nr64 is None else nr64.iters, "all_fp64_status": st64,
+                   "mixed_vs_all_fp64_speedup": None if ms64 is None else ms64 / ms,
                    "mixed_native_fp64_s": None if mixed_native_ms is None else mixed_native_ms / 1e3,
                    "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
                    "all_fp64_phase_ms_per_step": {k: v["ms"] / k64 for k, v in prof64.items() if v["ms"] > 0},
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n * n * (8 + 4)),
-                "d2h_bytes_per_step": int(n * n * 8)},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n * n * (8 + 4) * (2 if cplx else 1)),
+                "d2h_bytes_per_step": int(n * n * 8 * (2 if cplx else 1))},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -396,16 +422,20 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--hp", choices=["auto", "fp64", "ozaki"], default="auto")
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample-n", type=int, default=1024)
+    ap.add_argument("--cpu-sample-n", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batched"], default="single")
+    ap.add_argument("--workload", choices=["single", "complex", "batched"], default="single")
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--batch-streams", type=int, default=8)
     args = ap.parse_args()
+    if args.n is None:
+        args.n = 8192 if args.workload == "complex" else 4096
+    if args.cpu_sample_n is None:
+        args.cpu_sample_n = 2048 if args.workload == "complex" else 1024
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

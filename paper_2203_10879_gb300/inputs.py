@@ -101,9 +101,9 @@ def _skew(st: Stream, n: int, complex_: bool) -> np.ndarray:
 def _expm_small(x: np.ndarray, degree: int) -> np.ndarray:
     """Taylor polynomial of exp(x); for ||x|| <~ 1e-2 the omitted terms are far below 1e-16."""
     n = x.shape[0]
-    out = np.eye(n, dtype=x.dtype)
-    term = np.eye(n, dtype=x.dtype)
-    for k in range(1, degree + 1):
+    term = x.copy()                       # the k = 1 term, I x / 1, without a product
+    out = np.eye(n, dtype=x.dtype) + term
+    for k in range(2, degree + 1):
         term = term @ x / k
         out = out + term
     return out
@@ -126,9 +126,51 @@ class Planted:
         return self.A.shape[0]
 
 
+def _cache_path(key: str) -> str | None:
+    """File under $SR_INPUT_CACHE for a generated input (no caching when unset)."""
+    import hashlib
+    import os
+    d = os.environ.get("SR_INPUT_CACHE")
+    if not d:
+        return None
+    os.makedirs(d, exist_ok=True)
+    return os.path.join(d, hashlib.sha256(key.encode()).hexdigest()[:32] + ".npz")
+
+
 def planted(n: int, lam: np.ndarray, seed: int, *, pert: float = 1e-6,
             low: str = "f32", complex_: bool = False, recipe: str = "",
             upper_std: float | None = None) -> Planted:
+    """Build A = Q0 T0 Q0^H and Qhat = fl_low(Q0 expm(pert*S)); see _planted.
+
+    With the environment variable SR_INPUT_CACHE set to a directory, the arrays
+    are kept there and read back by later calls with the same arguments (large
+    orders take minutes of host BLAS to build)."""
+    lam = np.asarray(lam)
+    path = _cache_path(repr((n, hashlib_digest(lam), seed, pert, low, complex_, upper_std)))
+    if path is not None:
+        import os
+        if os.path.exists(path):
+            z = np.load(path)
+            return Planted(A=np.asfortranarray(z["A"]), Qhat=np.asfortranarray(z["Qhat"]),
+                           Q0=np.asfortranarray(z["Q0"]), T0=np.asfortranarray(z["T0"]), lam=z["lam"],
+                           seed=seed, recipe=recipe)
+    p = _planted(n, lam, seed, pert=pert, low=low, complex_=complex_, recipe=recipe, upper_std=upper_std)
+    if path is not None:
+        tmp = path + ".tmp.npz"
+        np.savez(tmp, A=p.A, Qhat=p.Qhat, Q0=p.Q0, T0=p.T0, lam=p.lam)
+        import os
+        os.replace(tmp, path)
+    return p
+
+
+def hashlib_digest(a: np.ndarray) -> str:
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def _planted(n: int, lam: np.ndarray, seed: int, *, pert: float = 1e-6,
+             low: str = "f32", complex_: bool = False, recipe: str = "",
+             upper_std: float | None = None) -> Planted:
     """Build A = Q0 T0 Q0^H and Qhat = fl_low(Q0 expm(pert*S)).
 
     T0 has diagonal ``lam`` and iid normal strictly-upper entries with mean 0
