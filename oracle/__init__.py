@@ -2,7 +2,8 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package. It shares no code with the CUDA library
-and never calls it. See :mod:`oracle.alg` for what each function follows.
+and never calls it. See :mod:`oracle.alg` for what each function follows;
+:mod:`oracle.ddtarget` holds the double-double working-precision form of Alg. 4.
 """
 from ._lib import build, set_threads, max_threads  # noqa: F401
 from .alg import (  # noqa: F401

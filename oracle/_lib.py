@@ -63,6 +63,12 @@ def _declare(L):
     L.sro_sample_entries_dd.restype = None
     L.sro_sample_entries_dd_c.argtypes = [_I, _P, _I, _P, _I, _I, _P, _P, _P, _P]
     L.sro_sample_entries_dd_c.restype = None
+    L.sro_alg2_f64_dd.argtypes = [_I, _P, _I, _P, _I, _P, _P, _P, _I]
+    L.sro_alg2_f64_dd.restype = ctypes.c_int
+    L.sro_residuals_q.argtypes = [_I, _P, _P, _I, _P, _P, _I, _P, _P]
+    L.sro_residuals_q.restype = None
+    L.sro_sample_entries_q.argtypes = [_I, _P, _P, _I, _P, _P, _I, _I, _P, _P, _P, _P, _P, _P]
+    L.sro_sample_entries_q.restype = None
     L.sro_set_threads.argtypes = [_I]
     L.sro_set_threads.restype = None
     L.sro_max_threads.argtypes = []

@@ -18,6 +18,10 @@
  *   - Residuals ||stril(Q^H A Q)||_F / ||A||_F and ||Q^H Q - I||_F evaluated
  *     with double-double dot products (Sec. 3 reports these two quantities).
  *   - A double-double dot product / GEMM used for the double-double target.
+ *   - For the double-double target (hp = double-double, lp = double): Alg. 2
+ *     with divisors formed from a double-double diagonal, and the two
+ *     residuals (full, or sampled entries) evaluated in 128-bit floating
+ *     point.
  *
  * Compile with -ffp-contract=off: every rounding here is the one written.
  * Return codes: 0 ok, 2 two diagonal entries of T coincide (Theorem 1),
@@ -562,4 +566,113 @@ int sro_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ */
+/* Double-double working precision (hp = double-double, lp = double). */
+
+/* Alg. 2 in double with the divisors of a double-double diagonal:
+ * t_ii - t_jj is formed in double-double from (dhi, dlo) and rounded once to
+ * double (the reading "form the divisor in hp, then round" of the FP64 forms,
+ * one precision level up). */
+int sro_alg2_f64_dd(int n, const double *T, int ldt, const double *E, int lde,
+                    const double *dhi, const double *dlo, double *L, int ldl)
+{
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) L[IDX(i, j, ldl)] = 0.0;
+    for (int j = 0; j < n - 1; ++j) {
+        for (int i = n - 1; i >= j + 1; --i) {
+            double e = E[IDX(i, j, lde)];
+            double s1 = 0.0, s2 = 0.0;
+            for (int k = i + 1; k < n; ++k) s1 += T[IDX(i, k, ldt)] * L[IDX(k, j, ldl)];
+            for (int k = 0; k < j; ++k) s2 += L[IDX(i, k, ldl)] * T[IDX(k, j, ldt)];
+            e = e + s1 - s2;
+            dd_t di = {dhi[i], dlo[i]}, mdj = {-dhi[j], -dlo[j]};
+            dd_t dd = dd_add(di, mdj);
+            double den = dd.hi + dd.lo;
+            if (den == 0.0) return SRO_NONDISTINCT;
+            double l = -e / den;
+            if (!isfinite(l)) return SRO_NONFINITE;
+            L[IDX(i, j, ldl)] = l;
+        }
+    }
+    return SRO_OK;
+}
+
+/* Residuals of a double-double decomposition in 128-bit floating point:
+ *   r_T = ||stril(Q^T A Q)||_F / ||A||_F,  r_Q = ||Q^T Q - I||_F,
+ * A = Ahi + Alo, Q = Qhi + Qlo (the lo planes may be NULL). */
+static inline f128_t q_of(const double *hi, const double *lo, size_t k)
+{
+    return (f128_t)hi[k] + (lo ? (f128_t)lo[k] : (f128_t)0);
+}
+
+void sro_residuals_q(int n, const double *Ahi, const double *Alo, int lda, const double *Qhi,
+                     const double *Qlo, int ldq, double *r_T, double *r_Q)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    f128_t *Q = (f128_t *)malloc(sizeof(f128_t) * nn), *M = (f128_t *)malloc(sizeof(f128_t) * nn);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) Q[IDX(i, j, n)] = q_of(Qhi, Qlo, IDX(i, j, ldq));
+    /* M = A Q */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            f128_t s = 0;
+            for (int l = 0; l < n; ++l) s += q_of(Ahi, Alo, IDX(i, l, lda)) * Q[IDX(l, j, n)];
+            M[IDX(i, j, n)] = s;
+        }
+    double st = 0.0, so = 0.0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : st, so)
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            if (i > j) {
+                f128_t s = 0;
+                for (int l = 0; l < n; ++l) s += Q[IDX(l, i, n)] * M[IDX(l, j, n)];
+                double v = (double)s;
+                st += v * v;
+            }
+            if (i <= j) {
+                f128_t s = 0;
+                for (int l = 0; l < n; ++l) s += Q[IDX(l, i, n)] * Q[IDX(l, j, n)];
+                if (i == j) s -= 1;
+                double v = (double)s;
+                so += (i == j ? 1.0 : 2.0) * v * v;
+            }
+        }
+    double sa = 0.0;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            double a = (double)q_of(Ahi, Alo, IDX(i, j, lda));
+            sa += a * a;
+        }
+    *r_T = sqrt(st) / sqrt(sa);
+    *r_Q = sqrt(so);
+    free(Q); free(M);
+}
+
+/* Sampled entries (rows[s], cols[s]) of Q^T A Q and of Q^T Q - I in 128-bit
+ * floating point for double-double A and Q, returned as double-double pairs
+ * (t_hi + t_lo, y_hi + y_lo). O(n^2) work per sample. */
+void sro_sample_entries_q(int n, const double *Ahi, const double *Alo, int lda, const double *Qhi,
+                          const double *Qlo, int ldq, int ns, const int *rows, const int *cols,
+                          double *t_hi, double *t_lo, double *y_hi, double *y_lo)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int s = 0; s < ns; ++s) {
+        int i = rows[s], j = cols[s];
+        f128_t t = 0;
+        for (int l = 0; l < n; ++l) {
+            f128_t aq = 0;
+            for (int k = 0; k < n; ++k) aq += q_of(Ahi, Alo, IDX(l, k, lda)) * q_of(Qhi, Qlo, IDX(k, j, ldq));
+            t += q_of(Qhi, Qlo, IDX(l, i, ldq)) * aq;
+        }
+        f128_t g = 0;
+        for (int l = 0; l < n; ++l) g += q_of(Qhi, Qlo, IDX(l, i, ldq)) * q_of(Qhi, Qlo, IDX(l, j, ldq));
+        if (i == j) g -= 1;
+        t_hi[s] = (double)t;
+        t_lo[s] = (double)(t - (f128_t)t_hi[s]);
+        y_hi[s] = (double)g;
+        y_lo[s] = (double)(g - (f128_t)y_hi[s]);
+    }
 }

@@ -249,3 +249,186 @@ def batch_sizes(count: int = 1024, lo: int = 32, hi: int = 512, seed: int = BASE
 def batch_problem(i: int, n: int, seed: int = BASE_SEED + 4) -> Planted:
     """Matrix ``i`` of the batched workload, built like the unit-step real problem."""
     return unit_step_real(int(n), seed=seed * 4099 + i + 1, low="f32")
+
+
+# ---------------------------------------------------------------------------
+# Double-double planted problems (working precision above FP64)
+#
+# A pair of float64 arrays (hi, lo) stands for the unevaluated sum hi + lo.
+# The factor Q0 is built from rotations whose cosine and sine are exact
+# rationals, so that Q0 is orthogonal to double-double accuracy without any
+# orthogonalisation step: two butterfly networks (stage b rotates the rows i
+# and i + 2^b for every i with bit b clear) around a random row permutation.
+# Applying the rotations to T0 from both sides gives A = Q0 T0 Q0^T in
+# double-double with a few roundings per entry. The elementary operations are
+# the error-free transformations of Knuth (TwoSum) and Dekker (Veltkamp
+# splitting, TwoProduct), written out for numpy arrays (no fused multiply-add
+# is assumed).
+
+_SPLITTER = 134217729.0   # 2^27 + 1
+
+
+def _two_sum(a, b):
+    s = a + b
+    bb = s - a
+    return s, (a - (s - bb)) + (b - bb)
+
+
+def _quick_two_sum(a, b):
+    s = a + b
+    return s, b - (s - a)
+
+
+def _split(a):
+    t = _SPLITTER * a
+    hi = t - (t - a)
+    return hi, a - hi
+
+
+def _two_prod(a, b):
+    p = a * b
+    ah, al = _split(a)
+    bh, bl = _split(b)
+    return p, ((ah * bh - p) + ah * bl + al * bh) + al * bl
+
+
+def _dd_add(ah, al, bh, bl):
+    s, e = _two_sum(ah, bh)
+    t, f = _two_sum(al, bl)
+    s, e = _quick_two_sum(s, e + t)
+    return _quick_two_sum(s, e + f)
+
+
+def _dd_mul(ah, al, bh, bl):
+    p, e = _two_prod(ah, bh)
+    return _quick_two_sum(p, e + (ah * bl + al * bh))
+
+
+def _dd_div(nh, d):
+    """(nh / d) in double-double for float64 nh, d."""
+    q = nh / d
+    p, e = _two_prod(q, d)
+    r = (nh - p) - e
+    return _quick_two_sum(q, r / d)
+
+
+def _rotation_set(st: Stream, count: int):
+    """cos/sin pairs c = (1 - t^2)/(1 + t^2), s = 2t/(1 + t^2) in double-double,
+    t = k / 2^20 with k uniform in [-2^20, 2^20]: numerators and denominator are
+    exact in float64, so c^2 + s^2 = 1 up to the double-double rounding."""
+    k = np.floor(st.uniform((count,)) * (2.0 ** 21 + 1.0)) - 2.0 ** 20
+    t = k * 2.0 ** -20
+    t2 = t * t                                 # exact: k^2 < 2^41
+    den = 1.0 + t2
+    ch, cl = _dd_div(1.0 - t2, den)
+    sh, sl = _dd_div(2.0 * t, den)
+    return ch, cl, sh, sl
+
+
+@dataclass
+class _Butterflies:
+    n: int
+    stages: list          # per stage: (rows i, rows i + 2^b, c_hi, c_lo, s_hi, s_lo)
+    perm: np.ndarray      # row permutation between the two networks
+    split: int            # stages before the permutation
+
+
+def _make_butterflies(st: Stream, n: int) -> _Butterflies:
+    nb = max(1, int(math.ceil(math.log2(max(n, 2)))))
+    stages = []
+    for _ in range(2):
+        for b in range(nb):
+            i = np.arange(n)
+            i = i[((i >> b) & 1) == 0]
+            i = i[i + (1 << b) < n]
+            stages.append((i, i + (1 << b)) + _rotation_set(st, len(i)))
+    perm = np.argsort(st.uniform((n,)), kind="stable")
+    return _Butterflies(n=n, stages=stages, perm=perm, split=nb)
+
+
+def _apply_rows(bf: _Butterflies, Xh: np.ndarray, Xl: np.ndarray):
+    """(Xh, Xl) <- Q0 (Xh, Xl): the rotations applied to the rows, in double-double."""
+    Xh = Xh.copy()
+    Xl = Xl.copy()
+    for k, (i, j, ch, cl, sh, sl) in enumerate(bf.stages):
+        if k == bf.split:
+            Xh = Xh[bf.perm]
+            Xl = Xl[bf.perm]
+        ch, cl, sh, sl = (v[:, None] for v in (ch, cl, sh, sl))
+        xh, xl, yh, yl = Xh[i], Xl[i], Xh[j], Xl[j]
+        p1 = _dd_mul(ch, cl, xh, xl)
+        p2 = _dd_mul(sh, sl, yh, yl)
+        p3 = _dd_mul(sh, sl, xh, xl)
+        p4 = _dd_mul(ch, cl, yh, yl)
+        Xh[i], Xl[i] = _dd_add(p1[0], p1[1], -p2[0], -p2[1])     # c x - s y
+        Xh[j], Xl[j] = _dd_add(p3[0], p3[1], p4[0], p4[1])       # s x + c y
+    return Xh, Xl
+
+
+@dataclass
+class PlantedDD:
+    """A = Q0 T0 Q0^T held as double-double planes, with a float64 start."""
+
+    A_hi: np.ndarray
+    A_lo: np.ndarray
+    Qhat: np.ndarray       # float64 starting factor
+    Q0_hi: np.ndarray
+    Q0_lo: np.ndarray
+    T0: np.ndarray         # float64, upper triangular
+    lam: np.ndarray
+    seed: int
+    recipe: str
+
+    @property
+    def n(self) -> int:
+        return self.A_hi.shape[0]
+
+
+def planted_dd(n: int, lam: np.ndarray, seed: int, *, pert: float = 1e-14,
+               recipe: str = "") -> PlantedDD:
+    """A = Q0 T0 Q0^T in double-double, Qhat = fl64(Q0 expm(pert S)).
+
+    T0 has diagonal ``lam`` and iid normal strictly-upper entries with standard
+    deviation 1/n (float64, exact in double-double). Q0 is the butterfly
+    factor described above. Cached under $SR_INPUT_CACHE like :func:`planted`."""
+    lam = np.asarray(lam, dtype=np.float64)
+    path = _cache_path(repr(("dd", n, hashlib_digest(lam), seed, pert)))
+    if path is not None:
+        import os
+        if os.path.exists(path):
+            z = np.load(path)
+            f = lambda k: np.asfortranarray(z[k])
+            return PlantedDD(A_hi=f("A_hi"), A_lo=f("A_lo"), Qhat=f("Qhat"), Q0_hi=f("Q0_hi"),
+                             Q0_lo=f("Q0_lo"), T0=f("T0"), lam=z["lam"], seed=seed, recipe=recipe)
+    st = Stream(seed)
+    T0 = np.triu(st.normal((n, n)) * (1.0 / n), 1) + np.diag(lam)
+    bf = _make_butterflies(st, n)
+    z = np.zeros((n, n))
+    Q0h, Q0l = _apply_rows(bf, np.eye(n), z)
+    Mh, Ml = _apply_rows(bf, T0, z)                   # Q0 T0
+    Ah, Al = _apply_rows(bf, Mh.T, Ml.T)              # Q0 (Q0 T0)^T = (Q0 T0 Q0^T)^T
+    Ah, Al = Ah.T, Al.T
+    # Qhat = fl64(Q0 + Q0 (expm(pert S) - I)); the correction is ~pert*n, so
+    # float64 products give it far below the final rounding
+    S = _skew(st, n, False)
+    X = pert * S
+    D = X + X @ X / 2.0 + X @ X @ X / 6.0             # expm(X) - I to third order
+    C = Q0h @ D
+    qh, ql = _dd_add(Q0h, Q0l, C, np.zeros_like(C))
+    Qhat = qh + ql
+    p = PlantedDD(A_hi=np.asfortranarray(Ah), A_lo=np.asfortranarray(Al), Qhat=np.asfortranarray(Qhat),
+                  Q0_hi=np.asfortranarray(Q0h), Q0_lo=np.asfortranarray(Q0l), T0=np.asfortranarray(T0),
+                  lam=lam, seed=seed, recipe=recipe)
+    if path is not None:
+        import os
+        tmp = path + ".tmp.npz"
+        np.savez(tmp, A_hi=p.A_hi, A_lo=p.A_lo, Qhat=p.Qhat, Q0_hi=p.Q0_hi, Q0_lo=p.Q0_lo, T0=p.T0, lam=p.lam)
+        os.replace(tmp, path)
+    return p
+
+
+def unit_step_dd(n: int = 2048, seed: int = BASE_SEED + 5) -> PlantedDD:
+    """Double-double planted problem, lambda_k = 1 + k/64, Qhat = fl64(Q0 expm(1e-14 S))."""
+    return planted_dd(n, eig_unit_step(n), seed, pert=1e-14,
+                      recipe=f"real n={n} double-double, lambda_k=1+k/64, upper std 1/n, "
+                             f"Qhat=fl64(Q0 expm(1e-14 S))")
