@@ -135,18 +135,24 @@ def run_reference(args):
     if rank != 0:
         return 0
     n, ns, cplx = args.n, args.cpu_sample_n, args.workload == "complex"
+    dd = args.workload == "dd"
     times = []
     for i in range(args.warmup + args.steps):
-        est, dt, r, cores = cpu_oracle_sample(n, ns, cplx)
+        est, dt, r, cores = cpu_oracle_sample_dd(n, ns) if dd else cpu_oracle_sample(n, ns, cplx)
         if i >= args.warmup:
             times.append(est)
     v = sum(times) / len(times)
-    sample = (f"oracle (numpy FP64 products + C Alg. 2 in FP32) full refinement at n={ns} of the same "
-              f"recipe, scaled by (n/{ns})^3 to n={n}")
+    if dd:
+        sample = (f"double-double oracle (C triple-loop TwoProd/TwoSum products + C Alg. 2 in FP64) full "
+                  f"refinement at n={ns} of the same recipe, scaled by (n/{ns})^3 to n={n}")
+    else:
+        sample = (f"oracle (numpy FP64 products + C Alg. 2 in FP32) full refinement at n={ns} of the same "
+                  f"recipe, scaled by (n/{ns})^3 to n={n}")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": _workload_name(n, cplx), "n": n, "form": "mixed FP32->FP64 (oracle)"},
+            "vs_baseline": None, "dtype": "dd+f64" if dd else "f64+f32", "data": "synthetic",
+            "config": {"workload": _dd_workload_name(n) if dd else _workload_name(n, cplx), "n": n,
+                       "form": "FP64->double-double (oracle)" if dd else "mixed FP32->FP64 (oracle)"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -416,6 +422,168 @@ def run_batched(args):
     return 0
 
 
+def _dd_workload_name(n):
+    return (f"real n={n} double-double planted A=Q0 T0 Q0^T (Q0 from exact-rational rotations), "
+            f"lambda_k=1+k/64, upper std 1/n, Qhat=fl64(Q0 expm(1e-14 S)); Alg. 4 with double-double hp and "
+            f"FP64 lp to ||stril||/||A||<=1e-28 n")
+
+
+def cpu_oracle_sample_dd(n_full: int, n_sample: int):
+    """The double-double oracle's full refinement at n_sample, scaled by (n_full/n_sample)^3."""
+    from oracle import ddtarget
+    from paper_2203_10879_gb300 import inputs
+    p = inputs.unit_step_dd(n_sample)
+    t0 = time.perf_counter()
+    r = ddtarget.refine_dd((p.A_hi, p.A_lo), p.Qhat)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return dt * (n_full / n_sample) ** 3, dt, r, cores
+
+
+def run_dd(args):
+    """The double-double workload: one step = one refinement of the n = 2048
+    planted double-double problem from its FP64 start to ||stril||/||A|| <= 1e-28 n.
+    The emulated double-double products (14 bf16 digits per operand on the
+    tensor cores) are timed; the same iteration with SIMT double-double
+    products built from FP64 TwoProd/TwoSum is timed beside it."""
+    import numpy as np
+    import torch
+
+    import paper_2203_10879_gb300 as P
+    from paper_2203_10879_gb300 import _binding as B
+    from paper_2203_10879_gb300 import inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+    n = args.n
+    p = inputs.unit_step_dd(n)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+    A = dev(np.hstack([p.A_hi, p.A_lo]))
+    Qhat = dev(p.Qhat)
+    Q = torch.empty((2 * n, n), dtype=torch.float64, device="cuda").t()
+    stream = torch.cuda.current_stream()
+    common = dict(target=B.SR_TARGET_DD, lp=B.SR_LP_FP64, qhat_type=B.SR_QHAT_FP64)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(ref, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            ref.step(A, Q, Qhat, check=False)
+        ref.reset_profile()
+        torch.cuda.synchronize()
+        barrier()
+        if clocks:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = nr = None
+        for _ in range(steps):
+            st, nr = ref.step(A, Q, Qhat, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if clocks else None
+        return e0.elapsed_time(e1) / steps, st, nr, clk
+
+    mixed = P.Refiner(n, hp_gemm=B.SR_HP_OZAKI_BF16, profile=1, ozaki_slices=args.slices, **common)
+    ms, status, nr, clk = timed(mixed, args.steps, args.warmup, Clocks(local))
+    prof = mixed.profile()
+    rT, rQ = mixed.residuals(A, Q)
+    launches = int(sum(v["launches"] for v in prof.values()))
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # end to end through pinned host buffers
+    hA = torch.from_numpy(np.ascontiguousarray(np.hstack([p.A_hi, p.A_lo]).T)).pin_memory()
+    hQh = torch.from_numpy(np.ascontiguousarray(p.Qhat.T)).pin_memory()
+    hQ = torch.empty((2 * n, n), dtype=torch.float64).pin_memory()
+    dA_t = torch.empty((2 * n, n), dtype=torch.float64, device="cuda")
+    dQh_t = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    dQ_t = torch.empty((2 * n, n), dtype=torch.float64, device="cuda")
+    ke = max(1, min(args.steps, 3))
+    for i in range(1 + ke):
+        if i == 1:
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+        dA_t.copy_(hA, non_blocking=True)
+        dQh_t.copy_(hQh, non_blocking=True)
+        mixed.step(dA_t.t(), dQ_t.t(), dQh_t.t(), check=False)
+        hQ.copy_(dQ_t, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke
+    mixed.close()
+    # the same iteration with SIMT double-double products (FP64 error-free transformations)
+    simt = P.Refiner(n, hp_gemm=B.SR_HP_FP64, profile=1, **common)
+    k64 = max(1, min(args.steps, args.fp64_steps))
+    ms64, st64, nr64, _ = timed(simt, k64, 1)
+    prof64 = simt.profile()
+    simt.close()
+    if rank != 0:
+        return 0
+    peaks = _peaks()
+    kinds = {k: v for k, v in prof.items() if v["ms"] > 0}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = prof[dom]
+    if dom == "oz_mma":
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "ozaki slice products (tcgen05 kind::f16 bf16), 14 digits",
+                "peak_source": "of measured bf16 sustained (MEASURED_PEAKS.json)"}
+    else:
+        gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs") or 6800.0
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                "traffic": None, "kernel": dom, "peak_source": "of measured HBM copy"}
+    roof["launch_ms"] = d["ms"] / max(1, d["spans"])
+    roof["share_of_step"] = d["ms"] / (ms * args.steps)
+    cpu = None
+    if not args.no_cpu_baseline:
+        ns = args.cpu_sample_n
+        est, dt, r, cores = cpu_oracle_sample_dd(n, ns)
+        cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": f"double-double oracle full refinement at n={ns} ({dt:.2f} s measured), "
+                         f"scaled by (n/{ns})^3 to n={n}"}
+    tol = 1e-28 * n
+    line = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "dd+f64", "data": "synthetic",
+        "config": {"workload": _dd_workload_name(n), "n": n,
+                   "form": "double-double hp (emulated, bf16 digits), FP64 solve/products",
+                   "hp_gemm": f"ozaki-bf16-s{args.slices or 14}",
+                   "l2": f"inputs larger than L2 (A {2 * n * n * 8 >> 20} MiB + Q + workspace)",
+                   "status": status, "iters": nr.iters, "hp_gemms": nr.hp_gemms,
+                   "certified": {"stril_rel": rT, "orth": rQ, "tol": tol,
+                                 "kind": "double-double residual products on the device",
+                                 "ok": bool(rT <= tol and rQ <= tol)},
+                   "simt_dd_s": ms64 / 1e3, "simt_dd_status": st64, "simt_dd_iters": nr64.iters,
+                   "emulated_vs_simt_dd_speedup": ms64 / ms,
+                   "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
+                   "simt_dd_phase_ms_per_step": {k: v["ms"] / k64 for k, v in prof64.items() if v["ms"] > 0},
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n * n * 8 * 3),
+                "d2h_bytes_per_step": int(n * n * 16)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,18 +596,20 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-n", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single", "complex", "batched"], default="single")
+    ap.add_argument("--workload", choices=["single", "complex", "batched", "dd"], default="single")
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--batch-streams", type=int, default=8)
     args = ap.parse_args()
     if args.n is None:
-        args.n = 8192 if args.workload == "complex" else 4096
+        args.n = {"complex": 8192, "dd": 2048}.get(args.workload, 4096)
     if args.cpu_sample_n is None:
-        args.cpu_sample_n = 2048 if args.workload == "complex" else 1024
+        args.cpu_sample_n = {"complex": 2048, "dd": 512}.get(args.workload, 1024)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "dd":
+        return run_dd(args)
     return run_ours(args)
 
 

@@ -59,8 +59,13 @@ typedef enum {
    precision) is built for hp_gemm = SR_HP_OZAKI_BF16 with lp = SR_LP_FP32 and
    orders up to 8192; other combinations give SR_ERR_UNSUPPORTED at create. */
 enum { SR_REAL = 0, SR_COMPLEX = 1 };
-/* working high precision */
-enum { SR_TARGET_FP64 = 0 };
+/* working high precision. SR_TARGET_DD (double-double, Sec. 3's higher
+   working precisions one level above FP64) is built for real data with
+   lp = SR_LP_FP64 and qhat_type = SR_QHAT_FP64. A double-double matrix is
+   two column-major planes with the same leading dimension ld, hi and lo,
+   standing for hi + lo; the lo plane starts ld * c elements after the hi
+   plane, c = the number of columns stored. */
+enum { SR_TARGET_FP64 = 0, SR_TARGET_DD = 1 };
 /* engine of the high-precision products (Sec. 2.4: "hp matrix-matrix
    multiplications"; the paper uses the Ozaki scheme, Sec. 3) */
 enum {
@@ -75,18 +80,19 @@ enum { SR_QHAT_FP32 = 0, SR_QHAT_FP64 = 1 };
 
 typedef struct {
     int dtype;        /* SR_REAL or SR_COMPLEX */
-    int target;       /* SR_TARGET_FP64 */
+    int target;       /* SR_TARGET_FP64 or SR_TARGET_DD */
     int hp_gemm;      /* SR_HP_FP64 or SR_HP_OZAKI_BF16 */
     int lp;           /* SR_LP_FP32 (mixed form) or SR_LP_FP64 (all-FP64 form) */
     int qhat_type;    /* SR_QHAT_FP32 or SR_QHAT_FP64 */
     int full_sigma;   /* 1: keep W^2 Y + W^2 Y W in Sigma (eq. NSmerged);
                          0 (default): drop them, as Sec. 2.4 does */
     int max_iter;     /* passes of the REPEAT loop; <= 0 selects 10 */
-    int ozaki_slices; /* bf16 slices per operand of the emulated products;
-                         <= 0 selects the library default (7) */
+    int ozaki_slices; /* bf16 slices per operand of the emulated
+                         high-precision products; <= 0 selects the library
+                         default (7; 14 for SR_TARGET_DD); at most 7 (14) */
     double tol;       /* stop when ||stril(T^)||_F / ||A||_F <= tol and the
                          last ||Q^H Q - I||_F <= sqrt(tol); <= 0 selects
-                         1e-14 * sqrt(n) */
+                         1e-14 * sqrt(n) (1e-28 * n for SR_TARGET_DD) */
     int profile;      /* 1: time every phase with CUDA events on the handle's
                          stream (see schur_refine_get_profile) */
     int batch_streams;/* schur_refine_batched: matrices refined concurrently,
@@ -120,11 +126,13 @@ sr_status schur_refine_create(schur_refine_t *h, int n_max, const sr_options *op
 /*
  * Runs Alg. 4 (Sec. 2.4) on one matrix of order n <= n_max.
  *   dA        device, n x n, lda: A in FP64 (interleaved complex128 when
- *             dtype is SR_COMPLEX). Not modified.
+ *             dtype is SR_COMPLEX; two planes when target is SR_TARGET_DD,
+ *             and likewise dQ and dT). Not modified.
  *   dQ        device, n x n, ldq, FP64 (complex128). In: the starting factor
  *             when dQhat is NULL. Out: the refined factor.
  *   dQhat     device, n x n with leading dimension ldq, element type
- *             qhat_type (complex64/complex128 when complex), or NULL. When
+ *             qhat_type (complex64/complex128 when complex; FP64, one
+ *             plane, for SR_TARGET_DD), or NULL. When
  *             given, Q is first set to one Newton-Schulz step of Qhat
  *             converted to FP64 (Alg. 4, second line; eq. NS), and dQ's input
  *             value is ignored.
@@ -167,8 +175,10 @@ sr_status schur_refine_batched(schur_refine_t h, int batch, const int *n, const 
  * The two accuracy measures of Sec. 3 (Examples 2 and 4):
  *   *stril_rel = ||stril(Q^H A Q)||_F / ||A||_F,  *orth = ||Q^H Q - I||_F,
  * with every product accumulated in double-double arithmetic (TwoProd/TwoSum)
- * so that values near 1e-16 are resolved. dA, dQ as in schur_refine_step;
- * stril_rel, orth: host. Synchronizes the stream.
+ * so that values near 1e-16 are resolved (for SR_TARGET_DD the double-double
+ * A and Q enter with both planes; the accumulation error, about n * 1e-32
+ * relative, stays far below the target 1e-28 n). dA, dQ as in
+ * schur_refine_step; stril_rel, orth: host. Synchronizes the stream.
  */
 sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int lda, const void *dQ,
                                  int ldq, double *stril_rel, double *orth);
@@ -206,7 +216,8 @@ sr_status schur_refine_residuals_noalloc(int n, const void *dA, int lda, const v
  *          triangle holds L; the upper triangle is unchanged.
  *   dDiag  device, n entries, FP64 (complex128): the diagonal of T in high
  *          precision; divisors t_ii - t_jj are formed from it and then
- *          rounded to the low precision.
+ *          rounded to the low precision. SR_TARGET_DD: 2n entries, the high
+ *          parts of the double-double diagonal followed by the low parts.
  * Returns SR_ERR_NONDISTINCT on a zero divisor (Theorem 1), SR_ERR_NONFINITE
  * on a non-finite entry of L. Synchronizes the stream.
  */
@@ -217,6 +228,8 @@ sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, cons
  * Q^H (A Q): C = op(A) B with op(A) = A (transA = 0) or A^H (transA = 1).
  *   dA  device, FP64 (complex128): m x k (transA = 0) or k x m (transA = 1), lda
  *   dB  device, k x n, ldb;  dC device, m x n, ldc (overwritten).
+ * SR_TARGET_DD: A, B and C are double-double (two planes each, see
+ * SR_TARGET_DD), C accurate to about k * 1e-32 relative to |op(A)| |B|.
  * Sizes up to n_max in every dimension.
  */
 sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, const void *dA,

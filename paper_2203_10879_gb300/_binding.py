@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libschur_refine.so")
 SR_OK, SR_ERR_INVALID_ARG, SR_ERR_NONDISTINCT, SR_ERR_NONFINITE = 0, 1, 2, 3
 SR_ERR_NOT_CONVERGED, SR_ERR_TIMEOUT, SR_ERR_CUDA, SR_ERR_OOM, SR_ERR_UNSUPPORTED = 4, 5, 6, 7, 8
 SR_REAL, SR_COMPLEX = 0, 1
-SR_TARGET_FP64 = 0
+SR_TARGET_FP64, SR_TARGET_DD = 0, 1
 SR_HP_FP64, SR_HP_OZAKI_BF16 = 0, 1
 SR_LP_FP32, SR_LP_FP64 = 0, 1
 SR_QHAT_FP32, SR_QHAT_FP64 = 0, 1
@@ -125,6 +125,15 @@ def _dev(t, what):
 def colmajor(t):
     """A column-major copy of a 2-D tensor (same device and dtype)."""
     return t.t().contiguous().t()
+
+
+def dd_pair(t):
+    """(hi, lo) views of a double-double matrix held as one column-major
+    tensor of shape (n, 2c): the hi plane in columns [0, c), lo in [c, 2c) --
+    the layout the C ABI expects for SR_TARGET_DD (lo plane ld * c elements
+    after hi)."""
+    c = t.shape[1] // 2
+    return t[:, :c], t[:, c:]
 
 
 def default_options(**kw) -> sr_options:

@@ -168,3 +168,63 @@ __device__ inline double sr_block_sum(double v)
     }
     return v;
 }
+
+// ---- double-double arithmetic (hi + lo, |lo| <= ulp(hi)/2 after renormalisation) ----
+// Knuth's TwoSum, the fast renormalisation of Dekker, and products through
+// fused multiply-adds (exact a*b = p + fma(a, b, -p)).
+struct ddv { double hi, lo; };
+
+__device__ inline ddv dd_two_sum(double a, double b)
+{
+    const double s = a + b;
+    const double z = s - a;
+    return {s, (a - (s - z)) + (b - z)};
+}
+__device__ inline ddv dd_renorm(double a, double b)
+{
+    const double s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ inline ddv dd_plus(ddv a, ddv b)
+{
+    ddv s = dd_two_sum(a.hi, b.hi);
+    const ddv t = dd_two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = dd_renorm(s.hi, s.lo);
+    s.lo += t.lo;
+    return dd_renorm(s.hi, s.lo);
+}
+// exact product a*b as hi + lo, plus a*c folded into the low part
+__device__ inline ddv dd_times(double a, double b, double c)
+{
+    const double p = a * b;
+    double e = fma(a, b, -p);
+    e = fma(a, c, e);
+    return {p, e};
+}
+
+// a + b for a double b
+__device__ inline ddv dd_plus_d(ddv a, double b)
+{
+    ddv s = dd_two_sum(a.hi, b);
+    s.lo += a.lo;
+    return dd_renorm(s.hi, s.lo);
+}
+// (ah + al)(bh + bl): the exact product of the high parts plus the two cross
+// terms (al*bl is below the double-double rounding and dropped)
+__device__ inline ddv dd_mul(ddv a, ddv b)
+{
+    const double p = a.hi * b.hi;
+    double e = fma(a.hi, b.hi, -p);
+    e = fma(a.hi, b.lo, e);
+    e = fma(a.lo, b.hi, e);
+    return dd_renorm(p, e);
+}
+// a + b with the low parts added in double (the accumulation of products:
+// the error stays below a few units of 2^-104 times |a| + |b|)
+__device__ inline ddv dd_acc(ddv a, ddv b)
+{
+    ddv s = dd_two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return dd_renorm(s.hi, s.lo);
+}

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dd.cuh"
 #include "gemm_simt.cuh"
 #include "kernels_misc.cuh"
 #include "ozaki.cuh"
@@ -43,6 +44,7 @@ struct schur_refine_ctx {
     int dev = 0;
     // workspace (ld = nmax)
     double *AQ = nullptr, *Qw = nullptr, *Y = nullptr, *Delta = nullptr, *diag = nullptr;
+    double *diag_lo = nullptr;   // double-double target: low parts of the diagonal of T^
     void *TE = nullptr, *W2 = nullptr, *YW = nullptr, *W2Y = nullptr, *W2YW = nullptr;   // low precision
     double *Wd = nullptr, *W2d = nullptr, *W2Yd = nullptr, *W2YWd = nullptr;   // FP64, emulated-product pass
     double *partial = nullptr;   // per-block partial sums
@@ -59,7 +61,7 @@ struct schur_refine_ctx {
     // the solve's two streams of work are captured once per (order, buffers)
     cudaStream_t cap_st = nullptr, aux_st = nullptr;
     cudaEvent_t sev0 = nullptr, sev1 = nullptr;
-    struct SolveGraph { int n; const void *TE; int ld; const void *dhp; int kind; cudaGraphExec_t exec; };
+    struct SolveGraph { int n; const void *TE; int ld; const void *dhp; const void *dlo; int kind; cudaGraphExec_t exec; };
     std::vector<SolveGraph> graphs;
     // workers of schur_refine_batched: sub-handles on their own streams
     std::vector<schur_refine_ctx *> subs;
@@ -127,16 +129,21 @@ namespace {
 
 bool is_cplx(const sr_options &o) { return o.dtype == SR_COMPLEX; }
 size_t lp_size(const sr_options &o) { return (o.lp == SR_LP_FP32 ? sizeof(float) : sizeof(double)) * (is_cplx(o) ? 2 : 1); }
-size_t hp_size(const sr_options &o) { return sizeof(double) * (is_cplx(o) ? 2 : 1); }
+// high-precision element: FP64, complex128, or a double-double pair (two planes)
+size_t hp_size(const sr_options &o) { return sizeof(double) * (is_cplx(o) || o.target == SR_TARGET_DD ? 2 : 1); }
 
 sr_status check_opts(const sr_options &o)
 {
     if (o.dtype != SR_REAL && o.dtype != SR_COMPLEX) return SR_ERR_INVALID_ARG;
-    if (o.target != SR_TARGET_FP64) return SR_ERR_INVALID_ARG;
+    if (o.target != SR_TARGET_FP64 && o.target != SR_TARGET_DD) return SR_ERR_INVALID_ARG;
     if (o.hp_gemm != SR_HP_FP64 && o.hp_gemm != SR_HP_OZAKI_BF16) return SR_ERR_INVALID_ARG;
     if (o.lp != SR_LP_FP32 && o.lp != SR_LP_FP64) return SR_ERR_INVALID_ARG;
     if (o.qhat_type != SR_QHAT_FP32 && o.qhat_type != SR_QHAT_FP64) return SR_ERR_INVALID_ARG;
-    if (o.ozaki_slices > sr::kOzakiMaxSlices) return SR_ERR_INVALID_ARG;
+    if (o.ozaki_slices > (o.target == SR_TARGET_DD ? sr::kOzakiMaxSlicesDD : sr::kOzakiMaxSlices))
+        return SR_ERR_INVALID_ARG;
+    // double-double target: real data, FP64 correction path, FP64 start
+    if (o.target == SR_TARGET_DD && (o.dtype != SR_REAL || o.lp != SR_LP_FP64 || o.qhat_type != SR_QHAT_FP64))
+        return SR_ERR_UNSUPPORTED;
     // complex data: the emulated products with the complex64 correction path
     if (o.dtype == SR_COMPLEX && (o.hp_gemm != SR_HP_OZAKI_BF16 || o.lp != SR_LP_FP32)) return SR_ERR_UNSUPPORTED;
     if (o.hp_gemm == SR_HP_OZAKI_BF16 && !sr::kOzakiBuilt) return SR_ERR_UNSUPPORTED;
@@ -266,19 +273,20 @@ sr_status ensure_plan(schur_refine_ctx *h, int n)
 }
 
 template <typename Tl>
-sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum<Tl>::hp *dhp)
+sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum<Tl>::hp *dhp,
+                const double *dlo = nullptr)
 {
     SR_TRY(ensure_plan(h, n));
     const int NB = (n + sr::kSolveTile - 1) / sr::kSolveTile;
     const int kind = SrNum<Tl>::kind;
     cudaGraphExec_t exec = nullptr;
     for (auto &g : h->graphs)
-        if (g.n == n && g.TE == TE && g.ld == ld && g.dhp == dhp && g.kind == kind) exec = g.exec;
+        if (g.n == n && g.TE == TE && g.ld == ld && g.dhp == dhp && g.dlo == dlo && g.kind == kind) exec = g.exec;
     if (!exec) {
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t el = sr::trisolve_launches<Tl>(h->cap_st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp,
+            cudaError_t el = sr::trisolve_launches<Tl>(h->cap_st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp, dlo,
                                                        h->dflags, h->plan, h->plan_off);
             e = cudaStreamEndCapture(h->cap_st, &graph);
             if (el != cudaSuccess) e = el;
@@ -286,7 +294,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e == cudaSuccess) {
-            h->graphs.push_back({n, TE, ld, dhp, kind, exec});
+            h->graphs.push_back({n, TE, ld, dhp, dlo, kind, exec});
         } else {
             // no graph (for example while the caller captures this stream): the same
             // launches, issued directly on the two streams
@@ -299,7 +307,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
     if (exec) {
         SR_CUDA_TRY(cudaGraphLaunch(exec, h->st));
     } else {
-        SR_CUDA_TRY(sr::trisolve_launches<Tl>(h->st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp, h->dflags,
+        SR_CUDA_TRY(sr::trisolve_launches<Tl>(h->st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp, dlo, h->dflags,
                                               h->plan, h->plan_off));
     }
     return SR_OK;
@@ -575,6 +583,259 @@ sr_status run_step(schur_refine_ctx *h, int n, const void *A, int lda, void *dQ,
     return status;
 }
 
+// ---- double-double working precision (target SR_TARGET_DD) --------------------------
+// Alg. 4 with hp = double-double and lp = FP64. A double-double matrix of the
+// caller is two planes, the low one ld * n elements after the high one; the
+// workspace's planes are nmax * nmax elements apart.
+
+struct DdMat {
+    double *hi, *lo;
+    int ld;
+};
+
+bool is_dd(const sr_options &o) { return o.target == SR_TARGET_DD; }
+int oz_s_dd(const schur_refine_ctx *h) { return h->opt.ozaki_slices > 0 ? h->opt.ozaki_slices : sr::kOzakiDefaultSlicesDD; }
+
+DdMat dd_caller(const void *p, int ld, int n)
+{
+    double *hi = (double *)p;
+    return {hi, hi + (size_t)ld * (size_t)n, ld};
+}
+DdMat dd_work(const schur_refine_ctx *h, double *p)
+{
+    return {p, p + (size_t)h->nmax * (size_t)h->nmax, h->nmax};
+}
+
+// C = op(A) B with the SIMT double-double kernel; epilogue ep, norms to dnorm[slot]
+template <class EP>
+sr_status ddk_gemm(schur_refine_ctx *h, bool transA, int m, int n, int k, DdMat A, DdMat B, EP ep, int slot)
+{
+    double *part = slot >= 0 ? h->partial : nullptr;
+    {
+        SrPhase ph(h, SR_PROF_HP_GEMM, 2LL * m * n * k, 16LL * ((long long)m * k + (long long)k * n + (long long)m * n),
+                   1);
+        const sr::LoadNDD lb{B.hi, B.lo, B.ld};
+        cudaError_t e;
+        if (transA)
+            e = sr::gemm_ddk(h->st, m, n, k, sr::LoadTDD{A.hi, A.lo, A.ld}, lb, ep, part);
+        else
+            e = sr::gemm_ddk(h->st, m, n, k, sr::LoadNDD{A.hi, A.lo, A.ld}, lb, ep, part);
+        SR_CUDA_TRY(e);
+    }
+    if (slot >= 0) SR_TRY(reduce_to(h, sr::ddk_blocks(m, n), slot));
+    return SR_OK;
+}
+
+// emulated: split a double-double matrix into the handle's hp digits
+sr_status oz_split_dd(schur_refine_ctx *h, int slot, int n, DdMat X, int layout)
+{
+    return sr::ozaki_split_dd(h, h->st, h->oz, slot, n, n, X.hi, X.lo, X.ld, layout, oz_s_dd(h));
+}
+
+// Y = Q^T Q - I (double-double) and ||Y||^2 -> dnorm[1]; emulated: from the
+// column digits of Q in slot OZS_COLS
+template <bool OZ>
+sr_status dd_gram(schur_refine_ctx *h, int n, DdMat Q)
+{
+    const DdMat Y = dd_work(h, h->Y);
+    const sr::EpMinusIDD ep{Y.hi, Y.lo, Y.ld};
+    if constexpr (OZ) {
+        const int s = oz_s_dd(h);
+        int blocks = 0;
+        SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_COLS, n, n, n, s, true, h->dflags));
+        SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_COLS, n, n, s, 1.0, true, ep, h->partial,
+                                 &blocks));
+        return reduce_to(h, blocks, 1);
+    } else {
+        return ddk_gemm(h, true, n, n, n, Q, Q, ep, 1);
+    }
+}
+
+// Qn = Q + alpha Q X in double-double
+template <bool OZ>
+sr_status dd_apply(schur_refine_ctx *h, int n, DdMat Q, DdMat X, DdMat Qn, double alpha)
+{
+    const sr::EpUpdateDD ep{Q.hi, Q.lo, Q.ld, Qn.hi, Qn.lo, Qn.ld, alpha};
+    if constexpr (OZ) {
+        const int s = oz_s_dd(h);
+        SR_TRY(oz_split_dd(h, sr::OZS_QROWS, n, Q, sr::OZ_ROWS));
+        SR_TRY(oz_split_dd(h, sr::OZS_X, n, X, sr::OZ_COLS));
+        SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_QROWS, sr::OZS_X, n, n, n, s, false, h->dflags));
+        return sr::ozaki_combine(h, h->st, h->oz, sr::OZS_QROWS, sr::OZS_X, n, n, s, 1.0, false, ep, nullptr,
+                                 nullptr);
+    } else {
+        return ddk_gemm(h, false, n, n, n, Q, X, ep, -1);
+    }
+}
+
+// S1 + S2 in double-double: A Q, T^ = Q^T (A Q) split into TE (FP64) and the
+// double-double diagonal; ||E||^2 -> dnorm[0]
+template <bool OZ>
+sr_status dd_form_residual(schur_refine_ctx *h, int n, DdMat A, DdMat Q, DdMat That)
+{
+    const DdMat AQ = dd_work(h, h->AQ);
+    const int ld = h->nmax;
+    const sr::EpSplitDD ep{(double *)h->TE, ld, h->diag, h->diag_lo, That.hi, That.lo, That.ld};
+    if constexpr (OZ) {
+        const int s = oz_s_dd(h);
+        int blocks = 0;
+        SR_TRY(oz_split_dd(h, sr::OZS_COLS, n, Q, sr::OZ_COLS));
+        SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, n, n, n, s, false, h->dflags));
+        SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, n, n, s, 1.0, false,
+                                 sr::EpStoreDD{AQ.hi, AQ.lo, AQ.ld}, nullptr, nullptr));
+        SR_TRY(oz_split_dd(h, sr::OZS_X, n, AQ, sr::OZ_COLS));
+        SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, n, s, false, h->dflags));
+        SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, s, 1.0, false, ep, h->partial,
+                                 &blocks));
+        return reduce_to(h, blocks, 0);
+    } else {
+        SR_TRY(ddk_gemm(h, false, n, n, n, A, Q, sr::EpStoreDD{AQ.hi, AQ.lo, AQ.ld}, -1));
+        return ddk_gemm(h, true, n, n, n, Q, AQ, ep, 0);
+    }
+}
+
+// S5-S8 in double-double: Y, W = L - L^T (FP64), YW, W^2, W^3 in FP64,
+// Delta = Sigma - 2I in double-double, Q_new = Q + 1/2 Q Delta
+template <bool OZ>
+sr_status dd_update(schur_refine_ctx *h, int n, DdMat Q, DdMat Qn)
+{
+    using namespace sr;
+    const int ld = h->nmax;
+    cudaStream_t st = h->st;
+    SR_TRY(dd_gram<OZ>(h, n, Q));   // emulated: Q's column digits are those of the residual
+    const DdMat Y = dd_work(h, h->Y), Dl = dd_work(h, h->Delta);
+    double *Wd = h->Wd, *W2 = (double *)h->W2, *YW = (double *)h->YW;
+    double *W2Y = (double *)h->W2Y, *W2YW = (double *)h->W2YW;
+    {
+        SrPhase ph(h, SR_PROF_OTHER, 0, 16LL * n * n, 1);
+        dim3 grid((n + 31) / 32, (n + 31) / 32);
+        form_skew_kernel<double><<<grid, 256, 0, st>>>(n, (const double *)h->TE, ld, Wd, ld);
+        SR_CUDA_TRY(cudaGetLastError());
+    }
+    const bool full = h->opt.full_sigma != 0;
+    EpDeltaDD ed{Wd, YW, W2, full ? W2Y : nullptr, full ? W2YW : nullptr, ld, Y.hi, Y.lo, Y.ld, Dl.hi, Dl.lo, Dl.ld};
+    if constexpr (OZ) {
+        // FP64-class emulated products (7 digits): W^2 = -W^T W, YW = Y^T W,
+        // W^3 = -W^T W^2, with Y rounded to FP64 (its high plane)
+        const int sl = kOzakiDefaultSlices;
+        OzakiWork &w = h->oz;
+        SR_TRY(ozaki_split(h, st, w, OZS_W, n, n, Wd, ld, OZ_COLS, sl));
+        SR_TRY(ozaki_split(h, st, w, OZS_Y, n, n, Y.hi, ld, OZ_COLS, sl));
+        SR_TRY(ozaki_product(h, st, w, OZS_W, OZS_W, n, n, n, sl, true, h->dflags));
+        SR_TRY(ozaki_combine(h, st, w, OZS_W, OZS_W, n, n, sl, -1.0, true, EpStore{W2, ld}, nullptr, nullptr));
+        SR_TRY(ozaki_product(h, st, w, OZS_Y, OZS_W, n, n, n, sl, false, h->dflags));
+        SR_TRY(ozaki_combine(h, st, w, OZS_Y, OZS_W, n, n, sl, 1.0, false, EpStore{YW, ld}, nullptr, nullptr));
+        SR_TRY(ozaki_split(h, st, w, OZS_W2, n, n, W2, ld, OZ_COLS, sl));
+        if (full) {
+            SR_TRY(ozaki_product(h, st, w, OZS_W2, OZS_Y, n, n, n, sl, false, h->dflags));
+            SR_TRY(ozaki_combine(h, st, w, OZS_W2, OZS_Y, n, n, sl, 1.0, false, EpStore{W2Y, ld}, nullptr, nullptr));
+            SR_TRY(ozaki_split(h, st, w, 7, n, n, W2Y, ld, OZ_ROWS, sl));
+            SR_TRY(ozaki_product(h, st, w, 7, OZS_W, n, n, n, sl, false, h->dflags));
+            SR_TRY(ozaki_combine(h, st, w, 7, OZS_W, n, n, sl, 1.0, false, EpStore{W2YW, ld}, nullptr, nullptr));
+        }
+        SR_TRY(ozaki_product(h, st, w, OZS_W, OZS_W2, n, n, n, sl, false, h->dflags));
+        SR_TRY(ozaki_combine(h, st, w, OZS_W, OZS_W2, n, n, sl, -1.0, false, ed, nullptr, nullptr));
+    } else {
+        const long long f1 = 2LL * n * n * n, b1 = 32LL * n * n;
+        SrPhase ph(h, SR_PROF_LP_GEMM, f1 * (full ? 5 : 3), b1 * (full ? 5 : 3), full ? 5 : 3);
+        const LoadN<double, double> w{Wd, ld};
+        SR_CUDA_TRY(gemm_simt<double>(st, n, n, n, w, w, EpStoreLp<double>{W2, ld}, nullptr));
+        SR_CUDA_TRY(gemm_simt<double>(st, n, n, n, LoadN<double, double>{Y.hi, ld}, w, EpStoreLp<double>{YW, ld},
+                                      nullptr));
+        if (full) {
+            SR_CUDA_TRY(gemm_simt<double>(st, n, n, n, LoadN<double, double>{W2, ld},
+                                          LoadN<double, double>{Y.hi, ld}, EpStoreLp<double>{W2Y, ld}, nullptr));
+            SR_CUDA_TRY(gemm_simt<double>(st, n, n, n, LoadN<double, double>{W2Y, ld}, w,
+                                          EpStoreLp<double>{W2YW, ld}, nullptr));
+        }
+        SR_CUDA_TRY(gemm_simt<double>(st, n, n, n, w, LoadN<double, double>{W2, ld}, ed, nullptr));
+    }
+    return dd_apply<OZ>(h, n, Q, Dl, Qn, 0.5);
+}
+
+sr_status copy_dd(schur_refine_ctx *h, int n, DdMat src, DdMat dst)
+{
+    if (src.hi == dst.hi) return SR_OK;
+    SrPhase ph(h, SR_PROF_OTHER, 0, 32LL * n * n, 2);
+    SR_CUDA_TRY(cudaMemcpy2DAsync(dst.hi, (size_t)dst.ld * 8, src.hi, (size_t)src.ld * 8, (size_t)n * 8, n,
+                                  cudaMemcpyDeviceToDevice, h->st));
+    SR_CUDA_TRY(cudaMemcpy2DAsync(dst.lo, (size_t)dst.ld * 8, src.lo, (size_t)src.ld * 8, (size_t)n * 8, n,
+                                  cudaMemcpyDeviceToDevice, h->st));
+    return SR_OK;
+}
+
+// One call of Alg. 4 with the double-double target. OZ: emulated products.
+template <bool OZ>
+sr_status run_step_dd(schur_refine_ctx *h, int n, const void *dA, int lda, void *dQ, int ldq, const void *dQhat,
+                      void *dT, sr_norms *out)
+{
+    const int ld = h->nmax;
+    const double tol = h->opt.tol > 0 ? h->opt.tol : 1e-28 * (double)n;
+    const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 10;
+    sr_norms nr{};
+    nr.stril_rel = nr.orth = nr.w_norm = NAN;
+    const DdMat A = dd_caller(dA, lda, n), Qcaller = dd_caller(dQ, ldq, n);
+    const DdMat That = dT ? dd_caller(dT, n, n) : DdMat{nullptr, nullptr, n};
+    SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
+    SR_TRY(sumsq<double>(h, n, A.hi, lda, 0, 3));
+    if constexpr (OZ) SR_TRY(oz_split_dd(h, sr::OZS_ROWS, n, A, sr::OZ_ROWS));
+    DdMat Qc = Qcaller, Qo = dd_work(h, h->Qw);
+    double y_last = NAN;
+    if (dQhat) {
+        // Alg. 4: Qhat (FP64) to double-double, then Q <- Q - 1/2 Q (Q^T Q - I) (eq. NS)
+        {
+            dim3 grid((n + 255) / 256, n);
+            SrPhase ph(h, SR_PROF_OTHER, 0, 24LL * n * n, 1);
+            sr::to_dd_kernel<<<grid, 256, 0, h->st>>>(n, (const double *)dQhat, ldq, Qc.hi, Qc.lo, Qc.ld);
+            SR_CUDA_TRY(cudaGetLastError());
+        }
+        if constexpr (OZ) SR_TRY(oz_split_dd(h, sr::OZS_COLS, n, Qc, sr::OZ_COLS));
+        SR_TRY(dd_gram<OZ>(h, n, Qc));
+        SR_TRY(dd_apply<OZ>(h, n, Qc, dd_work(h, h->Y), Qo, -0.5));
+        std::swap(Qc, Qo);
+        nr.hp_gemms += 2;
+        SR_TRY(read_back(h));
+        y_last = sqrt(h->hbuf[1]);
+        nr.orth = y_last;
+    }
+    const double anorm = sqrt(h->hbuf[3] > 0 ? h->hbuf[3] : 1.0);
+    sr_status status = SR_ERR_NOT_CONVERGED;
+    double prev = INFINITY;
+    for (int k = 1; k <= max_iter; ++k) {
+        SR_TRY(dd_form_residual<OZ>(h, n, A, Qc, That));
+        nr.hp_gemms += 2;
+        nr.iters = k;
+        SR_TRY(read_back(h));
+        if (timed_out(h)) { status = SR_ERR_TIMEOUT; break; }
+        const double rT = sqrt(h->hbuf[0]) / anorm;
+        nr.stril_rel = rT;
+        if (!isfinite(rT)) { status = SR_ERR_NONFINITE; break; }
+        const bool ok_y = !(y_last > sqrt(tol));
+        if (rT <= tol && ok_y) { status = SR_OK; break; }
+        if (k >= 3 && rT > 10.0 * prev) { status = SR_ERR_NOT_CONVERGED; break; }
+        prev = rT;
+        SR_TRY(solve<double>(h, n, (double *)h->TE, ld, h->diag, h->diag_lo));
+        SR_TRY(sumsq<double>(h, n, (const double *)h->TE, ld, 1, 2));
+        SR_TRY(read_back(h));
+        const int f = host_flags(h);
+        if (f & SR_FLAG_NONDISTINCT) { status = SR_ERR_NONDISTINCT; break; }
+        if (f & SR_FLAG_NONFINITE) { status = SR_ERR_NONFINITE; break; }
+        nr.w_norm = sqrt(2.0 * h->hbuf[2]);
+        SR_TRY(dd_update<OZ>(h, n, Qc, Qo));
+        nr.hp_gemms += 2;
+        std::swap(Qc, Qo);
+        SR_TRY(read_back(h));
+        y_last = sqrt(h->hbuf[1]);
+        nr.orth = y_last;
+        status = SR_ERR_NOT_CONVERGED;
+    }
+    SR_TRY(copy_dd(h, n, Qc, Qcaller));
+    SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+    harvest(h);
+    if (out) *out = nr;
+    return status;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -716,14 +977,24 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->sev0, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->sev1, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(h->dnorm, 0, 8 * sizeof(double));
+    const bool dd = o.target == SR_TARGET_DD;
+    if (e == cudaSuccess) h->diag_lo = dd ? h->diag + n_max : nullptr;
+    if (e == cudaSuccess && dd) e = cudaMalloc((void **)&h->Wd, nn * sizeof(double));
     if (e == cudaSuccess && o.hp_gemm == SR_HP_OZAKI_BF16) {
-        if (n_max > sr::ozaki_k_limit(is_cplx(o))) {
+        // the double-double product keeps 14 levels below 2^31: K up to 8192
+        if (n_max > (dd ? 8192 : sr::ozaki_k_limit(is_cplx(o)))) {
             schur_refine_destroy(h);
             return SR_ERR_UNSUPPORTED;
         }
-        const int shp = o.ozaki_slices > 0 ? o.ozaki_slices : sr::kOzakiDefaultSlices;
+        const int shp = o.ozaki_slices > 0 ? o.ozaki_slices
+                                           : (dd ? sr::kOzakiDefaultSlicesDD : sr::kOzakiDefaultSlices);
         const bool lp_oz = o.lp == SR_LP_FP32;
         int caps[sr::kOzakiSlots] = {shp, shp, shp, shp, 0, 0, 0, 0};
+        if (dd) {
+            // FP64-class digits of W, Y, W^2 (and W^2 Y) for the FP64 products YW, W^2, W^3
+            caps[sr::OZS_W] = caps[sr::OZS_Y] = caps[sr::OZS_W2] = sr::kOzakiDefaultSlices;
+            if (o.full_sigma) caps[7] = sr::kOzakiDefaultSlices;
+        }
         if (lp_oz) {
             caps[sr::OZS_W] = caps[sr::OZS_Y] = caps[sr::OZS_W2] = sr::kOzakiLpSlices;
             if (o.full_sigma) caps[7] = sr::kOzakiLpSlices;
@@ -749,6 +1020,10 @@ sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, vo
                             void *dT, sr_norms *out)
 {
     if (!h || !dA || !dQ || n < 1 || n > h->nmax || lda < n || ldq < n) return SR_ERR_INVALID_ARG;
+    if (is_dd(h->opt)) {
+        if (h->opt.hp_gemm == SR_HP_OZAKI_BF16) return run_step_dd<true>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
+        return run_step_dd<false>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
+    }
     if (is_cplx(h->opt)) return run_step<float, true>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
     if (h->opt.lp == SR_LP_FP32) return run_step<float, false>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
     return run_step<double, false>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
@@ -845,7 +1120,21 @@ sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int ld
     const size_t tiles = (size_t)((n + 15) / 16) * (size_t)((n + 15) / 16);
     if (tiles > h->npartial) return SR_ERR_INVALID_ARG;
     dim3 grid((n + 15) / 16, (n + 15) / 16);
-    if (is_cplx(h->opt)) {
+    if (is_dd(h->opt)) {
+        const DdMat A = dd_caller(dA, lda, n), Q = dd_caller(dQ, ldq, n), M = dd_work(h, h->AQ);
+        sr::gemm_ddq_kernel<0><<<grid, 256, 0, h->st>>>(n, 0, A.hi, A.lo, lda, Q.hi, Q.lo, ldq, M.hi, M.lo, ld,
+                                                        nullptr);
+        SR_CUDA_TRY(cudaGetLastError());
+        sr::gemm_ddq_kernel<1><<<grid, 256, 0, h->st>>>(n, 1, Q.hi, Q.lo, ldq, M.hi, M.lo, ld, nullptr, nullptr, 0,
+                                                        h->partial);
+        SR_CUDA_TRY(cudaGetLastError());
+        SR_TRY(reduce_to(h, (int)tiles, 4));
+        sr::gemm_ddq_kernel<2><<<grid, 256, 0, h->st>>>(n, 1, Q.hi, Q.lo, ldq, Q.hi, Q.lo, ldq, nullptr, nullptr, 0,
+                                                        h->partial);
+        SR_CUDA_TRY(cudaGetLastError());
+        SR_TRY(reduce_to(h, (int)tiles, 5));
+        SR_TRY(sumsq<double>(h, n, A.hi, lda, 0, 6));
+    } else if (is_cplx(h->opt)) {
         const cd *A = (const cd *)dA, *Q = (const cd *)dQ;
         cd *Mhi = (cd *)h->AQ, *Mlo = (cd *)h->Delta;
         sr::gemm_dd_c_kernel<0><<<grid, 256, 0, h->st>>>(n, 0, A, lda, Q, nullptr, ldq, Mhi, Mlo, ld, nullptr);
@@ -885,7 +1174,9 @@ sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, cons
 {
     if (!h || !dTE || !dDiag || n < 1 || n > h->nmax || ld < n) return SR_ERR_INVALID_ARG;
     SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
-    if (is_cplx(h->opt))
+    if (is_dd(h->opt))
+        SR_TRY(solve<double>(h, n, (double *)dTE, ld, (const double *)dDiag, (const double *)dDiag + n));
+    else if (is_cplx(h->opt))
         SR_TRY(solve<cf>(h, n, (cf *)dTE, ld, (const cd *)dDiag));
     else if (h->opt.lp == SR_LP_FP32)
         SR_TRY(solve<float>(h, n, (float *)dTE, ld, (const double *)dDiag));
@@ -905,7 +1196,21 @@ sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, c
     if (m > h->nmax || n > h->nmax || k > h->nmax) return SR_ERR_INVALID_ARG;
     if (lda < (transA ? k : m) || ldb < k || ldc < m) return SR_ERR_INVALID_ARG;
     SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
-    if (is_cplx(h->opt))
+    if (is_dd(h->opt)) {
+        const DdMat A = dd_caller(dA, lda, transA ? m : k), B = dd_caller(dB, ldb, n), C = dd_caller(dC, ldc, n);
+        const sr::EpStoreDD ep{C.hi, C.lo, C.ld};
+        if (h->opt.hp_gemm == SR_HP_OZAKI_BF16) {
+            const int s = oz_s_dd(h);
+            SR_TRY(sr::ozaki_split_dd(h, h->st, h->oz, sr::OZS_ROWS, m, k, A.hi, A.lo, lda,
+                                      transA ? sr::OZ_COLS : sr::OZ_ROWS, s));
+            SR_TRY(sr::ozaki_split_dd(h, h->st, h->oz, sr::OZS_COLS, n, k, B.hi, B.lo, ldb, sr::OZ_COLS, s));
+            SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, m, n, k, s, false, h->dflags));
+            SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, m, n, s, 1.0, false, ep, nullptr,
+                                     nullptr));
+        } else {
+            SR_TRY(ddk_gemm(h, transA != 0, m, n, k, A, B, ep, -1));
+        }
+    } else if (is_cplx(h->opt))
         SR_TRY(sr::ozaki_gemm(h, h->st, h->oz, transA != 0, m, n, k, dA, lda, dB, ldb, sr::EpStoreC{(cd *)dC, ldc},
                               nullptr, nullptr, h->opt.ozaki_slices, h->dflags));
     else

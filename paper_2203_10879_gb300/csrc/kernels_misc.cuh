@@ -227,37 +227,6 @@ static __global__ void __launch_bounds__(256) reduce_partials_kernel(const doubl
 
 // ---- double-double residual products -------------------------------------------
 
-struct ddv { double hi, lo; };
-
-__device__ inline ddv dd_two_sum(double a, double b)
-{
-    const double s = a + b;
-    const double z = s - a;
-    return {s, (a - (s - z)) + (b - z)};
-}
-__device__ inline ddv dd_renorm(double a, double b)
-{
-    const double s = a + b;
-    return {s, b - (s - a)};
-}
-__device__ inline ddv dd_plus(ddv a, ddv b)
-{
-    ddv s = dd_two_sum(a.hi, b.hi);
-    const ddv t = dd_two_sum(a.lo, b.lo);
-    s.lo += t.hi;
-    s = dd_renorm(s.hi, s.lo);
-    s.lo += t.lo;
-    return dd_renorm(s.hi, s.lo);
-}
-// exact product a*b as hi + lo, plus a*c folded into the low part
-__device__ inline ddv dd_times(double a, double b, double c)
-{
-    const double p = a * b;
-    double e = fma(a, b, -p);
-    e = fma(a, c, e);
-    return {p, e};
-}
-
 // C = op(A) * (Bhi + Blo) in double-double, 16 x 16 tiles, one entry per thread.
 // mode 0: store C (hi, lo).  mode 1: partial += sum over i > j of (hi + lo)^2.
 // mode 2: partial += sum over all (i, j) of (C - I)^2 (upper tiles only,

@@ -522,6 +522,69 @@ ozaki_digits_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, int
     }
 }
 
+// Double-double input: the fixed-point value of hi + lo with F = 7 + 8(s-1)
+// fraction bits is formed exactly in a signed 128-bit integer (each part
+// rounded to the nearest unit; |hi| < 2^e bounds both), then cut into s
+// digits like the FP64 split. The exponent comes from the largest |hi| of the
+// vector: |hi + lo| < 2^e as well, since |lo| is at most half an ulp of hi.
+__device__ __forceinline__ __int128 dd_fixed_part(double x, int F, int e)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int eb = (int)((bits >> 52) & 0x7ff);
+    unsigned long long mant = bits & 0xfffffffffffffull;
+    int ex;
+    if (eb == 0) ex = -1074; else { mant |= 1ull << 52; ex = eb - 1075; }
+    const int sh = ex + F - e;                     // x * 2^(F-e) = mant * 2^sh, sh <= F - 53
+    __int128 mag;
+    if (mant == 0) mag = 0;
+    else if (sh >= 0) mag = (__int128)mant << sh;
+    else if (-sh >= 64) mag = 0;
+    else mag = (__int128)((mant + (1ull << (-sh - 1))) >> (-sh));
+    return (bits >> 63) ? -mag : mag;
+}
+
+template <int LAYOUT>
+__global__ void __launch_bounds__(256)
+ozaki_digits_dd_kernel(int R, int K, int Kp, const double *__restrict__ Xh, const double *__restrict__ Xl, int ld,
+                       int s, int Pmax, int Kmax, const unsigned long long *__restrict__ vmax,
+                       __nv_bfloat16 *__restrict__ out, int *__restrict__ exps)
+{
+    __shared__ double th[32][33], tl[32][33];
+    __shared__ int sexp[32];
+    const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * DIGIT_KT;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (threadIdx.x < 32) {
+        const int r = r0 + threadIdx.x;
+        const int e = (r < R) ? split_exponent(vmax[r]) : 0;
+        sexp[threadIdx.x] = e;
+        if (blockIdx.y == 0) exps[r] = e;
+    }
+    const int F = 7 + 8 * (s - 1);
+    const size_t pstride = (size_t)Pmax * Kmax;
+    for (int k0 = kbeg; k0 < kbeg + DIGIT_KT && k0 < Kp; k0 += 32) {
+        __syncthreads();
+        split_load_tile<double, LAYOUT>(th, Xh, ld, R, K, INT_MAX, r0, k0);
+        split_load_tile<double, LAYOUT>(tl, Xl, ld, R, K, INT_MAX, r0, k0);
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int v = ty + 8 * w;
+            const int r = r0 + v;
+            const int kk = k0 + tx;
+            const int e = sexp[v];
+            __int128 Xi = 0;
+            if (e != kOzakiExpNonfinite && r < R) Xi = dd_fixed_part(th[v][tx], F, e) + dd_fixed_part(tl[v][tx], F, e);
+            __nv_bfloat16 *o = out + (size_t)r * Kmax + (size_t)kk;
+            for (int p = s - 1; p >= 1; --p) {
+                const int dg = (int)((long long)((Xi + 128) & (__int128)255)) - 128;
+                Xi = (Xi - dg) >> 8;
+                o[(size_t)p * pstride] = __int2bfloat16_rn(dg);
+            }
+            o[0] = __int2bfloat16_rn((int)(long long)Xi);
+        }
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 cudaError_t encode_digits_map(void *map, void *base, int rows, int Kmax, int box_rows)
@@ -552,8 +615,10 @@ cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx)
     w.cplx = cplx;
     w.Pmax = (nmax + kOzakiTileI - 1) / kOzakiTileI * kOzakiTileI;
     w.Kmax = (nmax + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk * (cplx ? 2 : 1);
+    w.levels = kOzakiMaxSlices;
+    for (int i = 0; i < kOzakiSlots; ++i) w.levels = std::max(w.levels, caps[i]);
     cudaError_t e = cudaMalloc((void **)&w.planes,
-                               (size_t)kOzakiMaxSlices * (cplx ? 2 : 1) * w.Pmax * w.Pmax * sizeof(int32_t));
+                               (size_t)w.levels * (cplx ? 2 : 1) * w.Pmax * w.Pmax * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&w.vmax, (size_t)w.Pmax * sizeof(unsigned long long));
     for (int i = 0; i < kOzakiSlots && e == cudaSuccess; ++i) {
         OzakiSlot &sl = w.slot[i];
@@ -620,13 +685,43 @@ sr_status ozaki_split(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int sl
     return SR_OK;
 }
 
+sr_status ozaki_split_dd(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K,
+                         const double *Xhi, const double *Xlo, int ld, int layout, int s)
+{
+    if (w.cplx || slot < 0 || slot >= kOzakiSlots || s < 1 || s > w.slot[slot].cap || s > kOzakiMaxSlicesDD ||
+        R > w.Pmax || K > ozaki_k_limit(false) || K > w.nmax)
+        return SR_ERR_INVALID_ARG;
+    const int Kp = (K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const int Rp = (R + 31) / 32 * 32;
+    SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, 2LL * R * K * 16 + 2LL * s * Kp * Rp, 2);
+    w.slot[slot].layout = layout;
+    __nv_bfloat16 *out = (__nv_bfloat16 *)w.slot[slot].dig;
+    int *ex = w.slot[slot].exps;
+    SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)Rp * sizeof(unsigned long long), st));
+    const dim3 gmax(Rp / 32, (K + SPLIT_KT - 1) / SPLIT_KT);
+    const dim3 gdig(Rp / 32, (Kp + DIGIT_KT - 1) / DIGIT_KT);
+    if (layout == OZ_COLS) {
+        ozaki_absmax_kernel<double, OZ_COLS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, Xhi, ld, w.vmax);
+        ozaki_digits_dd_kernel<OZ_COLS><<<gdig, 256, 0, st>>>(R, K, Kp, Xhi, Xlo, ld, s, w.Pmax, w.Kmax, w.vmax,
+                                                              out, ex);
+    } else {
+        ozaki_absmax_kernel<double, OZ_ROWS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, Xhi, ld, w.vmax);
+        ozaki_digits_dd_kernel<OZ_ROWS><<<gdig, 256, 0, st>>>(R, K, Kp, Xhi, Xlo, ld, s, w.Pmax, w.Kmax, w.vmax,
+                                                              out, ex);
+    }
+    SR_CUDA_TRY(cudaGetLastError());
+    return SR_OK;
+}
+
 sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n, int k,
                         int s, bool symmetric, int *flags)
 {
     if (k > ozaki_k_limit(w.cplx)) return SR_ERR_UNSUPPORTED;
-    if (s < 1 || s > w.slot[rows].cap || s > w.slot[cols].cap || s > kOzakiMaxSlices) return SR_ERR_INVALID_ARG;
+    if (s < 1 || s > w.slot[rows].cap || s > w.slot[cols].cap || s > w.levels) return SR_ERR_INVALID_ARG;
     const int Kc = (k + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
     const int Kp = w.cplx ? 2 * Kc : Kc;
+    // level l sums (l + 1) * chunks exact chunk results below 2^22: keep it below 2^31
+    if ((long long)s * (Kp / kOzakiKChunk) * (1LL << 22) >= (1LL << 31)) return SR_ERR_UNSUPPORTED;
     const int Mp = (m + BN - 1) / BN * BN;
     const int Np = (n + BM - 1) / BM * BM;
     const long long pairs = (long long)s * (s + 1) / 2;
@@ -654,7 +749,9 @@ sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
     a.pstride = (size_t)parts * w.Pmax * w.Pmax;
     a.flags = flags;
     int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = (int)std::min<long long>(active, sms > 0 ? sms : 1);
     // MMA "A" (TMEM lanes) = column-side digits, MMA "B" = row-side digits
     ozaki_mma_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.slot[rows].map_i,

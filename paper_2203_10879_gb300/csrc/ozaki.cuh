@@ -45,6 +45,9 @@ namespace sr {
 
 constexpr int kOzakiMaxSlices = 7;   // 7 + 8*6 = 55 fraction bits fit a 64-bit integer
 constexpr int kOzakiDefaultSlices = 7;
+// double-double operands: 7 + 8*13 = 111 fraction bits in a 128-bit integer
+constexpr int kOzakiMaxSlicesDD = 14;
+constexpr int kOzakiDefaultSlicesDD = 14;
 constexpr int kOzakiLpSlices = 3;    // 23 fraction bits: the FP32-class products YW, W^2, W^3
 constexpr bool kOzakiBuilt = true;
 constexpr int kOzakiTileI = 256;      // rows of C per slice-product tile (MMA N)
@@ -70,7 +73,8 @@ struct OzakiWork {
     int nmax = 0, Pmax = 0, Kmax = 0;
     bool cplx = false;                     // complex128 operands, stacked [re; im] digit vectors
     OzakiSlot slot[kOzakiSlots];
-    int32_t *planes = nullptr;             // [kOzakiMaxSlices][Pmax (2 Pmax if cplx) cols][Pmax rows]
+    int levels = 0;                        // level planes held (the largest slot capacity, at least 7)
+    int32_t *planes = nullptr;             // [levels][Pmax (2 Pmax if cplx) cols][Pmax rows]
     unsigned long long *vmax = nullptr;    // per-vector largest |x| (bit pattern) during a split
 };
 
@@ -86,6 +90,12 @@ inline int ozaki_k_limit(bool cplx) { return cplx ? kOzakiMaxK / 2 : kOzakiMaxK;
 // digits in `slot`.
 sr_status ozaki_split(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K, const void *X,
                       int ld, int layout, int s);
+
+// The same for double-double vectors X = Xhi + Xlo (real): the fixed-point
+// value of each entry is formed exactly in a 128-bit integer before the cut,
+// so up to kOzakiMaxSlicesDD digits carry the low part.
+sr_status ozaki_split_dd(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K,
+                         const double *Xhi, const double *Xlo, int ld, int layout, int s);
 
 // Level planes of the product of the vectors in slot `rows` (output rows i)
 // with those in slot `cols` (output columns j), inner length k. With
@@ -169,26 +179,98 @@ ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, in
 
 inline int ozaki_blocks(int m, int n) { return ((m + 31) / 32) * ((n + 31) / 32); }
 
+// int64 -> double-double, exact for |G| < 2^63 (the remainder after rounding
+// to 53 bits is an integer below 2^11)
+__device__ __forceinline__ ddv oz_i64_to_dd(long long G)
+{
+    const double hi = (double)G;
+    return {hi, (double)(G - (long long)hi)};
+}
+
+// One rebuilt entry in double-double: sign * 2^e * sum_l I_l 2^(-14-8l). The
+// levels are taken four at a time in exact 64-bit Horner sums (each below
+// 2^55 in magnitude for level sums below 2^31), every group converted exactly
+// to double-double and the groups added from the least significant one.
+__device__ __forceinline__ ddv oz_rebuild_dd(const int32_t *__restrict__ planes, size_t off, size_t pstride, int s,
+                                             double sign, int e)
+{
+    ddv acc = {0.0, 0.0};
+    const int ng = (s + 3) / 4;
+    for (int g = ng - 1; g >= 0; --g) {
+        const int l0 = 4 * g, l1 = min(s, l0 + 4) - 1;
+        long long G = 0;
+        for (int l = l0; l <= l1; ++l) G = G * 256 + (long long)planes[off + (size_t)l * pstride];
+        const double sc = sign * __longlong_as_double((long long)(1023 - 14 - 8 * l1) << 52);
+        const ddv t = oz_i64_to_dd(G);
+        acc = dd_plus(acc, ddv{t.hi * sc, t.lo * sc});
+    }
+    return {oz_scale(acc.hi, e), oz_scale(acc.lo, e)};
+}
+
+template <class EP>
+__global__ void __launch_bounds__(256)
+ozaki_combine_dd_kernel(int m, int n, int s, const int32_t *__restrict__ planes, int ldp, size_t pstride,
+                        const int *__restrict__ ea, const int *__restrict__ fb, double sign, int mirror, EP ep,
+                        double *partial)
+{
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int jb = blockIdx.y * 32 + (threadIdx.x >> 5);
+    double part = 0.0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int j = jb + 8 * w;
+        if (i < m && j < n) {
+            const bool mir = mirror && i > j;
+            const size_t off = mir ? (size_t)j + (size_t)i * (size_t)ldp : (size_t)i + (size_t)j * (size_t)ldp;
+            const int e1 = ea[i], e2 = fb[j];
+            const double nan = __longlong_as_double(0x7ff8000000000000LL);
+            const bool bad = e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite;
+            const ddv v = bad ? ddv{nan, nan} : oz_rebuild_dd(planes, off, pstride, s, sign, e1 + e2);
+            part += ep(i, j, v);
+        }
+    }
+    if (partial) {
+        part = sr_block_sum<256>(part);
+        if (threadIdx.x == 0) partial[blockIdx.x + (size_t)gridDim.x * blockIdx.y] = part;
+    }
+}
+
 // epilogues of complex products carry `static constexpr bool kComplex`
 template <class EP, class = void> struct ep_is_complex : std::false_type {};
 template <class EP> struct ep_is_complex<EP, std::void_t<decltype(EP::kComplex)>> : std::true_type {};
+
+// epilogues that take a double-double value carry `static constexpr bool kDD`
+template <class EP, class = void> struct ep_is_dd : std::false_type {};
+template <class EP> struct ep_is_dd<EP, std::void_t<decltype(EP::kDD)>> : std::true_type {};
 
 template <class EP>
 sr_status ozaki_combine(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n, int s,
                         double sign, bool mirror, EP ep, double *partial, int *blocks)
 {
-    constexpr bool CPLX = ep_is_complex<EP>::value;
-    if (CPLX != w.cplx) return SR_ERR_INVALID_ARG;
-    const int c = CPLX ? 2 : 1;
-    SrPhase ph(h, SR_PROF_OZ_COMBINE, 8LL * c * s * m * n, (long long)m * n * (4LL * c * s + 16 * c), 1);
-    dim3 grid((m + 31) / 32, (n + 31) / 32);
-    const size_t pstride = (size_t)c * w.Pmax * w.Pmax, imoff = (size_t)w.Pmax * w.Pmax;
-    ozaki_combine_kernel<EP, CPLX><<<grid, 256, 0, st>>>(m, n, s, w.planes, w.Pmax, pstride, imoff,
-                                                         w.slot[rows].exps, w.slot[cols].exps, sign, mirror ? 1 : 0,
-                                                         ep, partial);
-    SR_CUDA_TRY(cudaGetLastError());
-    if (blocks) *blocks = ozaki_blocks(m, n);
-    return SR_OK;
+    if constexpr (ep_is_dd<EP>::value) {
+        if (w.cplx || s > w.levels) return SR_ERR_INVALID_ARG;
+        SrPhase ph(h, SR_PROF_OZ_COMBINE, 24LL * s * m * n, (long long)m * n * (4LL * s + 32), 1);
+        dim3 grid((m + 31) / 32, (n + 31) / 32);
+        const size_t pstride = (size_t)w.Pmax * w.Pmax;
+        ozaki_combine_dd_kernel<EP><<<grid, 256, 0, st>>>(m, n, s, w.planes, w.Pmax, pstride, w.slot[rows].exps,
+                                                          w.slot[cols].exps, sign, mirror ? 1 : 0, ep, partial);
+        SR_CUDA_TRY(cudaGetLastError());
+        if (blocks) *blocks = ozaki_blocks(m, n);
+        return SR_OK;
+    } else {
+        constexpr bool CPLX = ep_is_complex<EP>::value;
+        if (CPLX != w.cplx) return SR_ERR_INVALID_ARG;
+        const int c = CPLX ? 2 : 1;
+        SrPhase ph(h, SR_PROF_OZ_COMBINE, 8LL * c * s * m * n, (long long)m * n * (4LL * c * s + 16 * c), 1);
+        dim3 grid((m + 31) / 32, (n + 31) / 32);
+        const size_t pstride = (size_t)c * w.Pmax * w.Pmax, imoff = (size_t)w.Pmax * w.Pmax;
+        ozaki_combine_kernel<EP, CPLX><<<grid, 256, 0, st>>>(m, n, s, w.planes, w.Pmax, pstride, imoff,
+                                                             w.slot[rows].exps, w.slot[cols].exps, sign, mirror ? 1 : 0,
+                                                             ep, partial);
+        SR_CUDA_TRY(cudaGetLastError());
+        if (blocks) *blocks = ozaki_blocks(m, n);
+        return SR_OK;
+    }
 }
 
 // slots used by the engine

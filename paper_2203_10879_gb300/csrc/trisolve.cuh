@@ -44,6 +44,17 @@ __device__ inline T sr_div_round(typename SrNum<T>::hp di, typename SrNum<T>::hp
     return SrNum<T>::from_hp(di - dj);
 }
 
+// t_ii - t_jj from a double-double diagonal (hi, lo): TwoSum of the high
+// parts, the low parts added, rounded once to FP64
+__device__ inline double sr_div_round_dd(double hi_i, double lo_i, double hi_j, double lo_j)
+{
+    const double s = hi_i - hi_j;
+    const double z = s - hi_i;
+    double e = (hi_i - (s - z)) + (-hi_j - z);
+    e += lo_i - lo_j;
+    return s + e;
+}
+
 // Launch plan: for step t, the tiles (I << 16 | J) of subdiagonal t (solved)
 // followed by the tiles with D < t that receive a product of subdiagonal t+1.
 void trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long long> &offsets);
@@ -168,8 +179,8 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
 // 1024 threads; thread (lane a, warp b) owns entry (a, b) of the tile.
 template <typename T>
 __global__ void __launch_bounds__(1024)
-trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>::hp *__restrict__ dhp, int t,
-                     const uint32_t *__restrict__ plan, int *__restrict__ flags)
+trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>::hp *__restrict__ dhp,
+                     const double *__restrict__ dlo, int t, const uint32_t *__restrict__ plan, int *__restrict__ flags)
 {
     using Hp = typename SrNum<T>::hp;
     constexpr int B = kSolveTile, S = B + 1;
@@ -189,6 +200,7 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
     T (*Ti)[S] = sm[1];
     T (*Tj)[S] = sm[2];
     __shared__ Hp dI[B], dJ[B];
+    __shared__ double dIl[B], dJl[B];   // low parts of a double-double diagonal (dlo given)
     const int a = threadIdx.x & 31, b = threadIdx.x >> 5;
     const bool own = a < nr && b < nc && (D > 0 || a > b);
 
@@ -201,8 +213,13 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
     Tb[1][a][b] = (hasM && kM + a < n && c0 + b < n) ? TE[sr_idx(kM + a, c0 + b, ld)] : Z;
     T acc = own ? TE[sr_idx(r0 + a, c0 + b, ld)] : Z;
     const Hp hz = SrNum<Hp>::zero();
-    if (threadIdx.x < B) dI[threadIdx.x] = (threadIdx.x < nr) ? dhp[r0 + threadIdx.x] : hz;
-    else if (threadIdx.x < 2 * B) dJ[threadIdx.x - B] = (threadIdx.x - B < nc) ? dhp[c0 + threadIdx.x - B] : hz;
+    if (threadIdx.x < B) {
+        dI[threadIdx.x] = (threadIdx.x < nr) ? dhp[r0 + threadIdx.x] : hz;
+        dIl[threadIdx.x] = (dlo && threadIdx.x < nr) ? dlo[r0 + threadIdx.x] : 0.0;
+    } else if (threadIdx.x < 2 * B) {
+        dJ[threadIdx.x - B] = (threadIdx.x - B < nc) ? dhp[c0 + threadIdx.x - B] : hz;
+        dJl[threadIdx.x - B] = (dlo && threadIdx.x - B < nc) ? dlo[c0 + threadIdx.x - B] : 0.0;
+    }
     __syncthreads();
     if (hasP || hasM) {
 #pragma unroll 8
@@ -213,7 +230,10 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
     }
     // divisor t_aa - t_bb formed in FP64 and rounded; its reciprocal (one IEEE
     // division, off the wavefront's critical path) turns each solve into a product
-    const T den = own ? sr_div_round<T>(dI[a], dJ[b]) : Z;
+    T den = own ? sr_div_round<T>(dI[a], dJ[b]) : Z;
+    if constexpr (SrNum<T>::kind == 1) {
+        if (own && dlo) den = sr_div_round_dd(dI[a], dIl[a], dJ[b], dJl[b]);
+    }
     const T rcp = (own && !(den == Z)) ? sr_recip(den) : Z;
     __syncthreads();
 
@@ -255,8 +275,8 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
 // plan: device copy of trisolve_plan's tiles; offsets: its host offsets.
 template <typename T>
 inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEvent_t ev0, cudaEvent_t ev1, int n,
-                                     T *TE, int ld, const typename SrNum<T>::hp *dhp, int *flags,
-                                     const uint32_t *plan, const std::vector<long long> &offsets)
+                                     T *TE, int ld, const typename SrNum<T>::hp *dhp, const double *dlo,
+                                     int *flags, const uint32_t *plan, const std::vector<long long> &offsets)
 {
     const int NB = (n + kSolveTile - 1) / kSolveTile;
     cudaError_t e = cudaEventRecord(ev0, st);
@@ -265,7 +285,7 @@ inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEven
         const int l = NB - 1 - t;
         const long long nleaf = NB - t;
         const long long nupd = offsets[l + 1] - offsets[l] - nleaf;
-        trisolve_leaf_kernel<T><<<(unsigned)nleaf, 1024, 0, st>>>(n, TE, ld, dhp, t, plan + offsets[l], flags);
+        trisolve_leaf_kernel<T><<<(unsigned)nleaf, 1024, 0, st>>>(n, TE, ld, dhp, dlo, t, plan + offsets[l], flags);
         if (nupd > 0)
             trisolve_update_kernel<T><<<(unsigned)nupd, 128, 0, aux>>>(n, TE, ld, t, plan + offsets[l] + nleaf);
         e = cudaGetLastError();
