@@ -38,9 +38,9 @@ METRIC = "sec to FP64-accurate Schur refinement, mixed vs all-FP64 GPU; % FP64/t
 FP64_NOMINAL_TFLOPS = 1.25        # GB300 FP64 (vector and tensor), nominal
 BF16_NOMINAL_TFLOPS = 2250.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one captured launch of the dominant
-# kernel (profiles/ozaki_mma_kernel_n4096.md: the 28-pair T^ product at n = 4096);
-# valid for that kernel version and size only
-OZ_MMA_TRAFFIC_BYTES_N4096 = 4.521404e9 + 0.468546e9
+# kernel (the 28-pair T^ product at n = 4096); valid for that kernel version and size
+# only, None until the current version has been captured
+OZ_MMA_TRAFFIC_BYTES_N4096 = None
 
 
 def _peaks():

@@ -68,14 +68,15 @@ struct EpMinusIDD {
 };
 
 // Q_new = Q + alpha * (product) in double-double; alpha = 1/2 (update with
-// Q Delta) or -1/2 (Newton-Schulz step with Q Y0), a power of two.
+// Q Delta) or -1/2 (Newton-Schulz step with Q Y0), a power of two. The
+// correction is small against Q, so the low parts are added in FP64 (dd_acc).
 struct EpUpdateDD {
     static constexpr bool kDD = true;
     const double *qhi, *qlo; int ldq; double *nhi, *nlo; int ldn; double alpha;
     __device__ double operator()(int i, int j, ddv v) const
     {
         const size_t p = sr_idx(i, j, ldq);
-        const ddv r = dd_plus(ddv{qhi[p], qlo[p]}, ddv{alpha * v.hi, alpha * v.lo});
+        const ddv r = dd_acc(ddv{qhi[p], qlo[p]}, ddv{alpha * v.hi, alpha * v.lo});
         const size_t q = sr_idx(i, j, ldn);
         nhi[q] = r.hi;
         nlo[q] = r.lo;

@@ -178,17 +178,38 @@ struct MmaArgs {
     int32_t *planes;  // [s][pstride]
     size_t pstride;   // Pmax * Pmax (2 Pmax * Pmax when complex)
     int *flags;
+    // work items: (active tile, level group); group g holds levels
+    // [lvl[g], lvl[g+1]). Item x is group x / nact of active tile x % nact.
+    int nact;         // tiles formed (all, or those on and above the diagonal)
+    int groups;
+    int nitems;       // nact * groups
+    int lvl[kOzakiMaxSlicesDD + 1];
 };
 
-// tile -> (first row i0, first column j0, imaginary part?); false if skipped
-__device__ __forceinline__ bool tile_coords(const MmaArgs &a, int tile, int &i0, int &j0, int &im)
+// number of row tiles formed in column tile bj (of one part)
+__device__ __forceinline__ int active_in_column(const MmaArgs &a, int bj)
 {
-    i0 = (tile % a.tiles_i) * BN;
-    int bj = tile / a.tiles_i;
+    if (!a.symmetric) return a.tiles_i;
+    return min(a.tiles_i, (bj * BM + BM - 1) / BN + 1);
+}
+
+// item -> tile (index as in tile_coords) and its level range
+__device__ __forceinline__ void item_coords(const MmaArgs &a, int item, int &i0, int &j0, int &im, int &lb, int &le)
+{
+    const int g = item / a.nact;
+    int r = item - g * a.nact;
+    lb = a.lvl[g];
+    le = a.lvl[g + 1];
+    int bj = 0;
+    const int cols = a.tiles_j * (a.cplx ? 2 : 1);
+    for (; bj < cols; ++bj) {
+        const int cnt = active_in_column(a, bj % a.tiles_j);
+        if (r < cnt) break;
+        r -= cnt;
+    }
+    i0 = r * BN;
     im = bj >= a.tiles_j;
-    if (im) bj -= a.tiles_j;
-    j0 = bj * BM;
-    return !(a.symmetric && i0 > j0 + BM - 1);
+    j0 = (im ? bj - a.tiles_j : bj) * BM;
 }
 
 // column-side K-chunk read for chunk c: the halves are swapped for an imaginary part
@@ -257,10 +278,10 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             uint32_t phase = 0;
             int issued = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < args.ntiles && ok; tile += gridDim.x) {
-                int i0, j0, im;
-                if (!tile_coords(args, tile, i0, j0, im)) continue;
-                for (int l = 0; l < s && ok; ++l)
+            for (int item = blockIdx.x; item < args.nitems && ok; item += gridDim.x) {
+                int i0, j0, im, lb, le;
+                item_coords(args, item, i0, j0, im, lb, le);
+                for (int l = lb; l < le && ok; ++l)
                     for (int p = 0; p <= l && ok; ++p) {
                         const int q = l - p;
                         for (int c = 0; c < nch && ok; ++c)
@@ -292,10 +313,10 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             uint32_t phase = 0;
             int t = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < args.ntiles && ok; tile += gridDim.x) {
-                int i0, j0, im;
-                if (!tile_coords(args, tile, i0, j0, im)) continue;
-                for (int l = 0; l < s && ok; ++l)
+            for (int item = blockIdx.x; item < args.nitems && ok; item += gridDim.x) {
+                int i0, j0, im, lb, le;
+                item_coords(args, item, i0, j0, im, lb, le);
+                for (int l = lb; l < le && ok; ++l)
                     for (int p = 0; p <= l && ok; ++p)
                         for (int c = 0; c < nch && ok; ++c) {
                             const uint32_t idesc = chunk_idesc(args, c, im);
@@ -333,11 +354,11 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         uint32_t acc[BN / 2];
         int t = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < args.ntiles && ok; tile += gridDim.x) {
-            int i0, j0, im;
-            if (!tile_coords(args, tile, i0, j0, im)) continue;
+        for (int item = blockIdx.x; item < args.nitems && ok; item += gridDim.x) {
+            int i0, j0, im, lb, le;
+            item_coords(args, item, i0, j0, im, lb, le);
             const int j = j0 + lg * 32 + lane + (im ? P : 0);   // plane column
-            for (int l = 0; l < s && ok; ++l) {
+            for (int l = lb; l < le && ok; ++l) {
 #pragma unroll
                 for (int c = 0; c < BN / 2; ++c) acc[c] = 0u;
                 uint32_t count = 0;
@@ -585,6 +606,51 @@ ozaki_digits_dd_kernel(int R, int K, int Kp, const double *__restrict__ Xh, cons
     }
 }
 
+// Splits levels 0..s-1 (level l costs l + 1 digit pairs) into G contiguous
+// non-empty groups minimising the largest group cost (linear partition by
+// dynamic programming); returns that cost.
+int split_levels(int s, int G, int *lvl)
+{
+    constexpr int S = kOzakiMaxSlicesDD + 1;
+    int best[S][S], cut[S][S];   // best[g][l]: levels 0..l-1 in g groups
+    auto cost = [](int a, int b) { return (b * (b + 1) - a * (a + 1)) / 2; };   // levels a..b-1
+    for (int l = 0; l <= s; ++l) best[1][l] = cost(0, l), cut[1][l] = 0;
+    for (int g = 2; g <= G; ++g)
+        for (int l = g; l <= s; ++l) {
+            best[g][l] = -1;
+            for (int k = g - 1; k < l; ++k) {
+                const int v = std::max(best[g - 1][k], cost(k, l));
+                if (best[g][l] < 0 || v < best[g][l]) { best[g][l] = v; cut[g][l] = k; }
+            }
+        }
+    lvl[G] = s;
+    for (int g = G, l = s; g >= 1; --g) {
+        l = cut[g][l];
+        lvl[g - 1] = l;
+    }
+    lvl[0] = 0;
+    return best[G][s];
+}
+
+// Work items per tile: the number of level groups G that minimises the
+// persistent grid's makespan, waves(active * G) * largest group cost; the
+// grid then has fewer idle SMs in its last wave (the groups write disjoint
+// level planes, so no reduction is needed).
+int level_groups(int s, int active, int sms, int *lvl)
+{
+    int best_g = 1;
+    long long best = -1;
+    int tmp[kOzakiMaxSlicesDD + 1];
+    for (int G = 1; G <= std::min(s, 8); ++G) {
+        const int worst = split_levels(s, G, tmp);
+        const long long waves = ((long long)active * G + sms - 1) / sms;
+        const long long est = waves * worst;
+        if (best < 0 || est < best) { best = est; best_g = G; }
+    }
+    split_levels(s, best_g, lvl);
+    return best_g;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 cudaError_t encode_digits_map(void *map, void *base, int rows, int Kmax, int box_rows)
@@ -732,6 +798,10 @@ sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
         for (int bi = 0; bi < tiles_i; ++bi)
             if (!(symmetric && bi * BN > bj * BM + BM - 1)) ++active;
     active *= parts;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
     const long long tile_flops = 2LL * BN * BM * Kp;
     SrPhase ph(h, SR_PROF_OZ_MMA, pairs * active * tile_flops,
                pairs * 2LL * Kp * (Mp + parts * Np) + 4LL * s * active * BN * BM, 1);
@@ -748,11 +818,10 @@ sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
     a.planes = w.planes;
     a.pstride = (size_t)parts * w.Pmax * w.Pmax;
     a.flags = flags;
-    int sms = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)std::min<long long>(active, sms > 0 ? sms : 1);
+    a.nact = (int)active;
+    a.groups = level_groups(s, (int)active, sms, a.lvl);
+    a.nitems = a.nact * a.groups;
+    const int grid = (int)std::min<long long>(a.nitems, sms);
     // MMA "A" (TMEM lanes) = column-side digits, MMA "B" = row-side digits
     ozaki_mma_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.slot[rows].map_i,
                                                             *(const CUtensorMap *)w.slot[cols].map_j, a);

@@ -179,32 +179,73 @@ ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, in
 
 inline int ozaki_blocks(int m, int n) { return ((m + 31) / 32) * ((n + 31) / 32); }
 
-// int64 -> double-double, exact for |G| < 2^63 (the remainder after rounding
-// to 53 bits is an integer below 2^11)
-__device__ __forceinline__ ddv oz_i64_to_dd(long long G)
+// m * 2^x as a double for 2^52 <= m < 2^53 (the leading bit at 52), built
+// from its fields when the result is normal, else by two exact scalings
+__device__ __forceinline__ double oz_make_double(unsigned long long m, int x, bool neg)
 {
-    const double hi = (double)G;
-    return {hi, (double)(G - (long long)hi)};
+    const int E = x + 52 + 1023;
+    if (E >= 1 && E <= 2046) {
+        const unsigned long long b = ((unsigned long long)E << 52) | (m & 0xfffffffffffffull);
+        return __longlong_as_double((long long)(neg ? (b | 0x8000000000000000ull) : b));
+    }
+    const double v = oz_pow2_scale((double)m, x);
+    return neg ? -v : v;
+}
+
+// the leading 53 bits of M > 0 as m * 2^sh (m in [2^52, 2^53); sh may be
+// negative) and the remainder M - m 2^sh (zero when sh <= 0)
+__device__ __forceinline__ unsigned long long oz_top53(unsigned __int128 M, int &sh, unsigned __int128 &rem)
+{
+    const unsigned long long hw = (unsigned long long)(M >> 64), lw = (unsigned long long)M;
+    const int msb = hw ? 127 - __clzll((long long)hw) : 63 - __clzll((long long)lw);
+    sh = msb - 52;
+    if (sh <= 0) {
+        rem = 0;
+        return lw << (-sh);
+    }
+    const unsigned long long m = (unsigned long long)(M >> sh);
+    rem = M - ((unsigned __int128)m << sh);
+    return m;
+}
+
+// V * 2^x as a double-double: the leading 53 bits of |V| (truncated) and the
+// leading 53 bits of the remainder, one renormalisation. Relative error below
+// 2^-105; integer work apart from the final fast TwoSum.
+__device__ __forceinline__ ddv oz_i128_to_dd(__int128 V, int x)
+{
+    if (V == 0) return {0.0, 0.0};
+    const bool neg = V < 0;
+    const unsigned __int128 M = neg ? (unsigned __int128)(-V) : (unsigned __int128)V;
+    int sh, sh2;
+    unsigned __int128 rem, rem2;
+    const unsigned long long m = oz_top53(M, sh, rem);
+    const double hi = oz_make_double(m, sh + x, neg);
+    if (rem == 0) return {hi, 0.0};
+    const unsigned long long m2 = oz_top53(rem, sh2, rem2);
+    return dd_renorm(hi, oz_make_double(m2, sh2 + x, neg));
 }
 
 // One rebuilt entry in double-double: sign * 2^e * sum_l I_l 2^(-14-8l). The
-// levels are taken four at a time in exact 64-bit Horner sums (each below
-// 2^55 in magnitude for level sums below 2^31), every group converted exactly
-// to double-double and the groups added from the least significant one.
+// levels are summed exactly in a 128-bit integer with the last level rounded
+// to whole units of the level before it, V = sum_{l <= s-2} I_l 256^(s-2-l) +
+// round(I_{s-1} / 256), so that |V| < 2^123 for level sums below 2^31 and
+// 14 levels; the entry is V 2^(e - 14 - 8(s-2)).
 __device__ __forceinline__ ddv oz_rebuild_dd(const int32_t *__restrict__ planes, size_t off, size_t pstride, int s,
                                              double sign, int e)
 {
-    ddv acc = {0.0, 0.0};
-    const int ng = (s + 3) / 4;
-    for (int g = ng - 1; g >= 0; --g) {
-        const int l0 = 4 * g, l1 = min(s, l0 + 4) - 1;
-        long long G = 0;
-        for (int l = l0; l <= l1; ++l) G = G * 256 + (long long)planes[off + (size_t)l * pstride];
-        const double sc = sign * __longlong_as_double((long long)(1023 - 14 - 8 * l1) << 52);
-        const ddv t = oz_i64_to_dd(G);
-        acc = dd_plus(acc, ddv{t.hi * sc, t.lo * sc});
+    __int128 V = 0;
+    int x;
+    if (s == 1) {
+        V = planes[off];
+        x = e - 14;
+    } else {
+        for (int l = 0; l <= s - 2; ++l) V = V * 256 + (__int128)planes[off + (size_t)l * pstride];
+        const int last = planes[off + (size_t)(s - 1) * pstride];
+        V += (__int128)((last + 128) >> 8);
+        x = e - 14 - 8 * (s - 2);
     }
-    return {oz_scale(acc.hi, e), oz_scale(acc.lo, e)};
+    if (sign < 0) V = -V;
+    return oz_i128_to_dd(V, x);
 }
 
 template <class EP>
