@@ -38,9 +38,11 @@ METRIC = "sec to FP64-accurate Schur refinement, mixed vs all-FP64 GPU; % FP64/t
 FP64_NOMINAL_TFLOPS = 1.25        # GB300 FP64 (vector and tensor), nominal
 BF16_NOMINAL_TFLOPS = 2250.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one captured launch of the dominant
-# kernel (the 28-pair T^ product at n = 4096); valid for that kernel version and size
-# only, None until the current version has been captured
-OZ_MMA_TRAFFIC_BYTES_N4096 = None
+# kernel (profiles/ozaki_mma_kernel_n4096.md: the 28-pair T^ product at n = 4096; and
+# profiles/ozaki_mma_kernel_dd_n2048.md: the 105-pair A Q product of the double-double
+# workload); valid for that kernel version and size only
+OZ_MMA_TRAFFIC_BYTES_N4096 = 5.787937e9 + 0.4733504e9
+OZ_MMA_TRAFFIC_BYTES_DD2048 = 1.619892e9 + 0.2217213e9
 
 
 def _peaks():
@@ -384,24 +386,31 @@ def run_batched(args):
     nmax = int(max(ns))
     stream = torch.cuda.current_stream()
     out = {}
-    for workers in (args.batch_streams, 1):
-        opt = B.default_options(hp_gemm=B.SR_HP_OZAKI_BF16, lp=B.SR_LP_FP32, batch_streams=workers)
+    # grouped launches (the measured path), the worker pool of streams, one matrix at a time
+    for key, mode, workers in (("grouped", 0, 1), ("streams", 1, args.batch_streams), ("serial", 1, 1)):
+        opt = B.default_options(hp_gemm=B.SR_HP_OZAKI_BF16, lp=B.SR_LP_FP32, batch_streams=workers,
+                                batch_mode=mode, profile=1 if key == "grouped" else 0)
         st, h = B.schur_refine_create(nmax, opt, stream.cuda_stream)
         assert st == 0
         sizes = [p.n for p in probs]
-        for _ in range(args.warmup):
+        for _ in range(args.warmup if key != "serial" else 1):
             B.schur_refine_batched(h, sizes, As, Qs, Qh)
+        B.schur_refine_reset_profile(h)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        steps = args.steps if workers != 1 else 1
+        steps = args.steps if key != "serial" else 1
         e0.record(stream)
         for _ in range(steps):
             st, iters, stats = B.schur_refine_batched(h, sizes, As, Qs, Qh)
         e1.record(stream)
         torch.cuda.synchronize()
-        out[workers] = (e0.elapsed_time(e1) / steps, st, iters, stats)
+        prof = None
+        if key == "grouped":
+            _, pp = B.schur_refine_get_profile(h)
+            prof = pp.as_dict()
+        out[key] = (e0.elapsed_time(e1) / steps, st, iters, stats, prof)
         B.schur_refine_destroy(h)
-    ms, st, iters, stats = out[args.batch_streams]
+    ms, st, iters, stats, prof = out["grouped"]
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], device="cuda")
@@ -414,10 +423,14 @@ def run_batched(args):
                 "data": "synthetic",
                 "config": {"workload": f"{len(ns)} real matrices, n log-uniform in [32,512] (sum n^3 = "
                                        f"{float(np.sum(ns.astype(float) ** 3)):.3g}), unit-step spectra, FP32 Qhat",
-                           "batch_streams": args.batch_streams, "status": st,
-                           "all_ok": all(x == 0 for x in stats), "mean_iters": float(np.mean(iters)),
-                           "one_at_a_time_ms": out[1][0],
-                           "speedup_vs_one_at_a_time": out[1][0] / ms}}
+                           "form": "grouped launches (every stage one launch for all live matrices)",
+                           "status": st, "all_ok": all(x == 0 for x in stats), "mean_iters": float(np.mean(iters)),
+                           "worker_streams_ms": out["streams"][0], "worker_streams": args.batch_streams,
+                           "one_at_a_time_ms": out["serial"][0],
+                           "speedup_vs_one_at_a_time": out["serial"][0] / ms,
+                           "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
+                           "launches_per_step": int(sum(v["launches"] for v in prof.values()) / args.steps)},
+                "gpu_launches": int(sum(v["launches"] for v in prof.values()))}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -537,7 +550,9 @@ def run_dd(args):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "ozaki slice products (tcgen05 kind::f16 bf16), 14 digits",
+                "traffic": OZ_MMA_TRAFFIC_BYTES_DD2048 if (n == 2048 and (args.slices or 14) == 14) else None,
+                "traffic_note": "bytes per launch of the captured 105-pair A Q product (ncu)",
+                "kernel": "ozaki slice products (tcgen05 kind::f16 bf16), 14 digits",
                 "peak_source": "of measured bf16 sustained (MEASURED_PEAKS.json)"}
     else:
         gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9
@@ -584,6 +599,88 @@ def run_dd(args):
     return 0
 
 
+def run_small(args):
+    """The small plain case: the unit-step problem of order 64 (lambda_k = 1 + k/64,
+    FP32 start) refined by the all-FP64 form (native FP64 products, FP64 solve) to
+    ||stril||/||A|| <= 1e-14 sqrt(n); the mixed form with emulated products is timed
+    beside it. Launch- and latency-bound: reported per refinement in microseconds."""
+    import numpy as np
+    import torch
+
+    import paper_2203_10879_gb300 as P
+    from paper_2203_10879_gb300 import _binding as B
+    from paper_2203_10879_gb300 import inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    n = args.n
+    p = inputs.unit_step_real(n)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+    A, Qhat = dev(p.A), dev(p.Qhat)
+    Q = torch.empty((n, n), dtype=torch.float64, device="cuda").t()
+    stream = torch.cuda.current_stream()
+    # L2 is not flushed: at this size every input stays in cache, as in any repeated use
+    res = {}
+    for key, kw in (("all_fp64", dict(hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP64)),
+                    ("mixed_emulated", dict(hp_gemm=B.SR_HP_OZAKI_BF16, lp=B.SR_LP_FP32))):
+        r = P.Refiner(n, profile=1 if key == "all_fp64" else 0, **kw)
+        for _ in range(args.warmup):
+            r.step(A, Q, Qhat, check=False)
+        r.reset_profile()
+        torch.cuda.synchronize()
+        clk = Clocks(local) if key == "all_fp64" else None
+        if clk:
+            clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, nr = r.step(A, Q, Qhat, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c = clk.stop() if clk else None
+        prof = r.profile()
+        rT, rQ = r.residuals(A, Q)
+        res[key] = (e0.elapsed_time(e1) / args.steps, st, nr, rT, rQ, prof, c)
+        r.close()
+    if rank != 0:
+        return 0
+    ms, st, nr, rT, rQ, prof, clk = res["all_fp64"]
+    tol = 1e-14 * math.sqrt(n)
+    d = prof["hp_gemm"]
+    achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < 2.0:
+            oracle.refine(p.A, p.Qhat, lp="f64")
+            k += 1
+        dt = (time.perf_counter() - t0) / k
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        cpu = {"value": dt * 1e6, "unit": "us", "cores": cores, "kind": "oracle",
+               "sample": f"{k} full all-FP64 oracle refinements of the same n={n} problem"}
+    line = {"metric": "sec to FP64-accurate Schur refinement (small plain case)", "value": ms * 1e3, "unit": "us",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"real n={n} planted, lambda_k=1+k/64, upper std 1/n, Qhat=fl32(Q0 expm(1e-6 S)); "
+                                   f"all-FP64 Alg. 4 to ||stril||/||A||<=1e-14 sqrt(n)", "n": n,
+                       "form": "all-FP64 (native FP64 products, FP64 solve)", "l2": "resident (n=64)",
+                       "status": st, "iters": nr.iters, "hp_gemms": nr.hp_gemms,
+                       "certified": {"stril_rel": rT, "orth": rQ, "tol": tol, "ok": bool(rT <= tol and rQ <= tol)},
+                       "mixed_emulated_us": res["mixed_emulated"][0] * 1e3,
+                       "phase_ms_per_step": {k2: v["ms"] / args.steps for k2, v in prof.items() if v["ms"] > 0}},
+            "roofline": {"bound": "latency", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                         "kernel": "gemm_simt_kernel<double> (n=64: one 64x64 tile per product)",
+                         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"},
+            "cpu_baseline": cpu,
+            "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -596,12 +693,12 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-n", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single", "complex", "batched", "dd"], default="single")
+    ap.add_argument("--workload", choices=["single", "complex", "batched", "dd", "small"], default="single")
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--batch-streams", type=int, default=8)
     args = ap.parse_args()
     if args.n is None:
-        args.n = {"complex": 8192, "dd": 2048}.get(args.workload, 4096)
+        args.n = {"complex": 8192, "dd": 2048, "small": 64}.get(args.workload, 4096)
     if args.cpu_sample_n is None:
         args.cpu_sample_n = {"complex": 2048, "dd": 512}.get(args.workload, 1024)
     if args.impl == "reference":
@@ -610,6 +707,8 @@ def main():
         return run_batched(args)
     if args.workload == "dd":
         return run_dd(args)
+    if args.workload == "small":
+        return run_small(args)
     return run_ours(args)
 
 

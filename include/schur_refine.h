@@ -95,9 +95,15 @@ typedef struct {
                          1e-14 * sqrt(n) (1e-28 * n for SR_TARGET_DD) */
     int profile;      /* 1: time every phase with CUDA events on the handle's
                          stream (see schur_refine_get_profile) */
-    int batch_streams;/* schur_refine_batched: matrices refined concurrently,
-                         each on its own stream and workspace; <= 0 selects 8,
-                         1 refines them one after another on the handle's stream */
+    int batch_streams;/* schur_refine_batched with worker streams: matrices
+                         refined concurrently, each on its own stream and
+                         workspace; <= 0 selects 8, 1 refines them one after
+                         another on the handle's stream */
+    int batch_mode;   /* schur_refine_batched: 0 (default) = grouped launches
+                         where built (real data, FP64 target, emulated
+                         products with 7 digits, FP32 low precision and Qhat,
+                         truncated Sigma, dQhat given), else worker streams;
+                         1 = worker streams always */
 } sr_options;
 
 /* Fills *opt with the defaults: real, FP64 target, native FP64 products,
@@ -158,12 +164,19 @@ sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, vo
  *   matrices with leading dimension n[b].
  *   iters_out[b], status_out[b]: host arrays (may be NULL) receiving each
  *   matrix's pass count and status.
- * The matrices are distributed over batch_streams workers (host threads),
- * each with its own stream and workspace (created on first use and kept by the
- * handle), so the refinements of different matrices overlap on the GPU. The
- * workers start after the work already enqueued on the handle's stream, and
- * that stream waits for all of them before the call returns. Each matrix's
- * result is the same as from schur_refine_step.
+ * Grouped launches (batch_mode 0 where built): all matrices advance pass by
+ * pass together on the handle's stream, and every stage of a pass is one
+ * launch for all matrices still iterating (per-matrix stop test, statuses and
+ * pass counts as schur_refine_step; two synchronizations per pass). The
+ * grouped workspace (about 60 bytes per matrix element plus 10 KiB per matrix
+ * row of digits) is allocated on first use, grown when a later call needs
+ * more, and kept by the handle.
+ * Worker streams (otherwise): the matrices are distributed over batch_streams
+ * workers (host threads), each with its own stream and workspace (created on
+ * first use and kept by the handle), so the refinements of different matrices
+ * overlap on the GPU. The workers start after the work already enqueued on the
+ * handle's stream, and that stream waits for all of them before the call
+ * returns. Each matrix's result is the same as from schur_refine_step.
  * Returns SR_OK if every matrix converged, else the first non-OK status in
  * batch order.
  */

@@ -1,0 +1,57 @@
+// The handle of the C ABI (schur_refine_t): options, stream, workspace and
+// the cached launch plans and graphs. Shared by the translation units of the
+// engine (single matrices: engine.cu; groups of matrices: batch.cu).
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+#include "ozaki.cuh"
+
+struct BatchWork;   // grouped-launch workspace of schur_refine_batched (batch.cu)
+
+struct schur_refine_ctx {
+    int nmax = 0;
+    sr_options opt{};
+    cudaStream_t st = nullptr;
+    int dev = 0;
+    // workspace (ld = nmax)
+    double *AQ = nullptr, *Qw = nullptr, *Y = nullptr, *Delta = nullptr, *diag = nullptr;
+    double *diag_lo = nullptr;   // double-double target: low parts of the diagonal of T^
+    void *TE = nullptr, *W2 = nullptr, *YW = nullptr, *W2Y = nullptr, *W2YW = nullptr;   // low precision
+    double *Wd = nullptr, *W2d = nullptr, *W2Yd = nullptr, *W2YWd = nullptr;   // FP64, emulated-product pass
+    double *partial = nullptr;   // per-block partial sums
+    size_t npartial = 0;
+    double *dnorm = nullptr;     // [0] ||E||^2 [1] ||Y||^2 [2] ||W||^2 [3] ||A||^2 [4..] scratch
+    int *dflags = nullptr;
+    double *hbuf = nullptr;      // pinned host mirror of dnorm (8) + flags
+    sr::OzakiWork oz{};
+    // launch plan of the triangular solve for order plan_n
+    int plan_n = 0;
+    uint32_t *plan = nullptr;
+    size_t plan_cap = 0;
+    std::vector<long long> plan_off;
+    // the solve's two streams of work are captured once per (order, buffers)
+    cudaStream_t cap_st = nullptr, aux_st = nullptr;
+    cudaEvent_t sev0 = nullptr, sev1 = nullptr;
+    struct SolveGraph { int n; const void *TE; int ld; const void *dhp; const void *dlo; int kind; cudaGraphExec_t exec; };
+    std::vector<SolveGraph> graphs;
+    // schur_refine_batched: grouped-launch workspace, or worker sub-handles on their own streams
+    BatchWork *bw = nullptr;
+    std::vector<schur_refine_ctx *> subs;
+    std::vector<cudaStream_t> sub_streams;
+    cudaEvent_t bfork = nullptr;
+    std::vector<cudaEvent_t> bjoin;
+    // profiling
+    sr_profile prof{};
+    std::vector<cudaEvent_t> ev_pool;
+    struct Span { int kind; cudaEvent_t a, b; };
+    std::vector<Span> pending;
+    std::vector<cudaEvent_t> open_ev;   // begin events of open phases (stack)
+};
+
+// schur_refine_batched with grouped launches (every stage of a pass runs for all
+// matrices of the group in one launch); batch.cu
+sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *n, const void *const *dA, void *const *dQ,
+                          const void *const *dQhat, int *iters_out, int *status_out);
+bool sr_batch_supported(const sr_options &o);
+void sr_batch_free(BatchWork *bw);

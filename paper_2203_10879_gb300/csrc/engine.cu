@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "ctx.cuh"
 #include "dd.cuh"
 #include "gemm_simt.cuh"
 #include "kernels_misc.cuh"
@@ -34,47 +35,42 @@ void sr::trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long lon
     }
 }
 
+void sr::trisolve_plan_group(const std::vector<int> &orders, std::vector<unsigned long long> &tiles,
+                             std::vector<long long> &offsets, std::vector<long long> &nleaf)
+{
+    int NBmax = 0;
+    for (int n : orders) NBmax = std::max(NBmax, (n + kSolveTile - 1) / kSolveTile);
+    tiles.clear();
+    nleaf.clear();
+    offsets.assign(1, 0);
+    for (int t = NBmax - 1; t >= 0; --t) {
+        const int d = t + 1;
+        long long nl = 0;
+        for (size_t b = 0; b < orders.size(); ++b) {
+            const int NB = (orders[b] + kSolveTile - 1) / kSolveTile;
+            for (int J = 0; J + t < NB; ++J) {
+                tiles.push_back((unsigned long long)b << 32 | (unsigned long long)((J + t) << 16 | J));
+                ++nl;
+            }
+        }
+        for (size_t b = 0; b < orders.size(); ++b) {
+            const int NB = (orders[b] + kSolveTile - 1) / kSolveTile;
+            if (t >= NB) continue;
+            for (int D = t - 1; D >= 0; --D)
+                for (int J = 0; J + D < NB; ++J) {
+                    const int I = J + D;
+                    if (J + d < NB || I - d >= 0)
+                        tiles.push_back((unsigned long long)b << 32 | (unsigned long long)(I << 16 | J));
+                }
+        }
+        nleaf.push_back(nl);
+        offsets.push_back((long long)tiles.size());
+    }
+}
+
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void sr_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
 
-struct schur_refine_ctx {
-    int nmax = 0;
-    sr_options opt{};
-    cudaStream_t st = nullptr;
-    int dev = 0;
-    // workspace (ld = nmax)
-    double *AQ = nullptr, *Qw = nullptr, *Y = nullptr, *Delta = nullptr, *diag = nullptr;
-    double *diag_lo = nullptr;   // double-double target: low parts of the diagonal of T^
-    void *TE = nullptr, *W2 = nullptr, *YW = nullptr, *W2Y = nullptr, *W2YW = nullptr;   // low precision
-    double *Wd = nullptr, *W2d = nullptr, *W2Yd = nullptr, *W2YWd = nullptr;   // FP64, emulated-product pass
-    double *partial = nullptr;   // per-block partial sums
-    size_t npartial = 0;
-    double *dnorm = nullptr;     // [0] ||E||^2 [1] ||Y||^2 [2] ||W||^2 [3] ||A||^2 [4..] scratch
-    int *dflags = nullptr;
-    double *hbuf = nullptr;      // pinned host mirror of dnorm (8) + flags
-    sr::OzakiWork oz{};
-    // launch plan of the triangular solve for order plan_n
-    int plan_n = 0;
-    uint32_t *plan = nullptr;
-    size_t plan_cap = 0;
-    std::vector<long long> plan_off;
-    // the solve's two streams of work are captured once per (order, buffers)
-    cudaStream_t cap_st = nullptr, aux_st = nullptr;
-    cudaEvent_t sev0 = nullptr, sev1 = nullptr;
-    struct SolveGraph { int n; const void *TE; int ld; const void *dhp; const void *dlo; int kind; cudaGraphExec_t exec; };
-    std::vector<SolveGraph> graphs;
-    // workers of schur_refine_batched: sub-handles on their own streams
-    std::vector<schur_refine_ctx *> subs;
-    std::vector<cudaStream_t> sub_streams;
-    cudaEvent_t bfork = nullptr;
-    std::vector<cudaEvent_t> bjoin;
-    // profiling
-    sr_profile prof{};
-    std::vector<cudaEvent_t> ev_pool;
-    struct Span { int kind; cudaEvent_t a, b; };
-    std::vector<Span> pending;
-    std::vector<cudaEvent_t> open_ev;   // begin events of open phases (stack)
-};
 
 static cudaEvent_t take_event(schur_refine_ctx *h)
 {
@@ -856,6 +852,7 @@ void schur_refine_default_options(sr_options *opt)
     opt->tol = 0.0;
     opt->profile = 0;
     opt->batch_streams = 0;
+    opt->batch_mode = 0;
 }
 
 const char *schur_refine_status_string(sr_status s)
@@ -913,6 +910,7 @@ void schur_refine_destroy(schur_refine_t h)
     cudaFree(h->W2Yd);
     cudaFree(h->W2YWd);
     for (auto *sub : h->subs) schur_refine_destroy(sub);
+    sr_batch_free(h->bw);
     for (auto s : h->sub_streams) cudaStreamDestroy(s);
     for (auto e : h->bjoin) cudaEventDestroy(e);
     if (h->bfork) cudaEventDestroy(h->bfork);
@@ -1036,6 +1034,11 @@ sr_status schur_refine_batched(schur_refine_t h, int batch, const int *n, const 
     for (int b = 0; b < batch; ++b)
         if (n[b] < 1 || n[b] > h->nmax || !dA[b] || !dQ[b]) return SR_ERR_INVALID_ARG;
     if (batch == 0) return SR_OK;
+    if (h->opt.batch_mode == 0 && dQhat && sr_batch_supported(h->opt)) {
+        bool all_qhat = true;
+        for (int b = 0; b < batch; ++b) all_qhat = all_qhat && dQhat[b] != nullptr;
+        if (all_qhat) return sr_batch_refine(h, batch, n, dA, dQ, dQhat, iters_out, status_out);
+    }
     const int want = h->opt.batch_streams > 0 ? h->opt.batch_streams : 8;
     const int W = std::min(want, batch);
     std::vector<int> st(batch, (int)SR_OK), it(batch, 0);

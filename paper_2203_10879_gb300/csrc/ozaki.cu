@@ -182,8 +182,15 @@ struct MmaArgs {
     // [lvl[g], lvl[g+1]). Item x is group x / nact of active tile x % nact.
     int nact;         // tiles formed (all, or those on and above the diagonal)
     int groups;
-    int nitems;       // nact * groups
+    int nitems;       // nact * groups (or the length of items)
     int lvl[kOzakiMaxSlicesDD + 1];
+    const MmaItem *items;   // explicit work items (grouped products), else null
+};
+
+// what one work item needs: digit rows, K-chunks, levels, where its planes go
+struct ItemView {
+    int ra, rb, nch, lb, le, im, ldp, rlim, clim;
+    long long poff;
 };
 
 // number of row tiles formed in column tile bj (of one part)
@@ -210,6 +217,23 @@ __device__ __forceinline__ void item_coords(const MmaArgs &a, int item, int &i0,
     i0 = r * BN;
     im = bj >= a.tiles_j;
     j0 = (im ? bj - a.tiles_j : bj) * BM;
+}
+
+__device__ __forceinline__ ItemView get_item(const MmaArgs &a, int item)
+{
+    ItemView v;
+    if (a.items) {
+        const MmaItem it = a.items[item];
+        v.ra = it.ra; v.rb = it.rb; v.nch = it.nch; v.lb = it.lb; v.le = it.le; v.im = 0;
+        v.ldp = it.ldp; v.rlim = it.rlim; v.clim = it.clim; v.poff = it.poff;
+        return v;
+    }
+    int i0, j0, im, lb, le;
+    item_coords(a, item, i0, j0, im, lb, le);
+    v.ra = i0; v.rb = j0; v.nch = a.nch; v.lb = lb; v.le = le; v.im = im;
+    v.ldp = a.Pmax; v.rlim = 1 << 30; v.clim = 1 << 30;
+    v.poff = (long long)(j0 + (im ? a.Pmax : 0)) * a.Pmax + i0;
+    return v;
 }
 
 // column-side K-chunk read for chunk c: the halves are swapped for an imaginary part
@@ -243,7 +267,7 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     volatile int *abort = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = args.s, nch = args.nch, P = args.Pmax;
+    const int P = args.Pmax;
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < STAGES; ++q) {
@@ -279,20 +303,19 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             int issued = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < args.nitems && ok; item += gridDim.x) {
-                int i0, j0, im, lb, le;
-                item_coords(args, item, i0, j0, im, lb, le);
-                for (int l = lb; l < le && ok; ++l)
+                const ItemView v = get_item(args, item);
+                for (int l = v.lb; l < v.le && ok; ++l)
                     for (int p = 0; p <= l && ok; ++p) {
                         const int q = l - p;
-                        for (int c = 0; c < nch && ok; ++c)
+                        for (int c = 0; c < v.nch && ok; ++c)
                             for (int kb = 0; kb < KB_PER_CHUNK; ++kb) {
                                 if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1, abort)) { ok = false; break; }
                                 const uint32_t fb = smem_u32(&full[stage]);
                                 mbar_expect_tx(fb, A_BYTES + B_BYTES);
                                 const int kc = c * kOzakiKChunk + kb * BK;
-                                const int kcj = col_chunk(args, c, im) * kOzakiKChunk + kb * BK;
-                                tma_load_2d(smem_u32(tileA + stage * A_BYTES), &tmB, fb, kcj, q * P + j0);
-                                tma_load_2d(smem_u32(tileB + stage * B_BYTES), &tmA, fb, kc, p * P + i0);
+                                const int kcj = col_chunk(args, c, v.im) * kOzakiKChunk + kb * BK;
+                                tma_load_2d(smem_u32(tileA + stage * A_BYTES), &tmB, fb, kcj, q * P + v.rb);
+                                tma_load_2d(smem_u32(tileB + stage * B_BYTES), &tmA, fb, kc, p * P + v.ra);
                                 ++issued;
                                 if (++stage == STAGES) { stage = 0; phase ^= 1; }
                             }
@@ -314,12 +337,11 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             int t = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < args.nitems && ok; item += gridDim.x) {
-                int i0, j0, im, lb, le;
-                item_coords(args, item, i0, j0, im, lb, le);
-                for (int l = lb; l < le && ok; ++l)
+                const ItemView v = get_item(args, item);
+                for (int l = v.lb; l < v.le && ok; ++l)
                     for (int p = 0; p <= l && ok; ++p)
-                        for (int c = 0; c < nch && ok; ++c) {
-                            const uint32_t idesc = chunk_idesc(args, c, im);
+                        for (int c = 0; c < v.nch && ok; ++c) {
+                            const uint32_t idesc = chunk_idesc(args, c, v.im);
                             const int b = t & 1;
                             const uint32_t aph = (t >> 1) & 1;
                             if (!mbar_wait(smem_u32(&acce[b]), aph ^ 1, abort)) { ok = false; break; }
@@ -355,15 +377,14 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         int t = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < args.nitems && ok; item += gridDim.x) {
-            int i0, j0, im, lb, le;
-            item_coords(args, item, i0, j0, im, lb, le);
-            const int j = j0 + lg * 32 + lane + (im ? P : 0);   // plane column
-            for (int l = lb; l < le && ok; ++l) {
+            const ItemView v = get_item(args, item);
+            const int jl = lg * 32 + lane;                        // plane column from the tile's origin
+            for (int l = v.lb; l < v.le && ok; ++l) {
 #pragma unroll
                 for (int c = 0; c < BN / 2; ++c) acc[c] = 0u;
                 uint32_t count = 0;
                 for (int p = 0; p <= l && ok; ++p)
-                    for (int c = 0; c < nch; ++c) {
+                    for (int c = 0; c < v.nch; ++c) {
                         const int b = t & 1;
                         const uint32_t aph = (t >> 1) & 1;
                         // one lane polls so the whole warp leaves together on a timeout
@@ -389,12 +410,16 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     }
                 if (!ok) break;
                 const uint32_t bias = count * 0x4B400000u;
-                int32_t *dst = args.planes + (size_t)l * args.pstride + (size_t)j * P + (size_t)(i0 + half * (BN / 2));
+                if (jl < v.clim) {
+                    int32_t *dst = args.planes + (size_t)l * args.pstride + (size_t)v.poff + (size_t)jl * v.ldp +
+                                   (size_t)(half * (BN / 2));
+                    const int rmax = v.rlim - half * (BN / 2);   // region rows come in multiples of 4
 #pragma unroll
-                for (int c = 0; c < BN / 2; c += 4) {
-                    int4 v = make_int4((int)(acc[c] - bias), (int)(acc[c + 1] - bias), (int)(acc[c + 2] - bias),
-                                       (int)(acc[c + 3] - bias));
-                    *reinterpret_cast<int4 *>(dst + c) = v;
+                    for (int c = 0; c < BN / 2; c += 4) {
+                        const int4 x4 = make_int4((int)(acc[c] - bias), (int)(acc[c + 1] - bias),
+                                                  (int)(acc[c + 2] - bias), (int)(acc[c + 3] - bias));
+                        if (c < rmax) *reinterpret_cast<int4 *>(dst + c) = x4;
+                    }
                 }
             }
         }
@@ -451,9 +476,8 @@ __device__ __forceinline__ void split_load_tile(double (&tile)[32][33], const Ti
 
 // Kv: length of the (stacked) vectors: K, or 2 Kh when complex
 template <typename Tin, int LAYOUT>
-__global__ void __launch_bounds__(256)
-ozaki_absmax_kernel(int R, int K, int Kh, int Kv, const Tin *__restrict__ X, int ld,
-                    unsigned long long *__restrict__ vmax)
+__device__ __forceinline__ void absmax_body(int R, int K, int Kh, int Kv, const Tin *__restrict__ X, int ld,
+                                            unsigned long long *__restrict__ vmax)
 {
     __shared__ double tile[32][33];
     __shared__ unsigned long long smax[32];
@@ -478,6 +502,14 @@ ozaki_absmax_kernel(int R, int K, int Kh, int Kv, const Tin *__restrict__ X, int
     if (threadIdx.x < 32 && r0 + threadIdx.x < R) atomicMax(&vmax[r0 + threadIdx.x], smax[threadIdx.x]);
 }
 
+template <typename Tin, int LAYOUT>
+__global__ void __launch_bounds__(256)
+ozaki_absmax_kernel(int R, int K, int Kh, int Kv, const Tin *__restrict__ X, int ld,
+                    unsigned long long *__restrict__ vmax)
+{
+    absmax_body<Tin, LAYOUT>(R, K, Kh, Kv, X, ld, vmax);
+}
+
 __device__ __forceinline__ int split_exponent(unsigned long long b)
 {
     const int eb = (int)(b >> 52);
@@ -488,10 +520,9 @@ __device__ __forceinline__ int split_exponent(unsigned long long b)
 
 // Kp: stacked length written (K rounded up to the chunk, or 2 Kh when complex)
 template <typename Tin, int LAYOUT>
-__global__ void __launch_bounds__(256)
-ozaki_digits_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, int ld, int s, int Pmax, int Kmax,
-                    const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
-                    int *__restrict__ exps)
+__device__ __forceinline__ void digits_body(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, int ld, int s,
+                                            int Pmax, int Kmax, const unsigned long long *__restrict__ vmax,
+                                            __nv_bfloat16 *__restrict__ out, int *__restrict__ exps)
 {
     __shared__ double tile[32][33];
     __shared__ int sexp[32];
@@ -541,6 +572,39 @@ ozaki_digits_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, int
             o[0] = __int2bfloat16_rn((int)Xi);
         }
     }
+}
+
+template <typename Tin, int LAYOUT>
+__global__ void __launch_bounds__(256)
+ozaki_digits_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, int ld, int s, int Pmax, int Kmax,
+                    const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
+                    int *__restrict__ exps)
+{
+    digits_body<Tin, LAYOUT>(R, K, Kh, Kp, X, ld, s, Pmax, Kmax, vmax, out, exps);
+}
+
+// Grouped split (blockIdx.z = matrix): each matrix's vectors go to its own
+// slot rows; blocks outside a matrix's extent return at once.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256)
+ozaki_absmax_group_kernel(const SplitMat *__restrict__ mats, unsigned long long *__restrict__ vmax)
+{
+    const SplitMat m = mats[blockIdx.z];
+    if ((int)blockIdx.x * 32 >= m.R || (int)blockIdx.y * SPLIT_KT >= m.K) return;
+    absmax_body<double, LAYOUT>(m.R, m.K, INT_MAX, m.K, m.X, m.ld, vmax + m.row0);
+}
+
+template <int LAYOUT>
+__global__ void __launch_bounds__(256)
+ozaki_digits_group_kernel(const SplitMat *__restrict__ mats, int s, int Pmax, int Kmax,
+                          const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
+                          int *__restrict__ exps)
+{
+    const SplitMat m = mats[blockIdx.z];
+    const int Kp = (m.K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    if ((int)blockIdx.x * 32 >= m.R || (int)blockIdx.y * DIGIT_KT >= Kp) return;
+    digits_body<double, LAYOUT>(m.R, m.K, INT_MAX, Kp, m.X, m.ld, s, Pmax, Kmax, vmax + m.row0,
+                                out + (size_t)m.row0 * Kmax, exps + m.row0);
 }
 
 // Double-double input: the fixed-point value of hi + lo with F = 7 + 8(s-1)
@@ -823,6 +887,88 @@ sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
     a.nitems = a.nact * a.groups;
     const int grid = (int)std::min<long long>(a.nitems, sms);
     // MMA "A" (TMEM lanes) = column-side digits, MMA "B" = row-side digits
+    ozaki_mma_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.slot[rows].map_i,
+                                                            *(const CUtensorMap *)w.slot[cols].map_j, a);
+    SR_CUDA_TRY(cudaGetLastError());
+    return SR_OK;
+}
+
+cudaError_t ozaki_alloc_group(OzakiWork &w, int rows, int kmax, const int *caps, long long plane_elems)
+{
+    w.nmax = kmax;
+    w.cplx = false;
+    w.Pmax = (rows + kOzakiTileI - 1) / kOzakiTileI * kOzakiTileI;
+    w.Kmax = (kmax + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    w.levels = kOzakiMaxSlices;
+    for (int i = 0; i < kOzakiSlots; ++i) w.levels = std::max(w.levels, caps[i]);
+    w.pstride_group = plane_elems;
+    cudaError_t e = cudaMalloc((void **)&w.planes, (size_t)w.levels * (size_t)plane_elems * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&w.vmax, (size_t)w.Pmax * sizeof(unsigned long long));
+    for (int i = 0; i < kOzakiSlots && e == cudaSuccess; ++i) {
+        OzakiSlot &sl = w.slot[i];
+        sl.cap = caps[i];
+        if (sl.cap <= 0) continue;
+        const size_t bytes = (size_t)sl.cap * w.Pmax * w.Kmax * 2;
+        e = cudaMalloc(&sl.dig, bytes);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sl.exps, (size_t)w.Pmax * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(sl.dig, 0, bytes);
+        if (e == cudaSuccess) e = encode_digits_map(sl.map_j, sl.dig, sl.cap * w.Pmax, w.Kmax, BM);
+        if (e == cudaSuccess) e = encode_digits_map(sl.map_i, sl.dig, sl.cap * w.Pmax, w.Kmax, BN);
+    }
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ozaki_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    return e;
+}
+
+sr_status ozaki_split_group(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, const SplitMat *mats,
+                            int count, int maxR, int maxK, int layout, int s, long long bytes)
+{
+    if (count <= 0) return SR_OK;
+    if (slot < 0 || slot >= kOzakiSlots || s < 1 || s > w.slot[slot].cap || s > kOzakiMaxSlices || maxK > w.Kmax)
+        return SR_ERR_INVALID_ARG;
+    SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, bytes, 2);
+    w.slot[slot].layout = layout;
+    __nv_bfloat16 *out = (__nv_bfloat16 *)w.slot[slot].dig;
+    int *ex = w.slot[slot].exps;
+    SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)w.Pmax * sizeof(unsigned long long), st));
+    const int Rp = (maxR + 31) / 32 * 32;
+    const int Kp = (maxK + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const dim3 gmax(Rp / 32, (maxK + SPLIT_KT - 1) / SPLIT_KT, count);
+    const dim3 gdig(Rp / 32, (Kp + DIGIT_KT - 1) / DIGIT_KT, count);
+    if (layout == OZ_COLS) {
+        ozaki_absmax_group_kernel<OZ_COLS><<<gmax, 256, 0, st>>>(mats, w.vmax);
+        ozaki_digits_group_kernel<OZ_COLS><<<gdig, 256, 0, st>>>(mats, s, w.Pmax, w.Kmax, w.vmax, out, ex);
+    } else {
+        ozaki_absmax_group_kernel<OZ_ROWS><<<gmax, 256, 0, st>>>(mats, w.vmax);
+        ozaki_digits_group_kernel<OZ_ROWS><<<gdig, 256, 0, st>>>(mats, s, w.Pmax, w.Kmax, w.vmax, out, ex);
+    }
+    SR_CUDA_TRY(cudaGetLastError());
+    return SR_OK;
+}
+
+sr_status ozaki_product_items(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols,
+                              const MmaItem *items, int nitems, int s, long long flops, int *flags)
+{
+    if (nitems <= 0) return SR_OK;
+    if (s < 1 || s > w.slot[rows].cap || s > w.slot[cols].cap || s > w.levels) return SR_ERR_INVALID_ARG;
+    // every item's K is at most w.Kmax: level sums stay below 2^31 when s * chunks * 2^22 does
+    if ((long long)s * (w.Kmax / kOzakiKChunk) * (1LL << 22) >= (1LL << 31)) return SR_ERR_UNSUPPORTED;
+    SrPhase ph(h, SR_PROF_OZ_MMA, flops, 0, 1);
+    MmaArgs a{};
+    a.s = s;
+    a.nch = w.Kmax / kOzakiKChunk;
+    a.Pmax = w.Pmax;
+    a.planes = w.planes;
+    a.pstride = (size_t)w.pstride_group;
+    a.flags = flags;
+    a.items = items;
+    a.nitems = nitems;
+    a.nact = nitems;
+    a.groups = 1;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(nitems, sms > 0 ? sms : 1);
     ozaki_mma_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.slot[rows].map_i,
                                                             *(const CUtensorMap *)w.slot[cols].map_j, a);
     SR_CUDA_TRY(cudaGetLastError());

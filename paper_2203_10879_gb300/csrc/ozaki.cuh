@@ -74,12 +74,49 @@ struct OzakiWork {
     bool cplx = false;                     // complex128 operands, stacked [re; im] digit vectors
     OzakiSlot slot[kOzakiSlots];
     int levels = 0;                        // level planes held (the largest slot capacity, at least 7)
+    long long pstride_group = 0;           // grouped work area: elements per level plane
     int32_t *planes = nullptr;             // [levels][Pmax (2 Pmax if cplx) cols][Pmax rows]
     unsigned long long *vmax = nullptr;    // per-vector largest |x| (bit pattern) during a split
 };
 
 // caps[i] = digits of slot i (0 = unused); cplx: complex128 operands
 cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx);
+
+// ---- groups of independent products (many matrices in one launch) -------------------
+// A work area for a group holds the vectors of every matrix one after another
+// in each digit slot: matrix b's vectors are slot rows [row0_b, row0_b + R_b),
+// row0_b a multiple of 32; `rows` is the total (the slot's row stride Pmax).
+// Level planes are per-matrix regions at plane offsets chosen by the caller.
+cudaError_t ozaki_alloc_group(OzakiWork &w, int rows, int kmax, const int *caps, long long plane_elems);
+
+// one matrix of a grouped split: vectors r < R of length K (layout as in
+// ozaki_split) go to slot rows row0 + r
+struct SplitMat {
+    const double *X;
+    int ld, R, K, row0;
+};
+
+// one output tile of a slice product (a work item of the grouped launch)
+struct MmaItem {
+    int ra, rb;         // slot rows of the tile's first output row (row side) and column (column side)
+    int nch;            // K-chunks of 256
+    int lb, le;         // levels [lb, le)
+    int ldp;            // plane leading dimension
+    int rlim, clim;     // rows / columns of the plane region from the tile's origin (writes beyond are dropped)
+    long long poff;     // plane element of the tile's origin
+};
+
+// one matrix of a grouped combine: C (m x n) from the plane region at poff
+// (leading dimension ldp); exponents of slot rows ra + i and rb + j
+struct CombMat {
+    long long poff;
+    int ldp, m, n, ra, rb;
+};
+
+sr_status ozaki_split_group(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, const SplitMat *mats,
+                            int count, int maxR, int maxK, int layout, int s, long long bytes);
+sr_status ozaki_product_items(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols,
+                              const MmaItem *items, int nitems, int s, long long flops, int *flags);
 void ozaki_free(OzakiWork &w);
 
 // longest inner dimension a work area of order nmax takes
@@ -312,6 +349,60 @@ sr_status ozaki_combine(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
         if (blocks) *blocks = ozaki_blocks(m, n);
         return SR_OK;
     }
+}
+
+// Grouped combine: blockIdx.z = matrix, eps[b] its epilogue (FP64 results);
+// partial[b * pb + block] receives the block sums (zero for blocks outside
+// the matrix), pb = gridDim.x * gridDim.y.
+template <class EP>
+__global__ void __launch_bounds__(256)
+ozaki_combine_group_kernel(int s, const int32_t *__restrict__ planes, size_t pstride, const CombMat *__restrict__ mats,
+                           const EP *__restrict__ eps, const int *__restrict__ ea, const int *__restrict__ fb,
+                           double sign, int mirror, double *partial)
+{
+    const CombMat cm = mats[blockIdx.z];
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int jb = blockIdx.y * 32 + (threadIdx.x >> 5);
+    double part = 0.0;
+    if (blockIdx.x * 32 < cm.m && blockIdx.y * 32 < cm.n) {
+        const EP ep = eps[blockIdx.z];
+        const int nh = s < 4 ? s : 4;
+        const double sh = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (nh - 1)) << 52);
+        const double sl = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (s - 1)) << 52);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int j = jb + 8 * w;
+            if (i < cm.m && j < cm.n) {
+                const bool mir = mirror && i > j;
+                const size_t off = (size_t)cm.poff + (mir ? (size_t)j + (size_t)i * (size_t)cm.ldp
+                                                          : (size_t)i + (size_t)j * (size_t)cm.ldp);
+                const int e1 = ea[cm.ra + i], e2 = fb[cm.rb + j];
+                const bool bad = e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite;
+                const double nan = __longlong_as_double(0x7ff8000000000000LL);
+                part += ep(i, j, bad ? nan : oz_rebuild(planes, off, pstride, s, sh, sl, e1 + e2));
+            }
+        }
+    }
+    if (partial) {
+        part = sr_block_sum<256>(part);
+        if (threadIdx.x == 0)
+            partial[(size_t)blockIdx.z * gridDim.x * gridDim.y + blockIdx.x + (size_t)gridDim.x * blockIdx.y] = part;
+    }
+}
+
+template <class EP>
+sr_status ozaki_combine_group(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols,
+                              const CombMat *mats, const EP *eps, int count, int maxM, int maxN, int s, double sign,
+                              bool mirror, double *partial, long long flops, long long bytes)
+{
+    if (count <= 0) return SR_OK;
+    SrPhase ph(h, SR_PROF_OZ_COMBINE, flops, bytes, 1);
+    dim3 grid((maxM + 31) / 32, (maxN + 31) / 32, count);
+    ozaki_combine_group_kernel<EP><<<grid, 256, 0, st>>>(s, w.planes, (size_t)w.pstride_group, mats, eps,
+                                                         w.slot[rows].exps, w.slot[cols].exps, sign,
+                                                         mirror ? 1 : 0, partial);
+    SR_CUDA_TRY(cudaGetLastError());
+    return SR_OK;
 }
 
 // slots used by the engine

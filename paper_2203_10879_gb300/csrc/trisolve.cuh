@@ -59,6 +59,20 @@ __device__ inline double sr_div_round_dd(double hi_i, double lo_i, double hi_j, 
 // followed by the tiles with D < t that receive a product of subdiagonal t+1.
 void trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long long> &offsets);
 
+// A group of independent solves in the same launches (schur_refine_batched):
+// matrix b of the group, and its tiles in the plan as (b << 32 | I << 16 | J).
+struct SolveMat {
+    void *TE;
+    int ld, n;
+    const void *dhp;
+};
+
+// Group plan: for every step t (from the largest order's last subdiagonal
+// down), the leaf tiles of all matrices with more than t block rows, then
+// their update tiles; leaf[t] and upd[t] give the counts.
+void trisolve_plan_group(const std::vector<int> &orders, std::vector<unsigned long long> &tiles,
+                         std::vector<long long> &offsets, std::vector<long long> &nleaf);
+
 // ---- contributions of subdiagonal t+1 to tiles with D < t --------------------
 // 128 threads; thread (tx, ty) owns the 4 x 2 block rows 4tx.., columns 2ty..,
 // read with vector loads from shared memory.
@@ -114,13 +128,25 @@ template <> struct SolveVec<cd> {
     }
 };
 
-template <typename T>
+template <typename T, bool GROUP = false>
 __global__ void __launch_bounds__(128)
-trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t *__restrict__ plan)
+trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t *__restrict__ plan,
+                       const SolveMat *__restrict__ mats = nullptr,
+                       const unsigned long long *__restrict__ gplan = nullptr)
 {
     constexpr int B = kSolveTile, SA = B + 4, SB = B + 2;
+    uint32_t tile;
+    if constexpr (GROUP) {
+        const unsigned long long g = gplan[blockIdx.x];
+        const SolveMat m = mats[g >> 32];
+        TE = (T *)m.TE;
+        ld = m.ld;
+        n = m.n;
+        tile = (uint32_t)g;
+    } else {
+        tile = plan[blockIdx.x];
+    }
     const int NB = (n + B - 1) / B;
-    const uint32_t tile = plan[blockIdx.x];
     const int I = (int)(tile >> 16), J = (int)(tile & 0xffffu);
     const int D = I - J;
     const int r0 = I * B, c0 = J * B;
@@ -177,16 +203,31 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
 
 // ---- solve of the tiles of subdiagonal t ---------------------------------------
 // 1024 threads; thread (lane a, warp b) owns entry (a, b) of the tile.
-template <typename T>
+template <typename T, bool GROUP = false>
 __global__ void __launch_bounds__(1024)
 trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>::hp *__restrict__ dhp,
-                     const double *__restrict__ dlo, int t, const uint32_t *__restrict__ plan, int *__restrict__ flags)
+                     const double *__restrict__ dlo, int t, const uint32_t *__restrict__ plan, int *__restrict__ flags,
+                     const SolveMat *__restrict__ mats = nullptr,
+                     const unsigned long long *__restrict__ gplan = nullptr)
 {
     using Hp = typename SrNum<T>::hp;
     constexpr int B = kSolveTile, S = B + 1;
     const T Z = SrNum<T>::zero();
+    uint32_t tile;
+    if constexpr (GROUP) {
+        // a group: each matrix has its own flag word
+        const unsigned long long g = gplan[blockIdx.x];
+        const SolveMat m = mats[g >> 32];
+        TE = (T *)m.TE;
+        ld = m.ld;
+        n = m.n;
+        dhp = (const Hp *)m.dhp;
+        flags += (g >> 32);
+        tile = (uint32_t)g;
+    } else {
+        tile = plan[blockIdx.x];
+    }
     const int NB = (n + B - 1) / B;
-    const uint32_t tile = plan[blockIdx.x];
     const int I = (int)(tile >> 16), J = (int)(tile & 0xffffu);
     const int D = I - J;
     const int r0 = I * B, c0 = J * B;
@@ -290,6 +331,35 @@ inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEven
             trisolve_update_kernel<T><<<(unsigned)nupd, 128, 0, aux>>>(n, TE, ld, t, plan + offsets[l] + nleaf);
         e = cudaGetLastError();
         // both kernels of this step finish before either of the next starts
+        if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev1, aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev1, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev0, 0);
+    }
+    return e;
+}
+
+// The launches of a group plan (no double-double divisors): the same two-stream
+// sequence as trisolve_launches, steps t = nsteps-1 .. 0.
+template <typename T>
+inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cudaEvent_t ev0, cudaEvent_t ev1,
+                                           const SolveMat *mats, int *flags, const unsigned long long *plan,
+                                           const std::vector<long long> &offsets, const std::vector<long long> &nleaf)
+{
+    const int nsteps = (int)nleaf.size();
+    cudaError_t e = cudaEventRecord(ev0, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev0, 0);
+    for (int l = 0; l < nsteps && e == cudaSuccess; ++l) {
+        const int t = nsteps - 1 - l;
+        const long long nl = nleaf[l];
+        const long long nupd = offsets[l + 1] - offsets[l] - nl;
+        if (nl > 0)
+            trisolve_leaf_kernel<T, true><<<(unsigned)nl, 1024, 0, st>>>(0, nullptr, 0, nullptr, nullptr, t, nullptr,
+                                                                        flags, mats, plan + offsets[l]);
+        if (nupd > 0)
+            trisolve_update_kernel<T, true><<<(unsigned)nupd, 128, 0, aux>>>(0, nullptr, 0, t, nullptr, mats,
+                                                                            plan + offsets[l] + nl);
+        e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
         if (e == cudaSuccess) e = cudaEventRecord(ev1, aux);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev1, 0);

@@ -3,9 +3,11 @@ workload: n log-uniform in [32, 512], each built like the unit-step problem).
 
 Each matrix must meet the same bar as a single refinement (residuals certified
 in double-double <= 1e-14 sqrt(n); Q columns against the oracle and the planted
-Q0 up to sign within 1e-12, gaps 1/64 >= 1e-2), and the worker pool must give
-bit-for-bit the results of the one-matrix-at-a-time loop (same kernels, same
-data, integer-exact emulated products).
+Q0 up to sign within 1e-12, gaps 1/64 >= 1e-2). The grouped launches and the
+worker pool must both give bit-for-bit the results of schur_refine_step on
+each matrix alone (same kernels, same data, integer-exact emulated products,
+the same tiles of the solve), and a matrix that fails must not disturb the
+others.
 """
 import numpy as np
 import pytest
@@ -18,10 +20,10 @@ from gpu_util import from_dev, sign_align, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def _run(problems, workers, **kw):
+def _run(problems, workers, mode=0, **kw):
     import torch
     nmax = max(p.n for p in problems)
-    s, h = B.schur_refine_create(nmax, B.default_options(batch_streams=workers, **kw), None)
+    s, h = B.schur_refine_create(nmax, B.default_options(batch_streams=workers, batch_mode=mode, **kw), None)
     assert s == B.SR_OK
     try:
         As = [to_dev(p.A) for p in problems]
@@ -56,11 +58,66 @@ def test_batched_matches_oracle(batch, hp):
 
 def test_worker_pool_equals_serial_loop(batch):
     sub = batch[:8]
-    _, it1, s1, Q1 = _run(sub, 1, hp_gemm=B.SR_HP_OZAKI_BF16)
-    _, it4, s4, Q4 = _run(sub, 4, hp_gemm=B.SR_HP_OZAKI_BF16)
+    _, it1, s1, Q1 = _run(sub, 1, mode=1, hp_gemm=B.SR_HP_OZAKI_BF16)
+    _, it4, s4, Q4 = _run(sub, 4, mode=1, hp_gemm=B.SR_HP_OZAKI_BF16)
     assert it1 == it4 and s1 == s4
     for a, b in zip(Q1, Q4):
         assert np.array_equal(a, b)
+
+
+def _single(p, **kw):
+    import torch
+    s, h = B.schur_refine_create(p.n, B.default_options(**kw), None)
+    assert s == B.SR_OK
+    try:
+        Q = torch.zeros((p.n, p.n), dtype=torch.float64, device="cuda").t()
+        st, nr = B.schur_refine_step(h, p.n, to_dev(p.A), Q, to_dev(p.Qhat))
+        return st, nr.iters, from_dev(Q)
+    finally:
+        B.schur_refine_destroy(h)
+
+
+def test_grouped_launches_equal_single_steps(batch):
+    st, iters, stats, Qs = _run(batch, 8, mode=0, hp_gemm=B.SR_HP_OZAKI_BF16)
+    assert st == B.SR_OK
+    for p, Q, k, s in zip(batch, Qs, iters, stats):
+        s1, k1, Q1 = _single(p, hp_gemm=B.SR_HP_OZAKI_BF16)
+        assert (s, k) == (s1, k1), p.n
+        assert np.array_equal(Q, Q1), p.n
+
+
+def test_grouped_launches_isolate_a_failing_matrix(batch):
+    # the variance reading of the upper entries (std 1/sqrt(n)) on a packed
+    # spectrum diverges (the analogue of Example 3); its neighbours must not care
+    bad = inputs.jittered_real(200, upper_std=1.0 / np.sqrt(200))
+    group = batch[:5] + [bad] + batch[5:9]
+    st, iters, stats, Qs = _run(group, 8, mode=0, hp_gemm=B.SR_HP_OZAKI_BF16)
+    assert stats[5] in (B.SR_ERR_NONFINITE, B.SR_ERR_NOT_CONVERGED, B.SR_ERR_NONDISTINCT)
+    assert st == stats[5]
+    _, _, _, Qok = _run(batch[:9], 8, mode=0, hp_gemm=B.SR_HP_OZAKI_BF16)
+    for a, b, s in zip(Qs[:5] + Qs[6:], Qok, stats[:5] + stats[6:]):
+        assert s == B.SR_OK
+        assert np.array_equal(a, b)
+
+
+def test_grouped_launches_grow_and_reuse_workspace(batch):
+    import torch
+    nmax = max(p.n for p in batch)
+    s, h = B.schur_refine_create(nmax, B.default_options(hp_gemm=B.SR_HP_OZAKI_BF16), None)
+    assert s == B.SR_OK
+    try:
+        for group in (batch[:3], batch, batch[2:6]):
+            As = [to_dev(p.A) for p in group]
+            Qh = [to_dev(p.Qhat) for p in group]
+            Qs = [torch.zeros((p.n, p.n), dtype=torch.float64, device="cuda").t() for p in group]
+            st, _, _ = B.schur_refine_batched(h, [p.n for p in group], As, Qs, Qh)
+            assert st == B.SR_OK
+            for p, Q in zip(group, Qs):
+                tol = oracle.default_tol(p.n)
+                cT, cQ = oracle.residuals_dd(p.A, from_dev(Q))
+                assert cT <= tol and cQ <= tol
+    finally:
+        B.schur_refine_destroy(h)
 
 
 def test_batched_rejects_bad_sizes():
