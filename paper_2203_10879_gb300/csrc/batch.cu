@@ -44,61 +44,88 @@ struct GMat {          // one matrix of a group: compact buffers at offset off
     void *out0;        // caller output (Q)
 };
 
-// Q (FP64, workspace) <- Qhat (FP32, caller)
-__global__ void __launch_bounds__(256) group_convert_kernel(const GMat *__restrict__ mats, double *__restrict__ Q)
+// The elementwise kernels below run on one flat grid of 32 x 32 tiles over
+// all matrices of a launch: matrix a owns blocks [start[a], start[a + 1]),
+// row-major over its ceil(n/32) x ceil(n/32) tiles; thread (tx, ty) covers
+// rows bx*32 + tx, columns by*32 + ty + 8w (w < 4).
+struct Tile32 {
+    int a, i, j0;
+};
+__device__ __forceinline__ Tile32 tile32(const int *__restrict__ start, int m, const GMat *__restrict__ mats)
 {
-    const GMat m = mats[blockIdx.z];
-    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (i < m.n && j < m.n) Q[m.off + sr_idx(i, j, m.n)] = (double)((const float *)m.in0)[sr_idx(i, j, m.ld_in)];
+    const int a = sr::group_find(start, m, blockIdx.x);
+    const int local = blockIdx.x - start[a], g = (mats[a].n + 31) / 32;
+    return {a, (local % g) * 32 + (int)(threadIdx.x & 31), (local / g) * 32 + (int)(threadIdx.x >> 5)};
+}
+
+// Q (FP64, workspace) <- Qhat (FP32, caller)
+__global__ void __launch_bounds__(256) group_convert_kernel(const GMat *__restrict__ mats, const int *__restrict__ start,
+                                                           int cnt, double *__restrict__ Q)
+{
+    const Tile32 t = tile32(start, cnt, mats);
+    const GMat m = mats[t.a];
+    for (int w = 0; w < 4; ++w) {
+        const int j = t.j0 + 8 * w;
+        if (t.i < m.n && j < m.n)
+            Q[m.off + sr_idx(t.i, j, m.n)] = (double)((const float *)m.in0)[sr_idx(t.i, j, m.ld_in)];
+    }
 }
 
 // caller Q (out0, ld_in) <- workspace Q (in0, compact)
-__global__ void __launch_bounds__(256) group_copy_out_kernel(const GMat *__restrict__ mats)
+__global__ void __launch_bounds__(256) group_copy_out_kernel(const GMat *__restrict__ mats,
+                                                            const int *__restrict__ start, int cnt)
 {
-    const GMat m = mats[blockIdx.z];
-    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (i < m.n && j < m.n) ((double *)m.out0)[sr_idx(i, j, m.ld_in)] = ((const double *)m.in0)[sr_idx(i, j, m.n)];
+    const Tile32 t = tile32(start, cnt, mats);
+    const GMat m = mats[t.a];
+    for (int w = 0; w < 4; ++w) {
+        const int j = t.j0 + 8 * w;
+        if (t.i < m.n && j < m.n)
+            ((double *)m.out0)[sr_idx(t.i, j, m.ld_in)] = ((const double *)m.in0)[sr_idx(t.i, j, m.n)];
+    }
 }
 
 // W = L - L^T (FP64) from the strictly lower triangle of TE (FP32)
-__global__ void __launch_bounds__(256) group_skew_kernel(const GMat *__restrict__ mats, const float *__restrict__ TE,
-                                                         double *__restrict__ W)
+__global__ void __launch_bounds__(256) group_skew_kernel(const GMat *__restrict__ mats, const int *__restrict__ start,
+                                                        int cnt, const float *__restrict__ TE, double *__restrict__ W)
 {
-    const GMat m = mats[blockIdx.z];
-    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (i < m.n && j < m.n) {
-        const float *L = TE + m.off;
-        const double w = i > j ? (double)L[sr_idx(i, j, m.n)] : (i < j ? -(double)L[sr_idx(j, i, m.n)] : 0.0);
-        W[m.off + sr_idx(i, j, m.n)] = w;
+    const Tile32 t = tile32(start, cnt, mats);
+    const GMat m = mats[t.a];
+    const float *L = TE + m.off;
+    for (int w = 0; w < 4; ++w) {
+        const int i = t.i, j = t.j0 + 8 * w;
+        if (i < m.n && j < m.n) {
+            const double v = i > j ? (double)L[sr_idx(i, j, m.n)] : (i < j ? -(double)L[sr_idx(j, i, m.n)] : 0.0);
+            W[m.off + sr_idx(i, j, m.n)] = v;
+        }
     }
 }
 
-// partial sums of ||A_b||^2 (caller's A)
-__global__ void __launch_bounds__(256) group_sumsq_kernel(const GMat *__restrict__ mats, double *__restrict__ partial,
-                                                         int pb)
+// partial[block] = sum of squares of the block's tile of the caller's A
+__global__ void __launch_bounds__(256) group_sumsq_kernel(const GMat *__restrict__ mats, const int *__restrict__ start,
+                                                         int cnt, double *__restrict__ partial)
 {
-    const GMat m = mats[blockIdx.z];
+    const Tile32 t = tile32(start, cnt, mats);
+    const GMat m = mats[t.a];
     double s = 0.0;
-    const size_t total = (size_t)m.n * m.n;
-    for (size_t e = (size_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (size_t)gridDim.x * 256) {
-        const double a = ((const double *)m.in0)[sr_idx((int)(e % m.n), (int)(e / m.n), m.ld_in)];
-        s += a * a;
+    for (int w = 0; w < 4; ++w) {
+        const int j = t.j0 + 8 * w;
+        if (t.i < m.n && j < m.n) {
+            const double v = ((const double *)m.in0)[sr_idx(t.i, j, m.ld_in)];
+            s += v * v;
+        }
     }
     s = sr_block_sum<256>(s);
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.z * pb + blockIdx.x] = s;
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// out[map[a] * stride + slot] = sum of partial[a * pb .. a * pb + pb) (fixed
-// order); a = position in the launch, map[a] = matrix of the group
-__global__ void __launch_bounds__(256) group_reduce_kernel(const double *__restrict__ partial, int pb,
-                                                          const int *__restrict__ map, double *__restrict__ out,
-                                                          int stride, int slot)
+// out[map[a] * stride + slot] = sum of partial[start[a] .. start[a + 1]) in a
+// fixed order; a = position in the launch, map[a] = matrix of the group
+__global__ void __launch_bounds__(256) group_reduce_kernel(const double *__restrict__ partial,
+                                                          const int *__restrict__ start, const int *__restrict__ map,
+                                                          double *__restrict__ out, int stride, int slot)
 {
     double s = 0.0;
-    for (int e = threadIdx.x; e < pb; e += 256) s += partial[(size_t)blockIdx.x * pb + e];
+    for (int e = start[blockIdx.x] + threadIdx.x; e < start[blockIdx.x + 1]; e += 256) s += partial[e];
     s = sr_block_sum<256>(s);
     if (threadIdx.x == 0) out[(size_t)map[blockIdx.x] * stride + slot] = s;
 }
@@ -246,6 +273,7 @@ void make_items(std::vector<sr::MmaItem> &items, const std::vector<int> &act, co
                 it.ra = row0[b] + i0;
                 it.rb = row0[b] + j0;
                 it.nch = (nb + sr::kOzakiKChunk - 1) / sr::kOzakiKChunk;
+                it.kbl = (nb - (it.nch - 1) * sr::kOzakiKChunk + 63) / 64;
                 it.lb = 0;
                 it.le = s;
                 it.ldp = ld;
@@ -257,11 +285,40 @@ void make_items(std::vector<sr::MmaItem> &items, const std::vector<int> &act, co
     }
 }
 
+// Flat-grid prefix sums of the matrices of one launch, in launch order
+struct Grids {
+    size_t o32 = 0, omax = 0, odig = 0;
+    int m = 0, t32 = 0, tmax = 0, tdig = 0;
+};
+
+Grids add_grids(DescPack &pk, const std::vector<int> &order, const std::vector<int> &n)
+{
+    const int m = (int)order.size();
+    std::vector<int> s32(m + 1, 0), smax(m + 1, 0), sdig(m + 1, 0);
+    for (int a = 0; a < m; ++a) {
+        const int nb = n[order[a]], g = (nb + 31) / 32;
+        const int kp = (nb + sr::kOzakiKChunk - 1) / sr::kOzakiKChunk * sr::kOzakiKChunk;
+        s32[a + 1] = s32[a] + g * g;
+        smax[a + 1] = smax[a] + g * ((nb + 255) / 256);   // absmax blocks cover 256 of K
+        sdig[a + 1] = sdig[a] + g * (kp / 64);             // digit blocks cover 64 of K
+    }
+    Grids G;
+    G.o32 = pk.add(s32);
+    G.omax = pk.add(smax);
+    G.odig = pk.add(sdig);
+    G.m = m;
+    G.t32 = s32[m];
+    G.tmax = smax[m];
+    G.tdig = sdig[m];
+    return G;
+}
+
 long long item_flops(const std::vector<sr::MmaItem> &items, int s)
 {
     long long f = 0;
     for (const auto &it : items)
-        f += (long long)s * (s + 1) / 2 * 2LL * sr::kOzakiTileI * sr::kOzakiTileJ * it.nch * sr::kOzakiKChunk;
+        f += (long long)s * (s + 1) / 2 * 2LL * sr::kOzakiTileI * sr::kOzakiTileJ *
+             ((it.nch - 1) * sr::kOzakiKChunk + it.kbl * 64);
     return f;
 }
 
@@ -289,10 +346,10 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
         planes += (long long)r32(n[b]) * r32(n[b]);
         nmx = std::max(nmx, n[b]);
     }
-    // partial sums: one per 32 x 32 block of the largest matrix, per launch
-    // position (the grouped combine's grid.x * grid.y)
-    const int pb = ((nmx + 31) / 32) * ((nmx + 31) / 32);
-    SR_TRY(ensure_capacity(bw, elems, rows, batch, planes, std::max(512, nmx), (size_t)batch * pb));
+    // partial sums: one per 32 x 32 block of every matrix (flat grids)
+    long long t32_all = 0;
+    for (int b = 0; b < batch; ++b) t32_all += (long long)((n[b] + 31) / 32) * ((n[b] + 31) / 32);
+    SR_TRY(ensure_capacity(bw, elems, rows, batch, planes, std::max(512, nmx), (size_t)t32_all));
 
     std::vector<int> cur(batch, 0);   // buffer holding the current Q: 0 = Q0, 1 = Q1
     std::vector<double> y_last(batch, NAN), prev(batch, INFINITY), anorm(batch, 1.0);
@@ -320,10 +377,10 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
     };
     auto P = [&](size_t o) { return (void *)(bw->ddesc + o); };
     const dim3 blk(256);
-    auto grid_e = [&](int cnt) { return dim3((nmx + 31) / 32, (nmx + 7) / 8, cnt); };
-    auto reduce = [&](int cnt, size_t o_map, int slot) -> sr_status {
-        SrPhase ph(h, SR_PROF_OTHER, 0, (long long)cnt * pb * 8, 1);
-        group_reduce_kernel<<<cnt, 256, 0, st>>>(bw->partial, pb, (const int *)P(o_map), bw->norms, kNorms, slot);
+    auto reduce = [&](const Grids &g, size_t o_map, int slot) -> sr_status {
+        SrPhase ph(h, SR_PROF_OTHER, 0, (long long)g.t32 * 8, 1);
+        group_reduce_kernel<<<g.m, 256, 0, st>>>(bw->partial, (const int *)P(g.o32), (const int *)P(o_map),
+                                                 bw->norms, kNorms, slot);
         SR_CUDA_TRY(cudaGetLastError());
         return SR_OK;
     };
@@ -348,8 +405,15 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
         memcpy(&f, h->hbuf + 8, sizeof(int));
         return (f & SR_FLAG_TIMEOUT) != 0;
     };
-    auto split = [&](int slot, size_t o, int cnt, int layout, int s, long long el) {
-        return ozaki_split_group(h, st, bw->oz, slot, (const SplitMat *)P(o), cnt, nmx, nmx, layout, s, 16 * el);
+    auto split = [&](int slot, size_t o, const Grids &g, int layout, int s, long long el) {
+        const GroupSplit gs{(const SplitMat *)P(o), (const int *)P(g.omax), (const int *)P(g.odig), g.m, g.tmax,
+                            g.tdig, nmx};
+        return ozaki_split_group(h, st, bw->oz, slot, gs, layout, s, 16 * el);
+    };
+    auto combine = [&](int rs, int cs, size_t o_cm, const auto *eps, const Grids &g, int s, double sign, bool mirror,
+                       double *partial, long long el, long long bytes_per) {
+        return ozaki_combine_group(h, st, bw->oz, rs, cs, (const CombMat *)P(o_cm), eps, (const int *)P(g.o32), g.m,
+                                   g.t32, s, sign, mirror, partial, 8LL * s * el, bytes_per * el);
     };
     auto product = [&](int rs, int cs, size_t o, const std::vector<MmaItem> &it, int s) {
         return ozaki_product_items(h, st, bw->oz, rs, cs, (const MmaItem *)P(o), (int)it.size(), s,
@@ -388,31 +452,30 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
         const size_t o_ga = pk.add(ga), o_gq = pk.add(gq), o_ar = pk.add(arows), o_qc = pk.add(qcols),
                      o_qr = pk.add(qrows), o_yc = pk.add(ycols), o_cm = pk.add(cm), o_epy = pk.add(epy),
                      o_epu = pk.add(epu), o_sym = pk.add(sym), o_full = pk.add(full), o_map = pk.add(act);
+        const Grids g = add_grids(pk, act, n);
         SR_TRY(upload(pk));
         {
             SrPhase ph(h, SR_PROF_OTHER, 2 * elems, 8 * elems, 1);
-            group_sumsq_kernel<<<dim3(pb, 1, batch), blk, 0, st>>>((const GMat *)P(o_ga), bw->partial, pb);
+            group_sumsq_kernel<<<g.t32, blk, 0, st>>>((const GMat *)P(o_ga), (const int *)P(g.o32), g.m, bw->partial);
             SR_CUDA_TRY(cudaGetLastError());
         }
-        SR_TRY(reduce(batch, o_map, 2));
-        SR_TRY(split(OZS_ROWS, o_ar, batch, OZ_ROWS, kHp, elems));
+        SR_TRY(reduce(g, o_map, 2));
+        SR_TRY(split(OZS_ROWS, o_ar, g, OZ_ROWS, kHp, elems));
         {
             SrPhase ph(h, SR_PROF_OTHER, 0, 12 * elems, 1);
-            group_convert_kernel<<<grid_e(batch), blk, 0, st>>>((const GMat *)P(o_gq), bw->Q0);
+            group_convert_kernel<<<g.t32, blk, 0, st>>>((const GMat *)P(o_gq), (const int *)P(g.o32), g.m, bw->Q0);
             SR_CUDA_TRY(cudaGetLastError());
         }
-        SR_TRY(split(OZS_COLS, o_qc, batch, OZ_COLS, kHp, elems));
+        SR_TRY(split(OZS_COLS, o_qc, g, OZ_COLS, kHp, elems));
         SR_TRY(product(OZS_COLS, OZS_COLS, o_sym, sym, kHp));
-        SR_TRY(ozaki_combine_group(h, st, bw->oz, OZS_COLS, OZS_COLS, (const CombMat *)P(o_cm),
-                                   (const EpMinusI *)P(o_epy), batch, nmx, nmx, kHp, 1.0, true, bw->partial,
-                                   8LL * kHp * elems, (4LL * kHp + 8) * elems));
-        SR_TRY(reduce(batch, o_map, 1));
-        SR_TRY(split(OZS_QROWS, o_qr, batch, OZ_ROWS, kHp, elems));
-        SR_TRY(split(OZS_X, o_yc, batch, OZ_COLS, kHp, elems));
+        SR_TRY(combine(OZS_COLS, OZS_COLS, o_cm, (const EpMinusI *)P(o_epy), g, kHp, 1.0, true, bw->partial, elems,
+                       4LL * kHp + 8));
+        SR_TRY(reduce(g, o_map, 1));
+        SR_TRY(split(OZS_QROWS, o_qr, g, OZ_ROWS, kHp, elems));
+        SR_TRY(split(OZS_X, o_yc, g, OZ_COLS, kHp, elems));
         SR_TRY(product(OZS_QROWS, OZS_X, o_full, full, kHp));
-        SR_TRY(ozaki_combine_group(h, st, bw->oz, OZS_QROWS, OZS_X, (const CombMat *)P(o_cm),
-                                   (const EpUpdate *)P(o_epu), batch, nmx, nmx, kHp, 1.0, false, nullptr,
-                                   8LL * kHp * elems, (4LL * kHp + 24) * elems));
+        SR_TRY(combine(OZS_QROWS, OZS_X, o_cm, (const EpUpdate *)P(o_epu), g, kHp, 1.0, false, nullptr, elems,
+                       4LL * kHp + 24));
         SR_TRY(sync_read());
         if (timed_out()) return SR_ERR_TIMEOUT;
         for (int b = 0; b < batch; ++b) {
@@ -447,18 +510,17 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
             make_items(full, act, n, row0, poff, kHp, false);
             const size_t o_qc = pk.add(qcols), o_aqc = pk.add(aqcols), o_cm = pk.add(cm), o_eaq = pk.add(e_aq),
                          o_esp = pk.add(e_sp), o_full = pk.add(full), o_map = pk.add(act);
+            const Grids g = add_grids(pk, act, n);
             SR_TRY(upload(pk));
-            SR_TRY(split(OZS_COLS, o_qc, m, OZ_COLS, kHp, el));
+            SR_TRY(split(OZS_COLS, o_qc, g, OZ_COLS, kHp, el));
             SR_TRY(product(OZS_ROWS, OZS_COLS, o_full, full, kHp));
-            SR_TRY(ozaki_combine_group(h, st, bw->oz, OZS_ROWS, OZS_COLS, (const CombMat *)P(o_cm),
-                                       (const EpStore *)P(o_eaq), m, nmx, nmx, kHp, 1.0, false, nullptr,
-                                       8LL * kHp * el, (4LL * kHp + 8) * el));
-            SR_TRY(split(OZS_X, o_aqc, m, OZ_COLS, kHp, el));
+            SR_TRY(combine(OZS_ROWS, OZS_COLS, o_cm, (const EpStore *)P(o_eaq), g, kHp, 1.0, false, nullptr, el,
+                           4LL * kHp + 8));
+            SR_TRY(split(OZS_X, o_aqc, g, OZ_COLS, kHp, el));
             SR_TRY(product(OZS_COLS, OZS_X, o_full, full, kHp));
-            SR_TRY(ozaki_combine_group(h, st, bw->oz, OZS_COLS, OZS_X, (const CombMat *)P(o_cm),
-                                       (const EpSplit<float> *)P(o_esp), m, nmx, nmx, kHp, 1.0, false, bw->partial,
-                                       8LL * kHp * el, (4LL * kHp + 4) * el));
-            SR_TRY(reduce(m, o_map, 0));
+            SR_TRY(combine(OZS_COLS, OZS_X, o_cm, (const EpSplit<float> *)P(o_esp), g, kHp, 1.0, false, bw->partial,
+                           el, 4LL * kHp + 4));
+            SR_TRY(reduce(g, o_map, 0));
             SR_TRY(sync_read());
             if (timed_out()) {
                 for (int b : act) st_b[b] = SR_ERR_TIMEOUT;
@@ -527,6 +589,7 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
                          o_cm = pk.add(cm), o_ey = pk.add(e_y), o_ew2 = pk.add(e_w2), o_eyw = pk.add(e_yw),
                          o_ed = pk.add(e_d), o_eu = pk.add(e_u), o_fh = pk.add(full_hp), o_sh = pk.add(sym_hp),
                          o_fl = pk.add(full_lp), o_sl = pk.add(sym_lp), o_map = pk.add(act);
+            const Grids g = add_grids(pk, act, n);
             SR_TRY(upload(pk));
             // S4: the group's solves, step by step
             {
@@ -539,38 +602,34 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
             }
             // S5: Y = Q^T Q - I from Q's column digits (still in slot OZS_COLS), W = L - L^T
             SR_TRY(product(OZS_COLS, OZS_COLS, o_sh, sym_hp, kHp));
-            SR_TRY(ozaki_combine_group(h, st, bw->oz, OZS_COLS, OZS_COLS, (const CombMat *)P(o_cm),
-                                       (const EpMinusI *)P(o_ey), m2, nmx, nmx, kHp, 1.0, true, bw->partial,
-                                       8LL * kHp * el, (4LL * kHp + 8) * el));
-            SR_TRY(reduce(m2, o_map, 1));
+            SR_TRY(combine(OZS_COLS, OZS_COLS, o_cm, (const EpMinusI *)P(o_ey), g, kHp, 1.0, true, bw->partial, el,
+                           4LL * kHp + 8));
+            SR_TRY(reduce(g, o_map, 1));
             {
                 SrPhase ph(h, SR_PROF_OTHER, 0, 12 * el, 1);
-                group_skew_kernel<<<grid_e(m2), blk, 0, st>>>((const GMat *)P(o_ga), bw->TE, bw->W);
+                group_skew_kernel<<<g.t32, blk, 0, st>>>((const GMat *)P(o_ga), (const int *)P(g.o32), g.m, bw->TE,
+                                                         bw->W);
                 SR_CUDA_TRY(cudaGetLastError());
             }
             // S6: W^2 = -W^T W, YW = Y^T W, W^3 = -W^T W^2 (FP32 class); S7 in the last epilogue
-            SR_TRY(split(OZS_W, o_wc, m2, OZ_COLS, kLp, el));
-            SR_TRY(split(OZS_Y, o_yc, m2, OZ_COLS, kLp, el));
+            SR_TRY(split(OZS_W, o_wc, g, OZ_COLS, kLp, el));
+            SR_TRY(split(OZS_Y, o_yc, g, OZ_COLS, kLp, el));
             SR_TRY(product(OZS_W, OZS_W, o_sl, sym_lp, kLp));
-            SR_TRY(ozaki_combine_group(h, st, bw->oz, OZS_W, OZS_W, (const CombMat *)P(o_cm),
-                                       (const EpStore *)P(o_ew2), m2, nmx, nmx, kLp, -1.0, true, nullptr,
-                                       8LL * kLp * el, (4LL * kLp + 8) * el));
+            SR_TRY(combine(OZS_W, OZS_W, o_cm, (const EpStore *)P(o_ew2), g, kLp, -1.0, true, nullptr, el,
+                           4LL * kLp + 8));
             SR_TRY(product(OZS_Y, OZS_W, o_fl, full_lp, kLp));
-            SR_TRY(ozaki_combine_group(h, st, bw->oz, OZS_Y, OZS_W, (const CombMat *)P(o_cm),
-                                       (const EpStore *)P(o_eyw), m2, nmx, nmx, kLp, 1.0, false, nullptr,
-                                       8LL * kLp * el, (4LL * kLp + 8) * el));
-            SR_TRY(split(OZS_W2, o_w2c, m2, OZ_COLS, kLp, el));
+            SR_TRY(combine(OZS_Y, OZS_W, o_cm, (const EpStore *)P(o_eyw), g, kLp, 1.0, false, nullptr, el,
+                           4LL * kLp + 8));
+            SR_TRY(split(OZS_W2, o_w2c, g, OZ_COLS, kLp, el));
             SR_TRY(product(OZS_W, OZS_W2, o_fl, full_lp, kLp));
-            SR_TRY(ozaki_combine_group(h, st, bw->oz, OZS_W, OZS_W2, (const CombMat *)P(o_cm),
-                                       (const EpDeltaD *)P(o_ed), m2, nmx, nmx, kLp, -1.0, false, nullptr,
-                                       8LL * kLp * el, (4LL * kLp + 40) * el));
+            SR_TRY(combine(OZS_W, OZS_W2, o_cm, (const EpDeltaD *)P(o_ed), g, kLp, -1.0, false, nullptr, el,
+                           4LL * kLp + 40));
             // S8: Q_new = Q + 1/2 Q Delta
-            SR_TRY(split(OZS_QROWS, o_qr, m2, OZ_ROWS, kHp, el));
-            SR_TRY(split(OZS_X, o_dc, m2, OZ_COLS, kHp, el));
+            SR_TRY(split(OZS_QROWS, o_qr, g, OZ_ROWS, kHp, el));
+            SR_TRY(split(OZS_X, o_dc, g, OZ_COLS, kHp, el));
             SR_TRY(product(OZS_QROWS, OZS_X, o_fh, full_hp, kHp));
-            SR_TRY(ozaki_combine_group(h, st, bw->oz, OZS_QROWS, OZS_X, (const CombMat *)P(o_cm),
-                                       (const EpUpdate *)P(o_eu), m2, nmx, nmx, kHp, 1.0, false, nullptr,
-                                       8LL * kHp * el, (4LL * kHp + 24) * el));
+            SR_TRY(combine(OZS_QROWS, OZS_X, o_cm, (const EpUpdate *)P(o_eu), g, kHp, 1.0, false, nullptr, el,
+                           4LL * kHp + 24));
             SR_TRY(sync_read());
         }
         if (timed_out()) {
@@ -598,9 +657,12 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
         std::vector<GMat> go(batch);
         for (int b = 0; b < batch; ++b) go[b] = GMat{off[b], n[b], n[b], Qbuf[cur[b]] + off[b], dQ[b]};
         const size_t o_go = pk.add(go);
+        std::vector<int> all(batch);
+        for (int b = 0; b < batch; ++b) all[b] = b;
+        const Grids g = add_grids(pk, all, n);
         SR_TRY(upload(pk));
         SrPhase ph(h, SR_PROF_OTHER, 0, 16 * elems, 1);
-        group_copy_out_kernel<<<grid_e(batch), blk, 0, st>>>((const GMat *)P(o_go));
+        group_copy_out_kernel<<<g.t32, blk, 0, st>>>((const GMat *)P(o_go), (const int *)P(g.o32), g.m);
         SR_CUDA_TRY(cudaGetLastError());
         SR_CUDA_TRY(cudaStreamSynchronize(st));
     }

@@ -189,9 +189,14 @@ struct MmaArgs {
 
 // what one work item needs: digit rows, K-chunks, levels, where its planes go
 struct ItemView {
-    int ra, rb, nch, lb, le, im, ldp, rlim, clim;
+    int ra, rb, nch, kbl, ppa, lb, le, im, ldp, rlim, clim;
     long long poff;
 };
+
+// Digit pairs per accumulator: a one-chunk item whose K is at most 128 (64)
+// accumulates 2 (4) pairs of a level before the drain, still at most 256
+// products in one FP32 sum (exact below 2^22, the bias trick's range).
+__device__ __forceinline__ int pairs_per_acc(int nch, int kbl) { return nch == 1 ? KB_PER_CHUNK / kbl : 1; }
 
 // number of row tiles formed in column tile bj (of one part)
 __device__ __forceinline__ int active_in_column(const MmaArgs &a, int bj)
@@ -224,14 +229,15 @@ __device__ __forceinline__ ItemView get_item(const MmaArgs &a, int item)
     ItemView v;
     if (a.items) {
         const MmaItem it = a.items[item];
-        v.ra = it.ra; v.rb = it.rb; v.nch = it.nch; v.lb = it.lb; v.le = it.le; v.im = 0;
+        v.ra = it.ra; v.rb = it.rb; v.nch = it.nch; v.kbl = it.kbl; v.lb = it.lb; v.le = it.le; v.im = 0;
         v.ldp = it.ldp; v.rlim = it.rlim; v.clim = it.clim; v.poff = it.poff;
+        v.ppa = pairs_per_acc(v.nch, v.kbl);
         return v;
     }
     int i0, j0, im, lb, le;
     item_coords(a, item, i0, j0, im, lb, le);
-    v.ra = i0; v.rb = j0; v.nch = a.nch; v.lb = lb; v.le = le; v.im = im;
-    v.ldp = a.Pmax; v.rlim = 1 << 30; v.clim = 1 << 30;
+    v.ra = i0; v.rb = j0; v.nch = a.nch; v.kbl = KB_PER_CHUNK; v.lb = lb; v.le = le; v.im = im;
+    v.ldp = a.Pmax; v.rlim = 1 << 30; v.clim = 1 << 30; v.ppa = 1;
     v.poff = (long long)(j0 + (im ? a.Pmax : 0)) * a.Pmax + i0;
     return v;
 }
@@ -308,7 +314,7 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     for (int p = 0; p <= l && ok; ++p) {
                         const int q = l - p;
                         for (int c = 0; c < v.nch && ok; ++c)
-                            for (int kb = 0; kb < KB_PER_CHUNK; ++kb) {
+                            for (int kb = 0; kb < (c == v.nch - 1 ? v.kbl : KB_PER_CHUNK); ++kb) {
                                 if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1, abort)) { ok = false; break; }
                                 const uint32_t fb = smem_u32(&full[stage]);
                                 mbar_expect_tx(fb, A_BYTES + B_BYTES);
@@ -338,8 +344,11 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             bool ok = true;
             for (int item = blockIdx.x; item < args.nitems && ok; item += gridDim.x) {
                 const ItemView v = get_item(args, item);
+                // one accumulator per (pair group, chunk); a group holds v.ppa pairs
+                // (more than one only for one-chunk items, whose order of loads is
+                // then the same pair by pair)
                 for (int l = v.lb; l < v.le && ok; ++l)
-                    for (int p = 0; p <= l && ok; ++p)
+                    for (int p0 = 0; p0 <= l && ok; p0 += v.ppa)
                         for (int c = 0; c < v.nch && ok; ++c) {
                             const uint32_t idesc = chunk_idesc(args, c, v.im);
                             const int b = t & 1;
@@ -347,18 +356,20 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                             if (!mbar_wait(smem_u32(&acce[b]), aph ^ 1, abort)) { ok = false; break; }
                             tc_fence_after();
                             const uint32_t dt = tmem + (uint32_t)(b * BN);
-                            for (int kb = 0; kb < KB_PER_CHUNK; ++kb) {
-                                if (!mbar_wait(smem_u32(&full[stage]), phase, abort)) { ok = false; break; }
-                                tc_fence_after();
-                                const uint64_t ad = sdesc_sw128(smem_u32(tileA + stage * A_BYTES));
-                                const uint64_t bd = sdesc_sw128(smem_u32(tileB + stage * B_BYTES));
+                            const int p1 = min(p0 + v.ppa, l + 1);
+                            for (int p = p0; p < p1 && ok; ++p)
+                                for (int kb = 0; kb < (c == v.nch - 1 ? v.kbl : KB_PER_CHUNK); ++kb) {
+                                    if (!mbar_wait(smem_u32(&full[stage]), phase, abort)) { ok = false; break; }
+                                    tc_fence_after();
+                                    const uint64_t ad = sdesc_sw128(smem_u32(tileA + stage * A_BYTES));
+                                    const uint64_t bd = sdesc_sw128(smem_u32(tileB + stage * B_BYTES));
 #pragma unroll
-                                for (int kk = 0; kk < BK / 16; ++kk)
-                                    mma_bf16(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc,
-                                             (kb | kk) != 0);
-                                mma_commit(smem_u32(&empty[stage]));
-                                if (++stage == STAGES) { stage = 0; phase ^= 1; }
-                            }
+                                    for (int kk = 0; kk < BK / 16; ++kk)
+                                        mma_bf16(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc,
+                                                 (p != p0 || kb != 0 || kk != 0) ? 1u : 0u);
+                                    mma_commit(smem_u32(&empty[stage]));
+                                    if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                                }
                             if (!ok) break;
                             mma_commit(smem_u32(&accf[b]));
                             ++t;
@@ -383,7 +394,7 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 #pragma unroll
                 for (int c = 0; c < BN / 2; ++c) acc[c] = 0u;
                 uint32_t count = 0;
-                for (int p = 0; p <= l && ok; ++p)
+                for (int p0 = 0; p0 <= l && ok; p0 += v.ppa)
                     for (int c = 0; c < v.nch; ++c) {
                         const int b = t & 1;
                         const uint32_t aph = (t >> 1) & 1;
@@ -476,12 +487,12 @@ __device__ __forceinline__ void split_load_tile(double (&tile)[32][33], const Ti
 
 // Kv: length of the (stacked) vectors: K, or 2 Kh when complex
 template <typename Tin, int LAYOUT>
-__device__ __forceinline__ void absmax_body(int R, int K, int Kh, int Kv, const Tin *__restrict__ X, int ld,
-                                            unsigned long long *__restrict__ vmax)
+__device__ __forceinline__ void absmax_body(int bx, int by, int R, int K, int Kh, int Kv, const Tin *__restrict__ X,
+                                            int ld, unsigned long long *__restrict__ vmax)
 {
     __shared__ double tile[32][33];
     __shared__ unsigned long long smax[32];
-    const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * SPLIT_KT;
+    const int r0 = bx * 32, kbeg = by * SPLIT_KT;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     if (threadIdx.x < 32) smax[threadIdx.x] = 0ull;
     unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
@@ -507,7 +518,7 @@ __global__ void __launch_bounds__(256)
 ozaki_absmax_kernel(int R, int K, int Kh, int Kv, const Tin *__restrict__ X, int ld,
                     unsigned long long *__restrict__ vmax)
 {
-    absmax_body<Tin, LAYOUT>(R, K, Kh, Kv, X, ld, vmax);
+    absmax_body<Tin, LAYOUT>(blockIdx.x, blockIdx.y, R, K, Kh, Kv, X, ld, vmax);
 }
 
 __device__ __forceinline__ int split_exponent(unsigned long long b)
@@ -520,19 +531,20 @@ __device__ __forceinline__ int split_exponent(unsigned long long b)
 
 // Kp: stacked length written (K rounded up to the chunk, or 2 Kh when complex)
 template <typename Tin, int LAYOUT>
-__device__ __forceinline__ void digits_body(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, int ld, int s,
-                                            int Pmax, int Kmax, const unsigned long long *__restrict__ vmax,
+__device__ __forceinline__ void digits_body(int bx, int by, int R, int K, int Kh, int Kp, const Tin *__restrict__ X,
+                                            int ld, int s, int Pmax, int Kmax,
+                                            const unsigned long long *__restrict__ vmax,
                                             __nv_bfloat16 *__restrict__ out, int *__restrict__ exps)
 {
     __shared__ double tile[32][33];
     __shared__ int sexp[32];
-    const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * DIGIT_KT;
+    const int r0 = bx * 32, kbeg = by * DIGIT_KT;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     if (threadIdx.x < 32) {
         const int r = r0 + threadIdx.x;
         const int e = (r < R) ? split_exponent(vmax[r]) : 0;
         sexp[threadIdx.x] = e;
-        if (blockIdx.y == 0) exps[r] = e;
+        if (by == 0) exps[r] = e;
     }
     const int F = 7 + 8 * (s - 1);
     const size_t pstride = (size_t)Pmax * Kmax;
@@ -580,31 +592,36 @@ ozaki_digits_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, int
                     const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
                     int *__restrict__ exps)
 {
-    digits_body<Tin, LAYOUT>(R, K, Kh, Kp, X, ld, s, Pmax, Kmax, vmax, out, exps);
+    digits_body<Tin, LAYOUT>(blockIdx.x, blockIdx.y, R, K, Kh, Kp, X, ld, s, Pmax, Kmax, vmax, out, exps);
 }
 
-// Grouped split (blockIdx.z = matrix): each matrix's vectors go to its own
-// slot rows; blocks outside a matrix's extent return at once.
+// Grouped split: the blocks of every matrix in one flat grid; block x belongs
+// to matrix a with start[a] <= x < start[a + 1] (a binary search), its
+// position within the matrix's grid of (32 vectors) x (K stretch) is
+// x - start[a]. Each matrix's vectors go to its own slot rows.
 template <int LAYOUT>
 __global__ void __launch_bounds__(256)
-ozaki_absmax_group_kernel(const SplitMat *__restrict__ mats, unsigned long long *__restrict__ vmax)
+ozaki_absmax_group_kernel(const SplitMat *__restrict__ mats, const int *__restrict__ start, int m,
+                          unsigned long long *__restrict__ vmax)
 {
-    const SplitMat m = mats[blockIdx.z];
-    if ((int)blockIdx.x * 32 >= m.R || (int)blockIdx.y * SPLIT_KT >= m.K) return;
-    absmax_body<double, LAYOUT>(m.R, m.K, INT_MAX, m.K, m.X, m.ld, vmax + m.row0);
+    const int a = group_find(start, m, blockIdx.x);
+    const SplitMat g = mats[a];
+    const int local = blockIdx.x - start[a], gx = (g.R + 31) / 32;
+    absmax_body<double, LAYOUT>(local % gx, local / gx, g.R, g.K, INT_MAX, g.K, g.X, g.ld, vmax + g.row0);
 }
 
 template <int LAYOUT>
 __global__ void __launch_bounds__(256)
-ozaki_digits_group_kernel(const SplitMat *__restrict__ mats, int s, int Pmax, int Kmax,
-                          const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
+ozaki_digits_group_kernel(const SplitMat *__restrict__ mats, const int *__restrict__ start, int m, int s, int Pmax,
+                          int Kmax, const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
                           int *__restrict__ exps)
 {
-    const SplitMat m = mats[blockIdx.z];
-    const int Kp = (m.K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
-    if ((int)blockIdx.x * 32 >= m.R || (int)blockIdx.y * DIGIT_KT >= Kp) return;
-    digits_body<double, LAYOUT>(m.R, m.K, INT_MAX, Kp, m.X, m.ld, s, Pmax, Kmax, vmax + m.row0,
-                                out + (size_t)m.row0 * Kmax, exps + m.row0);
+    const int a = group_find(start, m, blockIdx.x);
+    const SplitMat g = mats[a];
+    const int Kp = (g.K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const int local = blockIdx.x - start[a], gx = (g.R + 31) / 32;
+    digits_body<double, LAYOUT>(local % gx, local / gx, g.R, g.K, INT_MAX, Kp, g.X, g.ld, s, Pmax, Kmax,
+                                vmax + g.row0, out + (size_t)g.row0 * Kmax, exps + g.row0);
 }
 
 // Double-double input: the fixed-point value of hi + lo with F = 7 + 8(s-1)
@@ -920,27 +937,25 @@ cudaError_t ozaki_alloc_group(OzakiWork &w, int rows, int kmax, const int *caps,
     return e;
 }
 
-sr_status ozaki_split_group(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, const SplitMat *mats,
-                            int count, int maxR, int maxK, int layout, int s, long long bytes)
+sr_status ozaki_split_group(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, const GroupSplit &g,
+                            int layout, int s, long long bytes)
 {
-    if (count <= 0) return SR_OK;
-    if (slot < 0 || slot >= kOzakiSlots || s < 1 || s > w.slot[slot].cap || s > kOzakiMaxSlices || maxK > w.Kmax)
+    if (g.m <= 0) return SR_OK;
+    if (slot < 0 || slot >= kOzakiSlots || s < 1 || s > w.slot[slot].cap || s > kOzakiMaxSlices || g.maxK > w.Kmax)
         return SR_ERR_INVALID_ARG;
     SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, bytes, 2);
     w.slot[slot].layout = layout;
     __nv_bfloat16 *out = (__nv_bfloat16 *)w.slot[slot].dig;
     int *ex = w.slot[slot].exps;
     SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)w.Pmax * sizeof(unsigned long long), st));
-    const int Rp = (maxR + 31) / 32 * 32;
-    const int Kp = (maxK + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
-    const dim3 gmax(Rp / 32, (maxK + SPLIT_KT - 1) / SPLIT_KT, count);
-    const dim3 gdig(Rp / 32, (Kp + DIGIT_KT - 1) / DIGIT_KT, count);
     if (layout == OZ_COLS) {
-        ozaki_absmax_group_kernel<OZ_COLS><<<gmax, 256, 0, st>>>(mats, w.vmax);
-        ozaki_digits_group_kernel<OZ_COLS><<<gdig, 256, 0, st>>>(mats, s, w.Pmax, w.Kmax, w.vmax, out, ex);
+        ozaki_absmax_group_kernel<OZ_COLS><<<g.total_max, 256, 0, st>>>(g.mats, g.start_max, g.m, w.vmax);
+        ozaki_digits_group_kernel<OZ_COLS><<<g.total_dig, 256, 0, st>>>(g.mats, g.start_dig, g.m, s, w.Pmax, w.Kmax,
+                                                                        w.vmax, out, ex);
     } else {
-        ozaki_absmax_group_kernel<OZ_ROWS><<<gmax, 256, 0, st>>>(mats, w.vmax);
-        ozaki_digits_group_kernel<OZ_ROWS><<<gdig, 256, 0, st>>>(mats, s, w.Pmax, w.Kmax, w.vmax, out, ex);
+        ozaki_absmax_group_kernel<OZ_ROWS><<<g.total_max, 256, 0, st>>>(g.mats, g.start_max, g.m, w.vmax);
+        ozaki_digits_group_kernel<OZ_ROWS><<<g.total_dig, 256, 0, st>>>(g.mats, g.start_dig, g.m, s, w.Pmax, w.Kmax,
+                                                                        w.vmax, out, ex);
     }
     SR_CUDA_TRY(cudaGetLastError());
     return SR_OK;

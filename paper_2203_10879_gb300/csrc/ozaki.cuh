@@ -100,6 +100,7 @@ struct SplitMat {
 struct MmaItem {
     int ra, rb;         // slot rows of the tile's first output row (row side) and column (column side)
     int nch;            // K-chunks of 256
+    int kbl;            // K-blocks of 64 in the last chunk (1..4): K past the order is skipped
     int lb, le;         // levels [lb, le)
     int ldp;            // plane leading dimension
     int rlim, clim;     // rows / columns of the plane region from the tile's origin (writes beyond are dropped)
@@ -113,8 +114,28 @@ struct CombMat {
     int ldp, m, n, ra, rb;
 };
 
-sr_status ozaki_split_group(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, const SplitMat *mats,
-                            int count, int maxR, int maxK, int layout, int s, long long bytes);
+// The flat grids of a grouped split (device arrays): matrix a of the launch
+// owns blocks [start[a], start[a + 1]) of each kernel's grid.
+struct GroupSplit {
+    const SplitMat *mats;
+    const int *start_max;   // absmax blocks: ceil(R/32) x ceil(K/256) per matrix
+    const int *start_dig;   // digit blocks: ceil(R/32) x ceil(Kp/64) per matrix
+    int m, total_max, total_dig, maxK;
+};
+
+// matrix of flat block x: the largest a with start[a] <= x (start[m] = total)
+__device__ __forceinline__ int group_find(const int *__restrict__ start, int m, int x)
+{
+    int lo = 0, hi = m;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (start[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+sr_status ozaki_split_group(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, const GroupSplit &g,
+                            int layout, int s, long long bytes);
 sr_status ozaki_product_items(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols,
                               const MmaItem *items, int nitems, int s, long long flops, int *flags);
 void ozaki_free(OzakiWork &w);
@@ -351,56 +372,56 @@ sr_status ozaki_combine(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
     }
 }
 
-// Grouped combine: blockIdx.z = matrix, eps[b] its epilogue (FP64 results);
-// partial[b * pb + block] receives the block sums (zero for blocks outside
-// the matrix), pb = gridDim.x * gridDim.y.
+// Grouped combine: one flat grid of 32 x 32 output blocks over all matrices
+// (matrix a owns blocks [start[a], start[a + 1]), row-major over its
+// ceil(m/32) x ceil(n/32) blocks); eps[a] its epilogue (FP64 results);
+// partial[block] receives the block sums when partial is given.
 template <class EP>
 __global__ void __launch_bounds__(256)
 ozaki_combine_group_kernel(int s, const int32_t *__restrict__ planes, size_t pstride, const CombMat *__restrict__ mats,
-                           const EP *__restrict__ eps, const int *__restrict__ ea, const int *__restrict__ fb,
-                           double sign, int mirror, double *partial)
+                           const EP *__restrict__ eps, const int *__restrict__ start, int cnt,
+                           const int *__restrict__ ea, const int *__restrict__ fb, double sign, int mirror,
+                           double *partial)
 {
-    const CombMat cm = mats[blockIdx.z];
-    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int jb = blockIdx.y * 32 + (threadIdx.x >> 5);
+    const int a = group_find(start, cnt, blockIdx.x);
+    const CombMat cm = mats[a];
+    const int local = blockIdx.x - start[a], gx = (cm.m + 31) / 32;
+    const int i = (local % gx) * 32 + (threadIdx.x & 31);
+    const int jb = (local / gx) * 32 + (threadIdx.x >> 5);
+    const EP ep = eps[a];
+    const int nh = s < 4 ? s : 4;
+    const double sh = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (nh - 1)) << 52);
+    const double sl = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (s - 1)) << 52);
     double part = 0.0;
-    if (blockIdx.x * 32 < cm.m && blockIdx.y * 32 < cm.n) {
-        const EP ep = eps[blockIdx.z];
-        const int nh = s < 4 ? s : 4;
-        const double sh = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (nh - 1)) << 52);
-        const double sl = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (s - 1)) << 52);
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const int j = jb + 8 * w;
-            if (i < cm.m && j < cm.n) {
-                const bool mir = mirror && i > j;
-                const size_t off = (size_t)cm.poff + (mir ? (size_t)j + (size_t)i * (size_t)cm.ldp
-                                                          : (size_t)i + (size_t)j * (size_t)cm.ldp);
-                const int e1 = ea[cm.ra + i], e2 = fb[cm.rb + j];
-                const bool bad = e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite;
-                const double nan = __longlong_as_double(0x7ff8000000000000LL);
-                part += ep(i, j, bad ? nan : oz_rebuild(planes, off, pstride, s, sh, sl, e1 + e2));
-            }
+    for (int w = 0; w < 4; ++w) {
+        const int j = jb + 8 * w;
+        if (i < cm.m && j < cm.n) {
+            const bool mir = mirror && i > j;
+            const size_t off = (size_t)cm.poff + (mir ? (size_t)j + (size_t)i * (size_t)cm.ldp
+                                                      : (size_t)i + (size_t)j * (size_t)cm.ldp);
+            const int e1 = ea[cm.ra + i], e2 = fb[cm.rb + j];
+            const bool bad = e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite;
+            const double nan = __longlong_as_double(0x7ff8000000000000LL);
+            part += ep(i, j, bad ? nan : oz_rebuild(planes, off, pstride, s, sh, sl, e1 + e2));
         }
     }
     if (partial) {
         part = sr_block_sum<256>(part);
-        if (threadIdx.x == 0)
-            partial[(size_t)blockIdx.z * gridDim.x * gridDim.y + blockIdx.x + (size_t)gridDim.x * blockIdx.y] = part;
+        if (threadIdx.x == 0) partial[blockIdx.x] = part;
     }
 }
 
 template <class EP>
 sr_status ozaki_combine_group(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols,
-                              const CombMat *mats, const EP *eps, int count, int maxM, int maxN, int s, double sign,
-                              bool mirror, double *partial, long long flops, long long bytes)
+                              const CombMat *mats, const EP *eps, const int *start, int cnt, int total, int s,
+                              double sign, bool mirror, double *partial, long long flops, long long bytes)
 {
-    if (count <= 0) return SR_OK;
+    if (cnt <= 0 || total <= 0) return SR_OK;
     SrPhase ph(h, SR_PROF_OZ_COMBINE, flops, bytes, 1);
-    dim3 grid((maxM + 31) / 32, (maxN + 31) / 32, count);
-    ozaki_combine_group_kernel<EP><<<grid, 256, 0, st>>>(s, w.planes, (size_t)w.pstride_group, mats, eps,
-                                                         w.slot[rows].exps, w.slot[cols].exps, sign,
-                                                         mirror ? 1 : 0, partial);
+    ozaki_combine_group_kernel<EP><<<total, 256, 0, st>>>(s, w.planes, (size_t)w.pstride_group, mats, eps, start,
+                                                          cnt, w.slot[rows].exps, w.slot[cols].exps, sign,
+                                                          mirror ? 1 : 0, partial);
     SR_CUDA_TRY(cudaGetLastError());
     return SR_OK;
 }
