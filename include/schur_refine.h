@@ -104,6 +104,21 @@ typedef struct {
                          products with 7 digits, FP32 low precision and Qhat,
                          truncated Sigma, dQhat given), else worker streams;
                          1 = worker streams always */
+    int tune;         /* work split of the emulated slice products (groups of
+                         digit levels per output tile): 0 (default) = the
+                         analytic makespan estimate; 1 = on the first product
+                         of each shape, time the candidate splits (1 to 4
+                         groups) and keep the fastest for the handle's life
+                         (that first call synchronizes the stream) */
+    int graph;        /* schur_refine_step for real data and the FP64 target:
+                         0 (default) = the REPEAT loop runs on the host with
+                         one synchronization per step of the loop; 1 = the
+                         whole call is one CUDA graph (built on the first call
+                         for given order and buffers, then replayed) whose
+                         loop and stop test run on the device (conditional
+                         WHILE / IF nodes), one synchronization per call;
+                         same results; the profile (profile = 1) is not
+                         recorded in this mode */
 } sr_options;
 
 /* Fills *opt with the defaults: real, FP64 target, native FP64 products,

@@ -41,6 +41,17 @@ struct schur_refine_ctx {
     std::vector<cudaStream_t> sub_streams;
     cudaEvent_t bfork = nullptr;
     std::vector<cudaEvent_t> bjoin;
+    // graph mode (opt.graph): the refinement captured once per (order, buffers)
+    // as one graph with device-side stop tests; capturing = true while it is built
+    bool capturing = false;
+    struct RefineGraph {
+        int n = 0, lda = 0, ldq = 0;
+        const void *A = nullptr, *Q = nullptr, *Qhat = nullptr, *T = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+    } rgraph;
+    void *ctl = nullptr;                  // device state of the graph's REPEAT loop
+    std::vector<cudaStream_t> cstreams;   // capture streams of nested conditional bodies
     // profiling
     sr_profile prof{};
     std::vector<cudaEvent_t> ev_pool;

@@ -89,7 +89,7 @@ void sr_prof_begin(schur_refine_ctx *h, int kind, long long flops, long long byt
     h->prof.flops[kind] += flops;
     h->prof.bytes[kind] += bytes;
     h->prof.launches[kind] += launches;
-    if (!h->opt.profile) return;
+    if (!h->opt.profile || h->capturing) return;
     cudaEvent_t a = take_event(h);
     cudaEventRecord(a, h->st);
     h->open_ev.push_back(a);
@@ -97,7 +97,7 @@ void sr_prof_begin(schur_refine_ctx *h, int kind, long long flops, long long byt
 
 void sr_prof_end(schur_refine_ctx *h, int kind)
 {
-    if (!h->opt.profile || h->open_ev.empty()) return;
+    if (!h->opt.profile || h->capturing || h->open_ev.empty()) return;
     cudaEvent_t a = h->open_ev.back();
     h->open_ev.pop_back();
     cudaEvent_t b = take_event(h);
@@ -135,6 +135,8 @@ sr_status check_opts(const sr_options &o)
     if (o.hp_gemm != SR_HP_FP64 && o.hp_gemm != SR_HP_OZAKI_BF16) return SR_ERR_INVALID_ARG;
     if (o.lp != SR_LP_FP32 && o.lp != SR_LP_FP64) return SR_ERR_INVALID_ARG;
     if (o.qhat_type != SR_QHAT_FP32 && o.qhat_type != SR_QHAT_FP64) return SR_ERR_INVALID_ARG;
+    if ((o.batch_mode != 0 && o.batch_mode != 1) || (o.tune != 0 && o.tune != 1) || (o.graph != 0 && o.graph != 1))
+        return SR_ERR_INVALID_ARG;
     if (o.ozaki_slices > (o.target == SR_TARGET_DD ? sr::kOzakiMaxSlicesDD : sr::kOzakiMaxSlices))
         return SR_ERR_INVALID_ARG;
     // double-double target: real data, FP64 correction path, FP64 start
@@ -276,6 +278,12 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
     const int NB = (n + sr::kSolveTile - 1) / sr::kSolveTile;
     const int kind = SrNum<Tl>::kind;
     cudaGraphExec_t exec = nullptr;
+    if (h->capturing) {
+        // inside the refinement's own graph: the launches themselves are captured
+        SR_CUDA_TRY(sr::trisolve_launches<Tl>(h->st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp, dlo, h->dflags,
+                                              h->plan, h->plan_off));
+        return SR_OK;
+    }
     for (auto &g : h->graphs)
         if (g.n == n && g.TE == TE && g.ld == ld && g.dhp == dhp && g.dlo == dlo && g.kind == kind) exec = g.exec;
     if (!exec) {
@@ -579,6 +587,293 @@ sr_status run_step(schur_refine_ctx *h, int n, const void *A, int lda, void *dQ,
     return status;
 }
 
+// ---- graph mode: the whole call as one CUDA graph with a device-side loop ------------
+// The REPEAT loop of Alg. 4 becomes a conditional WHILE node whose body holds two
+// passes (Q in the caller's buffer, then in Qw: the buffers are fixed in a graph);
+// the decisions of the host loop (stop test, divergence guard, solve failures,
+// max_iter) are taken by one-thread control kernels that set the conditional
+// values of the enclosing WHILE and of the IF nodes that guard the solve and the
+// update. Results are the same as the host loop's.
+
+struct SrCtl {
+    int k, status, iters, hp_gemms, max_iter, loc;
+    double prev, y_last, rT, orth, w_norm, tol;
+};
+
+__global__ void ctl_start_kernel(SrCtl *c, const double *__restrict__ dnorm, int has_qhat, double tol, int max_iter)
+{
+    c->k = 0;
+    c->status = SR_ERR_NOT_CONVERGED;
+    c->iters = 0;
+    c->hp_gemms = has_qhat ? 2 : 0;
+    c->max_iter = max_iter;
+    c->loc = 0;
+    c->prev = INFINITY;
+    c->y_last = has_qhat ? sqrt(dnorm[1]) : NAN;
+    c->orth = c->y_last;
+    c->rT = NAN;
+    c->w_norm = NAN;
+    c->tol = tol;
+}
+
+// after T^: the stop test and the divergence guard of schur_refine_step
+__global__ void ctl_residual_kernel(SrCtl *c, const double *__restrict__ dnorm, const int *__restrict__ flags,
+                                    cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hb,
+                                    cudaGraphConditionalHandle hu, int set_hb)
+{
+    const int k = ++c->k;
+    c->iters = k;
+    c->hp_gemms += 2;
+    const double an = sqrt(dnorm[3]);
+    const double rT = sqrt(dnorm[0]) / (an > 0 ? an : 1.0);
+    c->rT = rT;
+    bool stop = true;
+    int st = SR_ERR_NOT_CONVERGED;
+    if (*flags & SR_FLAG_TIMEOUT) st = SR_ERR_TIMEOUT;
+    else if (!isfinite(rT)) st = SR_ERR_NONFINITE;
+    else if (rT <= c->tol && !(c->y_last > sqrt(c->tol))) st = SR_OK;
+    else if (k >= 3 && rT > 10.0 * c->prev) st = SR_ERR_NOT_CONVERGED;
+    else { stop = false; c->prev = rT; }
+    c->status = st;
+    const unsigned go = (!stop && k < c->max_iter) ? 1u : 0u;
+    cudaGraphSetConditional(hu, stop ? 0u : 1u);
+    cudaGraphSetConditional(hw, go);
+    if (set_hb) cudaGraphSetConditional(hb, go);
+}
+
+// after the solve: a zero divisor or a non-finite L ends the call before the update
+__global__ void ctl_solve_kernel(SrCtl *c, const double *__restrict__ dnorm, const int *__restrict__ flags,
+                                 cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hb,
+                                 cudaGraphConditionalHandle hu, int set_hb)
+{
+    const int f = *flags;
+    unsigned ok = 1;
+    if (f & SR_FLAG_NONDISTINCT) { c->status = SR_ERR_NONDISTINCT; ok = 0; }
+    else if (f & SR_FLAG_NONFINITE) { c->status = SR_ERR_NONFINITE; ok = 0; }
+    else c->w_norm = sqrt(2.0 * dnorm[2]);
+    cudaGraphSetConditional(hu, ok);
+    if (!ok) {
+        cudaGraphSetConditional(hw, 0u);
+        if (set_hb) cudaGraphSetConditional(hb, 0u);
+    }
+}
+
+__global__ void ctl_update_kernel(SrCtl *c, const double *__restrict__ dnorm, int loc)
+{
+    c->hp_gemms += 2;
+    c->y_last = sqrt(dnorm[1]);
+    c->orth = c->y_last;
+    c->loc = loc;
+    c->status = SR_ERR_NOT_CONVERGED;
+}
+
+// the caller's Q <- Qw when the last update left the factor in Qw
+__global__ void ctl_copy_kernel(const SrCtl *c, int n, const double *__restrict__ src, int lds, double *__restrict__ dst,
+                                int ldd)
+{
+    if (c->loc != 1) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i < n) dst[sr_idx(i, j, ldd)] = src[sr_idx(i, j, lds)];
+}
+
+// a conditional handle of the graph being captured on h->st
+sr_status cond_handle(schur_refine_ctx *h, unsigned defval, cudaGraphConditionalHandle *out)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    SR_CUDA_TRY(cudaStreamGetCaptureInfo(h->st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) return SR_ERR_CUDA;
+    SR_CUDA_TRY(cudaGraphConditionalHandleCreate(out, g, defval, cudaGraphCondAssignDefault));
+    return SR_OK;
+}
+
+// Adds a conditional node (WHILE or IF on handle hd) after the work captured so
+// far on h->st and captures body() into it on the capture stream of this depth.
+template <class F>
+sr_status cond_node(schur_refine_ctx *h, int depth, cudaGraphConditionalNodeType type, cudaGraphConditionalHandle hd,
+                    F body)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    SR_CUDA_TRY(cudaStreamGetCaptureInfo(h->st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return SR_ERR_CUDA;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hd;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    SR_CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+    SR_CUDA_TRY(cudaStreamUpdateCaptureDependencies(h->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    while ((int)h->cstreams.size() <= depth) {
+        cudaStream_t s = nullptr;
+        SR_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        h->cstreams.push_back(s);
+    }
+    cudaStream_t bs = h->cstreams[depth], saved = h->st;
+    SR_CUDA_TRY(cudaStreamBeginCaptureToGraph(bs, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed));
+    h->st = bs;
+    const sr_status r = body();
+    h->st = saved;
+    cudaGraph_t done = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(bs, &done);
+    if (r != SR_OK) return r;
+    SR_CUDA_TRY(e);
+    return SR_OK;
+}
+
+// one pass of the REPEAT loop inside the graph: Qc -> Qo; loc = the buffer the update leaves Q in
+template <typename Tl>
+sr_status graph_pass(schur_refine_ctx *h, int depth, int n, const double *A, int lda, double *Qc, int ldc, double *Qo,
+                     int ldo, double *dT, int loc, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hb,
+                     int set_hb)
+{
+    SrCtl *c = (SrCtl *)h->ctl;
+    const bool oz = oz_pass(h);
+    if (oz)
+        SR_TRY(oz_form_residual<false>(h, n, Qc, ldc, dT));
+    else
+        SR_TRY(form_residual<Tl>(h, n, A, lda, Qc, ldc, dT));
+    cudaGraphConditionalHandle hu = 0;
+    SR_TRY(cond_handle(h, 0, &hu));
+    ctl_residual_kernel<<<1, 1, 0, h->st>>>(c, h->dnorm, h->dflags, hw, hb, hu, set_hb);
+    SR_CUDA_TRY(cudaGetLastError());
+    return cond_node(h, depth, cudaGraphCondTypeIf, hu, [&]() -> sr_status {
+        SR_TRY(solve<Tl>(h, n, (Tl *)h->TE, h->nmax, h->diag));
+        SR_TRY(sumsq<Tl>(h, n, (const Tl *)h->TE, h->nmax, 1, 2));
+        cudaGraphConditionalHandle hu2 = 0;
+        SR_TRY(cond_handle(h, 0, &hu2));
+        ctl_solve_kernel<<<1, 1, 0, h->st>>>(c, h->dnorm, h->dflags, hw, hb, hu2, set_hb);
+        SR_CUDA_TRY(cudaGetLastError());
+        return cond_node(h, depth + 1, cudaGraphCondTypeIf, hu2, [&]() -> sr_status {
+            if (oz)
+                SR_TRY(oz_update<false>(h, n, Qc, ldc, Qo, ldo));
+            else
+                SR_TRY(update<Tl>(h, n, Qc, ldc, Qo, ldo));
+            ctl_update_kernel<<<1, 1, 0, h->st>>>(c, h->dnorm, loc);
+            SR_CUDA_TRY(cudaGetLastError());
+            return SR_OK;
+        });
+    });
+}
+
+template <typename Tl>
+sr_status build_refine_graph(schur_refine_ctx *h, int n, const void *dA, int lda, void *dQ, int ldq,
+                             const void *dQhat, void *dT)
+{
+    const int ld = h->nmax;
+    const double tol = tol_of(h, n);
+    const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 10;
+    const bool oz = oz_pass(h);
+    double *Q = (double *)dQ, *Qw = h->Qw;
+    const double *A = (const double *)dA;
+    if (!h->ctl) SR_CUDA_TRY(cudaMalloc(&h->ctl, sizeof(SrCtl)));
+    SR_TRY(ensure_plan(h, n));   // host work and a synchronization: not inside a capture
+    while (h->cstreams.empty()) {
+        cudaStream_t s = nullptr;
+        SR_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        h->cstreams.push_back(s);
+    }
+    cudaStream_t top = h->cstreams[0], saved = h->st;
+    // depth 0 is the top-level capture; conditional bodies use depths 1..4
+    SR_CUDA_TRY(cudaStreamBeginCapture(top, cudaStreamCaptureModeRelaxed));
+    h->st = top;
+    h->capturing = true;
+    auto body = [&]() -> sr_status {
+        SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
+        SR_TRY(sumsq<double>(h, n, A, lda, 0, 3));
+        if (oz) SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_ROWS, n, n, A, lda, sr::OZ_ROWS, oz_s(h)));
+        if (dQhat) {
+            dim3 grid((n + 255) / 256, n);
+            if (h->opt.qhat_type == SR_QHAT_FP32)
+                sr::convert_to_hp_kernel<float><<<grid, 256, 0, h->st>>>(n, (const float *)dQhat, ldq, Q, ldq);
+            else
+                sr::convert_to_hp_kernel<double><<<grid, 256, 0, h->st>>>(n, (const double *)dQhat, ldq, Q, ldq);
+            SR_CUDA_TRY(cudaGetLastError());
+            if (oz) {
+                SR_TRY(oz_ns_init<false>(h, n, Q, ldq, Qw, ld));
+            } else {
+                SR_TRY(hp_gemm(h, true, n, n, n, (const double *)Q, ldq, (const double *)Q, ldq,
+                               sr::EpMinusI{h->Y, ld}, 1));
+                SR_TRY(hp_gemm(h, false, n, n, n, (const double *)Q, ldq, h->Y, ld,
+                               sr::EpUpdate{(const double *)Q, ldq, Qw, ld, -0.5}, -1));
+            }
+            SR_CUDA_TRY(cudaMemcpy2DAsync(Q, (size_t)ldq * 8, Qw, (size_t)ld * 8, (size_t)n * 8, n,
+                                          cudaMemcpyDeviceToDevice, h->st));
+        }
+        ctl_start_kernel<<<1, 1, 0, h->st>>>((SrCtl *)h->ctl, h->dnorm, dQhat ? 1 : 0, tol, max_iter);
+        SR_CUDA_TRY(cudaGetLastError());
+        cudaGraphConditionalHandle hw = 0;
+        SR_TRY(cond_handle(h, 1, &hw));
+        SR_TRY(cond_node(h, 1, cudaGraphCondTypeWhile, hw, [&]() -> sr_status {
+            cudaGraphConditionalHandle hb = 0;
+            SR_TRY(cond_handle(h, 0, &hb));
+            SR_TRY(graph_pass<Tl>(h, 2, n, A, lda, Q, ldq, Qw, ld, (double *)dT, 1, hw, hb, 1));
+            return cond_node(h, 2, cudaGraphCondTypeIf, hb, [&]() -> sr_status {
+                return graph_pass<Tl>(h, 3, n, A, lda, Qw, ld, Q, ldq, (double *)dT, 0, hw, hb, 0);
+            });
+        }));
+        dim3 grid((n + 255) / 256, n);
+        ctl_copy_kernel<<<grid, 256, 0, h->st>>>((const SrCtl *)h->ctl, n, Qw, ld, Q, ldq);
+        SR_CUDA_TRY(cudaGetLastError());
+        return SR_OK;
+    };
+    const sr_status r = body();
+    h->st = saved;
+    h->capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(top, &graph);
+    if (r != SR_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (r != SR_OK) return r;
+        sr_set_last_cuda_error(e);
+        return SR_ERR_CUDA;
+    }
+    auto &rg = h->rgraph;
+    if (rg.exec) cudaGraphExecDestroy(rg.exec);
+    if (rg.graph) cudaGraphDestroy(rg.graph);
+    rg = schur_refine_ctx::RefineGraph{};
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    if (ei != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        sr_set_last_cuda_error(ei);
+        cudaGetLastError();
+        return SR_ERR_CUDA;
+    }
+    rg.n = n; rg.lda = lda; rg.ldq = ldq; rg.A = dA; rg.Q = dQ; rg.Qhat = dQhat; rg.T = dT;
+    rg.graph = graph;
+    rg.exec = exec;
+    return SR_OK;
+}
+
+template <typename Tl>
+sr_status run_step_graph(schur_refine_ctx *h, int n, const void *dA, int lda, void *dQ, int ldq, const void *dQhat,
+                         void *dT, sr_norms *out)
+{
+    auto &rg = h->rgraph;
+    if (!(rg.exec && rg.n == n && rg.lda == lda && rg.ldq == ldq && rg.A == dA && rg.Q == dQ && rg.Qhat == dQhat &&
+          rg.T == dT))
+        SR_TRY(build_refine_graph<Tl>(h, n, dA, lda, dQ, ldq, dQhat, dT));
+    SR_CUDA_TRY(cudaGraphLaunch(rg.exec, h->st));
+    SrCtl c{};
+    SR_CUDA_TRY(cudaMemcpyAsync(h->hbuf, h->ctl, sizeof(SrCtl), cudaMemcpyDeviceToHost, h->st));
+    SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+    memcpy(&c, h->hbuf, sizeof(SrCtl));
+    if (out) {
+        out->stril_rel = c.rT;
+        out->orth = c.orth;
+        out->w_norm = c.w_norm;
+        out->iters = c.iters;
+        out->hp_gemms = c.hp_gemms;
+    }
+    return (sr_status)c.status;
+}
+
 // ---- double-double working precision (target SR_TARGET_DD) --------------------------
 // Alg. 4 with hp = double-double and lp = FP64. A double-double matrix of the
 // caller is two planes, the low one ld * n elements after the high one; the
@@ -853,6 +1148,8 @@ void schur_refine_default_options(sr_options *opt)
     opt->profile = 0;
     opt->batch_streams = 0;
     opt->batch_mode = 0;
+    opt->tune = 0;
+    opt->graph = 0;
 }
 
 const char *schur_refine_status_string(sr_status s)
@@ -915,6 +1212,10 @@ void schur_refine_destroy(schur_refine_t h)
     for (auto e : h->bjoin) cudaEventDestroy(e);
     if (h->bfork) cudaEventDestroy(h->bfork);
     drop_graphs(h);
+    if (h->rgraph.exec) cudaGraphExecDestroy(h->rgraph.exec);
+    if (h->rgraph.graph) cudaGraphDestroy(h->rgraph.graph);
+    for (auto s : h->cstreams) cudaStreamDestroy(s);
+    cudaFree(h->ctl);
     if (h->cap_st) cudaStreamDestroy(h->cap_st);
     if (h->aux_st) cudaStreamDestroy(h->aux_st);
     if (h->sev0) cudaEventDestroy(h->sev0);
@@ -1002,6 +1303,7 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
             if (e == cudaSuccess && o.full_sigma) e = cudaMalloc((void **)&h->W2YWd, nn * hps);
         }
         if (e == cudaSuccess) e = sr::ozaki_alloc(h->oz, n_max, caps, is_cplx(o));
+        h->oz.autotune = o.tune == 1;
     }
     if (e != cudaSuccess) {
         sr_set_last_cuda_error(e);
@@ -1023,6 +1325,10 @@ sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, vo
         return run_step_dd<false>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
     }
     if (is_cplx(h->opt)) return run_step<float, true>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
+    if (h->opt.graph) {
+        if (h->opt.lp == SR_LP_FP32) return run_step_graph<float>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
+        return run_step_graph<double>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
+    }
     if (h->opt.lp == SR_LP_FP32) return run_step<float, false>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
     return run_step<double, false>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
 }

@@ -136,29 +136,47 @@ gemm_simt_kernel(int m, int n, int k, LA la, LB lb, EP ep, double *partial)
 
 // tile shapes
 struct TileF64 { static constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4; };
+struct TileF64Small { static constexpr int BM = 32, BN = 32, BK = 8, TM = 2, TN = 2; };
 struct TileF32 { static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8; };
 
 template <typename T> struct TileFor;
 template <> struct TileFor<double> { using type = TileF64; };
 template <> struct TileFor<float> { using type = TileF32; };
 
+// FP64 products whose 64 x 64 grid would fill less than half of the GPU's 152
+// SMs (small orders: latency-bound) use 32 x 32 tiles, 4x the blocks.
+template <typename T>
+inline bool simt_small(int m, int n)
+{
+    return sr_is_double<T>::value && ((m + 63) / 64) * ((n + 63) / 64) < 76;
+}
+
 // Number of blocks (= partial sums) a launch of an m x n product writes.
 template <typename T>
 inline int simt_blocks(int m, int n)
 {
+    if (simt_small<T>(m, n)) return ((m + 31) / 32) * ((n + 31) / 32);
     using Tl = typename TileFor<T>::type;
     return ((m + Tl::BM - 1) / Tl::BM) * ((n + Tl::BN - 1) / Tl::BN);
 }
 
-template <typename T, class LA, class LB, class EP>
-inline cudaError_t gemm_simt(cudaStream_t st, int m, int n, int k, LA la, LB lb, EP ep, double *partial)
+template <typename T, class Tl, class LA, class LB, class EP>
+inline cudaError_t gemm_simt_tile(cudaStream_t st, int m, int n, int k, LA la, LB lb, EP ep, double *partial)
 {
-    using Tl = typename TileFor<T>::type;
     dim3 grid((m + Tl::BM - 1) / Tl::BM, (n + Tl::BN - 1) / Tl::BN);
     constexpr int NT = (Tl::BM / Tl::TM) * (Tl::BN / Tl::TN);
     gemm_simt_kernel<T, Tl::BM, Tl::BN, Tl::BK, Tl::TM, Tl::TN><<<grid, NT, 0, st>>>(m, n, k, la, lb, ep,
                                                                                      partial);
     return cudaGetLastError();
+}
+
+template <typename T, class LA, class LB, class EP>
+inline cudaError_t gemm_simt(cudaStream_t st, int m, int n, int k, LA la, LB lb, EP ep, double *partial)
+{
+    if constexpr (sr_is_double<T>::value) {
+        if (simt_small<T>(m, n)) return gemm_simt_tile<T, TileF64Small>(st, m, n, k, la, lb, ep, partial);
+    }
+    return gemm_simt_tile<T, typename TileFor<T>::type>(st, m, n, k, la, lb, ep, partial);
 }
 
 }  // namespace sr

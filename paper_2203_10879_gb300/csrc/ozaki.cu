@@ -224,10 +224,11 @@ __device__ __forceinline__ void item_coords(const MmaArgs &a, int item, int &i0,
     j0 = (im ? bj - a.tiles_j : bj) * BM;
 }
 
+template <bool ITEMS>
 __device__ __forceinline__ ItemView get_item(const MmaArgs &a, int item)
 {
     ItemView v;
-    if (a.items) {
+    if constexpr (ITEMS) {
         const MmaItem it = a.items[item];
         v.ra = it.ra; v.rb = it.rb; v.nch = it.nch; v.kbl = it.kbl; v.lb = it.lb; v.le = it.le; v.im = 0;
         v.ldp = it.ldp; v.rlim = it.rlim; v.clim = it.clim; v.poff = it.poff;
@@ -260,6 +261,7 @@ __device__ __forceinline__ uint32_t chunk_idesc(const MmaArgs &a, int c, int im)
 
 // Persistent: CTA b takes tiles b, b + gridDim.x, ... Every role walks the same
 // sequence of (tile, level l, pair p, chunk c, K-block kb).
+template <bool ITEMS>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, MmaArgs args)
 {
@@ -309,12 +311,12 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             int issued = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < args.nitems && ok; item += gridDim.x) {
-                const ItemView v = get_item(args, item);
+                const ItemView v = get_item<ITEMS>(args, item);
                 for (int l = v.lb; l < v.le && ok; ++l)
                     for (int p = 0; p <= l && ok; ++p) {
                         const int q = l - p;
                         for (int c = 0; c < v.nch && ok; ++c)
-                            for (int kb = 0; kb < (c == v.nch - 1 ? v.kbl : KB_PER_CHUNK); ++kb) {
+                            for (int kb = 0; kb < (ITEMS && c == v.nch - 1 ? v.kbl : KB_PER_CHUNK); ++kb) {
                                 if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1, abort)) { ok = false; break; }
                                 const uint32_t fb = smem_u32(&full[stage]);
                                 mbar_expect_tx(fb, A_BYTES + B_BYTES);
@@ -343,12 +345,13 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             int t = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < args.nitems && ok; item += gridDim.x) {
-                const ItemView v = get_item(args, item);
+                const ItemView v = get_item<ITEMS>(args, item);
                 // one accumulator per (pair group, chunk); a group holds v.ppa pairs
                 // (more than one only for one-chunk items, whose order of loads is
                 // then the same pair by pair)
+                const int ppa = ITEMS ? v.ppa : 1;
                 for (int l = v.lb; l < v.le && ok; ++l)
-                    for (int p0 = 0; p0 <= l && ok; p0 += v.ppa)
+                    for (int p0 = 0; p0 <= l && ok; p0 += ppa)
                         for (int c = 0; c < v.nch && ok; ++c) {
                             const uint32_t idesc = chunk_idesc(args, c, v.im);
                             const int b = t & 1;
@@ -356,9 +359,9 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                             if (!mbar_wait(smem_u32(&acce[b]), aph ^ 1, abort)) { ok = false; break; }
                             tc_fence_after();
                             const uint32_t dt = tmem + (uint32_t)(b * BN);
-                            const int p1 = min(p0 + v.ppa, l + 1);
+                            const int p1 = min(p0 + ppa, l + 1);
                             for (int p = p0; p < p1 && ok; ++p)
-                                for (int kb = 0; kb < (c == v.nch - 1 ? v.kbl : KB_PER_CHUNK); ++kb) {
+                                for (int kb = 0; kb < (ITEMS && c == v.nch - 1 ? v.kbl : KB_PER_CHUNK); ++kb) {
                                     if (!mbar_wait(smem_u32(&full[stage]), phase, abort)) { ok = false; break; }
                                     tc_fence_after();
                                     const uint64_t ad = sdesc_sw128(smem_u32(tileA + stage * A_BYTES));
@@ -388,13 +391,13 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         int t = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < args.nitems && ok; item += gridDim.x) {
-            const ItemView v = get_item(args, item);
+            const ItemView v = get_item<ITEMS>(args, item);
             const int jl = lg * 32 + lane;                        // plane column from the tile's origin
             for (int l = v.lb; l < v.le && ok; ++l) {
 #pragma unroll
                 for (int c = 0; c < BN / 2; ++c) acc[c] = 0u;
                 uint32_t count = 0;
-                for (int p0 = 0; p0 <= l && ok; p0 += v.ppa)
+                for (int p0 = 0; p0 <= l && ok; p0 += (ITEMS ? v.ppa : 1))
                     for (int c = 0; c < v.nch; ++c) {
                         const int b = t & 1;
                         const uint32_t aph = (t >> 1) & 1;
@@ -421,7 +424,7 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     }
                 if (!ok) break;
                 const uint32_t bias = count * 0x4B400000u;
-                if (jl < v.clim) {
+                if (!ITEMS || jl < v.clim) {
                     int32_t *dst = args.planes + (size_t)l * args.pstride + (size_t)v.poff + (size_t)jl * v.ldp +
                                    (size_t)(half * (BN / 2));
                     const int rmax = v.rlim - half * (BN / 2);   // region rows come in multiples of 4
@@ -429,7 +432,7 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     for (int c = 0; c < BN / 2; c += 4) {
                         const int4 x4 = make_int4((int)(acc[c] - bias), (int)(acc[c + 1] - bias),
                                                   (int)(acc[c + 2] - bias), (int)(acc[c + 3] - bias));
-                        if (c < rmax) *reinterpret_cast<int4 *>(dst + c) = x4;
+                        if (!ITEMS || c < rmax) *reinterpret_cast<int4 *>(dst + c) = x4;
                     }
                 }
             }
@@ -734,6 +737,15 @@ int level_groups(int s, int active, int sms, int *lvl)
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
+cudaError_t set_mma_smem()
+{
+    cudaError_t e = cudaFuncSetAttribute(ozaki_mma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ozaki_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    return e;
+}
+
 cudaError_t encode_digits_map(void *map, void *base, int rows, int Kmax, int box_rows)
 {
     if (!g_encode) {
@@ -780,12 +792,15 @@ cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx)
         if (e == cudaSuccess) e = encode_digits_map(sl.map_i, sl.dig, sl.cap * w.Pmax, w.Kmax, BN);
     }
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ozaki_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        e = set_mma_smem();
     return e;
 }
 
 void ozaki_free(OzakiWork &w)
 {
+    for (auto &e : w.tev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+    w.tuned.clear();
     cudaFree(w.planes);
     cudaFree(w.vmax);
     w.planes = nullptr;
@@ -900,13 +915,44 @@ sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
     a.pstride = (size_t)parts * w.Pmax * w.Pmax;
     a.flags = flags;
     a.nact = (int)active;
-    a.groups = level_groups(s, (int)active, sms, a.lvl);
-    a.nitems = a.nact * a.groups;
-    const int grid = (int)std::min<long long>(a.nitems, sms);
     // MMA "A" (TMEM lanes) = column-side digits, MMA "B" = row-side digits
-    ozaki_mma_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.slot[rows].map_i,
-                                                            *(const CUtensorMap *)w.slot[cols].map_j, a);
-    SR_CUDA_TRY(cudaGetLastError());
+    auto launch = [&](int G) {
+        a.groups = G;
+        split_levels(s, G, a.lvl);
+        a.nitems = a.nact * a.groups;
+        const int grid = (int)std::min<long long>(a.nitems, sms);
+        ozaki_mma_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.slot[rows].map_i,
+                                                                       *(const CUtensorMap *)w.slot[cols].map_j, a);
+        return cudaGetLastError();
+    };
+    const long long key = active | (long long)s << 24 | (long long)a.nch << 32 | (long long)parts << 48;
+    int G = -1;
+    for (const auto &t : w.tuned)
+        if (t.key == key) G = t.groups;
+    if (G < 0) {
+        int lvl[kOzakiMaxSlicesDD + 1];
+        G = level_groups(s, (int)active, sms, lvl);   // the makespan estimate
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (w.autotune && cs == cudaStreamCaptureStatusNone) {
+            // time every candidate split twice (each launch rewrites the same planes)
+            if (!w.tev[0]) SR_CUDA_TRY(cudaEventCreate(&w.tev[0]));
+            if (!w.tev[1]) SR_CUDA_TRY(cudaEventCreate(&w.tev[1]));
+            float best = -1.f;
+            for (int cand = 1; cand <= std::min(s, 4); ++cand)
+                for (int rep = 0; rep < 2; ++rep) {
+                    SR_CUDA_TRY(cudaEventRecord(w.tev[0], st));
+                    SR_CUDA_TRY(launch(cand));
+                    SR_CUDA_TRY(cudaEventRecord(w.tev[1], st));
+                    SR_CUDA_TRY(cudaEventSynchronize(w.tev[1]));
+                    float ms = 0.f;
+                    SR_CUDA_TRY(cudaEventElapsedTime(&ms, w.tev[0], w.tev[1]));
+                    if (rep == 1 && (best < 0.f || ms < best)) { best = ms; G = cand; }
+                }
+        }
+        w.tuned.push_back({key, G});
+    }
+    SR_CUDA_TRY(launch(G));
     return SR_OK;
 }
 
@@ -933,7 +979,7 @@ cudaError_t ozaki_alloc_group(OzakiWork &w, int rows, int kmax, const int *caps,
         if (e == cudaSuccess) e = encode_digits_map(sl.map_i, sl.dig, sl.cap * w.Pmax, w.Kmax, BN);
     }
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ozaki_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        e = set_mma_smem();
     return e;
 }
 
@@ -984,8 +1030,8 @@ sr_status ozaki_product_items(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(nitems, sms > 0 ? sms : 1);
-    ozaki_mma_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.slot[rows].map_i,
-                                                            *(const CUtensorMap *)w.slot[cols].map_j, a);
+    ozaki_mma_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.slot[rows].map_i,
+                                                                  *(const CUtensorMap *)w.slot[cols].map_j, a);
     SR_CUDA_TRY(cudaGetLastError());
     return SR_OK;
 }

@@ -38,6 +38,7 @@
 #pragma once
 #include <climits>
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 
@@ -75,6 +76,13 @@ struct OzakiWork {
     OzakiSlot slot[kOzakiSlots];
     int levels = 0;                        // level planes held (the largest slot capacity, at least 7)
     long long pstride_group = 0;           // grouped work area: elements per level plane
+    // autotuner of the slice products' work split: the level-group count chosen
+    // for each product shape (active tiles, digits, K-chunks, parts) by timing
+    // the candidates on its first launch
+    struct Tuned { long long key; int groups; };
+    std::vector<Tuned> tuned;
+    bool autotune = false;
+    cudaEvent_t tev[2] = {nullptr, nullptr};
     int32_t *planes = nullptr;             // [levels][Pmax (2 Pmax if cplx) cols][Pmax rows]
     unsigned long long *vmax = nullptr;    // per-vector largest |x| (bit pattern) during a split
 };

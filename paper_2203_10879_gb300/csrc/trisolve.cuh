@@ -74,8 +74,9 @@ void trisolve_plan_group(const std::vector<int> &orders, std::vector<unsigned lo
                          std::vector<long long> &offsets, std::vector<long long> &nleaf);
 
 // ---- contributions of subdiagonal t+1 to tiles with D < t --------------------
-// 128 threads; thread (tx, ty) owns the 4 x 2 block rows 4tx.., columns 2ty..,
-// read with vector loads from shared memory.
+// 64 threads; thread (tx, ty) owns the 4 x 4 block rows 4tx.., columns 4ty..,
+// read with vector loads from shared memory (4 vector loads per 32 FMAs).
+constexpr int kUpdThreads = 64;
 template <typename T> struct SolveVec;
 template <> struct SolveVec<float> {
     __device__ static void ld4(const float *p, float (&v)[4])
@@ -129,12 +130,12 @@ template <> struct SolveVec<cd> {
 };
 
 template <typename T, bool GROUP = false>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kUpdThreads)
 trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t *__restrict__ plan,
                        const SolveMat *__restrict__ mats = nullptr,
                        const unsigned long long *__restrict__ gplan = nullptr)
 {
-    constexpr int B = kSolveTile, SA = B + 4, SB = B + 2;
+    constexpr int B = kSolveTile, SA = B + 4, SB = B + 4;
     uint32_t tile;
     if constexpr (GROUP) {
         const unsigned long long g = gplan[blockIdx.x];
@@ -155,39 +156,39 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
     __shared__ __align__(16) T Ta[2][B][SA];   // left operands, transposed: Ta[u][k][row]
     __shared__ __align__(16) T Tb[2][B][SB];   // right operands: Tb[u][k][col]
     const int tid = threadIdx.x;
-    const int lx = tid & 31, ly = tid >> 5;   // load mapping: element (lx, ly + 4q), q = 0..7
-    const int tx = tid & 7, ty = tid >> 3;    // block rows 4tx.., columns 2ty..
+    const int lx = tid & 31, ly = tid >> 5;   // load mapping: element (lx, ly + 2q), q = 0..15
+    const int tx = tid & 7, ty = tid >> 3;    // block rows 4tx.., columns 4ty..
     const T Z = SrNum<T>::zero();
     const bool hasP = J + d < NB, hasM = I - d >= 0;
     const int kP = (J + d) * B, kM = (I - d) * B;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int y = ly + 4 * q;
+    for (int q = 0; q < 16; ++q) {
+        const int y = ly + 2 * q;
         Ta[0][y][lx] = (hasP && r0 + lx < n && kP + y < n) ? TE[sr_idx(r0 + lx, kP + y, ld)] : Z;
         Tb[0][lx][y] = (hasP && kP + lx < n && c0 + y < n) ? TE[sr_idx(kP + lx, c0 + y, ld)] : Z;
         Ta[1][y][lx] = (hasM && r0 + lx < n && kM + y < n) ? TE[sr_idx(r0 + lx, kM + y, ld)] : Z;
         Tb[1][lx][y] = (hasM && kM + lx < n && c0 + y < n) ? TE[sr_idx(kM + lx, c0 + y, ld)] : Z;
     }
-    T acc[4][2];
+    T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int x = 4 * tx + i, y = 2 * ty + j;
+        for (int j = 0; j < 4; ++j) {
+            const int x = 4 * tx + i, y = 4 * ty + j;
             acc[i][j] = (x < nr && y < nc && (D > 0 || x > y)) ? TE[sr_idx(r0 + x, c0 + y, ld)] : Z;
         }
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < B; ++k) {
-        T a[4], b[2], m[4], c[2];
+        T a[4], b[4], m[4], c[4];
         SolveVec<T>::ld4(&Ta[0][k][4 * tx], a);
-        SolveVec<T>::ld2(&Tb[0][k][2 * ty], b);
+        SolveVec<T>::ld4(&Tb[0][k][4 * ty], b);
         SolveVec<T>::ld4(&Ta[1][k][4 * tx], m);
-        SolveVec<T>::ld2(&Tb[1][k][2 * ty], c);
+        SolveVec<T>::ld4(&Tb[1][k][4 * ty], c);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < 4; ++j) {
                 acc[i][j] = sr_fma(a[i], b[j], acc[i][j]);
                 acc[i][j] = sr_fma(-m[i], c[j], acc[i][j]);
             }
@@ -195,8 +196,8 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int x = 4 * tx + i, y = 2 * ty + j;
+        for (int j = 0; j < 4; ++j) {
+            const int x = 4 * tx + i, y = 4 * ty + j;
             if (x < nr && y < nc && (D > 0 || x > y)) TE[sr_idx(r0 + x, c0 + y, ld)] = acc[i][j];
         }
 }
@@ -328,7 +329,7 @@ inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEven
         const long long nupd = offsets[l + 1] - offsets[l] - nleaf;
         trisolve_leaf_kernel<T><<<(unsigned)nleaf, 1024, 0, st>>>(n, TE, ld, dhp, dlo, t, plan + offsets[l], flags);
         if (nupd > 0)
-            trisolve_update_kernel<T><<<(unsigned)nupd, 128, 0, aux>>>(n, TE, ld, t, plan + offsets[l] + nleaf);
+            trisolve_update_kernel<T><<<(unsigned)nupd, kUpdThreads, 0, aux>>>(n, TE, ld, t, plan + offsets[l] + nleaf);
         e = cudaGetLastError();
         // both kernels of this step finish before either of the next starts
         if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
@@ -357,8 +358,8 @@ inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cu
             trisolve_leaf_kernel<T, true><<<(unsigned)nl, 1024, 0, st>>>(0, nullptr, 0, nullptr, nullptr, t, nullptr,
                                                                         flags, mats, plan + offsets[l]);
         if (nupd > 0)
-            trisolve_update_kernel<T, true><<<(unsigned)nupd, 128, 0, aux>>>(0, nullptr, 0, t, nullptr, mats,
-                                                                            plan + offsets[l] + nl);
+            trisolve_update_kernel<T, true><<<(unsigned)nupd, kUpdThreads, 0, aux>>>(0, nullptr, 0, t, nullptr, mats,
+                                                                                    plan + offsets[l] + nl);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
         if (e == cudaSuccess) e = cudaEventRecord(ev1, aux);

@@ -166,3 +166,23 @@ def test_refine_ozaki_full_sigma(torch):
     cT, cQ = oracle.residuals_dd(p.A, Q)
     assert cT <= tol and cQ <= tol
     assert np.max(np.abs(sign_align(Q, ref.Q) - ref.Q)) <= 1e-9
+
+
+def test_autotuned_work_split_gives_identical_results(torch):
+    # the level groups of the slice products write disjoint exact integer planes:
+    # whichever split the autotuner keeps, the refinement is bit-for-bit the same
+    p = inputs.jittered_real(1000)
+    out = []
+    for tune in (0, 1):
+        st, h = B.schur_refine_create(1000, B.default_options(hp_gemm=B.SR_HP_OZAKI_BF16, lp=B.SR_LP_FP32,
+                                                              tune=tune), None)
+        assert st == B.SR_OK
+        try:
+            Q = torch.zeros((1000, 1000), dtype=torch.float64, device="cuda").t()
+            s, nr = B.schur_refine_step(h, 1000, to_dev(p.A), Q, to_dev(p.Qhat))
+            s2, nr2 = B.schur_refine_step(h, 1000, to_dev(p.A), Q, to_dev(p.Qhat))   # tuned shapes reused
+            assert s == s2 == B.SR_OK and nr.iters == nr2.iters
+            out.append(from_dev(Q))
+        finally:
+            B.schur_refine_destroy(h)
+    assert np.array_equal(out[0], out[1])
