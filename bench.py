@@ -45,6 +45,19 @@ OZ_MMA_TRAFFIC_BYTES_N4096 = 5.787937e9 + 0.4733504e9
 OZ_MMA_TRAFFIC_BYTES_DD2048 = 1.619892e9 + 0.2217213e9
 
 
+def phase_rooflines(prof, steps):
+    """Per-phase achieved rates from the library's profile (algorithmic flops and
+    bytes of each phase over its CUDA-event time)."""
+    out = {}
+    for k, v in prof.items():
+        if v["ms"] <= 0:
+            continue
+        sec = v["ms"] * 1e-3
+        out[k] = {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] / steps,
+                  "tflops": v["flops"] / sec / 1e12, "gbs": v["bytes"] / sec / 1e9}
+    return out
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -401,6 +414,7 @@ def run_ours(args):
                    "mixed_vs_all_fp64_speedup": None if ms64 is None else ms64 / ms,
                    "mixed_native_fp64_s": None if mixed_native_ms is None else mixed_native_ms / 1e3,
                    "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
+                   "phase_rates": phase_rooflines(prof, args.steps),
                    "all_fp64_phase_ms_per_step": {k: v["ms"] / k64 for k, v in prof64.items() if v["ms"] > 0},
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
@@ -637,6 +651,7 @@ def run_dd(args):
                    "simt_dd_s": ms64 / 1e3, "simt_dd_status": st64, "simt_dd_iters": nr64.iters,
                    "emulated_vs_simt_dd_speedup": ms64 / ms,
                    "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
+                   "phase_rates": phase_rooflines(prof, args.steps),
                    "simt_dd_phase_ms_per_step": {k: v["ms"] / k64 for k, v in prof64.items() if v["ms"] > 0},
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,

@@ -297,10 +297,9 @@ Grids add_grids(DescPack &pk, const std::vector<int> &order, const std::vector<i
     std::vector<int> s32(m + 1, 0), smax(m + 1, 0), sdig(m + 1, 0);
     for (int a = 0; a < m; ++a) {
         const int nb = n[order[a]], g = (nb + 31) / 32;
-        const int kp = (nb + sr::kOzakiKChunk - 1) / sr::kOzakiKChunk * sr::kOzakiKChunk;
         s32[a + 1] = s32[a] + g * g;
         smax[a + 1] = smax[a] + g * ((nb + 255) / 256);   // absmax blocks cover 256 of K
-        sdig[a + 1] = sdig[a] + g * (kp / 64);             // digit blocks cover 64 of K
+        sdig[a + 1] = sdig[a] + g * ((nb + 63) / 64);     // digit blocks cover 64 of K (up to the order)
     }
     Grids G;
     G.o32 = pk.add(s32);

@@ -621,7 +621,9 @@ ozaki_digits_group_kernel(const SplitMat *__restrict__ mats, const int *__restri
 {
     const int a = group_find(start, m, blockIdx.x);
     const SplitMat g = mats[a];
-    const int Kp = (g.K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    // work items stop their last K-chunk at the order rounded to 64 (MmaItem::kbl):
+    // digits past that are never read
+    const int Kp = (g.K + 63) / 64 * 64;
     const int local = blockIdx.x - start[a], gx = (g.R + 31) / 32;
     digits_body<double, LAYOUT>(local % gx, local / gx, g.R, g.K, INT_MAX, Kp, g.X, g.ld, s, Pmax, Kmax,
                                 vmax + g.row0, out + (size_t)g.row0 * Kmax, exps + g.row0);

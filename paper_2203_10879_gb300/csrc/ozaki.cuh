@@ -127,7 +127,7 @@ struct CombMat {
 struct GroupSplit {
     const SplitMat *mats;
     const int *start_max;   // absmax blocks: ceil(R/32) x ceil(K/256) per matrix
-    const int *start_dig;   // digit blocks: ceil(R/32) x ceil(Kp/64) per matrix
+    const int *start_dig;   // digit blocks: ceil(R/32) x ceil(K/64) per matrix
     int m, total_max, total_dig, maxK;
 };
 
@@ -190,17 +190,56 @@ __device__ inline double oz_scale(double v, int e)
     return oz_pow2_scale(v, e);
 }
 
-// one rebuilt entry: 2^e * sign * sum_l I_l 2^(-14-8l) (levels 0..3 in one
-// 64-bit Horner sum, the rest in a second; exact integers until the two
-// FP64 conversions and the final fused multiply-add)
-__device__ __forceinline__ double oz_rebuild(const int32_t *__restrict__ planes, size_t off, size_t pstride, int s,
-                                             double sh, double sl, int e)
+// m * 2^x as a double for 2^52 <= m < 2^53 (the leading bit at 52), built
+// from its fields when the result is normal, else by two exact scalings
+__device__ __forceinline__ double oz_make_double(unsigned long long m, int x, bool neg)
 {
-    const int nh = s < 4 ? s : 4;
-    long long H = 0, Lo = 0;
-    for (int l = 0; l < nh; ++l) H = H * 256 + (long long)planes[off + (size_t)l * pstride];
-    for (int l = nh; l < s; ++l) Lo = Lo * 256 + (long long)planes[off + (size_t)l * pstride];
-    return oz_scale(fma((double)Lo, sl, (double)H * sh), e);
+    const int E = x + 52 + 1023;
+    if (E >= 1 && E <= 2046) {
+        const unsigned long long b = ((unsigned long long)E << 52) | (m & 0xfffffffffffffull);
+        return __longlong_as_double((long long)(neg ? (b | 0x8000000000000000ull) : b));
+    }
+    const double v = oz_pow2_scale((double)m, x);
+    return neg ? -v : v;
+}
+
+// bit index of the leading one of M > 0
+__device__ __forceinline__ int oz_msb(unsigned __int128 M)
+{
+    const unsigned long long hw = (unsigned long long)(M >> 64), lw = (unsigned long long)M;
+    return hw ? 127 - __clzll((long long)hw) : 63 - __clzll((long long)lw);
+}
+
+// V * 2^x rounded once to the nearest double (ties away from zero): integer
+// work only, the fields of the result built directly
+__device__ __forceinline__ double oz_i128_to_double(__int128 V, int x)
+{
+    if (V == 0) return 0.0;
+    const bool neg = V < 0;
+    unsigned __int128 M = neg ? (unsigned __int128)(-V) : (unsigned __int128)V;
+    int sh = oz_msb(M) - 52;
+    unsigned long long m;
+    if (sh <= 0) {
+        m = (unsigned long long)M << (-sh);
+    } else {
+        M += (unsigned __int128)1 << (sh - 1);        // half a unit of the last kept bit
+        if ((M >> (sh + 53)) != 0) ++sh;              // the rounding carried into a new leading bit
+        m = (unsigned long long)(M >> sh);
+    }
+    return oz_make_double(m, sh + x, neg);
+}
+
+// One rebuilt entry: (-1)^neg 2^e sum_l I_l 2^(-14-8l). The s <= 7 level sums
+// are added exactly in a 128-bit integer, V = sum_l I_l 256^(s-1-l) (|V| < 2^80
+// for level sums below 2^31), and V 2^(e - 14 - 8(s-1)) is rounded once to a
+// double without FP64 instructions (the combine is otherwise bound by the FP64
+// pipe, the scarcest unit of this GPU).
+__device__ __forceinline__ double oz_rebuild(const int32_t *__restrict__ planes, size_t off, size_t pstride, int s,
+                                             bool neg, int e)
+{
+    __int128 V = 0;
+    for (int l = 0; l < s; ++l) V = V * 256 + (__int128)planes[off + (size_t)l * pstride];
+    return oz_i128_to_double(neg ? -V : V, e - 14 - 8 * (s - 1));
 }
 
 // C(i,j) = sign * (rebuilt product); ep as in gemm_simt.cuh (a complex value
@@ -214,9 +253,7 @@ ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, in
 {
     const int i = blockIdx.x * 32 + (threadIdx.x & 31);
     const int jb = blockIdx.y * 32 + (threadIdx.x >> 5);
-    const int nh = s < 4 ? s : 4;
-    const double sh = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (nh - 1)) << 52);
-    const double sl = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (s - 1)) << 52);
+    const bool neg = sign < 0;
     double part = 0.0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
@@ -227,9 +264,9 @@ ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, in
             const int e1 = ea[i], e2 = fb[j];
             const bool bad = e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite;
             const double nan = __longlong_as_double(0x7ff8000000000000LL);
-            const double re = bad ? nan : oz_rebuild(planes, off, pstride, s, sh, sl, e1 + e2);
+            const double re = bad ? nan : oz_rebuild(planes, off, pstride, s, neg, e1 + e2);
             if constexpr (CPLX) {
-                double im = bad ? nan : oz_rebuild(planes, off + imoff, pstride, s, sh, sl, e1 + e2);
+                double im = bad ? nan : oz_rebuild(planes, off + imoff, pstride, s, neg, e1 + e2);
                 if (mir) im = -im;
                 part += ep(i, j, cd{re, im});
             } else {
@@ -245,18 +282,6 @@ ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, in
 
 inline int ozaki_blocks(int m, int n) { return ((m + 31) / 32) * ((n + 31) / 32); }
 
-// m * 2^x as a double for 2^52 <= m < 2^53 (the leading bit at 52), built
-// from its fields when the result is normal, else by two exact scalings
-__device__ __forceinline__ double oz_make_double(unsigned long long m, int x, bool neg)
-{
-    const int E = x + 52 + 1023;
-    if (E >= 1 && E <= 2046) {
-        const unsigned long long b = ((unsigned long long)E << 52) | (m & 0xfffffffffffffull);
-        return __longlong_as_double((long long)(neg ? (b | 0x8000000000000000ull) : b));
-    }
-    const double v = oz_pow2_scale((double)m, x);
-    return neg ? -v : v;
-}
 
 // the leading 53 bits of M > 0 as m * 2^sh (m in [2^52, 2^53); sh may be
 // negative) and the remainder M - m 2^sh (zero when sh <= 0)
@@ -397,9 +422,7 @@ ozaki_combine_group_kernel(int s, const int32_t *__restrict__ planes, size_t pst
     const int i = (local % gx) * 32 + (threadIdx.x & 31);
     const int jb = (local / gx) * 32 + (threadIdx.x >> 5);
     const EP ep = eps[a];
-    const int nh = s < 4 ? s : 4;
-    const double sh = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (nh - 1)) << 52);
-    const double sl = sign * __longlong_as_double((long long)(1023 - 14 - 8 * (s - 1)) << 52);
+    const bool neg = sign < 0;
     double part = 0.0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
@@ -411,7 +434,7 @@ ozaki_combine_group_kernel(int s, const int32_t *__restrict__ planes, size_t pst
             const int e1 = ea[cm.ra + i], e2 = fb[cm.rb + j];
             const bool bad = e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite;
             const double nan = __longlong_as_double(0x7ff8000000000000LL);
-            part += ep(i, j, bad ? nan : oz_rebuild(planes, off, pstride, s, sh, sl, e1 + e2));
+            part += ep(i, j, bad ? nan : oz_rebuild(planes, off, pstride, s, neg, e1 + e2));
         }
     }
     if (partial) {

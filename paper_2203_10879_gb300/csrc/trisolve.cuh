@@ -74,9 +74,15 @@ void trisolve_plan_group(const std::vector<int> &orders, std::vector<unsigned lo
                          std::vector<long long> &offsets, std::vector<long long> &nleaf);
 
 // ---- contributions of subdiagonal t+1 to tiles with D < t --------------------
-// 64 threads; thread (tx, ty) owns the 4 x 4 block rows 4tx.., columns 4ty..,
-// read with vector loads from shared memory (4 vector loads per 32 FMAs).
-constexpr int kUpdThreads = 64;
+// Thread (tx, ty) owns the 4 x TN block rows 4tx.., columns TN*ty.., read with
+// vector loads from shared memory: TN = 4 (64 threads, 4 vector loads per 32
+// FMAs; shared-memory bandwidth bounds the FP32 update) except for FP64, whose
+// update is bound by the FP64 pipe and keeps TN = 2 with 128 threads for more
+// warps in flight.
+template <typename T> struct UpdShape {
+    static constexpr int TN = SrNum<T>::kind == 1 ? 2 : 4;
+    static constexpr int NT = 8 * (32 / TN);
+};
 template <typename T> struct SolveVec;
 template <> struct SolveVec<float> {
     __device__ static void ld4(const float *p, float (&v)[4])
@@ -130,7 +136,7 @@ template <> struct SolveVec<cd> {
 };
 
 template <typename T, bool GROUP = false>
-__global__ void __launch_bounds__(kUpdThreads)
+__global__ void __launch_bounds__(UpdShape<T>::NT)
 trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t *__restrict__ plan,
                        const SolveMat *__restrict__ mats = nullptr,
                        const unsigned long long *__restrict__ gplan = nullptr)
@@ -155,40 +161,46 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
     const int d = t + 1;
     __shared__ __align__(16) T Ta[2][B][SA];   // left operands, transposed: Ta[u][k][row]
     __shared__ __align__(16) T Tb[2][B][SB];   // right operands: Tb[u][k][col]
+    constexpr int TN = UpdShape<T>::TN, NT = UpdShape<T>::NT, LR = NT / 32;
     const int tid = threadIdx.x;
-    const int lx = tid & 31, ly = tid >> 5;   // load mapping: element (lx, ly + 2q), q = 0..15
-    const int tx = tid & 7, ty = tid >> 3;    // block rows 4tx.., columns 4ty..
+    const int lx = tid & 31, ly = tid >> 5;   // load mapping: element (lx, ly + LR q)
+    const int tx = tid & 7, ty = tid >> 3;    // block rows 4tx.., columns TN ty..
     const T Z = SrNum<T>::zero();
     const bool hasP = J + d < NB, hasM = I - d >= 0;
     const int kP = (J + d) * B, kM = (I - d) * B;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const int y = ly + 2 * q;
+    for (int q = 0; q < 32 / LR; ++q) {
+        const int y = ly + LR * q;
         Ta[0][y][lx] = (hasP && r0 + lx < n && kP + y < n) ? TE[sr_idx(r0 + lx, kP + y, ld)] : Z;
         Tb[0][lx][y] = (hasP && kP + lx < n && c0 + y < n) ? TE[sr_idx(kP + lx, c0 + y, ld)] : Z;
         Ta[1][y][lx] = (hasM && r0 + lx < n && kM + y < n) ? TE[sr_idx(r0 + lx, kM + y, ld)] : Z;
         Tb[1][lx][y] = (hasM && kM + lx < n && c0 + y < n) ? TE[sr_idx(kM + lx, c0 + y, ld)] : Z;
     }
-    T acc[4][4];
+    T acc[4][TN];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int x = 4 * tx + i, y = 4 * ty + j;
+        for (int j = 0; j < TN; ++j) {
+            const int x = 4 * tx + i, y = TN * ty + j;
             acc[i][j] = (x < nr && y < nc && (D > 0 || x > y)) ? TE[sr_idx(r0 + x, c0 + y, ld)] : Z;
         }
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < B; ++k) {
-        T a[4], b[4], m[4], c[4];
+        T a[4], b[TN], m[4], c[TN];
         SolveVec<T>::ld4(&Ta[0][k][4 * tx], a);
-        SolveVec<T>::ld4(&Tb[0][k][4 * ty], b);
         SolveVec<T>::ld4(&Ta[1][k][4 * tx], m);
-        SolveVec<T>::ld4(&Tb[1][k][4 * ty], c);
+        if constexpr (TN == 4) {
+            SolveVec<T>::ld4(&Tb[0][k][4 * ty], b);
+            SolveVec<T>::ld4(&Tb[1][k][4 * ty], c);
+        } else {
+            SolveVec<T>::ld2(&Tb[0][k][2 * ty], b);
+            SolveVec<T>::ld2(&Tb[1][k][2 * ty], c);
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < TN; ++j) {
                 acc[i][j] = sr_fma(a[i], b[j], acc[i][j]);
                 acc[i][j] = sr_fma(-m[i], c[j], acc[i][j]);
             }
@@ -196,8 +208,8 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int x = 4 * tx + i, y = 4 * ty + j;
+        for (int j = 0; j < TN; ++j) {
+            const int x = 4 * tx + i, y = TN * ty + j;
             if (x < nr && y < nc && (D > 0 || x > y)) TE[sr_idx(r0 + x, c0 + y, ld)] = acc[i][j];
         }
 }
@@ -329,7 +341,7 @@ inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEven
         const long long nupd = offsets[l + 1] - offsets[l] - nleaf;
         trisolve_leaf_kernel<T><<<(unsigned)nleaf, 1024, 0, st>>>(n, TE, ld, dhp, dlo, t, plan + offsets[l], flags);
         if (nupd > 0)
-            trisolve_update_kernel<T><<<(unsigned)nupd, kUpdThreads, 0, aux>>>(n, TE, ld, t, plan + offsets[l] + nleaf);
+            trisolve_update_kernel<T><<<(unsigned)nupd, UpdShape<T>::NT, 0, aux>>>(n, TE, ld, t, plan + offsets[l] + nleaf);
         e = cudaGetLastError();
         // both kernels of this step finish before either of the next starts
         if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
@@ -358,7 +370,7 @@ inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cu
             trisolve_leaf_kernel<T, true><<<(unsigned)nl, 1024, 0, st>>>(0, nullptr, 0, nullptr, nullptr, t, nullptr,
                                                                         flags, mats, plan + offsets[l]);
         if (nupd > 0)
-            trisolve_update_kernel<T, true><<<(unsigned)nupd, kUpdThreads, 0, aux>>>(0, nullptr, 0, t, nullptr, mats,
+            trisolve_update_kernel<T, true><<<(unsigned)nupd, UpdShape<T>::NT, 0, aux>>>(0, nullptr, 0, t, nullptr, mats,
                                                                                     plan + offsets[l] + nl);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
