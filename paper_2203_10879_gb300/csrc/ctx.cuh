@@ -41,6 +41,11 @@ struct schur_refine_ctx {
     std::vector<cudaStream_t> sub_streams;
     cudaEvent_t bfork = nullptr;
     std::vector<cudaEvent_t> bjoin;
+    // emulated pass: the Gram product Y = Q^H Q - I runs on gram_st while the
+    // solve runs on st (its block sums go to partial2)
+    cudaStream_t gram_st = nullptr;
+    cudaEvent_t gev0 = nullptr, gev1 = nullptr;
+    double *partial2 = nullptr;
     // graph mode (opt.graph): the refinement captured once per (order, buffers)
     // as one graph with device-side stop tests; capturing = true while it is built
     bool capturing = false;

@@ -383,16 +383,44 @@ template <> struct OzT<true> {
 };
 
 // Y = Q^H Q - I from the column digits of Q in slot OZS_COLS; ||Y||^2 -> dnorm[1]
+// (block sums in `partial`: h->partial, or h->partial2 when it runs beside the solve)
 template <bool C>
-sr_status oz_gram(schur_refine_ctx *h, int n)
+sr_status oz_gram(schur_refine_ctx *h, int n, double *partial = nullptr)
 {
     using H = typename OzT<C>::H;
     const int s = oz_s(h);
+    if (!partial) partial = h->partial;
     int blocks = 0;
     SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_COLS, n, n, n, s, true, h->dflags));
     SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_COLS, n, n, s, 1.0, true,
-                             typename OzT<C>::MinusI{(H *)h->Y, h->nmax}, h->partial, &blocks));
-    return reduce_to(h, blocks, 1);
+                             typename OzT<C>::MinusI{(H *)h->Y, h->nmax}, partial, &blocks));
+    SrPhase ph(h, SR_PROF_OTHER, 0, (long long)blocks * 8, 1);
+    sr::reduce_partials_kernel<<<1, 256, 0, h->st>>>(partial, blocks, h->dnorm + 1);
+    SR_CUDA_TRY(cudaGetLastError());
+    return SR_OK;
+}
+
+// Starts the Gram product on gram_st after the work on st so far; the solve
+// then runs on st beside it (the two share no buffer). oz_gram_join orders st
+// after it again.
+template <bool C>
+sr_status oz_gram_fork(schur_refine_ctx *h, int n)
+{
+    SR_CUDA_TRY(cudaEventRecord(h->gev0, h->st));
+    SR_CUDA_TRY(cudaStreamWaitEvent(h->gram_st, h->gev0, 0));
+    cudaStream_t saved = h->st;
+    h->st = h->gram_st;   // the phases' timing events follow the work
+    const sr_status r = oz_gram<C>(h, n, h->partial2);
+    h->st = saved;
+    SR_TRY(r);
+    SR_CUDA_TRY(cudaEventRecord(h->gev1, h->gram_st));
+    return SR_OK;
+}
+
+sr_status oz_gram_join(schur_refine_ctx *h)
+{
+    SR_CUDA_TRY(cudaStreamWaitEvent(h->st, h->gev1, 0));
+    return SR_OK;
 }
 
 // Q_new = Q + alpha * Q X (rows of Q, columns of X)
@@ -437,7 +465,7 @@ sr_status oz_form_residual(schur_refine_ctx *h, int n, const void *Q, int ldq, v
 }
 
 template <bool C>
-sr_status oz_update(schur_refine_ctx *h, int n, const void *Q, int ldq, void *Qn, int ldn)
+sr_status oz_update(schur_refine_ctx *h, int n, const void *Q, int ldq, void *Qn, int ldn, bool gram_done = false)
 {
     using namespace sr;
     using H = typename OzT<C>::H;
@@ -447,7 +475,7 @@ sr_status oz_update(schur_refine_ctx *h, int n, const void *Q, int ldq, void *Qn
     OzakiWork &w = h->oz;
     cudaStream_t st = h->st;
     H *Wd = (H *)h->Wd, *W2d = (H *)h->W2d, *W2Yd = (H *)h->W2Yd, *W2YWd = (H *)h->W2YWd, *Y = (H *)h->Y;
-    SR_TRY(oz_gram<C>(h, n));   // Q unchanged since oz_form_residual: its column digits are current
+    if (!gram_done) SR_TRY(oz_gram<C>(h, n));   // Q unchanged since oz_form_residual: its column digits are current
     {
         SrPhase ph(h, SR_PROF_OTHER, 0, (long long)n * n * (long long)(sizeof(L) + sizeof(H)), 1);
         dim3 grid((n + 31) / 32, (n + 31) / 32);
@@ -556,6 +584,7 @@ sr_status run_step(schur_refine_ctx *h, int n, const void *A, int lda, void *dQ,
         if (rT <= tol && ok_y) { status = SR_OK; break; }
         if (k >= 3 && rT > 10.0 * prev) { status = SR_ERR_NOT_CONVERGED; break; }
         prev = rT;
+        if (oz) SR_TRY(oz_gram_fork<C>(h, n));   // Y = Q^H Q - I beside the solve
         if constexpr (C) {
             SR_TRY(solve<cf>(h, n, (cf *)h->TE, ld, (const cd *)h->diag));
             SR_TRY(sumsq<cf>(h, n, (const cf *)h->TE, ld, 1, 2));
@@ -563,13 +592,14 @@ sr_status run_step(schur_refine_ctx *h, int n, const void *A, int lda, void *dQ,
             SR_TRY(solve<Tl>(h, n, (Tl *)h->TE, ld, h->diag));
             SR_TRY(sumsq<Tl>(h, n, (const Tl *)h->TE, ld, 1, 2));
         }
+        if (oz) SR_TRY(oz_gram_join(h));
         SR_TRY(read_back(h));
         const int f = host_flags(h);
         if (f & SR_FLAG_NONDISTINCT) { status = SR_ERR_NONDISTINCT; break; }
         if (f & SR_FLAG_NONFINITE) { status = SR_ERR_NONFINITE; break; }
         nr.w_norm = sqrt(2.0 * h->hbuf[2]);
         if (oz)
-            SR_TRY(oz_update<C>(h, n, Qc, ldc, Qo, ldo));
+            SR_TRY(oz_update<C>(h, n, Qc, ldc, Qo, ldo, true));
         else if constexpr (!C)
             SR_TRY(update<Tl>(h, n, Qc, ldc, Qo, ldo));
         nr.hp_gemms += 2;
@@ -1222,6 +1252,10 @@ void schur_refine_destroy(schur_refine_t h)
     if (h->sev1) cudaEventDestroy(h->sev1);
     cudaFree(h->plan);
     cudaFree(h->partial);
+    cudaFree(h->partial2);
+    if (h->gram_st) cudaStreamDestroy(h->gram_st);
+    if (h->gev0) cudaEventDestroy(h->gev0);
+    if (h->gev1) cudaEventDestroy(h->gev1);
     cudaFree(h->dnorm);
     cudaFree(h->dflags);
     if (h->hbuf) cudaFreeHost(h->hbuf);
@@ -1303,6 +1337,10 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
             if (e == cudaSuccess && o.full_sigma) e = cudaMalloc((void **)&h->W2YWd, nn * hps);
         }
         if (e == cudaSuccess) e = sr::ozaki_alloc(h->oz, n_max, caps, is_cplx(o));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->partial2, h->npartial * sizeof(double));
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->gram_st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gev0, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gev1, cudaEventDisableTiming);
         h->oz.autotune = o.tune == 1;
     }
     if (e != cudaSuccess) {
