@@ -119,6 +119,17 @@ typedef struct {
                          WHILE / IF nodes), one synchronization per call;
                          same results; the profile (profile = 1) is not
                          recorded in this mode */
+    int solve_mode;   /* triangular solve (Sec. 2.1): 0 (default) = the
+                         dataflow form for single matrices, the stepwise form
+                         for grouped batches (the faster of the two measured
+                         for each); 1 = dataflow always; 2 = stepwise always.
+                         Dataflow: one launch in which the tiles of the
+                         wavefront are claimed in subdiagonal order and each
+                         waits only for the tiles it reads (bounded waits;
+                         SR_ERR_TIMEOUT if one runs out). Stepwise: one
+                         launch pair per block subdiagonal, replayed from a
+                         CUDA graph. Same equations, sums in another order;
+                         complex128 always uses the stepwise form */
 } sr_options;
 
 /* Fills *opt with the defaults: real, FP64 target, native FP64 products,

@@ -151,6 +151,10 @@ struct BatchWork {
     size_t hnorms_cap = 0;
     cudaStream_t aux = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // dataflow solve of the group: ticket, abort and published words; its grid
+    int *flow = nullptr;
+    size_t flow_cap = 0;
+    int flow_ctas = 0;
 };
 
 void sr_batch_free(BatchWork *bw)
@@ -161,6 +165,7 @@ void sr_batch_free(BatchWork *bw)
     for (double *p : bufs) cudaFree(p);
     cudaFree(bw->TE);
     cudaFree(bw->flags);
+    cudaFree(bw->flow);
     cudaFree(bw->ddesc);
     if (bw->hdesc) cudaFreeHost(bw->hdesc);
     if (bw->hnorms) cudaFreeHost(bw->hnorms);
@@ -195,9 +200,29 @@ struct DescPack {
 };
 
 sr_status ensure_capacity(BatchWork *bw, long long elems, int rows, int count, long long planes, int kmax,
-                          size_t npartial)
+                          size_t npartial, size_t flow_words, int dev)
 {
     cudaError_t e = cudaSuccess;
+    if (flow_words > bw->flow_cap) {
+        cudaFree(bw->flow);
+        e = cudaMalloc((void **)&bw->flow, flow_words * sizeof(int));
+        if (e != cudaSuccess) { bw->flow = nullptr; bw->flow_cap = 0; sr_set_last_cuda_error(e); return SR_ERR_OOM; }
+        bw->flow_cap = flow_words;
+    }
+    if (!bw->flow_ctas) {
+        // the group form of the dataflow solve is launched from this file
+        using K = void (*)(int, float *, int, const double *, const double *, int *, int *, const sr::SolveMat *,
+                           const unsigned long long *, int);
+        const K kern = sr::trisolve_flow_kernel<float, true>;
+        const size_t sm = sr::FlowShape<float>::smem;
+        int per_sm = 0, sms = 0;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, sr::FlowShape<float>::NT, sm);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) { sr_set_last_cuda_error(e); return SR_ERR_CUDA; }
+        bw->flow_ctas = std::max(1, per_sm) * sms;
+    }
     if (elems > bw->cap_elems || rows > bw->cap_rows || planes > bw->cap_planes || count > bw->cap_count ||
         kmax > bw->cap_k) {
         // grow everything together (the group's buffers are replaced wholesale)
@@ -348,7 +373,10 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
     // partial sums: one per 32 x 32 block of every matrix (flat grids)
     long long t32_all = 0;
     for (int b = 0; b < batch; ++b) t32_all += (long long)((n[b] + 31) / 32) * ((n[b] + 31) / 32);
-    SR_TRY(ensure_capacity(bw, elems, rows, batch, planes, std::max(512, nmx), (size_t)t32_all));
+    // published words of the dataflow solve: NB_b^2 per matrix
+    size_t flow_words = 2;
+    for (int b = 0; b < batch; ++b) flow_words += (size_t)((n[b] + 31) / 32) * (size_t)((n[b] + 31) / 32);
+    SR_TRY(ensure_capacity(bw, elems, rows, batch, planes, std::max(512, nmx), (size_t)t32_all, flow_words, h->dev));
 
     std::vector<int> cur(batch, 0);   // buffer holding the current Q: 0 = Q0, 1 = Q1
     std::vector<double> y_last(batch, NAN), prev(batch, INFINITY), anorm(batch, 1.0);
@@ -402,7 +430,10 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
     auto timed_out = [&]() {
         int f;
         memcpy(&f, h->hbuf + 8, sizeof(int));
-        return (f & SR_FLAG_TIMEOUT) != 0;
+        if (f & SR_FLAG_TIMEOUT) return true;
+        for (int b = 0; b < batch; ++b)
+            if (flag(b) & SR_FLAG_TIMEOUT) return true;   // a wait of the dataflow solve
+        return false;
     };
     auto split = [&](int slot, size_t o, const Grids &g, int layout, int s, long long el) {
         const GroupSplit gs{(const SplitMat *)P(o), (const int *)P(g.omax), (const int *)P(g.odig), g.m, g.tmax,
@@ -547,7 +578,8 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
         for (int b : act) el += (long long)n[b] * n[b];
         {
             DescPack pk;
-            std::vector<SolveMat> sm(batch, SolveMat{nullptr, 0, 0, nullptr});
+            std::vector<SolveMat> sm(batch, SolveMat{nullptr, 0, 0, nullptr, 0});
+            long long fwords = 2;   // dataflow solve: published words of the matrices going on
             std::vector<int> orders(batch, 0);
             std::vector<GMat> ga(m2);
             std::vector<SplitMat> wcols(m2), ycols(m2), w2cols(m2), qrows(m2), dcols(m2);
@@ -560,7 +592,8 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
                 const int b = act[a], nb = n[b];
                 const long long o = off[b];
                 double *Qc = Qbuf[cur[b]] + o, *Qo = Qbuf[cur[b] ^ 1] + o;
-                sm[b] = SolveMat{bw->TE + o, nb, nb, bw->diag + row0[b]};
+                sm[b] = SolveMat{bw->TE + o, nb, nb, bw->diag + row0[b], fwords - 2};
+                fwords += (long long)((nb + 31) / 32) * ((nb + 31) / 32);
                 orders[b] = nb;
                 ga[a] = GMat{o, nb, nb, nullptr, nullptr};
                 wcols[a] = SplitMat{bw->W + o, nb, nb, nb, row0[b]};
@@ -578,6 +611,13 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
             std::vector<unsigned long long> plan;
             std::vector<long long> poffs, nleaf;
             trisolve_plan_group(orders, plan, poffs, nleaf);
+            // the dataflow solve's tickets: the plan's solved tiles, step by step
+            // (every tile after the tiles it reads)
+            const bool flow = h->opt.solve_mode == 1;   // the stepwise form unless asked
+            std::vector<unsigned long long> fplan;
+            if (flow)
+                for (size_t l = 0; l < nleaf.size(); ++l)
+                    fplan.insert(fplan.end(), plan.begin() + poffs[l], plan.begin() + poffs[l] + nleaf[l]);
             std::vector<MmaItem> full_hp, sym_hp, full_lp, sym_lp;
             make_items(full_hp, act, n, row0, poff, kHp, false);
             make_items(sym_hp, act, n, row0, poff, kHp, true);
@@ -587,17 +627,24 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
                          o_yc = pk.add(ycols), o_w2c = pk.add(w2cols), o_qr = pk.add(qrows), o_dc = pk.add(dcols),
                          o_cm = pk.add(cm), o_ey = pk.add(e_y), o_ew2 = pk.add(e_w2), o_eyw = pk.add(e_yw),
                          o_ed = pk.add(e_d), o_eu = pk.add(e_u), o_fh = pk.add(full_hp), o_sh = pk.add(sym_hp),
-                         o_fl = pk.add(full_lp), o_sl = pk.add(sym_lp), o_map = pk.add(act);
+                         o_fl = pk.add(full_lp), o_sl = pk.add(sym_lp), o_map = pk.add(act),
+                         o_fp = pk.add(fplan);
             const Grids g = add_grids(pk, act, n);
             SR_TRY(upload(pk));
-            // S4: the group's solves, step by step
+            // S4: the group's solves: one dataflow launch, or step by step
             {
                 long long fl = 0;
                 for (int b : act) fl += 2LL * n[b] * n[b] * n[b] / 3;
-                SrPhase ph(h, SR_PROF_SOLVE, fl, 4 * el, 2LL * (long long)nleaf.size());
-                SR_CUDA_TRY(trisolve_launches_group<float>(st, bw->aux, bw->ev0, bw->ev1, (const SolveMat *)P(o_sm),
-                                                           bw->flags, (const unsigned long long *)P(o_pl), poffs,
-                                                           nleaf));
+                SrPhase ph(h, SR_PROF_SOLVE, fl, 4 * el, flow ? 1 : 2LL * (long long)nleaf.size());
+                if (flow)
+                    SR_CUDA_TRY(trisolve_flow_launch_group<float>(st, (const SolveMat *)P(o_sm), bw->flags, bw->flow,
+                                                                  (size_t)fwords,
+                                                                  (const unsigned long long *)P(o_fp),
+                                                                  (int)fplan.size(), bw->flow_ctas));
+                else
+                    SR_CUDA_TRY(trisolve_launches_group<float>(st, bw->aux, bw->ev0, bw->ev1,
+                                                               (const SolveMat *)P(o_sm), bw->flags,
+                                                               (const unsigned long long *)P(o_pl), poffs, nleaf));
             }
             // S5: Y = Q^T Q - I from Q's column digits (still in slot OZS_COLS), W = L - L^T
             SR_TRY(product(OZS_COLS, OZS_COLS, o_sh, sym_hp, kHp));

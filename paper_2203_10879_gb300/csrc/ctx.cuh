@@ -35,6 +35,10 @@ struct schur_refine_ctx {
     cudaEvent_t sev0 = nullptr, sev1 = nullptr;
     struct SolveGraph { int n; const void *TE; int ld; const void *dhp; const void *dlo; int kind; cudaGraphExec_t exec; };
     std::vector<SolveGraph> graphs;
+    // dataflow solve (opt.solve_mode 0 or 1): ticket, abort and published words of
+    // 2 + NB^2 ints; grid per low-precision kind (float, double, complex64)
+    int *flow = nullptr;
+    int flow_ctas[3] = {0, 0, 0};
     // schur_refine_batched: grouped-launch workspace, or worker sub-handles on their own streams
     BatchWork *bw = nullptr;
     std::vector<schur_refine_ctx *> subs;

@@ -135,7 +135,8 @@ sr_status check_opts(const sr_options &o)
     if (o.hp_gemm != SR_HP_FP64 && o.hp_gemm != SR_HP_OZAKI_BF16) return SR_ERR_INVALID_ARG;
     if (o.lp != SR_LP_FP32 && o.lp != SR_LP_FP64) return SR_ERR_INVALID_ARG;
     if (o.qhat_type != SR_QHAT_FP32 && o.qhat_type != SR_QHAT_FP64) return SR_ERR_INVALID_ARG;
-    if ((o.batch_mode != 0 && o.batch_mode != 1) || (o.tune != 0 && o.tune != 1) || (o.graph != 0 && o.graph != 1))
+    if ((o.batch_mode != 0 && o.batch_mode != 1) || (o.tune != 0 && o.tune != 1) || (o.graph != 0 && o.graph != 1) ||
+        o.solve_mode < 0 || o.solve_mode > 2)
         return SR_ERR_INVALID_ARG;
     if (o.ozaki_slices > (o.target == SR_TARGET_DD ? sr::kOzakiMaxSlicesDD : sr::kOzakiMaxSlices))
         return SR_ERR_INVALID_ARG;
@@ -274,9 +275,19 @@ template <typename Tl>
 sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum<Tl>::hp *dhp,
                 const double *dlo = nullptr)
 {
-    SR_TRY(ensure_plan(h, n));
     const int NB = (n + sr::kSolveTile - 1) / sr::kSolveTile;
     const int kind = SrNum<Tl>::kind;
+    if constexpr (SrNum<Tl>::kind <= 2) {
+        if (h->opt.solve_mode != 2) {
+            // one launch: the dataflow over the tiles
+            const long long fl = 2LL * n * n * n / 3 * (kind == 2 ? 4 : 1);
+            SrPhase ph(h, SR_PROF_SOLVE, fl, (long long)n * n * (long long)sizeof(Tl), 1);
+            SR_CUDA_TRY(sr::trisolve_flow_launch<Tl>(h->st, n, TE, ld, dhp, dlo, h->dflags, h->flow,
+                                                     h->flow_ctas[kind]));
+            return SR_OK;
+        }
+    }
+    SR_TRY(ensure_plan(h, n));
     cudaGraphExec_t exec = nullptr;
     if (h->capturing) {
         // inside the refinement's own graph: the launches themselves are captured
@@ -595,6 +606,7 @@ sr_status run_step(schur_refine_ctx *h, int n, const void *A, int lda, void *dQ,
         if (oz) SR_TRY(oz_gram_join(h));
         SR_TRY(read_back(h));
         const int f = host_flags(h);
+        if (f & SR_FLAG_TIMEOUT) { status = SR_ERR_TIMEOUT; break; }
         if (f & SR_FLAG_NONDISTINCT) { status = SR_ERR_NONDISTINCT; break; }
         if (f & SR_FLAG_NONFINITE) { status = SR_ERR_NONFINITE; break; }
         nr.w_norm = sqrt(2.0 * h->hbuf[2]);
@@ -678,7 +690,8 @@ __global__ void ctl_solve_kernel(SrCtl *c, const double *__restrict__ dnorm, con
 {
     const int f = *flags;
     unsigned ok = 1;
-    if (f & SR_FLAG_NONDISTINCT) { c->status = SR_ERR_NONDISTINCT; ok = 0; }
+    if (f & SR_FLAG_TIMEOUT) { c->status = SR_ERR_TIMEOUT; ok = 0; }
+    else if (f & SR_FLAG_NONDISTINCT) { c->status = SR_ERR_NONDISTINCT; ok = 0; }
     else if (f & SR_FLAG_NONFINITE) { c->status = SR_ERR_NONFINITE; ok = 0; }
     else c->w_norm = sqrt(2.0 * dnorm[2]);
     cudaGraphSetConditional(hu, ok);
@@ -1139,6 +1152,7 @@ sr_status run_step_dd(schur_refine_ctx *h, int n, const void *dA, int lda, void 
         SR_TRY(sumsq<double>(h, n, (const double *)h->TE, ld, 1, 2));
         SR_TRY(read_back(h));
         const int f = host_flags(h);
+        if (f & SR_FLAG_TIMEOUT) { status = SR_ERR_TIMEOUT; break; }
         if (f & SR_FLAG_NONDISTINCT) { status = SR_ERR_NONDISTINCT; break; }
         if (f & SR_FLAG_NONFINITE) { status = SR_ERR_NONFINITE; break; }
         nr.w_norm = sqrt(2.0 * h->hbuf[2]);
@@ -1180,6 +1194,7 @@ void schur_refine_default_options(sr_options *opt)
     opt->batch_mode = 0;
     opt->tune = 0;
     opt->graph = 0;
+    opt->solve_mode = 0;
 }
 
 const char *schur_refine_status_string(sr_status s)
@@ -1258,6 +1273,7 @@ void schur_refine_destroy(schur_refine_t h)
     if (h->gev1) cudaEventDestroy(h->gev1);
     cudaFree(h->dnorm);
     cudaFree(h->dflags);
+    cudaFree(h->flow);
     if (h->hbuf) cudaFreeHost(h->hbuf);
     sr::ozaki_free(h->oz);
     delete h;
@@ -1303,7 +1319,17 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     SR_ALLOC(h->partial, h->npartial * sizeof(double));
     SR_ALLOC(h->dnorm, 8 * sizeof(double));
     SR_ALLOC(h->dflags, sizeof(int));
+    const size_t nbmax = (size_t)(n_max + sr::kSolveTile - 1) / sr::kSolveTile;
+    SR_ALLOC(h->flow, (2 + nbmax * nbmax) * sizeof(int));
 #undef SR_ALLOC
+    if (e == cudaSuccess) {
+        // grid of the dataflow solve for each low-precision kind this handle can use
+        h->flow_ctas[0] = sr::trisolve_flow_setup<float>(h->dev);
+        h->flow_ctas[1] = sr::trisolve_flow_setup<double>(h->dev);
+        h->flow_ctas[2] = sr::trisolve_flow_setup<cf>(h->dev);
+        if (!h->flow_ctas[0] || !h->flow_ctas[1] || !h->flow_ctas[2]) e = cudaGetLastError();
+        if (e == cudaSuccess && (!h->flow_ctas[0] || !h->flow_ctas[1] || !h->flow_ctas[2])) e = cudaErrorInvalidValue;
+    }
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hbuf, 16 * sizeof(double));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux_st, cudaStreamNonBlocking);
@@ -1531,6 +1557,7 @@ sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, cons
         SR_TRY(solve<double>(h, n, (double *)dTE, ld, (const double *)dDiag));
     SR_TRY(read_back(h));
     const int f = host_flags(h);
+    if (f & SR_FLAG_TIMEOUT) return SR_ERR_TIMEOUT;
     if (f & SR_FLAG_NONDISTINCT) return SR_ERR_NONDISTINCT;
     if (f & SR_FLAG_NONFINITE) return SR_ERR_NONFINITE;
     return SR_OK;

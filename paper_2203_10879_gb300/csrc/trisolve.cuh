@@ -29,6 +29,7 @@
 // Divisors t_ii - t_jj are formed in FP64 from the high-precision diagonal and
 // then rounded to the working type (the paper is silent here).
 #pragma once
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -65,6 +66,7 @@ struct SolveMat {
     void *TE;
     int ld, n;
     const void *dhp;
+    long long fbase;   // dataflow solve: first published word of this matrix
 };
 
 // Group plan: for every step t (from the largest order's last subdiagonal
@@ -379,6 +381,371 @@ inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cu
         if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev0, 0);
     }
     return e;
+}
+
+// ---- the whole solve in one launch: a dataflow over the tiles --------------
+// The same tile equations as above, solved by one persistent launch. Tiles
+// are claimed through a ticket counter in the wavefront's order (block
+// subdiagonal NB-1 first, then NB-2, ..., 0; by column within one). The CTA
+// holding tile (I, J), D = I - J, applies for d = NB-1, ..., D+1 the two
+// products of subdiagonal d (the block form of Alg. 3's update products)
+//     T(I, J+d) L(J+d, J)   and   -L(I, I-d) T(I-d, J)
+// as soon as the two L tiles of subdiagonal d are published, then solves the
+// tile equation by the wavefront of trisolve_leaf_kernel and publishes X.
+// The CTA has 512 threads, two entries of the tile each in the solve (the
+// wavefront's steps are barrier-bound: few entries per thread keep them
+// short), and two CTAs share an SM, so one CTA's products run while the
+// other waits at its wavefront's barriers. The products of one tile are
+// split over NG groups of NTG threads (subdiagonals d = top-g, top-g-NG, ...
+// for group g), each with its own operand buffers and named barrier, so a
+// group waits only on its own inputs; the partial sums meet in shared memory
+// before the solve.
+//
+// Forward progress does not need the CTAs to be co-resident: the inputs of a
+// tile lie on higher subdiagonals and so hold smaller tickets, and a ticket
+// is taken only by a running CTA, so the smallest unfinished ticket always
+// finds its inputs published. Every wait is bounded (kFlowSpin polls); one
+// that runs out sets SR_FLAG_TIMEOUT and an abort word that ends all other
+// waits, and the launch runs to its end without further waiting.
+//
+// work[0]: ticket counter; work[1]: abort word; work[2 + I NB + J]: tile
+// (I, J) published. The launcher clears them before the kernel.
+template <typename T> struct FlowShape {
+    using Hp = typename SrNum<T>::hp;
+    static constexpr int B = kSolveTile;
+    static constexpr int NT = 512;                  // threads of the CTA (two CTAs per SM)
+    static constexpr int EPT = B * B / NT;          // entries of the tile per thread in the solve
+    static constexpr int WS = NT / 32;              // warps: thread (a, w) owns columns w + WS q
+    // products: rows 4tx.., columns TN ty.. per thread (TN = 4: 64 threads a
+    // group; TN = 2: 128) and NG groups, as many as half the shared memory holds
+    static constexpr int TN = SrNum<T>::kind == 0 ? 4 : 2;
+    static constexpr int NTG = 8 * (B / TN);
+    static constexpr int NG = SrNum<T>::kind == 0 ? 4 : 2;
+    static constexpr int SA = B + 4;                // row stride of the operand buffers
+    static constexpr int SX = B + 1;                // row stride of the solve's tiles
+    static constexpr size_t kSlot = 4 * B * SA;     // elements of one group's operands
+    static constexpr size_t smem = (NG * kSlot + 3 * B * SX) * sizeof(T) + 2 * B * (sizeof(Hp) + sizeof(double))
+                                   + 16;
+    static_assert(NG * NTG <= NT, "product groups exceed the CTA");
+    static_assert(EPT * NT == B * B, "one or more whole entries per thread");
+};
+constexpr int kFlowSpin = 1 << 22;   // polls of one wait (a few hundred ns apart)
+
+__device__ inline int flow_ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ inline void flow_st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Wait, by a whole warp, until the published flag *f is set; false after an
+// abort or a timeout. Lane 0 loads (acquire) and broadcasts, so every branch
+// is uniform over the warp and the warp stays converged for the barrier that
+// follows.
+__device__ inline bool flow_wait(const int *f, int *abort_w, int *flags)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    for (int it = 0; it < kFlowSpin; ++it) {
+        int v = 0, ab = 0;
+        if (lane == 0) {
+            v = flow_ld_acquire(f);
+            if (!v) ab = *(volatile int *)abort_w;
+        }
+        v = __shfl_sync(0xffffffffu, v, 0);
+        ab = __shfl_sync(0xffffffffu, ab, 0);
+        if (v) return true;
+        if (ab) return false;
+        __nanosleep(it < 32 ? 32 : 256);
+    }
+    if (lane == 0) {
+        atomicOr(flags, SR_FLAG_TIMEOUT);
+        atomicExch(abort_w, 1);
+    }
+    __syncwarp();
+    return false;
+}
+// named barrier of nthreads threads (whole warps); the warp reconverges
+// first, as bar.sync requires of every warp that executes it
+__device__ inline void flow_bar(int id, int nthreads)
+{
+    __syncwarp();
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// loads of published tiles go to L2, never to a stale L1 line
+__device__ inline float flow_ldcg(const float *p) { return __ldcg(p); }
+__device__ inline double flow_ldcg(const double *p) { return __ldcg(p); }
+__device__ inline cf flow_ldcg(const cf *p)
+{
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return {v.x, v.y};
+}
+// ticket k -> tile (I, J): the m-th subdiagonal from the corner (D = NB-1-m)
+// holds m+1 tiles and starts at ticket m(m+1)/2
+__device__ inline void flow_tile(int k, int NB, int &I, int &J)
+{
+    int m = (int)((sqrtf(8.0f * (float)k + 1.0f) - 1.0f) * 0.5f);
+    while (m > 0 && m * (m + 1) / 2 > k) --m;
+    while ((m + 1) * (m + 2) / 2 <= k) ++m;
+    J = k - m * (m + 1) / 2;
+    I = J + (NB - 1 - m);
+}
+
+template <typename T, bool GROUP = false>
+__global__ void __launch_bounds__(FlowShape<T>::NT, 2)
+trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<T>::hp *__restrict__ dhp0,
+                     const double *__restrict__ dlo, int *__restrict__ flags0, int *__restrict__ work,
+                     const SolveMat *__restrict__ mats = nullptr, const unsigned long long *__restrict__ gplan = nullptr,
+                     int gtiles = 0)
+{
+    using S = FlowShape<T>;
+    using Hp = typename SrNum<T>::hp;
+    constexpr int B = S::B, SA = S::SA, SX = S::SX, NTG = S::NTG, NG = S::NG, TN = S::TN, EPT = S::EPT,
+                  WS = S::WS;
+    constexpr int LR = NTG / 32;
+    extern __shared__ __align__(16) unsigned char flow_smem[];
+    T *ops = reinterpret_cast<T *>(flow_smem);
+    T (*Ti)[SX] = reinterpret_cast<T (*)[SX]>(ops + NG * S::kSlot);
+    T (*Tj)[SX] = Ti + B;
+    T (*X)[SX] = Tj + B;
+    Hp *dI = reinterpret_cast<Hp *>(X + B);
+    Hp *dJ = dI + B;
+    double *dIl = reinterpret_cast<double *>(dJ + B);
+    double *dJl = dIl + B;
+    int *s_ticket = reinterpret_cast<int *>(dJl + B);
+
+    const int tid = threadIdx.x;
+    const int ntiles = GROUP ? gtiles : ((n0 + B - 1) / B) * ((n0 + B - 1) / B + 1) / 2;
+    int *abort_w = work + 1;
+    const int g = tid / NTG, gt = tid % NTG;   // product group (g < NG takes part)
+    T *slot = ops + (g < NG ? g : 0) * S::kSlot;
+    T (*Ta)[B][SA] = reinterpret_cast<T (*)[B][SA]>(slot);             // Ta[u][k][row]
+    T (*Tb)[B][SA] = reinterpret_cast<T (*)[B][SA]>(slot + 2 * B * SA);   // Tb[u][k][col]
+    const int lx = gt & 31, ly = gt >> 5;   // operand loads: element (lx, ly + LR q)
+    const int tx = gt & 7, ty = gt >> 3;    // products: rows 4tx.., columns TN ty..
+    const int a = tid & 31, wq = tid >> 5;  // solve: entries (a, wq + WS q), q < EPT
+    const T Z = SrNum<T>::zero();
+    const Hp hz = SrNum<Hp>::zero();
+
+    for (;;) {
+        if (tid == 0) *s_ticket = atomicAdd(work, 1);
+        __syncthreads();
+        const int k = *s_ticket;
+        if (k >= ntiles) break;
+        // the tile and its matrix (a group: from the plan; each matrix has
+        // its own error word and published words)
+        int n = n0, ld = ld0, I, J;
+        T *TE = TE0;
+        const Hp *dhp = dhp0;
+        int *flags = flags0, *pub = work + 2;
+        if constexpr (GROUP) {
+            const unsigned long long gp = gplan[k];
+            const SolveMat m = mats[gp >> 32];
+            TE = (T *)m.TE;
+            ld = m.ld;
+            n = m.n;
+            dhp = (const Hp *)m.dhp;
+            flags += (gp >> 32);
+            pub += m.fbase;
+            I = (int)((uint32_t)gp >> 16);
+            J = (int)(gp & 0xffffu);
+        } else {
+            flow_tile(k, (n + B - 1) / B, I, J);
+        }
+        const int NB = (n + B - 1) / B;
+        const int D = I - J, r0 = I * B, c0 = J * B;
+        const int nr = min(B, n - r0), nc = min(B, n - c0);
+
+        // inputs that no tile writes: T_II, T_JJ, the diagonals and E_IJ
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int b = wq + WS * q;
+            Ti[a][b] = (a <= b && b < nr) ? TE[sr_idx(r0 + a, r0 + b, ld)] : Z;
+            Tj[a][b] = (a <= b && b < nc) ? TE[sr_idx(c0 + a, c0 + b, ld)] : Z;
+        }
+        if (tid < B) {
+            dI[tid] = (tid < nr) ? dhp[r0 + tid] : hz;
+            dIl[tid] = (dlo && tid < nr) ? dlo[r0 + tid] : 0.0;
+        } else if (tid < 2 * B) {
+            dJ[tid - B] = (tid - B < nc) ? dhp[c0 + tid - B] : hz;
+            dJl[tid - B] = (dlo && tid - B < nc) ? dlo[c0 + tid - B] : 0.0;
+        }
+        bool own[EPT];
+        T acc[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int b = wq + WS * q;
+            own[q] = a < nr && b < nc && (D > 0 || a > b);
+            acc[q] = own[q] ? TE[sr_idx(r0 + a, c0 + b, ld)] : Z;
+        }
+        __syncthreads();
+        // divisors t_aa - t_bb formed in high precision, rounded, inverted once
+        // (before the waits: they need only the diagonals)
+        T rcp[EPT];
+        int bad = 0;
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int b = wq + WS * q;
+            T den = own[q] ? sr_div_round<T>(dI[a], dJ[b]) : Z;
+            if constexpr (SrNum<T>::kind == 1) {
+                if (own[q] && dlo) den = sr_div_round_dd(dI[a], dIl[a], dJ[b], dJl[b]);
+            }
+            if (own[q] && den == Z) bad |= SR_FLAG_NONDISTINCT;
+            rcp[q] = (own[q] && !(den == Z)) ? sr_recip(den) : Z;
+        }
+
+        // products of subdiagonals d = top-g, top-g-NG, ..., > D
+        T pacc[4][TN];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) pacc[i][j] = Z;
+        const int top = max(NB - 1 - J, I);
+        for (int d = top - g; g < NG && d > D; d -= NG) {
+            const bool hasP = J + d < NB, hasM = I - d >= 0;
+            if (gt < 32) {   // the group's first warp waits for both inputs
+                bool ok = true;
+                if (hasP) ok = flow_wait(pub + (J + d) * NB + J, abort_w, flags);
+                if (ok && hasM) flow_wait(pub + I * NB + (I - d), abort_w, flags);
+            }
+            flow_bar(1 + g, NTG);
+            const int kP = (J + d) * B, kM = (I - d) * B;
+#pragma unroll
+            for (int q = 0; q < 32 / LR; ++q) {
+                const int y = ly + LR * q;
+                Ta[0][y][lx] = (hasP && r0 + lx < n && kP + y < n) ? TE[sr_idx(r0 + lx, kP + y, ld)] : Z;
+                Tb[0][lx][y] = (hasP && kP + lx < n && c0 + y < n) ? flow_ldcg(&TE[sr_idx(kP + lx, c0 + y, ld)]) : Z;
+                Ta[1][y][lx] = (hasM && r0 + lx < n && kM + y < n) ? flow_ldcg(&TE[sr_idx(r0 + lx, kM + y, ld)]) : Z;
+                Tb[1][lx][y] = (hasM && kM + lx < n && c0 + y < n) ? TE[sr_idx(kM + lx, c0 + y, ld)] : Z;
+            }
+            flow_bar(1 + g, NTG);
+#pragma unroll 4
+            for (int kk = 0; kk < B; ++kk) {
+                T av[4], bv[TN], mv[4], cv[TN];
+                SolveVec<T>::ld4(&Ta[0][kk][4 * tx], av);
+                SolveVec<T>::ld4(&Ta[1][kk][4 * tx], mv);
+                if constexpr (TN == 4) {
+                    SolveVec<T>::ld4(&Tb[0][kk][4 * ty], bv);
+                    SolveVec<T>::ld4(&Tb[1][kk][4 * ty], cv);
+                } else {
+                    SolveVec<T>::ld2(&Tb[0][kk][2 * ty], bv);
+                    SolveVec<T>::ld2(&Tb[1][kk][2 * ty], cv);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) {
+                        pacc[i][j] = sr_fma(av[i], bv[j], pacc[i][j]);
+                        pacc[i][j] = sr_fma(-mv[i], cv[j], pacc[i][j]);
+                    }
+            }
+            flow_bar(1 + g, NTG);   // the next operands overwrite this group's buffers
+        }
+        __syncthreads();
+        // the groups' partial sums, each in its own operand buffer, added to E
+        if (g < NG) {
+            T (*P)[SX] = reinterpret_cast<T (*)[SX]>(slot);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) P[4 * tx + i][TN * ty + j] = pacc[i][j];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < EPT; ++q)
+#pragma unroll
+            for (int gg = 0; gg < NG; ++gg) {
+                const T (*P)[SX] = reinterpret_cast<const T (*)[SX]>(ops + gg * S::kSlot);
+                acc[q] = acc[q] + P[a][wq + WS * q];
+            }
+
+        // wavefront over the tile's subdiagonals w (see trisolve_leaf_kernel);
+        // an entry with a zero divisor is set to zero and flagged
+        const int wlo = (D > 0) ? -(B - 1) : 1;
+        T xv[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) xv[q] = Z;
+        for (int w = B - 1; w >= wlo; --w) {
+#pragma unroll
+            for (int q = 0; q < EPT; ++q)
+                if (own[q] && a - (wq + WS * q) == w) {
+                    xv[q] = -(acc[q] * rcp[q]);
+                    X[a][wq + WS * q] = xv[q];
+                }
+            __syncthreads();
+            const int c2 = a - w;                    // (a, c2): row a's entry of subdiagonal w
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                const int b = wq + WS * q;
+                const int c = b + w;                 // (c, b): lane c of this warp, same q
+                const T xcol = sr_shfl(xv[q], c & 31);
+                if (own[q] && a - b < w) {
+                    if (c < nr) acc[q] = sr_fma(Ti[a][c], xcol, acc[q]);
+                    if (c2 >= 0) acc[q] = sr_fma(-X[a][c2], Tj[c2][b], acc[q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < EPT; ++q)
+            if (own[q]) {
+                if (!sr_finite(xv[q])) bad |= SR_FLAG_NONFINITE;
+                TE[sr_idx(r0 + a, c0 + wq + WS * q, ld)] = xv[q];
+            }
+        if (bad) atomicOr(flags, bad);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) flow_st_release(pub + I * NB + J, 1);
+    }
+}
+
+// The dataflow solve of a group (no double-double divisors): plan = the
+// tiles (b << 32 | I << 16 | J) in an order that lists every tile after its
+// inputs; mats[b].fbase = start of matrix b's NB_b^2 published words in
+// work + 2; nwords = 2 + their total.
+template <typename T>
+inline cudaError_t trisolve_flow_launch_group(cudaStream_t st, const SolveMat *mats, int *flags, int *work,
+                                              size_t nwords, const unsigned long long *plan, int ntiles, int ctas)
+{
+    cudaError_t e = cudaMemsetAsync(work, 0, nwords * sizeof(int), st);
+    if (e != cudaSuccess || ntiles < 1) return e;
+    trisolve_flow_kernel<T, true><<<(unsigned)std::max(1, std::min(ctas, ntiles)), FlowShape<T>::NT,
+                                    FlowShape<T>::smem, st>>>(0, nullptr, 0, nullptr, nullptr, flags, work, mats, plan,
+                                                              ntiles);
+    return cudaGetLastError();
+}
+
+// Clears the flow state and launches the dataflow solve on st with at most
+// `ctas` CTAs (one ticket loop each). work holds 2 + NB^2 ints.
+template <typename T>
+inline cudaError_t trisolve_flow_launch(cudaStream_t st, int n, T *TE, int ld, const typename SrNum<T>::hp *dhp,
+                                        const double *dlo, int *flags, int *work, int ctas)
+{
+    const int NB = (n + kSolveTile - 1) / kSolveTile;
+    const int nt = NB * (NB + 1) / 2;
+    cudaError_t e = cudaMemsetAsync(work, 0, (2 + (size_t)NB * NB) * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    trisolve_flow_kernel<T><<<(unsigned)std::max(1, std::min(ctas, nt)), FlowShape<T>::NT, FlowShape<T>::smem, st>>>(
+        n, TE, ld, dhp, dlo, flags, work);
+    return cudaGetLastError();
+}
+
+// Opts the kernel into its shared memory and returns the CTAs that fit the
+// device at once (the launch's grid); 0 on error.
+template <typename T>
+inline int trisolve_flow_setup(int dev)
+{
+    if (cudaFuncSetAttribute(trisolve_flow_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)FlowShape<T>::smem) != cudaSuccess)
+        return 0;
+
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trisolve_flow_kernel<T>, FlowShape<T>::NT,
+                                                      FlowShape<T>::smem) != cudaSuccess)
+        return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return std::max(1, per_sm) * sms;
 }
 
 }  // namespace sr

@@ -77,11 +77,12 @@ def _single(p, **kw):
         B.schur_refine_destroy(h)
 
 
-def test_grouped_launches_equal_single_steps(batch):
-    st, iters, stats, Qs = _run(batch, 8, mode=0, hp_gemm=B.SR_HP_OZAKI_BF16)
+@pytest.mark.parametrize("solve_mode", [1, 2])
+def test_grouped_launches_equal_single_steps(batch, solve_mode):
+    st, iters, stats, Qs = _run(batch, 8, mode=0, hp_gemm=B.SR_HP_OZAKI_BF16, solve_mode=solve_mode)
     assert st == B.SR_OK
     for p, Q, k, s in zip(batch, Qs, iters, stats):
-        s1, k1, Q1 = _single(p, hp_gemm=B.SR_HP_OZAKI_BF16)
+        s1, k1, Q1 = _single(p, hp_gemm=B.SR_HP_OZAKI_BF16, solve_mode=solve_mode)
         assert (s, k) == (s1, k1), p.n
         assert np.array_equal(Q, Q1), p.n
 

@@ -120,10 +120,11 @@ def _csolve_problem(n, seed):
     return T, E
 
 
-@pytest.mark.parametrize("n", [1, 2, 33, 100, 257])
-def test_complex_trisolve_parity(torch, n):
+@pytest.mark.parametrize("solve_mode", [1, 2])
+@pytest.mark.parametrize("n", [1, 2, 33, 100, 257, 600])
+def test_complex_trisolve_parity(torch, n, solve_mode):
     T, E = _csolve_problem(n, 5 * n + 1)
-    h = _handle(n)
+    h = _handle(n, solve_mode=solve_mode)
     try:
         TE = to_dev((np.triu(T) + E).astype(np.complex64))
         s = B.schur_refine_trisolve(h, n, TE, to_dev(np.diagonal(T).copy()))
@@ -135,7 +136,10 @@ def test_complex_trisolve_parity(torch, n):
         Lo = oracle.alg2(np.triu(T).astype(np.complex64), E.astype(np.complex64), np.diagonal(T).copy())
         e_gpu = np.linalg.norm(Lg - L64)
         e_orc = np.linalg.norm(Lo.astype(np.complex128) - L64)
-        assert e_gpu <= 10 * max(e_orc, U32 * np.linalg.norm(L64))
+        # the stepwise form carries E in the running sum of every block update
+        # (Alg. 2 adds it once, after the two sums): up to ~10x the oracle's error
+        factor = 10 if solve_mode == 1 else 20
+        assert e_gpu <= factor * max(e_orc, U32 * np.linalg.norm(L64))
     finally:
         B.schur_refine_destroy(h)
 

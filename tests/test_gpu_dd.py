@@ -116,15 +116,16 @@ def test_dd_gemm_exact_on_integers(torch, hp):
         B.schur_refine_destroy(h)
 
 
-@pytest.mark.parametrize("n", [2, 33, 100, 257])
-def test_dd_trisolve_parity(torch, n):
+@pytest.mark.parametrize("solve_mode", [1, 2])
+@pytest.mark.parametrize("n", [2, 33, 100, 257, 500])
+def test_dd_trisolve_parity(torch, n, solve_mode):
     rng = np.random.default_rng(n)
     d = 1.0 + np.arange(n) / 64.0
     dlo = rng.uniform(-1, 1, n) * 2.0 ** -54 * d
     dlo = (d + dlo) - d
     T = np.triu(rng.standard_normal((n, n)) / n, 1) + np.diag(d)
     E = np.tril(rng.standard_normal((n, n)) * 1e-14, -1)
-    h = _handle(n, B.SR_HP_OZAKI_BF16)
+    h = _handle(n, B.SR_HP_OZAKI_BF16, solve_mode=solve_mode)
     try:
         TE = to_dev(np.triu(T) + E)
         s = B.schur_refine_trisolve(h, n, TE, to_dev(np.concatenate([d, dlo])))
