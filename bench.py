@@ -356,9 +356,11 @@ def run_ours(args):
         mn = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP32)
         mixed_native_ms, _, _ = timed(mn, k64, 1)
         mn.close()
-    # the same mixed form with the stepwise solve (one launch pair per block subdiagonal)
-    sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, solve_mode=2, **dtype_opt)
-    stepwise_ms, _, _ = timed(sw, max(1, min(args.steps, 3)), 2)
+    # the same mixed form with the other form of the solve: stepwise (one launch
+    # pair per block subdiagonal) for real data, dataflow (one launch) for complex
+    alt_mode = 1 if cplx else 2
+    sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, solve_mode=alt_mode, **dtype_opt)
+    alt_ms, _, _ = timed(sw, max(1, min(args.steps, 3)), 2)
     sw.close()
 
     if rank != 0:
@@ -417,8 +419,9 @@ def run_ours(args):
                    "all_fp64_iters": None if nr64 is None else nr64.iters, "all_fp64_status": st64,
                    "mixed_vs_all_fp64_speedup": None if ms64 is None else ms64 / ms,
                    "mixed_native_fp64_s": None if mixed_native_ms is None else mixed_native_ms / 1e3,
-                   "solve_form": "dataflow (one launch per solve)",
-                   "with_stepwise_solve_s": stepwise_ms / 1e3,
+                   "solve_form": "stepwise (launch pair per block subdiagonal)" if cplx
+                   else "dataflow (one launch per solve)",
+                   "with_other_solve_form_s": alt_ms / 1e3,
                    "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
                    "phase_rates": phase_rooflines(prof, args.steps),
                    "all_fp64_phase_ms_per_step": {k: v["ms"] / k64 for k, v in prof64.items() if v["ms"] > 0},

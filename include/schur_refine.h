@@ -120,15 +120,17 @@ typedef struct {
                          same results; the profile (profile = 1) is not
                          recorded in this mode */
     int solve_mode;   /* triangular solve (Sec. 2.1): 0 (default) = the
-                         dataflow form for single matrices, the stepwise form
-                         for grouped batches (the faster of the two measured
-                         for each); 1 = dataflow always; 2 = stepwise always.
-                         Dataflow: one launch in which the tiles of the
-                         wavefront are claimed in subdiagonal order and each
-                         waits only for the tiles it reads (bounded waits;
-                         SR_ERR_TIMEOUT if one runs out). Stepwise: one
-                         launch pair per block subdiagonal, replayed from a
-                         CUDA graph. Same equations, sums in another order;
+                         dataflow form for a single matrix with FP32 low
+                         precision, the stepwise form otherwise (FP64 and
+                         complex64 solves and grouped batches are bound by
+                         their arithmetic, where the stepwise form measured
+                         faster); 1 = dataflow wherever built; 2 = stepwise
+                         always. Dataflow: one launch in which the tiles of
+                         the wavefront are claimed in subdiagonal order and
+                         each waits only for the tiles it reads (bounded
+                         waits; SR_ERR_TIMEOUT if one runs out). Stepwise:
+                         one launch pair per block subdiagonal, replayed from
+                         a CUDA graph. Same equations, sums in another order;
                          complex128 always uses the stepwise form */
 } sr_options;
 

@@ -35,7 +35,7 @@ struct schur_refine_ctx {
     cudaEvent_t sev0 = nullptr, sev1 = nullptr;
     struct SolveGraph { int n; const void *TE; int ld; const void *dhp; const void *dlo; int kind; cudaGraphExec_t exec; };
     std::vector<SolveGraph> graphs;
-    // dataflow solve (opt.solve_mode 0 or 1): ticket, abort and published words of
+    // dataflow solve (see opt.solve_mode): ticket, abort and published words of
     // 2 + NB^2 ints; grid per low-precision kind (float, double, complex64)
     int *flow = nullptr;
     int flow_ctas[3] = {0, 0, 0};

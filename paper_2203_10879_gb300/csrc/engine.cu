@@ -278,7 +278,8 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
     const int NB = (n + sr::kSolveTile - 1) / sr::kSolveTile;
     const int kind = SrNum<Tl>::kind;
     if constexpr (SrNum<Tl>::kind <= 2) {
-        if (h->opt.solve_mode != 2) {
+        const int mode = h->opt.solve_mode;
+        if (mode == 1 || (mode == 0 && kind == 0)) {
             // one launch: the dataflow over the tiles
             const long long fl = 2LL * n * n * n / 3 * (kind == 2 ? 4 : 1);
             SrPhase ph(h, SR_PROF_SOLVE, fl, (long long)n * n * (long long)sizeof(Tl), 1);
