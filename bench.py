@@ -41,7 +41,7 @@ BF16_NOMINAL_TFLOPS = 2250.0
 # kernel (profiles/ozaki_mma_kernel_n4096.md: the 28-pair T^ product at n = 4096; and
 # profiles/ozaki_mma_kernel_dd_n2048.md: the 105-pair A Q product of the double-double
 # workload); valid for that kernel version and size only
-OZ_MMA_TRAFFIC_BYTES_N4096 = 5.787937e9 + 0.4733504e9
+OZ_MMA_TRAFFIC_BYTES_N4096 = 5.771999e9 + 0.471991e9
 OZ_MMA_TRAFFIC_BYTES_DD2048 = 1.619892e9 + 0.2217213e9
 
 
