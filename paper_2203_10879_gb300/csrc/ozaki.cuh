@@ -237,24 +237,67 @@ __device__ __forceinline__ double oz_i128_to_double(__int128 V, int x)
 __device__ __forceinline__ double oz_rebuild(const int32_t *__restrict__ planes, size_t off, size_t pstride, int s,
                                              bool neg, int e)
 {
+    // all level loads first (predicated), so that they are in flight together
+    int32_t v[kOzakiMaxSlices];
+#pragma unroll
+    for (int l = 0; l < kOzakiMaxSlices; ++l) v[l] = l < s ? planes[off + (size_t)l * pstride] : 0;
     __int128 V = 0;
-    for (int l = 0; l < s; ++l) V = V * 256 + (__int128)planes[off + (size_t)l * pstride];
+#pragma unroll
+    for (int l = 0; l < kOzakiMaxSlices; ++l)
+        if (l < s) V = V * 256 + (__int128)v[l];
     return oz_i128_to_double(neg ? -V : V, e - 14 - 8 * (s - 1));
 }
 
 // C(i,j) = sign * (rebuilt product); ep as in gemm_simt.cuh (a complex value
 // cd when CPLX). With mirror, the entries below the diagonal are read from the
-// transposed position (conjugated when CPLX: the product is Hermitian).
+// transposed position (conjugated when CPLX: the product is Hermitian). A block
+// wholly below the diagonal reads its mirrored block with lanes along the
+// planes' contiguous index and turns it in shared memory, so that both the
+// plane reads and the epilogue's accesses are coalesced.
 template <class EP, bool CPLX>
 __global__ void __launch_bounds__(256)
 ozaki_combine_kernel(int m, int n, int s, const int32_t *__restrict__ planes, int ldp, size_t pstride, size_t imoff,
                      const int *__restrict__ ea, const int *__restrict__ fb, double sign, int mirror, EP ep,
                      double *partial)
 {
+    using VT = std::conditional_t<CPLX, cd, double>;
     const int i = blockIdx.x * 32 + (threadIdx.x & 31);
     const int jb = blockIdx.y * 32 + (threadIdx.x >> 5);
     const bool neg = sign < 0;
     double part = 0.0;
+    if (mirror && blockIdx.x > blockIdx.y) {
+        __shared__ VT turned[32][33];
+        const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+        const int lj = threadIdx.x & 31, wi = threadIdx.x >> 5;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int li = wi + 8 * w, ii = i0 + li, jj = j0 + lj;
+            if (ii < m && jj < n) {
+                const size_t off = (size_t)jj + (size_t)ii * (size_t)ldp;   // entry (jj, ii) of the planes
+                const int e1 = ea[ii], e2 = fb[jj];
+                const bool bad = e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite;
+                const double nan = __longlong_as_double(0x7ff8000000000000LL);
+                const double re = bad ? nan : oz_rebuild(planes, off, pstride, s, neg, e1 + e2);
+                if constexpr (CPLX) {
+                    const double im = bad ? nan : oz_rebuild(planes, off + imoff, pstride, s, neg, e1 + e2);
+                    turned[li][lj] = cd{re, -im};
+                } else {
+                    turned[li][lj] = re;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int j = jb + 8 * w;
+            if (i < m && j < n) part += ep(i, j, turned[i - i0][j - j0]);
+        }
+        if (partial) {
+            part = sr_block_sum<256>(part);
+            if (threadIdx.x == 0) partial[blockIdx.x + (size_t)gridDim.x * blockIdx.y] = part;
+        }
+        return;
+    }
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
         const int j = jb + 8 * w;
@@ -419,11 +462,41 @@ ozaki_combine_group_kernel(int s, const int32_t *__restrict__ planes, size_t pst
     const int a = group_find(start, cnt, blockIdx.x);
     const CombMat cm = mats[a];
     const int local = blockIdx.x - start[a], gx = (cm.m + 31) / 32;
-    const int i = (local % gx) * 32 + (threadIdx.x & 31);
-    const int jb = (local / gx) * 32 + (threadIdx.x >> 5);
+    const int bx = local % gx, by = local / gx;
+    const int i = bx * 32 + (threadIdx.x & 31);
+    const int jb = by * 32 + (threadIdx.x >> 5);
     const EP ep = eps[a];
     const bool neg = sign < 0;
     double part = 0.0;
+    if (mirror && bx > by) {
+        // wholly below the diagonal: coalesced reads of the mirrored block,
+        // turned in shared memory (as in ozaki_combine_kernel)
+        __shared__ double turned[32][33];
+        const int i0 = bx * 32, j0 = by * 32;
+        const int lj = threadIdx.x & 31, wi = threadIdx.x >> 5;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int li = wi + 8 * w, ii = i0 + li, jj = j0 + lj;
+            if (ii < cm.m && jj < cm.n) {
+                const size_t off = (size_t)cm.poff + (size_t)jj + (size_t)ii * (size_t)cm.ldp;
+                const int e1 = ea[cm.ra + ii], e2 = fb[cm.rb + jj];
+                const bool bad = e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite;
+                const double nan = __longlong_as_double(0x7ff8000000000000LL);
+                turned[li][lj] = bad ? nan : oz_rebuild(planes, off, pstride, s, neg, e1 + e2);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int j = jb + 8 * w;
+            if (i < cm.m && j < cm.n) part += ep(i, j, turned[i - i0][j - j0]);
+        }
+        if (partial) {
+            part = sr_block_sum<256>(part);
+            if (threadIdx.x == 0) partial[blockIdx.x] = part;
+        }
+        return;
+    }
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
         const int j = jb + 8 * w;
