@@ -117,24 +117,28 @@ template <> struct SrNum<float> {
     using hp = double;
     static constexpr int kind = 0;
     __host__ __device__ static float zero() { return 0.0f; }
+    __host__ __device__ static float one() { return 1.0f; }
     __device__ static float from_hp(double v) { return (float)v; }
 };
 template <> struct SrNum<double> {
     using hp = double;
     static constexpr int kind = 1;
     __host__ __device__ static double zero() { return 0.0; }
+    __host__ __device__ static double one() { return 1.0; }
     __device__ static double from_hp(double v) { return v; }
 };
 template <> struct SrNum<cf> {
     using hp = cd;
     static constexpr int kind = 2;
     __host__ __device__ static cf zero() { return {0.0f, 0.0f}; }
+    __host__ __device__ static cf one() { return {1.0f, 0.0f}; }
     __device__ static cf from_hp(cd v) { return {(float)v.x, (float)v.y}; }
 };
 template <> struct SrNum<cd> {
     using hp = cd;
     static constexpr int kind = 3;
     __host__ __device__ static cd zero() { return {0.0, 0.0}; }
+    __host__ __device__ static cd one() { return {1.0, 0.0}; }
     __device__ static cd from_hp(cd v) { return v; }
 };
 

@@ -137,6 +137,56 @@ template <> struct SolveVec<cd> {
     }
 };
 
+// acc += Ta[0] Tb[0] - Ta[1] Tb[1] over the tile's K = 32 for one thread's
+// 4 x TN block (rows 4tx.., columns TN ty..); a product whose tiles do not
+// exist (hasP / hasM false: beyond the matrix) is skipped, not multiplied by
+// zeros. hasP and hasM are uniform over the threads that share the buffers.
+template <typename T, int TN, int SA>
+__device__ __forceinline__ void tile_pair_products(const T (*Ta)[kSolveTile][SA], const T (*Tb)[kSolveTile][SA],
+                                                   int tx, int ty, bool hasP, bool hasM, T (&acc)[4][TN])
+{
+    constexpr int B = kSolveTile;
+    auto ldb = [&](const T *p, T (&v)[TN]) {
+        if constexpr (TN == 4) {
+            SolveVec<T>::ld4(p, v);
+        } else {
+            SolveVec<T>::ld2(p, v);
+        }
+    };
+    if (hasP && hasM) {
+#pragma unroll 4
+        for (int k = 0; k < B; ++k) {
+            T a[4], b[TN], m[4], c[TN];
+            SolveVec<T>::ld4(&Ta[0][k][4 * tx], a);
+            SolveVec<T>::ld4(&Ta[1][k][4 * tx], m);
+            ldb(&Tb[0][k][TN * ty], b);
+            ldb(&Tb[1][k][TN * ty], c);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    acc[i][j] = sr_fma(a[i], b[j], acc[i][j]);
+                    acc[i][j] = sr_fma(-m[i], c[j], acc[i][j]);
+                }
+        }
+    } else if (hasP || hasM) {
+        const int u = hasP ? 0 : 1;
+        const T sg = hasP ? SrNum<T>::one() : -SrNum<T>::one();
+#pragma unroll 4
+        for (int k = 0; k < B; ++k) {
+            T a[4], b[TN];
+            SolveVec<T>::ld4(&Ta[u][k][4 * tx], a);
+            ldb(&Tb[u][k][TN * ty], b);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const T as = a[i] * sg;
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = sr_fma(as, b[j], acc[i][j]);
+            }
+        }
+    }
+}
+
 template <typename T, bool GROUP = false>
 __global__ void __launch_bounds__(UpdShape<T>::NT)
 trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t *__restrict__ plan,
@@ -187,26 +237,7 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
             acc[i][j] = (x < nr && y < nc && (D > 0 || x > y)) ? TE[sr_idx(r0 + x, c0 + y, ld)] : Z;
         }
     __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < B; ++k) {
-        T a[4], b[TN], m[4], c[TN];
-        SolveVec<T>::ld4(&Ta[0][k][4 * tx], a);
-        SolveVec<T>::ld4(&Ta[1][k][4 * tx], m);
-        if constexpr (TN == 4) {
-            SolveVec<T>::ld4(&Tb[0][k][4 * ty], b);
-            SolveVec<T>::ld4(&Tb[1][k][4 * ty], c);
-        } else {
-            SolveVec<T>::ld2(&Tb[0][k][2 * ty], b);
-            SolveVec<T>::ld2(&Tb[1][k][2 * ty], c);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                acc[i][j] = sr_fma(a[i], b[j], acc[i][j]);
-                acc[i][j] = sr_fma(-m[i], c[j], acc[i][j]);
-            }
-    }
+    tile_pair_products<T, TN, SA>(Ta, Tb, tx, ty, hasP, hasM, acc);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -621,26 +652,7 @@ trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<
                 Tb[1][lx][y] = (hasM && kM + lx < n && c0 + y < n) ? TE[sr_idx(kM + lx, c0 + y, ld)] : Z;
             }
             flow_bar(1 + g, NTG);
-#pragma unroll 4
-            for (int kk = 0; kk < B; ++kk) {
-                T av[4], bv[TN], mv[4], cv[TN];
-                SolveVec<T>::ld4(&Ta[0][kk][4 * tx], av);
-                SolveVec<T>::ld4(&Ta[1][kk][4 * tx], mv);
-                if constexpr (TN == 4) {
-                    SolveVec<T>::ld4(&Tb[0][kk][4 * ty], bv);
-                    SolveVec<T>::ld4(&Tb[1][kk][4 * ty], cv);
-                } else {
-                    SolveVec<T>::ld2(&Tb[0][kk][2 * ty], bv);
-                    SolveVec<T>::ld2(&Tb[1][kk][2 * ty], cv);
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < TN; ++j) {
-                        pacc[i][j] = sr_fma(av[i], bv[j], pacc[i][j]);
-                        pacc[i][j] = sr_fma(-mv[i], cv[j], pacc[i][j]);
-                    }
-            }
+            tile_pair_products<T, TN, SA>(Ta, Tb, tx, ty, hasP, hasM, pacc);
             flow_bar(1 + g, NTG);   // the next operands overwrite this group's buffers
         }
         __syncthreads();
