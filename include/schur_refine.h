@@ -265,6 +265,18 @@ sr_status schur_refine_residuals_noalloc(int n, const void *dA, int lda, const v
 sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, const void *dDiag);
 
 /*
+ * Self-test of the dataflow solve's bounded waits (no counterpart in the
+ * paper): solves a 64 x 64 FP32 problem (2 x 2 tiles) with a launch plan
+ * that lists tile (0, 0) but not the tile (1, 0) it reads, so that the wait
+ * for tile (1, 0) can never be satisfied. The wait gives up after its poll
+ * limit (about a second), the kernel records SR_FLAG_TIMEOUT and returns,
+ * and the call returns SR_ERR_TIMEOUT with the handle and its CUDA context
+ * still usable. Any other result means the bounded wait did not work.
+ * Allocates and frees its own small buffers; synchronizes the stream.
+ */
+sr_status schur_refine_selftest_wait_timeout(schur_refine_t h);
+
+/*
  * One high-precision product with the handle's engine, as used for A Q and
  * Q^H (A Q): C = op(A) B with op(A) = A (transA = 0) or A^H (transA = 1).
  *   dA  device, FP64 (complex128): m x k (transA = 0) or k x m (transA = 1), lda

@@ -31,6 +31,7 @@ EXPORTS = [
     "schur_refine_batched", "schur_refine_residuals", "schur_refine_trisolve",
     "schur_refine_gemm", "schur_refine_get_profile", "schur_refine_reset_profile",
     "schur_refine_destroy", "schur_refine_status_string", "schur_refine_residuals_noalloc",
+    "schur_refine_selftest_wait_timeout",
 ]
 
 
@@ -85,6 +86,7 @@ def lib() -> ctypes.CDLL:
         L.schur_refine_residuals.argtypes = [P, I, P, I, P, I, ctypes.POINTER(D), ctypes.POINTER(D)]
         L.schur_refine_residuals_noalloc.argtypes = [I, P, I, P, I, ctypes.POINTER(D), ctypes.POINTER(D), P]
         L.schur_refine_trisolve.argtypes = [P, I, P, I, P]
+        L.schur_refine_selftest_wait_timeout.argtypes = [P]
         L.schur_refine_gemm.argtypes = [P, I, I, I, I, P, I, P, I, P, I]
         L.schur_refine_get_profile.argtypes = [P, ctypes.POINTER(sr_profile)]
         L.schur_refine_reset_profile.argtypes = [P]
@@ -95,7 +97,7 @@ def lib() -> ctypes.CDLL:
         for f in ("schur_refine_create", "schur_refine_step", "schur_refine_batched",
                   "schur_refine_residuals", "schur_refine_trisolve", "schur_refine_gemm",
                   "schur_refine_get_profile", "schur_refine_reset_profile",
-                  "schur_refine_residuals_noalloc"):
+                  "schur_refine_residuals_noalloc", "schur_refine_selftest_wait_timeout"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -211,6 +213,10 @@ def schur_refine_trisolve(h, n: int, TE, diag):
     pt, ld = _dev(TE, "TE")
     pd, _ = _dev(diag, "diag")
     return lib().schur_refine_trisolve(h, int(n), pt, ld, pd)
+
+
+def schur_refine_selftest_wait_timeout(h):
+    return lib().schur_refine_selftest_wait_timeout(h)
 
 
 def schur_refine_gemm(h, transA: int, m: int, n: int, k: int, A, B, C):

@@ -720,3 +720,68 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
     }
     return first;
 }
+
+// schur_refine_selftest_wait_timeout: the group form of the dataflow solve on
+// one 64 x 64 FP32 matrix with a plan that omits tile (1, 0), which tile
+// (0, 0) reads; the kernel's wait for it runs out, SR_FLAG_TIMEOUT is set in
+// the matrix's error word and the launch ends. Every access stays inside the
+// buffers allocated here.
+sr_status sr_flow_selftest(schur_refine_ctx *h)
+{
+    using namespace sr;
+    constexpr int n = 64, NB = 2;
+    cudaStream_t st = h->st;
+    float *TE = nullptr;
+    double *diag = nullptr;
+    SolveMat *mat = nullptr;
+    unsigned long long *plan = nullptr;
+    int *flags = nullptr, *work = nullptr;
+    auto release = [&]() {
+        cudaFree(TE);
+        cudaFree(diag);
+        cudaFree(mat);
+        cudaFree(plan);
+        cudaFree(flags);
+        cudaFree(work);
+    };
+    const size_t nwords = 2 + (size_t)NB * NB;
+    cudaError_t e = cudaMalloc((void **)&TE, (size_t)n * n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&diag, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&mat, sizeof(SolveMat));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&plan, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&flags, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&work, nwords * sizeof(int));
+    if (e != cudaSuccess) {
+        sr_set_last_cuda_error(e);
+        cudaGetLastError();
+        release();
+        return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
+    }
+    // T = diag(1, 2, ..., 64), E = 0: a well-posed problem, were the plan complete
+    std::vector<float> hT((size_t)n * n, 0.0f);
+    std::vector<double> hd(n);
+    for (int i = 0; i < n; ++i) {
+        hT[(size_t)i + (size_t)i * n] = (float)(i + 1);
+        hd[i] = i + 1.0;
+    }
+    const SolveMat hm{TE, n, n, diag, 0};
+    const unsigned long long hp = 0ull;   // matrix 0, tile (0, 0) only
+    e = cudaMemcpyAsync(TE, hT.data(), hT.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(diag, hd.data(), n * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mat, &hm, sizeof(hm), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(plan, &hp, sizeof(hp), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(trisolve_flow_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FlowShape<float>::smem);
+    if (e == cudaSuccess) e = trisolve_flow_launch_group<float>(st, mat, flags, work, nwords, plan, 1, 1);
+    int hf = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) {
+        sr_set_last_cuda_error(e);
+        return SR_ERR_CUDA;
+    }
+    return (hf & SR_FLAG_TIMEOUT) ? SR_ERR_TIMEOUT : SR_OK;
+}

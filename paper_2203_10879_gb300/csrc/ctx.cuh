@@ -74,4 +74,6 @@ struct schur_refine_ctx {
 sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *n, const void *const *dA, void *const *dQ,
                           const void *const *dQhat, int *iters_out, int *status_out);
 bool sr_batch_supported(const sr_options &o);
+// schur_refine_selftest_wait_timeout (batch.cu: the group form of the dataflow solve)
+sr_status sr_flow_selftest(schur_refine_ctx *h);
 void sr_batch_free(BatchWork *bw);

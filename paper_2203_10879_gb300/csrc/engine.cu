@@ -1564,6 +1564,12 @@ sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, cons
     return SR_OK;
 }
 
+sr_status schur_refine_selftest_wait_timeout(schur_refine_t h)
+{
+    if (!h) return SR_ERR_INVALID_ARG;
+    return sr_flow_selftest(h);
+}
+
 sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, const void *dA, int lda,
                             const void *dB, int ldb, void *dC, int ldc)
 {

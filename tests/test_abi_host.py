@@ -51,6 +51,7 @@ def test_null_handle_and_bad_arguments(L):
     assert L.schur_refine_step(None, 4, P(1), 4, P(1), 4, None, None, None) == B.SR_ERR_INVALID_ARG
     assert L.schur_refine_residuals(None, 4, P(1), 4, P(1), 4, None, None) == B.SR_ERR_INVALID_ARG
     assert L.schur_refine_trisolve(None, 4, P(1), 4, P(1)) == B.SR_ERR_INVALID_ARG
+    assert L.schur_refine_selftest_wait_timeout(None) == B.SR_ERR_INVALID_ARG
     assert L.schur_refine_gemm(None, 0, 4, 4, 4, P(1), 4, P(1), 4, P(1), 4) == B.SR_ERR_INVALID_ARG
     assert L.schur_refine_batched(None, 1, None, None, None, None, None, None) == B.SR_ERR_INVALID_ARG
     p = B.sr_profile()
