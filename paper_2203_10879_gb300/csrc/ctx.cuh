@@ -35,10 +35,14 @@ struct schur_refine_ctx {
     cudaEvent_t sev0 = nullptr, sev1 = nullptr;
     struct SolveGraph { int n; const void *TE; int ld; const void *dhp; const void *dlo; int kind; cudaGraphExec_t exec; };
     std::vector<SolveGraph> graphs;
-    // dataflow solve (see opt.solve_mode): ticket, abort and published words of
-    // 2 + NB^2 ints; grid per low-precision kind (float, double, complex64)
+    // dataflow solve (see opt.solve_mode): ticket, abort, published and helper
+    // words, 2 + 2 NB^2 ints; grid per low-precision kind (float, double, complex64)
     int *flow = nullptr;
     int flow_ctas[3] = {0, 0, 0};
+    void *flow_acc = nullptr;                   // helpers' accumulators (n_max^2, low precision)
+    unsigned long long *flow_plan = nullptr;    // task list for order flow_plan_n
+    size_t flow_plan_cap = 0;
+    int flow_plan_n = 0, flow_ntasks = 0;
     // schur_refine_batched: grouped-launch workspace, or worker sub-handles on their own streams
     BatchWork *bw = nullptr;
     std::vector<schur_refine_ctx *> subs;

@@ -35,6 +35,46 @@ void sr::trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long lon
     }
 }
 
+void sr::trisolve_flow_plan(int n, std::vector<unsigned long long> &tasks)
+{
+    trisolve_flow_plan(n, tasks, kFlowNear, kFlowChunk, kFlowFarNum, kFlowLag);
+}
+
+void sr::trisolve_flow_plan(int n, std::vector<unsigned long long> &tasks, int near, int chunk, int far_num, int lag)
+{
+    using ull = unsigned long long;
+    const int NB = (n + kSolveTile - 1) / kSolveTile;
+    const int far = (far_num * NB) / 16;   // helpers take subdiagonals d >= far only
+    near = std::max(near, 1);
+    chunk = std::max(chunk, 1);
+    lag = std::max(0, std::min(lag, near - 1));   // a helper (lo >= D + near) precedes its owner
+    std::vector<std::vector<ull>> enabled(NB);   // helpers by the subdiagonal that completes their inputs
+    std::vector<int> nh((size_t)NB * NB, 0), own((size_t)NB * NB, 0);
+    for (int D = 0; D < NB; ++D)
+        for (int J = 0; J + D < NB; ++J) {
+            const int I = J + D, top = std::max(NB - 1 - J, I), dF = std::max(D + near, far);
+            own[(size_t)I * NB + J] = std::min(top, dF - 1);   // the owner's highest subdiagonal
+            if (top < dF) continue;
+            const int cnt = (top - dF + chunk) / chunk;
+            nh[(size_t)I * NB + J] = cnt;
+            for (int h = 0; h < cnt; ++h) {
+                const int hi = top - h * chunk, lo = std::max(dF, hi - chunk + 1);
+                enabled[lo].push_back(1ull << 63 | (ull)h << 56 | (ull)hi << 44 | (ull)lo << 32 | (ull)I << 16 |
+                                      (ull)J);
+            }
+        }
+    // the helpers that subdiagonal t completes follow the solves of t - lag:
+    // the next steps' solves (the critical path) are claimed before them
+    tasks.clear();
+    for (int t = NB - 1; t >= 0; --t) {
+        for (int J = 0; J + t < NB; ++J) {
+            const size_t x = (size_t)(J + t) * NB + J;
+            tasks.push_back((ull)own[x] << 48 | (ull)nh[x] << 32 | (ull)(J + t) << 16 | (ull)J);
+        }
+        if (t + lag < NB) tasks.insert(tasks.end(), enabled[t + lag].begin(), enabled[t + lag].end());
+    }
+}
+
 void sr::trisolve_plan_group(const std::vector<int> &orders, std::vector<unsigned long long> &tiles,
                              std::vector<long long> &offsets, std::vector<long long> &nleaf)
 {
@@ -271,6 +311,39 @@ sr_status ensure_plan(schur_refine_ctx *h, int n)
     return SR_OK;
 }
 
+// task list of the dataflow solve for order n (host work and a
+// synchronization: built before any capture)
+sr_status ensure_flow_plan(schur_refine_ctx *h, int n)
+{
+    if (h->flow_plan_n == n) return SR_OK;
+    std::vector<unsigned long long> tasks;
+    sr::trisolve_flow_plan(n, tasks);
+    if (tasks.size() > h->flow_plan_cap) {
+        SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+        cudaFree(h->flow_plan);
+        h->flow_plan = nullptr;
+        h->flow_plan_cap = 0;
+        cudaError_t e = cudaMalloc((void **)&h->flow_plan, tasks.size() * sizeof(unsigned long long));
+        if (e != cudaSuccess) {
+            sr_set_last_cuda_error(e);
+            return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
+        }
+        h->flow_plan_cap = tasks.size();
+    }
+    SR_CUDA_TRY(cudaMemcpyAsync(h->flow_plan, tasks.data(), tasks.size() * sizeof(unsigned long long),
+                                cudaMemcpyHostToDevice, h->st));
+    SR_CUDA_TRY(cudaStreamSynchronize(h->st));   // tasks is a temporary
+    h->flow_plan_n = n;
+    h->flow_ntasks = (int)tasks.size();
+    return SR_OK;
+}
+
+// the dataflow form serves this solve (see sr_options.solve_mode)
+bool use_flow(const schur_refine_ctx *h, int kind)
+{
+    return kind <= 2 && h->flow_acc && (h->opt.solve_mode == 1 || (h->opt.solve_mode == 0 && kind == 0));
+}
+
 template <typename Tl>
 sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum<Tl>::hp *dhp,
                 const double *dlo = nullptr)
@@ -278,12 +351,13 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
     const int NB = (n + sr::kSolveTile - 1) / sr::kSolveTile;
     const int kind = SrNum<Tl>::kind;
     if constexpr (SrNum<Tl>::kind <= 2) {
-        const int mode = h->opt.solve_mode;
-        if (mode == 1 || (mode == 0 && kind == 0)) {
+        if (use_flow(h, kind)) {
             // one launch: the dataflow over the tiles
+            SR_TRY(ensure_flow_plan(h, n));
             const long long fl = 2LL * n * n * n / 3 * (kind == 2 ? 4 : 1);
             SrPhase ph(h, SR_PROF_SOLVE, fl, (long long)n * n * (long long)sizeof(Tl), 1);
-            SR_CUDA_TRY(sr::trisolve_flow_launch<Tl>(h->st, n, TE, ld, dhp, dlo, h->dflags, h->flow,
+            SR_CUDA_TRY(sr::trisolve_flow_launch<Tl>(h->st, n, TE, ld, dhp, dlo, h->dflags, h->flow, h->flow_plan,
+                                                     h->flow_ntasks, (Tl *)h->flow_acc, h->nmax,
                                                      h->flow_ctas[kind]));
             return SR_OK;
         }
@@ -816,6 +890,7 @@ sr_status build_refine_graph(schur_refine_ctx *h, int n, const void *dA, int lda
     const double *A = (const double *)dA;
     if (!h->ctl) SR_CUDA_TRY(cudaMalloc(&h->ctl, sizeof(SrCtl)));
     SR_TRY(ensure_plan(h, n));   // host work and a synchronization: not inside a capture
+    SR_TRY(ensure_flow_plan(h, n));
     while (h->cstreams.empty()) {
         cudaStream_t s = nullptr;
         SR_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -1275,6 +1350,8 @@ void schur_refine_destroy(schur_refine_t h)
     cudaFree(h->dnorm);
     cudaFree(h->dflags);
     cudaFree(h->flow);
+    cudaFree(h->flow_acc);
+    cudaFree(h->flow_plan);
     if (h->hbuf) cudaFreeHost(h->hbuf);
     sr::ozaki_free(h->oz);
     delete h;
@@ -1321,7 +1398,10 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     SR_ALLOC(h->dnorm, 8 * sizeof(double));
     SR_ALLOC(h->dflags, sizeof(int));
     const size_t nbmax = (size_t)(n_max + sr::kSolveTile - 1) / sr::kSolveTile;
-    SR_ALLOC(h->flow, (2 + nbmax * nbmax) * sizeof(int));
+    SR_ALLOC(h->flow, (2 + 2 * nbmax * nbmax) * sizeof(int));
+    // the dataflow solve's helper accumulators, where that form can serve
+    if ((o.dtype == SR_REAL && o.lp == SR_LP_FP32 && o.solve_mode == 0) || o.solve_mode == 1)
+        SR_ALLOC(h->flow_acc, nn * lps);
 #undef SR_ALLOC
     if (e == cudaSuccess) {
         // grid of the dataflow solve for each low-precision kind this handle can use

@@ -60,6 +60,22 @@ __device__ inline double sr_div_round_dd(double hi_i, double lo_i, double hi_j, 
 // followed by the tiles with D < t that receive a product of subdiagonal t+1.
 void trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long long> &offsets);
 
+// Task list of the dataflow solve of one matrix (trisolve_flow_kernel): for
+// s = NB-1 down to 0, the solve tasks of block subdiagonal s, then the helper
+// tasks that subdiagonal s+1 is the last input of. A tile (I, J), D = I - J,
+// whose products reach the subdiagonals d >= max(D + kFlowNear, kFlowFarNum
+// NB / 16) leaves those (up to top = max(NB-1-J, I)) to helpers, kFlowChunk
+// subdiagonals each, the highest first.
+//   solve:  bit 63 = 0, J (bits 0-15), I (16-31), helper count (32-47),
+//           the owner's highest subdiagonal (48-59)
+//   helper: bit 63 = 1, J, I, lowest d (32-43), highest d (44-55), index (56-62)
+constexpr int kFlowNear = 8;
+constexpr int kFlowChunk = 16;
+constexpr int kFlowFarNum = 8;   // helpers only for d >= kFlowFarNum NB / 16
+constexpr int kFlowLag = 3;      // helpers completed by subdiagonal t follow the solves of t - kFlowLag
+void trisolve_flow_plan(int n, std::vector<unsigned long long> &tasks);
+void trisolve_flow_plan(int n, std::vector<unsigned long long> &tasks, int near, int chunk, int far_num, int lag);
+
 // A group of independent solves in the same launches (schur_refine_batched):
 // matrix b of the group, and its tiles in the plan as (b << 32 | I << 16 | J).
 struct SolveMat {
@@ -137,15 +153,15 @@ template <> struct SolveVec<cd> {
     }
 };
 
-// acc += Ta[0] Tb[0] - Ta[1] Tb[1] over the tile's K = 32 for one thread's
+// acc += Ta[0] Tb[0] - Ta[1] Tb[1] over the buffers' KB values of k for one thread's
 // 4 x TN block (rows 4tx.., columns TN ty..); a product whose tiles do not
 // exist (hasP / hasM false: beyond the matrix) is skipped, not multiplied by
 // zeros. hasP and hasM are uniform over the threads that share the buffers.
-template <typename T, int TN, int SA>
-__device__ __forceinline__ void tile_pair_products(const T (*Ta)[kSolveTile][SA], const T (*Tb)[kSolveTile][SA],
-                                                   int tx, int ty, bool hasP, bool hasM, T (&acc)[4][TN])
+template <typename T, int TN, int SA, int KB = kSolveTile>
+__device__ __forceinline__ void tile_pair_products(const T (*Ta)[KB][SA], const T (*Tb)[KB][SA], int tx, int ty,
+                                                   bool hasP, bool hasM, T (&acc)[4][TN])
 {
-    constexpr int B = kSolveTile;
+    constexpr int B = KB;
     auto ldb = [&](const T *p, T (&v)[TN]) {
         if constexpr (TN == 4) {
             SolveVec<T>::ld4(p, v);
@@ -427,10 +443,10 @@ inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cu
 // wavefront's steps are barrier-bound: few entries per thread keep them
 // short), and two CTAs share an SM, so one CTA's products run while the
 // other waits at its wavefront's barriers. The products of one tile are
-// split over NG groups of NTG threads (subdiagonals d = top-g, top-g-NG, ...
-// for group g), each with its own operand buffers and named barrier, so a
-// group waits only on its own inputs; the partial sums meet in shared memory
-// before the solve.
+// split over NPP pair lanes (subdiagonals d = top-l, top-l-NPP, ... for lane
+// l) of two groups each, one per half of K; every group has its own operand
+// buffers and named barrier, so it waits only on its own inputs; the partial
+// sums meet in shared memory before the solve.
 //
 // Forward progress does not need the CTAs to be co-resident: the inputs of a
 // tile lie on higher subdiagonals and so hold smaller tickets, and a ticket
@@ -439,8 +455,17 @@ inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cu
 // that runs out sets SR_FLAG_TIMEOUT and an abort word that ends all other
 // waits, and the launch runs to its end without further waiting.
 //
+// Helper tasks (one matrix): the products of the subdiagonals d >= D + kFlowNear
+// of a tile are computed ahead, as soon as those subdiagonals are published,
+// by helper tasks of kFlowChunk subdiagonals each; they add into the tile's
+// accumulator in a fixed order (helper h waits until h helpers are done), and
+// the owner adds E, that sum and its own products of the nearest subdiagonals.
+// Without them, the products of the tiles far down the wavefront pile up at
+// its end, when the subdiagonals hold the most tiles.
+//
 // work[0]: ticket counter; work[1]: abort word; work[2 + I NB + J]: tile
-// (I, J) published. The launcher clears them before the kernel.
+// (I, J) published; work[2 + NB^2 + I NB + J]: helpers of tile (I, J) done.
+// The launcher clears them before the kernel.
 template <typename T> struct FlowShape {
     using Hp = typename SrNum<T>::hp;
     static constexpr int B = kSolveTile;
@@ -448,17 +473,21 @@ template <typename T> struct FlowShape {
     static constexpr int EPT = B * B / NT;          // entries of the tile per thread in the solve
     static constexpr int WS = NT / 32;              // warps: thread (a, w) owns columns w + WS q
     // products: rows 4tx.., columns TN ty.. per thread (TN = 4: 64 threads a
-    // group; TN = 2: 128) and NG groups, as many as half the shared memory holds
+    // group; TN = 2: 128); every thread is in a group, and the two groups of a
+    // pair lane take the two halves (KH) of the subdiagonal's K = 32
     static constexpr int TN = SrNum<T>::kind == 0 ? 4 : 2;
     static constexpr int NTG = 8 * (B / TN);
-    static constexpr int NG = SrNum<T>::kind == 0 ? 4 : 2;
+    static constexpr int NG = NT / NTG;             // groups
+    static constexpr int NPP = NG / 2;              // pair lanes: subdiagonals in flight
+    static constexpr int KH = B / 2;
     static constexpr int SA = B + 4;                // row stride of the operand buffers
     static constexpr int SX = B + 1;                // row stride of the solve's tiles
-    static constexpr size_t kSlot = 4 * B * SA;     // elements of one group's operands
+    static constexpr size_t kSlot = 4 * KH * SA;    // elements of one group's operands
     static constexpr size_t smem = (NG * kSlot + 3 * B * SX) * sizeof(T) + 2 * B * (sizeof(Hp) + sizeof(double))
                                    + 16;
-    static_assert(NG * NTG <= NT, "product groups exceed the CTA");
+    static_assert(NG * NTG == NT && NG % 2 == 0, "pairs of groups fill the CTA");
     static_assert(EPT * NT == B * B, "one or more whole entries per thread");
+    static_assert(kSlot >= (size_t)B * SX, "a group's buffers hold its partial sums");
 };
 constexpr int kFlowSpin = 1 << 22;   // polls of one wait (a few hundred ns apart)
 
@@ -472,17 +501,18 @@ __device__ inline void flow_st_release(int *p, int v)
 {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-// Wait, by a whole warp, until the published flag *f is set; false after an
-// abort or a timeout. Lane 0 loads (acquire) and broadcasts, so every branch
-// is uniform over the warp and the warp stays converged for the barrier that
+// Wait, by a whole warp, until the word *f reaches `target` (a published
+// flag: 1; a helper count: the number of helpers done); false after an abort
+// or a timeout. Lane 0 loads (acquire) and broadcasts, so every branch is
+// uniform over the warp and the warp stays converged for the barrier that
 // follows.
-__device__ inline bool flow_wait(const int *f, int *abort_w, int *flags)
+__device__ inline bool flow_wait(const int *f, int *abort_w, int *flags, int target = 1)
 {
     const unsigned lane = threadIdx.x & 31u;
     for (int it = 0; it < kFlowSpin; ++it) {
         int v = 0, ab = 0;
         if (lane == 0) {
-            v = flow_ld_acquire(f);
+            v = flow_ld_acquire(f) >= target;
             if (!v) ab = *(volatile int *)abort_w;
         }
         v = __shfl_sync(0xffffffffu, v, 0);
@@ -513,29 +543,17 @@ __device__ inline cf flow_ldcg(const cf *p)
     const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
     return {v.x, v.y};
 }
-// ticket k -> tile (I, J): the m-th subdiagonal from the corner (D = NB-1-m)
-// holds m+1 tiles and starts at ticket m(m+1)/2
-__device__ inline void flow_tile(int k, int NB, int &I, int &J)
-{
-    int m = (int)((sqrtf(8.0f * (float)k + 1.0f) - 1.0f) * 0.5f);
-    while (m > 0 && m * (m + 1) / 2 > k) --m;
-    while ((m + 1) * (m + 2) / 2 <= k) ++m;
-    J = k - m * (m + 1) / 2;
-    I = J + (NB - 1 - m);
-}
-
 template <typename T, bool GROUP = false>
 __global__ void __launch_bounds__(FlowShape<T>::NT, 2)
 trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<T>::hp *__restrict__ dhp0,
                      const double *__restrict__ dlo, int *__restrict__ flags0, int *__restrict__ work,
-                     const SolveMat *__restrict__ mats = nullptr, const unsigned long long *__restrict__ gplan = nullptr,
-                     int gtiles = 0)
+                     const unsigned long long *__restrict__ plan, int ntasks, T *__restrict__ accb, int ldacc,
+                     const SolveMat *__restrict__ mats = nullptr)
 {
     using S = FlowShape<T>;
     using Hp = typename SrNum<T>::hp;
     constexpr int B = S::B, SA = S::SA, SX = S::SX, NTG = S::NTG, NG = S::NG, TN = S::TN, EPT = S::EPT,
-                  WS = S::WS;
-    constexpr int LR = NTG / 32;
+                  WS = S::WS, NPP = S::NPP, KH = S::KH;
     extern __shared__ __align__(16) unsigned char flow_smem[];
     T *ops = reinterpret_cast<T *>(flow_smem);
     T (*Ti)[SX] = reinterpret_cast<T (*)[SX]>(ops + NG * S::kSlot);
@@ -548,13 +566,12 @@ trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<
     int *s_ticket = reinterpret_cast<int *>(dJl + B);
 
     const int tid = threadIdx.x;
-    const int ntiles = GROUP ? gtiles : ((n0 + B - 1) / B) * ((n0 + B - 1) / B + 1) / 2;
     int *abort_w = work + 1;
-    const int g = tid / NTG, gt = tid % NTG;   // product group (g < NG takes part)
-    T *slot = ops + (g < NG ? g : 0) * S::kSlot;
-    T (*Ta)[B][SA] = reinterpret_cast<T (*)[B][SA]>(slot);             // Ta[u][k][row]
-    T (*Tb)[B][SA] = reinterpret_cast<T (*)[B][SA]>(slot + 2 * B * SA);   // Tb[u][k][col]
-    const int lx = gt & 31, ly = gt >> 5;   // operand loads: element (lx, ly + LR q)
+    const int g = tid / NTG, gt = tid % NTG;   // product group
+    const int pl = g >> 1, kh = g & 1;         // its pair lane and half of K
+    T *slot = ops + g * S::kSlot;
+    T (*Ta)[KH][SA] = reinterpret_cast<T (*)[KH][SA]>(slot);               // Ta[u][k][row]
+    T (*Tb)[KH][SA] = reinterpret_cast<T (*)[KH][SA]>(slot + 2 * KH * SA);   // Tb[u][k][col]
     const int tx = gt & 7, ty = gt >> 3;    // products: rows 4tx.., columns TN ty..
     const int a = tid & 31, wq = tid >> 5;  // solve: entries (a, wq + WS q), q < EPT
     const T Z = SrNum<T>::zero();
@@ -564,30 +581,118 @@ trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<
         if (tid == 0) *s_ticket = atomicAdd(work, 1);
         __syncthreads();
         const int k = *s_ticket;
-        if (k >= ntiles) break;
-        // the tile and its matrix (a group: from the plan; each matrix has
-        // its own error word and published words)
-        int n = n0, ld = ld0, I, J;
+        if (k >= ntasks) break;
+        // the task, its tile and matrix (a group: matrix b of the plan entry
+        // b << 32 | I << 16 | J, with its own error word and published words;
+        // one matrix: solve and helper tasks)
+        const unsigned long long task = plan[k];
+        int n = n0, ld = ld0;
         T *TE = TE0;
         const Hp *dhp = dhp0;
         int *flags = flags0, *pub = work + 2;
+        const int I = (int)((task >> 16) & 0xffffu), J = (int)(task & 0xffffu);
+        bool helper = false;
+        int nhelp = 0, dlow = 0, dhigh = 0, hidx = 0;
         if constexpr (GROUP) {
-            const unsigned long long gp = gplan[k];
-            const SolveMat m = mats[gp >> 32];
+            const SolveMat m = mats[task >> 32];
             TE = (T *)m.TE;
             ld = m.ld;
             n = m.n;
             dhp = (const Hp *)m.dhp;
-            flags += (gp >> 32);
+            flags += (task >> 32);
             pub += m.fbase;
-            I = (int)((uint32_t)gp >> 16);
-            J = (int)(gp & 0xffffu);
         } else {
-            flow_tile(k, (n + B - 1) / B, I, J);
+            helper = (task >> 63) != 0;
+            if (helper) {
+                dlow = (int)((task >> 32) & 0xfffu);
+                dhigh = (int)((task >> 44) & 0xfffu);
+                hidx = (int)((task >> 56) & 0x7fu);
+            } else {
+                nhelp = (int)((task >> 32) & 0xffffu);
+                dhigh = (int)((task >> 48) & 0xfffu);
+            }
         }
         const int NB = (n + B - 1) / B;
+        int *cnt = pub + NB * NB;   // helpers done per tile (one matrix only)
         const int D = I - J, r0 = I * B, c0 = J * B;
         const int nr = min(B, n - r0), nc = min(B, n - c0);
+
+        // the pair products of subdiagonals d = dh - pl, dh - pl - NPP, ... >= dl,
+        // each over this group's half of K, into pacc
+        T pacc[4][TN];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) pacc[i][j] = Z;
+        auto pair_products = [&](int dh, int dl) {
+            for (int d = dh - pl; d >= dl; d -= NPP) {
+                const bool hasP = J + d < NB, hasM = I - d >= 0;
+                if (gt < 32) {   // the group's first warp waits for both inputs
+                    bool ok = true;
+                    if (hasP) ok = flow_wait(pub + (J + d) * NB + J, abort_w, flags);
+                    if (ok && hasM) flow_wait(pub + I * NB + (I - d), abort_w, flags);
+                }
+                flow_bar(1 + g, NTG);
+                const int kP = (J + d) * B + kh * KH, kM = (I - d) * B + kh * KH;
+                // left operands: 32 rows x KH, rows along the lanes
+#pragma unroll
+                for (int e = gt; e < B * KH; e += NTG) {
+                    const int row = e & 31, kk = e >> 5;
+                    Ta[0][kk][row] = (hasP && r0 + row < n && kP + kk < n) ? TE[sr_idx(r0 + row, kP + kk, ld)] : Z;
+                    Ta[1][kk][row] =
+                        (hasM && r0 + row < n && kM + kk < n) ? flow_ldcg(&TE[sr_idx(r0 + row, kM + kk, ld)]) : Z;
+                }
+                // right operands: KH x 32 columns, k along the lanes
+#pragma unroll
+                for (int e = gt; e < KH * B; e += NTG) {
+                    const int kk = e % KH, col = e / KH;
+                    Tb[0][kk][col] =
+                        (hasP && kP + kk < n && c0 + col < n) ? flow_ldcg(&TE[sr_idx(kP + kk, c0 + col, ld)]) : Z;
+                    Tb[1][kk][col] = (hasM && kM + kk < n && c0 + col < n) ? TE[sr_idx(kM + kk, c0 + col, ld)] : Z;
+                }
+                flow_bar(1 + g, NTG);
+                tile_pair_products<T, TN, SA, KH>(Ta, Tb, tx, ty, hasP, hasM, pacc);
+                flow_bar(1 + g, NTG);   // the next operands overwrite this group's buffers
+            }
+        };
+        // the groups' partial sums, each into its own operand buffer (after a
+        // barrier: every group is done with its operands)
+        auto store_partials = [&]() {
+            T (*P)[SX] = reinterpret_cast<T (*)[SX]>(slot);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) P[4 * tx + i][TN * ty + j] = pacc[i][j];
+        };
+        auto partial_sum = [&](int b) {
+            T v = Z;
+#pragma unroll
+            for (int gg = 0; gg < NG; ++gg) v = v + reinterpret_cast<const T (*)[SX]>(ops + gg * S::kSlot)[a][b];
+            return v;
+        };
+
+        if (helper) {
+            // helper: subdiagonals dhigh .. dlow of tile (I, J) into its
+            // accumulator, after the helper before it (a fixed order of sums)
+            pair_products(dhigh, dlow);
+            __syncthreads();
+            store_partials();
+            if (tid < 32) flow_wait(cnt + I * NB + J, abort_w, flags, hidx);
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                const int b = wq + WS * q;
+                if (a < nr && b < nc) {
+                    T *pa = &accb[sr_idx(r0 + a, c0 + b, ldacc)];
+                    const T prev = hidx ? flow_ldcg(pa) : Z;
+                    *pa = prev + partial_sum(b);
+                }
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) flow_st_release(cnt + I * NB + J, hidx + 1);
+            continue;
+        }
 
         // inputs that no tile writes: T_II, T_JJ, the diagonals and E_IJ
 #pragma unroll
@@ -627,51 +732,21 @@ trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<
             rcp[q] = (own[q] && !(den == Z)) ? sr_recip(den) : Z;
         }
 
-        // products of subdiagonals d = top-g, top-g-NG, ..., > D
-        T pacc[4][TN];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < TN; ++j) pacc[i][j] = Z;
+        // the owner's products: the subdiagonals its helpers leave (all of
+        // them without helpers)
         const int top = max(NB - 1 - J, I);
-        for (int d = top - g; g < NG && d > D; d -= NG) {
-            const bool hasP = J + d < NB, hasM = I - d >= 0;
-            if (gt < 32) {   // the group's first warp waits for both inputs
-                bool ok = true;
-                if (hasP) ok = flow_wait(pub + (J + d) * NB + J, abort_w, flags);
-                if (ok && hasM) flow_wait(pub + I * NB + (I - d), abort_w, flags);
-            }
-            flow_bar(1 + g, NTG);
-            const int kP = (J + d) * B, kM = (I - d) * B;
-#pragma unroll
-            for (int q = 0; q < 32 / LR; ++q) {
-                const int y = ly + LR * q;
-                Ta[0][y][lx] = (hasP && r0 + lx < n && kP + y < n) ? TE[sr_idx(r0 + lx, kP + y, ld)] : Z;
-                Tb[0][lx][y] = (hasP && kP + lx < n && c0 + y < n) ? flow_ldcg(&TE[sr_idx(kP + lx, c0 + y, ld)]) : Z;
-                Ta[1][y][lx] = (hasM && r0 + lx < n && kM + y < n) ? flow_ldcg(&TE[sr_idx(r0 + lx, kM + y, ld)]) : Z;
-                Tb[1][lx][y] = (hasM && kM + lx < n && c0 + y < n) ? TE[sr_idx(kM + lx, c0 + y, ld)] : Z;
-            }
-            flow_bar(1 + g, NTG);
-            tile_pair_products<T, TN, SA>(Ta, Tb, tx, ty, hasP, hasM, pacc);
-            flow_bar(1 + g, NTG);   // the next operands overwrite this group's buffers
-        }
+        pair_products(GROUP ? top : dhigh, D + 1);
         __syncthreads();
-        // the groups' partial sums, each in its own operand buffer, added to E
-        if (g < NG) {
-            T (*P)[SX] = reinterpret_cast<T (*)[SX]>(slot);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j) P[4 * tx + i][TN * ty + j] = pacc[i][j];
-        }
+        store_partials();
+        if (nhelp && tid < 32) flow_wait(cnt + I * NB + J, abort_w, flags, nhelp);
         __syncthreads();
+        // E, then the helpers' sum, then the groups' partial sums
 #pragma unroll
-        for (int q = 0; q < EPT; ++q)
-#pragma unroll
-            for (int gg = 0; gg < NG; ++gg) {
-                const T (*P)[SX] = reinterpret_cast<const T (*)[SX]>(ops + gg * S::kSlot);
-                acc[q] = acc[q] + P[a][wq + WS * q];
-            }
+        for (int q = 0; q < EPT; ++q) {
+            const int b = wq + WS * q;
+            if (nhelp && own[q]) acc[q] = acc[q] + flow_ldcg(&accb[sr_idx(r0 + a, c0 + b, ldacc)]);
+            acc[q] = acc[q] + partial_sum(b);
+        }
 
         // wavefront over the tile's subdiagonals w (see trisolve_leaf_kernel);
         // an entry with a zero divisor is set to zero and flagged
@@ -712,10 +787,10 @@ trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<
     }
 }
 
-// The dataflow solve of a group (no double-double divisors): plan = the
-// tiles (b << 32 | I << 16 | J) in an order that lists every tile after its
-// inputs; mats[b].fbase = start of matrix b's NB_b^2 published words in
-// work + 2; nwords = 2 + their total.
+// The dataflow solve of a group (no double-double divisors, no helpers):
+// plan = the tiles (b << 32 | I << 16 | J) in an order that lists every tile
+// after its inputs; mats[b].fbase = start of matrix b's NB_b^2 published
+// words in work + 2; nwords = 2 + their total.
 template <typename T>
 inline cudaError_t trisolve_flow_launch_group(cudaStream_t st, const SolveMat *mats, int *flags, int *work,
                                               size_t nwords, const unsigned long long *plan, int ntiles, int ctas)
@@ -723,23 +798,26 @@ inline cudaError_t trisolve_flow_launch_group(cudaStream_t st, const SolveMat *m
     cudaError_t e = cudaMemsetAsync(work, 0, nwords * sizeof(int), st);
     if (e != cudaSuccess || ntiles < 1) return e;
     trisolve_flow_kernel<T, true><<<(unsigned)std::max(1, std::min(ctas, ntiles)), FlowShape<T>::NT,
-                                    FlowShape<T>::smem, st>>>(0, nullptr, 0, nullptr, nullptr, flags, work, mats, plan,
-                                                              ntiles);
+                                    FlowShape<T>::smem, st>>>(0, nullptr, 0, nullptr, nullptr, flags, work, plan,
+                                                              ntiles, nullptr, 0, mats);
     return cudaGetLastError();
 }
 
-// Clears the flow state and launches the dataflow solve on st with at most
-// `ctas` CTAs (one ticket loop each). work holds 2 + NB^2 ints.
+// Clears the flow state and launches the dataflow solve of one matrix on st
+// with at most `ctas` CTAs (one ticket loop each): plan = trisolve_flow_plan's
+// tasks (device), accb = the helpers' accumulators (n x n, leading dimension
+// ldacc), work = 2 + 2 NB^2 ints (ticket, abort, published words, helper
+// counts).
 template <typename T>
 inline cudaError_t trisolve_flow_launch(cudaStream_t st, int n, T *TE, int ld, const typename SrNum<T>::hp *dhp,
-                                        const double *dlo, int *flags, int *work, int ctas)
+                                        const double *dlo, int *flags, int *work, const unsigned long long *plan,
+                                        int ntasks, T *accb, int ldacc, int ctas)
 {
     const int NB = (n + kSolveTile - 1) / kSolveTile;
-    const int nt = NB * (NB + 1) / 2;
-    cudaError_t e = cudaMemsetAsync(work, 0, (2 + (size_t)NB * NB) * sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(work, 0, (2 + 2 * (size_t)NB * NB) * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    trisolve_flow_kernel<T><<<(unsigned)std::max(1, std::min(ctas, nt)), FlowShape<T>::NT, FlowShape<T>::smem, st>>>(
-        n, TE, ld, dhp, dlo, flags, work);
+    trisolve_flow_kernel<T><<<(unsigned)std::max(1, std::min(ctas, ntasks)), FlowShape<T>::NT, FlowShape<T>::smem,
+                              st>>>(n, TE, ld, dhp, dlo, flags, work, plan, ntasks, accb, ldacc);
     return cudaGetLastError();
 }
 

@@ -84,7 +84,13 @@ def test_grouped_launches_equal_single_steps(batch, solve_mode):
     for p, Q, k, s in zip(batch, Qs, iters, stats):
         s1, k1, Q1 = _single(p, hp_gemm=B.SR_HP_OZAKI_BF16, solve_mode=solve_mode)
         assert (s, k) == (s1, k1), p.n
-        assert np.array_equal(Q, Q1), p.n
+        if solve_mode == 2:
+            assert np.array_equal(Q, Q1), p.n
+        else:
+            # a single matrix's dataflow solve hands its far products to helper
+            # tasks (another FP32 summation order than the group form's): the
+            # refined factors agree to FP64 rounding
+            assert np.max(np.abs(Q - Q1)) <= 1e-13, p.n
 
 
 def test_grouped_launches_isolate_a_failing_matrix(batch):
