@@ -277,6 +277,22 @@ sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, cons
 sr_status schur_refine_selftest_wait_timeout(schur_refine_t h);
 
 /*
+ * The task list of the dataflow solve for order n (host code only; no device
+ * is used): the order in which the launch's CTAs claim tasks. 64-bit entries:
+ *   solve task  (bit 63 = 0): J = bits 0-15, I = bits 16-31 (tile (I, J) of
+ *               32 x 32 tiles), number of helper tasks of the tile = bits
+ *               32-47, highest block subdiagonal d the tile multiplies
+ *               itself = bits 48-59 (it multiplies d = I-J+1 .. that one);
+ *   helper task (bit 63 = 1): J, I, lowest d = bits 32-43, highest d = bits
+ *               44-55, index among the tile's helpers = bits 56-62.
+ * Every task follows, in the list, the tasks whose results it reads.
+ *   tasks  host array of cap entries, or NULL to query the count only
+ *   count  receives the number of tasks (copied: min(cap, count))
+ * Returns SR_ERR_INVALID_ARG for n < 1 or n > 32768 or a NULL count.
+ */
+sr_status schur_refine_solve_plan(int n, unsigned long long *tasks, long long cap, long long *count);
+
+/*
  * One high-precision product with the handle's engine, as used for A Q and
  * Q^H (A Q): C = op(A) B with op(A) = A (transA = 0) or A^H (transA = 1).
  *   dA  device, FP64 (complex128): m x k (transA = 0) or k x m (transA = 1), lda

@@ -31,7 +31,7 @@ EXPORTS = [
     "schur_refine_batched", "schur_refine_residuals", "schur_refine_trisolve",
     "schur_refine_gemm", "schur_refine_get_profile", "schur_refine_reset_profile",
     "schur_refine_destroy", "schur_refine_status_string", "schur_refine_residuals_noalloc",
-    "schur_refine_selftest_wait_timeout",
+    "schur_refine_selftest_wait_timeout", "schur_refine_solve_plan",
 ]
 
 
@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
         L.schur_refine_residuals_noalloc.argtypes = [I, P, I, P, I, ctypes.POINTER(D), ctypes.POINTER(D), P]
         L.schur_refine_trisolve.argtypes = [P, I, P, I, P]
         L.schur_refine_selftest_wait_timeout.argtypes = [P]
+        L.schur_refine_solve_plan.argtypes = [I, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_longlong,
+                                              ctypes.POINTER(ctypes.c_longlong)]
         L.schur_refine_gemm.argtypes = [P, I, I, I, I, P, I, P, I, P, I]
         L.schur_refine_get_profile.argtypes = [P, ctypes.POINTER(sr_profile)]
         L.schur_refine_reset_profile.argtypes = [P]
@@ -97,7 +99,8 @@ def lib() -> ctypes.CDLL:
         for f in ("schur_refine_create", "schur_refine_step", "schur_refine_batched",
                   "schur_refine_residuals", "schur_refine_trisolve", "schur_refine_gemm",
                   "schur_refine_get_profile", "schur_refine_reset_profile",
-                  "schur_refine_residuals_noalloc", "schur_refine_selftest_wait_timeout"):
+                  "schur_refine_residuals_noalloc", "schur_refine_selftest_wait_timeout",
+                  "schur_refine_solve_plan"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -213,6 +216,21 @@ def schur_refine_trisolve(h, n: int, TE, diag):
     pt, ld = _dev(TE, "TE")
     pd, _ = _dev(diag, "diag")
     return lib().schur_refine_trisolve(h, int(n), pt, ld, pd)
+
+
+def schur_refine_solve_plan(n: int):
+    """The dataflow solve's task list for order n (numpy uint64 array)."""
+    import numpy as np
+    cnt = ctypes.c_longlong(0)
+    s = lib().schur_refine_solve_plan(int(n), None, 0, ctypes.byref(cnt))
+    if s != 0:
+        raise SchurRefineError(s, "schur_refine_solve_plan")
+    out = np.zeros(cnt.value, dtype=np.uint64)
+    s = lib().schur_refine_solve_plan(int(n), out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)), cnt.value,
+                                      ctypes.byref(cnt))
+    if s != 0:
+        raise SchurRefineError(s, "schur_refine_solve_plan")
+    return out
 
 
 def schur_refine_selftest_wait_timeout(h):

@@ -1644,6 +1644,16 @@ sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, cons
     return SR_OK;
 }
 
+sr_status schur_refine_solve_plan(int n, unsigned long long *tasks, long long cap, long long *count)
+{
+    if (n < 1 || n > 32768 || !count || cap < 0) return SR_ERR_INVALID_ARG;
+    std::vector<unsigned long long> t;
+    sr::trisolve_flow_plan(n, t);
+    *count = (long long)t.size();
+    if (tasks) std::copy(t.begin(), t.begin() + (size_t)std::min<long long>(cap, (long long)t.size()), tasks);
+    return SR_OK;
+}
+
 sr_status schur_refine_selftest_wait_timeout(schur_refine_t h)
 {
     if (!h) return SR_ERR_INVALID_ARG;
