@@ -42,7 +42,7 @@ BF16_NOMINAL_TFLOPS = 2250.0
 # profiles/ozaki_mma_kernel_dd_n2048.md: the 105-pair A Q product of the double-double
 # workload); valid for that kernel version and size only
 OZ_MMA_TRAFFIC_BYTES_N4096 = 5.771999e9 + 0.471991e9
-OZ_MMA_TRAFFIC_BYTES_DD2048 = 1.619892e9 + 0.2217213e9
+OZ_MMA_TRAFFIC_BYTES_DD2048 = 1.625545e9 + 0.222098e9
 
 
 def phase_rooflines(prof, steps):
