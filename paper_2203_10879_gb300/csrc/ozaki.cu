@@ -532,6 +532,39 @@ __device__ __forceinline__ int split_exponent(unsigned long long b)
     return eb - 1022;                             // max < 2^e
 }
 
+// The s balanced base-256 digits of a fixed-point integer X (plane p holds
+// the digit of weight 256^(s-1-p), all in [-128, 127] but the top one) are
+// the bytes of Y = X + 128 (1 + 256 + ... + 256^(s-2)) less 128, and the top
+// digit is Y >> 8(s-1): adding 128 to every lower digit makes each a plain
+// byte, so no carries have to be propagated digit by digit.
+__device__ __forceinline__ void write_digits(long long X, int s, __nv_bfloat16 *__restrict__ o, size_t pstride)
+{
+    const unsigned long long bias = s > 1 ? 0x8080808080808080ull >> (8 * (9 - s)) : 0ull;
+    const unsigned long long Y = (unsigned long long)X + bias;
+#pragma unroll
+    for (int q = 0; q < kOzakiMaxSlices - 1; ++q)
+        if (q < s - 1) o[(size_t)(s - 1 - q) * pstride] = __int2bfloat16_rn((int)((Y >> (8 * q)) & 255u) - 128);
+    o[0] = __int2bfloat16_rn((int)((long long)Y >> (8 * (s - 1))));
+}
+
+// the same for a 128-bit X and up to kOzakiMaxSlicesDD digits
+__device__ __forceinline__ void write_digits128(__int128 X, int s, __nv_bfloat16 *__restrict__ o, size_t pstride)
+{
+    const int nb = s - 1;
+    const unsigned long long pat = 0x8080808080808080ull;
+    const unsigned long long blo = nb >= 8 ? pat : (nb > 0 ? pat >> (64 - 8 * nb) : 0ull);
+    const unsigned long long bhi = nb > 8 ? pat >> (64 - 8 * (nb - 8)) : 0ull;
+    const unsigned __int128 Y = (unsigned __int128)X + (((unsigned __int128)bhi << 64) | blo);
+    const unsigned long long ylo = (unsigned long long)Y, yhi = (unsigned long long)(Y >> 64);
+#pragma unroll
+    for (int q = 0; q < kOzakiMaxSlicesDD - 1; ++q)
+        if (q < nb) {
+            const unsigned long long w = q < 8 ? ylo >> (8 * q) : yhi >> (8 * (q - 8));
+            o[(size_t)(s - 1 - q) * pstride] = __int2bfloat16_rn((int)(w & 255u) - 128);
+        }
+    o[0] = __int2bfloat16_rn((int)(long long)((__int128)Y >> (8 * nb)));
+}
+
 // Kp: stacked length written (K rounded up to the chunk, or 2 Kh when complex)
 template <typename Tin, int LAYOUT>
 __device__ __forceinline__ void digits_body(int bx, int by, int R, int K, int Kh, int Kp, const Tin *__restrict__ X,
@@ -555,7 +588,7 @@ __device__ __forceinline__ void digits_body(int bx, int by, int R, int K, int Kh
         __syncthreads();
         split_load_tile<Tin, LAYOUT>(tile, X, ld, R, K, Kh, r0, k0);
         __syncthreads();
-#pragma unroll
+#pragma unroll 1
         for (int w = 0; w < 4; ++w) {
             const int v = ty + 8 * w;
             const int r = r0 + v;
@@ -577,20 +610,14 @@ __device__ __forceinline__ void digits_body(int bx, int by, int R, int K, int Kh
                 else mag = (mant + (1ull << (-sh - 1))) >> (-sh);
                 Xi = (bits >> 63) ? -(long long)mag : (long long)mag;
             }
-            // digits from the least significant: d in [-128, 127]; the top one takes the rest
-            __nv_bfloat16 *o = out + (size_t)r * Kmax + (size_t)kk;
-            for (int p = s - 1; p >= 1; --p) {
-                const long long dg = ((Xi + 128) & 255) - 128;
-                Xi = (Xi - dg) >> 8;
-                o[(size_t)p * pstride] = __int2bfloat16_rn((int)dg);
-            }
-            o[0] = __int2bfloat16_rn((int)Xi);
+            // digits in [-128, 127]; the top one takes the rest
+            write_digits(Xi, s, out + (size_t)r * Kmax + (size_t)kk, pstride);
         }
     }
 }
 
 template <typename Tin, int LAYOUT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 ozaki_digits_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, int ld, int s, int Pmax, int Kmax,
                     const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
                     int *__restrict__ exps)
@@ -614,7 +641,7 @@ ozaki_absmax_group_kernel(const SplitMat *__restrict__ mats, const int *__restri
 }
 
 template <int LAYOUT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 ozaki_digits_group_kernel(const SplitMat *__restrict__ mats, const int *__restrict__ start, int m, int s, int Pmax,
                           int Kmax, const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
                           int *__restrict__ exps)
@@ -651,7 +678,7 @@ __device__ __forceinline__ __int128 dd_fixed_part(double x, int F, int e)
 }
 
 template <int LAYOUT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 ozaki_digits_dd_kernel(int R, int K, int Kp, const double *__restrict__ Xh, const double *__restrict__ Xl, int ld,
                        int s, int Pmax, int Kmax, const unsigned long long *__restrict__ vmax,
                        __nv_bfloat16 *__restrict__ out, int *__restrict__ exps)
@@ -673,7 +700,7 @@ ozaki_digits_dd_kernel(int R, int K, int Kp, const double *__restrict__ Xh, cons
         split_load_tile<double, LAYOUT>(th, Xh, ld, R, K, INT_MAX, r0, k0);
         split_load_tile<double, LAYOUT>(tl, Xl, ld, R, K, INT_MAX, r0, k0);
         __syncthreads();
-#pragma unroll
+#pragma unroll 1
         for (int w = 0; w < 4; ++w) {
             const int v = ty + 8 * w;
             const int r = r0 + v;
@@ -681,13 +708,7 @@ ozaki_digits_dd_kernel(int R, int K, int Kp, const double *__restrict__ Xh, cons
             const int e = sexp[v];
             __int128 Xi = 0;
             if (e != kOzakiExpNonfinite && r < R) Xi = dd_fixed_part(th[v][tx], F, e) + dd_fixed_part(tl[v][tx], F, e);
-            __nv_bfloat16 *o = out + (size_t)r * Kmax + (size_t)kk;
-            for (int p = s - 1; p >= 1; --p) {
-                const int dg = (int)((long long)((Xi + 128) & (__int128)255)) - 128;
-                Xi = (Xi - dg) >> 8;
-                o[(size_t)p * pstride] = __int2bfloat16_rn(dg);
-            }
-            o[0] = __int2bfloat16_rn((int)(long long)Xi);
+            write_digits128(Xi, s, out + (size_t)r * Kmax + (size_t)kk, pstride);
         }
     }
 }
