@@ -462,6 +462,7 @@ def run_batched(args):
     nmax = int(max(ns))
     stream = torch.cuda.current_stream()
     out = {}
+    clk = None
     # grouped launches (the measured path), the worker pool of streams, one matrix at a time
     for key, mode, workers in (("grouped", 0, 1), ("streams", 1, args.batch_streams), ("serial", 1, 1)):
         opt = B.default_options(hp_gemm=B.SR_HP_OZAKI_BF16, lp=B.SR_LP_FP32, batch_streams=workers,
@@ -475,11 +476,16 @@ def run_batched(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         steps = args.steps if key != "serial" else 1
+        clocks = Clocks(local) if key == "grouped" else None
+        if clocks:
+            clocks.start()
         e0.record(stream)
         for _ in range(steps):
             st, iters, stats = B.schur_refine_batched(h, sizes, As, Qs, Qh)
         e1.record(stream)
         torch.cuda.synchronize()
+        if clocks:
+            clk = clocks.stop()
         prof = None
         if key == "grouped":
             _, pp = B.schur_refine_get_profile(h)
@@ -493,6 +499,32 @@ def run_batched(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     if rank == 0:
+        # the dominant kernel's roofline: the slice products of the group, live
+        peaks = _peaks()
+        mma = prof.get("oz_mma", {"ms": 0, "flops": 0, "spans": 0})
+        roof = None
+        if mma["ms"] > 0:
+            achieved = mma["flops"] / (mma["ms"] * 1e-3) / 1e12
+            peak = peaks.get("bf16_tflops_sustained") or 1700.0
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": "ozaki slice products, work-item form (tcgen05 kind::f16 bf16)",
+                    "peak_source": "of measured bf16 sustained (MEASURED_PEAKS.json)",
+                    "share_of_step": mma["ms"] / (ms * args.steps)}
+        cpu = None
+        if not args.no_cpu_baseline:
+            # the oracle on a bounded sample: the first matrices of the batch, scaled by sum n^3
+            import oracle
+            t0, k, done = time.perf_counter(), 0, 0.0
+            while k < len(probs) and time.perf_counter() - t0 < 10.0:
+                oracle.refine(probs[k].A, probs[k].Qhat, lp="f32")
+                done += float(probs[k].n) ** 3
+                k += 1
+            dt = time.perf_counter() - t0
+            total = float(np.sum(ns.astype(float) ** 3))
+            est = dt * total / done
+            cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+            cpu = {"value": len(ns) / est, "unit": "matrices/s", "cores": cores, "kind": "oracle",
+                   "sample": f"oracle full refinements of the first {k} matrices ({dt:.1f} s), scaled by sum n^3"}
         line = {"metric": "matrices/s refined to FP64 accuracy (batched)", "value": len(ns) / (ms / 1e3),
                 "unit": "matrices/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
@@ -506,6 +538,7 @@ def run_batched(args):
                            "speedup_vs_one_at_a_time": out["serial"][0] / ms,
                            "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
                            "launches_per_step": int(sum(v["launches"] for v in prof.values()) / args.steps)},
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(sum(v["launches"] for v in prof.values()))}
         print(json.dumps(line), flush=True)
     return 0
