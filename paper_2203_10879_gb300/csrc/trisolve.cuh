@@ -431,37 +431,38 @@ inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cu
 }
 
 // ---- the whole solve in one launch: a dataflow over the tiles --------------
-// The same tile equations as above, solved by one persistent launch. Tiles
-// are claimed through a ticket counter in the wavefront's order (block
-// subdiagonal NB-1 first, then NB-2, ..., 0; by column within one). The CTA
-// holding tile (I, J), D = I - J, applies for d = NB-1, ..., D+1 the two
-// products of subdiagonal d (the block form of Alg. 3's update products)
+// The same tile equations as above, solved by one persistent launch whose
+// CTAs claim tasks through a ticket counter, in the order of a task list
+// (trisolve_flow_plan; for a group of matrices, the tiles of the group plan).
+// A solve task for tile (I, J), D = I - J, applies the two products of each
+// of its subdiagonals d (the block form of Alg. 3's update products)
 //     T(I, J+d) L(J+d, J)   and   -L(I, I-d) T(I-d, J)
-// as soon as the two L tiles of subdiagonal d are published, then solves the
-// tile equation by the wavefront of trisolve_leaf_kernel and publishes X.
+// as soon as the two L tiles of subdiagonal d are published, adds E and the
+// helpers' sum, solves the tile equation by the wavefront of
+// trisolve_leaf_kernel and publishes X. Helper tasks (one matrix) take the
+// products of the far subdiagonals d >= max(D + kFlowNear, kFlowFarNum NB/16)
+// of a tile, kFlowChunk subdiagonals each, as soon as those are published, and
+// add them into the tile's accumulator in a fixed order (helper h waits until
+// h helpers are done), so the result does not depend on timing. Without them
+// the products of the tiles near the main diagonal, which have the most, pile
+// up at the end of the wavefront, when its subdiagonals hold the most tiles.
+//
 // The CTA has 512 threads, two entries of the tile each in the solve (the
 // wavefront's steps are barrier-bound: few entries per thread keep them
 // short), and two CTAs share an SM, so one CTA's products run while the
-// other waits at its wavefront's barriers. The products of one tile are
-// split over NPP pair lanes (subdiagonals d = top-l, top-l-NPP, ... for lane
-// l) of two groups each, one per half of K; every group has its own operand
+// other waits at its wavefront's barriers. The products of a task are split
+// over NPP pair lanes (subdiagonals d = hi-l, hi-l-NPP, ... for lane l) of
+// two groups each, one per half of K; every group has its own operand
 // buffers and named barrier, so it waits only on its own inputs; the partial
-// sums meet in shared memory before the solve.
+// sums meet in shared memory.
 //
-// Forward progress does not need the CTAs to be co-resident: the inputs of a
-// tile lie on higher subdiagonals and so hold smaller tickets, and a ticket
-// is taken only by a running CTA, so the smallest unfinished ticket always
-// finds its inputs published. Every wait is bounded (kFlowSpin polls); one
-// that runs out sets SR_FLAG_TIMEOUT and an abort word that ends all other
-// waits, and the launch runs to its end without further waiting.
-//
-// Helper tasks (one matrix): the products of the subdiagonals d >= D + kFlowNear
-// of a tile are computed ahead, as soon as those subdiagonals are published,
-// by helper tasks of kFlowChunk subdiagonals each; they add into the tile's
-// accumulator in a fixed order (helper h waits until h helpers are done), and
-// the owner adds E, that sum and its own products of the nearest subdiagonals.
-// Without them, the products of the tiles far down the wavefront pile up at
-// its end, when the subdiagonals hold the most tiles.
+// Forward progress does not need the CTAs to be co-resident: every input of
+// a task (tiles of higher subdiagonals, the tile's earlier helpers, a solve
+// task's helpers) holds a smaller ticket, and a ticket is taken only by a
+// running CTA, so the smallest unfinished ticket always finds its inputs
+// done. Every wait is bounded (kFlowSpin polls); one that runs out sets
+// SR_FLAG_TIMEOUT and an abort word that ends all other waits, and the launch
+// runs to its end without further waiting.
 //
 // work[0]: ticket counter; work[1]: abort word; work[2 + I NB + J]: tile
 // (I, J) published; work[2 + NB^2 + I NB + J]: helpers of tile (I, J) done.
