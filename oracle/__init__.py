@@ -8,6 +8,6 @@ and never calls it. See :mod:`oracle.alg` for what each function follows;
 from ._lib import build, set_threads, max_threads  # noqa: F401
 from .alg import (  # noqa: F401
     OK, NONDISTINCT, NONFINITE, NOT_CONVERGED, SolveError, IterInfo, RefineResult,
-    alg2, alg3, kron_solve, ns_init, form_residual, iteration, refine, default_tol,
+    alg2, sym_solve, alg3, kron_solve, ns_init, form_residual, iteration, refine, default_tol,
     residuals_dd, sample_entries_dd, gemm_dd,
 )

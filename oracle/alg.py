@@ -14,6 +14,8 @@ Every function follows the paper's steps in its order and notation:
 * :func:`alg3`         -- Alg. 3 (recursive block algorithm), Sec. 2.1.
 * :func:`kron_solve`   -- brute force of the same equation (dense solve of the
   operator's n(n-1)/2-square matrix in 128-bit arithmetic).
+* :func:`sym_solve`    -- Sec. 2.5 (symmetric A): with T diagonal the equation
+  decouples, l_ij = -e_ij / (t_ii - t_jj) for i > j (the sign of eq. (lij)).
 * :func:`iteration`    -- one pass of the REPEAT loop of Alg. 4 (Sec. 2.4):
   T^ = Q^H A Q in hp; E = stril(T^), T = T^ - E, to lp; solve in lp; L to
   hp; W = L - L^H; Y = Q^H Q - I in hp; YW, W^2, W^3 in lp; Sigma in hp;
@@ -139,6 +141,26 @@ class IterInfo:
     updated: bool = False
 
 
+def sym_solve(E: np.ndarray, d_hp: np.ndarray) -> np.ndarray:
+    """Sec. 2.5: the solution of stril(T L - L T) = -E for diagonal T, in the
+    precision of ``E``: l_ij = -e_ij / (t_ii - t_jj) for i > j, each divisor
+    formed from the hp diagonal ``d_hp`` and rounded to that precision (as in
+    :func:`alg2`). Raises :class:`SolveError` like alg2."""
+    n = E.shape[0]
+    dt = E.dtype
+    L = np.zeros((n, n), dtype=dt)
+    i, j = np.tril_indices(n, -1)
+    den = (np.asarray(d_hp)[i] - np.asarray(d_hp)[j]).astype(dt)
+    if np.any(den == 0):
+        raise SolveError(NONDISTINCT)
+    with np.errstate(over="ignore", invalid="ignore"):
+        vals = -E[i, j] / den
+    if not np.all(np.isfinite(vals)):
+        raise SolveError(NONFINITE)
+    L[i, j] = vals
+    return L
+
+
 def form_residual(A: np.ndarray, Q: np.ndarray):
     """T^ = Q^H A Q in hp (two products), split into E = stril(T^) and T = T^ - E."""
     That = Q.conj().T @ (A @ Q)
@@ -148,10 +170,12 @@ def form_residual(A: np.ndarray, Q: np.ndarray):
 
 
 def iteration(A: np.ndarray, Q: np.ndarray, lp: str = "f32", full_sigma: bool = False,
-              solver: str = "alg2", T_E=None, parts: dict | None = None):
+              solver: str = "alg2", T_E=None, parts: dict | None = None, symmetric: bool = False):
     """One pass of the REPEAT loop of Alg. 4; returns (Q_new, IterInfo).
 
     ``full_sigma`` adds the two terms W^2 Y + W^2 Y W that Sec. 2.4 drops.
+    ``symmetric`` takes Sec. 2.5's form for real symmetric A: T is the
+    diagonal of T^ and the solve is :func:`sym_solve`.
     If ``parts`` is a dict, the intermediates T, E, L, W, Y and Sigma are
     stored in it.
     """
@@ -165,7 +189,9 @@ def iteration(A: np.ndarray, Q: np.ndarray, lp: str = "f32", full_sigma: bool = 
     # E, T to lp; divisors from the hp diagonal
     T_lp = np.asfortranarray(T.astype(lpt))
     E_lp = np.asfortranarray(E.astype(lpt))
-    if solver == "alg2":
+    if symmetric:
+        L_lp = sym_solve(E_lp, np.diagonal(T).copy())
+    elif solver == "alg2":
         L_lp = alg2(T_lp, E_lp, np.diagonal(T).copy())
     elif solver == "alg3":
         if lpt != np.float64:
@@ -213,7 +239,7 @@ class RefineResult:
 
 def refine(A: np.ndarray, Qhat: np.ndarray, lp: str = "f32", tol: float | None = None,
            max_iter: int = 10, full_sigma: bool = False, solver: str = "alg2",
-           init_ns: bool = True) -> RefineResult:
+           init_ns: bool = True, symmetric: bool = False) -> RefineResult:
     """Alg. 4 lines "convert Qhat, NS step" and REPEAT ... UNTIL convergence.
 
     Stop test (the paper only says "when E becomes small enough"): after
@@ -253,7 +279,8 @@ def refine(A: np.ndarray, Qhat: np.ndarray, lp: str = "f32", tol: float | None =
             break
         prev_rT = r_T
         try:
-            Q, info = iteration(A, Q, lp=lp, full_sigma=full_sigma, solver=solver, T_E=(T, E))
+            Q, info = iteration(A, Q, lp=lp, full_sigma=full_sigma, solver=solver, T_E=(T, E),
+                                symmetric=symmetric)
         except SolveError as e:
             res.status = e.code
             res.history.append(IterInfo(r_T=r_T))

@@ -233,6 +233,16 @@ def jittered_real(n: int = 4096, seed: int = BASE_SEED + 2, low: str = "f32",
                    recipe=f"real n={n}, lambda_k=k/n+U(0,0.5/n), upper std 1/n, Qhat=fl_{low}(Q0 expm(1e-6 S))")
 
 
+def symmetric_real(n: int = 4096, seed: int = BASE_SEED + 5, low: str = "f32") -> Planted:
+    """Real symmetric planted problem (Sec. 2.5): T0 = diag(lambda), lambda_k =
+    k/n + U(0, 0.5/n); A = Q0 T0 Q0^T made exactly symmetric, (A + A^T)/2."""
+    p = planted(n, eig_jittered_grid(n, seed), seed, pert=1e-6, low=low, upper_std=0.0,
+                recipe=f"real symmetric n={n}, A=Q0 diag(lambda) Q0^T, lambda_k=k/n+U(0,0.5/n), "
+                       f"Qhat=fl_{low}(Q0 expm(1e-6 S))")
+    A = np.asfortranarray(0.5 * (p.A + p.A.T))
+    return Planted(A=A, Qhat=p.Qhat, Q0=p.Q0, T0=p.T0, lam=p.lam, seed=p.seed, recipe=p.recipe)
+
+
 def ring_complex(n: int = 8192, seed: int = BASE_SEED + 3) -> Planted:
     """Complex planted problem with ring eigenvalues and a complex64-rounded start."""
     return planted(n, eig_ring(n, seed), seed, pert=1e-6, low="f32", complex_=True,
