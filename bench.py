@@ -66,7 +66,10 @@ def _peaks():
         return {}
 
 
-def _workload_name(n, cplx=False):
+def _workload_name(n, cplx=False, sym=False):
+    if sym:
+        return (f"real symmetric n={n} planted A=Q0 diag(lambda) Q0^T, lambda_k=k/n+U(0,0.5/n), "
+                f"Qhat=fl32(Q0 expm(1e-6 S)); Alg. 4 in the form of Sec. 2.5 to ||stril||/||A||<=1e-14 sqrt(n)")
     if cplx:
         return (f"complex n={n} planted A=Q0 T0 Q0^H, lambda_k=0.5 exp(2 pi i k/n)(1+U(0,0.2)), complex upper "
                 f"std 1/n, Qhat=fl_c64(Q0 expm(1e-6 S)), S skew-Hermitian; Alg. 4 to ||stril||/||A||<=1e-14 sqrt(n)")
@@ -132,13 +135,16 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_sample(n_full: int, n_sample: int, cplx: bool = False):
+def cpu_oracle_sample(n_full: int, n_sample: int, cplx: bool = False, sym: bool = False):
     """The oracle's full refinement at n_sample, scaled by (n_full/n_sample)^3."""
     import oracle
     from paper_2203_10879_gb300 import inputs
-    p = inputs.ring_complex(n_sample) if cplx else inputs.jittered_real(n_sample)
+    if sym:
+        p = inputs.symmetric_real(n_sample)
+    else:
+        p = inputs.ring_complex(n_sample) if cplx else inputs.jittered_real(n_sample)
     t0 = time.perf_counter()
-    r = oracle.refine(p.A, p.Qhat, lp="f32")
+    r = oracle.refine(p.A, p.Qhat, lp="f32", symmetric=sym)
     dt = time.perf_counter() - t0
     scale = (n_full / n_sample) ** 3
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
@@ -150,10 +156,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     n, ns, cplx = args.n, args.cpu_sample_n, args.workload == "complex"
-    dd = args.workload == "dd"
+    dd, sym = args.workload == "dd", args.workload == "sym"
     times = []
     for i in range(args.warmup + args.steps):
-        est, dt, r, cores = cpu_oracle_sample_dd(n, ns) if dd else cpu_oracle_sample(n, ns, cplx)
+        est, dt, r, cores = cpu_oracle_sample_dd(n, ns) if dd else cpu_oracle_sample(n, ns, cplx, sym)
         if i >= args.warmup:
             times.append(est)
     v = sum(times) / len(times)
@@ -166,7 +172,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "dd+f64" if dd else "f64+f32", "data": "synthetic",
-            "config": {"workload": _dd_workload_name(n) if dd else _workload_name(n, cplx), "n": n,
+            "config": {"workload": _dd_workload_name(n) if dd else _workload_name(n, cplx, sym), "n": n,
                        "form": "FP64->double-double (oracle)" if dd else "mixed FP32->FP64 (oracle)"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -248,7 +254,11 @@ def run_ours(args):
 
     n = args.n
     cplx = args.workload == "complex"
-    p = inputs.ring_complex(n) if cplx else inputs.jittered_real(n)
+    sym = args.workload == "sym"
+    if sym:
+        p = inputs.symmetric_real(n)
+    else:
+        p = inputs.ring_complex(n) if cplx else inputs.jittered_real(n)
     hdt = torch.complex128 if cplx else torch.float64
     ldt = torch.complex64 if cplx else torch.float32
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
@@ -256,7 +266,7 @@ def run_ours(args):
     Qhat = dev(p.Qhat)
     Q = torch.empty((n, n), dtype=hdt, device="cuda").t()
     stream = torch.cuda.current_stream()
-    dtype_opt = {"dtype": B.SR_COMPLEX} if cplx else {}
+    dtype_opt = {"dtype": B.SR_COMPLEX} if cplx else ({"symmetric": 1} if sym else {})
 
     hp_name = {"fp64": B.SR_HP_FP64, "ozaki": B.SR_HP_OZAKI_BF16}
     hp = "ozaki" if cplx else args.hp
@@ -347,19 +357,23 @@ def run_ours(args):
     ms64 = st64 = nr64 = None
     prof64 = {}
     if not cplx:
-        allfp64 = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP64, profile=1)
+        allfp64 = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP64, profile=1, **dtype_opt)
         ms64, st64, nr64 = timed(allfp64, k64, 1)
         prof64 = allfp64.profile()
         allfp64.close()
     mixed_native_ms = None
     if hp != "fp64" and not cplx:
-        mn = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP32)
+        mn = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP32, **dtype_opt)
         mixed_native_ms, _, _ = timed(mn, k64, 1)
         mn.close()
     # the same mixed form with the other form of the solve: stepwise (one launch
-    # pair per block subdiagonal) for real data, dataflow (one launch) for complex
-    alt_mode = 1 if cplx else 2
-    sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, solve_mode=alt_mode, **dtype_opt)
+    # pair per block subdiagonal) for real data, dataflow (one launch) for complex;
+    # for symmetric A the general form (triangular solve instead of Sec. 2.5's)
+    if sym:
+        sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32)
+    else:
+        alt_mode = 1 if cplx else 2
+        sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, solve_mode=alt_mode, **dtype_opt)
     alt_ms, _, _ = timed(sw, max(1, min(args.steps, 3)), 2)
     sw.close()
 
@@ -397,7 +411,7 @@ def run_ours(args):
     cpu_val = None
     cpu = None
     if not args.no_cpu_baseline:
-        est, dt, r, cores = cpu_oracle_sample(n, args.cpu_sample_n, cplx)
+        est, dt, r, cores = cpu_oracle_sample(n, args.cpu_sample_n, cplx, sym)
         cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle",
                "sample": f"oracle full refinement at n={args.cpu_sample_n} ({dt:.2f} s measured), "
                          f"scaled by (n/{args.cpu_sample_n})^3 to n={n}"}
@@ -408,7 +422,7 @@ def run_ours(args):
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128+c64" if cplx else "f64+f32", "data": "synthetic",
-        "config": {"workload": _workload_name(n, cplx), "n": n,
+        "config": {"workload": _workload_name(n, cplx, sym), "n": n,
                    "form": "mixed: complex64 solve/products" if cplx else "mixed: FP32 solve/products",
                    "hp_gemm": hp if hp == "fp64" else f"ozaki-bf16-s{args.slices or 7}",
                    "l2": f"inputs larger than L2 (A {n * n * (16 if cplx else 8) >> 20} MiB + Q + workspace)",
@@ -420,7 +434,7 @@ def run_ours(args):
                    "mixed_vs_all_fp64_speedup": None if ms64 is None else ms64 / ms,
                    "mixed_native_fp64_s": None if mixed_native_ms is None else mixed_native_ms / 1e3,
                    "solve_form": "stepwise (launch pair per block subdiagonal)" if cplx
-                   else "dataflow (one launch per solve)",
+                   else ("elementwise (Sec. 2.5, symmetric A)" if sym else "dataflow (one launch per solve)"),
                    "with_other_solve_form_s": alt_ms / 1e3,
                    "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
                    "phase_rates": phase_rooflines(prof, args.steps),
@@ -811,7 +825,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-n", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single", "complex", "batched", "dd", "small"], default="single")
+    ap.add_argument("--workload", choices=["single", "complex", "batched", "dd", "small", "sym"], default="single")
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--batch-streams", type=int, default=8)
     args = ap.parse_args()

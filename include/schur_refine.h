@@ -132,6 +132,13 @@ typedef struct {
                          one launch pair per block subdiagonal, replayed from
                          a CUDA graph. Same equations, sums in another order;
                          complex128 always uses the stepwise form */
+    int symmetric;    /* 1: A is real symmetric (Sec. 2.5): its Schur form is
+                         diagonal, so T^ splits into its diagonal T and its
+                         off-diagonal part E, and the solve of S4 becomes
+                         elementwise, l_ij = -e_ij / (t_ii - t_jj) for i > j
+                         (the sign of eq. (lij)). Real data and the FP64
+                         target only; grouped batches fall back to worker
+                         streams. 0 (default): general A */
 } sr_options;
 
 /* Fills *opt with the defaults: real, FP64 target, native FP64 products,

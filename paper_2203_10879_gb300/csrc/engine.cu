@@ -176,7 +176,7 @@ sr_status check_opts(const sr_options &o)
     if (o.lp != SR_LP_FP32 && o.lp != SR_LP_FP64) return SR_ERR_INVALID_ARG;
     if (o.qhat_type != SR_QHAT_FP32 && o.qhat_type != SR_QHAT_FP64) return SR_ERR_INVALID_ARG;
     if ((o.batch_mode != 0 && o.batch_mode != 1) || (o.tune != 0 && o.tune != 1) || (o.graph != 0 && o.graph != 1) ||
-        o.solve_mode < 0 || o.solve_mode > 2)
+        o.solve_mode < 0 || o.solve_mode > 2 || (o.symmetric != 0 && o.symmetric != 1))
         return SR_ERR_INVALID_ARG;
     if (o.ozaki_slices > (o.target == SR_TARGET_DD ? sr::kOzakiMaxSlicesDD : sr::kOzakiMaxSlices))
         return SR_ERR_INVALID_ARG;
@@ -185,6 +185,8 @@ sr_status check_opts(const sr_options &o)
         return SR_ERR_UNSUPPORTED;
     // complex data: the emulated products with the complex64 correction path
     if (o.dtype == SR_COMPLEX && (o.hp_gemm != SR_HP_OZAKI_BF16 || o.lp != SR_LP_FP32)) return SR_ERR_UNSUPPORTED;
+    // Sec. 2.5 is stated for real symmetric A; the double-double target keeps the general form
+    if (o.symmetric && (o.dtype != SR_REAL || o.target != SR_TARGET_FP64)) return SR_ERR_UNSUPPORTED;
     if (o.hp_gemm == SR_HP_OZAKI_BF16 && !sr::kOzakiBuilt) return SR_ERR_UNSUPPORTED;
     return SR_OK;
 }
@@ -350,6 +352,16 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
 {
     const int NB = (n + sr::kSolveTile - 1) / sr::kSolveTile;
     const int kind = SrNum<Tl>::kind;
+    if constexpr (SrNum<Tl>::kind <= 1) {
+        if (h->opt.symmetric) {
+            // Sec. 2.5: T diagonal, one division per entry
+            SrPhase ph(h, SR_PROF_SOLVE, (long long)n * (n - 1) / 2, (long long)n * n * (long long)sizeof(Tl), 1);
+            const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+            sr::diag_solve_kernel<Tl><<<grid, 256, 0, h->st>>>(n, TE, ld, dhp, h->dflags);
+            SR_CUDA_TRY(cudaGetLastError());
+            return SR_OK;
+        }
+    }
     if constexpr (SrNum<Tl>::kind <= 2) {
         if (use_flow(h, kind)) {
             // one launch: the dataflow over the tiles
@@ -1271,6 +1283,7 @@ void schur_refine_default_options(sr_options *opt)
     opt->tune = 0;
     opt->graph = 0;
     opt->solve_mode = 0;
+    opt->symmetric = 0;
 }
 
 const char *schur_refine_status_string(sr_status s)

@@ -430,6 +430,38 @@ inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cu
     return e;
 }
 
+// ---- symmetric A (Sec. 2.5): T diagonal, the solve elementwise ---------------
+// l_ij = -e_ij / (t_ii - t_jj) for i > j (eq. "lij" with t_ik = 0 for k != i),
+// the divisor formed in high precision and rounded to the working type, then
+// one IEEE division: the same operations as Alg. 2 with a diagonal T. Thread
+// (lane, warp) of a 256-thread block takes rows of a 32 x 32 block, four
+// columns each.
+template <typename T>
+__global__ void __launch_bounds__(256)
+diag_solve_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>::hp *__restrict__ dhp,
+                  int *__restrict__ flags)
+{
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int jb = blockIdx.y * 32 + (threadIdx.x >> 5);
+    int bad = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int j = jb + 8 * w;
+        if (i < n && j < i) {
+            const T den = sr_div_round<T>(dhp[i], dhp[j]);
+            T x = SrNum<T>::zero();
+            if (den == SrNum<T>::zero()) {
+                bad |= SR_FLAG_NONDISTINCT;
+            } else {
+                x = -(TE[sr_idx(i, j, ld)] / den);
+                if (!sr_finite(x)) bad |= SR_FLAG_NONFINITE;
+            }
+            TE[sr_idx(i, j, ld)] = x;
+        }
+    }
+    if (bad) atomicOr(flags, bad);
+}
+
 // ---- the whole solve in one launch: a dataflow over the tiles --------------
 // The same tile equations as above, solved by one persistent launch whose
 // CTAs claim tasks through a ticket counter, in the order of a task list

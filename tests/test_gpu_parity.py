@@ -268,3 +268,61 @@ def test_profile_counts(torch):
         assert d["hp_gemm"]["ms"] > 0 and d["solve"]["ms"] > 0
     finally:
         B.schur_refine_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# symmetric A (Sec. 2.5)
+
+@pytest.mark.parametrize("lp,dt", [(B.SR_LP_FP32, np.float32), (B.SR_LP_FP64, np.float64)])
+@pytest.mark.parametrize("n", [1, 2, 33, 257])
+def test_symmetric_solve_bit_exact(torch, n, lp, dt):
+    """T diagonal: the GPU's elementwise solve performs the oracle's operations
+    (divisor from the FP64 diagonal rounded once, one IEEE division)."""
+    rng = np.random.default_rng(n)
+    d = np.sort(rng.uniform(-1.0, 1.0, n))
+    E = np.tril(rng.standard_normal((n, n)) * 1e-4, -1)
+    h = _handle(n, lp=lp, symmetric=1)
+    try:
+        TE = to_dev((np.diag(d) + np.triu(rng.standard_normal((n, n)), 1) + E).astype(dt))
+        assert B.schur_refine_trisolve(h, n, TE, to_dev(d.copy())) == B.SR_OK
+        L = np.tril(from_dev(TE), -1)
+        ref = oracle.sym_solve(E.astype(dt), d)
+        assert np.array_equal(L, ref)
+    finally:
+        B.schur_refine_destroy(h)
+
+
+def test_symmetric_solve_reports_equal_diagonal(torch):
+    n = 40
+    d = np.linspace(0.0, 1.0, n)
+    d[30] = d[3]
+    h = _handle(n, lp=B.SR_LP_FP32, symmetric=1)
+    try:
+        TE = to_dev((np.diag(d) + np.tril(np.ones((n, n)) * 1e-3, -1)).astype(np.float32))
+        assert B.schur_refine_trisolve(h, n, TE, to_dev(d.copy())) == B.SR_ERR_NONDISTINCT
+    finally:
+        B.schur_refine_destroy(h)
+
+
+@pytest.mark.parametrize("hp", [B.SR_HP_FP64, B.SR_HP_OZAKI_BF16])
+@pytest.mark.parametrize("n", [64, 300])
+def test_symmetric_refinement_parity(torch, n, hp):
+    p = inputs.symmetric_real(n)
+    s, nr, Q, T, (rT, rQ) = _refine_gpu(p, lp=B.SR_LP_FP32, hp_gemm=hp, symmetric=1)
+    ref = oracle.refine(p.A, p.Qhat, lp="f32", symmetric=True)
+    assert s == B.SR_OK and ref.status == oracle.OK
+    assert abs(nr.iters - ref.iters) <= 1
+    tol = oracle.default_tol(n)
+    cT, cQ = oracle.residuals_dd(p.A, Q)
+    assert cT <= tol and cQ <= tol
+    w, V = np.linalg.eigh(p.A)
+    assert np.max(np.abs(np.diagonal(T) - w)) <= 1e-13
+    assert np.max(np.abs(sign_align(Q, V) - V)) <= 1e-10
+    assert np.max(np.abs(sign_align(Q, ref.Q) - ref.Q)) <= 1e-10
+
+
+def test_symmetric_option_rejected_for_complex_and_dd(torch):
+    for kw in ({"dtype": B.SR_COMPLEX, "hp_gemm": B.SR_HP_OZAKI_BF16},
+               {"target": B.SR_TARGET_DD, "lp": B.SR_LP_FP64, "qhat_type": B.SR_QHAT_FP64}):
+        s, h = B.schur_refine_create(64, B.default_options(symmetric=1, **kw), None)
+        assert s == B.SR_ERR_UNSUPPORTED and not h
