@@ -65,12 +65,16 @@ def _ctype(a: np.ndarray):
 # ---------------------------------------------------------------------------
 # Triangular matrix equation stril(T L - L T) = -E  (Sec. 2.1)
 
-def alg2(T: np.ndarray, E: np.ndarray, d_hp: np.ndarray | None = None) -> np.ndarray:
+def alg2(T: np.ndarray, E: np.ndarray, d_hp: np.ndarray | None = None, cap: float = 0.0) -> np.ndarray:
     """Alg. 2 in the precision of ``T`` (float32/64, complex64/128).
 
     ``d_hp`` is the diagonal of T in high precision; when given, the divisors
     t_ii - t_jj are formed from it and then rounded to the precision of T.
-    Raises :class:`SolveError` on a zero divisor (Theorem 1) or a non-finite L.
+    ``cap`` > 0 applies the trick of Example 4 (Sec. 3): an entry of L larger
+    than ``cap`` in modulus (|l|^2 > cap^2 for complex data, in the working
+    precision) is set to zero as soon as it is computed, before later entries
+    use it. Raises :class:`SolveError` on a zero divisor (Theorem 1) or a
+    non-finite L.
     """
     n = T.shape[0]
     dt = T.dtype
@@ -85,7 +89,7 @@ def alg2(T: np.ndarray, E: np.ndarray, d_hp: np.ndarray | None = None) -> np.nda
         dh = None if d_hp is None else np.ascontiguousarray(d_hp, dtype=np.float64)
         fn = L_.sro_alg2_f32 if dt == np.float32 else L_.sro_alg2_f64
     rc = fn(n, _lib.ptr(T), n, _lib.ptr(E), n, None if dh is None else _lib.ptr(dh),
-            _lib.ptr(L), n)
+            _lib.ptr(L), n, float(cap))
     if rc:
         raise SolveError(rc)
     return L
@@ -141,7 +145,7 @@ class IterInfo:
     updated: bool = False
 
 
-def sym_solve(E: np.ndarray, d_hp: np.ndarray) -> np.ndarray:
+def sym_solve(E: np.ndarray, d_hp: np.ndarray, cap: float = 0.0) -> np.ndarray:
     """Sec. 2.5: the solution of stril(T L - L T) = -E for diagonal T, in the
     precision of ``E``: l_ij = -e_ij / (t_ii - t_jj) for i > j, each divisor
     formed from the hp diagonal ``d_hp`` and rounded to that precision (as in
@@ -155,6 +159,8 @@ def sym_solve(E: np.ndarray, d_hp: np.ndarray) -> np.ndarray:
         raise SolveError(NONDISTINCT)
     with np.errstate(over="ignore", invalid="ignore"):
         vals = -E[i, j] / den
+    if cap > 0:   # the trick of Example 4, as in alg2
+        vals[np.abs(vals) > dt.type(cap)] = 0
     if not np.all(np.isfinite(vals)):
         raise SolveError(NONFINITE)
     L[i, j] = vals
@@ -170,12 +176,14 @@ def form_residual(A: np.ndarray, Q: np.ndarray):
 
 
 def iteration(A: np.ndarray, Q: np.ndarray, lp: str = "f32", full_sigma: bool = False,
-              solver: str = "alg2", T_E=None, parts: dict | None = None, symmetric: bool = False):
+              solver: str = "alg2", T_E=None, parts: dict | None = None, symmetric: bool = False,
+              cap: float = 0.0):
     """One pass of the REPEAT loop of Alg. 4; returns (Q_new, IterInfo).
 
     ``full_sigma`` adds the two terms W^2 Y + W^2 Y W that Sec. 2.4 drops.
     ``symmetric`` takes Sec. 2.5's form for real symmetric A: T is the
-    diagonal of T^ and the solve is :func:`sym_solve`.
+    diagonal of T^ and the solve is :func:`sym_solve`. ``cap`` is the entry
+    threshold of :func:`alg2`.
     If ``parts`` is a dict, the intermediates T, E, L, W, Y and Sigma are
     stored in it.
     """
@@ -190,9 +198,9 @@ def iteration(A: np.ndarray, Q: np.ndarray, lp: str = "f32", full_sigma: bool = 
     T_lp = np.asfortranarray(T.astype(lpt))
     E_lp = np.asfortranarray(E.astype(lpt))
     if symmetric:
-        L_lp = sym_solve(E_lp, np.diagonal(T).copy())
+        L_lp = sym_solve(E_lp, np.diagonal(T).copy(), cap)
     elif solver == "alg2":
-        L_lp = alg2(T_lp, E_lp, np.diagonal(T).copy())
+        L_lp = alg2(T_lp, E_lp, np.diagonal(T).copy(), cap)
     elif solver == "alg3":
         if lpt != np.float64:
             raise ValueError("alg3 oracle is float64 only")
@@ -239,7 +247,7 @@ class RefineResult:
 
 def refine(A: np.ndarray, Qhat: np.ndarray, lp: str = "f32", tol: float | None = None,
            max_iter: int = 10, full_sigma: bool = False, solver: str = "alg2",
-           init_ns: bool = True, symmetric: bool = False) -> RefineResult:
+           init_ns: bool = True, symmetric: bool = False, cap: float = 0.0) -> RefineResult:
     """Alg. 4 lines "convert Qhat, NS step" and REPEAT ... UNTIL convergence.
 
     Stop test (the paper only says "when E becomes small enough"): after
@@ -280,7 +288,7 @@ def refine(A: np.ndarray, Qhat: np.ndarray, lp: str = "f32", tol: float | None =
         prev_rT = r_T
         try:
             Q, info = iteration(A, Q, lp=lp, full_sigma=full_sigma, solver=solver, T_E=(T, E),
-                                symmetric=symmetric)
+                                symmetric=symmetric, cap=cap)
         except SolveError as e:
             res.status = e.code
             res.history.append(IterInfo(r_T=r_T))

@@ -82,7 +82,7 @@ def gemm(x, y, transA: bool = False):
     return ch, cl
 
 
-def alg2_dd_divisors(T: np.ndarray, E: np.ndarray, d) -> np.ndarray:
+def alg2_dd_divisors(T: np.ndarray, E: np.ndarray, d, cap: float = 0.0) -> np.ndarray:
     """Alg. 2 in float64 with divisors t_ii - t_jj from the double-double diagonal d."""
     n = T.shape[0]
     T = _lib.fortran(T, np.float64)
@@ -91,7 +91,7 @@ def alg2_dd_divisors(T: np.ndarray, E: np.ndarray, d) -> np.ndarray:
     dl = np.ascontiguousarray(d[1], dtype=np.float64)
     L = np.zeros((n, n), order="F")
     rc = _lib.lib().sro_alg2_f64_dd(n, _lib.ptr(T), n, _lib.ptr(E), n, _lib.ptr(dh), _lib.ptr(dl),
-                                    _lib.ptr(L), n)
+                                    _lib.ptr(L), n, float(cap))
     if rc:
         raise SolveError(rc)
     return L

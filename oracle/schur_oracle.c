@@ -51,7 +51,7 @@ typedef long double f128_t; /* IEEE binary128 on AArch64 */
 /* Alg. 2 in double. The divisor t_ii - t_jj is formed from dhp if given
  * (the high-precision diagonal), else from T. */
 int sro_alg2_f64(int n, const double *T, int ldt, const double *E, int lde,
-                 const double *dhp, double *L, int ldl)
+                 const double *dhp, double *L, int ldl, double cap)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) L[IDX(i, j, ldl)] = 0.0;
@@ -67,6 +67,7 @@ int sro_alg2_f64(int n, const double *T, int ldt, const double *E, int lde,
             double den = di - dj;
             if (den == 0.0) return SRO_NONDISTINCT;
             double l = -e / den;
+            if (cap > 0.0 && fabs(l) > cap) l = 0.0;
             if (!isfinite(l)) return SRO_NONFINITE;
             L[IDX(i, j, ldl)] = l;
         }
@@ -77,7 +78,7 @@ int sro_alg2_f64(int n, const double *T, int ldt, const double *E, int lde,
 /* Alg. 2 in float (the low precision of the mixed form). The divisor is formed
  * in double from dhp and then rounded to float. */
 int sro_alg2_f32(int n, const float *T, int ldt, const float *E, int lde,
-                 const double *dhp, float *L, int ldl)
+                 const double *dhp, float *L, int ldl, double cap)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) L[IDX(i, j, ldl)] = 0.0f;
@@ -92,6 +93,7 @@ int sro_alg2_f32(int n, const float *T, int ldt, const float *E, int lde,
                             : (T[IDX(i, i, ldt)] - T[IDX(j, j, ldt)]);
             if (den == 0.0f) return SRO_NONDISTINCT;
             float l = -e / den;
+            if (cap > 0.0 && fabsf(l) > (float)cap) l = 0.0f;
             if (!isfinite(l)) return SRO_NONFINITE;
             L[IDX(i, j, ldl)] = l;
         }
@@ -101,7 +103,7 @@ int sro_alg2_f32(int n, const float *T, int ldt, const float *E, int lde,
 
 /* Alg. 2 in complex double (interleaved re, im). */
 int sro_alg2_c128(int n, const double complex *T, int ldt, const double complex *E, int lde,
-                  const double complex *dhp, double complex *L, int ldl)
+                  const double complex *dhp, double complex *L, int ldl, double cap)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) L[IDX(i, j, ldl)] = 0.0;
@@ -117,6 +119,7 @@ int sro_alg2_c128(int n, const double complex *T, int ldt, const double complex 
             double complex den = di - dj;
             if (den == 0.0) return SRO_NONDISTINCT;
             double complex l = -e / den;
+            if (cap > 0.0 && creal(l) * creal(l) + cimag(l) * cimag(l) > cap * cap) l = 0.0;
             if (!isfinite(creal(l)) || !isfinite(cimag(l))) return SRO_NONFINITE;
             L[IDX(i, j, ldl)] = l;
         }
@@ -126,7 +129,7 @@ int sro_alg2_c128(int n, const double complex *T, int ldt, const double complex 
 
 /* Alg. 2 in complex float with divisors formed in complex double. */
 int sro_alg2_c64(int n, const float complex *T, int ldt, const float complex *E, int lde,
-                 const double complex *dhp, float complex *L, int ldl)
+                 const double complex *dhp, float complex *L, int ldl, double cap)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) L[IDX(i, j, ldl)] = 0.0f;
@@ -141,6 +144,10 @@ int sro_alg2_c64(int n, const float complex *T, int ldt, const float complex *E,
                                     : (T[IDX(i, i, ldt)] - T[IDX(j, j, ldt)]);
             if (den == 0.0f) return SRO_NONDISTINCT;
             float complex l = -e / den;
+            if (cap > 0.0) {
+                const float c = (float)cap;
+                if (crealf(l) * crealf(l) + cimagf(l) * cimagf(l) > c * c) l = 0.0f;
+            }
             if (!isfinite(crealf(l)) || !isfinite(cimagf(l))) return SRO_NONFINITE;
             L[IDX(i, j, ldl)] = l;
         }
@@ -184,7 +191,7 @@ static int alg3_rec(int n, const double *T, int ldt, double *E, int lde, double 
         /* Alg. 2 on the block, reading E in place. */
         double *Lb = (double *)calloc((size_t)n * (size_t)n, sizeof(double));
         if (!Lb) return SRO_NONFINITE;
-        int rc = sro_alg2_f64(n, T, ldt, E, lde, NULL, Lb, n);
+        int rc = sro_alg2_f64(n, T, ldt, E, lde, NULL, Lb, n, 0.0);
         for (int j = 0; j < n; ++j)
             for (int i = j + 1; i < n; ++i) L[IDX(i, j, ldl)] = Lb[IDX(i, j, n)];
         free(Lb);
@@ -576,7 +583,7 @@ int sro_max_threads(void)
  * double (the reading "form the divisor in hp, then round" of the FP64 forms,
  * one precision level up). */
 int sro_alg2_f64_dd(int n, const double *T, int ldt, const double *E, int lde,
-                    const double *dhi, const double *dlo, double *L, int ldl)
+                    const double *dhi, const double *dlo, double *L, int ldl, double cap)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) L[IDX(i, j, ldl)] = 0.0;
@@ -592,6 +599,7 @@ int sro_alg2_f64_dd(int n, const double *T, int ldt, const double *E, int lde,
             double den = dd.hi + dd.lo;
             if (den == 0.0) return SRO_NONDISTINCT;
             double l = -e / den;
+            if (cap > 0.0 && fabs(l) > cap) l = 0.0;
             if (!isfinite(l)) return SRO_NONFINITE;
             L[IDX(i, j, ldl)] = l;
         }
