@@ -139,6 +139,13 @@ typedef struct {
                          (the sign of eq. (lij)). Real data and the FP64
                          target only; grouped batches fall back to worker
                          streams. 0 (default): general A */
+    double l_cap;     /* > 0: the trick of Example 4 (Sec. 3) for poorly
+                         separated eigenvalues: while L is computed, an entry
+                         with |l_ij| > l_cap (|l|^2 > l_cap^2 for complex
+                         data, in the low precision) is set to zero at once,
+                         before the entries computed after it use it; the
+                         paper's example value is 1e-5. 0 (default): off.
+                         Negative, NaN or infinite: SR_ERR_INVALID_ARG */
 } sr_options;
 
 /* Fills *opt with the defaults: real, FP64 target, native FP64 products,

@@ -212,7 +212,7 @@ sr_status ensure_capacity(BatchWork *bw, long long elems, int rows, int count, l
     if (!bw->flow_ctas) {
         // the group form of the dataflow solve is launched from this file
         using K = void (*)(int, float *, int, const double *, const double *, int *, int *,
-                           const unsigned long long *, int, float *, int, const sr::SolveMat *);
+                           const unsigned long long *, int, float *, int, double, const sr::SolveMat *);
         const K kern = sr::trisolve_flow_kernel<float, true>;
         const size_t sm = sr::FlowShape<float>::smem;
         int per_sm = 0, sms = 0;
@@ -640,11 +640,12 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
                     SR_CUDA_TRY(trisolve_flow_launch_group<float>(st, (const SolveMat *)P(o_sm), bw->flags, bw->flow,
                                                                   (size_t)fwords,
                                                                   (const unsigned long long *)P(o_fp),
-                                                                  (int)fplan.size(), bw->flow_ctas));
+                                                                  (int)fplan.size(), bw->flow_ctas, h->opt.l_cap));
                 else
                     SR_CUDA_TRY(trisolve_launches_group<float>(st, bw->aux, bw->ev0, bw->ev1,
                                                                (const SolveMat *)P(o_sm), bw->flags,
-                                                               (const unsigned long long *)P(o_pl), poffs, nleaf));
+                                                               (const unsigned long long *)P(o_pl), poffs, nleaf,
+                                                               h->opt.l_cap));
             }
             // S5: Y = Q^T Q - I from Q's column digits (still in slot OZS_COLS), W = L - L^T
             SR_TRY(product(OZS_COLS, OZS_COLS, o_sh, sym_hp, kHp));

@@ -88,6 +88,19 @@ __device__ inline float sr_shfl(float v, int src) { return __shfl_sync(0xfffffff
 __device__ inline double sr_shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ inline cf sr_shfl(cf v, int src) { return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)}; }
 __device__ inline cd sr_shfl(cd v, int src) { return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)}; }
+// |x| > cap (|x|^2 > cap^2 for complex x, products and sum rounded
+// separately), in the working precision: the entry threshold of Example 4
+__device__ inline bool sr_over_cap(float x, double cap) { return fabsf(x) > (float)cap; }
+__device__ inline bool sr_over_cap(double x, double cap) { return fabs(x) > cap; }
+__device__ inline bool sr_over_cap(cf x, double cap)
+{
+    const float c = (float)cap;
+    return __fadd_rn(__fmul_rn(x.x, x.x), __fmul_rn(x.y, x.y)) > __fmul_rn(c, c);
+}
+__device__ inline bool sr_over_cap(cd x, double cap)
+{
+    return __dadd_rn(__dmul_rn(x.x, x.x), __dmul_rn(x.y, x.y)) > __dmul_rn(cap, cap);
+}
 // 1 / z by Smith's scaling (avoids overflow in |z|^2)
 __device__ inline float sr_recip(float z) { return 1.0f / z; }
 __device__ inline double sr_recip(double z) { return 1.0 / z; }

@@ -176,7 +176,8 @@ sr_status check_opts(const sr_options &o)
     if (o.lp != SR_LP_FP32 && o.lp != SR_LP_FP64) return SR_ERR_INVALID_ARG;
     if (o.qhat_type != SR_QHAT_FP32 && o.qhat_type != SR_QHAT_FP64) return SR_ERR_INVALID_ARG;
     if ((o.batch_mode != 0 && o.batch_mode != 1) || (o.tune != 0 && o.tune != 1) || (o.graph != 0 && o.graph != 1) ||
-        o.solve_mode < 0 || o.solve_mode > 2 || (o.symmetric != 0 && o.symmetric != 1))
+        o.solve_mode < 0 || o.solve_mode > 2 || (o.symmetric != 0 && o.symmetric != 1) || !(o.l_cap >= 0.0) ||
+        std::isinf(o.l_cap))
         return SR_ERR_INVALID_ARG;
     if (o.ozaki_slices > (o.target == SR_TARGET_DD ? sr::kOzakiMaxSlicesDD : sr::kOzakiMaxSlices))
         return SR_ERR_INVALID_ARG;
@@ -357,7 +358,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
             // Sec. 2.5: T diagonal, one division per entry
             SrPhase ph(h, SR_PROF_SOLVE, (long long)n * (n - 1) / 2, (long long)n * n * (long long)sizeof(Tl), 1);
             const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
-            sr::diag_solve_kernel<Tl><<<grid, 256, 0, h->st>>>(n, TE, ld, dhp, h->dflags);
+            sr::diag_solve_kernel<Tl><<<grid, 256, 0, h->st>>>(n, TE, ld, dhp, h->dflags, h->opt.l_cap);
             SR_CUDA_TRY(cudaGetLastError());
             return SR_OK;
         }
@@ -370,7 +371,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
             SrPhase ph(h, SR_PROF_SOLVE, fl, (long long)n * n * (long long)sizeof(Tl), 1);
             SR_CUDA_TRY(sr::trisolve_flow_launch<Tl>(h->st, n, TE, ld, dhp, dlo, h->dflags, h->flow, h->flow_plan,
                                                      h->flow_ntasks, (Tl *)h->flow_acc, h->nmax,
-                                                     h->flow_ctas[kind]));
+                                                     h->flow_ctas[kind], h->opt.l_cap));
             return SR_OK;
         }
     }
@@ -379,7 +380,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
     if (h->capturing) {
         // inside the refinement's own graph: the launches themselves are captured
         SR_CUDA_TRY(sr::trisolve_launches<Tl>(h->st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp, dlo, h->dflags,
-                                              h->plan, h->plan_off));
+                                              h->plan, h->plan_off, h->opt.l_cap));
         return SR_OK;
     }
     for (auto &g : h->graphs)
@@ -389,7 +390,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
         cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaError_t el = sr::trisolve_launches<Tl>(h->cap_st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp, dlo,
-                                                       h->dflags, h->plan, h->plan_off);
+                                                       h->dflags, h->plan, h->plan_off, h->opt.l_cap);
             e = cudaStreamEndCapture(h->cap_st, &graph);
             if (el != cudaSuccess) e = el;
         }
@@ -410,7 +411,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
         SR_CUDA_TRY(cudaGraphLaunch(exec, h->st));
     } else {
         SR_CUDA_TRY(sr::trisolve_launches<Tl>(h->st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp, dlo, h->dflags,
-                                              h->plan, h->plan_off));
+                                              h->plan, h->plan_off, h->opt.l_cap));
     }
     return SR_OK;
 }
@@ -1284,6 +1285,7 @@ void schur_refine_default_options(sr_options *opt)
     opt->graph = 0;
     opt->solve_mode = 0;
     opt->symmetric = 0;
+    opt->l_cap = 0.0;
 }
 
 const char *schur_refine_status_string(sr_status s)

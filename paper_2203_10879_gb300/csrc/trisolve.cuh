@@ -269,6 +269,7 @@ template <typename T, bool GROUP = false>
 __global__ void __launch_bounds__(1024)
 trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>::hp *__restrict__ dhp,
                      const double *__restrict__ dlo, int t, const uint32_t *__restrict__ plan, int *__restrict__ flags,
+                     double cap,
                      const SolveMat *__restrict__ mats = nullptr,
                      const unsigned long long *__restrict__ gplan = nullptr)
 {
@@ -356,6 +357,7 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
                 bad |= SR_FLAG_NONDISTINCT;
             } else {
                 xv = -(acc * rcp);
+                if (cap > 0.0 && sr_over_cap(xv, cap)) xv = Z;   // Example 4's trick, before any use
                 if (!sr_finite(xv)) bad |= SR_FLAG_NONFINITE;
             }
             X[a][b] = xv;
@@ -379,7 +381,8 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
 template <typename T>
 inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEvent_t ev0, cudaEvent_t ev1, int n,
                                      T *TE, int ld, const typename SrNum<T>::hp *dhp, const double *dlo,
-                                     int *flags, const uint32_t *plan, const std::vector<long long> &offsets)
+                                     int *flags, const uint32_t *plan, const std::vector<long long> &offsets,
+                                     double cap = 0.0)
 {
     const int NB = (n + kSolveTile - 1) / kSolveTile;
     cudaError_t e = cudaEventRecord(ev0, st);
@@ -388,7 +391,8 @@ inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEven
         const int l = NB - 1 - t;
         const long long nleaf = NB - t;
         const long long nupd = offsets[l + 1] - offsets[l] - nleaf;
-        trisolve_leaf_kernel<T><<<(unsigned)nleaf, 1024, 0, st>>>(n, TE, ld, dhp, dlo, t, plan + offsets[l], flags);
+        trisolve_leaf_kernel<T><<<(unsigned)nleaf, 1024, 0, st>>>(n, TE, ld, dhp, dlo, t, plan + offsets[l], flags,
+                                                                 cap);
         if (nupd > 0)
             trisolve_update_kernel<T><<<(unsigned)nupd, UpdShape<T>::NT, 0, aux>>>(n, TE, ld, t, plan + offsets[l] + nleaf);
         e = cudaGetLastError();
@@ -406,7 +410,8 @@ inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEven
 template <typename T>
 inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cudaEvent_t ev0, cudaEvent_t ev1,
                                            const SolveMat *mats, int *flags, const unsigned long long *plan,
-                                           const std::vector<long long> &offsets, const std::vector<long long> &nleaf)
+                                           const std::vector<long long> &offsets, const std::vector<long long> &nleaf,
+                                           double cap = 0.0)
 {
     const int nsteps = (int)nleaf.size();
     cudaError_t e = cudaEventRecord(ev0, st);
@@ -417,7 +422,7 @@ inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cu
         const long long nupd = offsets[l + 1] - offsets[l] - nl;
         if (nl > 0)
             trisolve_leaf_kernel<T, true><<<(unsigned)nl, 1024, 0, st>>>(0, nullptr, 0, nullptr, nullptr, t, nullptr,
-                                                                        flags, mats, plan + offsets[l]);
+                                                                        flags, cap, mats, plan + offsets[l]);
         if (nupd > 0)
             trisolve_update_kernel<T, true><<<(unsigned)nupd, UpdShape<T>::NT, 0, aux>>>(0, nullptr, 0, t, nullptr, mats,
                                                                                     plan + offsets[l] + nl);
@@ -439,7 +444,7 @@ inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cu
 template <typename T>
 __global__ void __launch_bounds__(256)
 diag_solve_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>::hp *__restrict__ dhp,
-                  int *__restrict__ flags)
+                  int *__restrict__ flags, double cap)
 {
     const int i = blockIdx.x * 32 + (threadIdx.x & 31);
     const int jb = blockIdx.y * 32 + (threadIdx.x >> 5);
@@ -454,6 +459,7 @@ diag_solve_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>::hp
                 bad |= SR_FLAG_NONDISTINCT;
             } else {
                 x = -(TE[sr_idx(i, j, ld)] / den);
+                if (cap > 0.0 && sr_over_cap(x, cap)) x = SrNum<T>::zero();   // Example 4's trick
                 if (!sr_finite(x)) bad |= SR_FLAG_NONFINITE;
             }
             TE[sr_idx(i, j, ld)] = x;
@@ -581,7 +587,7 @@ __global__ void __launch_bounds__(FlowShape<T>::NT, 2)
 trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<T>::hp *__restrict__ dhp0,
                      const double *__restrict__ dlo, int *__restrict__ flags0, int *__restrict__ work,
                      const unsigned long long *__restrict__ plan, int ntasks, T *__restrict__ accb, int ldacc,
-                     const SolveMat *__restrict__ mats = nullptr)
+                     double cap, const SolveMat *__restrict__ mats = nullptr)
 {
     using S = FlowShape<T>;
     using Hp = typename SrNum<T>::hp;
@@ -792,6 +798,7 @@ trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<
             for (int q = 0; q < EPT; ++q)
                 if (own[q] && a - (wq + WS * q) == w) {
                     xv[q] = -(acc[q] * rcp[q]);
+                    if (cap > 0.0 && sr_over_cap(xv[q], cap)) xv[q] = Z;   // Example 4's trick, before any use
                     X[a][wq + WS * q] = xv[q];
                 }
             __syncthreads();
@@ -826,13 +833,14 @@ trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<
 // words in work + 2; nwords = 2 + their total.
 template <typename T>
 inline cudaError_t trisolve_flow_launch_group(cudaStream_t st, const SolveMat *mats, int *flags, int *work,
-                                              size_t nwords, const unsigned long long *plan, int ntiles, int ctas)
+                                              size_t nwords, const unsigned long long *plan, int ntiles, int ctas,
+                                              double cap = 0.0)
 {
     cudaError_t e = cudaMemsetAsync(work, 0, nwords * sizeof(int), st);
     if (e != cudaSuccess || ntiles < 1) return e;
     trisolve_flow_kernel<T, true><<<(unsigned)std::max(1, std::min(ctas, ntiles)), FlowShape<T>::NT,
                                     FlowShape<T>::smem, st>>>(0, nullptr, 0, nullptr, nullptr, flags, work, plan,
-                                                              ntiles, nullptr, 0, mats);
+                                                              ntiles, nullptr, 0, cap, mats);
     return cudaGetLastError();
 }
 
@@ -844,13 +852,13 @@ inline cudaError_t trisolve_flow_launch_group(cudaStream_t st, const SolveMat *m
 template <typename T>
 inline cudaError_t trisolve_flow_launch(cudaStream_t st, int n, T *TE, int ld, const typename SrNum<T>::hp *dhp,
                                         const double *dlo, int *flags, int *work, const unsigned long long *plan,
-                                        int ntasks, T *accb, int ldacc, int ctas)
+                                        int ntasks, T *accb, int ldacc, int ctas, double cap = 0.0)
 {
     const int NB = (n + kSolveTile - 1) / kSolveTile;
     cudaError_t e = cudaMemsetAsync(work, 0, (2 + 2 * (size_t)NB * NB) * sizeof(int), st);
     if (e != cudaSuccess) return e;
     trisolve_flow_kernel<T><<<(unsigned)std::max(1, std::min(ctas, ntasks)), FlowShape<T>::NT, FlowShape<T>::smem,
-                              st>>>(n, TE, ld, dhp, dlo, flags, work, plan, ntasks, accb, ldacc);
+                              st>>>(n, TE, ld, dhp, dlo, flags, work, plan, ntasks, accb, ldacc, cap);
     return cudaGetLastError();
 }
 

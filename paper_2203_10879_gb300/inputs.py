@@ -243,6 +243,35 @@ def symmetric_real(n: int = 4096, seed: int = BASE_SEED + 5, low: str = "f32") -
     return Planted(A=A, Qhat=p.Qhat, Q0=p.Q0, T0=p.T0, lam=p.lam, seed=p.seed, recipe=p.recipe)
 
 
+def clustered_complex(n: int = 150, cond: float = 1e5, radius: float = 1e-5, seed: int = BASE_SEED + 6,
+                      low: str = "f32") -> Planted:
+    """The setting of Example 3 (Sec. 3): A = X D X^-1 with X of condition
+    ``cond`` (singular values geometric between 1 and 1/cond, Haar singular
+    vectors) and D real diagonal, uniform in [-10, 10] except two clusters of
+    10 eigenvalues within ``radius`` of random centres. The start is the
+    complex Schur form computed by LAPACK in FP64 (scipy.linalg.schur), the
+    Schur vectors rounded to ``low``; Q0 holds the FP64 Schur vectors and T0
+    the FP64 Schur factor."""
+    import scipy.linalg
+    st = Stream(seed)
+    U = _haar_orthogonal(st, n, False)
+    V = _haar_orthogonal(st, n, False)
+    sv = np.exp(-np.log(cond) * np.arange(n) / (n - 1))
+    X = (U * sv) @ V.T
+    lam = -10.0 + 20.0 * st.uniform((n,))
+    for c in range(2):
+        centre = -10.0 + 20.0 * float(st.uniform((1,))[0])
+        lam[10 * c:10 * c + 10] = centre + radius * (2.0 * st.uniform((10,)) - 1.0)
+    A = np.asfortranarray(np.linalg.solve(X.T, (X * lam).T).T)   # X diag(lam) X^-1
+    Ac = A.astype(np.complex128)
+    T0, Z = scipy.linalg.schur(Ac, output="complex")
+    dt = {"f32": np.complex64, "f64": np.complex128}[low]
+    return Planted(A=np.asfortranarray(Ac), Qhat=np.asfortranarray(Z.astype(dt)), Q0=np.asfortranarray(Z),
+                   T0=np.asfortranarray(T0), lam=lam, seed=seed,
+                   recipe=f"Example 3 setting n={n}: A = X D X^-1, cond(X)={cond:g}, two clusters of 10 within "
+                          f"{radius:g}; Qhat = fl_{low}(complex Schur vectors of LAPACK in FP64)")
+
+
 def ring_complex(n: int = 8192, seed: int = BASE_SEED + 3) -> Planted:
     """Complex planted problem with ring eigenvalues and a complex64-rounded start."""
     return planted(n, eig_ring(n, seed), seed, pert=1e-6, low="f32", complex_=True,

@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(L):
 def test_default_options(L):
     o = B.default_options()
     assert (o.dtype, o.hp_gemm, o.lp, o.qhat_type, o.full_sigma, o.max_iter) == (0, 0, 0, 0, 0, 10)
-    assert (o.batch_mode, o.tune, o.graph, o.solve_mode) == (0, 0, 0, 0)
+    assert (o.batch_mode, o.tune, o.graph, o.solve_mode, o.symmetric, o.l_cap) == (0, 0, 0, 0, 0, 0.0)
     # the binding's struct has the C struct's size (the library fills every field)
     raw = (ctypes.c_char * (ctypes.sizeof(B.sr_options) + 64))(*([b"\xab"] * (ctypes.sizeof(B.sr_options) + 64)))
     L.schur_refine_default_options(ctypes.cast(raw, ctypes.POINTER(B.sr_options)))
@@ -69,7 +69,8 @@ def test_create_rejects_bad_sizes_and_options(L):
     assert L.schur_refine_create(ctypes.byref(h), 8, ctypes.byref(o), None) == B.SR_ERR_INVALID_ARG
     o = B.default_options(ozaki_slices=99)
     assert L.schur_refine_create(ctypes.byref(h), 8, ctypes.byref(o), None) == B.SR_ERR_INVALID_ARG
-    for bad in ({"solve_mode": 3}, {"solve_mode": -1}, {"graph": 2}, {"tune": 2}, {"batch_mode": 5}):
+    for bad in ({"solve_mode": 3}, {"solve_mode": -1}, {"graph": 2}, {"tune": 2}, {"batch_mode": 5},
+                {"symmetric": 2}, {"l_cap": -1.0}, {"l_cap": float("nan")}, {"l_cap": float("inf")}):
         o = B.default_options(**bad)
         assert L.schur_refine_create(ctypes.byref(h), 8, ctypes.byref(o), None) == B.SR_ERR_INVALID_ARG, bad
         assert h.value is None

@@ -237,3 +237,43 @@ def test_complex_workload_full_size(torch):
     assert np.max(np.abs(y)) <= tol
     diag = rows == cols
     assert np.max(np.abs(t[diag] - p.lam[rows[diag]])) <= 1e-11
+
+
+# ---------------------------------------------------------------------------
+# poorly separated eigenvalues: the setting of Example 3 and the entry
+# threshold of Example 4 (Sec. 3)
+
+FAIL = (B.SR_ERR_NOT_CONVERGED, B.SR_ERR_NONFINITE, B.SR_ERR_NONDISTINCT)
+
+
+def test_clustered_failure_and_threshold_match_oracle(torch):
+    """cond(X) = 1e5, clusters of radius 1e-5: without the threshold the
+    refinement diverges (the large entries of L for the clusters pollute it),
+    with l_cap = 1e-5 it converges to the attainable residual; the GPU and the
+    oracle take the same course. tol = 5e-13: the residual levels off near
+    1e-13 here, the conditioning's limit."""
+    p = inputs.clustered_complex(150, 1e5, 1e-5)
+    tol = 5e-13
+    st0, nr0, *_ = _refine(p, residuals=False, tol=tol)
+    r0 = oracle.refine(p.A, p.Qhat, lp="f32", tol=tol)
+    assert st0 in FAIL and r0.status in FAIL
+    st1, nr1, Q1, T1, _ = _refine(p, residuals=False, tol=tol, l_cap=1e-5)
+    r1 = oracle.refine(p.A, p.Qhat, lp="f32", tol=tol, cap=1e-5)
+    assert st1 == B.SR_OK and r1.status == oracle.OK
+    assert abs(nr1.iters - r1.iters) <= 1
+    cT, cQ = oracle.residuals_dd(p.A, Q1)
+    assert cT <= tol and cQ <= tol
+    # single Schur vectors inside a cluster are ill-determined (rotations
+    # within the cluster's invariant subspace); the Schur diagonal is not
+    D_ref = np.diagonal(r1.Q.conj().T @ p.A @ r1.Q)
+    assert np.max(np.abs(np.diagonal(T1) - D_ref)) <= 1e-8
+
+
+def test_threshold_inert_on_well_separated_clusters(torch):
+    """cond(X) = 1e3, radius 1e-3: no entry of L reaches 1e-5, so the
+    threshold changes nothing and both runs converge alike."""
+    p = inputs.clustered_complex(150, 1e3, 1e-3)
+    st0, nr0, Q0, *_ = _refine(p, residuals=False)
+    st1, nr1, Q1, *_ = _refine(p, residuals=False, l_cap=1e-5)
+    assert st0 == st1 == B.SR_OK and nr0.iters == nr1.iters
+    assert np.array_equal(Q0, Q1)

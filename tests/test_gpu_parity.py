@@ -326,3 +326,59 @@ def test_symmetric_option_rejected_for_complex_and_dd(torch):
                {"target": B.SR_TARGET_DD, "lp": B.SR_LP_FP64, "qhat_type": B.SR_QHAT_FP64}):
         s, h = B.schur_refine_create(64, B.default_options(symmetric=1, **kw), None)
         assert s == B.SR_ERR_UNSUPPORTED and not h
+
+
+# ---------------------------------------------------------------------------
+# entry threshold of Example 4 (Sec. 3)
+
+def _threshold_problem(n, seed):
+    """Evenly spaced eigenvalues k/n with weak coupling (|t_ij| ~ 0.1/n), except
+    a cluster of six 1e-9 apart: the entries of L inside the cluster are ~1e-3
+    and feed one another, every other entry is below ~1e-8, so GPU and oracle
+    take the same clamp decisions whatever the order of their sums."""
+    rng = np.random.default_rng(seed)
+    d = np.arange(n, dtype=np.float64) / n
+    k = n // 2
+    d[k - 5:k + 1] = d[k - 5] + 1e-9 * np.arange(6)
+    T = np.triu(rng.standard_normal((n, n)) * (0.1 / n), 1) + np.diag(d)
+    g = rng.standard_normal((n, n))
+    E = np.tril(np.sign(g) * (1.0 + np.abs(g)) * 1e-12, -1)   # |e_ij| >= 1e-12
+    return T, E, d
+
+
+@pytest.mark.parametrize("solve_mode", SOLVE_MODES)
+@pytest.mark.parametrize("lp,dt,rtol", [(B.SR_LP_FP32, np.float32, 1e-4), (B.SR_LP_FP64, np.float64, 1e-12)])
+@pytest.mark.parametrize("n", [33, 100, 257])
+def test_trisolve_threshold_parity(torch, n, lp, dt, rtol, solve_mode):
+    T, E, d = _threshold_problem(n, 3 * n)
+    h = _handle(n, lp=lp, solve_mode=solve_mode, l_cap=1e-5)
+    try:
+        TE = to_dev((np.triu(T) + E).astype(dt))
+        assert B.schur_refine_trisolve(h, n, TE, to_dev(d.copy())) == B.SR_OK
+        L = np.tril(from_dev(TE), -1).astype(np.float64)
+    finally:
+        B.schur_refine_destroy(h)
+    ref = oracle.alg2(np.triu(T).astype(dt), E.astype(dt), d, 1e-5).astype(np.float64)
+    free = oracle.alg2(np.triu(T).astype(dt), E.astype(dt), d).astype(np.float64)
+    assert np.max(np.abs(free)) > 1e-4                     # the cluster's entries exceed the threshold
+    assert np.max(np.abs(ref)) < 1e-7 and np.max(np.abs(L)) < 1e-7
+    assert np.array_equal(np.tril(L == 0, -1), np.tril(ref == 0, -1))
+    assert np.linalg.norm(L - ref) <= rtol * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("lp,dt", [(B.SR_LP_FP32, np.float32), (B.SR_LP_FP64, np.float64)])
+def test_symmetric_solve_threshold_bit_exact(torch, lp, dt):
+    n = 64
+    rng = np.random.default_rng(4)
+    d = np.sort(rng.uniform(0.0, 1.0, n))
+    d[10] = d[9] + 1e-9
+    E = np.tril(rng.standard_normal((n, n)) * 1e-12, -1)
+    h = _handle(n, lp=lp, symmetric=1, l_cap=1e-5)
+    try:
+        TE = to_dev((np.diag(d) + E).astype(dt))
+        assert B.schur_refine_trisolve(h, n, TE, to_dev(d.copy())) == B.SR_OK
+        L = np.tril(from_dev(TE), -1)
+    finally:
+        B.schur_refine_destroy(h)
+    ref = oracle.sym_solve(E.astype(dt), d, 1e-5)
+    assert ref[10, 9] == 0 and np.array_equal(L, ref)
