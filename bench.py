@@ -128,6 +128,27 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def shard(count: int, ws: int, rank: int) -> list:
+    """The units (matrices) rank `rank` of `ws` refines: every ws-th one from
+    index `rank` (replicas: no data-path collective)."""
+    return [i for i in range(count) if i % ws == rank]
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (the slowest rank's time)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_total: int, ms_max: float) -> float:
+    """Units of all ranks per second over the slowest rank's time."""
+    return units_total / (ms_max / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -321,10 +342,7 @@ def run_ours(args):
     else:
         rT, rQ = mixed.residuals(A, Q)
         cert_kind = "double-double residual products on the device"
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     launches = int(sum(v["launches"] for v in prof.values()))
 
     # ---- end to end through host buffers --------------------------------------------
@@ -346,10 +364,7 @@ def run_ours(args):
         hQ.copy_(dQ_t, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / ke
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     mixed.close()
 
     # ---- all-FP64 form of the same iteration on the same inputs -----------------------
@@ -467,7 +482,11 @@ def run_batched(args):
     torch.cuda.set_device(local)
     ns = inputs.batch_sizes(args.count)
     # replicas only: every rank refines its own share of the matrices (no collective)
-    mine = [i for i in range(len(ns)) if i % ws == rank]
+    mine = shard(len(ns), ws, rank)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     probs = [inputs.batch_problem(i, ns[i]) for i in mine]
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
     As = [dev(p.A) for p in probs]
@@ -507,11 +526,7 @@ def run_batched(args):
         out[key] = (e0.elapsed_time(e1) / steps, st, iters, stats, prof)
         B.schur_refine_destroy(h)
     ms, st, iters, stats, prof = out["grouped"]
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     if rank == 0:
         # the dominant kernel's roofline: the slice products of the group, live
         peaks = _peaks()
@@ -539,7 +554,7 @@ def run_batched(args):
             cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
             cpu = {"value": len(ns) / est, "unit": "matrices/s", "cores": cores, "kind": "oracle",
                    "sample": f"oracle full refinements of the first {k} matrices ({dt:.1f} s), scaled by sum n^3"}
-        line = {"metric": "matrices/s refined to FP64 accuracy (batched)", "value": len(ns) / (ms / 1e3),
+        line = {"metric": "matrices/s refined to FP64 accuracy (batched)", "value": whole_job_rate(len(ns), ms),
                 "unit": "matrices/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
                 "data": "synthetic",
@@ -555,6 +570,8 @@ def run_batched(args):
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": int(sum(v["launches"] for v in prof.values()))}
         print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
@@ -633,10 +650,7 @@ def run_dd(args):
     prof = mixed.profile()
     rT, rQ = mixed.residuals(A, Q)
     launches = int(sum(v["launches"] for v in prof.values()))
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     # end to end through pinned host buffers
     hA = torch.from_numpy(np.ascontiguousarray(np.hstack([p.A_hi, p.A_lo]).T)).pin_memory()
     hQh = torch.from_numpy(np.ascontiguousarray(p.Qhat.T)).pin_memory()
@@ -737,6 +751,10 @@ def run_small(args):
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:   # replicas: each rank refines its own copy; the slowest rank's time is reported
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = args.n
     p = inputs.unit_step_real(n)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
@@ -769,9 +787,13 @@ def run_small(args):
         rT, rQ = r.residuals(A, Q)
         res[key] = (e0.elapsed_time(e1) / args.steps, st, nr, rT, rQ, prof, c)
         r.close()
+    ms_max = max_over_ranks(res["all_fp64_graph"][0], dist, "cuda")
+    if dist is not None:
+        dist.destroy_process_group()
     if rank != 0:
         return 0
     ms, st, nr, rT, rQ, _, clk = res["all_fp64_graph"]
+    ms = ms_max
     prof = res["all_fp64"][5]    # the graph mode records no phase profile: the host-loop run's
     tol = 1e-14 * math.sqrt(n)
     d = prof["hp_gemm"]
