@@ -66,6 +66,21 @@ def _peaks():
         return {}
 
 
+def bf16_peak(clk, peaks):
+    """The measured bf16 peak that matches the timed region's clock: the burst
+    figure when the region's median SM clock is at (>= 95 % of) the maximum,
+    else the figure measured over seconds under the power cap."""
+    med, mx = (clk or {}).get("sm_mhz"), (clk or {}).get("sm_max_mhz")
+    burst, sustained = peaks.get("bf16_tflops"), peaks.get("bf16_tflops_sustained")
+    if med and mx and med >= 0.95 * mx and burst:
+        return burst, f"of measured bf16 burst (MEASURED_PEAKS.json; timed region's median SM clock {med:.0f} MHz " \
+                      f"= max {mx:.0f} MHz)"
+    if sustained:
+        return sustained, f"of measured bf16 sustained (MEASURED_PEAKS.json; timed region's median SM clock " \
+                          f"{med} MHz below max {mx})"
+    return 1900.0, "of fallback 1.9 PFLOP/s bf16 (no MEASURED_PEAKS.json)"
+
+
 def _workload_name(n, cplx=False, sym=False):
     if sym:
         return (f"real symmetric n={n} planted A=Q0 diag(lambda) Q0^T, lambda_k=k/n+U(0,0.5/n), "
@@ -128,10 +143,24 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def shard(count: int, ws: int, rank: int) -> list:
-    """The units (matrices) rank `rank` of `ws` refines: every ws-th one from
-    index `rank` (replicas: no data-path collective)."""
-    return [i for i in range(count) if i % ws == rank]
+def shard(sizes, ws: int, rank: int) -> list:
+    """The units (matrices) rank `rank` of `ws` refines, balanced by work: the
+    matrices are taken in decreasing order of n^3 (the cost of a refinement's
+    products and solve) and each goes to the rank with the least total so far
+    (lowest rank on ties). Every rank computes the same deal from the same
+    sizes, so no data-path collective is needed. `sizes` is a sequence of
+    orders, or an int count of equal-sized units."""
+    if isinstance(sizes, int):
+        sizes = [1] * sizes
+    order = sorted(range(len(sizes)), key=lambda i: (-float(sizes[i]) ** 3, i))
+    load = [0.0] * ws
+    mine = []
+    for i in order:
+        r = min(range(ws), key=lambda k: (load[k], k))
+        load[r] += float(sizes[i]) ** 3
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -156,45 +185,103 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_sample(n_full: int, n_sample: int, cplx: bool = False, sym: bool = False):
-    """The oracle's full refinement at n_sample, scaled by (n_full/n_sample)^3."""
-    import oracle
+def _cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def _oracle_problem(workload: str, n: int):
     from paper_2203_10879_gb300 import inputs
-    if sym:
-        p = inputs.symmetric_real(n_sample)
-    else:
-        p = inputs.ring_complex(n_sample) if cplx else inputs.jittered_real(n_sample)
+    if workload == "sym":
+        return inputs.symmetric_real(n)
+    if workload == "complex":
+        return inputs.ring_complex(n)
+    if workload == "dd":
+        return inputs.unit_step_dd(n)
+    return inputs.jittered_real(n)
+
+
+def oracle_refine_seconds(workload: str, n: int):
+    """One full refinement by the oracle (as it stands) of the workload's recipe at
+    order n, on this process's threads: numpy products (BLAS threads) and the C
+    Alg. 2. Returns (seconds, status, passes)."""
+    import oracle
+    p = _oracle_problem(workload, n)
     t0 = time.perf_counter()
-    r = oracle.refine(p.A, p.Qhat, lp="f32", symmetric=sym)
+    if workload == "dd":
+        from oracle import ddtarget
+        r = ddtarget.refine_dd((p.A_hi, p.A_lo), p.Qhat)
+    else:
+        r = oracle.refine(p.A, p.Qhat, lp="f32", symmetric=workload == "sym")
     dt = time.perf_counter() - t0
-    scale = (n_full / n_sample) ** 3
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return dt * scale, dt, r, cores
+    return dt, int(getattr(r, "status", -1)), int(getattr(r, "iters", -1))
+
+
+def oracle_refine_seconds_1t(workload: str, n: int):
+    """oracle_refine_seconds in a child process whose BLAS and OpenMP pools have one
+    thread (the thread counts are fixed when the libraries load)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               VECLIB_MAXIMUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-probe", workload, str(n)],
+                         env=env, capture_output=True, text=True, check=True)
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    return d["s"], d["status"], d["iters"]
+
+
+def cpu_baseline(workload: str, n: int, n_sample: int, full: bool, one_thread: bool = True):
+    """The oracle timed on the host cores. full: one refinement at the workload's own
+    order n (measured); otherwise one at n_sample (measured, and reported as such,
+    with the n^3 estimate for order n as a separate labelled field). one_thread adds
+    a one-thread measurement at n_sample."""
+    cores = _cores()
+    if full:
+        dt, st, it = oracle_refine_seconds(workload, n)
+        base = {"value": dt, "unit": "s", "cores": cores, "kind": "oracle", "n": n,
+                "sample": f"oracle full refinement measured at n = {n} ({it} passes, status {st}), "
+                          f"{cores} threads"}
+    else:
+        dt, st, it = oracle_refine_seconds(workload, n_sample)
+        base = {"value": dt, "unit": "s", "cores": cores, "kind": "oracle", "n": n_sample,
+                "sample": f"oracle full refinement measured at n = {n_sample} of the same recipe ({it} passes, "
+                          f"status {st}), {cores} threads; the workload's n = {n} takes too long to refine on "
+                          f"the host within the run",
+                "n3_estimate_at_n_s": dt * (n / n_sample) ** 3}
+    if one_thread:
+        d1, _, _ = oracle_refine_seconds_1t(workload, n_sample)
+        base["one_thread"] = {"value": d1, "unit": "s", "n": n_sample,
+                              "sample": f"oracle full refinement measured at n = {n_sample}, 1 thread"}
+    return base
 
 
 def run_reference(args):
+    """The oracle as the reference arm: every step is one full refinement by the
+    oracle of the workload's recipe at order n_ref (measured; the line's config
+    names that order), on the host cores of rank 0."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    n, ns, cplx = args.n, args.cpu_sample_n, args.workload == "complex"
-    dd, sym = args.workload == "dd", args.workload == "sym"
+    dd, sym, cplx = args.workload == "dd", args.workload == "sym", args.workload == "complex"
+    n_ref = args.cpu_sample_n
     times = []
+    st = it = None
     for i in range(args.warmup + args.steps):
-        est, dt, r, cores = cpu_oracle_sample_dd(n, ns) if dd else cpu_oracle_sample(n, ns, cplx, sym)
+        dt, st, it = oracle_refine_seconds(args.workload, n_ref)
         if i >= args.warmup:
-            times.append(est)
+            times.append(dt)
     v = sum(times) / len(times)
+    cores = _cores()
     if dd:
-        sample = (f"double-double oracle (C triple-loop TwoProd/TwoSum products + C Alg. 2 in FP64) full "
-                  f"refinement at n={ns} of the same recipe, scaled by (n/{ns})^3 to n={n}")
+        sample = f"double-double oracle (C TwoProd/TwoSum products + C Alg. 2 in FP64) full refinement at n={n_ref}"
     else:
-        sample = (f"oracle (numpy FP64 products + C Alg. 2 in FP32) full refinement at n={ns} of the same "
-                  f"recipe, scaled by (n/{ns})^3 to n={n}")
+        sample = f"oracle (numpy products + C Alg. 2 in the low precision) full refinement at n={n_ref}"
+    name = _dd_workload_name(n_ref) if dd else _workload_name(n_ref, cplx, sym)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "dd+f64" if dd else "f64+f32", "data": "synthetic",
-            "config": {"workload": _dd_workload_name(n) if dd else _workload_name(n, cplx, sym), "n": n,
-                       "form": "FP64->double-double (oracle)" if dd else "mixed FP32->FP64 (oracle)"},
+            "config": {"workload": name, "n": n_ref,
+                       "form": "FP64->double-double (oracle)" if dd else "mixed FP32->FP64 (oracle)",
+                       "note": f"measured at n = {n_ref}, not at the GPU line's n = {args.n} (a full oracle "
+                               f"refinement at n = {args.n} per step does not fit the run)",
+                       "status": st, "iters": it},
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -291,13 +378,6 @@ def run_ours(args):
 
     hp_name = {"fp64": B.SR_HP_FP64, "ozaki": B.SR_HP_OZAKI_BF16}
     hp = "ozaki" if cplx else args.hp
-    if hp == "auto":
-        hp = "ozaki"
-        try:
-            probe = P.Refiner(8, hp_gemm=B.SR_HP_OZAKI_BF16)
-            probe.close()
-        except P.SchurRefineError:
-            hp = "fp64"
 
     def timed(ref, steps, warmup, host=False):
         for _ in range(warmup):
@@ -408,13 +488,13 @@ def run_ours(args):
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table; no measured FP64 peak)"}
     elif dom == "oz_mma":
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        peak, psrc = bf16_peak(clk, peaks)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": OZ_MMA_TRAFFIC_BYTES_N4096 if (n == 4096 and not cplx and (args.slices or 7) == 7)
                 else None,
                 "traffic_note": "bytes per launch of the captured 28-pair product (ncu)",
                 "kernel": "ozaki slice products (tcgen05 kind::f16 bf16)",
-                "peak_source": "of measured bf16 sustained (MEASURED_PEAKS.json)"}
+                "peak_source": psrc}
     else:
         gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs") or 6800.0
@@ -423,14 +503,9 @@ def run_ours(args):
     roof["launch_ms"] = d["ms"] / max(1, d["spans"])
     roof["share_of_step"] = d["ms"] / (ms * args.steps)
 
-    cpu_val = None
     cpu = None
     if not args.no_cpu_baseline:
-        est, dt, r, cores = cpu_oracle_sample(n, args.cpu_sample_n, cplx, sym)
-        cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": f"oracle full refinement at n={args.cpu_sample_n} ({dt:.2f} s measured), "
-                         f"scaled by (n/{args.cpu_sample_n})^3 to n={n}"}
-        cpu_val = est
+        cpu = cpu_baseline(args.workload, n, args.cpu_sample_n, full=args.cpu_full)
 
     tol = 1e-14 * math.sqrt(n)
     line = {
@@ -482,7 +557,7 @@ def run_batched(args):
     torch.cuda.set_device(local)
     ns = inputs.batch_sizes(args.count)
     # replicas only: every rank refines its own share of the matrices (no collective)
-    mine = shard(len(ns), ws, rank)
+    mine = shard([int(x) for x in ns], ws, rank)
     dist = None
     if ws > 1:
         import torch.distributed as dist
@@ -534,29 +609,25 @@ def run_batched(args):
         roof = None
         if mma["ms"] > 0:
             achieved = mma["flops"] / (mma["ms"] * 1e-3) / 1e12
-            peak = peaks.get("bf16_tflops_sustained") or 1700.0
+            peak, psrc = bf16_peak(clk, peaks)
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": None, "kernel": "ozaki slice products, work-item form (tcgen05 kind::f16 bf16)",
-                    "peak_source": "of measured bf16 sustained (MEASURED_PEAKS.json)",
+                    "peak_source": psrc,
                     "share_of_step": mma["ms"] / (ms * args.steps)}
         cpu = None
         if not args.no_cpu_baseline:
-            # the oracle on a bounded sample: the first matrices of the batch, scaled by sum n^3
+            # the oracle refines every matrix of this rank's share, one after another
             import oracle
-            t0, k, done = time.perf_counter(), 0, 0.0
-            while k < len(probs) and time.perf_counter() - t0 < 10.0:
-                oracle.refine(probs[k].A, probs[k].Qhat, lp="f32")
-                done += float(probs[k].n) ** 3
-                k += 1
+            t0 = time.perf_counter()
+            for pr in probs:
+                oracle.refine(pr.A, pr.Qhat, lp="f32")
             dt = time.perf_counter() - t0
-            total = float(np.sum(ns.astype(float) ** 3))
-            est = dt * total / done
-            cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-            cpu = {"value": len(ns) / est, "unit": "matrices/s", "cores": cores, "kind": "oracle",
-                   "sample": f"oracle full refinements of the first {k} matrices ({dt:.1f} s), scaled by sum n^3"}
+            cpu = {"value": len(probs) / dt, "unit": "matrices/s", "cores": _cores(), "kind": "oracle",
+                   "sample": f"oracle full refinements of all {len(probs)} matrices of the batch, measured "
+                             f"({dt:.1f} s)"}
         line = {"metric": "matrices/s refined to FP64 accuracy (batched)", "value": whole_job_rate(len(ns), ms),
                 "unit": "matrices/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64+f32",
                 "data": "synthetic",
                 "config": {"workload": f"{len(ns)} real matrices, n log-uniform in [32,512] (sum n^3 = "
                                        f"{float(np.sum(ns.astype(float) ** 3)):.3g}), unit-step spectra, FP32 Qhat",
@@ -579,18 +650,6 @@ def _dd_workload_name(n):
     return (f"real n={n} double-double planted A=Q0 T0 Q0^T (Q0 from exact-rational rotations), "
             f"lambda_k=1+k/64, upper std 1/n, Qhat=fl64(Q0 expm(1e-14 S)); Alg. 4 with double-double hp and "
             f"FP64 lp to ||stril||/||A||<=1e-28 n")
-
-
-def cpu_oracle_sample_dd(n_full: int, n_sample: int):
-    """The double-double oracle's full refinement at n_sample, scaled by (n_full/n_sample)^3."""
-    from oracle import ddtarget
-    from paper_2203_10879_gb300 import inputs
-    p = inputs.unit_step_dd(n_sample)
-    t0 = time.perf_counter()
-    r = ddtarget.refine_dd((p.A_hi, p.A_lo), p.Qhat)
-    dt = time.perf_counter() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return dt * (n_full / n_sample) ** 3, dt, r, cores
 
 
 def run_dd(args):
@@ -685,12 +744,12 @@ def run_dd(args):
     d = prof[dom]
     if dom == "oz_mma":
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        peak, psrc = bf16_peak(clk, peaks)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": OZ_MMA_TRAFFIC_BYTES_DD2048 if (n == 2048 and (args.slices or 14) == 14) else None,
                 "traffic_note": "bytes per launch of the captured 105-pair A Q product (ncu)",
                 "kernel": "ozaki slice products (tcgen05 kind::f16 bf16), 14 digits",
-                "peak_source": "of measured bf16 sustained (MEASURED_PEAKS.json)"}
+                "peak_source": psrc}
     else:
         gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs") or 6800.0
@@ -700,11 +759,7 @@ def run_dd(args):
     roof["share_of_step"] = d["ms"] / (ms * args.steps)
     cpu = None
     if not args.no_cpu_baseline:
-        ns = args.cpu_sample_n
-        est, dt, r, cores = cpu_oracle_sample_dd(n, ns)
-        cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": f"double-double oracle full refinement at n={ns} ({dt:.2f} s measured), "
-                         f"scaled by (n/{ns})^3 to n={n}"}
+        cpu = cpu_baseline("dd", n, args.cpu_sample_n, full=args.cpu_full)
     tol = 1e-28 * n
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
@@ -835,26 +890,66 @@ def run_small(args):
     return 0
 
 
+def _launch_ranks(args) -> int | None:
+    """--gpus N: one process per GPU. Under an external launcher WORLD_SIZE must equal
+    N; without one, N > 1 re-executes this script under torch.distributed.run with N
+    local ranks (rendezvous on 127.0.0.1). Returns an exit code when this process
+    must not run the benchmark itself, else None."""
+    if args.gpus < 1:
+        sys.stderr.write("bench.py: --gpus must be >= 1\n")
+        return 2
+    if "WORLD_SIZE" in os.environ:
+        ws = int(os.environ["WORLD_SIZE"])
+        if ws != args.gpus:
+            sys.stderr.write(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={ws}\n")
+            return 2
+        return None
+    if args.gpus == 1:
+        return None
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
+    if len(sys.argv) == 4 and sys.argv[1] == "--oracle-probe":
+        # child of oracle_refine_seconds_1t: one oracle refinement, its time as JSON
+        dt, st, it = oracle_refine_seconds(sys.argv[2], int(sys.argv[3]))
+        print(json.dumps({"s": dt, "status": st, "iters": it}))
+        return 0
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=None)
-    ap.add_argument("--hp", choices=["auto", "fp64", "ozaki"], default="auto")
+    ap.add_argument("--hp", choices=["fp64", "ozaki"], default="ozaki")
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample-n", type=int, default=None)
+    ap.add_argument("--cpu-sample-n", type=int, default=None,
+                    help="order of the oracle's bounded sample (reference arm, one-thread baseline)")
+    ap.add_argument("--cpu-full", type=int, default=None,
+                    help="1: time the oracle at the workload's own order; 0: at --cpu-sample-n")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["single", "complex", "batched", "dd", "small", "sym"], default="single")
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--batch-streams", type=int, default=8)
     args = ap.parse_args()
+    rc = _launch_ranks(args)
+    if rc is not None:
+        return rc
     if args.n is None:
         args.n = {"complex": 8192, "dd": 2048, "small": 64}.get(args.workload, 4096)
     if args.cpu_sample_n is None:
         args.cpu_sample_n = {"complex": 2048, "dd": 512}.get(args.workload, 1024)
+    if args.cpu_full is None:
+        # the complex n = 8192 oracle refinement takes tens of minutes on the host
+        args.cpu_full = 0 if args.workload == "complex" else 1
+    args.cpu_full = bool(args.cpu_full)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

@@ -233,7 +233,8 @@ sr_status schur_refine_batched(schur_refine_t h, int batch, const int *n, const 
  * so that values near 1e-16 are resolved (for SR_TARGET_DD the double-double
  * A and Q enter with both planes; the accumulation error, about n * 1e-32
  * relative, stays far below the target 1e-28 n). dA, dQ as in
- * schur_refine_step; stril_rel, orth: host. Synchronizes the stream.
+ * schur_refine_step; stril_rel, orth: host (for A = 0, *stril_rel is 0).
+ * Synchronizes the stream.
  */
 sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int lda, const void *dQ,
                                  int ldq, double *stril_rel, double *orth);
@@ -250,13 +251,17 @@ sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int ld
  *   stril_rel, orth   host, as in schur_refine_residuals
  *   cuda_stream       the cudaStream_t to run on (NULL: legacy default stream)
  * The scratch (A Q in double-double plus partial sums, about 4 MiB) is a
- * fixed array inside the library's device image, present on every GPU that
- * loads the library until the process exits. No cudaMalloc, cudaFree or other
- * allocating routine is called. All calls on a device share that array:
- * calls whose GPU work overlaps (other streams or host threads) race and must
- * be ordered by the caller. The first call on each device looks up the
- * array's device address with that device current; make that first call
- * before any stream capture. Synchronizes cuda_stream.
+ * fixed array inside the library's device image; every GPU on which it has
+ * been loaded keeps it until the process exits. Under CUDA's default lazy
+ * module loading that memory is committed by the first call on a device:
+ * a caller whose pool allocator reserves the device should make one call on
+ * each device before the pool takes its memory (or set
+ * CUDA_MODULE_LOADING=EAGER), or that first call can fail for lack of memory.
+ * No cudaMalloc, cudaFree or other allocating routine is called. All calls on
+ * a device share that array: calls whose GPU work overlaps (other streams or
+ * host threads) race and must be ordered by the caller. Each call looks up
+ * the array's device address on the current device before launching its
+ * kernels. For A = 0, *stril_rel is 0. Synchronizes cuda_stream.
  */
 sr_status schur_refine_residuals_noalloc(int n, const void *dA, int lda, const void *dQ, int ldq,
                                          double *stril_rel, double *orth, void *cuda_stream);

@@ -47,10 +47,10 @@ _I = ctypes.c_int
 
 
 def _declare(L):
-    L.sro_alg2_f64.argtypes = [_I, _P, _I, _P, _I, _P, _P, _I, ctypes.c_double]
-    L.sro_alg2_f32.argtypes = [_I, _P, _I, _P, _I, _P, _P, _I, ctypes.c_double]
-    L.sro_alg2_c128.argtypes = [_I, _P, _I, _P, _I, _P, _P, _I, ctypes.c_double]
-    L.sro_alg2_c64.argtypes = [_I, _P, _I, _P, _I, _P, _P, _I, ctypes.c_double]
+    L.sro_alg2_f64.argtypes = [_I, _P, _I, _P, _I, _P, _P, _I, ctypes.c_double, _I]
+    L.sro_alg2_f32.argtypes = [_I, _P, _I, _P, _I, _P, _P, _I, ctypes.c_double, _I]
+    L.sro_alg2_c128.argtypes = [_I, _P, _I, _P, _I, _P, _P, _I, ctypes.c_double, _I]
+    L.sro_alg2_c64.argtypes = [_I, _P, _I, _P, _I, _P, _P, _I, ctypes.c_double, _I]
     L.sro_alg3_f64.argtypes = [_I, _P, _I, _P, _I, _P, _I, _I]
     L.sro_kron_solve.argtypes = [_I, _P, _I, _P, _I, _P, _P, _I]
     L.sro_gemm_dd.argtypes = [_I, _I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I]

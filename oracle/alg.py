@@ -65,7 +65,8 @@ def _ctype(a: np.ndarray):
 # ---------------------------------------------------------------------------
 # Triangular matrix equation stril(T L - L T) = -E  (Sec. 2.1)
 
-def alg2(T: np.ndarray, E: np.ndarray, d_hp: np.ndarray | None = None, cap: float = 0.0) -> np.ndarray:
+def alg2(T: np.ndarray, E: np.ndarray, d_hp: np.ndarray | None = None, cap: float = 0.0,
+         ncols: int | None = None) -> np.ndarray:
     """Alg. 2 in the precision of ``T`` (float32/64, complex64/128).
 
     ``d_hp`` is the diagonal of T in high precision; when given, the divisors
@@ -73,7 +74,10 @@ def alg2(T: np.ndarray, E: np.ndarray, d_hp: np.ndarray | None = None, cap: floa
     ``cap`` > 0 applies the trick of Example 4 (Sec. 3): an entry of L larger
     than ``cap`` in modulus (|l|^2 > cap^2 for complex data, in the working
     precision) is set to zero as soon as it is computed, before later entries
-    use it. Raises :class:`SolveError` on a zero divisor (Theorem 1) or a
+    use it. ``ncols`` limits the solve to the columns j < ncols of L (the
+    others are returned as zero): Alg. 2 forms column j from the columns
+    before it only, so these are the leading columns of the full solve.
+    Raises :class:`SolveError` on a zero divisor (Theorem 1) or a
     non-finite L.
     """
     n = T.shape[0]
@@ -89,7 +93,7 @@ def alg2(T: np.ndarray, E: np.ndarray, d_hp: np.ndarray | None = None, cap: floa
         dh = None if d_hp is None else np.ascontiguousarray(d_hp, dtype=np.float64)
         fn = L_.sro_alg2_f32 if dt == np.float32 else L_.sro_alg2_f64
     rc = fn(n, _lib.ptr(T), n, _lib.ptr(E), n, None if dh is None else _lib.ptr(dh),
-            _lib.ptr(L), n, float(cap))
+            _lib.ptr(L), n, float(cap), -1 if ncols is None else int(ncols))
     if rc:
         raise SolveError(rc)
     return L

@@ -49,13 +49,17 @@ typedef long double f128_t; /* IEEE binary128 on AArch64 */
 
 /* ------------------------------------------------------------------ */
 /* Alg. 2 in double. The divisor t_ii - t_jj is formed from dhp if given
- * (the high-precision diagonal), else from T. */
+ * (the high-precision diagonal), else from T. Every variant computes the
+ * columns j < ncols of L (all of them when ncols < 0 or ncols >= n - 1) and
+ * leaves the others zero: Alg. 2 forms column j from the columns before it
+ * only, so these leading columns are those of the full solve. */
 int sro_alg2_f64(int n, const double *T, int ldt, const double *E, int lde,
-                 const double *dhp, double *L, int ldl, double cap)
+                 const double *dhp, double *L, int ldl, double cap, int ncols)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) L[IDX(i, j, ldl)] = 0.0;
-    for (int j = 0; j < n - 1; ++j) {
+    const int jend = (ncols < 0 || ncols > n - 1) ? n - 1 : ncols;
+    for (int j = 0; j < jend; ++j) {
         for (int i = n - 1; i >= j + 1; --i) {
             double e = E[IDX(i, j, lde)];
             double s1 = 0.0, s2 = 0.0;
@@ -78,11 +82,12 @@ int sro_alg2_f64(int n, const double *T, int ldt, const double *E, int lde,
 /* Alg. 2 in float (the low precision of the mixed form). The divisor is formed
  * in double from dhp and then rounded to float. */
 int sro_alg2_f32(int n, const float *T, int ldt, const float *E, int lde,
-                 const double *dhp, float *L, int ldl, double cap)
+                 const double *dhp, float *L, int ldl, double cap, int ncols)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) L[IDX(i, j, ldl)] = 0.0f;
-    for (int j = 0; j < n - 1; ++j) {
+    const int jend = (ncols < 0 || ncols > n - 1) ? n - 1 : ncols;
+    for (int j = 0; j < jend; ++j) {
         for (int i = n - 1; i >= j + 1; --i) {
             float e = E[IDX(i, j, lde)];
             float s1 = 0.0f, s2 = 0.0f;
@@ -103,11 +108,12 @@ int sro_alg2_f32(int n, const float *T, int ldt, const float *E, int lde,
 
 /* Alg. 2 in complex double (interleaved re, im). */
 int sro_alg2_c128(int n, const double complex *T, int ldt, const double complex *E, int lde,
-                  const double complex *dhp, double complex *L, int ldl, double cap)
+                  const double complex *dhp, double complex *L, int ldl, double cap, int ncols)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) L[IDX(i, j, ldl)] = 0.0;
-    for (int j = 0; j < n - 1; ++j) {
+    const int jend = (ncols < 0 || ncols > n - 1) ? n - 1 : ncols;
+    for (int j = 0; j < jend; ++j) {
         for (int i = n - 1; i >= j + 1; --i) {
             double complex e = E[IDX(i, j, lde)];
             double complex s1 = 0.0, s2 = 0.0;
@@ -129,11 +135,12 @@ int sro_alg2_c128(int n, const double complex *T, int ldt, const double complex 
 
 /* Alg. 2 in complex float with divisors formed in complex double. */
 int sro_alg2_c64(int n, const float complex *T, int ldt, const float complex *E, int lde,
-                 const double complex *dhp, float complex *L, int ldl, double cap)
+                 const double complex *dhp, float complex *L, int ldl, double cap, int ncols)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) L[IDX(i, j, ldl)] = 0.0f;
-    for (int j = 0; j < n - 1; ++j) {
+    const int jend = (ncols < 0 || ncols > n - 1) ? n - 1 : ncols;
+    for (int j = 0; j < jend; ++j) {
         for (int i = n - 1; i >= j + 1; --i) {
             float complex e = E[IDX(i, j, lde)];
             float complex s1 = 0.0f, s2 = 0.0f;
@@ -191,7 +198,7 @@ static int alg3_rec(int n, const double *T, int ldt, double *E, int lde, double 
         /* Alg. 2 on the block, reading E in place. */
         double *Lb = (double *)calloc((size_t)n * (size_t)n, sizeof(double));
         if (!Lb) return SRO_NONFINITE;
-        int rc = sro_alg2_f64(n, T, ldt, E, lde, NULL, Lb, n, 0.0);
+        int rc = sro_alg2_f64(n, T, ldt, E, lde, NULL, Lb, n, 0.0, -1);
         for (int j = 0; j < n; ++j)
             for (int i = j + 1; i < n; ++i) L[IDX(i, j, ldl)] = Lb[IDX(i, j, n)];
         free(Lb);
@@ -271,13 +278,22 @@ int sro_kron_solve(int n, const double *T, int ldt, const double *E, int lde,
         for (int r = 0; r < N; ++r) M[IDX(r, c, N)] = R[IDX(ui[r], uj[r], n)];
     }
     for (int r = 0; r < N; ++r) M[IDX(r, N, N)] = -(f128_t)E[IDX(ui[r], uj[r], lde)];
-    /* Gaussian elimination with partial pivoting */
+    /* Gaussian elimination with partial pivoting. The operator is singular
+     * exactly when two diagonal entries of T coincide (Theorem 1); eliminating
+     * a singular matrix in 128-bit arithmetic leaves a pivot at the rounding
+     * level of the elimination rather than an exact zero, so a pivot below
+     * N * 2^-112 * max|M| counts as zero. */
+    f128_t mmax = 0;
+    for (int c = 0; c < N; ++c)
+        for (int r = 0; r < N; ++r)
+            if (qabs(M[IDX(r, c, N)]) > mmax) mmax = qabs(M[IDX(r, c, N)]);
+    const f128_t ptol = (f128_t)N * mmax * (f128_t)ldexp(1.0, -112);
     int rc = SRO_OK;
     for (int c = 0; c < N; ++c) {
         int p = c;
         for (int r = c + 1; r < N; ++r)
             if (qabs(M[IDX(r, c, N)]) > qabs(M[IDX(p, c, N)])) p = r;
-        if (M[IDX(p, c, N)] == 0) { rc = SRO_NONDISTINCT; break; }
+        if (qabs(M[IDX(p, c, N)]) <= ptol) { rc = SRO_NONDISTINCT; break; }
         if (p != c)
             for (int k = c; k <= N; ++k) {
                 f128_t t = M[IDX(c, k, N)];

@@ -1634,7 +1634,8 @@ sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int ld
         SR_TRY(sumsq<double>(h, n, A, lda, 0, 6));
     }
     SR_TRY(read_back(h));
-    *stril_rel = sqrt(h->hbuf[4]) / sqrt(h->hbuf[6]);
+    // A = 0 has Q^H A Q = 0: its relative residual is 0, not 0/0
+    *stril_rel = h->hbuf[6] > 0.0 ? sqrt(h->hbuf[4]) / sqrt(h->hbuf[6]) : 0.0;
     *orth = sqrt(h->hbuf[5]);
     return SR_OK;
 }

@@ -22,11 +22,19 @@
 // must order them.
 //
 // Host code must not pass the array's name to a kernel: on the host it is
-// only a stand-in symbol, not a device address. The device address is looked
-// up once per device with cudaGetSymbolAddress, by the first call made with
-// that device current; that first call should come before any stream capture.
+// only a stand-in symbol, not a device address. Every call looks up the
+// array's device address on the current device with cudaGetSymbolAddress
+// before it launches anything: the lookup is cheap, and an address cached
+// across calls would go stale when the context is torn down and created again
+// (cudaDeviceReset, or a released primary context), after which the module is
+// loaded again, possibly at another address.
+//
+// Under CUDA's default lazy module loading, the array's device memory is
+// committed when the first call on a device loads this file's module. A
+// caller whose pool allocator reserves the whole device should therefore make
+// one call on each device before the pool takes its memory (or run with
+// CUDA_MODULE_LOADING=EAGER), or that first call can fail for lack of memory.
 #include <math.h>
-#include <mutex>
 
 #include "common.cuh"
 #include "kernels_misc.cuh"
@@ -37,7 +45,6 @@ constexpr int kMaxN = 512;
 constexpr size_t kNN = (size_t)kMaxN * (size_t)kMaxN;
 constexpr int kTiles = ((kMaxN + 15) / 16) * ((kMaxN + 15) / 16);
 constexpr size_t kScratchDoubles = 2 * kNN + kTiles + 8;
-constexpr int kMaxDevices = 64;
 
 }  // namespace
 
@@ -53,23 +60,14 @@ static __global__ void __launch_bounds__(256) noalloc_sum_kernel(const double *_
     if (threadIdx.x == 0) *out = s;
 }
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device, looked up anew
+// on every call (see the header comment for why it is not cached).
 static cudaError_t scratch_address(double **out)
 {
-    static std::mutex mu;
-    static double *addr[kMaxDevices] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_residual_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_residual_scratch);
-        if (e != cudaSuccess) return e;
-        addr[dev] = (double *)p;
-    }
-    *out = addr[dev];
+    *out = (double *)p;
     return cudaSuccess;
 }
 
@@ -109,7 +107,8 @@ extern "C" sr_status schur_refine_residuals_noalloc(int n, const void *dA, int l
     double h[3] = {0.0, 0.0, 0.0};
     SR_CUDA_TRY(cudaMemcpyAsync(h, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     SR_CUDA_TRY(cudaStreamSynchronize(st));
-    *stril_rel = sqrt(h[0]) / sqrt(h[2]);
+    // A = 0 has Q^T A Q = 0: its relative residual is 0, not 0/0
+    *stril_rel = h[2] > 0.0 ? sqrt(h[0]) / sqrt(h[2]) : 0.0;
     *orth = sqrt(h[1]);
     return SR_OK;
 }

@@ -118,3 +118,80 @@ def test_alg3_matches_kronecker(rng):
     hi, _ = oracle.kron_solve(T, E)
     L3 = oracle.alg3(T, E, nmin=2)
     assert np.max(np.abs(L3 - hi)) <= 1e-13 * np.max(np.abs(hi))
+
+
+# ---------------------------------------------------------------------------
+# The divisor reading of the low-precision solves: t_ii - t_jj is formed from
+# the high-precision diagonal and rounded once to the low precision. Two
+# diagonal entries 1e-9 apart near 1 are equal once rounded to FP32, so a
+# divisor formed from the FP32 (or complex64) T would be zero.
+
+def _alg2_f32_py(T32, E32, d):
+    """Alg. 2 in FP32, each operation rounded by numpy's float32 scalars, with
+    the divisor formed in float64 from ``d`` and rounded once to float32."""
+    f = np.float32
+    n = T32.shape[0]
+    L = np.zeros((n, n), dtype=np.float32)
+    for j in range(n - 1):
+        for i in range(n - 1, j, -1):
+            s1 = f(0.0)
+            for k in range(i + 1, n):
+                s1 = f(s1 + f(T32[i, k] * L[k, j]))
+            s2 = f(0.0)
+            for k in range(j):
+                s2 = f(s2 + f(L[i, k] * T32[k, j]))
+            e = f(f(E32[i, j] + s1) - s2)
+            L[i, j] = f(-e / f(float(d[i]) - float(d[j])))
+    return L
+
+
+def _near_equal_pair(n, seed):
+    rng = np.random.default_rng(seed)
+    d = np.sort(rng.uniform(0.0, 3.0, n))
+    d[n // 2] = 1.0
+    d[n // 2 + 1] = 1.0 + 1e-9
+    assert np.float32(d[n // 2]) == np.float32(d[n // 2 + 1])
+    T = np.triu(rng.standard_normal((n, n)) * 0.1, 1) + np.diag(d)
+    E = np.tril(rng.standard_normal((n, n)) * 1e-12, -1)
+    return T, E, d
+
+
+def test_alg2_float32_divisor_formed_in_high_precision():
+    T, E, d = _near_equal_pair(6, 11)
+    T32, E32 = T.astype(np.float32), E.astype(np.float32)
+    L = oracle.alg2(T32, E32, d)
+    assert L.dtype == np.float32 and np.all(np.isfinite(L))
+    # bit for bit the FP32 operations with the divisor rounded once from float64
+    assert np.array_equal(L, _alg2_f32_py(T32, E32, d))
+    i = 6 // 2 + 1
+    assert L[i, i - 1] != 0.0
+    # the same solve with divisors formed from the FP32 diagonal hits a zero divisor
+    with pytest.raises(oracle.SolveError) as ei:
+        oracle.alg2(T32, E32)
+    assert ei.value.code == oracle.NONDISTINCT
+
+
+def test_alg2_complex64_divisor_formed_in_high_precision():
+    # n = 2: l_21 = -e_21 / fl32(t_22 - t_11) with a real divisor of 1e-9, so
+    # the complex division reduces to the two real ones
+    d = np.array([1.0 + 0.25j, 1.0 + 1e-9 + 0.25j])
+    assert np.complex64(d[0]) == np.complex64(d[1])
+    T = np.array([[d[0], 0.5 - 0.125j], [0.0, d[1]]]).astype(np.complex64)
+    E = np.array([[0.0, 0.0], [3e-12 - 2e-12j, 0.0]]).astype(np.complex64)
+    L = oracle.alg2(T, E, d)
+    den = np.float32(d[1].real - d[0].real)
+    assert L.dtype == np.complex64
+    assert L[1, 0].real == -E[1, 0].real / den and L[1, 0].imag == -E[1, 0].imag / den
+    with pytest.raises(oracle.SolveError) as ei:
+        oracle.alg2(T, E)
+    assert ei.value.code == oracle.NONDISTINCT
+    # a larger case: finite, and equal to the complex128 solve to FP32 accuracy
+    Tr, Er, dr = _near_equal_pair(8, 12)
+    Tc = (Tr + 0.5j * np.triu(Tr, 1)).astype(np.complex128)
+    dc = dr + 0.0j
+    np.fill_diagonal(Tc, dc)
+    Ec = (Er - 0.5j * Er).astype(np.complex128)
+    L64 = oracle.alg2(Tc.astype(np.complex64), Ec.astype(np.complex64), dc)
+    L128 = oracle.alg2(Tc, Ec, dc)
+    assert np.all(np.isfinite(L64))
+    assert np.max(np.abs(L64 - L128)) <= 1e-5 * np.max(np.abs(L128))
