@@ -56,7 +56,8 @@ typedef enum {
 } sr_status;
 
 /* element type of A and Q. SR_COMPLEX (complex128 data, complex64 low
-   precision) is built for hp_gemm = SR_HP_OZAKI_BF16 with lp = SR_LP_FP32 and
+   precision) is built for the emulated products (hp_gemm SR_HP_OZAKI_BF16 or
+   SR_HP_OZAKI_CRT) with lp = SR_LP_FP32 and
    orders up to 8192; other combinations give SR_ERR_UNSUPPORTED at create. */
 enum { SR_REAL = 0, SR_COMPLEX = 1 };
 /* working high precision. SR_TARGET_DD (double-double, Sec. 3's higher
@@ -70,8 +71,15 @@ enum { SR_TARGET_FP64 = 0, SR_TARGET_DD = 1 };
    multiplications"; the paper uses the Ozaki scheme, Sec. 3) */
 enum {
     SR_HP_FP64 = 0,       /* native FP64 arithmetic */
-    SR_HP_OZAKI_BF16 = 1  /* FP64 products emulated by splitting into bf16
+    SR_HP_OZAKI_BF16 = 1, /* FP64 products emulated by splitting into bf16
                              slices multiplied exactly on tensor cores */
+    SR_HP_OZAKI_CRT = 2   /* FP64 (double-double) products emulated by
+                             residues: each operand vector is scaled to
+                             integers of t bits, the integer product is formed
+                             exactly modulo N pairwise coprime moduli <= 256
+                             (one bf16 tensor-core product per modulus) and
+                             rebuilt by the Chinese remainder theorem; N = 16
+                             (32 for SR_TARGET_DD) by default */
 };
 /* low precision of the solve and of the products YW, W^2, W^3 (Alg. 4) */
 enum { SR_LP_FP32 = 0, SR_LP_FP64 = 1 };
@@ -89,7 +97,13 @@ typedef struct {
     int max_iter;     /* passes of the REPEAT loop; <= 0 selects 10 */
     int ozaki_slices; /* bf16 slices per operand of the emulated
                          high-precision products; <= 0 selects the library
-                         default (7; 14 for SR_TARGET_DD); at most 7 (14) */
+                         default (7; 14 for SR_TARGET_DD); at most 7 (14).
+                         SR_HP_OZAKI_CRT: the number of moduli N (default 16;
+                         32 for SR_TARGET_DD; at most 16 (32)); the operands
+                         then carry t bits, the largest t with
+                         K 2^(2t) < M / 2 for inner length K and M the
+                         product of the moduli (t = 56 for N = 16 and
+                         K <= 4096) */
     double tol;       /* stop when ||stril(T^)||_F / ||A||_F <= tol and the
                          last ||Q^H Q - I||_F <= sqrt(tol); <= 0 selects
                          1e-14 * sqrt(n) (1e-28 * n for SR_TARGET_DD) */
@@ -310,6 +324,28 @@ sr_status schur_refine_selftest_wait_timeout(schur_refine_t h);
  * Returns SR_ERR_INVALID_ARG for n < 1 or n > 32768 or a NULL count.
  */
 sr_status schur_refine_solve_plan(int n, unsigned long long *tasks, long long cap, long long *count);
+
+/*
+ * The constants of the residue form of the emulated products (hp_gemm =
+ * SR_HP_OZAKI_CRT; the paper computes its high-precision products with the
+ * Ozaki scheme, Sec. 3, and this is the Chinese-remainder variant of that
+ * scheme). Host code only; no device is used.
+ *   N        number of moduli, 1..32
+ *   limbs    4 (FP64 results, needs M < 2^128) or 8 (double-double results)
+ *   K        inner length of the product
+ *   moduli   host, N entries: the moduli, the N largest pairwise coprime
+ *            integers <= 256 taken greedily from 256 down
+ *   weights  host, N * limbs entries: weight l is M_l (M_l^-1 mod m_l) 2^sigma
+ *            (M = prod m_l, M_l = M / m_l) as little-endian 32-bit limbs
+ *   M        host, limbs entries: M 2^sigma, its top bit at 32 limbs - 1
+ *   sigma    host: the scaling exponent
+ *   t        host: bits of the integer operands, the largest t with
+ *            K 2^(2t) < M / 2
+ * Returns SR_ERR_INVALID_ARG for N or limbs out of range, M >= 2^(32 limbs),
+ * K < 1 or a NULL pointer.
+ */
+sr_status schur_refine_crt_info(int N, int limbs, long long K, int *moduli, unsigned *weights, unsigned *M,
+                                int *sigma, int *t);
 
 /*
  * One high-precision product with the handle's engine, as used for A Q and

@@ -19,7 +19,7 @@ SR_OK, SR_ERR_INVALID_ARG, SR_ERR_NONDISTINCT, SR_ERR_NONFINITE = 0, 1, 2, 3
 SR_ERR_NOT_CONVERGED, SR_ERR_TIMEOUT, SR_ERR_CUDA, SR_ERR_OOM, SR_ERR_UNSUPPORTED = 4, 5, 6, 7, 8
 SR_REAL, SR_COMPLEX = 0, 1
 SR_TARGET_FP64, SR_TARGET_DD = 0, 1
-SR_HP_FP64, SR_HP_OZAKI_BF16 = 0, 1
+SR_HP_FP64, SR_HP_OZAKI_BF16, SR_HP_OZAKI_CRT = 0, 1, 2
 SR_LP_FP32, SR_LP_FP64 = 0, 1
 SR_QHAT_FP32, SR_QHAT_FP64 = 0, 1
 PROF_KINDS = 8
@@ -31,7 +31,7 @@ EXPORTS = [
     "schur_refine_batched", "schur_refine_residuals", "schur_refine_trisolve",
     "schur_refine_gemm", "schur_refine_get_profile", "schur_refine_reset_profile",
     "schur_refine_destroy", "schur_refine_status_string", "schur_refine_residuals_noalloc",
-    "schur_refine_selftest_wait_timeout", "schur_refine_solve_plan",
+    "schur_refine_selftest_wait_timeout", "schur_refine_solve_plan", "schur_refine_crt_info",
 ]
 
 
@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
         L.schur_refine_solve_plan.argtypes = [I, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_longlong,
                                               ctypes.POINTER(ctypes.c_longlong)]
         L.schur_refine_gemm.argtypes = [P, I, I, I, I, P, I, P, I, P, I]
+        L.schur_refine_crt_info.argtypes = [I, I, ctypes.c_longlong, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_uint),
+                                            ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(I), ctypes.POINTER(I)]
         L.schur_refine_get_profile.argtypes = [P, ctypes.POINTER(sr_profile)]
         L.schur_refine_reset_profile.argtypes = [P]
         L.schur_refine_destroy.argtypes = [P]
@@ -101,7 +103,7 @@ def lib() -> ctypes.CDLL:
                   "schur_refine_residuals", "schur_refine_trisolve", "schur_refine_gemm",
                   "schur_refine_get_profile", "schur_refine_reset_profile",
                   "schur_refine_residuals_noalloc", "schur_refine_selftest_wait_timeout",
-                  "schur_refine_solve_plan"):
+                  "schur_refine_solve_plan", "schur_refine_crt_info"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -232,6 +234,24 @@ def schur_refine_solve_plan(n: int):
     if s != 0:
         raise SchurRefineError(s, "schur_refine_solve_plan")
     return out
+
+
+def schur_refine_crt_info(N: int, limbs: int, K: int):
+    """(status, moduli, weights as Python ints, M as a Python int, sigma, t) of the
+    residue form's table (host code; no device)."""
+    mod = (ctypes.c_int * max(N, 1))()
+    w = (ctypes.c_uint * max(N * limbs, 1))()
+    M = (ctypes.c_uint * max(limbs, 1))()
+    sg, t = ctypes.c_int(0), ctypes.c_int(0)
+    s = lib().schur_refine_crt_info(int(N), int(limbs), int(K), mod, w, M, ctypes.byref(sg), ctypes.byref(t))
+    if s != 0:
+        return s, None, None, None, None, None
+
+    def big(limbs_):
+        return sum(int(x) << (32 * k) for k, x in enumerate(limbs_))
+
+    weights = [big(w[l * limbs:(l + 1) * limbs]) for l in range(N)]
+    return s, list(mod[:N]), weights, big(M[:limbs]), sg.value, t.value
 
 
 def schur_refine_selftest_wait_timeout(h):

@@ -168,27 +168,45 @@ size_t lp_size(const sr_options &o) { return (o.lp == SR_LP_FP32 ? sizeof(float)
 // high-precision element: FP64, complex128, or a double-double pair (two planes)
 size_t hp_size(const sr_options &o) { return sizeof(double) * (is_cplx(o) || o.target == SR_TARGET_DD ? 2 : 1); }
 
+// high-precision products emulated on the tensor cores (digits or residues)
+bool is_emulated(const sr_options &o) { return o.hp_gemm == SR_HP_OZAKI_BF16 || o.hp_gemm == SR_HP_OZAKI_CRT; }
+
+// bf16 digits (7; 14 for double-double) or residues modulo 16 (32) moduli per operand
+int oz_count(const sr_options &o)
+{
+    if (o.ozaki_slices > 0) return o.ozaki_slices;
+    const bool dd = o.target == SR_TARGET_DD;
+    if (o.hp_gemm == SR_HP_OZAKI_CRT) return dd ? sr::kCrtDefaultModuliDD : sr::kCrtDefaultModuli;
+    return dd ? sr::kOzakiDefaultSlicesDD : sr::kOzakiDefaultSlices;
+}
+
 sr_status check_opts(const sr_options &o)
 {
     if (o.dtype != SR_REAL && o.dtype != SR_COMPLEX) return SR_ERR_INVALID_ARG;
     if (o.target != SR_TARGET_FP64 && o.target != SR_TARGET_DD) return SR_ERR_INVALID_ARG;
-    if (o.hp_gemm != SR_HP_FP64 && o.hp_gemm != SR_HP_OZAKI_BF16) return SR_ERR_INVALID_ARG;
+    if (o.hp_gemm != SR_HP_FP64 && o.hp_gemm != SR_HP_OZAKI_BF16 && o.hp_gemm != SR_HP_OZAKI_CRT)
+        return SR_ERR_INVALID_ARG;
     if (o.lp != SR_LP_FP32 && o.lp != SR_LP_FP64) return SR_ERR_INVALID_ARG;
     if (o.qhat_type != SR_QHAT_FP32 && o.qhat_type != SR_QHAT_FP64) return SR_ERR_INVALID_ARG;
     if ((o.batch_mode != 0 && o.batch_mode != 1) || (o.tune != 0 && o.tune != 1) || (o.graph != 0 && o.graph != 1) ||
         o.solve_mode < 0 || o.solve_mode > 2 || (o.symmetric != 0 && o.symmetric != 1) || !(o.l_cap >= 0.0) ||
         std::isinf(o.l_cap))
         return SR_ERR_INVALID_ARG;
-    if (o.ozaki_slices > (o.target == SR_TARGET_DD ? sr::kOzakiMaxSlicesDD : sr::kOzakiMaxSlices))
+    if (o.hp_gemm == SR_HP_OZAKI_CRT) {
+        // FP64 results: M < 2^128 holds for at most 16 moduli; double-double: 32
+        if (o.ozaki_slices > (o.target == SR_TARGET_DD ? sr::kCrtMaxModuli : sr::kCrtDefaultModuli))
+            return SR_ERR_INVALID_ARG;
+    } else if (o.ozaki_slices > (o.target == SR_TARGET_DD ? sr::kOzakiMaxSlicesDD : sr::kOzakiMaxSlices)) {
         return SR_ERR_INVALID_ARG;
+    }
     // double-double target: real data, FP64 correction path, FP64 start
     if (o.target == SR_TARGET_DD && (o.dtype != SR_REAL || o.lp != SR_LP_FP64 || o.qhat_type != SR_QHAT_FP64))
         return SR_ERR_UNSUPPORTED;
     // complex data: the emulated products with the complex64 correction path
-    if (o.dtype == SR_COMPLEX && (o.hp_gemm != SR_HP_OZAKI_BF16 || o.lp != SR_LP_FP32)) return SR_ERR_UNSUPPORTED;
+    if (o.dtype == SR_COMPLEX && (!is_emulated(o) || o.lp != SR_LP_FP32)) return SR_ERR_UNSUPPORTED;
     // Sec. 2.5 is stated for real symmetric A; the double-double target keeps the general form
     if (o.symmetric && (o.dtype != SR_REAL || o.target != SR_TARGET_FP64)) return SR_ERR_UNSUPPORTED;
-    if (o.hp_gemm == SR_HP_OZAKI_BF16 && !sr::kOzakiBuilt) return SR_ERR_UNSUPPORTED;
+    if (is_emulated(o) && !sr::kOzakiBuilt) return SR_ERR_UNSUPPORTED;
     return SR_OK;
 }
 
@@ -246,9 +264,9 @@ sr_status hp_gemm(schur_refine_ctx *h, bool transA, int m, int n, int k, const d
 {
     double *part = slot >= 0 ? h->partial : nullptr;
     int blocks = 0;
-    if (h->opt.hp_gemm == SR_HP_OZAKI_BF16) {
+    if (is_emulated(h->opt)) {
         SR_TRY(sr::ozaki_gemm(h, h->st, h->oz, transA, m, n, k, A, lda, B, ldb, ep, part, &blocks,
-                              h->opt.ozaki_slices, h->dflags));
+                              oz_count(h->opt), h->dflags));
     } else {
         SrPhase ph(h, SR_PROF_HP_GEMM, 2LL * m * n * k, 8LL * ((long long)m * k + (long long)k * n + (long long)m * n), 1);
         using sr::LoadN;
@@ -458,8 +476,8 @@ sr_status update(schur_refine_ctx *h, int n, const double *Q, int ldq, double *Q
 // The same code serves real (C = false) and complex (C = true) data; the
 // types and epilogues come from OzT<C>.
 
-bool oz_pass(const schur_refine_ctx *h) { return h->opt.hp_gemm == SR_HP_OZAKI_BF16 && h->opt.lp == SR_LP_FP32; }
-int oz_s(const schur_refine_ctx *h) { return h->opt.ozaki_slices > 0 ? h->opt.ozaki_slices : sr::kOzakiDefaultSlices; }
+bool oz_pass(const schur_refine_ctx *h) { return is_emulated(h->opt) && h->opt.lp == SR_LP_FP32; }
+int oz_s(const schur_refine_ctx *h) { return oz_count(h->opt); }
 
 template <bool C> struct OzT;
 template <> struct OzT<false> {
@@ -1017,7 +1035,7 @@ struct DdMat {
 };
 
 bool is_dd(const sr_options &o) { return o.target == SR_TARGET_DD; }
-int oz_s_dd(const schur_refine_ctx *h) { return h->opt.ozaki_slices > 0 ? h->opt.ozaki_slices : sr::kOzakiDefaultSlicesDD; }
+int oz_s_dd(const schur_refine_ctx *h) { return oz_count(h->opt); }
 
 DdMat dd_caller(const void *p, int ld, int n)
 {
@@ -1400,7 +1418,7 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     SR_ALLOC(h->diag, (size_t)n_max * hps);
     SR_ALLOC(h->TE, nn * lps);
     // low-precision products of the native path
-    const bool native_lp = !(o.hp_gemm == SR_HP_OZAKI_BF16 && o.lp == SR_LP_FP32);
+    const bool native_lp = !(is_emulated(o) && o.lp == SR_LP_FP32);
     if (native_lp) {
         SR_ALLOC(h->W2, nn * lps);
         SR_ALLOC(h->YW, nn * lps);
@@ -1435,14 +1453,13 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     const bool dd = o.target == SR_TARGET_DD;
     if (e == cudaSuccess) h->diag_lo = dd ? h->diag + n_max : nullptr;
     if (e == cudaSuccess && dd) e = cudaMalloc((void **)&h->Wd, nn * sizeof(double));
-    if (e == cudaSuccess && o.hp_gemm == SR_HP_OZAKI_BF16) {
+    if (e == cudaSuccess && is_emulated(o)) {
         // the double-double product keeps 14 levels below 2^31: K up to 8192
         if (n_max > (dd ? 8192 : sr::ozaki_k_limit(is_cplx(o)))) {
             schur_refine_destroy(h);
             return SR_ERR_UNSUPPORTED;
         }
-        const int shp = o.ozaki_slices > 0 ? o.ozaki_slices
-                                           : (dd ? sr::kOzakiDefaultSlicesDD : sr::kOzakiDefaultSlices);
+        const int shp = oz_count(o);
         const bool lp_oz = o.lp == SR_LP_FP32;
         int caps[sr::kOzakiSlots] = {shp, shp, shp, shp, 0, 0, 0, 0};
         if (dd) {
@@ -1458,7 +1475,14 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
             if (e == cudaSuccess && o.full_sigma) e = cudaMalloc((void **)&h->W2Yd, nn * hps);
             if (e == cudaSuccess && o.full_sigma) e = cudaMalloc((void **)&h->W2YWd, nn * hps);
         }
-        if (e == cudaSuccess) e = sr::ozaki_alloc(h->oz, n_max, caps, is_cplx(o));
+        // residue form: the four slots of the high-precision products (rows of A,
+        // columns of Q, columns of A Q and of Delta, rows of Q) hold residues
+        const bool crt = o.hp_gemm == SR_HP_OZAKI_CRT;
+        const unsigned crt_mask = crt ? ((1u << sr::OZS_ROWS) | (1u << sr::OZS_COLS) | (1u << sr::OZS_X) |
+                                         (1u << sr::OZS_QROWS))
+                                      : 0u;
+        if (e == cudaSuccess)
+            e = sr::ozaki_alloc(h->oz, n_max, caps, is_cplx(o), crt ? shp : 0, crt_mask, dd ? 8 : 4);
         if (e == cudaSuccess) e = cudaMalloc((void **)&h->partial2, h->npartial * sizeof(double));
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->gram_st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gev0, cudaEventDisableTiming);
@@ -1481,7 +1505,7 @@ sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, vo
 {
     if (!h || !dA || !dQ || n < 1 || n > h->nmax || lda < n || ldq < n) return SR_ERR_INVALID_ARG;
     if (is_dd(h->opt)) {
-        if (h->opt.hp_gemm == SR_HP_OZAKI_BF16) return run_step_dd<true>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
+        if (is_emulated(h->opt)) return run_step_dd<true>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
         return run_step_dd<false>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
     }
     if (is_cplx(h->opt)) return run_step<float, true>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
@@ -1686,7 +1710,7 @@ sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, c
     if (is_dd(h->opt)) {
         const DdMat A = dd_caller(dA, lda, transA ? m : k), B = dd_caller(dB, ldb, n), C = dd_caller(dC, ldc, n);
         const sr::EpStoreDD ep{C.hi, C.lo, C.ld};
-        if (h->opt.hp_gemm == SR_HP_OZAKI_BF16) {
+        if (is_emulated(h->opt)) {
             const int s = oz_s_dd(h);
             SR_TRY(sr::ozaki_split_dd(h, h->st, h->oz, sr::OZS_ROWS, m, k, A.hi, A.lo, lda,
                                       transA ? sr::OZ_COLS : sr::OZ_ROWS, s));
@@ -1699,7 +1723,7 @@ sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, c
         }
     } else if (is_cplx(h->opt))
         SR_TRY(sr::ozaki_gemm(h, h->st, h->oz, transA != 0, m, n, k, dA, lda, dB, ldb, sr::EpStoreC{(cd *)dC, ldc},
-                              nullptr, nullptr, h->opt.ozaki_slices, h->dflags));
+                              nullptr, nullptr, oz_count(h->opt), h->dflags));
     else
         SR_TRY(hp_gemm(h, transA != 0, m, n, k, (const double *)dA, lda, (const double *)dB, ldb,
                        sr::EpStore{(double *)dC, ldc}, -1));

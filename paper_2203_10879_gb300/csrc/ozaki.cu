@@ -24,6 +24,8 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
+#include <numeric>
 
 #include "ozaki.cuh"
 
@@ -183,8 +185,15 @@ struct MmaArgs {
     int nact;         // tiles formed (all, or those on and above the diagonal)
     int groups;
     int nitems;       // nact * groups (or the length of items)
-    int lvl[kOzakiMaxSlicesDD + 1];
+    int lvl[kCrtMaxModuli + 1];
     const MmaItem *items;   // explicit work items (grouped products), else null
+    // residue form: level l is the single product of the residues modulo mods[l]
+    // (row-side and column-side slot plane l), drained into an exact int32 sum
+    // and stored reduced modulo mods[l] as a byte plane
+    int crt;
+    int mods[kCrtMaxModuli];
+    unsigned long long inv40[kCrtMaxModuli];
+    unsigned off28[kCrtMaxModuli];
 };
 
 // what one work item needs: digit rows, K-chunks, levels, where its planes go
@@ -313,8 +322,8 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             for (int item = blockIdx.x; item < args.nitems && ok; item += gridDim.x) {
                 const ItemView v = get_item<ITEMS>(args, item);
                 for (int l = v.lb; l < v.le && ok; ++l)
-                    for (int p = 0; p <= l && ok; ++p) {
-                        const int q = l - p;
+                    for (int p = args.crt ? l : 0; p <= l && ok; ++p) {
+                        const int q = args.crt ? l : l - p;
                         for (int c = 0; c < v.nch && ok; ++c)
                             for (int kb = 0; kb < (ITEMS && c == v.nch - 1 ? v.kbl : KB_PER_CHUNK); ++kb) {
                                 if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1, abort)) { ok = false; break; }
@@ -351,7 +360,7 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 // then the same pair by pair)
                 const int ppa = ITEMS ? v.ppa : 1;
                 for (int l = v.lb; l < v.le && ok; ++l)
-                    for (int p0 = 0; p0 <= l && ok; p0 += ppa)
+                    for (int p0 = args.crt ? l : 0; p0 <= l && ok; p0 += ppa)
                         for (int c = 0; c < v.nch && ok; ++c) {
                             const uint32_t idesc = chunk_idesc(args, c, v.im);
                             const int b = t & 1;
@@ -397,7 +406,7 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 #pragma unroll
                 for (int c = 0; c < BN / 2; ++c) acc[c] = 0u;
                 uint32_t count = 0;
-                for (int p0 = 0; p0 <= l && ok; p0 += (ITEMS ? v.ppa : 1))
+                for (int p0 = args.crt ? l : 0; p0 <= l && ok; p0 += (ITEMS ? v.ppa : 1))
                     for (int c = 0; c < v.nch; ++c) {
                         const int b = t & 1;
                         const uint32_t aph = (t >> 1) & 1;
@@ -424,7 +433,29 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     }
                 if (!ok) break;
                 const uint32_t bias = count * 0x4B400000u;
-                if (!ITEMS || jl < v.clim) {
+                if (!ITEMS && args.crt) {
+                    // the exact sum (|sum| <= 64 chunks * 2^22 = 2^28) reduced modulo m into bytes
+                    const uint32_t m = (uint32_t)args.mods[l], off = args.off28[l];
+                    const unsigned long long inv = args.inv40[l];
+                    uint8_t *dst8 = reinterpret_cast<uint8_t *>(args.planes) + (size_t)l * args.pstride +
+                                    (size_t)v.poff + (size_t)jl * v.ldp + (size_t)(half * (BN / 2));
+#pragma unroll
+                    for (int c = 0; c < BN / 2; c += 16) {
+                        uint32_t wd[4];
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            uint32_t pk = 0;
+#pragma unroll
+                            for (int x = 0; x < 4; ++x) {
+                                const uint32_t u = (acc[c + 4 * b + x] - bias) + off;   // >= 0, < 2^30
+                                const uint32_t qq = (uint32_t)(((unsigned long long)u * inv) >> 40);
+                                pk |= (u - qq * m) << (8 * x);
+                            }
+                            wd[b] = pk;
+                        }
+                        *reinterpret_cast<uint4 *>(dst8 + c) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                    }
+                } else if (!ITEMS || jl < v.clim) {
                     int32_t *dst = args.planes + (size_t)l * args.pstride + (size_t)v.poff + (size_t)jl * v.ldp +
                                    (size_t)(half * (BN / 2));
                     const int rmax = v.rlim - half * (BN / 2);   // region rows come in multiples of 4
@@ -713,6 +744,141 @@ ozaki_digits_dd_kernel(int R, int K, int Kp, const double *__restrict__ Xh, cons
     }
 }
 
+// ---- residue form: X(r, kk) -> N bf16 residue matrices [l][r][kk] -----------------
+// Each entry becomes X = round(x 2^(t - e)) (|X| <= 2^t; e the vector's scale
+// exponent as for the digits) and is written as its symmetric residues modulo
+// the table's moduli, in [-128, 128]. |X| is cut into 16-bit pieces u_k, and
+// X mod m = (sum_k u_k (2^(16 k) mod m)) mod m with a sum below 2^27, reduced
+// by one multiply with ceil(2^40 / m) (exact for sums below 2^31).
+struct CrtSplitSm {
+    int m[kCrtMaxModuli];
+    unsigned long long inv40[kCrtMaxModuli];
+    unsigned pw16[8][kCrtMaxModuli];
+};
+
+__device__ __forceinline__ void crt_split_table(CrtSplitSm &sm, const CrtTable *__restrict__ tab, int N, int pieces)
+{
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+        sm.m[x] = tab->m[x];
+        sm.inv40[x] = tab->inv40[x];
+        for (int k = 0; k < pieces; ++k) sm.pw16[k][x] = tab->pw16[k][x];
+    }
+}
+
+// the residues of the integer with sign neg and 16-bit pieces u[0..P) into
+// planes o[l * pstride]
+template <int P>
+__device__ __forceinline__ void write_residues(const uint32_t (&u)[P], bool neg, const CrtSplitSm &sm, int N,
+                                               __nv_bfloat16 *__restrict__ o, size_t pstride)
+{
+#pragma unroll 4
+    for (int l = 0; l < N; ++l) {
+        const uint32_t m = (uint32_t)sm.m[l];
+        uint32_t v = u[0];
+#pragma unroll
+        for (int k = 1; k < P; ++k) v += u[k] * sm.pw16[k][l];
+        const uint32_t q = (uint32_t)(((unsigned long long)v * sm.inv40[l]) >> 40);
+        int r = (int)(v - q * m);
+        if (neg && r) r = (int)m - r;
+        if (2 * r > (int)m) r -= (int)m;
+        o[(size_t)l * pstride] = __int2bfloat16_rn(r);
+    }
+}
+
+template <typename Tin, int LAYOUT>
+__global__ void __launch_bounds__(256, 4)
+ozaki_residues_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, int ld, int t, int N, int Pmax,
+                      int Kmax, const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
+                      int *__restrict__ exps, const CrtTable *__restrict__ tab)
+{
+    __shared__ double tile[32][33];
+    __shared__ int sexp[32];
+    __shared__ CrtSplitSm sm;
+    const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * DIGIT_KT;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (threadIdx.x < 32) {
+        const int r = r0 + threadIdx.x;
+        const int e = (r < R) ? split_exponent(vmax[r]) : 0;
+        sexp[threadIdx.x] = e;
+        if (blockIdx.y == 0) exps[r] = e;
+    }
+    crt_split_table(sm, tab, N, 4);
+    const size_t pstride = (size_t)Pmax * Kmax;
+    for (int k0 = kbeg; k0 < kbeg + DIGIT_KT && k0 < Kp; k0 += 32) {
+        __syncthreads();
+        split_load_tile<Tin, LAYOUT>(tile, X, ld, R, K, Kh, r0, k0);
+        __syncthreads();
+#pragma unroll 1
+        for (int w = 0; w < 4; ++w) {
+            const int v = ty + 8 * w;
+            const int r = r0 + v;
+            const int kk = k0 + tx;
+            const double x = tile[v][tx];   // zero outside the matrix
+            const int e = sexp[v];
+            unsigned long long mag = 0;
+            bool neg = false;
+            if (e != kOzakiExpNonfinite && r < R) {
+                const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+                const int eb = (int)((bits >> 52) & 0x7ff);
+                unsigned long long mant = bits & 0xfffffffffffffull;
+                int ex;
+                if (eb == 0) ex = -1074; else { mant |= 1ull << 52; ex = eb - 1075; }
+                const int sh = ex + t - e;                // x 2^(t-e) = mant 2^sh, sh < t - 52
+                if (mant == 0) mag = 0;
+                else if (sh >= 0) mag = mant << sh;
+                else if (-sh >= 64) mag = 0;
+                else mag = (mant + (1ull << (-sh - 1))) >> (-sh);
+                neg = (bits >> 63) != 0;
+            }
+            const uint32_t u[4] = {(uint32_t)(mag & 0xffff), (uint32_t)((mag >> 16) & 0xffff),
+                                   (uint32_t)((mag >> 32) & 0xffff), (uint32_t)(mag >> 48)};
+            write_residues<4>(u, neg, sm, N, out + (size_t)r * Kmax + (size_t)kk, pstride);
+        }
+    }
+}
+
+template <int LAYOUT>
+__global__ void __launch_bounds__(256, 2)
+ozaki_residues_dd_kernel(int R, int K, int Kp, const double *__restrict__ Xh, const double *__restrict__ Xl, int ld,
+                         int t, int N, int Pmax, int Kmax, const unsigned long long *__restrict__ vmax,
+                         __nv_bfloat16 *__restrict__ out, int *__restrict__ exps, const CrtTable *__restrict__ tab)
+{
+    __shared__ double th[32][33], tl[32][33];
+    __shared__ int sexp[32];
+    __shared__ CrtSplitSm sm;
+    const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * DIGIT_KT;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (threadIdx.x < 32) {
+        const int r = r0 + threadIdx.x;
+        const int e = (r < R) ? split_exponent(vmax[r]) : 0;
+        sexp[threadIdx.x] = e;
+        if (blockIdx.y == 0) exps[r] = e;
+    }
+    crt_split_table(sm, tab, N, 8);
+    const size_t pstride = (size_t)Pmax * Kmax;
+    for (int k0 = kbeg; k0 < kbeg + DIGIT_KT && k0 < Kp; k0 += 32) {
+        __syncthreads();
+        split_load_tile<double, LAYOUT>(th, Xh, ld, R, K, INT_MAX, r0, k0);
+        split_load_tile<double, LAYOUT>(tl, Xl, ld, R, K, INT_MAX, r0, k0);
+        __syncthreads();
+#pragma unroll 1
+        for (int w = 0; w < 4; ++w) {
+            const int v = ty + 8 * w;
+            const int r = r0 + v;
+            const int kk = k0 + tx;
+            const int e = sexp[v];
+            __int128 Xi = 0;
+            if (e != kOzakiExpNonfinite && r < R) Xi = dd_fixed_part(th[v][tx], t, e) + dd_fixed_part(tl[v][tx], t, e);
+            const bool neg = Xi < 0;
+            const unsigned __int128 mag = neg ? (unsigned __int128)(-Xi) : (unsigned __int128)Xi;
+            uint32_t u[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) u[k] = (uint32_t)(mag >> (16 * k)) & 0xffffu;
+            write_residues<8>(u, neg, sm, N, out + (size_t)r * Kmax + (size_t)kk, pstride);
+        }
+    }
+}
+
 // Splits levels 0..s-1 (level l costs l + 1 digit pairs) into G contiguous
 // non-empty groups minimising the largest group cost (linear partition by
 // dynamic programming); returns that cost.
@@ -737,6 +903,30 @@ int split_levels(int s, int G, int *lvl)
     }
     lvl[0] = 0;
     return best[G][s];
+}
+
+// Residue products: N levels of one product each into G contiguous groups
+// whose sizes differ by at most one (larger groups first); returns the largest.
+int split_levels_uniform(int N, int G, int *lvl)
+{
+    lvl[0] = 0;
+    for (int g = 0; g < G; ++g) lvl[g + 1] = lvl[g] + N / G + (g < N % G ? 1 : 0);
+    return (N + G - 1) / G;
+}
+
+int level_groups_uniform(int N, int active, int sms, int *lvl)
+{
+    int best_g = 1;
+    long long best = -1;
+    int tmp[kCrtMaxModuli + 1];
+    for (int G = 1; G <= std::min(N, 8); ++G) {
+        const int worst = split_levels_uniform(N, G, tmp);
+        const long long waves = ((long long)active * G + sms - 1) / sms;
+        const long long est = waves * worst;
+        if (best < 0 || est < best) { best = est; best_g = G; }
+    }
+    split_levels_uniform(N, best_g, lvl);
+    return best_g;
 }
 
 // Work items per tile: the number of level groups G that minimises the
@@ -790,7 +980,110 @@ cudaError_t encode_digits_map(void *map, void *base, int rows, int Kmax, int box
 
 }  // namespace
 
-cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx)
+namespace {
+
+// little-endian 32-bit limbs, enough for M < 2^288 and its products by 256
+struct Big {
+    uint32_t v[10] = {};
+    void mul_small(uint32_t m)
+    {
+        unsigned long long c = 0;
+        for (auto &x : v) { const unsigned long long t = (unsigned long long)x * m + c; x = (uint32_t)t; c = t >> 32; }
+    }
+    uint32_t div_small(uint32_t m)   // *this /= m, returns the remainder
+    {
+        unsigned long long r = 0;
+        for (int k = 9; k >= 0; --k) {
+            const unsigned long long t = (r << 32) | v[k];
+            v[k] = (uint32_t)(t / m);
+            r = t % m;
+        }
+        return (uint32_t)r;
+    }
+    uint32_t mod_small(uint32_t m) const { Big c = *this; return c.div_small(m); }
+    int bits() const
+    {
+        for (int k = 9; k >= 0; --k)
+            if (v[k]) return 32 * k + 32 - __builtin_clz(v[k]);
+        return 0;
+    }
+    void shl(int s)
+    {
+        const int w = s / 32, b = s % 32;
+        for (int k = 9; k >= 0; --k) {
+            const uint32_t hi = k - w >= 0 ? v[k - w] : 0, lo = k - w - 1 >= 0 ? v[k - w - 1] : 0;
+            v[k] = b ? (hi << b) | (lo >> (32 - b)) : hi;
+        }
+    }
+    double to_double() const
+    {
+        double d = 0.0;
+        for (int k = 9; k >= 0; --k) d = d * 4294967296.0 + (double)v[k];
+        return d;
+    }
+};
+
+}  // namespace
+
+bool crt_build_table(int N, int L, CrtTable &t)
+{
+    if (N < 1 || N > kCrtMaxModuli || (L != 4 && L != 8)) return false;
+    t = CrtTable{};
+    t.N = N;
+    // the largest integers <= 256 that are coprime to every one taken before
+    int cnt = 0;
+    for (int m = 256; m >= 2 && cnt < N; --m) {
+        bool ok = true;
+        for (int k = 0; k < cnt && ok; ++k) ok = std::gcd(m, t.m[k]) == 1;
+        if (ok) t.m[cnt++] = m;
+    }
+    Big M;
+    M.v[0] = 1;
+    for (int l = 0; l < N; ++l) M.mul_small((uint32_t)t.m[l]);
+    const int bits = M.bits();
+    if (bits > 32 * L) return false;
+    t.log2M = std::log2(M.to_double());
+    t.L = L;
+    // the weights and M are scaled by 2^sigma so that M' = M 2^sigma has its top
+    // bit at 32 L - 1; rebuilt values are then exact multiples of 2^sigma
+    const int sigma = 32 * t.L - bits;
+    for (int l = 0; l < N; ++l) {
+        const uint32_t m = (uint32_t)t.m[l];
+        Big Ml = M;
+        Ml.div_small(m);                        // M_l = M / m_l (exact)
+        const uint32_t a = Ml.mod_small(m);     // M_l mod m_l, invertible
+        uint32_t y = 1;
+        while ((a * y) % m != 1) ++y;
+        Ml.mul_small(y);                        // w_l = M_l y_l < M
+        Ml.shl(sigma);
+        for (int k = 0; k < t.L; ++k) t.w[l][k] = Ml.v[k];
+        t.inv40[l] = ((1ull << 40) + m - 1) / m;
+        t.off28[l] = m * (((1u << 28) + m - 1) / m);
+        unsigned long long pw = 1;
+        for (int k = 0; k < 8; ++k) {
+            t.pw16[k][l] = (unsigned)(pw % m);
+            pw = (pw % m) * 65536ull;
+        }
+    }
+    Big Ms = M;
+    Ms.shl(sigma);
+    for (int k = 0; k < t.L; ++k) t.M[k] = Ms.v[k];
+    Big H = Ms;
+    H.div_small(2);
+    for (int k = 0; k < t.L; ++k) t.halfM[k] = H.v[k];
+    t.invMtop = (float)(1.0 / ((double)t.M[t.L - 1] + (double)t.M[t.L - 2] / 4294967296.0));
+    t.sigma = sigma;
+    return true;
+}
+
+int crt_bits(const CrtTable &t, long long K)
+{
+    if (K < 1) K = 1;
+    return (int)std::floor((t.log2M - 1.0 - std::log2((double)K)) / 2.0 - 1e-9);
+}
+
+cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx, int crt_moduli, unsigned crt_mask,
+                        int crt_limbs)
 {
     static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
     w.nmax = nmax;
@@ -798,13 +1091,24 @@ cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx)
     w.Pmax = (nmax + kOzakiTileI - 1) / kOzakiTileI * kOzakiTileI;
     w.Kmax = (nmax + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk * (cplx ? 2 : 1);
     w.levels = kOzakiMaxSlices;
-    for (int i = 0; i < kOzakiSlots; ++i) w.levels = std::max(w.levels, caps[i]);
-    cudaError_t e = cudaMalloc((void **)&w.planes,
-                               (size_t)w.levels * (cplx ? 2 : 1) * w.Pmax * w.Pmax * sizeof(int32_t));
+    for (int i = 0; i < kOzakiSlots; ++i)
+        if (!(crt_mask >> i & 1u)) w.levels = std::max(w.levels, caps[i]);
+    cudaError_t e = cudaSuccess;
+    if (crt_moduli > 0) {
+        if (!crt_build_table(crt_moduli, crt_limbs, w.crt)) return cudaErrorInvalidValue;
+        // byte planes of the residues share the int32 level planes' buffer
+        w.levels = std::max(w.levels, (crt_moduli + 3) / 4);
+        e = cudaMalloc((void **)&w.crt_dev, sizeof(CrtTable));
+        if (e == cudaSuccess) e = cudaMemcpy(w.crt_dev, &w.crt, sizeof(CrtTable), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMalloc((void **)&w.planes, (size_t)w.levels * (cplx ? 2 : 1) * w.Pmax * w.Pmax * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&w.vmax, (size_t)w.Pmax * sizeof(unsigned long long));
     for (int i = 0; i < kOzakiSlots && e == cudaSuccess; ++i) {
         OzakiSlot &sl = w.slot[i];
         sl.cap = caps[i];
+        sl.crt = (crt_mask >> i & 1u) && crt_moduli > 0 ? 1 : 0;
+        if (sl.crt) sl.cap = crt_moduli;
         if (sl.cap <= 0) continue;
         const size_t bytes = (size_t)sl.cap * w.Pmax * w.Kmax * 2;
         e = cudaMalloc(&sl.dig, bytes);
@@ -826,14 +1130,17 @@ void ozaki_free(OzakiWork &w)
     w.tuned.clear();
     cudaFree(w.planes);
     cudaFree(w.vmax);
+    cudaFree(w.crt_dev);
     w.planes = nullptr;
     w.vmax = nullptr;
+    w.crt_dev = nullptr;
     for (int i = 0; i < kOzakiSlots; ++i) {
         cudaFree(w.slot[i].dig);
         cudaFree(w.slot[i].exps);
         w.slot[i].dig = nullptr;
         w.slot[i].exps = nullptr;
         w.slot[i].cap = 0;
+        w.slot[i].crt = 0;
     }
 }
 
@@ -850,16 +1157,26 @@ sr_status ozaki_split(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int sl
     const int Rp = (R + 31) / 32 * 32;
     const int esz = w.cplx ? 16 : 8;
     SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, 2LL * R * K * esz + 2LL * s * Kp * Rp, 2);
-    w.slot[slot].layout = layout;
-    __nv_bfloat16 *out = (__nv_bfloat16 *)w.slot[slot].dig;
-    int *ex = w.slot[slot].exps;
+    OzakiSlot &sl = w.slot[slot];
+    sl.layout = layout;
+    __nv_bfloat16 *out = (__nv_bfloat16 *)sl.dig;
+    int *ex = sl.exps;
+    if (sl.crt) {
+        if (s != w.crt.N) return SR_ERR_INVALID_ARG;
+        sl.t = crt_bits(w.crt, (long long)K * (w.cplx ? 2 : 1));   // complex: dot products of 2K terms
+        if (sl.t < 1 || sl.t > 62) return SR_ERR_UNSUPPORTED;
+    }
     SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)Rp * sizeof(unsigned long long), st));
     const dim3 gmax(Rp / 32, (Kv + SPLIT_KT - 1) / SPLIT_KT);
     const dim3 gdig(Rp / 32, (Kp + DIGIT_KT - 1) / DIGIT_KT);
 #define SR_SPLIT_LAUNCH(TIN, LAY)                                                                                 \
     ozaki_absmax_kernel<TIN, LAY><<<gmax, 256, 0, st>>>(R, K, Kh, Kv, (const TIN *)X, ld, w.vmax);                \
-    ozaki_digits_kernel<TIN, LAY><<<gdig, 256, 0, st>>>(R, K, Kh, Kp, (const TIN *)X, ld, s, w.Pmax, w.Kmax,      \
-                                                        w.vmax, out, ex)
+    if (sl.crt)                                                                                                   \
+        ozaki_residues_kernel<TIN, LAY><<<gdig, 256, 0, st>>>(R, K, Kh, Kp, (const TIN *)X, ld, sl.t, s, w.Pmax,  \
+                                                              w.Kmax, w.vmax, out, ex, w.crt_dev);                \
+    else                                                                                                          \
+        ozaki_digits_kernel<TIN, LAY><<<gdig, 256, 0, st>>>(R, K, Kh, Kp, (const TIN *)X, ld, s, w.Pmax, w.Kmax,  \
+                                                            w.vmax, out, ex)
     if (w.cplx) {
         if (layout == OZ_COLS) { SR_SPLIT_LAUNCH(cd, OZ_COLS); } else { SR_SPLIT_LAUNCH(cd, OZ_ROWS); }
     } else {
@@ -873,26 +1190,40 @@ sr_status ozaki_split(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int sl
 sr_status ozaki_split_dd(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K,
                          const double *Xhi, const double *Xlo, int ld, int layout, int s)
 {
-    if (w.cplx || slot < 0 || slot >= kOzakiSlots || s < 1 || s > w.slot[slot].cap || s > kOzakiMaxSlicesDD ||
-        R > w.Pmax || K > ozaki_k_limit(false) || K > w.nmax)
+    OzakiSlot &sl = w.slot[slot];
+    if (w.cplx || slot < 0 || slot >= kOzakiSlots || s < 1 || s > sl.cap ||
+        s > (sl.crt ? kCrtMaxModuli : kOzakiMaxSlicesDD) || R > w.Pmax || K > ozaki_k_limit(false) || K > w.nmax)
         return SR_ERR_INVALID_ARG;
     const int Kp = (K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
     const int Rp = (R + 31) / 32 * 32;
     SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, 2LL * R * K * 16 + 2LL * s * Kp * Rp, 2);
-    w.slot[slot].layout = layout;
-    __nv_bfloat16 *out = (__nv_bfloat16 *)w.slot[slot].dig;
-    int *ex = w.slot[slot].exps;
+    sl.layout = layout;
+    __nv_bfloat16 *out = (__nv_bfloat16 *)sl.dig;
+    int *ex = sl.exps;
+    if (sl.crt) {
+        if (s != w.crt.N) return SR_ERR_INVALID_ARG;
+        sl.t = crt_bits(w.crt, K);
+        if (sl.t < 1 || sl.t > 120) return SR_ERR_UNSUPPORTED;
+    }
     SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)Rp * sizeof(unsigned long long), st));
     const dim3 gmax(Rp / 32, (K + SPLIT_KT - 1) / SPLIT_KT);
     const dim3 gdig(Rp / 32, (Kp + DIGIT_KT - 1) / DIGIT_KT);
     if (layout == OZ_COLS) {
         ozaki_absmax_kernel<double, OZ_COLS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, Xhi, ld, w.vmax);
-        ozaki_digits_dd_kernel<OZ_COLS><<<gdig, 256, 0, st>>>(R, K, Kp, Xhi, Xlo, ld, s, w.Pmax, w.Kmax, w.vmax,
-                                                              out, ex);
+        if (sl.crt)
+            ozaki_residues_dd_kernel<OZ_COLS><<<gdig, 256, 0, st>>>(R, K, Kp, Xhi, Xlo, ld, sl.t, s, w.Pmax, w.Kmax,
+                                                                    w.vmax, out, ex, w.crt_dev);
+        else
+            ozaki_digits_dd_kernel<OZ_COLS><<<gdig, 256, 0, st>>>(R, K, Kp, Xhi, Xlo, ld, s, w.Pmax, w.Kmax, w.vmax,
+                                                                  out, ex);
     } else {
         ozaki_absmax_kernel<double, OZ_ROWS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, Xhi, ld, w.vmax);
-        ozaki_digits_dd_kernel<OZ_ROWS><<<gdig, 256, 0, st>>>(R, K, Kp, Xhi, Xlo, ld, s, w.Pmax, w.Kmax, w.vmax,
-                                                              out, ex);
+        if (sl.crt)
+            ozaki_residues_dd_kernel<OZ_ROWS><<<gdig, 256, 0, st>>>(R, K, Kp, Xhi, Xlo, ld, sl.t, s, w.Pmax, w.Kmax,
+                                                                    w.vmax, out, ex, w.crt_dev);
+        else
+            ozaki_digits_dd_kernel<OZ_ROWS><<<gdig, 256, 0, st>>>(R, K, Kp, Xhi, Xlo, ld, s, w.Pmax, w.Kmax, w.vmax,
+                                                                  out, ex);
     }
     SR_CUDA_TRY(cudaGetLastError());
     return SR_OK;
@@ -902,14 +1233,19 @@ sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
                         int s, bool symmetric, int *flags)
 {
     if (k > ozaki_k_limit(w.cplx)) return SR_ERR_UNSUPPORTED;
-    if (s < 1 || s > w.slot[rows].cap || s > w.slot[cols].cap || s > w.levels) return SR_ERR_INVALID_ARG;
+    const bool crt = w.slot[rows].crt != 0;
+    if (crt != (w.slot[cols].crt != 0)) return SR_ERR_INVALID_ARG;
+    if (s < 1 || s > w.slot[rows].cap || s > w.slot[cols].cap) return SR_ERR_INVALID_ARG;
+    if (crt ? (s != w.crt.N || s > 4 * w.levels) : s > w.levels) return SR_ERR_INVALID_ARG;
     const int Kc = (k + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
     const int Kp = w.cplx ? 2 * Kc : Kc;
-    // level l sums (l + 1) * chunks exact chunk results below 2^22: keep it below 2^31
-    if ((long long)s * (Kp / kOzakiKChunk) * (1LL << 22) >= (1LL << 31)) return SR_ERR_UNSUPPORTED;
+    // digits: level l sums (l + 1) * chunks exact chunk results below 2^22: keep it below 2^31;
+    // residues: one product per level, its sum below 2^28 (the drain's reduction modulo m)
+    if (crt ? (Kp / kOzakiKChunk) > 64 : (long long)s * (Kp / kOzakiKChunk) * (1LL << 22) >= (1LL << 31))
+        return SR_ERR_UNSUPPORTED;
     const int Mp = (m + BN - 1) / BN * BN;
     const int Np = (n + BM - 1) / BM * BM;
-    const long long pairs = (long long)s * (s + 1) / 2;
+    const long long pairs = crt ? s : (long long)s * (s + 1) / 2;
     const int tiles_i = Mp / BN, tiles_j = Np / BM;
     const int parts = w.cplx ? 2 : 1;
     long long active = 0;
@@ -938,23 +1274,32 @@ sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
     a.pstride = (size_t)parts * w.Pmax * w.Pmax;
     a.flags = flags;
     a.nact = (int)active;
+    a.crt = crt ? 1 : 0;
+    if (crt)
+        for (int l = 0; l < s; ++l) {
+            a.mods[l] = w.crt.m[l];
+            a.inv40[l] = w.crt.inv40[l];
+            a.off28[l] = w.crt.off28[l];
+        }
     // MMA "A" (TMEM lanes) = column-side digits, MMA "B" = row-side digits
     auto launch = [&](int G) {
         a.groups = G;
-        split_levels(s, G, a.lvl);
+        if (crt) split_levels_uniform(s, G, a.lvl); else split_levels(s, G, a.lvl);
         a.nitems = a.nact * a.groups;
         const int grid = (int)std::min<long long>(a.nitems, sms);
         ozaki_mma_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*(const CUtensorMap *)w.slot[rows].map_i,
                                                                        *(const CUtensorMap *)w.slot[cols].map_j, a);
         return cudaGetLastError();
     };
-    const long long key = active | (long long)s << 24 | (long long)a.nch << 32 | (long long)parts << 48;
+    const long long key = active | (long long)s << 24 | (long long)a.nch << 32 | (long long)parts << 48 |
+                          (long long)a.crt << 52;
     int G = -1;
     for (const auto &t : w.tuned)
         if (t.key == key) G = t.groups;
     if (G < 0) {
-        int lvl[kOzakiMaxSlicesDD + 1];
-        G = level_groups(s, (int)active, sms, lvl);   // the makespan estimate
+        int lvl[kCrtMaxModuli + 1];
+        G = crt ? level_groups_uniform(s, (int)active, sms, lvl)
+                : level_groups(s, (int)active, sms, lvl);   // the makespan estimate
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         cudaStreamIsCapturing(st, &cs);
         if (w.autotune && cs == cudaStreamCaptureStatusNone) {
@@ -1060,3 +1405,19 @@ sr_status ozaki_product_items(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w
 }
 
 }  // namespace sr
+
+extern "C" sr_status schur_refine_crt_info(int N, int limbs, long long K, int *moduli, unsigned *weights,
+                                           unsigned *M, int *sigma, int *t)
+{
+    if (!moduli || !weights || !M || !sigma || !t || K < 1) return SR_ERR_INVALID_ARG;
+    sr::CrtTable tab;
+    if (!sr::crt_build_table(N, limbs, tab)) return SR_ERR_INVALID_ARG;
+    for (int l = 0; l < N; ++l) {
+        moduli[l] = tab.m[l];
+        for (int k = 0; k < limbs; ++k) weights[l * limbs + k] = tab.w[l][k];
+    }
+    for (int k = 0; k < limbs; ++k) M[k] = tab.M[k];
+    *sigma = tab.sigma;
+    *t = sr::crt_bits(tab, K);
+    return SR_OK;
+}

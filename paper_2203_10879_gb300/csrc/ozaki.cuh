@@ -35,6 +35,20 @@
 // swapped, and the chunks that carry a minus sign are issued with the
 // instruction descriptor's negate-A bit. Every partial sum stays an exact
 // integer, as in the real case.
+//
+// Residue form (the Chinese-remainder variant of the scheme, selected per
+// slot): instead of cutting x into digits, every vector's entries become one
+// integer X = round(x 2^(t - e)) with |X| <= 2^t, and X is stored as its
+// residues modulo N pairwise coprime moduli m_1..N <= 256 (symmetric residues
+// in [-128, 128], exact in bf16). The integer product C = A_int B_int is then
+// formed exactly modulo each m_l by ONE tcgen05 product of the residue
+// matrices (FP32 sums exact as above, drained into an exact int32 sum and
+// reduced modulo m_l into a byte plane), and rebuilt from its N residues by
+// the Chinese remainder theorem: C = sum_l R_l w_l mod M, w_l = M_l (M_l^-1
+// mod m_l), M = prod m_l, M_l = M / m_l, taken in (-M/2, M/2]. The rebuild is
+// exact when K 2^(2t) < M / 2, which fixes t from N and the inner length K:
+// N = 16 gives t = 56 at K <= 4096 (16 products where 7 digits take 28 digit
+// pairs), N = 32 gives t = 113 at K <= 8192 for double-double operands.
 #pragma once
 #include <climits>
 #include <type_traits>
@@ -57,12 +71,45 @@ constexpr int kOzakiKChunk = 256;
 constexpr int kOzakiMaxK = 16384;     // keeps every level sum below 2^31
 constexpr int kOzakiExpNonfinite = INT_MIN;
 constexpr int kOzakiSlots = 8;
+// residue form
+constexpr int kCrtMaxModuli = 32;
+constexpr int kCrtDefaultModuli = 16;     // FP64 operands: t = 56 bits at K <= 4096
+constexpr int kCrtDefaultModuliDD = 32;   // double-double operands: t = 113 bits at K <= 8192
+constexpr int kCrtMaxLimbs = 8;           // 32-bit limbs of M (4 for N <= 16, 8 for N <= 32)
+
+// Moduli, CRT weights and the constants of the residue kernels (host-built,
+// one copy per work area in device memory).
+struct CrtTable {
+    int N = 0;                                   // moduli in use
+    int L = 0;                                   // 32-bit limbs holding M (M < 2^(32 L))
+    double log2M = 0.0;
+    int sigma = 0;                               // M and the weights are stored times 2^sigma
+    float invMtop = 0.f;                         // 2^(32 (L - 1)) / (M 2^sigma)
+    int m[kCrtMaxModuli];                        // the moduli, pairwise coprime, <= 256
+    unsigned long long inv40[kCrtMaxModuli];     // ceil(2^40 / m): v / m = (v inv40) >> 40 for v < 2^31
+    unsigned off28[kCrtMaxModuli];               // m ceil(2^28 / m): makes |v| < 2^28 non-negative mod m
+    unsigned pw16[8][kCrtMaxModuli];             // 2^(16 k) mod m
+    unsigned w[kCrtMaxModuli][kCrtMaxLimbs];     // CRT weights w_l < M, times 2^sigma, little-endian limbs
+    unsigned M[kCrtMaxLimbs];                    // M 2^sigma (top bit at 32 L - 1)
+    unsigned halfM[kCrtMaxLimbs];                // M 2^(sigma - 1)
+};
+
+// Builds the table for the first N moduli of the fixed list (the largest
+// pairwise coprime integers <= 256, greedily), with M held in L = 4 limbs
+// (FP64 results) or 8 (double-double results). Returns false for N outside
+// [1, kCrtMaxModuli] or M >= 2^(32 L).
+bool crt_build_table(int N, int L, CrtTable &t);
+// Bits t of the integer operands for N moduli and inner length K: the
+// largest t with K 2^(2t) < M / 2 (every rebuilt C is then exact).
+int crt_bits(const CrtTable &t, long long K);
 
 // vectors of a split: columns (contiguous in a column-major matrix) or rows
 enum { OZ_COLS = 0, OZ_ROWS = 1 };
 
 struct OzakiSlot {
-    int cap = 0;                           // digits this slot can hold
+    int cap = 0;                           // digits (residues) this slot can hold
+    int crt = 0;                           // 1: residue form (see the header), 0: digits
+    int t = 0;                             // residue form: bits of the integers of the last split
     int layout = OZ_COLS;                  // vectors of the last split (OZ_COLS or OZ_ROWS)
     void *dig = nullptr;                   // bf16 digits [cap][Pmax][Kmax]
     int *exps = nullptr;                   // [Pmax]
@@ -83,12 +130,19 @@ struct OzakiWork {
     std::vector<Tuned> tuned;
     bool autotune = false;
     cudaEvent_t tev[2] = {nullptr, nullptr};
-    int32_t *planes = nullptr;             // [levels][Pmax (2 Pmax if cplx) cols][Pmax rows]
+    int32_t *planes = nullptr;             // [levels][Pmax (2 Pmax if cplx) cols][Pmax rows]; the
+                                           // residue form keeps byte planes [N][...] in the same buffer
+    CrtTable crt;                          // residue form: host copy of the table
+    CrtTable *crt_dev = nullptr;           // and its device copy (null when no slot uses residues)
     unsigned long long *vmax = nullptr;    // per-vector largest |x| (bit pattern) during a split
 };
 
-// caps[i] = digits of slot i (0 = unused); cplx: complex128 operands
-cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx);
+// caps[i] = digits of slot i (0 = unused); cplx: complex128 operands;
+// crt_moduli > 0: slots with crt_mask bit i set hold residues modulo that
+// many moduli instead of digits, rebuilt into FP64 (crt_limbs = 4) or
+// double-double (crt_limbs = 8) results
+cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx, int crt_moduli = 0,
+                        unsigned crt_mask = 0, int crt_limbs = 4);
 
 // ---- groups of independent products (many matrices in one launch) -------------------
 // A work area for a group holds the vectors of every matrix one after another
@@ -410,6 +464,286 @@ ozaki_combine_dd_kernel(int m, int n, int s, const int32_t *__restrict__ planes,
     }
 }
 
+// ---- residue form: rebuild by the Chinese remainder theorem -------------------------
+// The table's part the rebuild needs, staged in shared memory by every block.
+struct CrtRebuildSm {
+    unsigned w[kCrtMaxModuli][kCrtMaxLimbs];
+    unsigned M[kCrtMaxLimbs], halfM[kCrtMaxLimbs];
+    float invMtop;
+    int N, sigma;
+};
+
+__device__ __forceinline__ void crt_stage(CrtRebuildSm &sm, const CrtTable *__restrict__ tab, int L)
+{
+    for (int x = threadIdx.x; x < tab->N * L; x += blockDim.x) sm.w[x / L][x % L] = tab->w[x / L][x % L];
+    if (threadIdx.x < L) {
+        sm.M[threadIdx.x] = tab->M[threadIdx.x];
+        sm.halfM[threadIdx.x] = tab->halfM[threadIdx.x];
+    }
+    if (threadIdx.x == 0) {
+        sm.invMtop = tab->invMtop;
+        sm.N = tab->N;
+        sm.sigma = tab->sigma;
+    }
+}
+
+// S' = sum_l R_l w'_l is given as per-limb column sums acc[k] (no carries yet;
+// each below 2^45). Returns the sign of r = S' mod M' taken in (-M'/2, M'/2]
+// and writes |r| to mag (r = C 2^sigma for the rebuilt integer C).
+template <int L>
+__device__ __forceinline__ bool crt_reduce(const unsigned long long (&acc)[L], const CrtRebuildSm &T,
+                                           uint32_t (&mag)[L])
+{
+    uint32_t S[L + 1];
+    unsigned long long c = 0;
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const unsigned long long v = acc[k] + c;
+        S[k] = (uint32_t)v;
+        c = v >> 32;
+    }
+    S[L] = (uint32_t)c;
+    // q = floor(S'/M') < 2^13 from the top 64 bits (M' has its top bit at 32 L - 1),
+    // lowered by one: the estimate is within 0.01 of S'/M', so 0 <= S' - q M' < 3 M'
+    const float est = ((float)S[L] * 4294967296.0f + (float)S[L - 1]) * T.invMtop;
+    int q = (int)est - 1;
+    q = q < 0 ? 0 : q;
+    unsigned long long cm = 0;
+    long long br = 0;
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const unsigned long long pk = (unsigned long long)(uint32_t)q * T.M[k] + cm;
+        cm = pk >> 32;
+        const long long d = (long long)S[k] - (long long)(uint32_t)pk + br;
+        S[k] = (uint32_t)d;
+        br = d >> 32;
+    }
+    S[L] = (uint32_t)((long long)S[L] - (long long)cm + br);
+    // at most two subtractions of M' bring S' into [0, M')
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+        uint32_t d[L + 1];
+        long long b = 0;
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const long long x = (long long)S[k] - (long long)T.M[k] + b;
+            d[k] = (uint32_t)x;
+            b = x >> 32;
+        }
+        const long long x = (long long)S[L] + b;
+        d[L] = (uint32_t)x;
+        if ((x >> 32) == 0) {
+#pragma unroll
+            for (int k = 0; k <= L; ++k) S[k] = d[k];
+        }
+    }
+    // symmetric range: r > M'/2 stands for r - M'
+    bool gt = false, decided = false;
+#pragma unroll
+    for (int k = L - 1; k >= 0; --k) {
+        if (!decided && S[k] != T.halfM[k]) {
+            gt = S[k] > T.halfM[k];
+            decided = true;
+        }
+    }
+    if (gt) {
+        long long b = 0;
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const long long x = (long long)T.M[k] - (long long)S[k] + b;
+            mag[k] = (uint32_t)x;
+            b = x >> 32;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < L; ++k) mag[k] = S[k];
+    }
+    return gt;
+}
+
+// (-1)^neg |r| 2^x as a double, rounded once (|r| < 2^127 for L = 4)
+__device__ __forceinline__ double crt_to_double(const uint32_t (&mag)[4], bool neg, int x)
+{
+    const unsigned __int128 V = ((unsigned __int128)mag[3] << 96) | ((unsigned __int128)mag[2] << 64) |
+                                ((unsigned __int128)mag[1] << 32) | (unsigned __int128)mag[0];
+    return oz_i128_to_double(neg ? -(__int128)V : (__int128)V, x);
+}
+
+// the same as a double-double (L = 8): the 127 leading bits of |r| are taken
+// (the bits below them are beyond the double-double's 106) and converted as in
+// oz_i128_to_dd
+__device__ __forceinline__ ddv crt_to_dd(const uint32_t (&mag)[8], bool neg, int x)
+{
+    int k = 3;
+#pragma unroll
+    for (int a = 7; a >= 4; --a)
+        if (k == 3 && mag[a] != 0) k = a;
+    uint32_t w3 = 0, w2 = 0, w1 = 0, w0 = 0, wm = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        if (a == k) w3 = mag[a];
+        if (a == k - 1) w2 = mag[a];
+        if (a == k - 2) w1 = mag[a];
+        if (a == k - 3) w0 = mag[a];
+        if (a == k - 4) wm = mag[a];
+    }
+    unsigned __int128 W = ((unsigned __int128)w3 << 96) | ((unsigned __int128)w2 << 64) |
+                          ((unsigned __int128)w1 << 32) | (unsigned __int128)w0;
+    int xe = x + 32 * (k - 3);
+    if (w3 != 0) {
+        const int lz = __clz((int)w3) - 1;   // leading bit to position 126
+        if (lz > 0) {
+            W = (W << lz) | (unsigned __int128)(wm >> (32 - lz));
+            xe -= lz;
+        } else if (lz < 0) {
+            W >>= 1;
+            xe += 1;
+        }
+    }
+    return oz_i128_to_dd(neg ? -(__int128)W : (__int128)W, xe);
+}
+
+// One rebuilt plane entry at off: sign * C 2^(e1 + e2 - tsum), C from its residues
+template <int L>
+__device__ __forceinline__ std::conditional_t<L == 8, ddv, double>
+crt_value(const uint8_t *__restrict__ planes, size_t off, size_t pstride, const CrtRebuildSm &T, int e1, int e2,
+          int tsum, bool negs)
+{
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite) {
+        if constexpr (L == 8) return ddv{nan, nan}; else return nan;
+    }
+    unsigned long long acc[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) acc[k] = 0ull;
+    for (int l = 0; l < T.N; ++l) {
+        const uint32_t R = planes[off + (size_t)l * pstride];
+#pragma unroll
+        for (int k = 0; k < L; ++k) acc[k] += (unsigned long long)R * T.w[l][k];
+    }
+    uint32_t mag[L];
+    const bool ng = crt_reduce<L>(acc, T, mag) != negs;
+    if constexpr (L == 8) return crt_to_dd(mag, ng, e1 + e2 - tsum - T.sigma);
+    else return crt_to_double(mag, ng, e1 + e2 - tsum - T.sigma);
+}
+
+// C(i, j) = sign * (rebuilt product) with the epilogue ep, FP64 results
+// (L = 4) or double-double results (L = 8). Each thread takes 4 consecutive
+// rows of one column (one 32-bit load per residue plane); a block covers 32 x
+// 32 entries. With mirror, a block wholly below the diagonal rebuilds the
+// mirrored block (coalesced along the planes' contiguous index) and turns it
+// in shared memory; entries below the diagonal of a diagonal block read the
+// mirrored position directly.
+template <class EP, bool CPLX, int L>
+__global__ void __launch_bounds__(256)
+ozaki_crt_combine_kernel(int m, int n, const uint8_t *__restrict__ planes, int ldp, size_t pstride, size_t imoff,
+                         const int *__restrict__ ea, const int *__restrict__ fb, int tsum, double sign, int mirror,
+                         EP ep, double *partial, const CrtTable *__restrict__ tab)
+{
+    static_assert(!(CPLX && L == 8), "complex products rebuild FP64 parts");
+    using RV = std::conditional_t<L == 8, ddv, double>;
+    using VT = std::conditional_t<CPLX, cd, RV>;
+    __shared__ CrtRebuildSm T;
+    __shared__ VT turned[32][33];
+    crt_stage(T, tab, L);
+    __syncthreads();
+    const int N = T.N;
+    const bool negs = sign < 0;
+    const int ig = threadIdx.x & 7, jl = threadIdx.x >> 3;
+    const bool below = mirror && blockIdx.x > blockIdx.y;
+    // rebuilt entries (ra + 4 ig + u, ca + jl) of the planes, u = 0..3
+    const int ra = (below ? blockIdx.y : blockIdx.x) * 32 + 4 * ig;
+    const int ca = (below ? blockIdx.x : blockIdx.y) * 32 + jl;
+    const int rlim = below ? n : m, clim = below ? m : n;
+    VT val[4];
+    auto rebuild = [&](size_t base, int e2, RV (&out)[4]) {
+        unsigned long long acc[4][L];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < L; ++k) acc[u][k] = 0ull;
+        for (int l = 0; l < N; ++l) {
+            const uint32_t r4 = *reinterpret_cast<const uint32_t *>(planes + base + (size_t)l * pstride);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t R = (r4 >> (8 * u)) & 255u;
+#pragma unroll
+                for (int k = 0; k < L; ++k) acc[u][k] += (unsigned long long)R * T.w[l][k];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            uint32_t mag[L];
+            const bool ng = crt_reduce<L>(acc[u], T, mag) != negs;
+            const int e1 = ea[min(ra + u, rlim - 1)];
+            const int x = e1 + e2 - tsum - T.sigma;
+            const bool bad = e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite;
+            const double nan = __longlong_as_double(0x7ff8000000000000LL);
+            if constexpr (L == 8) {
+                out[u] = bad ? ddv{nan, nan} : crt_to_dd(mag, ng, x);
+            } else {
+                out[u] = bad ? nan : crt_to_double(mag, ng, x);
+            }
+        }
+    };
+    const bool active = ra < rlim && ca < clim;
+    if (active) {
+        const size_t base = (size_t)ra + (size_t)ca * (size_t)ldp;
+        const int e2 = fb[ca];
+        RV re[4];
+        rebuild(base, e2, re);
+        if constexpr (CPLX) {
+            RV im[4];
+            rebuild(base + imoff, e2, im);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) val[u] = cd{re[u], below ? -im[u] : im[u]};
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) val[u] = re[u];
+        }
+    }
+    double part = 0.0;
+    if (below) {
+        // turn the mirrored block: entry (ca, ra + u) of the output
+        if (active)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) turned[jl][4 * ig + u] = val[u];
+        __syncthreads();
+        const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + 4 * ig + u, j = j0 + jl;
+            if (i < m && j < n) part += ep(i, j, turned[4 * ig + u][jl]);
+        }
+    } else if (active) {
+        const int j = ca;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = ra + u;
+            if (i >= m) break;
+            VT v = val[u];
+            if (mirror && i > j) {
+                // below the diagonal inside a diagonal block: the mirrored entry
+                // (conjugated when complex: the product is Hermitian)
+                const size_t off = (size_t)j + (size_t)i * (size_t)ldp;
+                if constexpr (CPLX) {
+                    v = cd{crt_value<L>(planes, off, pstride, T, ea[j], fb[i], tsum, negs),
+                           -crt_value<L>(planes, off + imoff, pstride, T, ea[j], fb[i], tsum, negs)};
+                } else {
+                    v = crt_value<L>(planes, off, pstride, T, ea[j], fb[i], tsum, negs);
+                }
+            }
+            part += ep(i, j, v);
+        }
+    }
+    if (partial) {
+        part = sr_block_sum<256>(part);
+        if (threadIdx.x == 0) partial[blockIdx.x + (size_t)gridDim.x * blockIdx.y] = part;
+    }
+}
+
+inline int ozaki_crt_limbs(const OzakiWork &w) { return w.crt.L; }
+
 // epilogues of complex products carry `static constexpr bool kComplex`
 template <class EP, class = void> struct ep_is_complex : std::false_type {};
 template <class EP> struct ep_is_complex<EP, std::void_t<decltype(EP::kComplex)>> : std::true_type {};
@@ -422,6 +756,31 @@ template <class EP>
 sr_status ozaki_combine(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n, int s,
                         double sign, bool mirror, EP ep, double *partial, int *blocks)
 {
+    if (w.slot[rows].crt || w.slot[cols].crt) {
+        // residue form: rebuild by the Chinese remainder theorem
+        if (!(w.slot[rows].crt && w.slot[cols].crt) || s != w.crt.N) return SR_ERR_INVALID_ARG;
+        const int tsum = w.slot[rows].t + w.slot[cols].t;
+        const dim3 grid((m + 31) / 32, (n + 31) / 32);
+        const uint8_t *pl = reinterpret_cast<const uint8_t *>(w.planes);
+        if constexpr (ep_is_dd<EP>::value) {
+            if (w.cplx || w.crt.L != 8) return SR_ERR_INVALID_ARG;
+            SrPhase ph(h, SR_PROF_OZ_COMBINE, 16LL * 8 * s * m * n, (long long)m * n * (1LL * s + 32), 1);
+            ozaki_crt_combine_kernel<EP, false, 8><<<grid, 256, 0, st>>>(
+                m, n, pl, w.Pmax, (size_t)w.Pmax * w.Pmax, 0, w.slot[rows].exps, w.slot[cols].exps, tsum, sign,
+                mirror ? 1 : 0, ep, partial, w.crt_dev);
+        } else {
+            constexpr bool CPLX = ep_is_complex<EP>::value;
+            const int c = CPLX ? 2 : 1;
+            if (CPLX != w.cplx || w.crt.L != 4) return SR_ERR_INVALID_ARG;
+            SrPhase ph(h, SR_PROF_OZ_COMBINE, 8LL * c * s * m * n, (long long)m * n * (1LL * c * s + 16 * c), 1);
+            ozaki_crt_combine_kernel<EP, CPLX, 4><<<grid, 256, 0, st>>>(
+                m, n, pl, w.Pmax, (size_t)c * w.Pmax * w.Pmax, (size_t)w.Pmax * w.Pmax, w.slot[rows].exps,
+                w.slot[cols].exps, tsum, sign, mirror ? 1 : 0, ep, partial, w.crt_dev);
+        }
+        SR_CUDA_TRY(cudaGetLastError());
+        if (blocks) *blocks = ozaki_blocks(m, n);
+        return SR_OK;
+    }
     if constexpr (ep_is_dd<EP>::value) {
         if (w.cplx || s > w.levels) return SR_ERR_INVALID_ARG;
         SrPhase ph(h, SR_PROF_OZ_COMBINE, 24LL * s * m * n, (long long)m * n * (4LL * s + 32), 1);

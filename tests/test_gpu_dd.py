@@ -7,6 +7,9 @@ The CUDA library, called through its C ABI, against the double-double oracle
     with 14 bf16 digits per operand drops terms below (s + 2) 2^-8s of the
     vector scales, about k 2^-108 max|a_i| max|b_j|; the bound used is
     8 k 2^-104 times the row and column maxima;
+  * the residue form (32 moduli) holds every operand as an integer of t bits
+    (t = 113 to 115 at these inner lengths), so its product is within
+    k 2^-t of the row and column maxima: inside the same bound;
   * integer operands make every product exact: bit-exact agreement;
   * the FP64 solve with double-double divisors agrees with the oracle's Alg. 2
     to a few hundred u64 relative to |L|;
@@ -27,7 +30,8 @@ pytestmark = pytest.mark.gpu
 
 U64 = 2.0 ** -53
 U_DD = 2.0 ** -104
-ENGINES = [B.SR_HP_OZAKI_BF16, B.SR_HP_FP64]
+ENGINES = [B.SR_HP_OZAKI_BF16, B.SR_HP_OZAKI_CRT, B.SR_HP_FP64]
+EMULATED = [B.SR_HP_OZAKI_BF16, B.SR_HP_OZAKI_CRT]
 
 
 @pytest.fixture(scope="module")
@@ -196,19 +200,21 @@ def test_dd_engines_agree_and_full_sigma(torch):
     p = inputs.unit_step_dd(96)
     _, _, Qa, _, _ = _refine_gpu(torch, p, B.SR_HP_OZAKI_BF16)
     _, _, Qb, _, _ = _refine_gpu(torch, p, B.SR_HP_FP64)
+    _, _, Qd, _, _ = _refine_gpu(torch, p, B.SR_HP_OZAKI_CRT)
     s, nr, Qc, _, (rT, rQ) = _refine_gpu(torch, p, B.SR_HP_OZAKI_BF16, full_sigma=1)
     assert s == B.SR_OK and rT <= D.default_tol_dd(96) and rQ <= D.default_tol_dd(96)
-    for X in (Qb, Qc):
+    for X in (Qb, Qc, Qd):
         assert np.max(np.abs((Qa[0] - X[0]) + (Qa[1] - X[1]))) <= 1e-26
 
 
-def test_dd_workload_full_size(torch):
+@pytest.mark.parametrize("hp", EMULATED)
+def test_dd_workload_full_size(torch, hp):
     """The n = 2048 double-double workload as the benchmark runs it: certified
     on the device, and sampled entries of Q^T A Q and Q^T Q - I of the GPU's Q
     evaluated by the oracle in 128-bit arithmetic."""
     n = 2048
     p = inputs.unit_step_dd(n)
-    s, nr, Q, T, (rT, rQ) = _refine_gpu(torch, p, B.SR_HP_OZAKI_BF16)
+    s, nr, Q, T, (rT, rQ) = _refine_gpu(torch, p, hp)
     tol = D.default_tol_dd(n)
     assert s == B.SR_OK and nr.iters <= 3
     assert rT <= tol and rQ <= tol, (rT, rQ, tol)
