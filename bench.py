@@ -66,6 +66,14 @@ def _peaks():
         return {}
 
 
+def _engine_name(hp, slices, dd):
+    if hp == "fp64":
+        return "fp64"
+    if hp == "crt":
+        return f"crt-bf16-N{slices or (32 if dd else 16)}"
+    return f"ozaki-bf16-s{slices or (14 if dd else 7)}"
+
+
 def bf16_peak(clk, peaks):
     """The measured bf16 peak that matches the timed region's clock: the burst
     figure when the region's median SM clock is at (>= 95 % of) the maximum,
@@ -376,8 +384,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     dtype_opt = {"dtype": B.SR_COMPLEX} if cplx else ({"symmetric": 1} if sym else {})
 
-    hp_name = {"fp64": B.SR_HP_FP64, "ozaki": B.SR_HP_OZAKI_BF16}
-    hp = "ozaki" if cplx else args.hp
+    hp_name = {"fp64": B.SR_HP_FP64, "ozaki": B.SR_HP_OZAKI_BF16, "crt": B.SR_HP_OZAKI_CRT}
+    hp = ("ozaki" if args.hp == "fp64" else args.hp) if cplx else args.hp
 
     def timed(ref, steps, warmup, host=False):
         for _ in range(warmup):
@@ -471,6 +479,13 @@ def run_ours(args):
         sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, solve_mode=alt_mode, **dtype_opt)
     alt_ms, _, _ = timed(sw, max(1, min(args.steps, 3)), 2)
     sw.close()
+    # the same mixed form with the other emulated engine (digits <-> residues)
+    other_ms, other_hp = None, None
+    if hp in ("ozaki", "crt"):
+        other_hp = "crt" if hp == "ozaki" else "ozaki"
+        oe = P.Refiner(n, hp_gemm=hp_name[other_hp], lp=B.SR_LP_FP32, **dtype_opt)
+        other_ms, _, _ = timed(oe, max(1, min(args.steps, 3)), 2)
+        oe.close()
 
     if rank != 0:
         return 0
@@ -490,8 +505,8 @@ def run_ours(args):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         peak, psrc = bf16_peak(clk, peaks)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": OZ_MMA_TRAFFIC_BYTES_N4096 if (n == 4096 and not cplx and (args.slices or 7) == 7)
-                else None,
+                "traffic": OZ_MMA_TRAFFIC_BYTES_N4096 if (n == 4096 and not cplx and hp == "ozaki" and
+                                                          (args.slices or 7) == 7) else None,
                 "traffic_note": "bytes per launch of the captured 28-pair product (ncu)",
                 "kernel": "ozaki slice products (tcgen05 kind::f16 bf16)",
                 "peak_source": psrc}
@@ -514,7 +529,9 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "c128+c64" if cplx else "f64+f32", "data": "synthetic",
         "config": {"workload": _workload_name(n, cplx, sym), "n": n,
                    "form": "mixed: complex64 solve/products" if cplx else "mixed: FP32 solve/products",
-                   "hp_gemm": hp if hp == "fp64" else f"ozaki-bf16-s{args.slices or 7}",
+                   "hp_gemm": _engine_name(hp, args.slices, dd=False),
+                   "with_other_engine_s": None if other_ms is None else other_ms / 1e3,
+                   "other_engine": None if other_ms is None else _engine_name(other_hp, 0, dd=False),
                    "l2": f"inputs larger than L2 (A {n * n * (16 if cplx else 8) >> 20} MiB + Q + workspace)",
                    "status": status, "iters": nr.iters, "hp_gemms": nr.hp_gemms,
                    "certified": {"stril_rel": rT, "orth": rQ, "tol": tol, "kind": cert_kind,
@@ -704,7 +721,9 @@ def run_dd(args):
         clk = clocks.stop() if clocks else None
         return e0.elapsed_time(e1) / steps, st, nr, clk
 
-    mixed = P.Refiner(n, hp_gemm=B.SR_HP_OZAKI_BF16, profile=1, ozaki_slices=args.slices, **common)
+    dd_hp = {"crt": B.SR_HP_OZAKI_CRT}.get(args.hp, B.SR_HP_OZAKI_BF16)
+    dd_hp_name = "crt" if args.hp == "crt" else "ozaki"
+    mixed = P.Refiner(n, hp_gemm=dd_hp, profile=1, ozaki_slices=args.slices, **common)
     ms, status, nr, clk = timed(mixed, args.steps, args.warmup, Clocks(local))
     prof = mixed.profile()
     rT, rQ = mixed.residuals(A, Q)
@@ -746,9 +765,10 @@ def run_dd(args):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         peak, psrc = bf16_peak(clk, peaks)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": OZ_MMA_TRAFFIC_BYTES_DD2048 if (n == 2048 and (args.slices or 14) == 14) else None,
+                "traffic": OZ_MMA_TRAFFIC_BYTES_DD2048 if (n == 2048 and dd_hp_name == "ozaki" and
+                                                           (args.slices or 14) == 14) else None,
                 "traffic_note": "bytes per launch of the captured 105-pair A Q product (ncu)",
-                "kernel": "ozaki slice products (tcgen05 kind::f16 bf16), 14 digits",
+                "kernel": f"ozaki slice products (tcgen05 kind::f16 bf16), {_engine_name(dd_hp_name, args.slices, True)}",
                 "peak_source": psrc}
     else:
         gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9
@@ -767,7 +787,7 @@ def run_dd(args):
         "vs_baseline": None, "dtype": "dd+f64", "data": "synthetic",
         "config": {"workload": _dd_workload_name(n), "n": n,
                    "form": "double-double hp (emulated, bf16 digits), FP64 solve/products",
-                   "hp_gemm": f"ozaki-bf16-s{args.slices or 14}",
+                   "hp_gemm": _engine_name(dd_hp_name, args.slices, dd=True),
                    "l2": f"inputs larger than L2 (A {2 * n * n * 8 >> 20} MiB + Q + workspace)",
                    "status": status, "iters": nr.iters, "hp_gemms": nr.hp_gemms,
                    "certified": {"stril_rel": rT, "orth": rQ, "tol": tol,
@@ -927,7 +947,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=None)
-    ap.add_argument("--hp", choices=["fp64", "ozaki"], default="ozaki")
+    ap.add_argument("--hp", choices=["fp64", "ozaki", "crt"], default="ozaki")
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-n", type=int, default=None,

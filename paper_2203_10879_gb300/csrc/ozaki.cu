@@ -879,6 +879,116 @@ ozaki_residues_dd_kernel(int R, int K, int Kp, const double *__restrict__ Xh, co
     }
 }
 
+// The same with the modulus count fixed at compile time (16 for FP64 operands,
+// 32 for double-double ones): the modulus loop unrolls and every constant of a
+// modulus is an immediate. The integer X is cut into 16-bit pieces with a
+// signed top piece (two's complement), X = sum_k u_k 2^(16 k), so that
+// v = off + sum_k u_k (2^(16 k) mod m) is a non-negative integer below 2^28
+// with v = X + floor(m/2) (mod m) for either sign of X (off: floor(m/2) plus
+// a multiple of m above the most negative top term). Then
+// s = v - floor(v / m) m - floor(m/2) is the symmetric residue of X, in
+// [-floor(m/2), m - 1 - floor(m/2)], and its bf16 bits come from the FP32
+// value 1.5 2^23 + s (exact) less 1.5 2^23: the top half of the float's bits,
+// since |s| <= 128 has at most 8 significant bits. Each thread turns 4
+// consecutive entries of one vector into residues and stores the 4 bf16
+// values of a modulus at once.
+constexpr int RES_KT = 256;   // K per block of the fixed-count residue kernel
+
+template <int P>
+__device__ __forceinline__ float crt_res_float(const int32_t (&u)[P], int l)
+{
+    const int m = crt_mod(l);
+    int32_t v = (int32_t)crt_off27(l) + m / 2 + u[0];
+#pragma unroll
+    for (int k = 1; k < P; ++k) v += u[k] * (int32_t)crt_pw16(k, l);    // in [0, 2^28)
+    const uint32_t q = __umulhi((uint32_t)v, crt_inv38(l)) >> 6;
+    const int32_t bits = v + (0x4B400000 - m / 2) - (int32_t)q * m;      // 0x4B400000 + s
+    return __fsub_rn(__int_as_float(bits), 12582912.0f);                // s, exactly
+}
+
+// the bf16 bits of two exact small floats, packed (a low, b high)
+__device__ __forceinline__ uint32_t crt_pack_bf16(float a, float b)
+{
+    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+
+// x 2^(t - e) rounded to the nearest integer (|x| < 2^e), as signed 16-bit
+// pieces: P = 4 for t <= 62 (64-bit integer), P = 8 for double-double input
+template <int P>
+__device__ __forceinline__ void crt_pieces(double xh, double xl, int t, int e, int32_t (&u)[P])
+{
+    if constexpr (P == 4) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(xh);
+        const int eb = (int)((bits >> 52) & 0x7ff);
+        unsigned long long mant = bits & 0xfffffffffffffull;
+        int ex;
+        if (eb == 0) ex = -1074; else { mant |= 1ull << 52; ex = eb - 1075; }
+        const int sh = ex + t - e;                // x 2^(t-e) = mant 2^sh, sh < t - 52 <= 10
+        unsigned long long mag;
+        if (mant == 0) mag = 0;
+        else if (sh >= 0) mag = mant << sh;
+        else if (-sh >= 64) mag = 0;
+        else mag = (mant + (1ull << (-sh - 1))) >> (-sh);
+        const long long X = (bits >> 63) ? -(long long)mag : (long long)mag;
+        u[0] = (int32_t)(X & 0xffff);
+        u[1] = (int32_t)((X >> 16) & 0xffff);
+        u[2] = (int32_t)((X >> 32) & 0xffff);
+        u[3] = (int32_t)(X >> 48);                 // signed top piece
+    } else {
+        const __int128 X = dd_fixed_part(xh, t, e) + dd_fixed_part(xl, t, e);
+#pragma unroll
+        for (int k = 0; k < P - 1; ++k) u[k] = (int32_t)((unsigned long long)(X >> (16 * k)) & 0xffffull);
+        u[P - 1] = (int32_t)(long long)(X >> (16 * (P - 1)));   // signed top piece
+    }
+}
+
+template <typename Tin, int LAYOUT, int NM, bool DD>
+__global__ void __launch_bounds__(256)
+ozaki_residues_fast_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, const double *__restrict__ Xl,
+                           int ld, int t, int Pmax, int Kmax, const unsigned long long *__restrict__ vmax,
+                           __nv_bfloat16 *__restrict__ out, int *__restrict__ exps)
+{
+    constexpr int P = DD ? 8 : 4;
+    __shared__ double th[32][33];
+    __shared__ double tl[DD ? 32 : 1][33];
+    __shared__ int sexp[32];
+    const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * RES_KT;
+    if (threadIdx.x < 32) {
+        const int r = r0 + threadIdx.x;
+        const int e = (r < R) ? split_exponent(vmax[r]) : 0;
+        sexp[threadIdx.x] = e;
+        if (blockIdx.y == 0) exps[r] = e;
+    }
+    const int v = threadIdx.x >> 3, g = threadIdx.x & 7;
+    const size_t pstride = (size_t)Pmax * Kmax;
+    for (int k0 = kbeg; k0 < kbeg + RES_KT && k0 < Kp; k0 += 32) {
+        __syncthreads();
+        split_load_tile<Tin, LAYOUT>(th, X, ld, R, K, Kh, r0, k0);
+        if constexpr (DD) split_load_tile<double, LAYOUT>(tl, Xl, ld, R, K, INT_MAX, r0, k0);
+        __syncthreads();
+        const int r = r0 + v, kk = k0 + 4 * g;
+        const int e = sexp[v];
+        const bool live = e != kOzakiExpNonfinite && r < R;
+        int32_t u[4][P];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            if (live) {
+                crt_pieces<P>(th[v][4 * g + x], DD ? tl[v][4 * g + x] : 0.0, t, e, u[x]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < P; ++k) u[x][k] = 0;
+            }
+        }
+        __nv_bfloat16 *o = out + (size_t)r * Kmax + (size_t)kk;
+#pragma unroll
+        for (int l = 0; l < NM; ++l) {
+            const uint32_t w01 = crt_pack_bf16(crt_res_float<P>(u[0], l), crt_res_float<P>(u[1], l));
+            const uint32_t w23 = crt_pack_bf16(crt_res_float<P>(u[2], l), crt_res_float<P>(u[3], l));
+            *reinterpret_cast<uint2 *>(o + (size_t)l * pstride) = make_uint2(w01, w23);
+        }
+    }
+}
+
 // Splits levels 0..s-1 (level l costs l + 1 digit pairs) into G contiguous
 // non-empty groups minimising the largest group cost (linear partition by
 // dynamic programming); returns that cost.
@@ -1031,12 +1141,15 @@ bool crt_build_table(int N, int L, CrtTable &t)
     t = CrtTable{};
     t.N = N;
     // the largest integers <= 256 that are coprime to every one taken before
+    // (the list crt_mod holds as literals for the device code)
     int cnt = 0;
     for (int m = 256; m >= 2 && cnt < N; --m) {
         bool ok = true;
         for (int k = 0; k < cnt && ok; ++k) ok = std::gcd(m, t.m[k]) == 1;
         if (ok) t.m[cnt++] = m;
     }
+    for (int l = 0; l < N; ++l)
+        if (t.m[l] != crt_mod(l)) return false;
     Big M;
     M.v[0] = 1;
     for (int l = 0; l < N; ++l) M.mul_small((uint32_t)t.m[l]);
@@ -1169,9 +1282,13 @@ sr_status ozaki_split(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int sl
     SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)Rp * sizeof(unsigned long long), st));
     const dim3 gmax(Rp / 32, (Kv + SPLIT_KT - 1) / SPLIT_KT);
     const dim3 gdig(Rp / 32, (Kp + DIGIT_KT - 1) / DIGIT_KT);
+    const dim3 gres(Rp / 32, (Kp + RES_KT - 1) / RES_KT);
 #define SR_SPLIT_LAUNCH(TIN, LAY)                                                                                 \
     ozaki_absmax_kernel<TIN, LAY><<<gmax, 256, 0, st>>>(R, K, Kh, Kv, (const TIN *)X, ld, w.vmax);                \
-    if (sl.crt)                                                                                                   \
+    if (sl.crt && s == 16)                                                                                        \
+        ozaki_residues_fast_kernel<TIN, LAY, 16, false><<<gres, 256, 0, st>>>(                                    \
+            R, K, Kh, Kp, (const TIN *)X, nullptr, ld, sl.t, w.Pmax, w.Kmax, w.vmax, out, ex);                    \
+    else if (sl.crt)                                                                                              \
         ozaki_residues_kernel<TIN, LAY><<<gdig, 256, 0, st>>>(R, K, Kh, Kp, (const TIN *)X, ld, sl.t, s, w.Pmax,  \
                                                               w.Kmax, w.vmax, out, ex, w.crt_dev);                \
     else                                                                                                          \
@@ -1208,9 +1325,13 @@ sr_status ozaki_split_dd(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int
     SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)Rp * sizeof(unsigned long long), st));
     const dim3 gmax(Rp / 32, (K + SPLIT_KT - 1) / SPLIT_KT);
     const dim3 gdig(Rp / 32, (Kp + DIGIT_KT - 1) / DIGIT_KT);
+    const dim3 gres(Rp / 32, (Kp + RES_KT - 1) / RES_KT);
     if (layout == OZ_COLS) {
         ozaki_absmax_kernel<double, OZ_COLS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, Xhi, ld, w.vmax);
-        if (sl.crt)
+        if (sl.crt && s == 32)
+            ozaki_residues_fast_kernel<double, OZ_COLS, 32, true><<<gres, 256, 0, st>>>(
+                R, K, INT_MAX, Kp, Xhi, Xlo, ld, sl.t, w.Pmax, w.Kmax, w.vmax, out, ex);
+        else if (sl.crt)
             ozaki_residues_dd_kernel<OZ_COLS><<<gdig, 256, 0, st>>>(R, K, Kp, Xhi, Xlo, ld, sl.t, s, w.Pmax, w.Kmax,
                                                                     w.vmax, out, ex, w.crt_dev);
         else
@@ -1218,7 +1339,10 @@ sr_status ozaki_split_dd(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int
                                                                   out, ex);
     } else {
         ozaki_absmax_kernel<double, OZ_ROWS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, Xhi, ld, w.vmax);
-        if (sl.crt)
+        if (sl.crt && s == 32)
+            ozaki_residues_fast_kernel<double, OZ_ROWS, 32, true><<<gres, 256, 0, st>>>(
+                R, K, INT_MAX, Kp, Xhi, Xlo, ld, sl.t, w.Pmax, w.Kmax, w.vmax, out, ex);
+        else if (sl.crt)
             ozaki_residues_dd_kernel<OZ_ROWS><<<gdig, 256, 0, st>>>(R, K, Kp, Xhi, Xlo, ld, sl.t, s, w.Pmax, w.Kmax,
                                                                     w.vmax, out, ex, w.crt_dev);
         else

@@ -77,6 +77,37 @@ constexpr int kCrtDefaultModuli = 16;     // FP64 operands: t = 56 bits at K <= 
 constexpr int kCrtDefaultModuliDD = 32;   // double-double operands: t = 113 bits at K <= 8192
 constexpr int kCrtMaxLimbs = 8;           // 32-bit limbs of M (4 for N <= 16, 8 for N <= 32)
 
+// The moduli in order: the largest pairwise coprime integers <= 256 taken
+// greedily from 256 down (the host table builder computes the same list).
+// A function of literals, so that in fully unrolled device loops every
+// constant derived from a modulus folds into an immediate.
+__host__ __device__ constexpr int crt_mod(int l)
+{
+    constexpr int kList[kCrtMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223,
+                                          217, 211, 199, 197, 193, 191, 181, 179, 173, 167, 163,
+                                          157, 151, 149, 139, 137, 131, 127, 113, 109, 107};
+    return l >= 0 && l < kCrtMaxModuli ? kList[l] : 1;
+}
+// 2^(16 k) mod m_l
+__host__ __device__ constexpr uint32_t crt_pw16(int k, int l)
+{
+    unsigned long long p = 1;
+    for (int i = 0; i < k; ++i) p = (p * 65536ull) % (unsigned long long)crt_mod(l);
+    return (uint32_t)(p % (unsigned long long)crt_mod(l));
+}
+// ceil(2^38 / m_l): for 0 <= v < 2^28, floor(v / m) = (v * inv38) >> 38 (the
+// rounding up adds less than v / 2^38 < 2^-10 < 1/m, and v / m is at least
+// 1/m below the next integer); it fits 32 bits for every m >= 65
+__host__ __device__ constexpr uint32_t crt_inv38(int l)
+{
+    return (uint32_t)(((1ull << 38) + (unsigned long long)crt_mod(l) - 1) / (unsigned long long)crt_mod(l));
+}
+// a multiple of m_l that is at least 2^27
+__host__ __device__ constexpr uint32_t crt_off27(int l)
+{
+    return (uint32_t)crt_mod(l) * (((1u << 27) + (uint32_t)crt_mod(l) - 1) / (uint32_t)crt_mod(l));
+}
+
 // Moduli, CRT weights and the constants of the residue kernels (host-built,
 // one copy per work area in device memory).
 struct CrtTable {
@@ -466,7 +497,7 @@ ozaki_combine_dd_kernel(int m, int n, int s, const int32_t *__restrict__ planes,
 
 // ---- residue form: rebuild by the Chinese remainder theorem -------------------------
 // The table's part the rebuild needs, staged in shared memory by every block.
-struct CrtRebuildSm {
+struct __align__(16) CrtRebuildSm {
     unsigned w[kCrtMaxModuli][kCrtMaxLimbs];
     unsigned M[kCrtMaxLimbs], halfM[kCrtMaxLimbs];
     float invMtop;
@@ -489,74 +520,79 @@ __device__ __forceinline__ void crt_stage(CrtRebuildSm &sm, const CrtTable *__re
 
 // S' = sum_l R_l w'_l is given as per-limb column sums acc[k] (no carries yet;
 // each below 2^45). Returns the sign of r = S' mod M' taken in (-M'/2, M'/2]
-// and writes |r| to mag (r = C 2^sigma for the rebuilt integer C).
+// and writes |r| to mag (r = C 2^sigma for the rebuilt integer C). The value
+// is carried as 64-bit limbs with 128-bit temporaries for the carries.
 template <int L>
 __device__ __forceinline__ bool crt_reduce(const unsigned long long (&acc)[L], const CrtRebuildSm &T,
                                            uint32_t (&mag)[L])
 {
-    uint32_t S[L + 1];
+    constexpr int H = L / 2;
+    using u128 = unsigned __int128;
+    unsigned long long S[H];
     unsigned long long c = 0;
+    uint32_t lo32 = 0;
 #pragma unroll
     for (int k = 0; k < L; ++k) {
         const unsigned long long v = acc[k] + c;
-        S[k] = (uint32_t)v;
         c = v >> 32;
+        if (k & 1) S[k >> 1] = ((unsigned long long)(uint32_t)v << 32) | lo32; else lo32 = (uint32_t)v;
     }
-    S[L] = (uint32_t)c;
+    uint32_t top = (uint32_t)c;                       // S' = top 2^(32 L) + S
+    const unsigned long long *Mw = reinterpret_cast<const unsigned long long *>(T.M);
+    const unsigned long long *Hw = reinterpret_cast<const unsigned long long *>(T.halfM);
     // q = floor(S'/M') < 2^13 from the top 64 bits (M' has its top bit at 32 L - 1),
     // lowered by one: the estimate is within 0.01 of S'/M', so 0 <= S' - q M' < 3 M'
-    const float est = ((float)S[L] * 4294967296.0f + (float)S[L - 1]) * T.invMtop;
-    int q = (int)est - 1;
-    q = q < 0 ? 0 : q;
-    unsigned long long cm = 0;
-    long long br = 0;
+    const float est = ((float)top * 4294967296.0f + (float)(uint32_t)(S[H - 1] >> 32)) * T.invMtop;
+    const int qi = (int)est - 1;
+    const unsigned long long q = (unsigned long long)(qi < 0 ? 0 : qi);
+    unsigned long long cm = 0, br = 0;
 #pragma unroll
-    for (int k = 0; k < L; ++k) {
-        const unsigned long long pk = (unsigned long long)(uint32_t)q * T.M[k] + cm;
-        cm = pk >> 32;
-        const long long d = (long long)S[k] - (long long)(uint32_t)pk + br;
-        S[k] = (uint32_t)d;
-        br = d >> 32;
+    for (int h = 0; h < H; ++h) {
+        const u128 p = (u128)q * Mw[h] + cm;
+        cm = (unsigned long long)(p >> 64);
+        const u128 d = (u128)S[h] - (unsigned long long)p - br;
+        S[h] = (unsigned long long)d;
+        br = (unsigned long long)(d >> 64) & 1ull;
     }
-    S[L] = (uint32_t)((long long)S[L] - (long long)cm + br);
+    top = top - (uint32_t)cm - (uint32_t)br;
     // at most two subtractions of M' bring S' into [0, M')
 #pragma unroll
     for (int rep = 0; rep < 2; ++rep) {
-        uint32_t d[L + 1];
-        long long b = 0;
+        unsigned long long d[H];
+        unsigned long long b = 0;
 #pragma unroll
-        for (int k = 0; k < L; ++k) {
-            const long long x = (long long)S[k] - (long long)T.M[k] + b;
-            d[k] = (uint32_t)x;
-            b = x >> 32;
+        for (int h = 0; h < H; ++h) {
+            const u128 x = (u128)S[h] - Mw[h] - b;
+            d[h] = (unsigned long long)x;
+            b = (unsigned long long)(x >> 64) & 1ull;
         }
-        const long long x = (long long)S[L] + b;
-        d[L] = (uint32_t)x;
-        if ((x >> 32) == 0) {
+        if ((int)top - (int)b >= 0) {
+            top -= (uint32_t)b;
 #pragma unroll
-            for (int k = 0; k <= L; ++k) S[k] = d[k];
+            for (int h = 0; h < H; ++h) S[h] = d[h];
         }
     }
     // symmetric range: r > M'/2 stands for r - M'
     bool gt = false, decided = false;
 #pragma unroll
-    for (int k = L - 1; k >= 0; --k) {
-        if (!decided && S[k] != T.halfM[k]) {
-            gt = S[k] > T.halfM[k];
+    for (int h = H - 1; h >= 0; --h)
+        if (!decided && S[h] != Hw[h]) {
+            gt = S[h] > Hw[h];
             decided = true;
         }
-    }
     if (gt) {
-        long long b = 0;
+        unsigned long long b = 0;
 #pragma unroll
-        for (int k = 0; k < L; ++k) {
-            const long long x = (long long)T.M[k] - (long long)S[k] + b;
-            mag[k] = (uint32_t)x;
-            b = x >> 32;
+        for (int h = 0; h < H; ++h) {
+            const u128 x = (u128)Mw[h] - S[h] - b;
+            S[h] = (unsigned long long)x;
+            b = (unsigned long long)(x >> 64) & 1ull;
         }
-    } else {
+    }
 #pragma unroll
-        for (int k = 0; k < L; ++k) mag[k] = S[k];
+    for (int h = 0; h < H; ++h) {
+        mag[2 * h] = (uint32_t)S[h];
+        mag[2 * h + 1] = (uint32_t)(S[h] >> 32);
     }
     return gt;
 }
@@ -634,7 +670,7 @@ crt_value(const uint8_t *__restrict__ planes, size_t off, size_t pstride, const 
 // mirrored block (coalesced along the planes' contiguous index) and turns it
 // in shared memory; entries below the diagonal of a diagonal block read the
 // mirrored position directly.
-template <class EP, bool CPLX, int L>
+template <class EP, bool CPLX, int L, int NM>
 __global__ void __launch_bounds__(256)
 ozaki_crt_combine_kernel(int m, int n, const uint8_t *__restrict__ planes, int ldp, size_t pstride, size_t imoff,
                          const int *__restrict__ ea, const int *__restrict__ fb, int tsum, double sign, int mirror,
@@ -662,13 +698,35 @@ ozaki_crt_combine_kernel(int m, int n, const uint8_t *__restrict__ planes, int l
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int k = 0; k < L; ++k) acc[u][k] = 0ull;
-        for (int l = 0; l < N; ++l) {
-            const uint32_t r4 = *reinterpret_cast<const uint32_t *>(planes + base + (size_t)l * pstride);
+        if constexpr (NM > 0) {
+            // the modulus count is fixed: every plane's word is loaded before the sums
+            uint32_t r4[NM];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t R = (r4 >> (8 * u)) & 255u;
+            for (int l = 0; l < NM; ++l) r4[l] = *reinterpret_cast<const uint32_t *>(planes + base + (size_t)l * pstride);
 #pragma unroll
-                for (int k = 0; k < L; ++k) acc[u][k] += (unsigned long long)R * T.w[l][k];
+            for (int l = 0; l < NM; ++l) {
+                uint32_t wl[L];
+#pragma unroll
+                for (int k = 0; k < L; k += 4) {
+                    const uint4 w4 = *reinterpret_cast<const uint4 *>(&T.w[l][k]);
+                    wl[k] = w4.x; wl[k + 1] = w4.y; wl[k + 2] = w4.z; wl[k + 3] = w4.w;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t R = (r4[l] >> (8 * u)) & 255u;
+#pragma unroll
+                    for (int k = 0; k < L; ++k) acc[u][k] += (unsigned long long)R * wl[k];
+                }
+            }
+        } else {
+            for (int l = 0; l < N; ++l) {
+                const uint32_t r4 = *reinterpret_cast<const uint32_t *>(planes + base + (size_t)l * pstride);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t R = (r4 >> (8 * u)) & 255u;
+#pragma unroll
+                    for (int k = 0; k < L; ++k) acc[u][k] += (unsigned long long)R * T.w[l][k];
+                }
             }
         }
 #pragma unroll
@@ -765,17 +823,27 @@ sr_status ozaki_combine(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
         if constexpr (ep_is_dd<EP>::value) {
             if (w.cplx || w.crt.L != 8) return SR_ERR_INVALID_ARG;
             SrPhase ph(h, SR_PROF_OZ_COMBINE, 16LL * 8 * s * m * n, (long long)m * n * (1LL * s + 32), 1);
-            ozaki_crt_combine_kernel<EP, false, 8><<<grid, 256, 0, st>>>(
-                m, n, pl, w.Pmax, (size_t)w.Pmax * w.Pmax, 0, w.slot[rows].exps, w.slot[cols].exps, tsum, sign,
-                mirror ? 1 : 0, ep, partial, w.crt_dev);
+            if (s == kCrtDefaultModuliDD)
+                ozaki_crt_combine_kernel<EP, false, 8, kCrtDefaultModuliDD><<<grid, 256, 0, st>>>(
+                    m, n, pl, w.Pmax, (size_t)w.Pmax * w.Pmax, 0, w.slot[rows].exps, w.slot[cols].exps, tsum, sign,
+                    mirror ? 1 : 0, ep, partial, w.crt_dev);
+            else
+                ozaki_crt_combine_kernel<EP, false, 8, 0><<<grid, 256, 0, st>>>(
+                    m, n, pl, w.Pmax, (size_t)w.Pmax * w.Pmax, 0, w.slot[rows].exps, w.slot[cols].exps, tsum, sign,
+                    mirror ? 1 : 0, ep, partial, w.crt_dev);
         } else {
             constexpr bool CPLX = ep_is_complex<EP>::value;
             const int c = CPLX ? 2 : 1;
             if (CPLX != w.cplx || w.crt.L != 4) return SR_ERR_INVALID_ARG;
             SrPhase ph(h, SR_PROF_OZ_COMBINE, 8LL * c * s * m * n, (long long)m * n * (1LL * c * s + 16 * c), 1);
-            ozaki_crt_combine_kernel<EP, CPLX, 4><<<grid, 256, 0, st>>>(
-                m, n, pl, w.Pmax, (size_t)c * w.Pmax * w.Pmax, (size_t)w.Pmax * w.Pmax, w.slot[rows].exps,
-                w.slot[cols].exps, tsum, sign, mirror ? 1 : 0, ep, partial, w.crt_dev);
+            if (s == kCrtDefaultModuli)
+                ozaki_crt_combine_kernel<EP, CPLX, 4, kCrtDefaultModuli><<<grid, 256, 0, st>>>(
+                    m, n, pl, w.Pmax, (size_t)c * w.Pmax * w.Pmax, (size_t)w.Pmax * w.Pmax, w.slot[rows].exps,
+                    w.slot[cols].exps, tsum, sign, mirror ? 1 : 0, ep, partial, w.crt_dev);
+            else
+                ozaki_crt_combine_kernel<EP, CPLX, 4, 0><<<grid, 256, 0, st>>>(
+                    m, n, pl, w.Pmax, (size_t)c * w.Pmax * w.Pmax, (size_t)w.Pmax * w.Pmax, w.slot[rows].exps,
+                    w.slot[cols].exps, tsum, sign, mirror ? 1 : 0, ep, partial, w.crt_dev);
         }
         SR_CUDA_TRY(cudaGetLastError());
         if (blocks) *blocks = ozaki_blocks(m, n);
