@@ -404,7 +404,7 @@ def run_ours(args):
         return e0.elapsed_time(e1) / steps, st, nr
 
     # ---- mixed form (the measured path) --------------------------------------------
-    mixed = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, profile=1, **dtype_opt)
+    mixed = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, profile=1, lp_slices=args.lp_slices, **dtype_opt)
     for _ in range(args.warmup):
         mixed.step(A, Q, Qhat, check=False)
     mixed.reset_profile()
@@ -530,6 +530,7 @@ def run_ours(args):
         "config": {"workload": _workload_name(n, cplx, sym), "n": n,
                    "form": "mixed: complex64 solve/products" if cplx else "mixed: FP32 solve/products",
                    "hp_gemm": _engine_name(hp, args.slices, dd=False),
+                   "lp_products": f"emulated, {args.lp_slices or 3} bf16 digits per operand",
                    "with_other_engine_s": None if other_ms is None else other_ms / 1e3,
                    "other_engine": None if other_ms is None else _engine_name(other_hp, 0, dd=False),
                    "l2": f"inputs larger than L2 (A {n * n * (16 if cplx else 8) >> 20} MiB + Q + workspace)",
@@ -949,6 +950,8 @@ def main():
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--hp", choices=["fp64", "ozaki", "crt"], default="ozaki")
     ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--lp-slices", type=int, default=0,
+                    help="digits of the FP32-class products YW, W^2, W^3 (mixed form; 0 = 3)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-n", type=int, default=None,
                     help="order of the oracle's bounded sample (reference arm, one-thread baseline)")

@@ -160,6 +160,13 @@ typedef struct {
                          before the entries computed after it use it; the
                          paper's example value is 1e-5. 0 (default): off.
                          Negative, NaN or infinite: SR_ERR_INVALID_ARG */
+    int lp_slices;    /* the mixed form with emulated products (lp =
+                         SR_LP_FP32): bf16 digits per operand of the
+                         low-precision products YW, W^2, W^3 (Alg. 4, "can
+                         all be computed in lp"): 3 (default, <= 0) carries
+                         23 fraction bits, FP32-class; 2 carries 15 bits
+                         (3 digit pairs instead of 6); 1 carries 7 bits, a
+                         single bf16 product. More than 3: SR_ERR_INVALID_ARG */
 } sr_options;
 
 /* Fills *opt with the defaults: real, FP64 target, native FP64 products,

@@ -180,7 +180,8 @@ bool sr_batch_supported(const sr_options &o)
 {
     return o.dtype == SR_REAL && o.target == SR_TARGET_FP64 && o.hp_gemm == SR_HP_OZAKI_BF16 &&
            o.lp == SR_LP_FP32 && o.qhat_type == SR_QHAT_FP32 && !o.full_sigma && sr::kOzakiBuilt &&
-           (o.ozaki_slices <= 0 || o.ozaki_slices == kHp) && !o.symmetric;
+           (o.ozaki_slices <= 0 || o.ozaki_slices == kHp) && (o.lp_slices <= 0 || o.lp_slices == kLp) &&
+           !o.symmetric;
 }
 
 namespace {

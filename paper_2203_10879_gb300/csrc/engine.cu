@@ -190,7 +190,7 @@ sr_status check_opts(const sr_options &o)
     if (o.qhat_type != SR_QHAT_FP32 && o.qhat_type != SR_QHAT_FP64) return SR_ERR_INVALID_ARG;
     if ((o.batch_mode != 0 && o.batch_mode != 1) || (o.tune != 0 && o.tune != 1) || (o.graph != 0 && o.graph != 1) ||
         o.solve_mode < 0 || o.solve_mode > 2 || (o.symmetric != 0 && o.symmetric != 1) || !(o.l_cap >= 0.0) ||
-        std::isinf(o.l_cap))
+        std::isinf(o.l_cap) || o.lp_slices > sr::kOzakiLpSlices)
         return SR_ERR_INVALID_ARG;
     if (o.hp_gemm == SR_HP_OZAKI_CRT) {
         // FP64 results: M < 2^128 holds for at most 16 moduli; double-double: 32
@@ -588,7 +588,7 @@ sr_status oz_update(schur_refine_ctx *h, int n, const void *Q, int ldq, void *Qn
     using H = typename OzT<C>::H;
     using L = typename OzT<C>::L;
     using Store = typename OzT<C>::Store;
-    const int ld = h->nmax, sl = kOzakiLpSlices;
+    const int ld = h->nmax, sl = h->opt.lp_slices > 0 ? h->opt.lp_slices : kOzakiLpSlices;
     OzakiWork &w = h->oz;
     cudaStream_t st = h->st;
     H *Wd = (H *)h->Wd, *W2d = (H *)h->W2d, *W2Yd = (H *)h->W2Yd, *W2YWd = (H *)h->W2YWd, *Y = (H *)h->Y;
@@ -1304,6 +1304,7 @@ void schur_refine_default_options(sr_options *opt)
     opt->solve_mode = 0;
     opt->symmetric = 0;
     opt->l_cap = 0.0;
+    opt->lp_slices = 0;
 }
 
 const char *schur_refine_status_string(sr_status s)
