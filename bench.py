@@ -43,6 +43,9 @@ BF16_NOMINAL_TFLOPS = 2250.0
 # workload); valid for that kernel version and size only
 OZ_MMA_TRAFFIC_BYTES_N4096 = 5.771999e9 + 0.471991e9
 OZ_MMA_TRAFFIC_BYTES_DD2048 = 1.625545e9 + 0.222098e9
+# the same for the residue form: the 16-modulus T^ product at n = 4096
+# (profiles/ozaki_mma_kernel_crt_n4096.md)
+OZ_MMA_TRAFFIC_BYTES_CRT_N4096 = 2.818361e9 + 0.262020e9
 
 
 def phase_rooflines(prof, steps):
@@ -348,6 +351,73 @@ def certify_complex(A, Q, stream):
     return r_t, r_q
 
 
+def _comparisons(args, mixed, p, n, cplx, sym, hp, hp_name, hdt, ldt, dtype_opt, timed, barrier, dist, A, Q, Qhat):
+    """The parts of the single-matrix line beside the measured path: the end-to-end
+    call from pinned host buffers, the all-FP64 form, the mixed form with native FP64
+    products, with the other solve form and with the other emulated engine."""
+    import numpy as np
+    import torch
+
+    import paper_2203_10879_gb300 as P
+    from paper_2203_10879_gb300 import _binding as B
+
+    # ---- end to end through host buffers --------------------------------------------
+    hA = torch.from_numpy(np.ascontiguousarray(p.A.T)).pin_memory()
+    hQh = torch.from_numpy(np.ascontiguousarray(p.Qhat.T)).pin_memory()
+    hQ = torch.empty((n, n), dtype=hdt).pin_memory()
+    dA_t = torch.empty((n, n), dtype=hdt, device="cuda")
+    dQh_t = torch.empty((n, n), dtype=ldt, device="cuda")
+    dQ_t = torch.empty((n, n), dtype=hdt, device="cuda")
+    ke = max(1, min(args.steps, 3))
+    for i in range(1 + ke):
+        if i == 1:
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+        dA_t.copy_(hA, non_blocking=True)
+        dQh_t.copy_(hQh, non_blocking=True)
+        mixed.step(dA_t.t(), dQ_t.t(), dQh_t.t(), check=False)
+        hQ.copy_(dQ_t, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    mixed.close()
+
+    # ---- all-FP64 form of the same iteration on the same inputs -----------------------
+    k64 = max(1, min(args.steps, args.fp64_steps))
+    ms64 = st64 = nr64 = None
+    prof64 = {}
+    if not cplx:
+        allfp64 = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP64, profile=1, **dtype_opt)
+        ms64, st64, nr64 = timed(allfp64, k64, 1)
+        prof64 = allfp64.profile()
+        allfp64.close()
+    mixed_native_ms = None
+    if hp != "fp64" and not cplx:
+        mn = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP32, **dtype_opt)
+        mixed_native_ms, _, _ = timed(mn, k64, 1)
+        mn.close()
+    # the same mixed form with the other form of the solve: stepwise (one launch
+    # pair per block subdiagonal) for real data, dataflow (one launch) for complex;
+    # for symmetric A the general form (triangular solve instead of Sec. 2.5's)
+    if sym:
+        sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32)
+    else:
+        alt_mode = 1 if cplx else 2
+        sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, solve_mode=alt_mode, **dtype_opt)
+    alt_ms, _, _ = timed(sw, max(1, min(args.steps, 3)), 2)
+    sw.close()
+    # the same mixed form with the other emulated engine (digits <-> residues)
+    other_ms, other_hp = None, None
+    if hp in ("ozaki", "crt"):
+        other_hp = "crt" if hp == "ozaki" else "ozaki"
+        oe = P.Refiner(n, hp_gemm=hp_name[other_hp], lp=B.SR_LP_FP32, **dtype_opt)
+        other_ms, _, _ = timed(oe, max(1, min(args.steps, 3)), 2)
+        oe.close()
+
+    return e2e_s, ms64, st64, nr64, prof64, mixed_native_ms, alt_ms, other_ms, other_hp
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -433,59 +503,16 @@ def run_ours(args):
     ms = max_over_ranks(ms, dist, "cuda")
     launches = int(sum(v["launches"] for v in prof.values()))
 
-    # ---- end to end through host buffers --------------------------------------------
-    hA = torch.from_numpy(np.ascontiguousarray(p.A.T)).pin_memory()
-    hQh = torch.from_numpy(np.ascontiguousarray(p.Qhat.T)).pin_memory()
-    hQ = torch.empty((n, n), dtype=hdt).pin_memory()
-    dA_t = torch.empty((n, n), dtype=hdt, device="cuda")
-    dQh_t = torch.empty((n, n), dtype=ldt, device="cuda")
-    dQ_t = torch.empty((n, n), dtype=hdt, device="cuda")
-    ke = max(1, min(args.steps, 3))
-    for i in range(1 + ke):
-        if i == 1:
-            torch.cuda.synchronize()
-            barrier()
-            t0 = time.perf_counter()
-        dA_t.copy_(hA, non_blocking=True)
-        dQh_t.copy_(hQh, non_blocking=True)
-        mixed.step(dA_t.t(), dQ_t.t(), dQh_t.t(), check=False)
-        hQ.copy_(dQ_t, non_blocking=True)
-        torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / ke
-    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
-    mixed.close()
-
-    # ---- all-FP64 form of the same iteration on the same inputs -----------------------
-    k64 = max(1, min(args.steps, args.fp64_steps))
+    e2e_s = None
     ms64 = st64 = nr64 = None
     prof64 = {}
-    if not cplx:
-        allfp64 = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP64, profile=1, **dtype_opt)
-        ms64, st64, nr64 = timed(allfp64, k64, 1)
-        prof64 = allfp64.profile()
-        allfp64.close()
-    mixed_native_ms = None
-    if hp != "fp64" and not cplx:
-        mn = P.Refiner(n, hp_gemm=B.SR_HP_FP64, lp=B.SR_LP_FP32, **dtype_opt)
-        mixed_native_ms, _, _ = timed(mn, k64, 1)
-        mn.close()
-    # the same mixed form with the other form of the solve: stepwise (one launch
-    # pair per block subdiagonal) for real data, dataflow (one launch) for complex;
-    # for symmetric A the general form (triangular solve instead of Sec. 2.5's)
-    if sym:
-        sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32)
+    mixed_native_ms = alt_ms = other_ms = other_hp = None
+    k64 = max(1, min(args.steps, args.fp64_steps))
+    if args.measured_only:
+        mixed.close()
     else:
-        alt_mode = 1 if cplx else 2
-        sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, solve_mode=alt_mode, **dtype_opt)
-    alt_ms, _, _ = timed(sw, max(1, min(args.steps, 3)), 2)
-    sw.close()
-    # the same mixed form with the other emulated engine (digits <-> residues)
-    other_ms, other_hp = None, None
-    if hp in ("ozaki", "crt"):
-        other_hp = "crt" if hp == "ozaki" else "ozaki"
-        oe = P.Refiner(n, hp_gemm=hp_name[other_hp], lp=B.SR_LP_FP32, **dtype_opt)
-        other_ms, _, _ = timed(oe, max(1, min(args.steps, 3)), 2)
-        oe.close()
+        e2e_s, ms64, st64, nr64, prof64, mixed_native_ms, alt_ms, other_ms, other_hp = _comparisons(
+            args, mixed, p, n, cplx, sym, hp, hp_name, hdt, ldt, dtype_opt, timed, barrier, dist, A, Q, Qhat)
 
     if rank != 0:
         return 0
@@ -505,9 +532,11 @@ def run_ours(args):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         peak, psrc = bf16_peak(clk, peaks)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": OZ_MMA_TRAFFIC_BYTES_N4096 if (n == 4096 and not cplx and hp == "ozaki" and
-                                                          (args.slices or 7) == 7) else None,
-                "traffic_note": "bytes per launch of the captured 28-pair product (ncu)",
+                "traffic": (OZ_MMA_TRAFFIC_BYTES_N4096 if hp == "ozaki" and (args.slices or 7) == 7 else
+                            OZ_MMA_TRAFFIC_BYTES_CRT_N4096 if hp == "crt" and (args.slices or 16) == 16 else None)
+                if (n == 4096 and not cplx) else None,
+                "traffic_note": ("bytes per launch of the captured 16-modulus T^ product (ncu)" if hp == "crt" else
+                                 "bytes per launch of the captured 28-pair product (ncu)"),
                 "kernel": "ozaki slice products (tcgen05 kind::f16 bf16)",
                 "peak_source": psrc}
     else:
@@ -543,15 +572,16 @@ def run_ours(args):
                    "mixed_native_fp64_s": None if mixed_native_ms is None else mixed_native_ms / 1e3,
                    "solve_form": "stepwise (launch pair per block subdiagonal)" if cplx
                    else ("elementwise (Sec. 2.5, symmetric A)" if sym else "dataflow (one launch per solve)"),
-                   "with_other_solve_form_s": alt_ms / 1e3,
+                   "with_other_solve_form_s": None if alt_ms is None else alt_ms / 1e3,
                    "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
                    "phase_rates": phase_rooflines(prof, args.steps),
                    "all_fp64_phase_ms_per_step": {k: v["ms"] / k64 for k, v in prof64.items() if v["ms"] > 0},
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n * n * (8 + 4) * (2 if cplx else 1)),
-                "d2h_bytes_per_step": int(n * n * 8 * (2 if cplx else 1))},
+        "e2e": None if e2e_s is None else {
+            "value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n * n * (8 + 4) * (2 if cplx else 1)),
+            "d2h_bytes_per_step": int(n * n * 8 * (2 if cplx else 1))},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -670,6 +700,43 @@ def _dd_workload_name(n):
             f"FP64 lp to ||stril||/||A||<=1e-28 n")
 
 
+def _dd_comparisons(args, mixed, p, n, common, timed, barrier, k64):
+    """Beside the double-double line's measured path: the end-to-end call from pinned
+    host buffers and the same iteration with SIMT double-double products."""
+    import numpy as np
+    import torch
+
+    import paper_2203_10879_gb300 as P
+    from paper_2203_10879_gb300 import _binding as B
+
+    # end to end through pinned host buffers
+    hA = torch.from_numpy(np.ascontiguousarray(np.hstack([p.A_hi, p.A_lo]).T)).pin_memory()
+    hQh = torch.from_numpy(np.ascontiguousarray(p.Qhat.T)).pin_memory()
+    hQ = torch.empty((2 * n, n), dtype=torch.float64).pin_memory()
+    dA_t = torch.empty((2 * n, n), dtype=torch.float64, device="cuda")
+    dQh_t = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    dQ_t = torch.empty((2 * n, n), dtype=torch.float64, device="cuda")
+    ke = max(1, min(args.steps, 3))
+    for i in range(1 + ke):
+        if i == 1:
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+        dA_t.copy_(hA, non_blocking=True)
+        dQh_t.copy_(hQh, non_blocking=True)
+        mixed.step(dA_t.t(), dQ_t.t(), dQh_t.t(), check=False)
+        hQ.copy_(dQ_t, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke
+    mixed.close()
+    # the same iteration with SIMT double-double products (FP64 error-free transformations)
+    simt = P.Refiner(n, hp_gemm=B.SR_HP_FP64, profile=1, **common)
+    ms64, st64, nr64, _ = timed(simt, k64, 1)
+    prof64 = simt.profile()
+    simt.close()
+    return e2e_s, ms64, st64, nr64, prof64
+
+
 def run_dd(args):
     """The double-double workload: one step = one refinement of the n = 2048
     planted double-double problem from its FP64 start to ||stril||/||A|| <= 1e-28 n.
@@ -730,32 +797,13 @@ def run_dd(args):
     rT, rQ = mixed.residuals(A, Q)
     launches = int(sum(v["launches"] for v in prof.values()))
     ms = max_over_ranks(ms, dist, "cuda")
-    # end to end through pinned host buffers
-    hA = torch.from_numpy(np.ascontiguousarray(np.hstack([p.A_hi, p.A_lo]).T)).pin_memory()
-    hQh = torch.from_numpy(np.ascontiguousarray(p.Qhat.T)).pin_memory()
-    hQ = torch.empty((2 * n, n), dtype=torch.float64).pin_memory()
-    dA_t = torch.empty((2 * n, n), dtype=torch.float64, device="cuda")
-    dQh_t = torch.empty((n, n), dtype=torch.float64, device="cuda")
-    dQ_t = torch.empty((2 * n, n), dtype=torch.float64, device="cuda")
-    ke = max(1, min(args.steps, 3))
-    for i in range(1 + ke):
-        if i == 1:
-            torch.cuda.synchronize()
-            barrier()
-            t0 = time.perf_counter()
-        dA_t.copy_(hA, non_blocking=True)
-        dQh_t.copy_(hQh, non_blocking=True)
-        mixed.step(dA_t.t(), dQ_t.t(), dQh_t.t(), check=False)
-        hQ.copy_(dQ_t, non_blocking=True)
-        torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / ke
-    mixed.close()
-    # the same iteration with SIMT double-double products (FP64 error-free transformations)
-    simt = P.Refiner(n, hp_gemm=B.SR_HP_FP64, profile=1, **common)
+    e2e_s = ms64 = st64 = nr64 = None
+    prof64 = {}
     k64 = max(1, min(args.steps, args.fp64_steps))
-    ms64, st64, nr64, _ = timed(simt, k64, 1)
-    prof64 = simt.profile()
-    simt.close()
+    if args.measured_only:
+        mixed.close()
+    else:
+        e2e_s, ms64, st64, nr64, prof64 = _dd_comparisons(args, mixed, p, n, common, timed, barrier, k64)
     if rank != 0:
         return 0
     peaks = _peaks()
@@ -771,6 +819,13 @@ def run_dd(args):
                 "traffic_note": "bytes per launch of the captured 105-pair A Q product (ncu)",
                 "kernel": f"ozaki slice products (tcgen05 kind::f16 bf16), {_engine_name(dd_hp_name, args.slices, True)}",
                 "peak_source": psrc}
+    elif dom == "solve":
+        # the FP64 stepwise solve with double-double divisors: FP64 FMA work
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        peak = FP64_NOMINAL_TFLOPS
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "trisolve_leaf/update_kernel<double> (FP64 FMA, n^3/3 per solve)",
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 peak)"}
     else:
         gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs") or 6800.0
@@ -794,16 +849,17 @@ def run_dd(args):
                    "certified": {"stril_rel": rT, "orth": rQ, "tol": tol,
                                  "kind": "double-double residual products on the device",
                                  "ok": bool(rT <= tol and rQ <= tol)},
-                   "simt_dd_s": ms64 / 1e3, "simt_dd_status": st64, "simt_dd_iters": nr64.iters,
-                   "emulated_vs_simt_dd_speedup": ms64 / ms,
+                   "simt_dd_s": None if ms64 is None else ms64 / 1e3, "simt_dd_status": st64,
+                   "simt_dd_iters": None if nr64 is None else nr64.iters,
+                   "emulated_vs_simt_dd_speedup": None if ms64 is None else ms64 / ms,
                    "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
                    "phase_rates": phase_rooflines(prof, args.steps),
                    "simt_dd_phase_ms_per_step": {k: v["ms"] / k64 for k, v in prof64.items() if v["ms"] > 0},
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n * n * 8 * 3),
-                "d2h_bytes_per_step": int(n * n * 16)},
+        "e2e": None if e2e_s is None else {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n * n * 8 * 3),
+                                           "d2h_bytes_per_step": int(n * n * 16)},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -948,7 +1004,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=None)
-    ap.add_argument("--hp", choices=["fp64", "ozaki", "crt"], default="ozaki")
+    ap.add_argument("--hp", choices=["fp64", "ozaki", "crt"], default="crt")
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--lp-slices", type=int, default=0,
                     help="digits of the FP32-class products YW, W^2, W^3 (mixed form; 0 = 3)")
@@ -958,6 +1014,9 @@ def main():
     ap.add_argument("--cpu-full", type=int, default=None,
                     help="1: time the oracle at the workload's own order; 0: at --cpu-sample-n")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--measured-only", action="store_true",
+                    help="time the measured path only (no end-to-end, comparison forms or CPU baseline): "
+                         "the command the ncu summaries under profiles/ capture")
     ap.add_argument("--workload", choices=["single", "complex", "batched", "dd", "small", "sym"], default="single")
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--batch-streams", type=int, default=8)
@@ -973,6 +1032,8 @@ def main():
         # the complex n = 8192 oracle refinement takes tens of minutes on the host
         args.cpu_full = 0 if args.workload == "complex" else 1
     args.cpu_full = bool(args.cpu_full)
+    if args.measured_only:
+        args.no_cpu_baseline = True
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
