@@ -220,10 +220,15 @@ def eig_ring(n: int, seed: int) -> np.ndarray:
     return 0.5 * np.exp(2j * np.pi * k / n) * (1.0 + 0.2 * st.uniform((n,)))
 
 
-def unit_step_real(n: int = 64, seed: int = BASE_SEED + 1, low: str = "f32") -> Planted:
-    """Real planted problem with lambda_k = 1 + k/64 and a FP32-rounded start."""
-    return planted(n, eig_unit_step(n), seed, pert=1e-6, low=low,
-                   recipe=f"real n={n}, lambda_k=1+k/64, upper std 1/n, Qhat=fl_{low}(Q0 expm(1e-6 S))")
+def unit_step_real(n: int = 64, seed: int = BASE_SEED + 1, low: str = "f32",
+                   upper_std: float | None = None) -> Planted:
+    """Real planted problem with lambda_k = 1 + k/64 and a FP32-rounded start.
+
+    The strictly upper entries of T0 have standard deviation 1/n unless
+    upper_std is given (1/sqrt(n) is the variance-1/n reading of "N(0, 1/n)")."""
+    sd = 1.0 / n if upper_std is None else float(upper_std)
+    return planted(n, eig_unit_step(n), seed, pert=1e-6, low=low, upper_std=sd,
+                   recipe=f"real n={n}, lambda_k=1+k/64, upper std {sd:.3g}, Qhat=fl_{low}(Q0 expm(1e-6 S))")
 
 
 def jittered_real(n: int = 4096, seed: int = BASE_SEED + 2, low: str = "f32",
@@ -424,14 +429,16 @@ class PlantedDD:
 
 
 def planted_dd(n: int, lam: np.ndarray, seed: int, *, pert: float = 1e-14,
-               recipe: str = "") -> PlantedDD:
+               recipe: str = "", upper_std: float | None = None) -> PlantedDD:
     """A = Q0 T0 Q0^T in double-double, Qhat = fl64(Q0 expm(pert S)).
 
     T0 has diagonal ``lam`` and iid normal strictly-upper entries with standard
-    deviation 1/n (float64, exact in double-double). Q0 is the butterfly
-    factor described above. Cached under $SR_INPUT_CACHE like :func:`planted`."""
+    deviation ``upper_std`` (default 1/n; float64, exact in double-double). Q0
+    is the butterfly factor described above. Cached under $SR_INPUT_CACHE like
+    :func:`planted`."""
     lam = np.asarray(lam, dtype=np.float64)
-    path = _cache_path(repr(("dd", n, hashlib_digest(lam), seed, pert)))
+    key = ("dd", n, hashlib_digest(lam), seed, pert) + (() if upper_std is None else (upper_std,))
+    path = _cache_path(repr(key))
     if path is not None:
         import os
         if os.path.exists(path):
@@ -440,7 +447,8 @@ def planted_dd(n: int, lam: np.ndarray, seed: int, *, pert: float = 1e-14,
             return PlantedDD(A_hi=f("A_hi"), A_lo=f("A_lo"), Qhat=f("Qhat"), Q0_hi=f("Q0_hi"),
                              Q0_lo=f("Q0_lo"), T0=f("T0"), lam=z["lam"], seed=seed, recipe=recipe)
     st = Stream(seed)
-    T0 = np.triu(st.normal((n, n)) * (1.0 / n), 1) + np.diag(lam)
+    sd = (1.0 / n) if upper_std is None else float(upper_std)
+    T0 = np.triu(st.normal((n, n)) * sd, 1) + np.diag(lam)
     bf = _make_butterflies(st, n)
     z = np.zeros((n, n))
     Q0h, Q0l = _apply_rows(bf, np.eye(n), z)
@@ -466,8 +474,10 @@ def planted_dd(n: int, lam: np.ndarray, seed: int, *, pert: float = 1e-14,
     return p
 
 
-def unit_step_dd(n: int = 2048, seed: int = BASE_SEED + 5) -> PlantedDD:
-    """Double-double planted problem, lambda_k = 1 + k/64, Qhat = fl64(Q0 expm(1e-14 S))."""
-    return planted_dd(n, eig_unit_step(n), seed, pert=1e-14,
-                      recipe=f"real n={n} double-double, lambda_k=1+k/64, upper std 1/n, "
+def unit_step_dd(n: int = 2048, seed: int = BASE_SEED + 5, upper_std: float | None = None) -> PlantedDD:
+    """Double-double planted problem, lambda_k = 1 + k/64, Qhat = fl64(Q0 expm(1e-14 S));
+    strictly upper entries of standard deviation 1/n unless upper_std is given."""
+    sd = 1.0 / n if upper_std is None else float(upper_std)
+    return planted_dd(n, eig_unit_step(n), seed, pert=1e-14, upper_std=sd,
+                      recipe=f"real n={n} double-double, lambda_k=1+k/64, upper std {sd:.3g}, "
                              f"Qhat=fl64(Q0 expm(1e-14 S))")

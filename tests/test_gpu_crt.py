@@ -267,3 +267,21 @@ def test_crt_headline_workload_full_size(torch):
     assert np.max(np.abs(y)) <= tol
     diag = rows == cols
     assert np.max(np.abs(t[diag] - p.lam[rows[diag]])) <= 1e-11
+
+
+@pytest.mark.parametrize("n", [64, 512])
+def test_crt_refine_nonnormal_unit_step(torch, n):
+    """The unit-step spectrum with strictly upper entries of standard deviation
+    1/sqrt(n) (the variance reading of "N(0, 1/n)"): strongly non-normal T0,
+    against the oracle's refinement of the same input."""
+    p = inputs.unit_step_real(n, upper_std=1.0 / np.sqrt(n))
+    st, nr, Q, T = _refine(p, T=True)
+    ref = oracle.refine(p.A, p.Qhat, lp="f32")
+    assert st == B.SR_OK and ref.status == oracle.OK and abs(nr.iters - ref.iters) <= 1
+    tol = oracle.default_tol(n)
+    cT, cQ = oracle.residuals_dd(p.A, Q)
+    assert cT <= tol and cQ <= tol
+    # the Schur diagonal against the oracle's: eigenvalues of a non-normal T0 are
+    # ill-conditioned, so both sit about kappa u from the planted ones
+    Tr = ref.Q.T @ p.A @ ref.Q
+    assert np.max(np.abs(np.diagonal(T) - np.diagonal(Tr))) <= 1e-10

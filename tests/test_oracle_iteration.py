@@ -232,3 +232,17 @@ def test_gemm_dd_matches_exact(rng):
             ex = sum(Fraction(A[k, i]) * (Fraction(B[k, j]) + Fraction(Bl[k, j])) for k in range(n))
             got = Fraction(Ch[i, j]) + Fraction(Cl[i, j])
             assert abs(float(got - ex)) <= 1e-30 * max(1.0, abs(float(ex)))
+
+
+@pytest.mark.parametrize("n,passes", [(64, 5), (512, 3)])
+def test_variance_reading_of_upper_entries_converges_on_unit_step(n, passes):
+    # "N(0, 1/n)" read as variance 1/n (standard deviation 1/sqrt(n)) on the
+    # unit-step spectrum (gap 1/64): T0 is then strongly non-normal (strictly
+    # upper entries of 0.125 against the gap 1/64 at n = 64), and the mixed
+    # iteration still converges to the FP64 target, in 5 passes at n = 64
+    p = inputs.unit_step_real(n, upper_std=1.0 / math.sqrt(n))
+    r = oracle.refine(p.A, p.Qhat, lp="f32")
+    assert r.status == oracle.OK and r.iters == passes
+    rT, rQ = oracle.residuals_dd(p.A, r.Q)
+    tol = oracle.default_tol(n)
+    assert rT <= tol and rQ <= tol
