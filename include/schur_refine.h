@@ -146,13 +146,15 @@ typedef struct {
                          one launch pair per block subdiagonal, replayed from
                          a CUDA graph. Same equations, sums in another order;
                          complex128 always uses the stepwise form */
-    int symmetric;    /* 1: A is real symmetric (Sec. 2.5): its Schur form is
-                         diagonal, so T^ splits into its diagonal T and its
-                         off-diagonal part E, and the solve of S4 becomes
-                         elementwise, l_ij = -e_ij / (t_ii - t_jj) for i > j
-                         (the sign of eq. (lij)). Real data and the FP64
-                         target only; grouped batches fall back to worker
-                         streams. 0 (default): general A */
+    int symmetric;    /* 1: A is real symmetric or complex Hermitian
+                         (Sec. 2.5): its Schur form is real diagonal, so T^
+                         splits into its diagonal T and its off-diagonal part
+                         E, and the solve of S4 becomes elementwise,
+                         l_ij = -e_ij / (t_ii - t_jj) for i > j (the sign of
+                         eq. (lij)); for complex data the divisor is formed
+                         from the real parts of the diagonal. FP64 target
+                         only; grouped batches fall back to worker streams.
+                         0 (default): general A */
     double l_cap;     /* > 0: the trick of Example 4 (Sec. 3) for poorly
                          separated eigenvalues: while L is computed, an entry
                          with |l_ij| > l_cap (|l|^2 > l_cap^2 for complex

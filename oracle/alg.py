@@ -153,18 +153,37 @@ def sym_solve(E: np.ndarray, d_hp: np.ndarray, cap: float = 0.0) -> np.ndarray:
     """Sec. 2.5: the solution of stril(T L - L T) = -E for diagonal T, in the
     precision of ``E``: l_ij = -e_ij / (t_ii - t_jj) for i > j, each divisor
     formed from the hp diagonal ``d_hp`` and rounded to that precision (as in
-    :func:`alg2`). Raises :class:`SolveError` like alg2."""
+    :func:`alg2`). For Hermitian A (complex ``E``) the Schur form is real
+    diagonal, so the divisor is formed from the real parts of ``d_hp`` and
+    divides the real and imaginary parts of e_ij separately. Raises
+    :class:`SolveError` like alg2."""
     n = E.shape[0]
     dt = E.dtype
     L = np.zeros((n, n), dtype=dt)
     i, j = np.tril_indices(n, -1)
-    den = (np.asarray(d_hp)[i] - np.asarray(d_hp)[j]).astype(dt)
+    cplx = np.iscomplexobj(E)
+    if cplx:
+        rt = np.float32 if dt == np.complex64 else np.float64
+        dr = np.real(np.asarray(d_hp)).astype(np.float64)
+        den = (dr[i] - dr[j]).astype(rt)
+    else:
+        den = (np.asarray(d_hp)[i] - np.asarray(d_hp)[j]).astype(dt)
     if np.any(den == 0):
         raise SolveError(NONDISTINCT)
     with np.errstate(over="ignore", invalid="ignore"):
-        vals = -E[i, j] / den
-    if cap > 0:   # the trick of Example 4, as in alg2
-        vals[np.abs(vals) > dt.type(cap)] = 0
+        if cplx:
+            e = E[i, j]
+            vals = np.empty(len(i), dtype=dt)
+            vals.real = -(e.real / den)
+            vals.imag = -(e.imag / den)
+        else:
+            vals = -E[i, j] / den
+    if cap > 0:   # the trick of Example 4, as in alg2 (|l|^2 > cap^2 for complex data)
+        if cplx:
+            rt = vals.real.dtype.type
+            vals[vals.real * vals.real + vals.imag * vals.imag > rt(cap) * rt(cap)] = 0
+        else:
+            vals[np.abs(vals) > dt.type(cap)] = 0
     if not np.all(np.isfinite(vals)):
         raise SolveError(NONFINITE)
     L[i, j] = vals

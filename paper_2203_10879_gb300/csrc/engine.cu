@@ -204,8 +204,8 @@ sr_status check_opts(const sr_options &o)
         return SR_ERR_UNSUPPORTED;
     // complex data: the emulated products with the complex64 correction path
     if (o.dtype == SR_COMPLEX && (!is_emulated(o) || o.lp != SR_LP_FP32)) return SR_ERR_UNSUPPORTED;
-    // Sec. 2.5 is stated for real symmetric A; the double-double target keeps the general form
-    if (o.symmetric && (o.dtype != SR_REAL || o.target != SR_TARGET_FP64)) return SR_ERR_UNSUPPORTED;
+    // Sec. 2.5 (real symmetric or complex Hermitian A); the double-double target keeps the general form
+    if (o.symmetric && o.target != SR_TARGET_FP64) return SR_ERR_UNSUPPORTED;
     if (is_emulated(o) && !sr::kOzakiBuilt) return SR_ERR_UNSUPPORTED;
     return SR_OK;
 }
@@ -371,7 +371,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
 {
     const int NB = (n + sr::kSolveTile - 1) / sr::kSolveTile;
     const int kind = SrNum<Tl>::kind;
-    if constexpr (SrNum<Tl>::kind <= 1) {
+    {
         if (h->opt.symmetric) {
             // Sec. 2.5: T diagonal, one division per entry
             SrPhase ph(h, SR_PROF_SOLVE, (long long)n * (n - 1) / 2, (long long)n * n * (long long)sizeof(Tl), 1);

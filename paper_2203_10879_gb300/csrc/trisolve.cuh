@@ -453,14 +453,30 @@ diag_solve_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>::hp
     for (int w = 0; w < 4; ++w) {
         const int j = jb + 8 * w;
         if (i < n && j < i) {
-            const T den = sr_div_round<T>(dhp[i], dhp[j]);
             T x = SrNum<T>::zero();
-            if (den == SrNum<T>::zero()) {
-                bad |= SR_FLAG_NONDISTINCT;
+            if constexpr (SrNum<T>::kind >= 2) {
+                // Hermitian A: the Schur form is real diagonal, so the divisor is
+                // formed from the real parts of the hp diagonal, rounded once to the
+                // low precision, and divides both parts of e_ij (two IEEE divisions)
+                using R = decltype(x.x);
+                const R den = (R)(dhp[i].x - dhp[j].x);
+                if (den == (R)0) {
+                    bad |= SR_FLAG_NONDISTINCT;
+                } else {
+                    const T e = TE[sr_idx(i, j, ld)];
+                    x = T{-(e.x / den), -(e.y / den)};
+                    if (cap > 0.0 && sr_over_cap(x, cap)) x = SrNum<T>::zero();   // Example 4's trick
+                    if (!sr_finite(x)) bad |= SR_FLAG_NONFINITE;
+                }
             } else {
-                x = -(TE[sr_idx(i, j, ld)] / den);
-                if (cap > 0.0 && sr_over_cap(x, cap)) x = SrNum<T>::zero();   // Example 4's trick
-                if (!sr_finite(x)) bad |= SR_FLAG_NONFINITE;
+                const T den = sr_div_round<T>(dhp[i], dhp[j]);
+                if (den == SrNum<T>::zero()) {
+                    bad |= SR_FLAG_NONDISTINCT;
+                } else {
+                    x = -(TE[sr_idx(i, j, ld)] / den);
+                    if (cap > 0.0 && sr_over_cap(x, cap)) x = SrNum<T>::zero();   // Example 4's trick
+                    if (!sr_finite(x)) bad |= SR_FLAG_NONFINITE;
+                }
             }
             TE[sr_idx(i, j, ld)] = x;
         }

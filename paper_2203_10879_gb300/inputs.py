@@ -248,6 +248,18 @@ def symmetric_real(n: int = 4096, seed: int = BASE_SEED + 5, low: str = "f32") -
     return Planted(A=A, Qhat=p.Qhat, Q0=p.Q0, T0=p.T0, lam=p.lam, seed=p.seed, recipe=p.recipe)
 
 
+def hermitian_complex(n: int = 2048, seed: int = BASE_SEED + 7, low: str = "f32") -> Planted:
+    """Complex Hermitian planted problem (Sec. 2.5): T0 = diag(lambda) real,
+    lambda_k = k/n + U(0, 0.5/n); A = Q0 T0 Q0^H with Q0 Haar unitary, made
+    exactly Hermitian, (A + A^H)/2; Qhat = fl_c64(Q0 expm(1e-6 S)), S
+    skew-Hermitian."""
+    p = planted(n, eig_jittered_grid(n, seed), seed, pert=1e-6, low=low, complex_=True, upper_std=0.0,
+                recipe=f"complex Hermitian n={n}, A=Q0 diag(lambda) Q0^H, lambda_k=k/n+U(0,0.5/n), "
+                       f"Qhat=fl_c64(Q0 expm(1e-6 S))")
+    A = np.asfortranarray(0.5 * (p.A + p.A.conj().T))
+    return Planted(A=A, Qhat=p.Qhat, Q0=p.Q0, T0=p.T0, lam=p.lam, seed=p.seed, recipe=p.recipe)
+
+
 def clustered_complex(n: int = 150, cond: float = 1e5, radius: float = 1e-5, seed: int = BASE_SEED + 6,
                       low: str = "f32") -> Planted:
     """The setting of Example 3 (Sec. 3): A = X D X^-1 with X of condition

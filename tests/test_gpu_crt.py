@@ -282,6 +282,14 @@ def test_crt_refine_nonnormal_unit_step(torch, n):
     cT, cQ = oracle.residuals_dd(p.A, Q)
     assert cT <= tol and cQ <= tol
     # the Schur diagonal against the oracle's: eigenvalues of a non-normal T0 are
-    # ill-conditioned, so both sit about kappa u from the planted ones
+    # ill-conditioned (condition numbers kappa_i up to 5e7 at n = 64), so the two
+    # may differ by about kappa_i u ||A|| (first-order perturbation by a backward
+    # error of u ||A||): the bound is ten times that
+    import scipy.linalg as sl
+    w, VL, VR = sl.eig(p.T0, left=True, right=True)
+    kappa = 1.0 / np.abs(np.sum(np.conj(VL) * VR, axis=0))
+    order = np.argsort(w.real)
+    kap = kappa[order]                       # the planted diagonal is ascending, like w
     Tr = ref.Q.T @ p.A @ ref.Q
-    assert np.max(np.abs(np.diagonal(T) - np.diagonal(Tr))) <= 1e-10
+    bound = 10 * kap * U64 * np.linalg.norm(p.A) + 1e-13
+    assert np.all(np.abs(np.diagonal(T) - np.diagonal(Tr)) <= bound)

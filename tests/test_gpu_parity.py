@@ -19,7 +19,7 @@ import pytest
 import oracle
 from paper_2203_10879_gb300 import _binding as B
 from paper_2203_10879_gb300 import inputs
-from gpu_util import from_dev, sign_align, to_dev
+from gpu_util import from_dev, phase_align, sign_align, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -163,8 +163,9 @@ def _refine_gpu(p, **kw):
     try:
         A = to_dev(p.A)
         Qhat = to_dev(p.Qhat)
-        Q = torch.zeros((n, n), dtype=torch.float64, device="cuda").t()
-        T = torch.zeros((n, n), dtype=torch.float64, device="cuda").t()
+        dt = torch.complex128 if np.iscomplexobj(p.A) else torch.float64
+        Q = torch.zeros((n, n), dtype=dt, device="cuda").t()
+        T = torch.zeros((n, n), dtype=dt, device="cuda").t()
         s, nr = B.schur_refine_step(h, n, A, Q, Qhat, T)
         sr, rT, rQ = B.schur_refine_residuals(h, n, A, Q)
         assert sr == B.SR_OK
@@ -321,11 +322,47 @@ def test_symmetric_refinement_parity(torch, n, hp):
     assert np.max(np.abs(sign_align(Q, ref.Q) - ref.Q)) <= 1e-10
 
 
-def test_symmetric_option_rejected_for_complex_and_dd(torch):
-    for kw in ({"dtype": B.SR_COMPLEX, "hp_gemm": B.SR_HP_OZAKI_BF16},
-               {"target": B.SR_TARGET_DD, "lp": B.SR_LP_FP64, "qhat_type": B.SR_QHAT_FP64}):
-        s, h = B.schur_refine_create(64, B.default_options(symmetric=1, **kw), None)
-        assert s == B.SR_ERR_UNSUPPORTED and not h
+def test_symmetric_option_rejected_for_dd(torch):
+    kw = {"target": B.SR_TARGET_DD, "lp": B.SR_LP_FP64, "qhat_type": B.SR_QHAT_FP64}
+    s, h = B.schur_refine_create(64, B.default_options(symmetric=1, **kw), None)
+    assert s == B.SR_ERR_UNSUPPORTED and not h
+
+
+# Hermitian A (Sec. 2.5 for complex data): the divisor from the real parts of
+# the hp diagonal, rounded once to FP32, dividing both parts of e_ij
+
+@pytest.mark.parametrize("n", [2, 33, 257])
+def test_hermitian_solve_bit_exact(torch, n):
+    rng = np.random.default_rng(3 * n)
+    d = np.sort(rng.uniform(-1.0, 1.0, n)) + 1j * rng.uniform(-1e-17, 1e-17, n)   # rounding-level imaginary parts
+    E = np.tril(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)), -1) * 1e-4
+    h = _handle(n, dtype=B.SR_COMPLEX, hp_gemm=B.SR_HP_OZAKI_CRT, lp=B.SR_LP_FP32, symmetric=1)
+    try:
+        U = np.triu(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)), 1)
+        TE = to_dev((np.diag(d) + U + E).astype(np.complex64))
+        assert B.schur_refine_trisolve(h, n, TE, to_dev(d.copy())) == B.SR_OK
+        L = np.tril(from_dev(TE), -1)
+        ref = oracle.sym_solve(E.astype(np.complex64), d)
+        assert np.array_equal(L, ref)
+    finally:
+        B.schur_refine_destroy(h)
+
+
+@pytest.mark.parametrize("hp", [B.SR_HP_OZAKI_CRT, B.SR_HP_OZAKI_BF16])
+@pytest.mark.parametrize("n", [64, 300])
+def test_hermitian_refinement_parity(torch, n, hp):
+    p = inputs.hermitian_complex(n)
+    s, nr, Q, T, (rT, rQ) = _refine_gpu(p, lp=B.SR_LP_FP32, hp_gemm=hp, symmetric=1, dtype=B.SR_COMPLEX)
+    ref = oracle.refine(p.A, p.Qhat, lp="f32", symmetric=True)
+    assert s == B.SR_OK and ref.status == oracle.OK
+    assert abs(nr.iters - ref.iters) <= 1
+    tol = oracle.default_tol(n)
+    cT, cQ = oracle.residuals_dd(p.A, Q)
+    assert cT <= tol and cQ <= tol
+    w, V = np.linalg.eigh(p.A)
+    assert np.max(np.abs(np.diagonal(T) - w)) <= 1e-13
+    assert np.max(np.abs(phase_align(Q, V) - V)) <= 1e-10
+    assert np.max(np.abs(phase_align(Q, ref.Q) - ref.Q)) <= 1e-10
 
 
 # ---------------------------------------------------------------------------
