@@ -9,5 +9,6 @@ from ._lib import build, set_threads, max_threads  # noqa: F401
 from .alg import (  # noqa: F401
     OK, NONDISTINCT, NONFINITE, NOT_CONVERGED, SolveError, IterInfo, RefineResult,
     alg2, sym_solve, alg3, kron_solve, ns_init, form_residual, iteration, refine, default_tol,
+    quasi_blocks, block_lower_mask, alg2_quasi,
     residuals_dd, sample_entries_dd, gemm_dd,
 )

@@ -57,6 +57,8 @@ def _declare(L):
     L.sro_gemm_dd.restype = None
     L.sro_residuals_dd.argtypes = [_I, _P, _I, _P, _I, _P, _P]
     L.sro_residuals_dd.restype = None
+    L.sro_residuals_dd_quasi.argtypes = [_I, _P, _I, _P, _I, _P, _P, _P]
+    L.sro_residuals_dd_quasi.restype = None
     L.sro_residuals_dd_c.argtypes = [_I, _P, _I, _P, _I, _P, _P]
     L.sro_residuals_dd_c.restype = None
     L.sro_sample_entries_dd.argtypes = [_I, _P, _I, _P, _I, _I, _P, _P, _P, _P]
@@ -69,6 +71,9 @@ def _declare(L):
     L.sro_residuals_q.restype = None
     L.sro_sample_entries_q.argtypes = [_I, _P, _P, _I, _P, _P, _I, _I, _P, _P, _P, _P, _P, _P]
     L.sro_sample_entries_q.restype = None
+    for name in ("sro_alg2_quasi_f64", "sro_alg2_quasi_f32"):
+        getattr(L, name).argtypes = [_I, _P, _I, _P, _I, _P, _P, _P, _I, ctypes.c_double]
+        getattr(L, name).restype = ctypes.c_int
     L.sro_set_threads.argtypes = [_I]
     L.sro_set_threads.restype = None
     L.sro_max_threads.argtypes = []

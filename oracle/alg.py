@@ -14,6 +14,9 @@ Every function follows the paper's steps in its order and notation:
 * :func:`alg3`         -- Alg. 3 (recursive block algorithm), Sec. 2.1.
 * :func:`kron_solve`   -- brute force of the same equation (dense solve of the
   operator's n(n-1)/2-square matrix in 128-bit arithmetic).
+* :func:`alg2_quasi`   -- Alg. 2 for the real quasi-triangular Schur form of
+  Sec. 3 (2 x 2 diagonal blocks for complex-conjugate pairs; blocks read off
+  T^ by :func:`quasi_blocks`).
 * :func:`sym_solve`    -- Sec. 2.5 (symmetric A): with T diagonal the equation
   decouples, l_ij = -e_ij / (t_ii - t_jj) for i > j (the sign of eq. (lij)).
 * :func:`iteration`    -- one pass of the REPEAT loop of Alg. 4 (Sec. 2.4):
@@ -190,17 +193,77 @@ def sym_solve(E: np.ndarray, d_hp: np.ndarray, cap: float = 0.0) -> np.ndarray:
     return L
 
 
-def form_residual(A: np.ndarray, Q: np.ndarray):
-    """T^ = Q^H A Q in hp (two products), split into E = stril(T^) and T = T^ - E."""
+def quasi_blocks(That: np.ndarray) -> np.ndarray:
+    """Diagonal block sizes of a real quasi-triangular Schur form read off T^
+    (Sec. 3, real Schur decompositions): blk[k] = 2 when rows k, k+1 form a 2 x 2
+    block, with blk[k + 1] = 0, else 1. Rows are taken from the top; rows k, k+1
+    form a block when the 2 x 2 diagonal block of T^ there has non-real
+    eigenvalues, (t_kk - t_k+1,k+1)^2 + 4 t_k,k+1 t_k+1,k < 0 (evaluated in hp)."""
+    n = That.shape[0]
+    blk = np.ones(n, dtype=np.int32)
+    k = 0
+    while k < n:
+        if k + 1 < n:
+            a, b, c, d = That[k, k], That[k, k + 1], That[k + 1, k], That[k + 1, k + 1]
+            if (a - d) * (a - d) + 4.0 * b * c < 0.0:
+                blk[k], blk[k + 1] = 2, 0
+                k += 2
+                continue
+        k += 1
+    return blk
+
+
+def block_lower_mask(blk: np.ndarray) -> np.ndarray:
+    """Mask of the entries below the diagonal blocks (the strictly block-lower part)."""
+    n = len(blk)
+    owner = np.arange(n)
+    for k in range(n):
+        if blk[k] == 0:
+            owner[k] = k - 1
+    return owner[:, None] > owner[None, :]
+
+
+def form_residual(A: np.ndarray, Q: np.ndarray, quasi: bool = False):
+    """T^ = Q^H A Q in hp (two products), split into E = stril(T^) and T = T^ - E.
+    With ``quasi`` (real quasi-triangular Schur form), E is the strictly
+    block-lower part for the blocks :func:`quasi_blocks` reads off T^, and the
+    block sizes are returned third."""
     That = Q.conj().T @ (A @ Q)
+    if quasi:
+        blk = quasi_blocks(That)
+        E = np.where(block_lower_mask(blk), That, 0.0)
+        return That - E, E, blk
     E = np.tril(That, -1)
     T = That - E
     return T, E
 
 
+def alg2_quasi(T: np.ndarray, E: np.ndarray, blk: np.ndarray, d_hp: np.ndarray, cap: float = 0.0) -> np.ndarray:
+    """Alg. 2 for the real quasi-triangular form in the precision of ``T``
+    (float32/64): sbl(T L - L T) = -E for strictly block-lower L, block columns
+    left to right and block rows bottom to top, each block equation
+    T_II X - X T_JJ = -C_IJ solved through its Kronecker matrix (at most 4 x 4)
+    whose diagonal entries t_rr - t_cc are formed from the hp diagonal ``d_hp``
+    and rounded once, by Gaussian elimination with partial pivoting. With every
+    block 1 x 1 it is :func:`alg2`. Raises :class:`SolveError` on a shared
+    eigenvalue of two blocks (a zero pivot) or a non-finite L."""
+    n = T.shape[0]
+    dt = T.dtype
+    T = _lib.fortran(T, dt)
+    E = _lib.fortran(E, dt)
+    L = np.zeros((n, n), dtype=dt, order="F")
+    dh = np.ascontiguousarray(d_hp, dtype=np.float64)
+    b = np.ascontiguousarray(blk, dtype=np.int32)
+    fn = _lib.lib().sro_alg2_quasi_f32 if dt == np.float32 else _lib.lib().sro_alg2_quasi_f64
+    rc = fn(n, _lib.ptr(T), n, _lib.ptr(E), n, _lib.ptr(dh), _lib.ptr(b), _lib.ptr(L), n, float(cap))
+    if rc:
+        raise SolveError(rc)
+    return L
+
+
 def iteration(A: np.ndarray, Q: np.ndarray, lp: str = "f32", full_sigma: bool = False,
               solver: str = "alg2", T_E=None, parts: dict | None = None, symmetric: bool = False,
-              cap: float = 0.0):
+              cap: float = 0.0, quasi: bool = False):
     """One pass of the REPEAT loop of Alg. 4; returns (Q_new, IterInfo).
 
     ``full_sigma`` adds the two terms W^2 Y + W^2 Y W that Sec. 2.4 drops.
@@ -215,13 +278,18 @@ def iteration(A: np.ndarray, Q: np.ndarray, lp: str = "f32", full_sigma: bool = 
     lpt = _lp_dtype(lp, cplx)
     n = A.shape[0]
     I = np.eye(n, dtype=hp)
-    T, E = form_residual(A, Q) if T_E is None else T_E
+    if quasi:
+        T, E, blk = form_residual(A, Q, quasi=True) if T_E is None else T_E
+    else:
+        T, E = form_residual(A, Q) if T_E is None else T_E
     info = IterInfo(r_T=float(np.linalg.norm(E) / np.linalg.norm(A)))
     # E, T to lp; divisors from the hp diagonal
     T_lp = np.asfortranarray(T.astype(lpt))
     E_lp = np.asfortranarray(E.astype(lpt))
     if symmetric:
         L_lp = sym_solve(E_lp, np.diagonal(T).copy(), cap)
+    elif quasi:
+        L_lp = alg2_quasi(T_lp, E_lp, blk, np.diagonal(T).copy(), cap)
     elif solver == "alg2":
         L_lp = alg2(T_lp, E_lp, np.diagonal(T).copy(), cap)
     elif solver == "alg3":
@@ -270,7 +338,8 @@ class RefineResult:
 
 def refine(A: np.ndarray, Qhat: np.ndarray, lp: str = "f32", tol: float | None = None,
            max_iter: int = 10, full_sigma: bool = False, solver: str = "alg2",
-           init_ns: bool = True, symmetric: bool = False, cap: float = 0.0) -> RefineResult:
+           init_ns: bool = True, symmetric: bool = False, cap: float = 0.0,
+           quasi: bool = False) -> RefineResult:
     """Alg. 4 lines "convert Qhat, NS step" and REPEAT ... UNTIL convergence.
 
     Stop test (the paper only says "when E becomes small enough"): after
@@ -291,7 +360,8 @@ def refine(A: np.ndarray, Qhat: np.ndarray, lp: str = "f32", tol: float | None =
     y_last = y
     prev_rT = math.inf
     for k in range(1, max_iter + 1):
-        T, E = form_residual(A, Q)
+        TE = form_residual(A, Q, quasi=quasi)
+        T, E = TE[0], TE[1]
         res.hp_gemms += 2
         res.iters = k
         r_T = float(np.linalg.norm(E) / np.linalg.norm(A))
@@ -310,8 +380,8 @@ def refine(A: np.ndarray, Qhat: np.ndarray, lp: str = "f32", tol: float | None =
             break
         prev_rT = r_T
         try:
-            Q, info = iteration(A, Q, lp=lp, full_sigma=full_sigma, solver=solver, T_E=(T, E),
-                                symmetric=symmetric, cap=cap)
+            Q, info = iteration(A, Q, lp=lp, full_sigma=full_sigma, solver=solver, T_E=TE,
+                                symmetric=symmetric, cap=cap, quasi=quasi)
         except SolveError as e:
             res.status = e.code
             res.history.append(IterInfo(r_T=r_T))
@@ -329,13 +399,22 @@ def refine(A: np.ndarray, Qhat: np.ndarray, lp: str = "f32", tol: float | None =
 # ---------------------------------------------------------------------------
 # Residuals in double-double (Sec. 3 error measures)
 
-def residuals_dd(A: np.ndarray, Q: np.ndarray, threads: int | None = None):
-    """(r_T, r_Q) = (||stril(Q^H A Q)||_F/||A||_F, ||Q^H Q - I||_F) in double-double."""
+def residuals_dd(A: np.ndarray, Q: np.ndarray, threads: int | None = None, blk: np.ndarray | None = None):
+    """(r_T, r_Q) = (||stril(Q^H A Q)||_F/||A||_F, ||Q^H Q - I||_F) in double-double.
+    With ``blk`` (real quasi-triangular form, see :func:`quasi_blocks`) r_T is
+    the norm of the entries below the diagonal blocks."""
     n = A.shape[0]
     if threads is not None:
         _lib.set_threads(threads)
     rT = np.zeros(1)
     rQ = np.zeros(1)
+    if blk is not None:
+        Af = _lib.fortran(A, np.float64)
+        Qf = _lib.fortran(Q, np.float64)
+        b = np.ascontiguousarray(blk, dtype=np.int32)
+        _lib.lib().sro_residuals_dd_quasi(n, _lib.ptr(Af), n, _lib.ptr(Qf), n, _lib.ptr(b), _lib.ptr(rT),
+                                          _lib.ptr(rQ))
+        return float(rT[0]), float(rQ[0])
     if np.iscomplexobj(A) or np.iscomplexobj(Q):
         Af = _lib.fortran(A, np.complex128)
         Qf = _lib.fortran(Q, np.complex128)

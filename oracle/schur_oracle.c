@@ -401,8 +401,27 @@ void sro_gemm_dd(int transA, int m, int n, int k,
 
 /* Residuals of a real decomposition, evaluated in double-double:
  *   r_T = ||stril(Q^T A Q)||_F / ||A||_F,  r_Q = ||Q^T Q - I||_F. */
+/* r_T counts the entries below the diagonal blocks: for a quasi-triangular
+ * form (blk[k] = 2 at the first row of a 2 x 2 block, see sro_alg2_quasi_f64)
+ * the coupling entry (k+1, k) of each 2 x 2 block is part of T, not of the
+ * residual; blk NULL: every block 1 x 1 (stril). */
+static void residuals_dd_blk(int n, const double *A, int lda, const double *Q, int ldq, const int *blk,
+                             double *r_T, double *r_Q);
+
 void sro_residuals_dd(int n, const double *A, int lda, const double *Q, int ldq,
                       double *r_T, double *r_Q)
+{
+    residuals_dd_blk(n, A, lda, Q, ldq, NULL, r_T, r_Q);
+}
+
+void sro_residuals_dd_quasi(int n, const double *A, int lda, const double *Q, int ldq, const int *blk,
+                            double *r_T, double *r_Q)
+{
+    residuals_dd_blk(n, A, lda, Q, ldq, blk, r_T, r_Q);
+}
+
+static void residuals_dd_blk(int n, const double *A, int lda, const double *Q, int ldq, const int *blk,
+                             double *r_T, double *r_Q)
 {
     double *Mhi = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
     double *Mlo = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
@@ -412,7 +431,7 @@ void sro_residuals_dd(int n, const double *A, int lda, const double *Q, int ldq,
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : st, so)
     for (int j = 0; j < n; ++j) {
         for (int i = 0; i < n; ++i) {
-            if (i > j) { /* (Q^T M)(i,j) */
+            if (i > j && !(blk && i == j + 1 && blk[j] == 2)) { /* (Q^T M)(i,j) */
                 dd_t s = {0.0, 0.0};
                 for (int l = 0; l < n; ++l) {
                     dd_t m = {Mhi[IDX(l, j, n)], Mlo[IDX(l, j, n)]};
@@ -700,3 +719,99 @@ void sro_sample_entries_q(int n, const double *Ahi, const double *Alo, int lda, 
         y_lo[s] = (double)(g - (f128_t)y_hi[s]);
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Alg. 2 for the real quasi-triangular Schur form (Sec. 3: real Schur
+ * decompositions with 2 x 2 diagonal blocks holding complex-conjugate pairs).
+ * blk[k] = 2 when a 2 x 2 diagonal block starts at row k (and blk[k + 1] = 0),
+ * 1 for a 1 x 1 block. T holds the block upper triangular part (with the
+ * coupling entries t_{k+1,k} of the 2 x 2 blocks), E the strictly block-lower
+ * part, L receives the strictly block-lower solution of
+ *     sbl(T L - L T) = -E
+ * (sbl: the entries below the diagonal blocks). Block column J is taken left to
+ * right and block rows I bottom to top, as Alg. 2 does entries:
+ *     C_IJ = E_IJ + T(I, after I) L(after I, J) - L(I, before J) T(before J, J)
+ * entry by entry in the order of Alg. 2's sums, then T_II X - X T_JJ = -C_IJ is
+ * solved through its Kronecker matrix K = I (x) T_II - T_JJ^T (x) I of order
+ * p q <= 4 (vec(X) column-major): its diagonal entries t_rr - t_cc are formed
+ * from the high-precision diagonal dhp and rounded once, its other entries
+ * are entries of T; Gaussian elimination with partial pivoting (the first
+ * largest pivot) in the low precision, a zero pivot meaning a shared
+ * eigenvalue (SRO_NONDISTINCT). With every block 1 x 1 this is Alg. 2 step
+ * for step: x = (-c) / (t_ii - t_jj). */
+#define SRO_ALG2_QUASI(NAME, R, ABS)                                                                  \
+int NAME(int n, const R *T, int ldt, const R *E, int lde, const double *dhp, const int *blk,         \
+         R *L, int ldl, double cap)                                                                  \
+{                                                                                                    \
+    for (int j = 0; j < n; ++j)                                                                      \
+        for (int i = 0; i < n; ++i) L[IDX(i, j, ldl)] = 0;                                           \
+    for (int j0 = 0; j0 < n; j0 += blk[j0]) {                                                        \
+        const int q = blk[j0];                                                                       \
+        if (q != 1 && q != 2) return SRO_NONFINITE;                                                  \
+        /* block rows below the block column, bottom to top (the second row of  \
+           a 2 x 2 block has blk = 0) */                                                             \
+        for (int ib = n - 1; ib >= j0 + q;) {                                                        \
+            const int i0 = blk[ib] == 0 ? ib - 1 : ib, p = blk[i0];                                  \
+            ib = i0 - 1;                                                                             \
+            R c[2][2];                                                                               \
+            for (int r = 0; r < p; ++r)                                                              \
+                for (int cc = 0; cc < q; ++cc) {                                                     \
+                    const int i = i0 + r, j = j0 + cc;                                               \
+                    R e = E[IDX(i, j, lde)];                                                         \
+                    R s1 = 0, s2 = 0;                                                                \
+                    for (int k = i0 + p; k < n; ++k) s1 += T[IDX(i, k, ldt)] * L[IDX(k, j, ldl)];    \
+                    for (int k = 0; k < j0; ++k) s2 += L[IDX(i, k, ldl)] * T[IDX(k, j, ldt)];        \
+                    c[r][cc] = e + s1 - s2;                                                          \
+                }                                                                                    \
+            /* Kronecker system K vec(X) = -vec(C), index r + cc p */                                \
+            const int m = p * q;                                                                     \
+            R K[4][4], rhs[4];                                                                       \
+            for (int u = 0; u < m; ++u) {                                                            \
+                const int ru = u % p, cu = u / p;                                                    \
+                rhs[u] = -c[ru][cu];                                                                 \
+                for (int v = 0; v < m; ++v) {                                                        \
+                    const int rv = v % p, cv = v / p;                                                \
+                    R kv = 0;                                                                        \
+                    if (u == v) {                                                                    \
+                        kv = (R)(dhp[i0 + ru] - dhp[j0 + cu]);                                       \
+                    } else {                                                                         \
+                        if (cu == cv) kv = T[IDX(i0 + ru, i0 + rv, ldt)];                            \
+                        if (ru == rv) kv = -T[IDX(j0 + cv, j0 + cu, ldt)];                           \
+                    }                                                                                \
+                    K[u][v] = kv;                                                                    \
+                }                                                                                    \
+            }                                                                                        \
+            for (int k = 0; k < m; ++k) {                                                            \
+                int piv = k;                                                                         \
+                for (int u = k + 1; u < m; ++u)                                                      \
+                    if (ABS(K[u][k]) > ABS(K[piv][k])) piv = u;                                      \
+                if (K[piv][k] == 0) return SRO_NONDISTINCT;                                          \
+                if (piv != k) {                                                                      \
+                    for (int v = 0; v < m; ++v) { R t = K[k][v]; K[k][v] = K[piv][v]; K[piv][v] = t; } \
+                    R t = rhs[k]; rhs[k] = rhs[piv]; rhs[piv] = t;                                   \
+                }                                                                                    \
+                for (int u = k + 1; u < m; ++u) {                                                    \
+                    const R f = K[u][k] / K[k][k];                                                   \
+                    for (int v = k; v < m; ++v) K[u][v] -= f * K[k][v];                              \
+                    rhs[u] -= f * rhs[k];                                                            \
+                }                                                                                    \
+            }                                                                                        \
+            R x[4];                                                                                  \
+            for (int u = m - 1; u >= 0; --u) {                                                       \
+                R sacc = rhs[u];                                                                     \
+                for (int v = u + 1; v < m; ++v) sacc -= K[u][v] * x[v];                              \
+                x[u] = sacc / K[u][u];                                                               \
+            }                                                                                        \
+            for (int u = 0; u < m; ++u) {                                                            \
+                R xv = x[u];                                                                         \
+                if (cap > 0.0 && ABS(xv) > (R)cap) xv = 0;                                           \
+                if (!isfinite(xv)) return SRO_NONFINITE;                                             \
+                L[IDX(i0 + u % p, j0 + u / p, ldl)] = xv;                                            \
+            }                                                                                        \
+        }                                                                                            \
+    }                                                                                                \
+    return SRO_OK;                                                                                   \
+}
+
+SRO_ALG2_QUASI(sro_alg2_quasi_f64, double, fabs)
+SRO_ALG2_QUASI(sro_alg2_quasi_f32, float, fabsf)

@@ -248,6 +248,52 @@ def symmetric_real(n: int = 4096, seed: int = BASE_SEED + 5, low: str = "f32") -
     return Planted(A=A, Qhat=p.Qhat, Q0=p.Q0, T0=p.T0, lam=p.lam, seed=p.seed, recipe=p.recipe)
 
 
+def quasi_real(n: int = 4096, seed: int = BASE_SEED + 8, pair_prob: float = 1.0 / 3.0,
+               low: str = "f32") -> Planted:
+    """Real planted problem whose Schur form is quasi-triangular (Sec. 3: real
+    Schur decompositions, 2 x 2 diagonal blocks for complex-conjugate pairs).
+
+    Base values mu_k = k/n + U(0, 0.5/n) (sorted, as the jittered grid). Going
+    down the diagonal, a 2 x 2 block starts at row k (k + 1 < n) with
+    probability pair_prob; it is [[alpha, beta s], [-beta/s, alpha]] with
+    alpha = (mu_k + mu_k+1)/2, beta = (mu_k+1 - mu_k) U(0.5, 1.5), s = 2^U(-1, 1),
+    eigenvalues alpha +- i beta; other rows are 1 x 1 blocks mu_k. Entries above
+    the blocks: normal with standard deviation 1/n. A = Q0 T0 Q0^T in FP64,
+    Qhat = fl_low(Q0 expm(1e-6 S)). `lam` holds the planted eigenvalues row by
+    row (alpha + i beta, alpha - i beta for a block) and `blk` the block sizes
+    (2 at a block's first row, 0 at its second, else 1)."""
+    st = Stream(seed)
+    mu = np.sort(np.arange(n, dtype=np.float64) / n + st.uniform((n,)) * (0.5 / n))
+    u = st.uniform((n, 3))
+    blk = np.ones(n, dtype=np.int32)
+    T0 = np.triu(st.normal((n, n)) * (1.0 / n), 1)
+    lam = mu.astype(np.complex128)
+    k = 0
+    while k < n:
+        if k + 1 < n and u[k, 0] < pair_prob:
+            alpha = 0.5 * (mu[k] + mu[k + 1])
+            beta = (mu[k + 1] - mu[k]) * (0.5 + u[k, 1])
+            sc = 2.0 ** (2.0 * u[k, 2] - 1.0)
+            T0[k, k] = T0[k + 1, k + 1] = alpha
+            T0[k, k + 1] = beta * sc
+            T0[k + 1, k] = -beta / sc
+            lam[k], lam[k + 1] = alpha + 1j * beta, alpha - 1j * beta
+            blk[k], blk[k + 1] = 2, 0
+            k += 2
+        else:
+            T0[k, k] = mu[k]
+            k += 1
+    Q0 = _haar_orthogonal(st, n, False)
+    A = np.asfortranarray((Q0 @ T0) @ Q0.T)
+    S = _skew(st, n, False)
+    Qhat = np.asfortranarray((Q0 @ _expm_small(1e-6 * S, 6)).astype(np.float32 if low == "f32" else np.float64))
+    p = Planted(A=A, Qhat=Qhat, Q0=Q0, T0=np.asfortranarray(T0), lam=lam, seed=seed,
+                recipe=f"real quasi-triangular n={n}, pairs with probability {pair_prob:.3g}, "
+                       f"Qhat=fl_{low}(Q0 expm(1e-6 S))")
+    p.blk = blk
+    return p
+
+
 def hermitian_complex(n: int = 2048, seed: int = BASE_SEED + 7, low: str = "f32") -> Planted:
     """Complex Hermitian planted problem (Sec. 2.5): T0 = diag(lambda) real,
     lambda_k = k/n + U(0, 0.5/n); A = Q0 T0 Q0^H with Q0 Haar unitary, made
