@@ -169,6 +169,21 @@ typedef struct {
                          23 fraction bits, FP32-class; 2 carries 15 bits
                          (3 digit pairs instead of 6); 1 carries 7 bits, a
                          single bf16 product. More than 3: SR_ERR_INVALID_ARG */
+    int quasi;        /* 1: real quasi-triangular Schur form (Sec. 3, real
+                         Schur decompositions): complex-conjugate eigenvalue
+                         pairs of real A stay in 2 x 2 diagonal blocks of T.
+                         Each pass reads the blocks off T^ (rows k, k+1 form a
+                         block where the 2 x 2 diagonal block of T^ has
+                         non-real eigenvalues, taken from the top); E and the
+                         residual are the entries below the diagonal blocks,
+                         L is strictly block-lower, and each block equation
+                         T_II X - X T_JJ = -C is solved through its Kronecker
+                         matrix (at most 4 x 4). Real data, FP64 target, the
+                         stepwise solve, graph = 0, symmetric = 0; with every
+                         block 1 x 1 the iteration is the triangular one.
+                         schur_refine_residuals and schur_refine_trisolve of
+                         such a handle use the blocks too. 0 (default): the
+                         triangular Schur form */
 } sr_options;
 
 /* Fills *opt with the defaults: real, FP64 target, native FP64 products,

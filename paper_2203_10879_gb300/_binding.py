@@ -41,7 +41,8 @@ class sr_options(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("ozaki_slices", ctypes.c_int), ("tol", ctypes.c_double),
                 ("profile", ctypes.c_int), ("batch_streams", ctypes.c_int), ("batch_mode", ctypes.c_int),
                 ("tune", ctypes.c_int), ("graph", ctypes.c_int), ("solve_mode", ctypes.c_int),
-                ("symmetric", ctypes.c_int), ("l_cap", ctypes.c_double), ("lp_slices", ctypes.c_int)]
+                ("symmetric", ctypes.c_int), ("l_cap", ctypes.c_double), ("lp_slices", ctypes.c_int),
+                ("quasi", ctypes.c_int)]
 
 
 class sr_norms(ctypes.Structure):

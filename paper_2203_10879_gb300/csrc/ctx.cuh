@@ -65,6 +65,15 @@ struct schur_refine_ctx {
     } rgraph;
     void *ctl = nullptr;                  // device state of the graph's REPEAT loop
     std::vector<cudaStream_t> cstreams;   // capture streams of nested conditional bodies
+    // real quasi-triangular form (opt.quasi): band of T^ (sub, super, diagonal
+    // at offsets 0, nmax, 2 nmax), block array (device and pinned host copy), the
+    // padded problem (order up to nqmax) and its index maps
+    double *band = nullptr;
+    int *qblk = nullptr, *hblk = nullptr;
+    int nqmax = 0;
+    void *TEq = nullptr, *qcpl = nullptr;   // qcpl: couplings of the 2 x 2 blocks, padded order
+    double *dhpq = nullptr;
+    int *qpos = nullptr, *qinv = nullptr, *qblkq = nullptr, *hmaps = nullptr;
     // profiling
     sr_profile prof{};
     std::vector<cudaEvent_t> ev_pool;

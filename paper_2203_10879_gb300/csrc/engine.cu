@@ -17,6 +17,7 @@
 #include "kernels_misc.cuh"
 #include "ozaki.cuh"
 #include "trisolve.cuh"
+#include "quasi.cuh"
 
 void sr::trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long long> &offsets)
 {
@@ -190,7 +191,7 @@ sr_status check_opts(const sr_options &o)
     if (o.qhat_type != SR_QHAT_FP32 && o.qhat_type != SR_QHAT_FP64) return SR_ERR_INVALID_ARG;
     if ((o.batch_mode != 0 && o.batch_mode != 1) || (o.tune != 0 && o.tune != 1) || (o.graph != 0 && o.graph != 1) ||
         o.solve_mode < 0 || o.solve_mode > 2 || (o.symmetric != 0 && o.symmetric != 1) || !(o.l_cap >= 0.0) ||
-        std::isinf(o.l_cap) || o.lp_slices > sr::kOzakiLpSlices)
+        std::isinf(o.l_cap) || o.lp_slices > sr::kOzakiLpSlices || (o.quasi != 0 && o.quasi != 1))
         return SR_ERR_INVALID_ARG;
     if (o.hp_gemm == SR_HP_OZAKI_CRT) {
         // FP64 results: M < 2^128 holds for at most 16 moduli; double-double: 32
@@ -206,6 +207,9 @@ sr_status check_opts(const sr_options &o)
     if (o.dtype == SR_COMPLEX && (!is_emulated(o) || o.lp != SR_LP_FP32)) return SR_ERR_UNSUPPORTED;
     // Sec. 2.5 (real symmetric or complex Hermitian A); the double-double target keeps the general form
     if (o.symmetric && o.target != SR_TARGET_FP64) return SR_ERR_UNSUPPORTED;
+    // the real quasi-triangular form: real data, FP64 target, host loop, general A
+    if (o.quasi && (o.dtype != SR_REAL || o.target != SR_TARGET_FP64 || o.graph || o.symmetric))
+        return SR_ERR_UNSUPPORTED;
     if (is_emulated(o) && !sr::kOzakiBuilt) return SR_ERR_UNSUPPORTED;
     return SR_OK;
 }
@@ -295,6 +299,10 @@ sr_status form_residual(schur_refine_ctx *h, int n, const double *A, int lda, co
     const int ld = h->nmax;
     SR_TRY(hp_gemm(h, false, n, n, n, A, lda, Q, ldq, sr::EpStore{h->AQ, ld}, -1));
     sr::EpSplit<Tl> ep{(Tl *)h->TE, ld, h->diag, That, n};
+    if (h->opt.quasi) {
+        ep.sub = h->band;
+        ep.sup = h->band + h->nmax;
+    }
     SR_TRY(hp_gemm(h, true, n, n, n, Q, ldq, h->AQ, ld, ep, 0));
     return SR_OK;
 }
@@ -575,10 +583,78 @@ sr_status oz_form_residual(schur_refine_ctx *h, int n, const void *Q, int ldq, v
                              typename OzT<C>::Store{(H *)h->AQ, ld}, nullptr, nullptr));
     SR_TRY(sr::ozaki_split(h, h->st, h->oz, sr::OZS_X, n, n, h->AQ, ld, sr::OZ_COLS, s));
     SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, n, s, false, h->dflags));
-    SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, s, 1.0, false,
-                             typename OzT<C>::Split{(L *)h->TE, ld, (H *)h->diag, (H *)That, n}, h->partial,
+    typename OzT<C>::Split sp{(L *)h->TE, ld, (H *)h->diag, (H *)That, n};
+    if constexpr (!C) {
+        if (h->opt.quasi) {
+            sp.sub = h->band;
+            sp.sup = h->band + h->nmax;
+        }
+    }
+    SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, s, 1.0, false, sp, h->partial,
                              &blocks));
     return reduce_to(h, blocks, 0);
+}
+
+// ---- the real quasi-triangular form (opt.quasi) -----------------------------------
+// After T^ is formed: its blocks from its band, the subdiagonal entries that
+// are not couplings of 2 x 2 blocks added to ||E||^2 (dnorm[0], which the split
+// epilogue summed below the subdiagonal), and the block array copied to the
+// host for the solve's padded layout (read after the pass's synchronization).
+sr_status quasi_detect(schur_refine_ctx *h, int n, double *norm)
+{
+    SrPhase ph(h, SR_PROF_OTHER, 0, 4LL * n * (long long)sizeof(double), 1);
+    sr::quasi_blocks_kernel<<<1, 1024, 0, h->st>>>(n, h->diag, h->band, h->band + h->nmax, h->qblk, norm);
+    SR_CUDA_TRY(cudaGetLastError());
+    SR_CUDA_TRY(cudaMemcpyAsync(h->hblk, h->qblk, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    return SR_OK;
+}
+
+// S4 in the quasi-triangular form: the padded problem solved stepwise (the
+// host's block array must be current: called after a synchronization).
+template <typename Tl>
+sr_status solve_quasi(schur_refine_ctx *h, int n, Tl *TE, int ld, const double *dhp)
+{
+    if constexpr (SrNum<Tl>::kind >= 2) {
+        return SR_ERR_UNSUPPORTED;
+    } else {
+        std::vector<int> pos, inv, blkq;
+        const int np = sr::quasi_pad_layout(n, h->hblk, pos, inv, blkq);
+        if (np > h->nqmax) return SR_ERR_INVALID_ARG;
+        // the maps go up through the pinned staging buffer (free again: the
+        // previous upload finished before the last synchronization)
+        int *hp = h->hmaps;
+        std::copy(pos.begin(), pos.end(), hp);
+        std::copy(inv.begin(), inv.end(), hp + n);
+        std::copy(blkq.begin(), blkq.end(), hp + n + np);
+        SR_CUDA_TRY(cudaMemcpyAsync(h->qpos, hp, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, h->st));
+        SR_CUDA_TRY(cudaMemcpyAsync(h->qinv, hp + n, (size_t)np * sizeof(int), cudaMemcpyHostToDevice, h->st));
+        SR_CUDA_TRY(cudaMemcpyAsync(h->qblkq, hp + n + np, (size_t)np * sizeof(int), cudaMemcpyHostToDevice, h->st));
+        SR_TRY(ensure_plan(h, np));
+        Tl *TEq = (Tl *)h->TEq;
+        const int ldq = h->nqmax;
+        {
+            SrPhase ph(h, SR_PROF_OTHER, 0, 2LL * np * np * (long long)sizeof(Tl), 1);
+            const dim3 g((unsigned)((np + 31) / 32), (unsigned)((np + 31) / 32));
+            sr::quasi_pad_kernel<Tl><<<g, 256, 0, h->st>>>(np, h->qinv, h->qblkq, TE, ld, dhp, TEq, ldq, h->dhpq,
+                                                           (Tl *)h->qcpl);
+            SR_CUDA_TRY(cudaGetLastError());
+        }
+        {
+            const int NB = (np + sr::kSolveTile - 1) / sr::kSolveTile;
+            const long long fl = 2LL * np * np * np / 3;
+            SrPhase ph(h, SR_PROF_SOLVE, fl, (long long)np * np * (long long)sizeof(Tl), 2LL * NB);
+            SR_CUDA_TRY(sr::trisolve_quasi_launches<Tl>(h->st, h->aux_st, h->sev0, h->sev1, np, TEq, ldq, h->dhpq,
+                                                        h->qblkq, (const Tl *)h->qcpl, h->dflags, h->plan, h->plan_off,
+                                                        h->opt.l_cap));
+        }
+        {
+            SrPhase ph(h, SR_PROF_OTHER, 0, 2LL * n * n * (long long)sizeof(Tl), 1);
+            const dim3 g((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+            sr::quasi_unpad_kernel<Tl><<<g, 256, 0, h->st>>>(n, h->qpos, h->qblk, TEq, ldq, TE, ld);
+            SR_CUDA_TRY(cudaGetLastError());
+        }
+        return SR_OK;
+    }
 }
 
 template <bool C>
@@ -689,6 +765,7 @@ sr_status run_step(schur_refine_ctx *h, int n, const void *A, int lda, void *dQ,
             SR_TRY(oz_form_residual<C>(h, n, Qc, ldc, dT));
         else if constexpr (!C)
             SR_TRY(form_residual<Tl>(h, n, (const double *)A, lda, Qc, ldc, (double *)dT));
+        if (h->opt.quasi) SR_TRY(quasi_detect(h, n, h->dnorm));
         nr.hp_gemms += 2;
         nr.iters = k;
         SR_TRY(read_back(h));
@@ -706,7 +783,10 @@ sr_status run_step(schur_refine_ctx *h, int n, const void *A, int lda, void *dQ,
             SR_TRY(solve<cf>(h, n, (cf *)h->TE, ld, (const cd *)h->diag));
             SR_TRY(sumsq<cf>(h, n, (const cf *)h->TE, ld, 1, 2));
         } else {
-            SR_TRY(solve<Tl>(h, n, (Tl *)h->TE, ld, h->diag));
+            if (h->opt.quasi)
+                SR_TRY(solve_quasi<Tl>(h, n, (Tl *)h->TE, ld, h->diag));
+            else
+                SR_TRY(solve<Tl>(h, n, (Tl *)h->TE, ld, h->diag));
             SR_TRY(sumsq<Tl>(h, n, (const Tl *)h->TE, ld, 1, 2));
         }
         if (oz) SR_TRY(oz_gram_join(h));
@@ -1305,6 +1385,7 @@ void schur_refine_default_options(sr_options *opt)
     opt->symmetric = 0;
     opt->l_cap = 0.0;
     opt->lp_slices = 0;
+    opt->quasi = 0;
 }
 
 const char *schur_refine_status_string(sr_status s)
@@ -1387,6 +1468,16 @@ void schur_refine_destroy(schur_refine_t h)
     cudaFree(h->flow_acc);
     cudaFree(h->flow_plan);
     if (h->hbuf) cudaFreeHost(h->hbuf);
+    cudaFree(h->band);
+    cudaFree(h->qblk);
+    cudaFree(h->TEq);
+    cudaFree(h->dhpq);
+    cudaFree(h->qpos);
+    cudaFree(h->qinv);
+    cudaFree(h->qblkq);
+    cudaFree(h->qcpl);
+    if (h->hblk) cudaFreeHost(h->hblk);
+    if (h->hmaps) cudaFreeHost(h->hmaps);
     sr::ozaki_free(h->oz);
     delete h;
 }
@@ -1436,6 +1527,21 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     // the dataflow solve's helper accumulators, where that form can serve
     if ((o.dtype == SR_REAL && o.lp == SR_LP_FP32 && o.solve_mode == 0) || o.solve_mode == 1)
         SR_ALLOC(h->flow_acc, nn * lps);
+    if (o.quasi) {
+        // the padded order: at most one padding row per tile of 32 rows
+        h->nqmax = n_max + (n_max + sr::kSolveTile - 2) / (sr::kSolveTile - 1) + 1;
+        const size_t nq = (size_t)h->nqmax;
+        SR_ALLOC(h->band, 3 * (size_t)n_max * sizeof(double));
+        SR_ALLOC(h->qblk, (size_t)n_max * sizeof(int));
+        SR_ALLOC(h->TEq, nq * nq * lps);
+        SR_ALLOC(h->dhpq, nq * sizeof(double));
+        SR_ALLOC(h->qpos, (size_t)n_max * sizeof(int));
+        SR_ALLOC(h->qinv, nq * sizeof(int));
+        SR_ALLOC(h->qblkq, nq * sizeof(int));
+        SR_ALLOC(h->qcpl, nq * lps);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hblk, (size_t)n_max * sizeof(int));
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hmaps, ((size_t)n_max + 2 * nq) * sizeof(int));
+    }
 #undef SR_ALLOC
     if (e == cudaSuccess) {
         // grid of the dataflow solve for each low-precision kind this handle can use
@@ -1648,10 +1754,22 @@ sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int ld
         sr::gemm_dd_kernel<0><<<grid, 256, 0, h->st>>>(n, 0, A, lda, Q, nullptr, ldq, h->AQ, h->Delta, ld,
                                                        nullptr);
         SR_CUDA_TRY(cudaGetLastError());
-        sr::gemm_dd_kernel<1><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, h->AQ, h->Delta, ld, nullptr, nullptr, 0,
-                                                       h->partial);
-        SR_CUDA_TRY(cudaGetLastError());
-        SR_TRY(reduce_to(h, (int)tiles, 4));
+        if (h->opt.quasi) {
+            // the quasi-triangular form: the entries below the diagonal blocks, the
+            // blocks read off the band of this Q^T A Q
+            sr::gemm_dd_kernel<3><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, h->AQ, h->Delta, ld, nullptr, nullptr, 0,
+                                                           h->partial, h->band);
+            SR_CUDA_TRY(cudaGetLastError());
+            SR_TRY(reduce_to(h, (int)tiles, 4));
+            sr::quasi_blocks_kernel<<<1, 1024, 0, h->st>>>(n, h->band + 2 * n, h->band, h->band + n, h->qblk,
+                                                           h->dnorm + 4);
+            SR_CUDA_TRY(cudaGetLastError());
+        } else {
+            sr::gemm_dd_kernel<1><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, h->AQ, h->Delta, ld, nullptr, nullptr, 0,
+                                                           h->partial);
+            SR_CUDA_TRY(cudaGetLastError());
+            SR_TRY(reduce_to(h, (int)tiles, 4));
+        }
         sr::gemm_dd_kernel<2><<<grid, 256, 0, h->st>>>(n, 1, Q, ldq, Q, nullptr, ldq, nullptr, nullptr, 0,
                                                        h->partial);
         SR_CUDA_TRY(cudaGetLastError());
@@ -1669,7 +1787,25 @@ sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, cons
 {
     if (!h || !dTE || !dDiag || n < 1 || n > h->nmax || ld < n) return SR_ERR_INVALID_ARG;
     SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
-    if (is_dd(h->opt))
+    if (h->opt.quasi) {
+        // the blocks from the band of the low-precision T in dTE and the FP64 diagonal
+        const double *d = (const double *)dDiag;
+        const unsigned g = (unsigned)((n + 255) / 256);
+        if (h->opt.lp == SR_LP_FP32)
+            sr::quasi_band_kernel<float><<<g, 256, 0, h->st>>>(n, (const float *)dTE, ld, h->band, h->band + h->nmax);
+        else
+            sr::quasi_band_kernel<double><<<g, 256, 0, h->st>>>(n, (const double *)dTE, ld, h->band,
+                                                                 h->band + h->nmax);
+        SR_CUDA_TRY(cudaGetLastError());
+        sr::quasi_blocks_kernel<<<1, 1024, 0, h->st>>>(n, d, h->band, h->band + h->nmax, h->qblk, nullptr);
+        SR_CUDA_TRY(cudaGetLastError());
+        SR_CUDA_TRY(cudaMemcpyAsync(h->hblk, h->qblk, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+        if (h->opt.lp == SR_LP_FP32)
+            SR_TRY(solve_quasi<float>(h, n, (float *)dTE, ld, d));
+        else
+            SR_TRY(solve_quasi<double>(h, n, (double *)dTE, ld, d));
+    } else if (is_dd(h->opt))
         SR_TRY(solve<double>(h, n, (double *)dTE, ld, (const double *)dDiag, (const double *)dDiag + n));
     else if (is_cplx(h->opt))
         SR_TRY(solve<cf>(h, n, (cf *)dTE, ld, (const cd *)dDiag));

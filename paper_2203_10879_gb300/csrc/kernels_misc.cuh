@@ -29,6 +29,11 @@ struct EpStoreLp {
 template <typename Tl>
 struct EpSplit {
     Tl *TE; int ldte; double *diag; double *That; int ldt;
+    // real quasi-triangular form: T^(k+1, k) to sub[k], T^(k, k+1) to sup[k], and
+    // the subdiagonal left out of ||E||^2 (the entries that are not couplings of
+    // 2 x 2 blocks are added back once the blocks are known: subtracting the
+    // couplings' squares afterwards would cancel ||E||^2 away)
+    double *sub = nullptr, *sup = nullptr;
     template <typename V>
     __device__ double operator()(int i, int j, V v) const
     {
@@ -36,7 +41,11 @@ struct EpSplit {
         TE[sr_idx(i, j, ldte)] = (Tl)x;
         if (That) That[sr_idx(i, j, ldt)] = x;
         if (i == j) diag[i] = x;
-        return i > j ? x * x : 0.0;
+        if (sub) {
+            if (i == j + 1) sub[j] = x;
+            if (j == i + 1) sup[i] = x;
+        }
+        return (i > j && !(sub && i == j + 1)) ? x * x : 0.0;
     }
 };
 
@@ -231,11 +240,15 @@ static __global__ void __launch_bounds__(256) reduce_partials_kernel(const doubl
 // mode 0: store C (hi, lo).  mode 1: partial += sum over i > j of (hi + lo)^2.
 // mode 2: partial += sum over all (i, j) of (C - I)^2 (upper tiles only,
 // off-diagonal entries counted twice; C symmetric).
+// MODE 3 (the quasi-triangular form): as MODE 1 but every subdiagonal entry
+// (j+1, j) is left out of the sum, and the band of C is written to
+// band[0..n) (subdiagonal C(k+1, k)), band[n..2n) (superdiagonal C(k, k+1)) and
+// band[2n..3n) (diagonal), each entry's double-double value rounded once.
 template <int MODE>
 __global__ void __launch_bounds__(256)
 gemm_dd_kernel(int n, int transA, const double *__restrict__ A, int lda, const double *__restrict__ Bhi,
                const double *__restrict__ Blo, int ldb, double *__restrict__ Chi, double *__restrict__ Clo,
-               int ldc, double *__restrict__ partial)
+               int ldc, double *__restrict__ partial, double *__restrict__ band = nullptr)
 {
     constexpr int T = 16;
     __shared__ double As[T][T + 1];
@@ -244,8 +257,9 @@ gemm_dd_kernel(int n, int transA, const double *__restrict__ A, int lda, const d
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int i0 = blockIdx.x * T, j0 = blockIdx.y * T;
     const size_t bid = blockIdx.x + (size_t)gridDim.x * blockIdx.y;
-    // tiles that contribute nothing in modes 1 and 2
-    if ((MODE == 1 && i0 + T - 1 <= j0) || (MODE == 2 && i0 > j0 + T - 1)) {
+    // tiles that contribute nothing in modes 1 and 2 (mode 3 keeps the tiles
+    // that hold superdiagonal entries)
+    if ((MODE == 1 && i0 + T - 1 <= j0) || (MODE == 3 && i0 + T < j0) || (MODE == 2 && i0 > j0 + T - 1)) {
         if (threadIdx.x == 0) partial[bid] = 0.0;
         return;
     }
@@ -281,6 +295,12 @@ gemm_dd_kernel(int n, int transA, const double *__restrict__ A, int lda, const d
                 const double v = acc.hi + acc.lo;
                 part = v * v;
             }
+        } else if (MODE == 3) {
+            const double v = acc.hi + acc.lo;
+            if (i == j + 1) band[j] = v;
+            else if (i > j) part = v * v;
+            if (j == i + 1) band[n + i] = v;
+            if (i == j) band[2 * n + i] = v;
         } else {
             if (i <= j) {
                 if (i == j) acc = dd_plus(acc, {-1.0, 0.0});
