@@ -8,12 +8,16 @@ Qhat = fl32(Q0 expm(1e-6 S))), with A and Qhat resident in HBM. The mixed form
 the all-FP64 form of the same iteration on the same inputs is timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload single|complex|batched]
+                    [--workload single|complex|batched|dd|sym|quasi|small]
 
 --workload complex refines the complex n = 8192 ring problem instead
 (eigenvalues 0.5 exp(2 pi i k/n)(1 + U(0, 0.2)), complex64 starting factor,
 complex64 correction path, emulated complex128 products); the library builds no
-all-FP64 complex form, so that line carries no all-FP64 time.
+all-FP64 complex form, so that line carries no all-FP64 time. --workload dd
+refines n = 2048 to double-double, sym a symmetric n = 4096 problem in the form
+of Sec. 2.5, quasi a real n = 4096 problem whose Schur form has 2 x 2 blocks
+(the real Schur form of Sec. 3), small the n = 64 unit-step problem, batched
+1024 matrices of orders 32 to 512.
 
 Prints one JSON line (rank 0). With N > 1 (torchrun) every rank refines its own
 copy (replicas only: a single refinement does not shard); the value is the
@@ -92,7 +96,12 @@ def bf16_peak(clk, peaks):
     return 1900.0, "of fallback 1.9 PFLOP/s bf16 (no MEASURED_PEAKS.json)"
 
 
-def _workload_name(n, cplx=False, sym=False):
+def _workload_name(n, cplx=False, sym=False, quasi=False):
+    if quasi:
+        return (f"real n={n} planted quasi-triangular A=Q0 T0 Q0^T, mu_k=k/n+U(0,0.5/n), 2x2 blocks "
+                f"[[a, b s], [-b/s, a]] with probability 1/3 (eigenvalues a +- i b), upper std 1/n, "
+                f"Qhat=fl32(Q0 expm(1e-6 S)); Alg. 4 in the real Schur form (Sec. 3) to "
+                f"||below the diagonal blocks||/||A||<=1e-14 sqrt(n)")
     if sym:
         return (f"real symmetric n={n} planted A=Q0 diag(lambda) Q0^T, lambda_k=k/n+U(0,0.5/n), "
                 f"Qhat=fl32(Q0 expm(1e-6 S)); Alg. 4 in the form of Sec. 2.5 to ||stril||/||A||<=1e-14 sqrt(n)")
@@ -204,6 +213,8 @@ def _oracle_problem(workload: str, n: int):
     from paper_2203_10879_gb300 import inputs
     if workload == "sym":
         return inputs.symmetric_real(n)
+    if workload == "quasi":
+        return inputs.quasi_real(n)
     if workload == "complex":
         return inputs.ring_complex(n)
     if workload == "dd":
@@ -222,7 +233,7 @@ def oracle_refine_seconds(workload: str, n: int):
         from oracle import ddtarget
         r = ddtarget.refine_dd((p.A_hi, p.A_lo), p.Qhat)
     else:
-        r = oracle.refine(p.A, p.Qhat, lp="f32", symmetric=workload == "sym")
+        r = oracle.refine(p.A, p.Qhat, lp="f32", symmetric=workload == "sym", quasi=workload == "quasi")
     dt = time.perf_counter() - t0
     return dt, int(getattr(r, "status", -1)), int(getattr(r, "iters", -1))
 
@@ -271,6 +282,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     dd, sym, cplx = args.workload == "dd", args.workload == "sym", args.workload == "complex"
+    quasi = args.workload == "quasi"
     n_ref = args.cpu_sample_n
     times = []
     st = it = None
@@ -284,7 +296,7 @@ def run_reference(args):
         sample = f"double-double oracle (C TwoProd/TwoSum products + C Alg. 2 in FP64) full refinement at n={n_ref}"
     else:
         sample = f"oracle (numpy products + C Alg. 2 in the low precision) full refinement at n={n_ref}"
-    name = _dd_workload_name(n_ref) if dd else _workload_name(n_ref, cplx, sym)
+    name = _dd_workload_name(n_ref) if dd else _workload_name(n_ref, cplx, sym, quasi)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "dd+f64" if dd else "f64+f32", "data": "synthetic",
@@ -399,14 +411,17 @@ def _comparisons(args, mixed, p, n, cplx, sym, hp, hp_name, hdt, ldt, dtype_opt,
         mn.close()
     # the same mixed form with the other form of the solve: stepwise (one launch
     # pair per block subdiagonal) for real data, dataflow (one launch) for complex;
-    # for symmetric A the general form (triangular solve instead of Sec. 2.5's)
-    if sym:
-        sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32)
-    else:
-        alt_mode = 1 if cplx else 2
-        sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, solve_mode=alt_mode, **dtype_opt)
-    alt_ms, _, _ = timed(sw, max(1, min(args.steps, 3)), 2)
-    sw.close()
+    # for symmetric A the general form (triangular solve instead of Sec. 2.5's); the
+    # quasi-triangular form has one solve form (the triangular one fails on its inputs)
+    alt_ms = None
+    if args.workload != "quasi":
+        if sym:
+            sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32)
+        else:
+            alt_mode = 1 if cplx else 2
+            sw = P.Refiner(n, hp_gemm=hp_name[hp], lp=B.SR_LP_FP32, solve_mode=alt_mode, **dtype_opt)
+        alt_ms, _, _ = timed(sw, max(1, min(args.steps, 3)), 2)
+        sw.close()
     # the same mixed form with the other emulated engine (digits <-> residues)
     other_ms, other_hp = None, None
     if hp in ("ozaki", "crt"):
@@ -441,8 +456,11 @@ def run_ours(args):
     n = args.n
     cplx = args.workload == "complex"
     sym = args.workload == "sym"
+    quasi = args.workload == "quasi"
     if sym:
         p = inputs.symmetric_real(n)
+    elif quasi:
+        p = inputs.quasi_real(n)
     else:
         p = inputs.ring_complex(n) if cplx else inputs.jittered_real(n)
     hdt = torch.complex128 if cplx else torch.float64
@@ -452,7 +470,7 @@ def run_ours(args):
     Qhat = dev(p.Qhat)
     Q = torch.empty((n, n), dtype=hdt, device="cuda").t()
     stream = torch.cuda.current_stream()
-    dtype_opt = {"dtype": B.SR_COMPLEX} if cplx else ({"symmetric": 1} if sym else {})
+    dtype_opt = {"dtype": B.SR_COMPLEX} if cplx else ({"symmetric": 1} if sym else ({"quasi": 1} if quasi else {}))
 
     hp_name = {"fp64": B.SR_HP_FP64, "ozaki": B.SR_HP_OZAKI_BF16, "crt": B.SR_HP_OZAKI_CRT}
     hp = ("ozaki" if args.hp == "fp64" else args.hp) if cplx else args.hp
@@ -556,7 +574,7 @@ def run_ours(args):
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128+c64" if cplx else "f64+f32", "data": "synthetic",
-        "config": {"workload": _workload_name(n, cplx, sym), "n": n,
+        "config": {"workload": _workload_name(n, cplx, sym, quasi), "n": n,
                    "form": "mixed: complex64 solve/products" if cplx else "mixed: FP32 solve/products",
                    "hp_gemm": _engine_name(hp, args.slices, dd=False),
                    "lp_products": f"emulated, {args.lp_slices or 3} bf16 digits per operand",
@@ -571,7 +589,9 @@ def run_ours(args):
                    "mixed_vs_all_fp64_speedup": None if ms64 is None else ms64 / ms,
                    "mixed_native_fp64_s": None if mixed_native_ms is None else mixed_native_ms / 1e3,
                    "solve_form": "stepwise (launch pair per block subdiagonal)" if cplx
-                   else ("elementwise (Sec. 2.5, symmetric A)" if sym else "dataflow (one launch per solve)"),
+                   else ("elementwise (Sec. 2.5, symmetric A)" if sym else
+                         "stepwise over 2x2/1x1 block entries, padded order (real Schur form)" if quasi
+                         else "dataflow (one launch per solve)"),
                    "with_other_solve_form_s": None if alt_ms is None else alt_ms / 1e3,
                    "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
                    "phase_rates": phase_rooflines(prof, args.steps),
@@ -1017,7 +1037,8 @@ def main():
     ap.add_argument("--measured-only", action="store_true",
                     help="time the measured path only (no end-to-end, comparison forms or CPU baseline): "
                          "the command the ncu summaries under profiles/ capture")
-    ap.add_argument("--workload", choices=["single", "complex", "batched", "dd", "small", "sym"], default="single")
+    ap.add_argument("--workload", choices=["single", "complex", "batched", "dd", "small", "sym", "quasi"],
+                    default="single")
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--batch-streams", type=int, default=8)
     args = ap.parse_args()
@@ -1029,8 +1050,9 @@ def main():
     if args.cpu_sample_n is None:
         args.cpu_sample_n = {"complex": 2048, "dd": 512}.get(args.workload, 1024)
     if args.cpu_full is None:
-        # the complex n = 8192 oracle refinement takes tens of minutes on the host
-        args.cpu_full = 0 if args.workload == "complex" else 1
+        # the complex n = 8192 oracle refinement takes tens of minutes on the host; the
+        # quasi-triangular line samples at n = 1024 to stay within a few minutes
+        args.cpu_full = 0 if args.workload in ("complex", "quasi") else 1
     args.cpu_full = bool(args.cpu_full)
     if args.measured_only:
         args.no_cpu_baseline = True

@@ -13,9 +13,10 @@
 // block-lower solution of sbl(T L - L T) = -E. Each block entry (I, J) solves
 // T_II X - X T_JJ = -C_IJ (sizes p x q, p, q <= 2) through its Kronecker
 // matrix I (x) T_II - T_JJ^T (x) I (vec(X) column-major), whose diagonal
-// entries t_rr - t_cc are formed from the FP64 diagonal and rounded once,
-// by Gaussian elimination with partial pivoting in the working precision
-// (the first largest pivot; a zero pivot is a shared eigenvalue).
+// entries t_rr - t_cc are formed from the FP64 diagonal and rounded once. The
+// matrix is inverted by Gauss-Jordan elimination with partial pivoting in the
+// working precision (a zero pivot is a shared eigenvalue) before the
+// wavefront reaches the entry, and the inverse applied to -C_IJ when it does.
 //
 // Tiles. The tiled solver needs every block inside one 32 x 32 tile, so the
 // problem is solved in a padded order n': where a 2 x 2 block would start on
@@ -160,8 +161,8 @@ __global__ void quasi_unpad_kernel(int n, const int *__restrict__ pos, const int
     }
 }
 
-// rounded operations without contraction (the Kronecker solves follow the
-// oracle's operations one by one)
+// rounded operations without contraction: the elimination below takes the
+// oracle's steps one by one, so a zero pivot is found exactly where it finds one
 __device__ __forceinline__ float q_mul(float x, float y) { return __fmul_rn(x, y); }
 __device__ __forceinline__ double q_mul(double x, double y) { return __dmul_rn(x, y); }
 __device__ __forceinline__ float q_sub(float x, float y) { return __fsub_rn(x, y); }
@@ -169,11 +170,75 @@ __device__ __forceinline__ double q_sub(double x, double y) { return __dsub_rn(x
 __device__ __forceinline__ float q_div(float x, float y) { return __fdiv_rn(x, y); }
 __device__ __forceinline__ double q_div(double x, double y) { return __ddiv_rn(x, y); }
 
+// Row u of the inverse of a Kronecker matrix of order m <= 4 (padded to 4 x 4
+// with the identity): Gaussian elimination with partial pivoting (the first
+// largest pivot; the padding rows are never chosen while a real row has a
+// nonzero in the column), applied to the identity alongside, then back
+// substitution. Fully unrolled, in registers. Returns false on a zero pivot
+// (a shared eigenvalue).
+template <typename T>
+__device__ __forceinline__ bool kron_inverse_row(T (&M)[4][4], int u, T (&row)[4])
+{
+    const T Z = (T)0, One = (T)1;
+    T R[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) R[r][c] = r == c ? One : Z;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int p = k;
+#pragma unroll
+        for (int r = k + 1; r < 4; ++r)
+            if (fabs(M[r][k]) > fabs(M[p][k])) p = r;
+#pragma unroll
+        for (int r = k + 1; r < 4; ++r) {
+            if (p == r) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const T t0 = M[k][c]; M[k][c] = M[r][c]; M[r][c] = t0;
+                    const T t1 = R[k][c]; R[k][c] = R[r][c]; R[r][c] = t1;
+                }
+            }
+        }
+        if (M[k][k] == Z) { ok = false; M[k][k] = One; }
+#pragma unroll
+        for (int r = k + 1; r < 4; ++r) {
+            const T f = q_div(M[r][k], M[k][k]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c >= k) M[r][c] = q_sub(M[r][c], q_mul(f, M[k][c]));
+                R[r][c] = q_sub(R[r][c], q_mul(f, R[k][c]));
+            }
+        }
+    }
+    T Xc[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 3; r >= 0; --r) {
+            T acc = R[r][c];
+#pragma unroll
+            for (int v = r + 1; v < 4; ++v) acc = q_sub(acc, q_mul(M[r][v], Xc[v][c]));
+            Xc[r][c] = q_div(acc, M[r][r]);
+        }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        if (r == u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) row[c] = Xc[r][c];
+    return ok;
+}
+
 // Solve of the tiles of subdiagonal t in the padded order (the stepwise form):
 // 1024 threads, thread (lane a, warp b) owns entry (a, b) of the tile. Phase 1
-// adds E and the two products of subdiagonal t + 1 (as trisolve_leaf_kernel);
-// phase 2 is the wavefront over block entries described at the top of this
-// file, each block entry solved by the thread of its first entry.
+// adds E and the two products of subdiagonal t + 1 (as trisolve_leaf_kernel).
+// Phase 2 is the wavefront over block entries described at the top of this
+// file. Each block entry's Kronecker matrix depends on T alone, so every
+// thread of the entry inverts it before the wavefront and keeps its own row
+// of the inverse; when the entry is final, each thread reads the entry's
+// pending sums and forms its own unknown (a product of the row with -C).
 template <typename T>
 __global__ void __launch_bounds__(1024, 1)
 trisolve_quasi_leaf_kernel(int n, T *__restrict__ TE, int ld, const double *__restrict__ dhp,
@@ -237,73 +302,49 @@ trisolve_quasi_leaf_kernel(int n, T *__restrict__ TE, int ld, const double *__re
     Cs[a][b] = Z;
     __syncthreads();
     const int fs = ra - cl;                          // step at which a's and b's block entry is final
-    const bool leader = own && a == ra && b == cs;
-    const int p = rb[ra] == 2 ? 2 : 1, q = cb[cs] == 2 ? 2 : 1;
+    const int p = rb[ra] == 2 ? 2 : 1, q = cb[cs] == 2 ? 2 : 1, m = p * q;
+    const int ru = a - ra, cu = b - cs, me = ru + cu * p;   // this entry's index in vec(X)
+    int bad = 0;
+    // T_II X - X T_JJ = -C through the Kronecker matrix, vec index r + c p; the
+    // diagonal t_rr - t_cc formed in FP64 and rounded once
+    T kinv[4] = {Z, Z, Z, Z};
+    if (own) {
+        T K[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int ur = u % p, uc = u / p;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int vr = v % p, vc = v / p;
+                T kv = (u == v) ? (T)1 : Z;
+                if (u < m && v < m) {
+                    if (u == v) kv = (T)(dI[ra + ur] - dJ[cs + uc]);
+                    else if (uc == vc) kv = Ti[ra + ur][ra + vr];
+                    else if (ur == vr) kv = -Tj[cs + vc][cs + uc];
+                    else kv = Z;
+                }
+                K[u][v] = kv;
+            }
+        }
+        if (!kron_inverse_row(K, me, kinv)) bad |= SR_FLAG_NONDISTINCT;
+    }
     const int wlo = (D > 0) ? -(B - 1) : 1;
     T xv = Z;
-    int bad = 0;
     for (int w = B - 1; w >= wlo; --w) {
         const bool fin = own && fs == w;
         if (fin) Cs[a][b] = acc;
         __syncthreads();
-        if (fin && leader) {
-            // T_II X - X T_JJ = -C through the Kronecker matrix, vec index r + c p
-            const int m = p * q;
-            T K[4][4], rhs[4], x[4];
+        if (fin) {
+            T x = Z;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int ru = u % p, cu = u / p;
-                rhs[u] = u < m ? -Cs[ra + ru][cs + cu] : Z;
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int rv = v % p, cv = v / p;
-                    T kv = Z;
-                    if (u < m && v < m) {
-                        if (u == v) {
-                            kv = (T)(dI[ra + ru] - dJ[cs + cu]);
-                        } else {
-                            if (cu == cv) kv = Ti[ra + ru][ra + rv];
-                            if (ru == rv) kv = -Tj[cs + cv][cs + cu];
-                        }
-                    }
-                    K[u][v] = kv;
-                }
-            }
-            bool zero = false;
-            for (int k = 0; k < m && !zero; ++k) {
-                int piv = k;
-                for (int u = k + 1; u < m; ++u)
-                    if (fabs((double)K[u][k]) > fabs((double)K[piv][k])) piv = u;
-                if (K[piv][k] == Z) { zero = true; break; }
-                if (piv != k) {
-                    for (int v = 0; v < m; ++v) { const T tt = K[k][v]; K[k][v] = K[piv][v]; K[piv][v] = tt; }
-                    const T tt = rhs[k]; rhs[k] = rhs[piv]; rhs[piv] = tt;
-                }
-                for (int u = k + 1; u < m; ++u) {
-                    const T f = q_div(K[u][k], K[k][k]);
-                    for (int v = k; v < m; ++v) K[u][v] = q_sub(K[u][v], q_mul(f, K[k][v]));
-                    rhs[u] = q_sub(rhs[u], q_mul(f, rhs[k]));
-                }
-            }
-            if (zero) {
-                bad |= SR_FLAG_NONDISTINCT;
-                for (int u = 0; u < m; ++u) X[ra + u % p][cs + u / p] = Z;
-            } else {
-                for (int u = m - 1; u >= 0; --u) {
-                    T sacc = rhs[u];
-                    for (int v = u + 1; v < m; ++v) sacc = q_sub(sacc, q_mul(K[u][v], x[v]));
-                    x[u] = q_div(sacc, K[u][u]);
-                }
-                for (int u = 0; u < m; ++u) {
-                    T xu = x[u];
-                    if (cap > 0.0 && fabs((double)xu) > (double)(T)cap) xu = Z;   // Example 4's trick
-                    if (!sr_finite(xu)) bad |= SR_FLAG_NONFINITE;
-                    X[ra + u % p][cs + u / p] = xu;
-                }
-            }
+            for (int v = 0; v < 4; ++v)
+                if (v < m) x = sr_fma(kinv[v], -Cs[ra + v % p][cs + v / p], x);
+            if (cap > 0.0 && fabs((double)x) > (double)(T)cap) x = Z;   // Example 4's trick
+            if (!sr_finite(x)) bad |= SR_FLAG_NONFINITE;
+            X[a][b] = x;
+            xv = x;
         }
         __syncthreads();
-        if (fin) xv = X[a][b];
         if (own && fs < w) {
             // the row block finished in column b starts at row s; the column
             // block finished in row a ends at column e
