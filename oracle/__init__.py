@@ -3,7 +3,9 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package. It shares no code with the CUDA library
 and never calls it. See :mod:`oracle.alg` for what each function follows;
-:mod:`oracle.ddtarget` holds the double-double working-precision form of Alg. 4.
+:mod:`oracle.ddtarget` holds the double-double working-precision form of Alg. 4,
+:mod:`oracle.mptarget` the form with an exact fixed-point high precision that
+checks the multi-word (triple-double) forms.
 """
 from ._lib import build, set_threads, max_threads  # noqa: F401
 from .alg import (  # noqa: F401

@@ -539,3 +539,81 @@ def unit_step_dd(n: int = 2048, seed: int = BASE_SEED + 5, upper_std: float | No
     return planted_dd(n, eig_unit_step(n), seed, pert=1e-14, upper_std=sd,
                       recipe=f"real n={n} double-double, lambda_k=1+k/64, upper std {sd:.3g}, "
                              f"Qhat=fl64(Q0 expm(1e-14 S))")
+
+
+# ---------------------------------------------------------------------------
+# Planted problems whose Schur decomposition is known exactly (working
+# precisions above double-double)
+#
+# For n a power of two, Q0 = D1 P1 (H D2 H / n) P2, with H the Sylvester
+# Hadamard matrix (entries +-1, H H = n I), D1, D2 random sign diagonals and
+# P1, P2 random permutations, is exactly orthogonal, and its entries are
+# multiples of 1/n. With T0 upper triangular of dyadic entries (multiples of
+# 2^-20), every entry of Q0 T0 and of (Q0 T0) Q0^T, and every partial sum of
+# the float64 products that form them, is a multiple of 2^-20 / n^2 below
+# ||T0||_2 in magnitude (Cauchy-Schwarz over any subset of the terms): below
+# 2^53 units while ||T0||_2 < 2^53 / (2^20 n^2), so float64 forms
+# A = Q0 T0 Q0^T exactly. The refined factors can then be compared with the
+# exact Q0 and T0 at any precision.
+
+@dataclass
+class PlantedExact:
+    """A = Q0 T0 Q0^T exactly in float64, Q0 exactly orthogonal, float64 start."""
+
+    A: np.ndarray
+    Qhat: np.ndarray
+    Q0: np.ndarray
+    T0: np.ndarray
+    lam: np.ndarray
+    seed: int
+    recipe: str
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[0]
+
+
+def _sylvester_hadamard(n: int) -> np.ndarray:
+    H = np.ones((1, 1))
+    while H.shape[0] < n:
+        H = np.block([[H, H], [H, -H]])
+    return H
+
+
+def planted_exact(n: int, lam: np.ndarray, seed: int, *, pert: float = 1e-14, upper_std: float | None = None,
+                  frac_bits: int = 20, recipe: str = "") -> PlantedExact:
+    """The exact planted problem described above. ``lam`` must be dyadic (it is
+    the diagonal of T0 as given); the strictly upper entries are normal with
+    standard deviation ``upper_std`` (default 1/n) rounded to multiples of
+    2^-frac_bits. Qhat = fl64(Q0 expm(pert S)), S skew-symmetric N(0,1)."""
+    if n < 1 or n & (n - 1):
+        raise ValueError("n must be a power of two")
+    lam = np.asarray(lam, dtype=np.float64)
+    st = Stream(seed)
+    sd = (1.0 / n) if upper_std is None else float(upper_std)
+    scale = float(2 ** frac_bits)
+    U = np.round(st.normal((n, n)) * sd * scale) / scale
+    T0 = np.triu(U, 1) + np.diag(lam)
+    H = _sylvester_hadamard(n)
+    d1 = np.where(st.uniform((n,)) < 0.5, -1.0, 1.0)
+    d2 = np.where(st.uniform((n,)) < 0.5, -1.0, 1.0)
+    p1 = np.argsort(st.uniform((n,)), kind="stable")
+    p2 = np.argsort(st.uniform((n,)), kind="stable")
+    C = (H * d2[None, :]) @ H / n                       # H D2 H / n, exact
+    Q0 = np.asfortranarray(d1[:, None] * C[p1][:, p2])
+    A = np.asfortranarray((Q0 @ T0) @ Q0.T)
+    S = _skew(st, n, False)
+    X = pert * S
+    D = X + X @ X / 2.0 + X @ X @ X / 6.0               # expm(X) - I to third order
+    Qhat = np.asfortranarray(Q0 + Q0 @ D)
+    return PlantedExact(A=A, Qhat=Qhat, Q0=Q0, T0=np.asfortranarray(T0), lam=lam, seed=seed,
+                        recipe=recipe or f"real n={n} exact planted (Hadamard Q0), upper std {sd:.3g} "
+                                         f"in multiples of 2^-{frac_bits}, Qhat=fl64(Q0 expm({pert:g} S))")
+
+
+def unit_step_exact(n: int = 2048, seed: int = BASE_SEED + 9) -> PlantedExact:
+    """The triple-double workload: lambda_k = 1 + k/64 (dyadic), exact A."""
+    return planted_exact(n, eig_unit_step(n), seed, pert=1e-14,
+                         recipe=f"real n={n} exact planted A=Q0 T0 Q0^T (Q0 = D1 P1 H D2 H P2 / n, Hadamard H), "
+                                f"lambda_k=1+k/64, upper std 1/n in multiples of 2^-20, "
+                                f"Qhat=fl64(Q0 expm(1e-14 S))")
