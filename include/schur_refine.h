@@ -65,8 +65,15 @@ enum { SR_REAL = 0, SR_COMPLEX = 1 };
    lp = SR_LP_FP64 and qhat_type = SR_QHAT_FP64. A double-double matrix is
    two column-major planes with the same leading dimension ld, hi and lo,
    standing for hi + lo; the lo plane starts ld * c elements after the hi
-   plane, c = the number of columns stored. */
-enum { SR_TARGET_FP64 = 0, SR_TARGET_DD = 1 };
+   plane, c = the number of columns stored.
+   SR_TARGET_TD (triple-double, about 159 bits: Sec. 3's multi-double high
+   precisions one level further) is built for real data with lp =
+   SR_LP_FP64, qhat_type = SR_QHAT_FP64, hp_gemm = SR_HP_OZAKI_CRT (48
+   moduli; ozaki_slices 0 or 48) and orders up to 8192. A triple-double
+   matrix is three planes x0, x1, x2 (each ld * c elements after the one
+   before), standing for x0 + x1 + x2 with x1 the double nearest to
+   x - x0 and x2 the double nearest to x - x0 - x1. */
+enum { SR_TARGET_FP64 = 0, SR_TARGET_DD = 1, SR_TARGET_TD = 2 };
 /* engine of the high-precision products (Sec. 2.4: "hp matrix-matrix
    multiplications"; the paper uses the Ozaki scheme, Sec. 3) */
 enum {
@@ -88,7 +95,7 @@ enum { SR_QHAT_FP32 = 0, SR_QHAT_FP64 = 1 };
 
 typedef struct {
     int dtype;        /* SR_REAL or SR_COMPLEX */
-    int target;       /* SR_TARGET_FP64 or SR_TARGET_DD */
+    int target;       /* SR_TARGET_FP64, SR_TARGET_DD or SR_TARGET_TD */
     int hp_gemm;      /* SR_HP_FP64 or SR_HP_OZAKI_BF16 */
     int lp;           /* SR_LP_FP32 (mixed form) or SR_LP_FP64 (all-FP64 form) */
     int qhat_type;    /* SR_QHAT_FP32 or SR_QHAT_FP64 */
@@ -99,14 +106,16 @@ typedef struct {
                          high-precision products; <= 0 selects the library
                          default (7; 14 for SR_TARGET_DD); at most 7 (14).
                          SR_HP_OZAKI_CRT: the number of moduli N (default 16;
-                         32 for SR_TARGET_DD; at most 16 (32)); the operands
+                         32 for SR_TARGET_DD, 48 for SR_TARGET_TD; at most 16
+                         (34; 48)); the operands
                          then carry t bits, the largest t with
                          K 2^(2t) < M / 2 for inner length K and M the
                          product of the moduli (t = 56 for N = 16 and
                          K <= 4096) */
     double tol;       /* stop when ||stril(T^)||_F / ||A||_F <= tol and the
                          last ||Q^H Q - I||_F <= sqrt(tol); <= 0 selects
-                         1e-14 * sqrt(n) (1e-28 * n for SR_TARGET_DD) */
+                         1e-14 * sqrt(n) (1e-28 * n for SR_TARGET_DD, 1e-45 * n
+                         for SR_TARGET_TD) */
     int profile;      /* 1: time every phase with CUDA events on the handle's
                          stream (see schur_refine_get_profile) */
     int batch_streams;/* schur_refine_batched with worker streams: matrices
@@ -213,12 +222,12 @@ sr_status schur_refine_create(schur_refine_t *h, int n_max, const sr_options *op
  * Runs Alg. 4 (Sec. 2.4) on one matrix of order n <= n_max.
  *   dA        device, n x n, lda: A in FP64 (interleaved complex128 when
  *             dtype is SR_COMPLEX; two planes when target is SR_TARGET_DD,
- *             and likewise dQ and dT). Not modified.
+ *             three for SR_TARGET_TD, and likewise dQ and dT). Not modified.
  *   dQ        device, n x n, ldq, FP64 (complex128). In: the starting factor
  *             when dQhat is NULL. Out: the refined factor.
  *   dQhat     device, n x n with leading dimension ldq, element type
  *             qhat_type (complex64/complex128 when complex; FP64, one
- *             plane, for SR_TARGET_DD), or NULL. When
+ *             plane, for SR_TARGET_DD and SR_TARGET_TD), or NULL. When
  *             given, Q is first set to one Newton-Schulz step of Qhat
  *             converted to FP64 (Alg. 4, second line; eq. NS), and dQ's input
  *             value is ignored.
@@ -314,8 +323,9 @@ sr_status schur_refine_residuals_noalloc(int n, const void *dA, int lda, const v
  *          triangle holds L; the upper triangle is unchanged.
  *   dDiag  device, n entries, FP64 (complex128): the diagonal of T in high
  *          precision; divisors t_ii - t_jj are formed from it and then
- *          rounded to the low precision. SR_TARGET_DD: 2n entries, the high
- *          parts of the double-double diagonal followed by the low parts.
+ *          rounded to the low precision. SR_TARGET_DD and SR_TARGET_TD: 2n
+ *          entries, the high parts of the double-double diagonal (for
+ *          SR_TARGET_TD the two leading words) followed by the low parts.
  * Returns SR_ERR_NONDISTINCT on a zero divisor (Theorem 1), SR_ERR_NONFINITE
  * on a non-finite entry of L. Synchronizes the stream.
  */
@@ -354,8 +364,9 @@ sr_status schur_refine_solve_plan(int n, unsigned long long *tasks, long long ca
  * SR_HP_OZAKI_CRT; the paper computes its high-precision products with the
  * Ozaki scheme, Sec. 3, and this is the Chinese-remainder variant of that
  * scheme). Host code only; no device is used.
- *   N        number of moduli, 1..32
- *   limbs    4 (FP64 results, needs M < 2^128) or 8 (double-double results)
+ *   N        number of moduli, 1..49
+ *   limbs    4 (FP64 results, needs M < 2^128), 8 (double-double results,
+ *            M < 2^256) or 12 (triple-double results, M < 2^384)
  *   K        inner length of the product
  *   moduli   host, N entries: the moduli, the N largest pairwise coprime
  *            integers <= 256 taken greedily from 256 down
@@ -378,6 +389,9 @@ sr_status schur_refine_crt_info(int N, int limbs, long long K, int *moduli, unsi
  *   dB  device, k x n, ldb;  dC device, m x n, ldc (overwritten).
  * SR_TARGET_DD: A, B and C are double-double (two planes each, see
  * SR_TARGET_DD), C accurate to about k * 1e-32 relative to |op(A)| |B|.
+ * SR_TARGET_TD: three planes each; C is the exact product of the operands cut
+ * to t = 162 bits per row of op(A) and column of B (K <= 4096), rounded once
+ * to a triple-double.
  * Sizes up to n_max in every dimension.
  */
 sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, const void *dA,

@@ -24,7 +24,7 @@ Steps, in the order of Alg. 4 (Sec. 2.4):
     lp; Alg. 2 in lp; W; Y = Q^T Q - I in hp; YW, W^2, W^3 in lp;
     Sigma = 2I + 2W - Y - YW + W^2 + W^3 in hp; Q <- 1/2 Q Sigma in hp.
   * :func:`refine_fx`    -- the REPEAT loop with the stop test of the other
-    forms and the tolerance 1e-44 n.
+    forms and the tolerance 1e-45 n.
   * :func:`residuals_exact` -- ||stril(Q^T A Q)||_F / ||A||_F and
     ||Q^T Q - I||_F of given A, Q evaluated exactly.
 """
@@ -187,8 +187,11 @@ def iteration_fx(A: np.ndarray, Q: np.ndarray, F: int = FBITS, full_sigma: bool 
 
 
 def default_tol_td(n: int) -> float:
-    """The triple-double target: 1e-44 n (about 7000 n units of 2^-159)."""
-    return 1e-44 * n
+    """The triple-double target: 1e-45 n (about 700 n units of 2^-159). The
+    passes from a float64 start reach about 1e-14, 1e-28, 1e-42 and then the
+    working precision's floor: the tolerance lies inside the last gap, so the
+    count of passes does not hang on the third pass's rounding."""
+    return 1e-45 * n
 
 
 @dataclass

@@ -166,8 +166,13 @@ namespace {
 
 bool is_cplx(const sr_options &o) { return o.dtype == SR_COMPLEX; }
 size_t lp_size(const sr_options &o) { return (o.lp == SR_LP_FP32 ? sizeof(float) : sizeof(double)) * (is_cplx(o) ? 2 : 1); }
-// high-precision element: FP64, complex128, or a double-double pair (two planes)
-size_t hp_size(const sr_options &o) { return sizeof(double) * (is_cplx(o) || o.target == SR_TARGET_DD ? 2 : 1); }
+// high-precision element: FP64, complex128, a double-double pair (two planes)
+// or a triple-double (three planes)
+size_t hp_size(const sr_options &o)
+{
+    if (o.target == SR_TARGET_TD) return 3 * sizeof(double);
+    return sizeof(double) * (is_cplx(o) || o.target == SR_TARGET_DD ? 2 : 1);
+}
 
 // high-precision products emulated on the tensor cores (digits or residues)
 bool is_emulated(const sr_options &o) { return o.hp_gemm == SR_HP_OZAKI_BF16 || o.hp_gemm == SR_HP_OZAKI_CRT; }
@@ -175,6 +180,7 @@ bool is_emulated(const sr_options &o) { return o.hp_gemm == SR_HP_OZAKI_BF16 || 
 // bf16 digits (7; 14 for double-double) or residues modulo 16 (32) moduli per operand
 int oz_count(const sr_options &o)
 {
+    if (o.target == SR_TARGET_TD) return sr::kCrtDefaultModuliTD;
     if (o.ozaki_slices > 0) return o.ozaki_slices;
     const bool dd = o.target == SR_TARGET_DD;
     if (o.hp_gemm == SR_HP_OZAKI_CRT) return dd ? sr::kCrtDefaultModuliDD : sr::kCrtDefaultModuli;
@@ -184,7 +190,7 @@ int oz_count(const sr_options &o)
 sr_status check_opts(const sr_options &o)
 {
     if (o.dtype != SR_REAL && o.dtype != SR_COMPLEX) return SR_ERR_INVALID_ARG;
-    if (o.target != SR_TARGET_FP64 && o.target != SR_TARGET_DD) return SR_ERR_INVALID_ARG;
+    if (o.target != SR_TARGET_FP64 && o.target != SR_TARGET_DD && o.target != SR_TARGET_TD) return SR_ERR_INVALID_ARG;
     if (o.hp_gemm != SR_HP_FP64 && o.hp_gemm != SR_HP_OZAKI_BF16 && o.hp_gemm != SR_HP_OZAKI_CRT)
         return SR_ERR_INVALID_ARG;
     if (o.lp != SR_LP_FP32 && o.lp != SR_LP_FP64) return SR_ERR_INVALID_ARG;
@@ -194,14 +200,23 @@ sr_status check_opts(const sr_options &o)
         std::isinf(o.l_cap) || o.lp_slices > sr::kOzakiLpSlices || (o.quasi != 0 && o.quasi != 1))
         return SR_ERR_INVALID_ARG;
     if (o.hp_gemm == SR_HP_OZAKI_CRT) {
-        // FP64 results: M < 2^128 holds for at most 16 moduli; double-double: 32
-        if (o.ozaki_slices > (o.target == SR_TARGET_DD ? sr::kCrtMaxModuli : sr::kCrtDefaultModuli))
+        // FP64 results: M < 2^128 holds for at most 16 moduli; double-double
+        // (M < 2^256): 34; triple-double: the 48 of its form
+        const int mx = o.target == SR_TARGET_DD   ? sr::kCrtMaxModuliDD
+                       : o.target == SR_TARGET_TD ? sr::kCrtDefaultModuliTD
+                                                  : sr::kCrtDefaultModuli;
+        if (o.ozaki_slices > mx ||
+            (o.target == SR_TARGET_TD && o.ozaki_slices > 0 && o.ozaki_slices != sr::kCrtDefaultModuliTD))
             return SR_ERR_INVALID_ARG;
     } else if (o.ozaki_slices > (o.target == SR_TARGET_DD ? sr::kOzakiMaxSlicesDD : sr::kOzakiMaxSlices)) {
         return SR_ERR_INVALID_ARG;
     }
     // double-double target: real data, FP64 correction path, FP64 start
     if (o.target == SR_TARGET_DD && (o.dtype != SR_REAL || o.lp != SR_LP_FP64 || o.qhat_type != SR_QHAT_FP64))
+        return SR_ERR_UNSUPPORTED;
+    // triple-double target: the same, with the residue-form products only
+    if (o.target == SR_TARGET_TD && (o.dtype != SR_REAL || o.lp != SR_LP_FP64 || o.qhat_type != SR_QHAT_FP64 ||
+                                     o.hp_gemm != SR_HP_OZAKI_CRT || o.graph))
         return SR_ERR_UNSUPPORTED;
     // complex data: the emulated products with the complex64 correction path
     if (o.dtype == SR_COMPLEX && (!is_emulated(o) || o.lp != SR_LP_FP32)) return SR_ERR_UNSUPPORTED;
@@ -1113,6 +1128,11 @@ struct DdMat {
     double *hi, *lo;
     int ld;
 };
+// a triple-double matrix: three planes (caller: ld * n elements apart)
+struct TdMat {
+    double *x0, *x1, *x2;
+    int ld;
+};
 
 bool is_dd(const sr_options &o) { return o.target == SR_TARGET_DD; }
 int oz_s_dd(const schur_refine_ctx *h) { return oz_count(h->opt); }
@@ -1358,6 +1378,202 @@ sr_status run_step_dd(schur_refine_ctx *h, int n, const void *dA, int lda, void 
     return status;
 }
 
+// ---- the triple-double target (SR_TARGET_TD) -----------------------------------------
+// Sec. 3 refines to working precisions above double-double by holding each
+// high-precision number as several doubles; here three (about 159 bits), the
+// most that one set of moduli <= 256 carries: the products are the residue
+// form with 48 moduli (t = 162-bit operands at K <= 4096), rebuilt into
+// 12-limb integers and rounded once to triple-doubles; the sums of the
+// epilogues are exact and rounded once. The low precision is FP64 (solve with
+// divisors from the two leading words of the diagonal, FP64-class products YW,
+// W^2, W^3 with 7 digits), as in the double-double form.
+bool is_td(const sr_options &o) { return o.target == SR_TARGET_TD; }
+
+TdMat td_caller(const void *p, int ld, int n)
+{
+    double *a = (double *)p;
+    const size_t pl = (size_t)ld * (size_t)n;
+    return {a, a + pl, a + 2 * pl, ld};
+}
+TdMat td_work(const schur_refine_ctx *h, double *p)
+{
+    const size_t pl = (size_t)h->nmax * (size_t)h->nmax;
+    return {p, p + pl, p + 2 * pl, h->nmax};
+}
+
+sr_status td_split(schur_refine_ctx *h, int slot, int n, TdMat X, int layout)
+{
+    return sr::ozaki_split_td(h, h->st, h->oz, slot, n, n, X.x0, X.x1, X.x2, X.ld, layout, sr::kCrtDefaultModuliTD);
+}
+
+// Y = Q^T Q - I and ||Y||^2 -> dnorm[1], from the column residues of Q in OZS_COLS
+sr_status td_gram(schur_refine_ctx *h, int n)
+{
+    const int s = sr::kCrtDefaultModuliTD;
+    const TdMat Y = td_work(h, h->Y);
+    int blocks = 0;
+    SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_COLS, n, n, n, s, true, h->dflags));
+    SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_COLS, n, n, s, 1.0, true,
+                             sr::EpMinusITD{Y.x0, Y.x1, Y.x2, Y.ld}, h->partial, &blocks));
+    return reduce_to(h, blocks, 1);
+}
+
+// Qn = Q + alpha Q X
+sr_status td_apply(schur_refine_ctx *h, int n, TdMat Q, TdMat X, TdMat Qn, double alpha)
+{
+    const int s = sr::kCrtDefaultModuliTD;
+    SR_TRY(td_split(h, sr::OZS_QROWS, n, Q, sr::OZ_ROWS));
+    SR_TRY(td_split(h, sr::OZS_X, n, X, sr::OZ_COLS));
+    SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_QROWS, sr::OZS_X, n, n, n, s, false, h->dflags));
+    return sr::ozaki_combine(h, h->st, h->oz, sr::OZS_QROWS, sr::OZS_X, n, n, s, 1.0, false,
+                             sr::EpUpdateTD{Q.x0, Q.x1, Q.x2, Q.ld, Qn.x0, Qn.x1, Qn.x2, Qn.ld, alpha}, nullptr,
+                             nullptr);
+}
+
+// S1 + S2: A Q (A's row residues in OZS_ROWS), T^ = Q^T (A Q) into TE, the
+// diagonal's two leading words and That; ||E||^2 (leading words) -> dnorm[slot]
+sr_status td_form_residual(schur_refine_ctx *h, int n, TdMat Q, TdMat That, int slot)
+{
+    const int s = sr::kCrtDefaultModuliTD;
+    const TdMat AQ = td_work(h, h->AQ);
+    int blocks = 0;
+    SR_TRY(td_split(h, sr::OZS_COLS, n, Q, sr::OZ_COLS));
+    SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, n, n, n, s, false, h->dflags));
+    SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, n, n, s, 1.0, false,
+                             sr::EpStoreTD{AQ.x0, AQ.x1, AQ.x2, AQ.ld}, nullptr, nullptr));
+    SR_TRY(td_split(h, sr::OZS_X, n, AQ, sr::OZ_COLS));
+    SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, n, s, false, h->dflags));
+    const sr::EpSplitTD ep{(double *)h->TE, h->nmax, h->diag, h->diag_lo, That.x0, That.x1, That.x2, That.ld};
+    SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, s, 1.0, false, ep, h->partial, &blocks));
+    return reduce_to(h, blocks, slot);
+}
+
+// S5-S8: Y, W = L - L^T (FP64), YW, W^2, W^3 (FP64-class, 7 digits, Y rounded to
+// its leading word), Delta = Sigma - 2I summed exactly, Q_new = Q + 1/2 Q Delta
+sr_status td_update(schur_refine_ctx *h, int n, TdMat Q, TdMat Qn)
+{
+    using namespace sr;
+    const int ld = h->nmax;
+    cudaStream_t st = h->st;
+    SR_TRY(td_gram(h, n));   // Q's column residues are those of the residual's product
+    const TdMat Y = td_work(h, h->Y), Dl = td_work(h, h->Delta);
+    double *Wd = h->Wd, *W2 = (double *)h->W2, *YW = (double *)h->YW;
+    double *W2Y = (double *)h->W2Y, *W2YW = (double *)h->W2YW;
+    {
+        SrPhase ph(h, SR_PROF_OTHER, 0, 16LL * n * n, 1);
+        dim3 grid((n + 31) / 32, (n + 31) / 32);
+        form_skew_kernel<double><<<grid, 256, 0, st>>>(n, (const double *)h->TE, ld, Wd, ld);
+        SR_CUDA_TRY(cudaGetLastError());
+    }
+    const bool full = h->opt.full_sigma != 0;
+    const EpDeltaTD ed{(const double *)h->TE, ld, YW, W2, full ? W2Y : nullptr, full ? W2YW : nullptr, ld,
+                       Y.x0, Y.x1, Y.x2, Y.ld, Dl.x0, Dl.x1, Dl.x2, Dl.ld};
+    const int sl = kOzakiDefaultSlices;
+    OzakiWork &w = h->oz;
+    SR_TRY(ozaki_split(h, st, w, OZS_W, n, n, Wd, ld, OZ_COLS, sl));
+    SR_TRY(ozaki_split(h, st, w, OZS_Y, n, n, Y.x0, ld, OZ_COLS, sl));
+    SR_TRY(ozaki_product(h, st, w, OZS_W, OZS_W, n, n, n, sl, true, h->dflags));
+    SR_TRY(ozaki_combine(h, st, w, OZS_W, OZS_W, n, n, sl, -1.0, true, EpStore{W2, ld}, nullptr, nullptr));
+    SR_TRY(ozaki_product(h, st, w, OZS_Y, OZS_W, n, n, n, sl, false, h->dflags));
+    SR_TRY(ozaki_combine(h, st, w, OZS_Y, OZS_W, n, n, sl, 1.0, false, EpStore{YW, ld}, nullptr, nullptr));
+    SR_TRY(ozaki_split(h, st, w, OZS_W2, n, n, W2, ld, OZ_COLS, sl));
+    if (full) {
+        SR_TRY(ozaki_product(h, st, w, OZS_W2, OZS_Y, n, n, n, sl, false, h->dflags));
+        SR_TRY(ozaki_combine(h, st, w, OZS_W2, OZS_Y, n, n, sl, 1.0, false, EpStore{W2Y, ld}, nullptr, nullptr));
+        SR_TRY(ozaki_split(h, st, w, 7, n, n, W2Y, ld, OZ_ROWS, sl));
+        SR_TRY(ozaki_product(h, st, w, 7, OZS_W, n, n, n, sl, false, h->dflags));
+        SR_TRY(ozaki_combine(h, st, w, 7, OZS_W, n, n, sl, 1.0, false, EpStore{W2YW, ld}, nullptr, nullptr));
+    }
+    SR_TRY(ozaki_product(h, st, w, OZS_W, OZS_W2, n, n, n, sl, false, h->dflags));
+    SR_TRY(ozaki_combine(h, st, w, OZS_W, OZS_W2, n, n, sl, -1.0, false, ed, nullptr, nullptr));
+    return td_apply(h, n, Q, Dl, Qn, 0.5);
+}
+
+sr_status copy_td(schur_refine_ctx *h, int n, TdMat src, TdMat dst)
+{
+    if (src.x0 == dst.x0) return SR_OK;
+    SrPhase ph(h, SR_PROF_OTHER, 0, 48LL * n * n, 3);
+    const double *s[3] = {src.x0, src.x1, src.x2};
+    double *d[3] = {dst.x0, dst.x1, dst.x2};
+    for (int k = 0; k < 3; ++k)
+        SR_CUDA_TRY(cudaMemcpy2DAsync(d[k], (size_t)dst.ld * 8, s[k], (size_t)src.ld * 8, (size_t)n * 8, n,
+                                      cudaMemcpyDeviceToDevice, h->st));
+    return SR_OK;
+}
+
+// One call of Alg. 4 with the triple-double target (residue-form products).
+sr_status run_step_td(schur_refine_ctx *h, int n, const void *dA, int lda, void *dQ, int ldq, const void *dQhat,
+                      void *dT, sr_norms *out)
+{
+    const int ld = h->nmax;
+    const double tol = h->opt.tol > 0 ? h->opt.tol : 1e-45 * (double)n;
+    const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 10;
+    sr_norms nr{};
+    nr.stril_rel = nr.orth = nr.w_norm = NAN;
+    const TdMat A = td_caller(dA, lda, n), Qcaller = td_caller(dQ, ldq, n);
+    const TdMat That = dT ? td_caller(dT, n, n) : TdMat{nullptr, nullptr, nullptr, n};
+    SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
+    SR_TRY(sumsq<double>(h, n, A.x0, lda, 0, 3));
+    SR_TRY(td_split(h, sr::OZS_ROWS, n, A, sr::OZ_ROWS));
+    TdMat Qc = Qcaller, Qo = td_work(h, h->Qw);
+    double y_last = NAN;
+    if (dQhat) {
+        // Alg. 4: Qhat (FP64) as a triple-double, then Q <- Q - 1/2 Q (Q^T Q - I) (eq. NS)
+        {
+            SrPhase ph(h, SR_PROF_OTHER, 0, 32LL * n * n, 3);
+            SR_CUDA_TRY(cudaMemcpy2DAsync(Qc.x0, (size_t)Qc.ld * 8, dQhat, (size_t)ldq * 8, (size_t)n * 8, n,
+                                          cudaMemcpyDeviceToDevice, h->st));
+            SR_CUDA_TRY(cudaMemset2DAsync(Qc.x1, (size_t)Qc.ld * 8, 0, (size_t)n * 8, n, h->st));
+            SR_CUDA_TRY(cudaMemset2DAsync(Qc.x2, (size_t)Qc.ld * 8, 0, (size_t)n * 8, n, h->st));
+        }
+        SR_TRY(td_split(h, sr::OZS_COLS, n, Qc, sr::OZ_COLS));
+        SR_TRY(td_gram(h, n));
+        SR_TRY(td_apply(h, n, Qc, td_work(h, h->Y), Qo, -0.5));
+        std::swap(Qc, Qo);
+        nr.hp_gemms += 2;
+        SR_TRY(read_back(h));
+        y_last = sqrt(h->hbuf[1]);
+        nr.orth = y_last;
+    }
+    const double anorm = sqrt(h->hbuf[3] > 0 ? h->hbuf[3] : 1.0);
+    sr_status status = SR_ERR_NOT_CONVERGED;
+    double prev = INFINITY;
+    for (int k = 1; k <= max_iter; ++k) {
+        SR_TRY(td_form_residual(h, n, Qc, That, 0));
+        nr.hp_gemms += 2;
+        nr.iters = k;
+        SR_TRY(read_back(h));
+        if (timed_out(h)) { status = SR_ERR_TIMEOUT; break; }
+        const double rT = sqrt(h->hbuf[0]) / anorm;
+        nr.stril_rel = rT;
+        if (!isfinite(rT)) { status = SR_ERR_NONFINITE; break; }
+        const bool ok_y = !(y_last > sqrt(tol));
+        if (rT <= tol && ok_y) { status = SR_OK; break; }
+        if (k >= 3 && rT > 10.0 * prev) { status = SR_ERR_NOT_CONVERGED; break; }
+        prev = rT;
+        SR_TRY(solve<double>(h, n, (double *)h->TE, ld, h->diag, h->diag_lo));
+        SR_TRY(sumsq<double>(h, n, (const double *)h->TE, ld, 1, 2));
+        SR_TRY(read_back(h));
+        const int f = host_flags(h);
+        if (f & SR_FLAG_TIMEOUT) { status = SR_ERR_TIMEOUT; break; }
+        if (f & SR_FLAG_NONDISTINCT) { status = SR_ERR_NONDISTINCT; break; }
+        if (f & SR_FLAG_NONFINITE) { status = SR_ERR_NONFINITE; break; }
+        nr.w_norm = sqrt(2.0 * h->hbuf[2]);
+        SR_TRY(td_update(h, n, Qc, Qo));
+        nr.hp_gemms += 2;
+        std::swap(Qc, Qo);
+        SR_TRY(read_back(h));
+        y_last = sqrt(h->hbuf[1]);
+        nr.orth = y_last;
+        status = SR_ERR_NOT_CONVERGED;
+    }
+    SR_TRY(copy_td(h, n, Qc, Qcaller));
+    SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+    harvest(h);
+    if (out) *out = nr;
+    return status;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -1557,7 +1773,8 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->sev0, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->sev1, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(h->dnorm, 0, 8 * sizeof(double));
-    const bool dd = o.target == SR_TARGET_DD;
+    const bool td = o.target == SR_TARGET_TD;
+    const bool dd = o.target == SR_TARGET_DD || td;   // FP64 low precision with a multi-word diagonal
     if (e == cudaSuccess) h->diag_lo = dd ? h->diag + n_max : nullptr;
     if (e == cudaSuccess && dd) e = cudaMalloc((void **)&h->Wd, nn * sizeof(double));
     if (e == cudaSuccess && is_emulated(o)) {
@@ -1589,7 +1806,7 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
                                          (1u << sr::OZS_QROWS))
                                       : 0u;
         if (e == cudaSuccess)
-            e = sr::ozaki_alloc(h->oz, n_max, caps, is_cplx(o), crt ? shp : 0, crt_mask, dd ? 8 : 4);
+            e = sr::ozaki_alloc(h->oz, n_max, caps, is_cplx(o), crt ? shp : 0, crt_mask, td ? 12 : dd ? 8 : 4);
         if (e == cudaSuccess) e = cudaMalloc((void **)&h->partial2, h->npartial * sizeof(double));
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->gram_st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gev0, cudaEventDisableTiming);
@@ -1611,6 +1828,7 @@ sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, vo
                             void *dT, sr_norms *out)
 {
     if (!h || !dA || !dQ || n < 1 || n > h->nmax || lda < n || ldq < n) return SR_ERR_INVALID_ARG;
+    if (is_td(h->opt)) return run_step_td(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
     if (is_dd(h->opt)) {
         if (is_emulated(h->opt)) return run_step_dd<true>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
         return run_step_dd<false>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
@@ -1720,7 +1938,18 @@ sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int ld
     const size_t tiles = (size_t)((n + 15) / 16) * (size_t)((n + 15) / 16);
     if (tiles > h->npartial) return SR_ERR_INVALID_ARG;
     dim3 grid((n + 15) / 16, (n + 15) / 16);
-    if (is_dd(h->opt)) {
+    if (is_td(h->opt)) {
+        // the triple-double products of the iteration (residue form, 48 moduli),
+        // each rounded once: T^'s entries below the diagonal carry errors near
+        // 2^-159 ||A||, far below the target
+        const TdMat A = td_caller(dA, lda, n), Q = td_caller(dQ, ldq, n);
+        SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
+        SR_TRY(td_split(h, sr::OZS_ROWS, n, A, sr::OZ_ROWS));
+        SR_TRY(td_form_residual(h, n, Q, TdMat{nullptr, nullptr, nullptr, n}, 4));
+        SR_TRY(td_gram(h, n));
+        SR_CUDA_TRY(cudaMemcpyAsync(h->dnorm + 5, h->dnorm + 1, sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        SR_TRY(sumsq<double>(h, n, A.x0, lda, 0, 6));
+    } else if (is_dd(h->opt)) {
         const DdMat A = dd_caller(dA, lda, n), Q = dd_caller(dQ, ldq, n), M = dd_work(h, h->AQ);
         sr::gemm_ddq_kernel<0><<<grid, 256, 0, h->st>>>(n, 0, A.hi, A.lo, lda, Q.hi, Q.lo, ldq, M.hi, M.lo, ld,
                                                         nullptr);
@@ -1805,7 +2034,7 @@ sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, cons
             SR_TRY(solve_quasi<float>(h, n, (float *)dTE, ld, d));
         else
             SR_TRY(solve_quasi<double>(h, n, (double *)dTE, ld, d));
-    } else if (is_dd(h->opt))
+    } else if (is_dd(h->opt) || is_td(h->opt))
         SR_TRY(solve<double>(h, n, (double *)dTE, ld, (const double *)dDiag, (const double *)dDiag + n));
     else if (is_cplx(h->opt))
         SR_TRY(solve<cf>(h, n, (cf *)dTE, ld, (const cd *)dDiag));
@@ -1844,7 +2073,16 @@ sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, c
     if (m > h->nmax || n > h->nmax || k > h->nmax) return SR_ERR_INVALID_ARG;
     if (lda < (transA ? k : m) || ldb < k || ldc < m) return SR_ERR_INVALID_ARG;
     SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
-    if (is_dd(h->opt)) {
+    if (is_td(h->opt)) {
+        const TdMat A = td_caller(dA, lda, transA ? m : k), B = td_caller(dB, ldb, n), C = td_caller(dC, ldc, n);
+        const int s = sr::kCrtDefaultModuliTD;
+        SR_TRY(sr::ozaki_split_td(h, h->st, h->oz, sr::OZS_ROWS, m, k, A.x0, A.x1, A.x2, lda,
+                                  transA ? sr::OZ_COLS : sr::OZ_ROWS, s));
+        SR_TRY(sr::ozaki_split_td(h, h->st, h->oz, sr::OZS_COLS, n, k, B.x0, B.x1, B.x2, ldb, sr::OZ_COLS, s));
+        SR_TRY(sr::ozaki_product(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, m, n, k, s, false, h->dflags));
+        SR_TRY(sr::ozaki_combine(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, m, n, s, 1.0, false,
+                                 sr::EpStoreTD{C.x0, C.x1, C.x2, C.ld}, nullptr, nullptr));
+    } else if (is_dd(h->opt)) {
         const DdMat A = dd_caller(dA, lda, transA ? m : k), B = dd_caller(dB, ldb, n), C = dd_caller(dC, ldc, n);
         const sr::EpStoreDD ep{C.hi, C.lo, C.ld};
         if (is_emulated(h->opt)) {

@@ -989,6 +989,123 @@ ozaki_residues_fast_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__
     }
 }
 
+// Triple-double operands: x0 + x1 + x2 times 2^(t - e), each word rounded to the
+// nearest unit, summed exactly in a 192-bit two's complement integer
+// (|x| < 2^e, so the sum stays below 2^(t+1) < 2^175).
+__device__ __forceinline__ void td_fixed_add(double x, int t, int e, u64 (&X)[3])
+{
+    const u64 bits = (u64)__double_as_longlong(x);
+    const int eb = (int)((bits >> 52) & 0x7ff);
+    u64 mant = bits & 0xfffffffffffffull;
+    int ex;
+    if (eb == 0) ex = -1074; else { mant |= 1ull << 52; ex = eb - 1075; }
+    if (mant == 0) return;
+    const int sh = ex + t - e;                     // x 2^(t-e) = mant 2^sh, sh <= t - 52 <= 122
+    u64 v[3] = {0, 0, 0};
+    if (sh >= 0) {
+        const int q = sh >> 6, r = sh & 63;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (k == q) v[k] = mant << r;
+            if (k == q + 1 && r) v[k] = mant >> (64 - r);
+        }
+    } else if (-sh < 64) {
+        v[0] = (mant + (1ull << (-sh - 1))) >> (-sh);
+    }
+    if (bits >> 63) {
+        u64 c = 1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const u64 nv = ~v[k] + c;
+            c = (c && nv == 0) ? 1ull : 0ull;
+            v[k] = nv;
+        }
+    }
+    u64 c = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const u64 s1 = X[k] + v[k];
+        const u64 c1 = s1 < X[k] ? 1ull : 0ull;
+        const u64 s2 = s1 + c;
+        const u64 c2 = s2 < s1 ? 1ull : 0ull;
+        X[k] = s2;
+        c = c1 | c2;
+    }
+}
+
+// The residues of triple-double operands modulo the NM moduli (NM fixed at
+// compile time, so that every modulus is an immediate). The fixed-point
+// integer is cut into 11 pieces of 16 bits, the top one signed (bits 160-175;
+// t <= 174 keeps the integer inside them); for modulus m,
+// v = off + sum_k u_k (2^(16 k) mod m) is non-negative and below 2^31
+// (off = m (floor(2^24 / m) + 1) lifts the most negative top term), and
+// v mod m is the residue, taken in the symmetric range. Each thread turns 4
+// consecutive entries of one vector into residues and stores the 4 bf16
+// values of a modulus at once (the layout of ozaki_residues_fast_kernel).
+template <int LAYOUT, int NM>
+__global__ void __launch_bounds__(256)
+ozaki_residues_td_kernel(int R, int K, int Kp, const double *__restrict__ X0, const double *__restrict__ X1,
+                         const double *__restrict__ X2, int ld, int t, int Pmax, int Kmax,
+                         const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
+                         int *__restrict__ exps)
+{
+    constexpr int P = 11;
+    __shared__ double tw[3][32][33];
+    __shared__ int sexp[32];
+    const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * RES_KT;
+    if (threadIdx.x < 32) {
+        const int r = r0 + threadIdx.x;
+        const int e = (r < R) ? split_exponent(vmax[r]) : 0;
+        sexp[threadIdx.x] = e;
+        if (blockIdx.y == 0) exps[r] = e;
+    }
+    const int v = threadIdx.x >> 3, g = threadIdx.x & 7;
+    const size_t pstride = (size_t)Pmax * Kmax;
+    for (int k0 = kbeg; k0 < kbeg + RES_KT && k0 < Kp; k0 += 32) {
+        __syncthreads();
+        split_load_tile<double, LAYOUT>(tw[0], X0, ld, R, K, INT_MAX, r0, k0);
+        split_load_tile<double, LAYOUT>(tw[1], X1, ld, R, K, INT_MAX, r0, k0);
+        split_load_tile<double, LAYOUT>(tw[2], X2, ld, R, K, INT_MAX, r0, k0);
+        __syncthreads();
+        const int r = r0 + v, kk = k0 + 4 * g;
+        const int e = sexp[v];
+        const bool live = e != kOzakiExpNonfinite && r < R;
+        int32_t u[4][P];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            u64 X[3] = {0, 0, 0};
+            if (live) {
+#pragma unroll
+                for (int wd = 0; wd < 3; ++wd) td_fixed_add(tw[wd][v][4 * g + x], t, e, X);
+            }
+#pragma unroll
+            for (int k = 0; k < P - 1; ++k) {
+                const int b = 16 * k;
+                u[x][k] = (int32_t)((X[b >> 6] >> (b & 63)) & 0xffffull);
+            }
+            u[x][P - 1] = (int32_t)(int16_t)((X[2] >> 32) & 0xffffull);   // bits 160-175, signed
+        }
+        __nv_bfloat16 *o = out + (size_t)r * Kmax + (size_t)kk;
+#pragma unroll
+        for (int l = 0; l < NM; ++l) {
+            constexpr int kOffUnit = 1 << 24;
+            const int m = crt_mod(l);
+            float f[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                int32_t s = m * (kOffUnit / m + 1);
+#pragma unroll
+                for (int k = 0; k < P; ++k) s += u[x][k] * (int32_t)crt_pw16(k, l);
+                int32_t rr = (int32_t)((uint32_t)s % (uint32_t)m);
+                if (2 * rr > m) rr -= m;
+                f[x] = (float)rr;
+            }
+            *reinterpret_cast<uint2 *>(o + (size_t)l * pstride) =
+                make_uint2(crt_pack_bf16(f[0], f[1]), crt_pack_bf16(f[2], f[3]));
+        }
+    }
+}
+
 // Splits levels 0..s-1 (level l costs l + 1 digit pairs) into G contiguous
 // non-empty groups minimising the largest group cost (linear partition by
 // dynamic programming); returns that cost.
@@ -1092,9 +1209,10 @@ cudaError_t encode_digits_map(void *map, void *base, int rows, int Kmax, int box
 
 namespace {
 
-// little-endian 32-bit limbs, enough for M < 2^288 and its products by 256
+// little-endian 32-bit limbs, enough for M < 2^384 and its products by 2^64
 struct Big {
-    uint32_t v[10] = {};
+    static constexpr int kW = kCrtMaxLimbs + 2;   // room for M y_l before the shift
+    uint32_t v[kW] = {};
     void mul_small(uint32_t m)
     {
         unsigned long long c = 0;
@@ -1103,7 +1221,7 @@ struct Big {
     uint32_t div_small(uint32_t m)   // *this /= m, returns the remainder
     {
         unsigned long long r = 0;
-        for (int k = 9; k >= 0; --k) {
+        for (int k = kW - 1; k >= 0; --k) {
             const unsigned long long t = (r << 32) | v[k];
             v[k] = (uint32_t)(t / m);
             r = t % m;
@@ -1113,14 +1231,14 @@ struct Big {
     uint32_t mod_small(uint32_t m) const { Big c = *this; return c.div_small(m); }
     int bits() const
     {
-        for (int k = 9; k >= 0; --k)
+        for (int k = kW - 1; k >= 0; --k)
             if (v[k]) return 32 * k + 32 - __builtin_clz(v[k]);
         return 0;
     }
     void shl(int s)
     {
         const int w = s / 32, b = s % 32;
-        for (int k = 9; k >= 0; --k) {
+        for (int k = kW - 1; k >= 0; --k) {
             const uint32_t hi = k - w >= 0 ? v[k - w] : 0, lo = k - w - 1 >= 0 ? v[k - w - 1] : 0;
             v[k] = b ? (hi << b) | (lo >> (32 - b)) : hi;
         }
@@ -1128,7 +1246,7 @@ struct Big {
     double to_double() const
     {
         double d = 0.0;
-        for (int k = 9; k >= 0; --k) d = d * 4294967296.0 + (double)v[k];
+        for (int k = kW - 1; k >= 0; --k) d = d * 4294967296.0 + (double)v[k];
         return d;
     }
 };
@@ -1137,7 +1255,7 @@ struct Big {
 
 bool crt_build_table(int N, int L, CrtTable &t)
 {
-    if (N < 1 || N > kCrtMaxModuli || (L != 4 && L != 8)) return false;
+    if (N < 1 || N > kCrtMaxModuli || (L != 4 && L != 8 && L != 12)) return false;
     t = CrtTable{};
     t.N = N;
     // the largest integers <= 256 that are coprime to every one taken before
@@ -1309,7 +1427,7 @@ sr_status ozaki_split_dd(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int
 {
     OzakiSlot &sl = w.slot[slot];
     if (w.cplx || slot < 0 || slot >= kOzakiSlots || s < 1 || s > sl.cap ||
-        s > (sl.crt ? kCrtMaxModuli : kOzakiMaxSlicesDD) || R > w.Pmax || K > ozaki_k_limit(false) || K > w.nmax)
+        s > (sl.crt ? kCrtMaxModuliDD : kOzakiMaxSlicesDD) || R > w.Pmax || K > ozaki_k_limit(false) || K > w.nmax)
         return SR_ERR_INVALID_ARG;
     const int Kp = (K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
     const int Rp = (R + 31) / 32 * 32;
@@ -1348,6 +1466,37 @@ sr_status ozaki_split_dd(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int
         else
             ozaki_digits_dd_kernel<OZ_ROWS><<<gdig, 256, 0, st>>>(R, K, Kp, Xhi, Xlo, ld, s, w.Pmax, w.Kmax, w.vmax,
                                                                   out, ex);
+    }
+    SR_CUDA_TRY(cudaGetLastError());
+    return SR_OK;
+}
+
+sr_status ozaki_split_td(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K,
+                         const double *X0, const double *X1, const double *X2, int ld, int layout, int s)
+{
+    if (w.cplx || slot < 0 || slot >= kOzakiSlots) return SR_ERR_INVALID_ARG;
+    OzakiSlot &sl = w.slot[slot];
+    if (!sl.crt || s != kCrtDefaultModuliTD || s != w.crt.N || w.crt.L != 12 || s > sl.cap || R > w.Pmax ||
+        K > ozaki_k_limit(false) || K > w.nmax)
+        return SR_ERR_INVALID_ARG;
+    const int Kp = (K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const int Rp = (R + 31) / 32 * 32;
+    SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, 3LL * R * K * 8 + 2LL * s * Kp * Rp, 2);
+    sl.layout = layout;
+    sl.t = crt_bits(w.crt, K);
+    if (sl.t < 1 || sl.t > 174) return SR_ERR_UNSUPPORTED;
+    __nv_bfloat16 *out = (__nv_bfloat16 *)sl.dig;
+    SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)Rp * sizeof(unsigned long long), st));
+    const dim3 gmax(Rp / 32, (K + SPLIT_KT - 1) / SPLIT_KT);
+    const dim3 gres(Rp / 32, (Kp + RES_KT - 1) / RES_KT);
+    if (layout == OZ_COLS) {
+        ozaki_absmax_kernel<double, OZ_COLS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, X0, ld, w.vmax);
+        ozaki_residues_td_kernel<OZ_COLS, kCrtDefaultModuliTD><<<gres, 256, 0, st>>>(
+            R, K, Kp, X0, X1, X2, ld, sl.t, w.Pmax, w.Kmax, w.vmax, out, sl.exps);
+    } else {
+        ozaki_absmax_kernel<double, OZ_ROWS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, X0, ld, w.vmax);
+        ozaki_residues_td_kernel<OZ_ROWS, kCrtDefaultModuliTD><<<gres, 256, 0, st>>>(
+            R, K, Kp, X0, X1, X2, ld, sl.t, w.Pmax, w.Kmax, w.vmax, out, sl.exps);
     }
     SR_CUDA_TRY(cudaGetLastError());
     return SR_OK;

@@ -55,6 +55,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "td.cuh"
 
 namespace sr {
 
@@ -72,10 +73,12 @@ constexpr int kOzakiMaxK = 16384;     // keeps every level sum below 2^31
 constexpr int kOzakiExpNonfinite = INT_MIN;
 constexpr int kOzakiSlots = 8;
 // residue form
-constexpr int kCrtMaxModuli = 32;
+constexpr int kCrtMaxModuli = 49;         // every pairwise coprime integer <= 256 the greedy rule takes
 constexpr int kCrtDefaultModuli = 16;     // FP64 operands: t = 56 bits at K <= 4096
 constexpr int kCrtDefaultModuliDD = 32;   // double-double operands: t = 113 bits at K <= 8192
-constexpr int kCrtMaxLimbs = 8;           // 32-bit limbs of M (4 for N <= 16, 8 for N <= 32)
+constexpr int kCrtMaxModuliDD = 34;       // the most whose product stays below 2^256 (8 limbs)
+constexpr int kCrtDefaultModuliTD = 48;   // triple-double operands: t = 162 bits at K <= 4096
+constexpr int kCrtMaxLimbs = 12;          // 32-bit limbs of M (4 for N <= 16, 8 for N <= 34, 12 for N <= 49)
 
 // The moduli in order: the largest pairwise coprime integers <= 256 taken
 // greedily from 256 down (the host table builder computes the same list).
@@ -83,9 +86,10 @@ constexpr int kCrtMaxLimbs = 8;           // 32-bit limbs of M (4 for N <= 16, 8
 // constant derived from a modulus folds into an immediate.
 __host__ __device__ constexpr int crt_mod(int l)
 {
-    constexpr int kList[kCrtMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223,
-                                          217, 211, 199, 197, 193, 191, 181, 179, 173, 167, 163,
-                                          157, 151, 149, 139, 137, 131, 127, 113, 109, 107};
+    constexpr int kList[kCrtMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211,
+                                          199, 197, 193, 191, 181, 179, 173, 167, 163, 157, 151, 149, 139,
+                                          137, 131, 127, 113, 109, 107, 103, 101, 97,  89,  83,  79,  73,
+                                          71,  67,  61,  59,  53,  47,  43,  41,  37,  29};
     return l >= 0 && l < kCrtMaxModuli ? kList[l] : 1;
 }
 // 2^(16 k) mod m_l
@@ -127,8 +131,8 @@ struct CrtTable {
 
 // Builds the table for the first N moduli of the fixed list (the largest
 // pairwise coprime integers <= 256, greedily), with M held in L = 4 limbs
-// (FP64 results) or 8 (double-double results). Returns false for N outside
-// [1, kCrtMaxModuli] or M >= 2^(32 L).
+// (FP64 results), 8 (double-double results) or 12 (triple-double results).
+// Returns false for N outside [1, kCrtMaxModuli] or M >= 2^(32 L).
 bool crt_build_table(int N, int L, CrtTable &t);
 // Bits t of the integer operands for N moduli and inner length K: the
 // largest t with K 2^(2t) < M / 2 (every rebuilt C is then exact).
@@ -247,6 +251,10 @@ sr_status ozaki_split(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int sl
 // so up to kOzakiMaxSlicesDD digits carry the low part.
 sr_status ozaki_split_dd(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K,
                          const double *Xhi, const double *Xlo, int ld, int layout, int s);
+// Triple-double operands (three planes): residues modulo the 48 moduli of the
+// triple-double form (t = 162 bits at K <= 4096)
+sr_status ozaki_split_td(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K,
+                         const double *X0, const double *X1, const double *X2, int ld, int layout, int s);
 
 // Level planes of the product of the vectors in slot `rows` (output rows i)
 // with those in slot `cols` (output columns j), inner length k. With
@@ -800,6 +808,111 @@ ozaki_crt_combine_kernel(int m, int n, const uint8_t *__restrict__ planes, int l
     }
 }
 
+// Triple-double results (L = 12 limbs, the 48 moduli of the triple-double
+// operands): one entry per rebuild, so that the twelve 64-bit column sums
+// stay in registers; a block covers 32 x 32 entries, thread (lane a, warp w)
+// rebuilds rows a of columns w, w + 8, w + 16, w + 24. The rebuilt integer is
+// rounded to a triple-double from its 256 leading bits (the bits below them
+// lie far beyond the 159 kept). Mirrored blocks are turned in shared memory as
+// in ozaki_crt_combine_kernel.
+__device__ __forceinline__ tdv crt_to_td(const uint32_t (&mag)[12], bool neg, int x)
+{
+    int k = 7;   // leading limb of the 256-bit window (limbs k-7 .. k)
+#pragma unroll
+    for (int a = 11; a >= 8; --a)
+        if (k == 7 && mag[a] != 0) k = a;
+    u64 W[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int a = 0; a < 12; ++a) {
+            if (a == k - 7 + 2 * q) lo = mag[a];
+            if (a == k - 6 + 2 * q) hi = mag[a];
+        }
+        W[q] = ((u64)hi << 32) | lo;
+    }
+    return td_round_u256(W, neg, x + 32 * (k - 7));
+}
+
+template <int NM>
+__device__ __forceinline__ tdv crt_value_td(const uint8_t *__restrict__ planes, size_t off, size_t pstride,
+                                            const CrtRebuildSm &T, int e1, int e2, int tsum, bool negs)
+{
+    constexpr int L = 12;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite) return {nan, nan, nan};
+    u64 acc[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) acc[k] = 0ull;
+#pragma unroll 4
+    for (int l = 0; l < NM; ++l) {
+        const uint32_t R = planes[off + (size_t)l * pstride];
+#pragma unroll
+        for (int k = 0; k < L; k += 4) {
+            const uint4 w4 = *reinterpret_cast<const uint4 *>(&T.w[l][k]);
+            acc[k] += (u64)R * w4.x;
+            acc[k + 1] += (u64)R * w4.y;
+            acc[k + 2] += (u64)R * w4.z;
+            acc[k + 3] += (u64)R * w4.w;
+        }
+    }
+    uint32_t mag[L];
+    const bool ng = crt_reduce<L>(acc, T, mag) != negs;
+    return crt_to_td(mag, ng, e1 + e2 - tsum - T.sigma);
+}
+
+template <class EP, int NM>
+__global__ void __launch_bounds__(256)
+ozaki_crt_combine_td_kernel(int m, int n, const uint8_t *__restrict__ planes, int ldp, size_t pstride,
+                            const int *__restrict__ ea, const int *__restrict__ fb, int tsum, double sign, int mirror,
+                            EP ep, double *partial, const CrtTable *__restrict__ tab)
+{
+    __shared__ CrtRebuildSm T;
+    __shared__ tdv turned[32][33];
+    crt_stage(T, tab, 12);
+    __syncthreads();
+    const bool negs = sign < 0;
+    const int a = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    const bool below = mirror && blockIdx.x > blockIdx.y;
+    const int rb = (below ? blockIdx.y : blockIdx.x) * 32, cb = (below ? blockIdx.x : blockIdx.y) * 32;
+    const int rlim = below ? n : m, clim = below ? m : n;
+    double part = 0.0;
+    if (below) {
+        // rebuild the mirrored block (rows along the planes' contiguous index), turn it
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const int r = rb + a, c = cb + wv + 8 * q;
+            if (r < rlim && c < clim)
+                turned[wv + 8 * q][a] = crt_value_td<NM>(planes, (size_t)r + (size_t)c * ldp, pstride, T, ea[r],
+                                                         fb[c], tsum, negs);
+        }
+        __syncthreads();
+        const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + a, j = j0 + wv + 8 * q;
+            if (i < m && j < n) part += ep(i, j, turned[a][wv + 8 * q]);
+        }
+    } else {
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const int i = rb + a, j = cb + wv + 8 * q;
+            if (i >= m || j >= n) continue;
+            tdv v;
+            if (mirror && i > j)   // below the diagonal of a diagonal block: the mirrored entry
+                v = crt_value_td<NM>(planes, (size_t)j + (size_t)i * ldp, pstride, T, ea[j], fb[i], tsum, negs);
+            else
+                v = crt_value_td<NM>(planes, (size_t)i + (size_t)j * ldp, pstride, T, ea[i], fb[j], tsum, negs);
+            part += ep(i, j, v);
+        }
+    }
+    if (partial) {
+        part = sr_block_sum<256>(part);
+        if (threadIdx.x == 0) partial[blockIdx.x + (size_t)gridDim.x * blockIdx.y] = part;
+    }
+}
+
 inline int ozaki_crt_limbs(const OzakiWork &w) { return w.crt.L; }
 
 // epilogues of complex products carry `static constexpr bool kComplex`
@@ -820,7 +933,13 @@ sr_status ozaki_combine(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
         const int tsum = w.slot[rows].t + w.slot[cols].t;
         const dim3 grid((m + 31) / 32, (n + 31) / 32);
         const uint8_t *pl = reinterpret_cast<const uint8_t *>(w.planes);
-        if constexpr (ep_is_dd<EP>::value) {
+        if constexpr (ep_is_td<EP>::value) {
+            if (w.cplx || w.crt.L != 12 || s != kCrtDefaultModuliTD) return SR_ERR_INVALID_ARG;
+            SrPhase ph(h, SR_PROF_OZ_COMBINE, 24LL * 12 * s * m * n, (long long)m * n * (1LL * s + 48), 1);
+            ozaki_crt_combine_td_kernel<EP, kCrtDefaultModuliTD><<<grid, 256, 0, st>>>(
+                m, n, pl, w.Pmax, (size_t)w.Pmax * w.Pmax, w.slot[rows].exps, w.slot[cols].exps, tsum, sign,
+                mirror ? 1 : 0, ep, partial, w.crt_dev);
+        } else if constexpr (ep_is_dd<EP>::value) {
             if (w.cplx || w.crt.L != 8) return SR_ERR_INVALID_ARG;
             SrPhase ph(h, SR_PROF_OZ_COMBINE, 16LL * 8 * s * m * n, (long long)m * n * (1LL * s + 32), 1);
             if (s == kCrtDefaultModuliDD)
@@ -849,7 +968,9 @@ sr_status ozaki_combine(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
         if (blocks) *blocks = ozaki_blocks(m, n);
         return SR_OK;
     }
-    if constexpr (ep_is_dd<EP>::value) {
+    if constexpr (ep_is_td<EP>::value) {
+        return SR_ERR_INVALID_ARG;   // triple-double products exist in the residue form only
+    } else if constexpr (ep_is_dd<EP>::value) {
         if (w.cplx || s > w.levels) return SR_ERR_INVALID_ARG;
         SrPhase ph(h, SR_PROF_OZ_COMBINE, 24LL * s * m * n, (long long)m * n * (4LL * s + 32), 1);
         dim3 grid((m + 31) / 32, (n + 31) / 32);

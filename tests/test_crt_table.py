@@ -23,7 +23,8 @@ def _moduli(N):
     return ms
 
 
-@pytest.mark.parametrize("N,limbs", [(1, 4), (8, 4), (15, 4), (16, 4), (20, 8), (31, 8), (32, 8)])
+@pytest.mark.parametrize("N,limbs", [(1, 4), (8, 4), (15, 4), (16, 4), (20, 8), (31, 8), (32, 8), (34, 8),
+                                     (40, 12), (48, 12), (49, 12)])
 def test_table_matches_definition(N, limbs):
     for K in (1, 64, 1000, 4096, 16384):
         s, mods, w, Ms, sigma, t = B.schur_refine_crt_info(N, limbs, K)
@@ -43,7 +44,8 @@ def test_table_matches_definition(N, limbs):
 def test_table_rejects_what_does_not_fit():
     assert B.schur_refine_crt_info(17, 4, 64)[0] == B.SR_ERR_INVALID_ARG   # M >= 2^128
     assert B.schur_refine_crt_info(0, 4, 64)[0] == B.SR_ERR_INVALID_ARG
-    assert B.schur_refine_crt_info(33, 8, 64)[0] == B.SR_ERR_INVALID_ARG
+    assert B.schur_refine_crt_info(35, 8, 64)[0] == B.SR_ERR_INVALID_ARG   # M >= 2^256
+    assert B.schur_refine_crt_info(50, 12, 64)[0] == B.SR_ERR_INVALID_ARG  # no 50th coprime modulus <= 256
     assert B.schur_refine_crt_info(8, 5, 64)[0] == B.SR_ERR_INVALID_ARG
     assert B.schur_refine_crt_info(8, 4, 0)[0] == B.SR_ERR_INVALID_ARG
 
@@ -52,3 +54,18 @@ def test_sixteen_moduli_give_56_bits_at_4096():
     # the default of the FP64 form: 56-bit operands where 7 digits hold 55
     assert B.schur_refine_crt_info(16, 4, 4096)[5] == 56
     assert B.schur_refine_crt_info(32, 8, 2048)[5] == 114
+
+
+def test_greedy_list_has_49_moduli():
+    # the greedy rule finds no 50th integer <= 256 coprime to all before it
+    assert len(_moduli(49)) == 49 and min(_moduli(49)) == 29
+    taken = _moduli(49)
+    assert all(any(gcd(m, x) > 1 for x in taken) for m in range(2, 257) if m not in taken)
+
+
+def test_forty_eight_moduli_give_triple_double_operands():
+    # the triple-double form: 48 moduli, M < 2^338, operands of t >= 159 bits
+    # (three doubles) up to K = 8192
+    s, mods, w, Ms, sigma, t = B.schur_refine_crt_info(48, 12, 4096)
+    assert s == B.SR_OK and t == 162 and prod(mods).bit_length() == 338
+    assert B.schur_refine_crt_info(48, 12, 8192)[5] >= 159

@@ -138,3 +138,41 @@ def test_batched_rejects_bad_sizes():
         assert st == B.SR_OK
     finally:
         B.schur_refine_destroy(h)
+
+
+def test_full_batched_workload_certified():
+    """The benchmarked group itself: all 1024 matrices of the batched workload in
+    one schur_refine_batched call with the bench's options. Every matrix's
+    residuals are certified in double-double on the device
+    (schur_refine_residuals, <= 1e-14 sqrt(n)); that certifier is checked against
+    the oracle's double-double residuals on 25 matrices, the largest among them."""
+    import torch
+    ns = [int(n) for n in inputs.batch_sizes(1024)]
+    nmax = max(ns)
+    s, h = B.schur_refine_create(nmax, B.default_options(hp_gemm=B.SR_HP_OZAKI_BF16, lp=B.SR_LP_FP32,
+                                                         batch_streams=8), None)
+    assert s == B.SR_OK
+    try:
+        problems = [inputs.batch_problem(i, n) for i, n in enumerate(ns)]
+        As = [to_dev(p.A) for p in problems]
+        Qh = [to_dev(p.Qhat) for p in problems]
+        Qs = [torch.zeros((n, n), dtype=torch.float64, device="cuda").t() for n in ns]
+        st, iters, stats = B.schur_refine_batched(h, ns, As, Qs, Qh)
+        torch.cuda.synchronize()
+        assert st == B.SR_OK and all(x == B.SR_OK for x in stats)
+        assert all(2 <= k <= 4 for k in iters)
+        lib = []
+        for n, A, Q in zip(ns, As, Qs):
+            rs, rT, rQ = B.schur_refine_residuals(h, n, A, Q)
+            assert rs == B.SR_OK
+            tol = oracle.default_tol(n)
+            assert rT <= tol and rQ <= tol, (n, rT, rQ)
+            lib.append((rT, rQ))
+        order = np.argsort(ns)
+        sample = sorted(set(order[-4:].tolist() + list(range(0, 1024, 51))))
+        for i in sample:
+            cT, cQ = oracle.residuals_dd(problems[i].A, from_dev(Qs[i]))
+            assert cT <= oracle.default_tol(ns[i]) and cQ <= oracle.default_tol(ns[i])
+            assert lib[i][0] == pytest.approx(cT, rel=1e-6) and lib[i][1] == pytest.approx(cQ, rel=1e-6)
+    finally:
+        B.schur_refine_destroy(h)
