@@ -753,7 +753,8 @@ ozaki_digits_dd_kernel(int R, int K, int Kp, const double *__restrict__ Xh, cons
 struct CrtSplitSm {
     int m[kCrtMaxModuli];
     unsigned long long inv40[kCrtMaxModuli];
-    unsigned pw16[8][kCrtMaxModuli];
+    unsigned off28[kCrtMaxModuli];
+    unsigned pw16[12][kCrtMaxModuli];
 };
 
 __device__ __forceinline__ void crt_split_table(CrtSplitSm &sm, const CrtTable *__restrict__ tab, int N, int pieces)
@@ -761,6 +762,7 @@ __device__ __forceinline__ void crt_split_table(CrtSplitSm &sm, const CrtTable *
     for (int x = threadIdx.x; x < N; x += blockDim.x) {
         sm.m[x] = tab->m[x];
         sm.inv40[x] = tab->inv40[x];
+        sm.off28[x] = tab->off28[x];
         for (int k = 0; k < pieces; ++k) sm.pw16[k][x] = tab->pw16[k][x];
     }
 }
@@ -1033,25 +1035,28 @@ __device__ __forceinline__ void td_fixed_add(double x, int t, int e, u64 (&X)[3]
     }
 }
 
-// The residues of triple-double operands modulo the NM moduli (NM fixed at
-// compile time, so that every modulus is an immediate). The fixed-point
+// The residues of triple-double operands modulo the NM moduli. The fixed-point
 // integer is cut into 11 pieces of 16 bits, the top one signed (bits 160-175;
 // t <= 174 keeps the integer inside them); for modulus m,
-// v = off + sum_k u_k (2^(16 k) mod m) is non-negative and below 2^31
-// (off = m (floor(2^24 / m) + 1) lifts the most negative top term), and
-// v mod m is the residue, taken in the symmetric range. Each thread turns 4
-// consecutive entries of one vector into residues and stores the 4 bf16
-// values of a modulus at once (the layout of ozaki_residues_fast_kernel).
-template <int LAYOUT, int NM>
+// v = off + sum_k u_k (2^(16 k) mod m) lies in [0, 2^31) (off = m ceil(2^28 / m)
+// lifts the most negative top term; the positive pieces add below 1.8e8), and
+// v - floor(v / m) m, with the quotient from ceil(2^40 / m), is the residue,
+// taken in the symmetric range. The moduli, their reciprocals and the powers
+// come from the table, staged in shared memory (read as broadcasts). Each
+// thread turns 4 consecutive entries of one vector into residues and stores
+// the 4 bf16 values of a modulus at once (the layout of
+// ozaki_residues_fast_kernel).
+template <int LAYOUT>
 __global__ void __launch_bounds__(256)
 ozaki_residues_td_kernel(int R, int K, int Kp, const double *__restrict__ X0, const double *__restrict__ X1,
-                         const double *__restrict__ X2, int ld, int t, int Pmax, int Kmax,
+                         const double *__restrict__ X2, int ld, int t, int N, int Pmax, int Kmax,
                          const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
-                         int *__restrict__ exps)
+                         int *__restrict__ exps, const CrtTable *__restrict__ tab)
 {
     constexpr int P = 11;
     __shared__ double tw[3][32][33];
     __shared__ int sexp[32];
+    __shared__ CrtSplitSm sm;
     const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * RES_KT;
     if (threadIdx.x < 32) {
         const int r = r0 + threadIdx.x;
@@ -1059,6 +1064,7 @@ ozaki_residues_td_kernel(int R, int K, int Kp, const double *__restrict__ X0, co
         sexp[threadIdx.x] = e;
         if (blockIdx.y == 0) exps[r] = e;
     }
+    crt_split_table(sm, tab, N, P);
     const int v = threadIdx.x >> 3, g = threadIdx.x & 7;
     const size_t pstride = (size_t)Pmax * Kmax;
     for (int k0 = kbeg; k0 < kbeg + RES_KT && k0 < Kp; k0 += 32) {
@@ -1086,17 +1092,21 @@ ozaki_residues_td_kernel(int R, int K, int Kp, const double *__restrict__ X0, co
             u[x][P - 1] = (int32_t)(int16_t)((X[2] >> 32) & 0xffffull);   // bits 160-175, signed
         }
         __nv_bfloat16 *o = out + (size_t)r * Kmax + (size_t)kk;
+#pragma unroll 2
+        for (int l = 0; l < N; ++l) {
+            const int m = sm.m[l];
+            const unsigned long long inv = sm.inv40[l];
+            int32_t pw[P];
 #pragma unroll
-        for (int l = 0; l < NM; ++l) {
-            constexpr int kOffUnit = 1 << 24;
-            const int m = crt_mod(l);
+            for (int k = 0; k < P; ++k) pw[k] = (int32_t)sm.pw16[k][l];
             float f[4];
 #pragma unroll
             for (int x = 0; x < 4; ++x) {
-                int32_t s = m * (kOffUnit / m + 1);
+                int32_t s = (int32_t)sm.off28[l];
 #pragma unroll
-                for (int k = 0; k < P; ++k) s += u[x][k] * (int32_t)crt_pw16(k, l);
-                int32_t rr = (int32_t)((uint32_t)s % (uint32_t)m);
+                for (int k = 0; k < P; ++k) s += u[x][k] * pw[k];
+                const uint32_t q = (uint32_t)(((unsigned long long)(uint32_t)s * inv) >> 40);
+                int32_t rr = s - (int32_t)q * m;
                 if (2 * rr > m) rr -= m;
                 f[x] = (float)rr;
             }
@@ -1291,7 +1301,7 @@ bool crt_build_table(int N, int L, CrtTable &t)
         t.inv40[l] = ((1ull << 40) + m - 1) / m;
         t.off28[l] = m * (((1u << 28) + m - 1) / m);
         unsigned long long pw = 1;
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < 12; ++k) {
             t.pw16[k][l] = (unsigned)(pw % m);
             pw = (pw % m) * 65536ull;
         }
@@ -1491,12 +1501,12 @@ sr_status ozaki_split_td(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int
     const dim3 gres(Rp / 32, (Kp + RES_KT - 1) / RES_KT);
     if (layout == OZ_COLS) {
         ozaki_absmax_kernel<double, OZ_COLS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, X0, ld, w.vmax);
-        ozaki_residues_td_kernel<OZ_COLS, kCrtDefaultModuliTD><<<gres, 256, 0, st>>>(
-            R, K, Kp, X0, X1, X2, ld, sl.t, w.Pmax, w.Kmax, w.vmax, out, sl.exps);
+        ozaki_residues_td_kernel<OZ_COLS><<<gres, 256, 0, st>>>(R, K, Kp, X0, X1, X2, ld, sl.t, s, w.Pmax, w.Kmax,
+                                                               w.vmax, out, sl.exps, w.crt_dev);
     } else {
         ozaki_absmax_kernel<double, OZ_ROWS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, X0, ld, w.vmax);
-        ozaki_residues_td_kernel<OZ_ROWS, kCrtDefaultModuliTD><<<gres, 256, 0, st>>>(
-            R, K, Kp, X0, X1, X2, ld, sl.t, w.Pmax, w.Kmax, w.vmax, out, sl.exps);
+        ozaki_residues_td_kernel<OZ_ROWS><<<gres, 256, 0, st>>>(R, K, Kp, X0, X1, X2, ld, sl.t, s, w.Pmax, w.Kmax,
+                                                               w.vmax, out, sl.exps, w.crt_dev);
     }
     SR_CUDA_TRY(cudaGetLastError());
     return SR_OK;

@@ -123,7 +123,7 @@ struct CrtTable {
     int m[kCrtMaxModuli];                        // the moduli, pairwise coprime, <= 256
     unsigned long long inv40[kCrtMaxModuli];     // ceil(2^40 / m): v / m = (v inv40) >> 40 for v < 2^31
     unsigned off28[kCrtMaxModuli];               // m ceil(2^28 / m): makes |v| < 2^28 non-negative mod m
-    unsigned pw16[8][kCrtMaxModuli];             // 2^(16 k) mod m
+    unsigned pw16[12][kCrtMaxModuli];            // 2^(16 k) mod m
     unsigned w[kCrtMaxModuli][kCrtMaxLimbs];     // CRT weights w_l < M, times 2^sigma, little-endian limbs
     unsigned M[kCrtMaxLimbs];                    // M 2^sigma (top bit at 32 L - 1)
     unsigned halfM[kCrtMaxLimbs];                // M 2^(sigma - 1)
