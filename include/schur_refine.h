@@ -187,8 +187,11 @@ typedef struct {
                          residual are the entries below the diagonal blocks,
                          L is strictly block-lower, and each block equation
                          T_II X - X T_JJ = -C is solved through its Kronecker
-                         matrix (at most 4 x 4). Real data, FP64 target, the
-                         stepwise solve, graph = 0, symmetric = 0; with every
+                         matrix (at most 4 x 4). Real data, FP64 target,
+                         graph = 0, symmetric = 0. The solve is the stepwise
+                         form unless solve_mode = 1 selects the dataflow form
+                         (both in a padded order in which no 2 x 2 block
+                         crosses a 32-row tile); with every
                          block 1 x 1 the iteration is the triangular one.
                          schur_refine_residuals and schur_refine_trisolve of
                          such a handle use the blocks too. 0 (default): the

@@ -213,7 +213,8 @@ sr_status ensure_capacity(BatchWork *bw, long long elems, int rows, int count, l
     if (!bw->flow_ctas) {
         // the group form of the dataflow solve is launched from this file
         using K = void (*)(int, float *, int, const double *, const double *, int *, int *,
-                           const unsigned long long *, int, float *, int, double, const sr::SolveMat *);
+                           const unsigned long long *, int, float *, int, double, const sr::SolveMat *,
+                           const int *);
         const K kern = sr::trisolve_flow_kernel<float, true>;
         const size_t sm = sr::FlowShape<float>::smem;
         int per_sm = 0, sms = 0;

@@ -161,76 +161,6 @@ __global__ void quasi_unpad_kernel(int n, const int *__restrict__ pos, const int
     }
 }
 
-// rounded operations without contraction: the elimination below takes the
-// oracle's steps one by one, so a zero pivot is found exactly where it finds one
-__device__ __forceinline__ float q_mul(float x, float y) { return __fmul_rn(x, y); }
-__device__ __forceinline__ double q_mul(double x, double y) { return __dmul_rn(x, y); }
-__device__ __forceinline__ float q_sub(float x, float y) { return __fsub_rn(x, y); }
-__device__ __forceinline__ double q_sub(double x, double y) { return __dsub_rn(x, y); }
-__device__ __forceinline__ float q_div(float x, float y) { return __fdiv_rn(x, y); }
-__device__ __forceinline__ double q_div(double x, double y) { return __ddiv_rn(x, y); }
-
-// Row u of the inverse of a Kronecker matrix of order m <= 4 (padded to 4 x 4
-// with the identity): Gaussian elimination with partial pivoting (the first
-// largest pivot; the padding rows are never chosen while a real row has a
-// nonzero in the column), applied to the identity alongside, then back
-// substitution. Fully unrolled, in registers. Returns false on a zero pivot
-// (a shared eigenvalue).
-template <typename T>
-__device__ __forceinline__ bool kron_inverse_row(T (&M)[4][4], int u, T (&row)[4])
-{
-    const T Z = (T)0, One = (T)1;
-    T R[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) R[r][c] = r == c ? One : Z;
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        int p = k;
-#pragma unroll
-        for (int r = k + 1; r < 4; ++r)
-            if (fabs(M[r][k]) > fabs(M[p][k])) p = r;
-#pragma unroll
-        for (int r = k + 1; r < 4; ++r) {
-            if (p == r) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const T t0 = M[k][c]; M[k][c] = M[r][c]; M[r][c] = t0;
-                    const T t1 = R[k][c]; R[k][c] = R[r][c]; R[r][c] = t1;
-                }
-            }
-        }
-        if (M[k][k] == Z) { ok = false; M[k][k] = One; }
-#pragma unroll
-        for (int r = k + 1; r < 4; ++r) {
-            const T f = q_div(M[r][k], M[k][k]);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (c >= k) M[r][c] = q_sub(M[r][c], q_mul(f, M[k][c]));
-                R[r][c] = q_sub(R[r][c], q_mul(f, R[k][c]));
-            }
-        }
-    }
-    T Xc[4][4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int r = 3; r >= 0; --r) {
-            T acc = R[r][c];
-#pragma unroll
-            for (int v = r + 1; v < 4; ++v) acc = q_sub(acc, q_mul(M[r][v], Xc[v][c]));
-            Xc[r][c] = q_div(acc, M[r][r]);
-        }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-        if (r == u)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) row[c] = Xc[r][c];
-    return ok;
-}
-
 // Solve of the tiles of subdiagonal t in the padded order (the stepwise form):
 // 1024 threads, thread (lane a, warp b) owns entry (a, b) of the tile. Phase 1
 // adds E and the two products of subdiagonal t + 1 (as trisolve_leaf_kernel).

@@ -484,6 +484,81 @@ diag_solve_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>::hp
     if (bad) atomicOr(flags, bad);
 }
 
+// ---- block entries of the real Schur form (2 x 2 diagonal blocks) ----------
+// rounded operations without contraction: the elimination below takes the
+// oracle's steps one by one, so a zero pivot is found exactly where it finds one
+__device__ __forceinline__ float q_mul(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ double q_mul(double x, double y) { return __dmul_rn(x, y); }
+__device__ __forceinline__ float q_sub(float x, float y) { return __fsub_rn(x, y); }
+__device__ __forceinline__ double q_sub(double x, double y) { return __dsub_rn(x, y); }
+__device__ __forceinline__ float q_div(float x, float y) { return __fdiv_rn(x, y); }
+__device__ __forceinline__ double q_div(double x, double y) { return __ddiv_rn(x, y); }
+
+// Row u of the inverse of a Kronecker matrix of order m <= 4 (padded to 4 x 4
+// with the identity): Gaussian elimination with partial pivoting (the first
+// largest pivot; the padding rows are never chosen while a real row has a
+// nonzero in the column), applied to the identity alongside, then back
+// substitution. Fully unrolled, in registers. Returns false on a zero pivot
+// (a shared eigenvalue).
+template <typename T>
+__device__ __forceinline__ bool kron_inverse_row(T (&M)[4][4], int u, T (&row)[4])
+{
+    const T Z = (T)0, One = (T)1;
+    T R[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) R[r][c] = r == c ? One : Z;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int p = k;
+        T best = fabs(M[k][k]);
+#pragma unroll
+        for (int r = k + 1; r < 4; ++r)
+            if (fabs(M[r][k]) > best) {
+                best = fabs(M[r][k]);
+                p = r;
+            }
+#pragma unroll
+        for (int r = k + 1; r < 4; ++r) {
+            if (p == r) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const T t0 = M[k][c]; M[k][c] = M[r][c]; M[r][c] = t0;
+                    const T t1 = R[k][c]; R[k][c] = R[r][c]; R[r][c] = t1;
+                }
+            }
+        }
+        if (M[k][k] == Z) { ok = false; M[k][k] = One; }
+#pragma unroll
+        for (int r = k + 1; r < 4; ++r) {
+            const T f = q_div(M[r][k], M[k][k]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c >= k) M[r][c] = q_sub(M[r][c], q_mul(f, M[k][c]));
+                R[r][c] = q_sub(R[r][c], q_mul(f, R[k][c]));
+            }
+        }
+    }
+    T Xc[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 3; r >= 0; --r) {
+            T acc = R[r][c];
+#pragma unroll
+            for (int v = r + 1; v < 4; ++v) acc = q_sub(acc, q_mul(M[r][v], Xc[v][c]));
+            Xc[r][c] = q_div(acc, M[r][r]);
+        }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        if (r == u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) row[c] = Xc[r][c];
+    return ok;
+}
+
 // ---- the whole solve in one launch: a dataflow over the tiles --------------
 // The same tile equations as above, solved by one persistent launch whose
 // CTAs claim tasks through a ticket counter, in the order of a task list
@@ -539,7 +614,7 @@ template <typename T> struct FlowShape {
     static constexpr int SX = B + 1;                // row stride of the solve's tiles
     static constexpr size_t kSlot = 4 * KH * SA;    // elements of one group's operands
     static constexpr size_t smem = (NG * kSlot + 3 * B * SX) * sizeof(T) + 2 * B * (sizeof(Hp) + sizeof(double))
-                                   + 16;
+                                   + 16 + 2 * B * sizeof(int);
     static_assert(NG * NTG == NT && NG % 2 == 0, "pairs of groups fill the CTA");
     static_assert(EPT * NT == B * B, "one or more whole entries per thread");
     static_assert(kSlot >= (size_t)B * SX, "a group's buffers hold its partial sums");
@@ -598,12 +673,87 @@ __device__ inline cf flow_ldcg(const cf *p)
     const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
     return {v.x, v.y};
 }
-template <typename T, bool GROUP = false>
+// The wavefront of one tile of the real Schur form in the dataflow solve, and
+// the store of its unknowns: over block entries, as in
+// trisolve_quasi_leaf_kernel. The pending sums of a block entry meet in Cs,
+// each thread forms its unknown from its row of the inverse of the block
+// entry's Kronecker matrix, and entries still pending take the products with
+// the block entries just finished (the row block starting at s in their
+// column, the column block ending at e in their row). A call of its own:
+// the block structure is read from rbq, cbq here. Returns the error flags.
+template <typename T, int EPT, int WS, int SX>
+__device__ __noinline__ int flow_quasi_tile(T *__restrict__ TE, int ld, int r0, int c0, int nr, int nc, int D,
+                                            int a, int wq, const bool *own, T *acc, const T *kinv, T (*Ti)[SX],
+                                            T (*Tj)[SX], T (*X)[SX], T (*Cs)[SX], const int *rbq, const int *cbq,
+                                            double cap)
+{
+    constexpr int B = kSolveTile;
+    const T Z = (T)0;
+    const int ra = rbq[a] == 0 ? a - 1 : a;
+    const int pq = rbq[ra] == 2 ? 2 : 1;
+    int fsq[EPT], csq[EPT], clq[EPT], mq[EPT];
+    T xv[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+        const int b = wq + WS * q;
+        csq[q] = cbq[b] == 0 ? b - 1 : b;
+        clq[q] = cbq[b] == 2 ? b + 1 : b;
+        mq[q] = pq * (cbq[csq[q]] == 2 ? 2 : 1);
+        fsq[q] = ra - clq[q];
+        xv[q] = Z;
+    }
+    const int wlo = (D > 0) ? -(B - 1) : 1;
+    __syncthreads();
+    for (int w = B - 1; w >= wlo; --w) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q)
+            if (own[q] && fsq[q] == w) Cs[a][wq + WS * q] = acc[q];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < EPT; ++q)
+            if (own[q] && fsq[q] == w) {
+                T x = Z;
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (v < mq[q]) x = sr_fma(kinv[4 * q + v], -Cs[ra + v % pq][csq[q] + v / pq], x);
+                if (cap > 0.0 && sr_over_cap(x, cap)) x = Z;   // Example 4's trick, before any use
+                X[a][wq + WS * q] = x;
+                xv[q] = x;
+            }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int b = wq + WS * q;
+            if (own[q] && fsq[q] < w) {
+                const int sr0 = w + clq[q];
+                if (sr0 >= 0 && sr0 < nr && rbq[sr0] != 0) {
+                    acc[q] = sr_fma(Ti[a][sr0], X[sr0][b], acc[q]);
+                    if (rbq[sr0] == 2) acc[q] = sr_fma(Ti[a][sr0 + 1], X[sr0 + 1][b], acc[q]);
+                }
+                const int e = ra - w;
+                if (e >= 0 && e < nc && cbq[e] != 2) {
+                    if (cbq[e] == 0) acc[q] = sr_fma(-X[a][e - 1], Tj[e - 1][b], acc[q]);
+                    acc[q] = sr_fma(-X[a][e], Tj[e][b], acc[q]);
+                }
+            }
+        }
+    }
+    int bad = 0;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q)
+        if (own[q]) {
+            if (!sr_finite(xv[q])) bad |= SR_FLAG_NONFINITE;
+            TE[sr_idx(r0 + a, c0 + wq + WS * q, ld)] = xv[q];
+        }
+    return bad;
+}
+
+template <typename T, bool GROUP = false, bool QUASI = false>
 __global__ void __launch_bounds__(FlowShape<T>::NT, 2)
 trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<T>::hp *__restrict__ dhp0,
                      const double *__restrict__ dlo, int *__restrict__ flags0, int *__restrict__ work,
                      const unsigned long long *__restrict__ plan, int ntasks, T *__restrict__ accb, int ldacc,
-                     double cap, const SolveMat *__restrict__ mats = nullptr)
+                     double cap, const SolveMat *__restrict__ mats = nullptr, const int *__restrict__ qblk = nullptr)
 {
     using S = FlowShape<T>;
     using Hp = typename SrNum<T>::hp;
@@ -619,6 +769,7 @@ trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<
     double *dIl = reinterpret_cast<double *>(dJ + B);
     double *dJl = dIl + B;
     int *s_ticket = reinterpret_cast<int *>(dJl + B);
+    int *rbq = s_ticket + 4, *cbq = rbq + B;   // real Schur form: block arrays of the tile's rows, columns
 
     const int tid = threadIdx.x;
     int *abort_w = work + 1;
@@ -749,42 +900,92 @@ trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<
             continue;
         }
 
-        // inputs that no tile writes: T_II, T_JJ, the diagonals and E_IJ
+        // inputs that no tile writes: T_II, T_JJ, the diagonals and E_IJ (the
+        // real Schur form: with the couplings of the 2 x 2 blocks in T_II, T_JJ)
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
             const int b = wq + WS * q;
-            Ti[a][b] = (a <= b && b < nr) ? TE[sr_idx(r0 + a, r0 + b, ld)] : Z;
-            Tj[a][b] = (a <= b && b < nc) ? TE[sr_idx(c0 + a, c0 + b, ld)] : Z;
+            bool ci = false, cj = false;
+            if constexpr (QUASI) {
+                ci = a == b + 1 && b < nr && qblk[r0 + b] == 2;
+                cj = a == b + 1 && b < nc && qblk[c0 + b] == 2;
+            }
+            Ti[a][b] = ((a <= b && b < nr) || ci) ? TE[sr_idx(r0 + a, r0 + b, ld)] : Z;
+            Tj[a][b] = ((a <= b && b < nc) || cj) ? TE[sr_idx(c0 + a, c0 + b, ld)] : Z;
         }
         if (tid < B) {
             dI[tid] = (tid < nr) ? dhp[r0 + tid] : hz;
             dIl[tid] = (dlo && tid < nr) ? dlo[r0 + tid] : 0.0;
+            if constexpr (QUASI) rbq[tid] = tid < nr ? qblk[r0 + tid] : 1;
         } else if (tid < 2 * B) {
             dJ[tid - B] = (tid - B < nc) ? dhp[c0 + tid - B] : hz;
             dJl[tid - B] = (dlo && tid - B < nc) ? dlo[c0 + tid - B] : 0.0;
+            if constexpr (QUASI) cbq[tid - B] = tid - B < nc ? qblk[c0 + tid - B] : 1;
         }
         bool own[EPT];
         T acc[EPT];
+        if constexpr (!QUASI) {
 #pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            const int b = wq + WS * q;
-            own[q] = a < nr && b < nc && (D > 0 || a > b);
-            acc[q] = own[q] ? TE[sr_idx(r0 + a, c0 + b, ld)] : Z;
+            for (int q = 0; q < EPT; ++q) {
+                const int b = wq + WS * q;
+                own[q] = a < nr && b < nc && (D > 0 || a > b);
+                acc[q] = own[q] ? TE[sr_idx(r0 + a, c0 + b, ld)] : Z;
+            }
         }
         __syncthreads();
-        // divisors t_aa - t_bb formed in high precision, rounded, inverted once
-        // (before the waits: they need only the diagonals)
         T rcp[EPT];
         int bad = 0;
+        // real Schur form: each entry's block entry (first row ra of its row
+        // block, columns cs..cl) and its row of the inverse of the block entry's
+        // Kronecker matrix (as the leaf kernel of the padded stepwise form); the
+        // block structure is read again from rbq, cbq where it is used
+        T kinv[EPT][4];
+        if constexpr (QUASI) {
+            const int ra = rbq[a] == 0 ? a - 1 : a;
+            const int p = rbq[ra] == 2 ? 2 : 1;
 #pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            const int b = wq + WS * q;
-            T den = own[q] ? sr_div_round<T>(dI[a], dJ[b]) : Z;
-            if constexpr (SrNum<T>::kind == 1) {
-                if (own[q] && dlo) den = sr_div_round_dd(dI[a], dIl[a], dJ[b], dJl[b]);
+            for (int q = 0; q < EPT; ++q) {
+                const int b = wq + WS * q;
+                const int cs = cbq[b] == 0 ? b - 1 : b;
+                const int m = p * (cbq[cs] == 2 ? 2 : 1);
+                own[q] = a < nr && b < nc && (D > 0 || ra > cs);
+                acc[q] = own[q] ? TE[sr_idx(r0 + a, c0 + b, ld)] : Z;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) kinv[q][v] = Z;
+                if (own[q]) {
+                    T K[4][4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int ur = u % p, uc = u / p;
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            const int vr = v % p, vc = v / p;
+                            T kv = (u == v) ? (T)1 : Z;
+                            if (u < m && v < m) {
+                                if (u == v) kv = (T)(dI[ra + ur] - dJ[cs + uc]);
+                                else if (uc == vc) kv = Ti[ra + ur][ra + vr];
+                                else if (ur == vr) kv = -Tj[cs + vc][cs + uc];
+                                else kv = Z;
+                            }
+                            K[u][v] = kv;
+                        }
+                    }
+                    if (!kron_inverse_row(K, (a - ra) + (b - cs) * p, kinv[q])) bad |= SR_FLAG_NONDISTINCT;
+                }
             }
-            if (own[q] && den == Z) bad |= SR_FLAG_NONDISTINCT;
-            rcp[q] = (own[q] && !(den == Z)) ? sr_recip(den) : Z;
+        } else {
+            // divisors t_aa - t_bb formed in high precision, rounded, inverted once
+            // (before the waits: they need only the diagonals)
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                const int b = wq + WS * q;
+                T den = own[q] ? sr_div_round<T>(dI[a], dJ[b]) : Z;
+                if constexpr (SrNum<T>::kind == 1) {
+                    if (own[q] && dlo) den = sr_div_round_dd(dI[a], dIl[a], dJ[b], dJl[b]);
+                }
+                if (own[q] && den == Z) bad |= SR_FLAG_NONDISTINCT;
+                rcp[q] = (own[q] && !(den == Z)) ? sr_recip(den) : Z;
+            }
         }
 
         // the owner's products: the subdiagonals its helpers leave (all of
@@ -809,6 +1010,12 @@ trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<
         T xv[EPT];
 #pragma unroll
         for (int q = 0; q < EPT; ++q) xv[q] = Z;
+        if constexpr (QUASI) {
+            // the block-entry wavefront and the store (flow_quasi_tile); Cs is the
+            // first group's product buffers, free once every partial sum is read
+            bad |= flow_quasi_tile<T, EPT, WS, SX>(TE, ld, r0, c0, nr, nc, D, a, wq, own, acc, &kinv[0][0], Ti, Tj,
+                                                   X, reinterpret_cast<T (*)[SX]>(ops), rbq, cbq, cap);
+        } else
         for (int w = B - 1; w >= wlo; --w) {
 #pragma unroll
             for (int q = 0; q < EPT; ++q)
@@ -830,12 +1037,14 @@ trisolve_flow_kernel(int n0, T *__restrict__ TE0, int ld0, const typename SrNum<
                 }
             }
         }
+        if constexpr (!QUASI) {
 #pragma unroll
-        for (int q = 0; q < EPT; ++q)
-            if (own[q]) {
-                if (!sr_finite(xv[q])) bad |= SR_FLAG_NONFINITE;
-                TE[sr_idx(r0 + a, c0 + wq + WS * q, ld)] = xv[q];
-            }
+            for (int q = 0; q < EPT; ++q)
+                if (own[q]) {
+                    if (!sr_finite(xv[q])) bad |= SR_FLAG_NONFINITE;
+                    TE[sr_idx(r0 + a, c0 + wq + WS * q, ld)] = xv[q];
+                }
+        }
         if (bad) atomicOr(flags, bad);
         __threadfence();
         __syncthreads();
@@ -868,13 +1077,24 @@ inline cudaError_t trisolve_flow_launch_group(cudaStream_t st, const SolveMat *m
 template <typename T>
 inline cudaError_t trisolve_flow_launch(cudaStream_t st, int n, T *TE, int ld, const typename SrNum<T>::hp *dhp,
                                         const double *dlo, int *flags, int *work, const unsigned long long *plan,
-                                        int ntasks, T *accb, int ldacc, int ctas, double cap = 0.0)
+                                        int ntasks, T *accb, int ldacc, int ctas, double cap = 0.0,
+                                        const int *qblk = nullptr)
 {
     const int NB = (n + kSolveTile - 1) / kSolveTile;
     cudaError_t e = cudaMemsetAsync(work, 0, (2 + 2 * (size_t)NB * NB) * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    trisolve_flow_kernel<T><<<(unsigned)std::max(1, std::min(ctas, ntasks)), FlowShape<T>::NT, FlowShape<T>::smem,
-                              st>>>(n, TE, ld, dhp, dlo, flags, work, plan, ntasks, accb, ldacc, cap);
+    const unsigned grid = (unsigned)std::max(1, std::min(ctas, ntasks));
+    if (qblk) {
+        // the real Schur form (padded order, block array qblk)
+        if constexpr (SrNum<T>::kind <= 1)
+            trisolve_flow_kernel<T, false, true><<<grid, FlowShape<T>::NT, FlowShape<T>::smem, st>>>(
+                n, TE, ld, dhp, dlo, flags, work, plan, ntasks, accb, ldacc, cap, nullptr, qblk);
+        else
+            return cudaErrorInvalidValue;
+    } else {
+        trisolve_flow_kernel<T><<<grid, FlowShape<T>::NT, FlowShape<T>::smem, st>>>(n, TE, ld, dhp, dlo, flags, work,
+                                                                                  plan, ntasks, accb, ldacc, cap);
+    }
     return cudaGetLastError();
 }
 
@@ -886,6 +1106,11 @@ inline int trisolve_flow_setup(int dev)
     if (cudaFuncSetAttribute(trisolve_flow_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)FlowShape<T>::smem) != cudaSuccess)
         return 0;
+    if constexpr (SrNum<T>::kind <= 1) {
+        if (cudaFuncSetAttribute(trisolve_flow_kernel<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FlowShape<T>::smem) != cudaSuccess)
+            return 0;
+    }
 
     int per_sm = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trisolve_flow_kernel<T>, FlowShape<T>::NT,

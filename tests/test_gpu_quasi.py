@@ -73,9 +73,12 @@ def _problem(n, blk, seed):
     return T, E
 
 
-def _gpu_solve(n, T, E, lp):
+SOLVE_MODES = [1, 2]   # the dataflow form (one launch), the stepwise form
+
+
+def _gpu_solve(n, T, E, lp, solve_mode=0):
     dt = np.float32 if lp == B.SR_LP_FP32 else np.float64
-    h = _handle(n, lp=lp)
+    h = _handle(n, lp=lp, solve_mode=solve_mode)
     try:
         TE = to_dev((T + E).astype(dt))
         s = B.schur_refine_trisolve(h, n, TE, to_dev(np.diagonal(T).copy()))
@@ -85,11 +88,12 @@ def _gpu_solve(n, T, E, lp):
     return s, out
 
 
+@pytest.mark.parametrize("solve_mode", SOLVE_MODES)
 @pytest.mark.parametrize("n", [2, 5, 33, 64, 100, 257])
-def test_quasi_trisolve_fp64_parity(torch, n):
+def test_quasi_trisolve_fp64_parity(torch, n, solve_mode):
     blk = _blocks(n, n)
     T, E = _problem(n, blk, 3 * n)
-    s, out = _gpu_solve(n, T, E, B.SR_LP_FP64)
+    s, out = _gpu_solve(n, T, E, B.SR_LP_FP64, solve_mode)
     assert s == B.SR_OK, B.status_string(s)
     mask = oracle.block_lower_mask(blk)
     L = np.where(mask, out, 0.0)
@@ -100,11 +104,12 @@ def test_quasi_trisolve_fp64_parity(torch, n):
     assert np.max(np.abs(L - ref)) <= 1e3 * U64 * scale
 
 
-@pytest.mark.parametrize("n", [33, 100, 257, 700])
-def test_quasi_trisolve_fp32_parity(torch, n):
+@pytest.mark.parametrize("solve_mode", SOLVE_MODES)
+@pytest.mark.parametrize("n", [33, 100, 257, 700, 1500])
+def test_quasi_trisolve_fp32_parity(torch, n, solve_mode):
     blk = _blocks(n, n + 1)
     T, E = _problem(n, blk, 5 * n)
-    s, out = _gpu_solve(n, T, E, B.SR_LP_FP32)
+    s, out = _gpu_solve(n, T, E, B.SR_LP_FP32, solve_mode)
     assert s == B.SR_OK, B.status_string(s)
     mask = oracle.block_lower_mask(blk)
     L32 = np.where(mask, out.astype(np.float64), 0.0)
@@ -116,14 +121,15 @@ def test_quasi_trisolve_fp32_parity(torch, n):
     assert e_gpu <= 20 * max(e_orc, U32 * np.linalg.norm(L64))
 
 
-def test_quasi_trisolve_shared_pair_is_nondistinct(torch):
+@pytest.mark.parametrize("solve_mode", SOLVE_MODES)
+def test_quasi_trisolve_shared_pair_is_nondistinct(torch, solve_mode):
     n = 40
     blk = np.ones(n, dtype=np.int32)
     for k in (4, 20):
         blk[k], blk[k + 1] = 2, 0
     T, E = _problem(n, blk, 9)
     T[20:22, 20:22] = T[4:6, 4:6]           # the same complex pair twice
-    s, _ = _gpu_solve(n, T, E, B.SR_LP_FP64)
+    s, _ = _gpu_solve(n, T, E, B.SR_LP_FP64, solve_mode)
     assert s == B.SR_ERR_NONDISTINCT
 
 
@@ -143,11 +149,11 @@ def _refine(p, hp, **kw):
         B.schur_refine_destroy(h)
 
 
-@pytest.mark.parametrize("hp", [B.SR_HP_OZAKI_CRT, B.SR_HP_FP64])
+@pytest.mark.parametrize("hp,solve_mode", [(B.SR_HP_OZAKI_CRT, 1), (B.SR_HP_OZAKI_CRT, 2), (B.SR_HP_FP64, 0)])
 @pytest.mark.parametrize("n", [64, 300])
-def test_quasi_refinement_matches_oracle(torch, n, hp):
+def test_quasi_refinement_matches_oracle(torch, n, hp, solve_mode):
     p = inputs.quasi_real(n)
-    st, nr, Q, T, (rT, rQ) = _refine(p, hp)
+    st, nr, Q, T, (rT, rQ) = _refine(p, hp, solve_mode=solve_mode)
     ref = oracle.refine(p.A, p.Qhat, lp="f32", quasi=True)
     assert ref.status == oracle.OK
     assert st == B.SR_OK, B.status_string(st)
@@ -167,6 +173,20 @@ def test_quasi_refinement_matches_oracle(torch, n, hp):
         elif blk[k] == 1:
             ev[k] = T[k, k]
     assert np.max(np.abs(ev - p.lam)) <= 1e-12
+
+
+def test_quasi_solve_forms_agree(torch):
+    # both launch forms solve the same block equations on a ragged order of many
+    # tiles: they agree to the working precision's rounding
+    n = 1000
+    blk = _blocks(n, 17)
+    T, E = _problem(n, blk, 19)
+    outs = []
+    for mode in SOLVE_MODES:
+        s, out = _gpu_solve(n, T, E, B.SR_LP_FP32, mode)
+        assert s == B.SR_OK
+        outs.append(np.where(oracle.block_lower_mask(blk), out.astype(np.float64), 0.0))
+    assert np.linalg.norm(outs[0] - outs[1]) <= 100 * U32 * np.linalg.norm(outs[1])
 
 
 def test_quasi_workload_n1000(torch):
