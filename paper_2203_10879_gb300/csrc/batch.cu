@@ -139,6 +139,7 @@ struct BatchWork {
     double *Q0 = nullptr, *Q1 = nullptr, *AQ = nullptr, *Y = nullptr, *Delta = nullptr, *W = nullptr,
            *W2 = nullptr, *YW = nullptr, *diag = nullptr;
     float *TE = nullptr;
+    float *acc = nullptr;      // stepwise group solve: far products' sums, apart from E (as TE)
     double *partial = nullptr;
     size_t npartial = 0;
     double *norms = nullptr;   // [count][kNorms]
@@ -164,6 +165,7 @@ void sr_batch_free(BatchWork *bw)
                       bw->norms};
     for (double *p : bufs) cudaFree(p);
     cudaFree(bw->TE);
+    cudaFree(bw->acc);
     cudaFree(bw->flags);
     cudaFree(bw->flow);
     cudaFree(bw->ddesc);
@@ -231,6 +233,7 @@ sr_status ensure_capacity(BatchWork *bw, long long elems, int rows, int count, l
         double **bufs[] = {&bw->Q0, &bw->Q1, &bw->AQ, &bw->Y, &bw->Delta, &bw->W, &bw->W2, &bw->YW};
         for (double **p : bufs) { cudaFree(*p); *p = nullptr; }
         cudaFree(bw->TE); bw->TE = nullptr;
+        cudaFree(bw->acc); bw->acc = nullptr;
         cudaFree(bw->diag); bw->diag = nullptr;
         cudaFree(bw->norms); bw->norms = nullptr;
         cudaFree(bw->flags); bw->flags = nullptr;
@@ -242,6 +245,7 @@ sr_status ensure_capacity(BatchWork *bw, long long elems, int rows, int count, l
         for (double **p : bufs)
             if (e == cudaSuccess) e = cudaMalloc((void **)p, (size_t)E * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc((void **)&bw->TE, (size_t)E * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&bw->acc, (size_t)E * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc((void **)&bw->diag, (size_t)R * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc((void **)&bw->norms, (size_t)C * kNorms * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc((void **)&bw->flags, (size_t)C * sizeof(int));
@@ -594,7 +598,7 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
                 const int b = act[a], nb = n[b];
                 const long long o = off[b];
                 double *Qc = Qbuf[cur[b]] + o, *Qo = Qbuf[cur[b] ^ 1] + o;
-                sm[b] = SolveMat{bw->TE + o, nb, nb, bw->diag + row0[b], fwords - 2};
+                sm[b] = SolveMat{bw->TE + o, nb, nb, bw->diag + row0[b], fwords - 2, bw->acc + o};
                 fwords += (long long)((nb + 31) / 32) * ((nb + 31) / 32);
                 orders[b] = nb;
                 ga[a] = GMat{o, nb, nb, nullptr, nullptr};
@@ -643,11 +647,14 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
                                                                   (size_t)fwords,
                                                                   (const unsigned long long *)P(o_fp),
                                                                   (int)fplan.size(), bw->flow_ctas, h->opt.l_cap));
-                else
+                else {
+                    // the matrices' accumulators start at zero (offsets below the capacity)
+                    SR_CUDA_TRY(cudaMemsetAsync(bw->acc, 0, (size_t)bw->cap_elems * sizeof(float), st));
                     SR_CUDA_TRY(trisolve_launches_group<float>(st, bw->aux, bw->ev0, bw->ev1,
                                                                (const SolveMat *)P(o_sm), bw->flags,
                                                                (const unsigned long long *)P(o_pl), poffs, nleaf,
                                                                h->opt.l_cap));
+                }
             }
             // S5: Y = Q^T Q - I from Q's column digits (still in slot OZS_COLS), W = L - L^T
             SR_TRY(product(OZS_COLS, OZS_COLS, o_sh, sym_hp, kHp));

@@ -72,6 +72,7 @@ struct schur_refine_ctx {
     int *qblk = nullptr, *hblk = nullptr;
     int nqmax = 0;
     void *TEq = nullptr, *qcpl = nullptr;   // qcpl: couplings of the 2 x 2 blocks, padded order
+    void *step_acc = nullptr;               // stepwise solve: far products' sums, apart from E
     double *dhpq = nullptr;
     int *qpos = nullptr, *qinv = nullptr, *qblkq = nullptr, *hmaps = nullptr;
     // profiling

@@ -421,7 +421,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
     if (h->capturing) {
         // inside the refinement's own graph: the launches themselves are captured
         SR_CUDA_TRY(sr::trisolve_launches<Tl>(h->st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp, dlo, h->dflags,
-                                              h->plan, h->plan_off, h->opt.l_cap));
+                                              h->plan, h->plan_off, h->opt.l_cap, (Tl *)h->step_acc, h->nmax));
         return SR_OK;
     }
     for (auto &g : h->graphs)
@@ -431,7 +431,8 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
         cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaError_t el = sr::trisolve_launches<Tl>(h->cap_st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp, dlo,
-                                                       h->dflags, h->plan, h->plan_off, h->opt.l_cap);
+                                                       h->dflags, h->plan, h->plan_off, h->opt.l_cap,
+                                                       (Tl *)h->step_acc, h->nmax);
             e = cudaStreamEndCapture(h->cap_st, &graph);
             if (el != cudaSuccess) e = el;
         }
@@ -452,7 +453,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
         SR_CUDA_TRY(cudaGraphLaunch(exec, h->st));
     } else {
         SR_CUDA_TRY(sr::trisolve_launches<Tl>(h->st, h->aux_st, h->sev0, h->sev1, n, TE, ld, dhp, dlo, h->dflags,
-                                              h->plan, h->plan_off, h->opt.l_cap));
+                                              h->plan, h->plan_off, h->opt.l_cap, (Tl *)h->step_acc, h->nmax));
     }
     return SR_OK;
 }
@@ -1702,6 +1703,7 @@ void schur_refine_destroy(schur_refine_t h)
     cudaFree(h->qinv);
     cudaFree(h->qblkq);
     cudaFree(h->qcpl);
+    cudaFree(h->step_acc);
     if (h->hblk) cudaFreeHost(h->hblk);
     if (h->hmaps) cudaFreeHost(h->hmaps);
     sr::ozaki_free(h->oz);
@@ -1756,6 +1758,8 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     // the dataflow solve's helper accumulators (leading dimension nsolve), where that form can serve
     if ((o.dtype == SR_REAL && o.lp == SR_LP_FP32 && o.solve_mode == 0) || o.solve_mode == 1)
         SR_ALLOC(h->flow_acc, nsolve * nsolve * lps);
+    // the stepwise solve's sums of far products, kept apart from E (leading dimension n_max)
+    if (!o.quasi) SR_ALLOC(h->step_acc, nn * lps);
     if (o.quasi) {
         const size_t nq = (size_t)h->nqmax;
         SR_ALLOC(h->band, 3 * (size_t)n_max * sizeof(double));

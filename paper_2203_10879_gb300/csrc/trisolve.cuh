@@ -82,7 +82,8 @@ struct SolveMat {
     void *TE;
     int ld, n;
     const void *dhp;
-    long long fbase;   // dataflow solve: first published word of this matrix
+    long long fbase;       // dataflow solve: first published word of this matrix
+    void *acc = nullptr;   // stepwise solve: far products' sums apart from E (ld as TE), or none
 };
 
 // Group plan: for every step t (from the largest order's last subdiagonal
@@ -207,7 +208,8 @@ template <typename T, bool GROUP = false>
 __global__ void __launch_bounds__(UpdShape<T>::NT)
 trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t *__restrict__ plan,
                        const SolveMat *__restrict__ mats = nullptr,
-                       const unsigned long long *__restrict__ gplan = nullptr)
+                       const unsigned long long *__restrict__ gplan = nullptr, T *__restrict__ accb = nullptr,
+                       int ldacc = 0)
 {
     constexpr int B = kSolveTile, SA = B + 4, SB = B + 4;
     uint32_t tile;
@@ -217,6 +219,8 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
         TE = (T *)m.TE;
         ld = m.ld;
         n = m.n;
+        accb = (T *)m.acc;
+        ldacc = m.ld;
         tile = (uint32_t)g;
     } else {
         tile = plan[blockIdx.x];
@@ -250,7 +254,10 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             const int x = 4 * tx + i, y = TN * ty + j;
-            acc[i][j] = (x < nr && y < nc && (D > 0 || x > y)) ? TE[sr_idx(r0 + x, c0 + y, ld)] : Z;
+            // with an accumulator the products sum apart from E, else into E in place
+            acc[i][j] = (x < nr && y < nc && (D > 0 || x > y))
+                            ? (accb ? accb[sr_idx(r0 + x, c0 + y, ldacc)] : TE[sr_idx(r0 + x, c0 + y, ld)])
+                            : Z;
         }
     __syncthreads();
     tile_pair_products<T, TN, SA>(Ta, Tb, tx, ty, hasP, hasM, acc);
@@ -259,7 +266,10 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             const int x = 4 * tx + i, y = TN * ty + j;
-            if (x < nr && y < nc && (D > 0 || x > y)) TE[sr_idx(r0 + x, c0 + y, ld)] = acc[i][j];
+            if (x < nr && y < nc && (D > 0 || x > y)) {
+                if (accb) accb[sr_idx(r0 + x, c0 + y, ldacc)] = acc[i][j];
+                else TE[sr_idx(r0 + x, c0 + y, ld)] = acc[i][j];
+            }
         }
 }
 
@@ -271,7 +281,8 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
                      const double *__restrict__ dlo, int t, const uint32_t *__restrict__ plan, int *__restrict__ flags,
                      double cap,
                      const SolveMat *__restrict__ mats = nullptr,
-                     const unsigned long long *__restrict__ gplan = nullptr)
+                     const unsigned long long *__restrict__ gplan = nullptr, T *__restrict__ accb = nullptr,
+                     int ldacc = 0)
 {
     using Hp = typename SrNum<T>::hp;
     constexpr int B = kSolveTile, S = B + 1;
@@ -284,6 +295,8 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
         TE = (T *)m.TE;
         ld = m.ld;
         n = m.n;
+        accb = (T *)m.acc;
+        ldacc = m.ld;
         dhp = (const Hp *)m.dhp;
         flags += (g >> 32);
         tile = (uint32_t)g;
@@ -315,7 +328,9 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
     Tb[0][a][b] = (hasP && kP + a < n && c0 + b < n) ? TE[sr_idx(kP + a, c0 + b, ld)] : Z;
     Ta[1][b][a] = (hasM && r0 + a < n && kM + b < n) ? TE[sr_idx(r0 + a, kM + b, ld)] : Z;
     Tb[1][a][b] = (hasM && kM + a < n && c0 + b < n) ? TE[sr_idx(kM + a, c0 + b, ld)] : Z;
+    // E; with an accumulator, the far subdiagonals' products summed apart from it
     T acc = own ? TE[sr_idx(r0 + a, c0 + b, ld)] : Z;
+    const T far = (own && accb) ? accb[sr_idx(r0 + a, c0 + b, ldacc)] : Z;
     const Hp hz = SrNum<Hp>::zero();
     if (threadIdx.x < B) {
         dI[threadIdx.x] = (threadIdx.x < nr) ? dhp[r0 + threadIdx.x] : hz;
@@ -325,7 +340,18 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
         dJl[threadIdx.x - B] = (dlo && threadIdx.x - B < nc) ? dlo[c0 + threadIdx.x - B] : 0.0;
     }
     __syncthreads();
-    if (hasP || hasM) {
+    if (accb) {
+        // the near products join the far ones, and E is added to their sum once
+        T pn = far;
+        if (hasP || hasM) {
+#pragma unroll 8
+            for (int k = 0; k < B; ++k) {
+                pn = sr_fma(Ta[0][k][a], Tb[0][k][b], pn);
+                pn = sr_fma(-Ta[1][k][a], Tb[1][k][b], pn);
+            }
+        }
+        acc = acc + pn;
+    } else if (hasP || hasM) {
 #pragma unroll 8
         for (int k = 0; k < B; ++k) {
             acc = sr_fma(Ta[0][k][a], Tb[0][k][b], acc);
@@ -382,19 +408,23 @@ template <typename T>
 inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEvent_t ev0, cudaEvent_t ev1, int n,
                                      T *TE, int ld, const typename SrNum<T>::hp *dhp, const double *dlo,
                                      int *flags, const uint32_t *plan, const std::vector<long long> &offsets,
-                                     double cap = 0.0)
+                                     double cap = 0.0, T *accb = nullptr, int ldacc = 0)
 {
     const int NB = (n + kSolveTile - 1) / kSolveTile;
-    cudaError_t e = cudaEventRecord(ev0, st);
+    // accb (optional): the far products' sums, apart from E; cleared first
+    cudaError_t e = accb ? cudaMemset2DAsync(accb, (size_t)ldacc * sizeof(T), 0, (size_t)n * sizeof(T), n, st)
+                         : cudaSuccess;
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev0, 0);
     for (int t = NB - 1; t >= 0 && e == cudaSuccess; --t) {
         const int l = NB - 1 - t;
         const long long nleaf = NB - t;
         const long long nupd = offsets[l + 1] - offsets[l] - nleaf;
         trisolve_leaf_kernel<T><<<(unsigned)nleaf, 1024, 0, st>>>(n, TE, ld, dhp, dlo, t, plan + offsets[l], flags,
-                                                                 cap);
+                                                                 cap, nullptr, nullptr, accb, ldacc);
         if (nupd > 0)
-            trisolve_update_kernel<T><<<(unsigned)nupd, UpdShape<T>::NT, 0, aux>>>(n, TE, ld, t, plan + offsets[l] + nleaf);
+            trisolve_update_kernel<T><<<(unsigned)nupd, UpdShape<T>::NT, 0, aux>>>(
+                n, TE, ld, t, plan + offsets[l] + nleaf, nullptr, nullptr, accb, ldacc);
         e = cudaGetLastError();
         // both kernels of this step finish before either of the next starts
         if (e == cudaSuccess) e = cudaEventRecord(ev0, st);

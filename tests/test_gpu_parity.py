@@ -110,10 +110,9 @@ def test_trisolve_fp32_parity(torch, n, solve_mode):
         Lo32 = oracle.alg2(np.triu(T).astype(np.float32), E.astype(np.float32), np.diagonal(T).copy())
         e_gpu = np.linalg.norm(L32 - L64)
         e_orc = np.linalg.norm(Lo32.astype(np.float64) - L64)
-        # the stepwise form carries E in the running sum of every block update
-        # (Alg. 2 adds it once, after the two sums): up to ~10x the oracle's error
-        factor = 10 if solve_mode == 1 else 20
-        assert e_gpu <= factor * max(e_orc, U32 * np.linalg.norm(L64))
+        # both forms sum each tile's block products apart from E and add E once
+        # (as Alg. 2 adds e_ij once after the two sums)
+        assert e_gpu <= 10 * max(e_orc, U32 * np.linalg.norm(L64))
     finally:
         B.schur_refine_destroy(h)
 
