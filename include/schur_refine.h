@@ -72,8 +72,14 @@ enum { SR_REAL = 0, SR_COMPLEX = 1 };
    moduli; ozaki_slices 0 or 48) and orders up to 8192. A triple-double
    matrix is three planes x0, x1, x2 (each ld * c elements after the one
    before), standing for x0 + x1 + x2 with x1 the double nearest to
-   x - x0 and x2 the double nearest to x - x0 - x1. */
-enum { SR_TARGET_FP64 = 0, SR_TARGET_DD = 1, SR_TARGET_TD = 2 };
+   x - x0 and x2 the double nearest to x - x0 - x1.
+   SR_TARGET_D6 (six doubles, about 318 bits: the 100-digit precision of
+   Sec. 3, held as 6 doubles as the paper does) is built with the same
+   options as SR_TARGET_TD; matrices are six planes x0 .. x5 in the same
+   layout, each word the double nearest to what the words before it leave.
+   Each high-precision product is four residue products of the operands'
+   halves (48 moduli each). */
+enum { SR_TARGET_FP64 = 0, SR_TARGET_DD = 1, SR_TARGET_TD = 2, SR_TARGET_D6 = 3 };
 /* engine of the high-precision products (Sec. 2.4: "hp matrix-matrix
    multiplications"; the paper uses the Ozaki scheme, Sec. 3) */
 enum {
@@ -95,7 +101,7 @@ enum { SR_QHAT_FP32 = 0, SR_QHAT_FP64 = 1 };
 
 typedef struct {
     int dtype;        /* SR_REAL or SR_COMPLEX */
-    int target;       /* SR_TARGET_FP64, SR_TARGET_DD or SR_TARGET_TD */
+    int target;       /* SR_TARGET_FP64, SR_TARGET_DD, SR_TARGET_TD or SR_TARGET_D6 */
     int hp_gemm;      /* SR_HP_FP64 or SR_HP_OZAKI_BF16 */
     int lp;           /* SR_LP_FP32 (mixed form) or SR_LP_FP64 (all-FP64 form) */
     int qhat_type;    /* SR_QHAT_FP32 or SR_QHAT_FP64 */
@@ -106,8 +112,8 @@ typedef struct {
                          high-precision products; <= 0 selects the library
                          default (7; 14 for SR_TARGET_DD); at most 7 (14).
                          SR_HP_OZAKI_CRT: the number of moduli N (default 16;
-                         32 for SR_TARGET_DD, 48 for SR_TARGET_TD; at most 16
-                         (34; 48)); the operands
+                         32 for SR_TARGET_DD, 48 for SR_TARGET_TD and
+                         SR_TARGET_D6; at most 16 (34; 48)); the operands
                          then carry t bits, the largest t with
                          K 2^(2t) < M / 2 for inner length K and M the
                          product of the moduli (t = 56 for N = 16 and
@@ -115,7 +121,7 @@ typedef struct {
     double tol;       /* stop when ||stril(T^)||_F / ||A||_F <= tol and the
                          last ||Q^H Q - I||_F <= sqrt(tol); <= 0 selects
                          1e-14 * sqrt(n) (1e-28 * n for SR_TARGET_DD, 1e-45 * n
-                         for SR_TARGET_TD) */
+                         for SR_TARGET_TD, 1e-93 * n for SR_TARGET_D6) */
     int profile;      /* 1: time every phase with CUDA events on the handle's
                          stream (see schur_refine_get_profile) */
     int batch_streams;/* schur_refine_batched with worker streams: matrices
@@ -225,7 +231,8 @@ sr_status schur_refine_create(schur_refine_t *h, int n_max, const sr_options *op
  * Runs Alg. 4 (Sec. 2.4) on one matrix of order n <= n_max.
  *   dA        device, n x n, lda: A in FP64 (interleaved complex128 when
  *             dtype is SR_COMPLEX; two planes when target is SR_TARGET_DD,
- *             three for SR_TARGET_TD, and likewise dQ and dT). Not modified.
+ *             three for SR_TARGET_TD, six for SR_TARGET_D6, and likewise dQ
+ *             and dT). Not modified.
  *   dQ        device, n x n, ldq, FP64 (complex128). In: the starting factor
  *             when dQhat is NULL. Out: the refined factor.
  *   dQhat     device, n x n with leading dimension ldq, element type
@@ -394,7 +401,8 @@ sr_status schur_refine_crt_info(int N, int limbs, long long K, int *moduli, unsi
  * SR_TARGET_DD), C accurate to about k * 1e-32 relative to |op(A)| |B|.
  * SR_TARGET_TD: three planes each; C is the exact product of the operands cut
  * to t = 162 bits per row of op(A) and column of B (K <= 4096), rounded once
- * to a triple-double.
+ * to a triple-double. SR_TARGET_D6: six planes each, m = n = k; the operands
+ * are cut to 2t - 2 = 322 bits, and C is rounded once to six doubles.
  * Sizes up to n_max in every dimension.
  */
 sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, const void *dA,

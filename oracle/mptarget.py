@@ -2,7 +2,8 @@
 
 Sec. 3 refines to working precisions held as several doubles per number (two
 for quadruple precision, six for 100 digits). This module checks the
-library's triple-double form (about 159 bits). It models the high precision
+library's triple-double form (about 159 bits, F = 256) and six-double form
+(about 318 bits, F = 512). It models the high precision
 (hp) by exact binary fixed point: an hp matrix is a numpy object array of
 Python integers X standing for X 2^-F, F = 256 fraction bits by default. Every
 hp product is the exact integer matrix product, rounded once to the grid;
@@ -192,6 +193,16 @@ def default_tol_td(n: int) -> float:
     working precision's floor: the tolerance lies inside the last gap, so the
     count of passes does not hang on the third pass's rounding."""
     return 1e-45 * n
+
+
+def default_tol_d6(n: int) -> float:
+    """The six-double target: 1e-93 n (about 500 n units of 2^-318). From a float64
+    start the passes reach about 1e-14, 1e-28, ..., 1e-84 and then the working
+    precision's floor near 1e-95: seven passes."""
+    return 1e-93 * n
+
+
+FBITS_D6 = 512   # fixed-point fraction bits for the six-double checks
 
 
 @dataclass

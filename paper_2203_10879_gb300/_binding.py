@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libschur_refine.so")
 SR_OK, SR_ERR_INVALID_ARG, SR_ERR_NONDISTINCT, SR_ERR_NONFINITE = 0, 1, 2, 3
 SR_ERR_NOT_CONVERGED, SR_ERR_TIMEOUT, SR_ERR_CUDA, SR_ERR_OOM, SR_ERR_UNSUPPORTED = 4, 5, 6, 7, 8
 SR_REAL, SR_COMPLEX = 0, 1
-SR_TARGET_FP64, SR_TARGET_DD, SR_TARGET_TD = 0, 1, 2
+SR_TARGET_FP64, SR_TARGET_DD, SR_TARGET_TD, SR_TARGET_D6 = 0, 1, 2, 3
 SR_HP_FP64, SR_HP_OZAKI_BF16, SR_HP_OZAKI_CRT = 0, 1, 2
 SR_LP_FP32, SR_LP_FP64 = 0, 1
 SR_QHAT_FP32, SR_QHAT_FP64 = 0, 1

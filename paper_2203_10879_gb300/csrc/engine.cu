@@ -171,6 +171,7 @@ size_t lp_size(const sr_options &o) { return (o.lp == SR_LP_FP32 ? sizeof(float)
 size_t hp_size(const sr_options &o)
 {
     if (o.target == SR_TARGET_TD) return 3 * sizeof(double);
+    if (o.target == SR_TARGET_D6) return sr::kD6Words * sizeof(double);
     return sizeof(double) * (is_cplx(o) || o.target == SR_TARGET_DD ? 2 : 1);
 }
 
@@ -180,7 +181,7 @@ bool is_emulated(const sr_options &o) { return o.hp_gemm == SR_HP_OZAKI_BF16 || 
 // bf16 digits (7; 14 for double-double) or residues modulo 16 (32) moduli per operand
 int oz_count(const sr_options &o)
 {
-    if (o.target == SR_TARGET_TD) return sr::kCrtDefaultModuliTD;
+    if (o.target == SR_TARGET_TD || o.target == SR_TARGET_D6) return sr::kCrtDefaultModuliTD;
     if (o.ozaki_slices > 0) return o.ozaki_slices;
     const bool dd = o.target == SR_TARGET_DD;
     if (o.hp_gemm == SR_HP_OZAKI_CRT) return dd ? sr::kCrtDefaultModuliDD : sr::kCrtDefaultModuli;
@@ -190,7 +191,9 @@ int oz_count(const sr_options &o)
 sr_status check_opts(const sr_options &o)
 {
     if (o.dtype != SR_REAL && o.dtype != SR_COMPLEX) return SR_ERR_INVALID_ARG;
-    if (o.target != SR_TARGET_FP64 && o.target != SR_TARGET_DD && o.target != SR_TARGET_TD) return SR_ERR_INVALID_ARG;
+    if (o.target != SR_TARGET_FP64 && o.target != SR_TARGET_DD && o.target != SR_TARGET_TD &&
+        o.target != SR_TARGET_D6)
+        return SR_ERR_INVALID_ARG;
     if (o.hp_gemm != SR_HP_FP64 && o.hp_gemm != SR_HP_OZAKI_BF16 && o.hp_gemm != SR_HP_OZAKI_CRT)
         return SR_ERR_INVALID_ARG;
     if (o.lp != SR_LP_FP32 && o.lp != SR_LP_FP64) return SR_ERR_INVALID_ARG;
@@ -202,11 +205,11 @@ sr_status check_opts(const sr_options &o)
     if (o.hp_gemm == SR_HP_OZAKI_CRT) {
         // FP64 results: M < 2^128 holds for at most 16 moduli; double-double
         // (M < 2^256): 34; triple-double: the 48 of its form
-        const int mx = o.target == SR_TARGET_DD   ? sr::kCrtMaxModuliDD
-                       : o.target == SR_TARGET_TD ? sr::kCrtDefaultModuliTD
-                                                  : sr::kCrtDefaultModuli;
-        if (o.ozaki_slices > mx ||
-            (o.target == SR_TARGET_TD && o.ozaki_slices > 0 && o.ozaki_slices != sr::kCrtDefaultModuliTD))
+        const bool mw = o.target == SR_TARGET_TD || o.target == SR_TARGET_D6;
+        const int mx = o.target == SR_TARGET_DD ? sr::kCrtMaxModuliDD
+                       : mw                     ? sr::kCrtDefaultModuliTD
+                                                : sr::kCrtDefaultModuli;
+        if (o.ozaki_slices > mx || (mw && o.ozaki_slices > 0 && o.ozaki_slices != sr::kCrtDefaultModuliTD))
             return SR_ERR_INVALID_ARG;
     } else if (o.ozaki_slices > (o.target == SR_TARGET_DD ? sr::kOzakiMaxSlicesDD : sr::kOzakiMaxSlices)) {
         return SR_ERR_INVALID_ARG;
@@ -214,9 +217,10 @@ sr_status check_opts(const sr_options &o)
     // double-double target: real data, FP64 correction path, FP64 start
     if (o.target == SR_TARGET_DD && (o.dtype != SR_REAL || o.lp != SR_LP_FP64 || o.qhat_type != SR_QHAT_FP64))
         return SR_ERR_UNSUPPORTED;
-    // triple-double target: the same, with the residue-form products only
-    if (o.target == SR_TARGET_TD && (o.dtype != SR_REAL || o.lp != SR_LP_FP64 || o.qhat_type != SR_QHAT_FP64 ||
-                                     o.hp_gemm != SR_HP_OZAKI_CRT || o.graph))
+    // triple- and six-double targets: the same, with the residue-form products only
+    if ((o.target == SR_TARGET_TD || o.target == SR_TARGET_D6) &&
+        (o.dtype != SR_REAL || o.lp != SR_LP_FP64 || o.qhat_type != SR_QHAT_FP64 || o.hp_gemm != SR_HP_OZAKI_CRT ||
+         o.graph))
         return SR_ERR_UNSUPPORTED;
     // complex data: the emulated products with the complex64 correction path
     if (o.dtype == SR_COMPLEX && (!is_emulated(o) || o.lp != SR_LP_FP32)) return SR_ERR_UNSUPPORTED;
@@ -1585,6 +1589,204 @@ sr_status run_step_td(schur_refine_ctx *h, int n, const void *dA, int lda, void 
     return status;
 }
 
+// ---- the six-double target (SR_TARGET_D6) ---------------------------------------------
+// Sec. 3's 100-digit runs hold each high-precision number as 6 doubles (about
+// 318 bits). The residue form carries at most 164 bits per operand with the
+// 49 pairwise coprime moduli <= 256, so each operand is held as two halves of
+// t = 162 bits (the fixed-point value of T = 2t - 2 bits, X = X_hi 2^t + X_lo),
+// and each product is four residue products (HH, HL, LH, LL) of 48 moduli,
+// rebuilt, combined exactly and rounded once to six words. The epilogues sum
+// their terms exactly; the low precision is FP64 as in the other multi-word
+// forms.
+bool is_d6(const sr_options &o) { return o.target == SR_TARGET_D6; }
+
+struct D6Mat {
+    double *x;   // plane k at x + k pl
+    size_t pl;
+    int ld;
+};
+D6Mat d6_caller(const void *p, int ld, int n) { return {(double *)p, (size_t)ld * (size_t)n, ld}; }
+D6Mat d6_work(const schur_refine_ctx *h, double *p) { return {p, (size_t)h->nmax * (size_t)h->nmax, h->nmax}; }
+D6Mat d6_none(int n) { return {nullptr, 0, n}; }
+
+sr_status d6_split(schur_refine_ctx *h, int slot_hi, int slot_lo, int n, D6Mat X, int layout)
+{
+    return sr::ozaki_split_d6(h, h->st, h->oz, slot_hi, slot_lo, n, n, X.x, X.pl, X.ld, layout);
+}
+
+// the four residue products of a six-double product into the plane sets 0..3
+sr_status d6_products(schur_refine_ctx *h, int rows_hi, int rows_lo, int cols_hi, int cols_lo, int n)
+{
+    const int s = sr::kCrtDefaultModuliTD;
+    uint8_t *base = reinterpret_cast<uint8_t *>(h->oz.planes);
+    const size_t set = (size_t)s * h->oz.Pmax * h->oz.Pmax;
+    const int rs[4] = {rows_hi, rows_hi, rows_lo, rows_lo}, cs[4] = {cols_hi, cols_lo, cols_hi, cols_lo};
+    for (int k = 0; k < 4; ++k)
+        SR_TRY(sr::ozaki_product(h, h->st, h->oz, rs[k], cs[k], n, n, n, s, false, h->dflags,
+                                 reinterpret_cast<int32_t *>(base + (size_t)k * set)));
+    return SR_OK;
+}
+
+// Y = Q^T Q - I and ||Y||^2 -> dnorm[1], from Q's column halves in OZS_COLS, OZS_COLS_LO
+sr_status d6_gram(schur_refine_ctx *h, int n)
+{
+    const D6Mat Y = d6_work(h, h->Y);
+    int blocks = 0;
+    SR_TRY(d6_products(h, sr::OZS_COLS, sr::OZS_COLS_LO, sr::OZS_COLS, sr::OZS_COLS_LO, n));
+    SR_TRY(sr::ozaki_combine_d6(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_COLS, n, n, 1.0,
+                                sr::EpMinusID6{Y.x, Y.ld, Y.pl}, h->partial, &blocks));
+    return reduce_to(h, blocks, 1);
+}
+
+// Qn = Q + alpha Q X
+sr_status d6_apply(schur_refine_ctx *h, int n, D6Mat Q, D6Mat X, D6Mat Qn, double alpha)
+{
+    SR_TRY(d6_split(h, sr::OZS_QROWS, sr::OZS_QROWS_LO, n, Q, sr::OZ_ROWS));
+    SR_TRY(d6_split(h, sr::OZS_X, sr::OZS_X_LO, n, X, sr::OZ_COLS));
+    SR_TRY(d6_products(h, sr::OZS_QROWS, sr::OZS_QROWS_LO, sr::OZS_X, sr::OZS_X_LO, n));
+    return sr::ozaki_combine_d6(h, h->st, h->oz, sr::OZS_QROWS, sr::OZS_X, n, n, 1.0,
+                                sr::EpUpdateD6{Q.x, Q.ld, Q.pl, Qn.x, Qn.ld, Qn.pl, alpha}, nullptr, nullptr);
+}
+
+// S1 + S2: A Q (A's row halves in OZS_ROWS, OZS_ROWS_LO), T^ = Q^T (A Q); ||E||^2 -> dnorm[slot]
+sr_status d6_form_residual(schur_refine_ctx *h, int n, D6Mat Q, D6Mat That, int slot)
+{
+    const D6Mat AQ = d6_work(h, h->AQ);
+    int blocks = 0;
+    SR_TRY(d6_split(h, sr::OZS_COLS, sr::OZS_COLS_LO, n, Q, sr::OZ_COLS));
+    SR_TRY(d6_products(h, sr::OZS_ROWS, sr::OZS_ROWS_LO, sr::OZS_COLS, sr::OZS_COLS_LO, n));
+    SR_TRY(sr::ozaki_combine_d6(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, n, n, 1.0,
+                                sr::EpStoreD6{AQ.x, AQ.ld, AQ.pl}, nullptr, nullptr));
+    SR_TRY(d6_split(h, sr::OZS_X, sr::OZS_X_LO, n, AQ, sr::OZ_COLS));
+    SR_TRY(d6_products(h, sr::OZS_COLS, sr::OZS_COLS_LO, sr::OZS_X, sr::OZS_X_LO, n));
+    const sr::EpSplitD6 ep{(double *)h->TE, h->nmax, h->diag, h->diag_lo, That.x, That.ld, That.pl};
+    SR_TRY(sr::ozaki_combine_d6(h, h->st, h->oz, sr::OZS_COLS, sr::OZS_X, n, n, 1.0, ep, h->partial, &blocks));
+    return reduce_to(h, blocks, slot);
+}
+
+// S5-S8 (as td_update with six words)
+sr_status d6_update(schur_refine_ctx *h, int n, D6Mat Q, D6Mat Qn)
+{
+    using namespace sr;
+    const int ld = h->nmax;
+    cudaStream_t st = h->st;
+    SR_TRY(d6_gram(h, n));   // Q's column halves are those of the residual's product
+    const D6Mat Y = d6_work(h, h->Y), Dl = d6_work(h, h->Delta);
+    double *Wd = h->Wd, *W2 = (double *)h->W2, *YW = (double *)h->YW;
+    double *W2Y = (double *)h->W2Y, *W2YW = (double *)h->W2YW;
+    {
+        SrPhase ph(h, SR_PROF_OTHER, 0, 16LL * n * n, 1);
+        dim3 grid((n + 31) / 32, (n + 31) / 32);
+        form_skew_kernel<double><<<grid, 256, 0, st>>>(n, (const double *)h->TE, ld, Wd, ld);
+        SR_CUDA_TRY(cudaGetLastError());
+    }
+    const bool full = h->opt.full_sigma != 0;
+    const EpDeltaD6 ed{(const double *)h->TE, ld, YW, W2, full ? W2Y : nullptr, full ? W2YW : nullptr, ld,
+                       Y.x, Y.ld, Y.pl, Dl.x, Dl.ld, Dl.pl};
+    const int sl = kOzakiDefaultSlices;
+    OzakiWork &w = h->oz;
+    SR_TRY(ozaki_split(h, st, w, OZS_W, n, n, Wd, ld, OZ_COLS, sl));
+    SR_TRY(ozaki_split(h, st, w, OZS_Y, n, n, Y.x, ld, OZ_COLS, sl));
+    SR_TRY(ozaki_product(h, st, w, OZS_W, OZS_W, n, n, n, sl, true, h->dflags));
+    SR_TRY(ozaki_combine(h, st, w, OZS_W, OZS_W, n, n, sl, -1.0, true, EpStore{W2, ld}, nullptr, nullptr));
+    SR_TRY(ozaki_product(h, st, w, OZS_Y, OZS_W, n, n, n, sl, false, h->dflags));
+    SR_TRY(ozaki_combine(h, st, w, OZS_Y, OZS_W, n, n, sl, 1.0, false, EpStore{YW, ld}, nullptr, nullptr));
+    SR_TRY(ozaki_split(h, st, w, OZS_W2, n, n, W2, ld, OZ_COLS, sl));
+    if (full) {
+        SR_TRY(ozaki_product(h, st, w, OZS_W2, OZS_Y, n, n, n, sl, false, h->dflags));
+        SR_TRY(ozaki_combine(h, st, w, OZS_W2, OZS_Y, n, n, sl, 1.0, false, EpStore{W2Y, ld}, nullptr, nullptr));
+        SR_TRY(ozaki_split(h, st, w, 7, n, n, W2Y, ld, OZ_ROWS, sl));
+        SR_TRY(ozaki_product(h, st, w, 7, OZS_W, n, n, n, sl, false, h->dflags));
+        SR_TRY(ozaki_combine(h, st, w, 7, OZS_W, n, n, sl, 1.0, false, EpStore{W2YW, ld}, nullptr, nullptr));
+    }
+    SR_TRY(ozaki_product(h, st, w, OZS_W, OZS_W2, n, n, n, sl, false, h->dflags));
+    SR_TRY(ozaki_combine(h, st, w, OZS_W, OZS_W2, n, n, sl, -1.0, false, ed, nullptr, nullptr));
+    return d6_apply(h, n, Q, Dl, Qn, 0.5);
+}
+
+sr_status copy_d6(schur_refine_ctx *h, int n, D6Mat src, D6Mat dst)
+{
+    if (src.x == dst.x) return SR_OK;
+    SrPhase ph(h, SR_PROF_OTHER, 0, 96LL * n * n, sr::kD6Words);
+    for (int k = 0; k < sr::kD6Words; ++k)
+        SR_CUDA_TRY(cudaMemcpy2DAsync(dst.x + k * dst.pl, (size_t)dst.ld * 8, src.x + k * src.pl, (size_t)src.ld * 8,
+                                      (size_t)n * 8, n, cudaMemcpyDeviceToDevice, h->st));
+    return SR_OK;
+}
+
+// One call of Alg. 4 with the six-double target.
+sr_status run_step_d6(schur_refine_ctx *h, int n, const void *dA, int lda, void *dQ, int ldq, const void *dQhat,
+                      void *dT, sr_norms *out)
+{
+    const int ld = h->nmax;
+    const double tol = h->opt.tol > 0 ? h->opt.tol : 1e-93 * (double)n;
+    const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 10;
+    sr_norms nr{};
+    nr.stril_rel = nr.orth = nr.w_norm = NAN;
+    const D6Mat A = d6_caller(dA, lda, n), Qcaller = d6_caller(dQ, ldq, n);
+    const D6Mat That = dT ? d6_caller(dT, n, n) : d6_none(n);
+    SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
+    SR_TRY(sumsq<double>(h, n, A.x, lda, 0, 3));
+    SR_TRY(d6_split(h, sr::OZS_ROWS, sr::OZS_ROWS_LO, n, A, sr::OZ_ROWS));
+    D6Mat Qc = Qcaller, Qo = d6_work(h, h->Qw);
+    double y_last = NAN;
+    if (dQhat) {
+        // Alg. 4: Qhat (FP64) as a six-double, then Q <- Q - 1/2 Q (Q^T Q - I) (eq. NS)
+        {
+            SrPhase ph(h, SR_PROF_OTHER, 0, 56LL * n * n, sr::kD6Words);
+            SR_CUDA_TRY(cudaMemcpy2DAsync(Qc.x, (size_t)Qc.ld * 8, dQhat, (size_t)ldq * 8, (size_t)n * 8, n,
+                                          cudaMemcpyDeviceToDevice, h->st));
+            for (int k = 1; k < sr::kD6Words; ++k)
+                SR_CUDA_TRY(cudaMemset2DAsync(Qc.x + k * Qc.pl, (size_t)Qc.ld * 8, 0, (size_t)n * 8, n, h->st));
+        }
+        SR_TRY(d6_split(h, sr::OZS_COLS, sr::OZS_COLS_LO, n, Qc, sr::OZ_COLS));
+        SR_TRY(d6_gram(h, n));
+        SR_TRY(d6_apply(h, n, Qc, d6_work(h, h->Y), Qo, -0.5));
+        std::swap(Qc, Qo);
+        nr.hp_gemms += 2;
+        SR_TRY(read_back(h));
+        y_last = sqrt(h->hbuf[1]);
+        nr.orth = y_last;
+    }
+    const double anorm = sqrt(h->hbuf[3] > 0 ? h->hbuf[3] : 1.0);
+    sr_status status = SR_ERR_NOT_CONVERGED;
+    double prev = INFINITY;
+    for (int k = 1; k <= max_iter; ++k) {
+        SR_TRY(d6_form_residual(h, n, Qc, That, 0));
+        nr.hp_gemms += 2;
+        nr.iters = k;
+        SR_TRY(read_back(h));
+        if (timed_out(h)) { status = SR_ERR_TIMEOUT; break; }
+        const double rT = sqrt(h->hbuf[0]) / anorm;
+        nr.stril_rel = rT;
+        if (!isfinite(rT)) { status = SR_ERR_NONFINITE; break; }
+        const bool ok_y = !(y_last > sqrt(tol));
+        if (rT <= tol && ok_y) { status = SR_OK; break; }
+        if (k >= 3 && rT > 10.0 * prev) { status = SR_ERR_NOT_CONVERGED; break; }
+        prev = rT;
+        SR_TRY(solve<double>(h, n, (double *)h->TE, ld, h->diag, h->diag_lo));
+        SR_TRY(sumsq<double>(h, n, (const double *)h->TE, ld, 1, 2));
+        SR_TRY(read_back(h));
+        const int f = host_flags(h);
+        if (f & SR_FLAG_TIMEOUT) { status = SR_ERR_TIMEOUT; break; }
+        if (f & SR_FLAG_NONDISTINCT) { status = SR_ERR_NONDISTINCT; break; }
+        if (f & SR_FLAG_NONFINITE) { status = SR_ERR_NONFINITE; break; }
+        nr.w_norm = sqrt(2.0 * h->hbuf[2]);
+        SR_TRY(d6_update(h, n, Qc, Qo));
+        nr.hp_gemms += 2;
+        std::swap(Qc, Qo);
+        SR_TRY(read_back(h));
+        y_last = sqrt(h->hbuf[1]);
+        nr.orth = y_last;
+        status = SR_ERR_NOT_CONVERGED;
+    }
+    SR_TRY(copy_d6(h, n, Qc, Qcaller));
+    SR_CUDA_TRY(cudaStreamSynchronize(h->st));
+    harvest(h);
+    if (out) *out = nr;
+    return status;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -1788,7 +1990,8 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->sev0, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->sev1, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(h->dnorm, 0, 8 * sizeof(double));
-    const bool td = o.target == SR_TARGET_TD;
+    const bool d6 = o.target == SR_TARGET_D6;
+    const bool td = o.target == SR_TARGET_TD || d6;   // 12-limb rebuilds
     const bool dd = o.target == SR_TARGET_DD || td;   // FP64 low precision with a multi-word diagonal
     if (e == cudaSuccess) h->diag_lo = dd ? h->diag + n_max : nullptr;
     if (e == cudaSuccess && dd) e = cudaMalloc((void **)&h->Wd, nn * sizeof(double));
@@ -1817,11 +2020,18 @@ sr_status schur_refine_create(schur_refine_t *hp, int n_max, const sr_options *o
         // residue form: the four slots of the high-precision products (rows of A,
         // columns of Q, columns of A Q and of Delta, rows of Q) hold residues
         const bool crt = o.hp_gemm == SR_HP_OZAKI_CRT;
-        const unsigned crt_mask = crt ? ((1u << sr::OZS_ROWS) | (1u << sr::OZS_COLS) | (1u << sr::OZS_X) |
-                                         (1u << sr::OZS_QROWS))
-                                      : 0u;
+        unsigned crt_mask = crt ? ((1u << sr::OZS_ROWS) | (1u << sr::OZS_COLS) | (1u << sr::OZS_X) |
+                                   (1u << sr::OZS_QROWS))
+                                : 0u;
+        if (d6) {
+            // the low halves of the six-double operands
+            crt_mask |= (1u << sr::OZS_ROWS_LO) | (1u << sr::OZS_COLS_LO) | (1u << sr::OZS_X_LO) |
+                        (1u << sr::OZS_QROWS_LO);
+            caps[sr::OZS_ROWS_LO] = caps[sr::OZS_COLS_LO] = caps[sr::OZS_X_LO] = caps[sr::OZS_QROWS_LO] = shp;
+        }
         if (e == cudaSuccess)
-            e = sr::ozaki_alloc(h->oz, n_max, caps, is_cplx(o), crt ? shp : 0, crt_mask, td ? 12 : dd ? 8 : 4);
+            e = sr::ozaki_alloc(h->oz, n_max, caps, is_cplx(o), crt ? shp : 0, crt_mask, td ? 12 : dd ? 8 : 4,
+                                d6 ? 4 : 1);
         if (e == cudaSuccess) e = cudaMalloc((void **)&h->partial2, h->npartial * sizeof(double));
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->gram_st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gev0, cudaEventDisableTiming);
@@ -1844,6 +2054,7 @@ sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, vo
 {
     if (!h || !dA || !dQ || n < 1 || n > h->nmax || lda < n || ldq < n) return SR_ERR_INVALID_ARG;
     if (is_td(h->opt)) return run_step_td(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
+    if (is_d6(h->opt)) return run_step_d6(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
     if (is_dd(h->opt)) {
         if (is_emulated(h->opt)) return run_step_dd<true>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
         return run_step_dd<false>(h, n, dA, lda, dQ, ldq, dQhat, dT, out);
@@ -1953,7 +2164,16 @@ sr_status schur_refine_residuals(schur_refine_t h, int n, const void *dA, int ld
     const size_t tiles = (size_t)((n + 15) / 16) * (size_t)((n + 15) / 16);
     if (tiles > h->npartial) return SR_ERR_INVALID_ARG;
     dim3 grid((n + 15) / 16, (n + 15) / 16);
-    if (is_td(h->opt)) {
+    if (is_d6(h->opt)) {
+        // the six-double products of the iteration, each rounded once
+        const D6Mat A = d6_caller(dA, lda, n), Q = d6_caller(dQ, ldq, n);
+        SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
+        SR_TRY(d6_split(h, sr::OZS_ROWS, sr::OZS_ROWS_LO, n, A, sr::OZ_ROWS));
+        SR_TRY(d6_form_residual(h, n, Q, d6_none(n), 4));
+        SR_TRY(d6_gram(h, n));
+        SR_CUDA_TRY(cudaMemcpyAsync(h->dnorm + 5, h->dnorm + 1, sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        SR_TRY(sumsq<double>(h, n, A.x, lda, 0, 6));
+    } else if (is_td(h->opt)) {
         // the triple-double products of the iteration (residue form, 48 moduli),
         // each rounded once: T^'s entries below the diagonal carry errors near
         // 2^-159 ||A||, far below the target
@@ -2049,7 +2269,7 @@ sr_status schur_refine_trisolve(schur_refine_t h, int n, void *dTE, int ld, cons
             SR_TRY(solve_quasi<float>(h, n, (float *)dTE, ld, d));
         else
             SR_TRY(solve_quasi<double>(h, n, (double *)dTE, ld, d));
-    } else if (is_dd(h->opt) || is_td(h->opt))
+    } else if (is_dd(h->opt) || is_td(h->opt) || is_d6(h->opt))
         SR_TRY(solve<double>(h, n, (double *)dTE, ld, (const double *)dDiag, (const double *)dDiag + n));
     else if (is_cplx(h->opt))
         SR_TRY(solve<cf>(h, n, (cf *)dTE, ld, (const cd *)dDiag));
@@ -2088,7 +2308,16 @@ sr_status schur_refine_gemm(schur_refine_t h, int transA, int m, int n, int k, c
     if (m > h->nmax || n > h->nmax || k > h->nmax) return SR_ERR_INVALID_ARG;
     if (lda < (transA ? k : m) || ldb < k || ldc < m) return SR_ERR_INVALID_ARG;
     SR_CUDA_TRY(cudaMemsetAsync(h->dflags, 0, sizeof(int), h->st));
-    if (is_td(h->opt)) {
+    if (is_d6(h->opt)) {
+        if (m != n || n != k) return SR_ERR_INVALID_ARG;   // square products only
+        const D6Mat A = d6_caller(dA, lda, k), B = d6_caller(dB, ldb, n), C = d6_caller(dC, ldc, n);
+        SR_TRY(sr::ozaki_split_d6(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_ROWS_LO, m, k, A.x, A.pl, A.ld,
+                                  transA ? sr::OZ_COLS : sr::OZ_ROWS));
+        SR_TRY(d6_split(h, sr::OZS_COLS, sr::OZS_COLS_LO, n, B, sr::OZ_COLS));
+        SR_TRY(d6_products(h, sr::OZS_ROWS, sr::OZS_ROWS_LO, sr::OZS_COLS, sr::OZS_COLS_LO, n));
+        SR_TRY(sr::ozaki_combine_d6(h, h->st, h->oz, sr::OZS_ROWS, sr::OZS_COLS, m, n, 1.0,
+                                    sr::EpStoreD6{C.x, C.ld, C.pl}, nullptr, nullptr));
+    } else if (is_td(h->opt)) {
         const TdMat A = td_caller(dA, lda, transA ? m : k), B = td_caller(dB, ldb, n), C = td_caller(dC, ldc, n);
         const int s = sr::kCrtDefaultModuliTD;
         SR_TRY(sr::ozaki_split_td(h, h->st, h->oz, sr::OZS_ROWS, m, k, A.x0, A.x1, A.x2, lda,

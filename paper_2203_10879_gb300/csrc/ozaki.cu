@@ -1116,6 +1116,128 @@ ozaki_residues_td_kernel(int R, int K, int Kp, const double *__restrict__ X0, co
     }
 }
 
+// Six-double operands: x0 + ... + x5 times 2^(T - e), T = 2t - 2, each word
+// rounded to the nearest unit, summed exactly in a 384-bit two's complement
+// integer (|x| < 2^e: the sum stays below 2^(T+1) = 2^(2t-1)).
+__device__ __forceinline__ void d6_fixed_add(double x, int T, int e, u64 (&X)[6])
+{
+    const u64 bits = (u64)__double_as_longlong(x);
+    const int eb = (int)((bits >> 52) & 0x7ff);
+    u64 mant = bits & 0xfffffffffffffull;
+    int ex;
+    if (eb == 0) ex = -1074; else { mant |= 1ull << 52; ex = eb - 1075; }
+    if (mant == 0) return;
+    const int sh = ex + T - e;                     // x 2^(T-e) = mant 2^sh, sh <= T - 52 <= 270
+    u64 v[6] = {0, 0, 0, 0, 0, 0};
+    if (sh >= 0) {
+        const int q = sh >> 6, r = sh & 63;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (k == q) v[k] = mant << r;
+            if (k == q + 1 && r) v[k] = mant >> (64 - r);
+        }
+    } else if (-sh < 64) {
+        v[0] = (mant + (1ull << (-sh - 1))) >> (-sh);
+    }
+    if (bits >> 63) mw_neg<6>(v);
+    mw_add<6>(X, v);
+}
+
+// The residues of six-double operands: the fixed-point integer X of T = 2t - 2
+// bits is cut into X = X_hi 2^t + X_lo (0 <= X_lo < 2^t, |X_hi| < 2^(t-1)), and
+// each half is reduced modulo the N moduli as in ozaki_residues_td_kernel (11
+// pieces of 16 bits, the top one signed), into the slots' planes out_hi and
+// out_lo. The six planes are read one after another through one shared tile.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256)
+ozaki_residues_d6_kernel(int R, int K, int Kp, const double *__restrict__ X, size_t pl, int ld, int t, int N,
+                         int Pmax, int Kmax, const unsigned long long *__restrict__ vmax,
+                         __nv_bfloat16 *__restrict__ out_hi, __nv_bfloat16 *__restrict__ out_lo,
+                         int *__restrict__ exps_hi, int *__restrict__ exps_lo, const CrtTable *__restrict__ tab)
+{
+    constexpr int P = 11;
+    __shared__ double tw[32][33];
+    __shared__ int sexp[32];
+    __shared__ CrtSplitSm sm;
+    const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * RES_KT;
+    if (threadIdx.x < 32) {
+        const int r = r0 + threadIdx.x;
+        const int e = (r < R) ? split_exponent(vmax[r]) : 0;
+        sexp[threadIdx.x] = e;
+        if (blockIdx.y == 0) {
+            exps_hi[r] = e;
+            exps_lo[r] = e;
+        }
+    }
+    crt_split_table(sm, tab, N, P);
+    const int T = 2 * t - 2;
+    const int v = threadIdx.x >> 3, g = threadIdx.x & 7;
+    const size_t pstride = (size_t)Pmax * Kmax;
+    for (int k0 = kbeg; k0 < kbeg + RES_KT && k0 < Kp; k0 += 32) {
+        const int r = r0 + v, kk = k0 + 4 * g;
+        u64 Xf[4][6];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Xf[x][k] = 0;
+#pragma unroll 1
+        for (int wd = 0; wd < 6; ++wd) {
+            __syncthreads();
+            split_load_tile<double, LAYOUT>(tw, X + (size_t)wd * pl, ld, R, K, INT_MAX, r0, k0);
+            __syncthreads();
+            const int e = sexp[v];
+            if (e != kOzakiExpNonfinite && r < R) {
+#pragma unroll
+                for (int x = 0; x < 4; ++x) d6_fixed_add(tw[v][4 * g + x], T, e, Xf[x]);
+            }
+        }
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            int32_t u[4][P];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    if (half == 0) {
+                        // X_hi = X >> t (arithmetic): piece k is bits t + 16k .. t + 16k + 15
+                        const u64 b = mw_bits64<6>(Xf[x], t + 16 * k) & 0xffffull;
+                        u[x][k] = k == P - 1 ? (int32_t)(int16_t)b : (int32_t)b;
+                    } else {
+                        // X_lo = X mod 2^t: piece k is bits 16k .. 16k + 15 below bit t
+                        u64 b = mw_bits64<6>(Xf[x], 16 * k) & 0xffffull;
+                        const int keep = t - 16 * k;
+                        if (keep <= 0) b = 0;
+                        else if (keep < 16) b &= (1ull << keep) - 1ull;
+                        u[x][k] = (int32_t)b;
+                    }
+                }
+            }
+            __nv_bfloat16 *o = (half == 0 ? out_hi : out_lo) + (size_t)r * Kmax + (size_t)kk;
+#pragma unroll 2
+            for (int l = 0; l < N; ++l) {
+                const int m = sm.m[l];
+                const unsigned long long inv = sm.inv40[l];
+                int32_t pw[P];
+#pragma unroll
+                for (int k = 0; k < P; ++k) pw[k] = (int32_t)sm.pw16[k][l];
+                float f[4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    int32_t s = (int32_t)sm.off28[l];
+#pragma unroll
+                    for (int k = 0; k < P; ++k) s += u[x][k] * pw[k];
+                    const uint32_t q = (uint32_t)(((unsigned long long)(uint32_t)s * inv) >> 40);
+                    int32_t rr = s - (int32_t)q * m;
+                    if (2 * rr > m) rr -= m;
+                    f[x] = (float)rr;
+                }
+                *reinterpret_cast<uint2 *>(o + (size_t)l * pstride) =
+                    make_uint2(crt_pack_bf16(f[0], f[1]), crt_pack_bf16(f[2], f[3]));
+            }
+        }
+    }
+}
+
 // Splits levels 0..s-1 (level l costs l + 1 digit pairs) into G contiguous
 // non-empty groups minimising the largest group cost (linear partition by
 // dynamic programming); returns that cost.
@@ -1324,7 +1446,7 @@ int crt_bits(const CrtTable &t, long long K)
 }
 
 cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx, int crt_moduli, unsigned crt_mask,
-                        int crt_limbs)
+                        int crt_limbs, int crt_sets)
 {
     static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
     w.nmax = nmax;
@@ -1338,7 +1460,7 @@ cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx, int 
     if (crt_moduli > 0) {
         if (!crt_build_table(crt_moduli, crt_limbs, w.crt)) return cudaErrorInvalidValue;
         // byte planes of the residues share the int32 level planes' buffer
-        w.levels = std::max(w.levels, (crt_moduli + 3) / 4);
+        w.levels = std::max(w.levels, crt_sets * ((crt_moduli + 3) / 4));
         e = cudaMalloc((void **)&w.crt_dev, sizeof(CrtTable));
         if (e == cudaSuccess) e = cudaMemcpy(w.crt_dev, &w.crt, sizeof(CrtTable), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return e;
@@ -1512,8 +1634,41 @@ sr_status ozaki_split_td(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int
     return SR_OK;
 }
 
+sr_status ozaki_split_d6(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot_hi, int slot_lo, int R, int K,
+                         const double *X, size_t pl, int ld, int layout)
+{
+    if (w.cplx || slot_hi < 0 || slot_hi >= kOzakiSlots || slot_lo < 0 || slot_lo >= kOzakiSlots) return SR_ERR_INVALID_ARG;
+    OzakiSlot &sh = w.slot[slot_hi], &sl = w.slot[slot_lo];
+    const int s = kCrtDefaultModuliTD;
+    if (!sh.crt || !sl.crt || s != w.crt.N || w.crt.L != 12 || s > sh.cap || s > sl.cap || R > w.Pmax ||
+        K > ozaki_k_limit(false) || K > w.nmax)
+        return SR_ERR_INVALID_ARG;
+    const int Kp = (K + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
+    const int Rp = (R + 31) / 32 * 32;
+    SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, 6LL * R * K * 8 + 4LL * s * Kp * Rp, 2);
+    const int t = crt_bits(w.crt, K);
+    if (t < 160 || t > 174) return SR_ERR_UNSUPPORTED;   // 2t - 2 >= 318 bits: six doubles
+    sh.layout = sl.layout = layout;
+    sh.t = sl.t = t;
+    SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)Rp * sizeof(unsigned long long), st));
+    const dim3 gmax(Rp / 32, (K + SPLIT_KT - 1) / SPLIT_KT);
+    const dim3 gres(Rp / 32, (Kp + RES_KT - 1) / RES_KT);
+    __nv_bfloat16 *oh = (__nv_bfloat16 *)sh.dig, *ol = (__nv_bfloat16 *)sl.dig;
+    if (layout == OZ_COLS) {
+        ozaki_absmax_kernel<double, OZ_COLS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, X, ld, w.vmax);
+        ozaki_residues_d6_kernel<OZ_COLS><<<gres, 256, 0, st>>>(R, K, Kp, X, pl, ld, t, s, w.Pmax, w.Kmax, w.vmax, oh,
+                                                                ol, sh.exps, sl.exps, w.crt_dev);
+    } else {
+        ozaki_absmax_kernel<double, OZ_ROWS><<<gmax, 256, 0, st>>>(R, K, INT_MAX, K, X, ld, w.vmax);
+        ozaki_residues_d6_kernel<OZ_ROWS><<<gres, 256, 0, st>>>(R, K, Kp, X, pl, ld, t, s, w.Pmax, w.Kmax, w.vmax, oh,
+                                                                ol, sh.exps, sl.exps, w.crt_dev);
+    }
+    SR_CUDA_TRY(cudaGetLastError());
+    return SR_OK;
+}
+
 sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n, int k,
-                        int s, bool symmetric, int *flags)
+                        int s, bool symmetric, int *flags, int32_t *planes)
 {
     if (k > ozaki_k_limit(w.cplx)) return SR_ERR_UNSUPPORTED;
     const bool crt = w.slot[rows].crt != 0;
@@ -1553,7 +1708,7 @@ sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
     a.symmetric = symmetric ? 1 : 0;
     a.cplx = w.cplx ? 1 : 0;
     a.conj = (w.cplx && w.slot[rows].layout == OZ_COLS) ? 1 : 0;
-    a.planes = w.planes;
+    a.planes = planes ? planes : w.planes;
     a.pstride = (size_t)parts * w.Pmax * w.Pmax;
     a.flags = flags;
     a.nact = (int)active;

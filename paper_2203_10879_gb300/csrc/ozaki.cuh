@@ -56,6 +56,7 @@
 
 #include "common.cuh"
 #include "td.cuh"
+#include "d6.cuh"
 
 namespace sr {
 
@@ -71,7 +72,7 @@ constexpr int kOzakiTileJ = 128;      // columns of C per slice-product tile (MM
 constexpr int kOzakiKChunk = 256;
 constexpr int kOzakiMaxK = 16384;     // keeps every level sum below 2^31
 constexpr int kOzakiExpNonfinite = INT_MIN;
-constexpr int kOzakiSlots = 8;
+constexpr int kOzakiSlots = 12;
 // residue form
 constexpr int kCrtMaxModuli = 49;         // every pairwise coprime integer <= 256 the greedy rule takes
 constexpr int kCrtDefaultModuli = 16;     // FP64 operands: t = 56 bits at K <= 4096
@@ -174,10 +175,11 @@ struct OzakiWork {
 
 // caps[i] = digits of slot i (0 = unused); cplx: complex128 operands;
 // crt_moduli > 0: slots with crt_mask bit i set hold residues modulo that
-// many moduli instead of digits, rebuilt into FP64 (crt_limbs = 4) or
-// double-double (crt_limbs = 8) results
+// many moduli instead of digits, rebuilt into FP64 (crt_limbs = 4),
+// double-double (8) or triple- and six-double (12) results; crt_sets plane
+// sets of byte planes are kept (4 for the six-double products)
 cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx, int crt_moduli = 0,
-                        unsigned crt_mask = 0, int crt_limbs = 4);
+                        unsigned crt_mask = 0, int crt_limbs = 4, int crt_sets = 1);
 
 // ---- groups of independent products (many matrices in one launch) -------------------
 // A work area for a group holds the vectors of every matrix one after another
@@ -255,13 +257,18 @@ sr_status ozaki_split_dd(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int
 // triple-double form (t = 162 bits at K <= 4096)
 sr_status ozaki_split_td(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot, int R, int K,
                          const double *X0, const double *X1, const double *X2, int ld, int layout, int s);
+// Six-double operands (6 planes, plane k at X + k * pl): the fixed-point value of
+// T = 2t - 2 bits cut into halves X_hi 2^t + X_lo, their residues into the
+// slots slot_hi and slot_lo (48 moduli each, t = 162 bits at K <= 4096)
+sr_status ozaki_split_d6(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int slot_hi, int slot_lo, int R, int K,
+                         const double *X, size_t pl, int ld, int layout);
 
 // Level planes of the product of the vectors in slot `rows` (output rows i)
 // with those in slot `cols` (output columns j), inner length k. With
 // symmetric = true only tiles with i-tile <= j-tile are formed. Complex: the
 // row side is conjugated when slot `rows` holds columns (op = ^H).
 sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n, int k,
-                        int s, bool symmetric, int *flags);
+                        int s, bool symmetric, int *flags, int32_t *planes = nullptr);
 
 // v * 2^e as a product of two normal doubles (e within +-2044)
 __device__ inline double oz_pow2_scale(double v, int e)
@@ -913,6 +920,130 @@ ozaki_crt_combine_td_kernel(int m, int n, const uint8_t *__restrict__ planes, in
     }
 }
 
+// Six-double results: the product of operands held as two residue halves,
+// X = X_hi 2^t + X_lo for each vector, is HH 2^(2t) + (HL + LH) 2^t + LL. The
+// four integer products are the four plane sets (48 byte planes each) of one
+// entry; each is rebuilt into 12 limbs as for the triple-double form, the four
+// are summed exactly in a 768-bit two's complement integer, and its 512
+// leading bits are rounded once to six words. One entry per rebuild, 32 x 32
+// entries per block (no mirrored form: the Gram products are formed whole).
+template <int NM>
+__device__ __forceinline__ d6v crt_value_d6(const uint8_t *__restrict__ planes, size_t off, size_t pstride,
+                                            size_t setstride, const CrtRebuildSm &T, int e1, int e2, int t,
+                                            bool negs)
+{
+    constexpr int L = 12, NS = 12;   // limbs of one rebuild; 64-bit words of the sum
+    d6v r;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite) {
+#pragma unroll
+        for (int k = 0; k < kD6Words; ++k) r.x[k] = nan;
+        return r;
+    }
+    u64 S[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) S[k] = 0;
+#pragma unroll 1
+    for (int set = 0; set < 4; ++set) {
+        u64 acc[L];
+#pragma unroll
+        for (int k = 0; k < L; ++k) acc[k] = 0ull;
+        const size_t base = off + (size_t)set * setstride;
+#pragma unroll 4
+        for (int l = 0; l < NM; ++l) {
+            const uint32_t R = planes[base + (size_t)l * pstride];
+#pragma unroll
+            for (int k = 0; k < L; k += 4) {
+                const uint4 w4 = *reinterpret_cast<const uint4 *>(&T.w[l][k]);
+                acc[k] += (u64)R * w4.x;
+                acc[k + 1] += (u64)R * w4.y;
+                acc[k + 2] += (u64)R * w4.z;
+                acc[k + 3] += (u64)R * w4.w;
+            }
+        }
+        uint32_t mag[L];
+        const bool ng = crt_reduce<L>(acc, T, mag) != negs;
+        // mag (6 words) shifted by 2t (HH), t (HL, LH) or 0 (LL) into the sum
+        const int sh = set == 0 ? 2 * t : (set == 3 ? 0 : t);
+        const int q = sh >> 6, rr = sh & 63;
+        u64 v[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            u64 lo = 0, hi = 0;   // words k - q and k - q - 1 of mag
+#pragma unroll
+            for (int j = 0; j < L / 2; ++j) {
+                const u64 mj = ((u64)mag[2 * j + 1] << 32) | mag[2 * j];
+                if (j == k - q) lo = mj;
+                if (j == k - q - 1) hi = mj;
+            }
+            v[k] = rr ? (lo << rr) | (hi >> (64 - rr)) : lo;
+        }
+        if (ng) mw_neg<NS>(v);
+        mw_add<NS>(S, v);
+    }
+    const bool neg = (S[NS - 1] >> 63) != 0;
+    if (neg) mw_neg<NS>(S);
+    int top = 7;   // the 512-bit window: words top - 7 .. top
+#pragma unroll
+    for (int k = NS - 1; k >= 8; --k)
+        if (top == 7 && S[k] != 0) top = k;
+    u64 W[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) W[j] = mw_word<NS>(S, top - 7 + j);
+    const int T2 = 2 * (2 * t - 2);   // the operands hold T = 2t - 2 bits each
+    mw_round<kD6Words, 8>(W, neg, e1 + e2 - T2 - T.sigma + 64 * (top - 7), r.x);
+    return r;
+}
+
+template <class EP, int NM>
+__global__ void __launch_bounds__(256)
+ozaki_crt_combine_d6_kernel(int m, int n, const uint8_t *__restrict__ planes, int ldp, size_t pstride,
+                            size_t setstride, const int *__restrict__ ea, const int *__restrict__ fb, int t,
+                            double sign, EP ep, double *partial, const CrtTable *__restrict__ tab)
+{
+    __shared__ CrtRebuildSm T;
+    crt_stage(T, tab, 12);
+    __syncthreads();
+    const bool negs = sign < 0;
+    const int a = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    double part = 0.0;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+        const int i = blockIdx.x * 32 + a, j = blockIdx.y * 32 + wv + 8 * q;
+        if (i >= m || j >= n) continue;
+        const d6v v = crt_value_d6<NM>(planes, (size_t)i + (size_t)j * ldp, pstride, setstride, T, ea[i], fb[j],
+                                       t, negs);
+        part += ep(i, j, v);
+    }
+    if (partial) {
+        part = sr_block_sum<256>(part);
+        if (threadIdx.x == 0) partial[blockIdx.x + (size_t)gridDim.x * blockIdx.y] = part;
+    }
+}
+
+// The six-double product C = sign (rows) (cols) from the four products already
+// formed into the plane sets 0..3 of w.planes (HH, HL, LH, LL; rows and cols
+// are the high-half slots), with the epilogue ep.
+template <class EP>
+sr_status ozaki_combine_d6(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int rows, int cols, int m, int n,
+                           double sign, EP ep, double *partial, int *blocks)
+{
+    static_assert(ep_is_d6<EP>::value, "six-double epilogue");
+    if (w.cplx || w.crt.L != 12 || w.crt.N != kCrtDefaultModuliTD || !w.slot[rows].crt || !w.slot[cols].crt ||
+        w.slot[rows].t != w.slot[cols].t)
+        return SR_ERR_INVALID_ARG;
+    const int s = w.crt.N;
+    const dim3 grid((m + 31) / 32, (n + 31) / 32);
+    const size_t pstride = (size_t)w.Pmax * w.Pmax;
+    SrPhase ph(h, SR_PROF_OZ_COMBINE, 4LL * 24 * 12 * s * m * n, (long long)m * n * (4LL * s + 48), 1);
+    ozaki_crt_combine_d6_kernel<EP, kCrtDefaultModuliTD><<<grid, 256, 0, st>>>(
+        m, n, reinterpret_cast<const uint8_t *>(w.planes), w.Pmax, pstride, (size_t)s * pstride, w.slot[rows].exps,
+        w.slot[cols].exps, w.slot[rows].t, sign, ep, partial, w.crt_dev);
+    SR_CUDA_TRY(cudaGetLastError());
+    if (blocks) *blocks = ozaki_blocks(m, n);
+    return SR_OK;
+}
+
 inline int ozaki_crt_limbs(const OzakiWork &w) { return w.crt.L; }
 
 // epilogues of complex products carry `static constexpr bool kComplex`
@@ -1086,7 +1217,13 @@ enum {
     OZS_QROWS = 3,  // rows of Q (update product)
     OZS_W = 4,      // columns of W (low-precision digits)
     OZS_Y = 5,      // columns of Y (low-precision digits)
-    OZS_W2 = 6      // columns of W^2 (low-precision digits)
+    OZS_W2 = 6,     // columns of W^2 (low-precision digits)
+    // six-double products: the low halves of the residue operands (the high
+    // halves are in OZS_ROWS .. OZS_QROWS)
+    OZS_ROWS_LO = 8,
+    OZS_COLS_LO = 9,
+    OZS_X_LO = 10,
+    OZS_QROWS_LO = 11
 };
 
 // One emulated product C = op(A) B with the generic slots, epilogue ep

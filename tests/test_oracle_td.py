@@ -158,3 +158,20 @@ def test_fixed_point_oracle_agrees_with_double_double_oracle():
     rTd, rQd = mp.residuals_exact((p.A_hi, p.A_lo), Qf)
     rTf, rQf = mp.residuals_exact((p.A_hi, p.A_lo), rf.Q)
     assert rTd == pytest.approx(rTf, rel=1e-4) and rQf < 1e-38 and rQd < 1e-29
+
+
+def test_six_double_tolerance_is_reached_in_seven_passes():
+    # the 100-digit setting of Sec. 3 (six doubles): from a float64 start each
+    # pass gains about the factor u64 that the float64 correction allows, so the
+    # tolerance 1e-93 n is reached on the seventh pass (the paper reports 7-8
+    # iterations for 100 digits), and the factors are the exact planted ones
+    F6 = mp.FBITS_D6
+    p = inputs.unit_step_exact(16)
+    r = mp.refine_fx(p.A, p.Qhat, tol=mp.default_tol_d6(16), F=F6)
+    assert r.status == 0 and r.iters == 7 and r.hp_gemms == 28
+    rT, rQ = mp.residuals_exact(p.A, r.Q, F=F6)
+    assert rT <= mp.default_tol_d6(16) and rQ <= mp.default_tol_d6(16)
+    Q0 = mp.to_fx(p.Q0, F6)
+    s = [1 if sum(r.Q[:, j] * Q0[:, j]) > 0 else -1 for j in range(16)]
+    err = max(abs(int(r.Q[i, j]) - s[j] * int(Q0[i, j])) for i in range(16) for j in range(16))
+    assert err <= 2 ** (F6 - 330)
