@@ -8,14 +8,14 @@ Qhat = fl32(Q0 expm(1e-6 S))), with A and Qhat resident in HBM. The mixed form
 the all-FP64 form of the same iteration on the same inputs is timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload single|complex|batched|dd|td|sym|quasi|small]
+                    [--workload single|complex|batched|dd|td|d6|sym|quasi|small]
 
 --workload complex refines the complex n = 8192 ring problem instead
 (eigenvalues 0.5 exp(2 pi i k/n)(1 + U(0, 0.2)), complex64 starting factor,
 complex64 correction path, emulated complex128 products); the library builds no
 all-FP64 complex form, so that line carries no all-FP64 time. --workload dd
-refines n = 2048 to double-double, td n = 2048 to triple-double (an exact
-planted problem), sym a symmetric n = 4096 problem in the form
+refines n = 2048 to double-double, td n = 2048 to triple-double and d6
+n = 1024 to six-double (an exact planted problem), sym a symmetric n = 4096 problem in the form
 of Sec. 2.5, quasi a real n = 4096 problem whose Schur form has 2 x 2 blocks
 (the real Schur form of Sec. 3), small the n = 64 unit-step problem, batched
 1024 matrices of orders 32 to 512.
@@ -220,7 +220,7 @@ def _oracle_problem(workload: str, n: int):
         return inputs.ring_complex(n)
     if workload == "dd":
         return inputs.unit_step_dd(n)
-    if workload == "td":
+    if workload in ("td", "d6"):
         return inputs.unit_step_exact(n)
     return inputs.jittered_real(n)
 
@@ -238,6 +238,9 @@ def oracle_refine_seconds(workload: str, n: int):
     elif workload == "td":
         from oracle import mptarget
         r = mptarget.refine_fx(p.A, p.Qhat)
+    elif workload == "d6":
+        from oracle import mptarget
+        r = mptarget.refine_fx(p.A, p.Qhat, tol=mptarget.default_tol_d6(n), F=mptarget.FBITS_D6)
     else:
         r = oracle.refine(p.A, p.Qhat, lp="f32", symmetric=workload == "sym", quasi=workload == "quasi")
     dt = time.perf_counter() - t0
@@ -300,12 +303,14 @@ def run_reference(args):
     cores = _cores()
     if dd:
         sample = f"double-double oracle (C TwoProd/TwoSum products + C Alg. 2 in FP64) full refinement at n={n_ref}"
-    elif args.workload == "td":
-        sample = (f"fixed-point oracle (exact Python-integer hp products at 2^-256 + C Alg. 2 in FP64) full "
+    elif args.workload in ("td", "d6"):
+        fb = 512 if args.workload == "d6" else 256
+        sample = (f"fixed-point oracle (exact Python-integer hp products at 2^-{fb} + C Alg. 2 in FP64) full "
                   f"refinement at n={n_ref}")
     else:
         sample = f"oracle (numpy products + C Alg. 2 in the low precision) full refinement at n={n_ref}"
-    name = (_dd_workload_name(n_ref) if dd else _td_workload_name(n_ref) if args.workload == "td"
+    mw = {"td": 3, "d6": 6}.get(args.workload)
+    name = (_dd_workload_name(n_ref) if dd else _mw_workload_name(n_ref, mw) if mw
             else _workload_name(n_ref, cplx, sym, quasi))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
@@ -899,17 +904,23 @@ def run_dd(args):
     return 0
 
 
-def _td_workload_name(n):
+_MW_FORMS = {3: ("triple-double", 1e-45, "td"), 6: ("six-double", 1e-93, "d6")}
+
+
+def _mw_workload_name(n, words):
+    form, tol, _ = _MW_FORMS[words]
     return (f"real n={n} exact planted A=Q0 T0 Q0^T (Q0 = D1 P1 H D2 H P2 / n, Hadamard H, exactly orthogonal; "
             f"A exact in FP64), lambda_k=1+k/64, upper std 1/n in multiples of 2^-20, Qhat=fl64(Q0 expm(1e-14 S)); "
-            f"Alg. 4 with triple-double hp and FP64 lp to ||stril||/||A||<=1e-45 n")
+            f"Alg. 4 with {form} hp and FP64 lp to ||stril||/||A||<={tol:g} n")
 
 
-def run_td(args):
-    """The triple-double workload: one step = one refinement of the n = 2048 exact
-    planted problem from its FP64 start to ||stril||/||A|| <= 1e-45 n, with the
-    residue-form products (48 moduli, one bf16 tensor-core product each). The
-    refined factor is checked against the exact Q0 over every entry."""
+def run_mw(args, words):
+    """The multi-word workloads: one step = one refinement of the exact planted
+    problem (n = 2048 for three words, 1024 for six) from its FP64 start to
+    ||stril||/||A|| <= 1e-45 n (three words) or 1e-93 n (six), with the
+    residue-form products (48 moduli; one bf16 tensor-core product each for three
+    words, four for six). The refined factor is checked against the exact Q0
+    over every entry."""
     import numpy as np
     import torch
 
@@ -926,19 +937,21 @@ def run_td(args):
         dist = None
     n = args.n
     p = inputs.unit_step_exact(n)
+    form, tol_c, tag = _MW_FORMS[words]
     z = np.zeros_like(p.A)
-    hA_np = np.hstack([p.A, z, z])
+    hA_np = np.hstack([p.A] + [z] * (words - 1))
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
     A = dev(hA_np)
     Qhat = dev(p.Qhat)
-    Q = torch.empty((3 * n, n), dtype=torch.float64, device="cuda").t()
+    Q = torch.empty((words * n, n), dtype=torch.float64, device="cuda").t()
     stream = torch.cuda.current_stream()
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    ref = P.Refiner(n, target=B.SR_TARGET_TD, lp=B.SR_LP_FP64, qhat_type=B.SR_QHAT_FP64,
+    target = B.SR_TARGET_TD if words == 3 else B.SR_TARGET_D6
+    ref = P.Refiner(n, target=target, lp=B.SR_LP_FP64, qhat_type=B.SR_QHAT_FP64,
                     hp_gemm=B.SR_HP_OZAKI_CRT, profile=1)
     for _ in range(args.warmup):
         ref.step(A, Q, Qhat, check=False)
@@ -963,18 +976,21 @@ def run_td(args):
     # the refined factor against the exact Q0 (columns up to sign): x0 - q0 is
     # exact and the later words cancel what is left
     Qw = Q.t().contiguous().cpu().numpy().T
-    q = [np.asfortranarray(Qw[:, k * n:(k + 1) * n]) for k in range(3)]
+    q = [np.asfortranarray(Qw[:, k * n:(k + 1) * n]) for k in range(words)]
     sg = np.sign(np.sum(q[0] * p.Q0, axis=0))
     sg[sg == 0] = 1.0
-    q0_err = float(np.max(np.abs(((q[0] - p.Q0 * sg) + q[1]) + q[2])))
+    dq = q[0] - p.Q0 * sg
+    for k in range(1, words):
+        dq = dq + q[k]
+    q0_err = float(np.max(np.abs(dq)))
     e2e_s = None
     if not args.measured_only:
         hA = torch.from_numpy(np.ascontiguousarray(hA_np.T)).pin_memory()
         hQh = torch.from_numpy(np.ascontiguousarray(p.Qhat.T)).pin_memory()
-        hQ = torch.empty((3 * n, n), dtype=torch.float64).pin_memory()
-        dA_t = torch.empty((3 * n, n), dtype=torch.float64, device="cuda")
+        hQ = torch.empty((words * n, n), dtype=torch.float64).pin_memory()
+        dA_t = torch.empty((words * n, n), dtype=torch.float64, device="cuda")
         dQh_t = torch.empty((n, n), dtype=torch.float64, device="cuda")
-        dQ_t = torch.empty((3 * n, n), dtype=torch.float64, device="cuda")
+        dQ_t = torch.empty((words * n, n), dtype=torch.float64, device="cuda")
         ke = max(1, min(args.steps, 3))
         for i in range(1 + ke):
             if i == 1:
@@ -998,15 +1014,19 @@ def run_td(args):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         peak, psrc = bf16_peak(clk, peaks)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "residue products (tcgen05 kind::f16 bf16), crt-bf16-N48",
+                "traffic": None,
+                "kernel": "residue products (tcgen05 kind::f16 bf16), crt-bf16-N48" + ("" if words == 3 else " x 4"),
                 "peak_source": psrc}
     elif dom == "oz_combine":
-        # the rebuild: 48 x 12 64-bit multiply-adds per entry plus the reduction
-        # and rounding; bound by integer issue, its bytes are the planes it reads
+        # the rebuild: 48 x 12 64-bit multiply-adds per entry (per residue
+        # product) plus the reduction and rounding; bound by integer issue, its
+        # bytes are the planes it reads
         gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs") or 6800.0
+        kn = ("ozaki_crt_combine_td_kernel (48 byte planes in, 3 planes out)" if words == 3
+              else "ozaki_crt_combine_d6_kernel (4 x 48 byte planes in, 6 planes out)")
         roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                "traffic": None, "kernel": "ozaki_crt_combine_td_kernel (48 byte planes in, 3 planes out)",
+                "traffic": None, "kernel": kn,
                 "peak_source": "of measured HBM copy"}
     elif dom == "solve":
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
@@ -1023,19 +1043,21 @@ def run_td(args):
     roof["share_of_step"] = d["ms"] / (ms * args.steps)
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = cpu_baseline("td", n, args.cpu_sample_n, full=False)
-    tol = 1e-45 * n
+        cpu = cpu_baseline(tag, n, args.cpu_sample_n, full=False)
+    tol = tol_c * n
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "td+f64", "data": "synthetic",
-        "config": {"workload": _td_workload_name(n), "n": n,
-                   "form": "triple-double hp (residue form, 48 moduli), FP64 solve/products",
-                   "hp_gemm": "crt-bf16-N48",
-                   "l2": f"inputs larger than L2 (A {3 * n * n * 8 >> 20} MiB + Q + workspace)",
+        "vs_baseline": None, "dtype": f"{tag}+f64", "data": "synthetic",
+        "config": {"workload": _mw_workload_name(n, words), "n": n,
+                   "form": f"{form} hp (residue form, 48 moduli" + (")" if words == 3 else
+                           "; two halves of 162 bits per operand, four residue products)") +
+                           ", FP64 solve/products",
+                   "hp_gemm": "crt-bf16-N48" + ("" if words == 3 else "x4"),
+                   "l2": f"inputs larger than L2 (A {words * n * n * 8 >> 20} MiB + Q + workspace)",
                    "status": status, "iters": nr.iters, "hp_gemms": nr.hp_gemms,
                    "certified": {"stril_rel": rT, "orth": rQ, "tol": tol,
-                                 "kind": "the library's triple-double residual products",
+                                 "kind": f"the library's {form} residual products",
                                  "ok": bool(rT <= tol and rQ <= tol)},
                    "max_abs_Q_minus_exact_Q0": q0_err,
                    "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
@@ -1043,8 +1065,9 @@ def run_td(args):
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": None if e2e_s is None else {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n * n * 8 * 4),
-                                           "d2h_bytes_per_step": int(n * n * 24)},
+        "e2e": None if e2e_s is None else {"value": e2e_s, "unit": "s",
+                                           "h2d_bytes_per_step": int(n * n * 8 * (words + 1)),
+                                           "d2h_bytes_per_step": int(n * n * 8 * words)},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -1202,7 +1225,8 @@ def main():
     ap.add_argument("--measured-only", action="store_true",
                     help="time the measured path only (no end-to-end, comparison forms or CPU baseline): "
                          "the command the ncu summaries under profiles/ capture")
-    ap.add_argument("--workload", choices=["single", "complex", "batched", "dd", "td", "small", "sym", "quasi"],
+    ap.add_argument("--workload", choices=["single", "complex", "batched", "dd", "td", "d6", "small", "sym",
+                                           "quasi"],
                     default="single")
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--batch-streams", type=int, default=8)
@@ -1211,13 +1235,13 @@ def main():
     if rc is not None:
         return rc
     if args.n is None:
-        args.n = {"complex": 8192, "dd": 2048, "td": 2048, "small": 64}.get(args.workload, 4096)
+        args.n = {"complex": 8192, "dd": 2048, "td": 2048, "d6": 1024, "small": 64}.get(args.workload, 4096)
     if args.cpu_sample_n is None:
-        args.cpu_sample_n = {"complex": 2048, "dd": 512, "td": 128}.get(args.workload, 1024)
+        args.cpu_sample_n = {"complex": 2048, "dd": 512, "td": 128, "d6": 128}.get(args.workload, 1024)
     if args.cpu_full is None:
         # the complex n = 8192 oracle refinement takes tens of minutes on the host; the
         # quasi-triangular line samples at n = 1024 to stay within a few minutes
-        args.cpu_full = 0 if args.workload in ("complex", "quasi", "td") else 1
+        args.cpu_full = 0 if args.workload in ("complex", "quasi", "td", "d6") else 1
     args.cpu_full = bool(args.cpu_full)
     if args.measured_only:
         args.no_cpu_baseline = True
@@ -1227,8 +1251,8 @@ def main():
         return run_batched(args)
     if args.workload == "dd":
         return run_dd(args)
-    if args.workload == "td":
-        return run_td(args)
+    if args.workload in ("td", "d6"):
+        return run_mw(args, 3 if args.workload == "td" else 6)
     if args.workload == "small":
         return run_small(args)
     return run_ours(args)
