@@ -25,8 +25,8 @@ struct schur_refine_ctx {
     int *dflags = nullptr;
     double *hbuf = nullptr;      // pinned host mirror of dnorm (8) + flags
     sr::OzakiWork oz{};
-    // launch plan of the triangular solve for order plan_n
-    int plan_n = 0;
+    // launch plan of the stepwise triangular solve
+    int plan_n = 0, plan_b = 0;   // for order plan_n and tile plan_b
     uint32_t *plan = nullptr;
     size_t plan_cap = 0;
     std::vector<long long> plan_off;

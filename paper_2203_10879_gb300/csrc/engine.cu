@@ -19,9 +19,9 @@
 #include "trisolve.cuh"
 #include "quasi.cuh"
 
-void sr::trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long long> &offsets)
+void sr::trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long long> &offsets, int B)
 {
-    const int NB = (n + kSolveTile - 1) / kSolveTile;
+    const int NB = (n + B - 1) / B;
     tiles.clear();
     offsets.assign(1, 0);
     for (int t = NB - 1; t >= 0; --t) {
@@ -77,10 +77,10 @@ void sr::trisolve_flow_plan(int n, std::vector<unsigned long long> &tasks, int n
 }
 
 void sr::trisolve_plan_group(const std::vector<int> &orders, std::vector<unsigned long long> &tiles,
-                             std::vector<long long> &offsets, std::vector<long long> &nleaf)
+                             std::vector<long long> &offsets, std::vector<long long> &nleaf, int B)
 {
     int NBmax = 0;
-    for (int n : orders) NBmax = std::max(NBmax, (n + kSolveTile - 1) / kSolveTile);
+    for (int n : orders) NBmax = std::max(NBmax, (n + B - 1) / B);
     tiles.clear();
     nleaf.clear();
     offsets.assign(1, 0);
@@ -88,14 +88,14 @@ void sr::trisolve_plan_group(const std::vector<int> &orders, std::vector<unsigne
         const int d = t + 1;
         long long nl = 0;
         for (size_t b = 0; b < orders.size(); ++b) {
-            const int NB = (orders[b] + kSolveTile - 1) / kSolveTile;
+            const int NB = (orders[b] + B - 1) / B;
             for (int J = 0; J + t < NB; ++J) {
                 tiles.push_back((unsigned long long)b << 32 | (unsigned long long)((J + t) << 16 | J));
                 ++nl;
             }
         }
         for (size_t b = 0; b < orders.size(); ++b) {
-            const int NB = (orders[b] + kSolveTile - 1) / kSolveTile;
+            const int NB = (orders[b] + B - 1) / B;
             if (t >= NB) continue;
             for (int D = t - 1; D >= 0; --D)
                 for (int J = 0; J + D < NB; ++J) {
@@ -333,12 +333,13 @@ void drop_graphs(schur_refine_ctx *h)
     h->graphs.clear();
 }
 
-sr_status ensure_plan(schur_refine_ctx *h, int n)
+// the stepwise form's launch plan for order n and tile B
+sr_status ensure_plan(schur_refine_ctx *h, int n, int B)
 {
-    if (h->plan_n == n) return SR_OK;
+    if (h->plan_n == n && h->plan_b == B) return SR_OK;
     drop_graphs(h);   // graphs hold the old plan's pointer and contents
     std::vector<uint32_t> tiles;
-    sr::trisolve_plan(n, tiles, h->plan_off);
+    sr::trisolve_plan(n, tiles, h->plan_off, B);
     if (tiles.size() > h->plan_cap) {
         // the plan is built once per order; its buffer grows only when needed
         SR_CUDA_TRY(cudaStreamSynchronize(h->st));
@@ -356,6 +357,7 @@ sr_status ensure_plan(schur_refine_ctx *h, int n)
                                 h->st));
     SR_CUDA_TRY(cudaStreamSynchronize(h->st));   // tiles is a temporary
     h->plan_n = n;
+    h->plan_b = B;
     return SR_OK;
 }
 
@@ -396,7 +398,8 @@ template <typename Tl>
 sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum<Tl>::hp *dhp,
                 const double *dlo = nullptr)
 {
-    const int NB = (n + sr::kSolveTile - 1) / sr::kSolveTile;
+    constexpr int B = sr::StepTile<Tl>::B;
+    const int NB = (n + B - 1) / B;
     const int kind = SrNum<Tl>::kind;
     {
         if (h->opt.symmetric) {
@@ -420,7 +423,7 @@ sr_status solve(schur_refine_ctx *h, int n, Tl *TE, int ld, const typename SrNum
             return SR_OK;
         }
     }
-    SR_TRY(ensure_plan(h, n));
+    SR_TRY(ensure_plan(h, n, B));
     cudaGraphExec_t exec = nullptr;
     if (h->capturing) {
         // inside the refinement's own graph: the launches themselves are captured
@@ -669,7 +672,7 @@ sr_status solve_quasi(schur_refine_ctx *h, int n, Tl *TE, int ld, const double *
                                                      h->flow_plan, h->flow_ntasks, (Tl *)h->flow_acc, ldq,
                                                      h->flow_ctas[SrNum<Tl>::kind], h->opt.l_cap, h->qblkq));
         } else {
-            SR_TRY(ensure_plan(h, np));
+            SR_TRY(ensure_plan(h, np, sr::kSolveTile));   // the padded order's 32-row tiles
             const int NB = (np + sr::kSolveTile - 1) / sr::kSolveTile;
             const long long fl = 2LL * np * np * np / 3;
             SrPhase ph(h, SR_PROF_SOLVE, fl, (long long)np * np * (long long)sizeof(Tl), 2LL * NB);
@@ -1030,7 +1033,7 @@ sr_status build_refine_graph(schur_refine_ctx *h, int n, const void *dA, int lda
     double *Q = (double *)dQ, *Qw = h->Qw;
     const double *A = (const double *)dA;
     if (!h->ctl) SR_CUDA_TRY(cudaMalloc(&h->ctl, sizeof(SrCtl)));
-    SR_TRY(ensure_plan(h, n));   // host work and a synchronization: not inside a capture
+    SR_TRY(ensure_plan(h, n, sr::StepTile<Tl>::B));   // host work and a synchronization: not inside a capture
     SR_TRY(ensure_flow_plan(h, n));
     while (h->cstreams.empty()) {
         cudaStream_t s = nullptr;

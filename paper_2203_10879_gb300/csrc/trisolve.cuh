@@ -38,6 +38,16 @@ namespace sr {
 
 constexpr int kSolveTile = 32;
 
+// Tile of the stepwise form: 16 for FP64, 32 otherwise. A leaf tile's wavefront
+// runs on one SM and lies on the critical path; GB300's FP64 pipe retires about
+// 2 FMA per SM per cycle, so a 32 x 32 FP64 tile (about 4000 FP64 warp
+// instructions) takes ~60-100 us per block step, a 16 x 16 one about 8 times
+// less for twice the steps. The update kernels' FP64 work is the same n^3/3
+// FMAs for either size and runs beside the leaves.
+template <typename T> struct StepTile {
+    static constexpr int B = SrNum<T>::kind == 1 ? 16 : kSolveTile;
+};
+
 // divisor t_ii - t_jj formed in high precision and rounded to the working type
 template <typename T>
 __device__ inline T sr_div_round(typename SrNum<T>::hp di, typename SrNum<T>::hp dj)
@@ -58,7 +68,7 @@ __device__ inline double sr_div_round_dd(double hi_i, double lo_i, double hi_j, 
 
 // Launch plan: for step t, the tiles (I << 16 | J) of subdiagonal t (solved)
 // followed by the tiles with D < t that receive a product of subdiagonal t+1.
-void trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long long> &offsets);
+void trisolve_plan(int n, std::vector<uint32_t> &tiles, std::vector<long long> &offsets, int B = kSolveTile);
 
 // Task list of the dataflow solve of one matrix (trisolve_flow_kernel): for
 // s = NB-1 down to 0, the solve tasks of block subdiagonal s, then the helper
@@ -90,17 +100,18 @@ struct SolveMat {
 // down), the leaf tiles of all matrices with more than t block rows, then
 // their update tiles; leaf[t] and upd[t] give the counts.
 void trisolve_plan_group(const std::vector<int> &orders, std::vector<unsigned long long> &tiles,
-                         std::vector<long long> &offsets, std::vector<long long> &nleaf);
+                         std::vector<long long> &offsets, std::vector<long long> &nleaf, int B = kSolveTile);
 
 // ---- contributions of subdiagonal t+1 to tiles with D < t --------------------
 // Thread (tx, ty) owns the 4 x TN block rows 4tx.., columns TN*ty.., read with
-// vector loads from shared memory: TN = 4 (64 threads, 4 vector loads per 32
-// FMAs; shared-memory bandwidth bounds the FP32 update) except for FP64, whose
-// update is bound by the FP64 pipe and keeps TN = 2 with 128 threads for more
-// warps in flight.
-template <typename T> struct UpdShape {
+// vector loads from shared memory: TN = 4 (64 threads for a 32 x 32 tile, 4
+// vector loads per 32 FMAs; shared-memory bandwidth bounds the FP32 update)
+// except for FP64, whose update is bound by the FP64 pipe and keeps TN = 2
+// (128 threads for a 32 x 32 tile, 32 for a 16 x 16 one).
+template <typename T, int B = kSolveTile> struct UpdShape {
     static constexpr int TN = SrNum<T>::kind == 1 ? 2 : 4;
-    static constexpr int NT = 8 * (32 / TN);
+    static constexpr int TX = B / 4;   // row groups of 4
+    static constexpr int NT = TX * (B / TN);
 };
 template <typename T> struct SolveVec;
 template <> struct SolveVec<float> {
@@ -204,14 +215,14 @@ __device__ __forceinline__ void tile_pair_products(const T (*Ta)[KB][SA], const 
     }
 }
 
-template <typename T, bool GROUP = false>
-__global__ void __launch_bounds__(UpdShape<T>::NT)
+template <typename T, bool GROUP = false, int B = kSolveTile>
+__global__ void __launch_bounds__(UpdShape<T, B>::NT)
 trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t *__restrict__ plan,
                        const SolveMat *__restrict__ mats = nullptr,
                        const unsigned long long *__restrict__ gplan = nullptr, T *__restrict__ accb = nullptr,
                        int ldacc = 0)
 {
-    constexpr int B = kSolveTile, SA = B + 4, SB = B + 4;
+    constexpr int SA = B + 4, SB = B + 4;
     uint32_t tile;
     if constexpr (GROUP) {
         const unsigned long long g = gplan[blockIdx.x];
@@ -233,16 +244,15 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
     const int d = t + 1;
     __shared__ __align__(16) T Ta[2][B][SA];   // left operands, transposed: Ta[u][k][row]
     __shared__ __align__(16) T Tb[2][B][SB];   // right operands: Tb[u][k][col]
-    constexpr int TN = UpdShape<T>::TN, NT = UpdShape<T>::NT, LR = NT / 32;
+    constexpr int TN = UpdShape<T, B>::TN, NT = UpdShape<T, B>::NT, TX = UpdShape<T, B>::TX;
     const int tid = threadIdx.x;
-    const int lx = tid & 31, ly = tid >> 5;   // load mapping: element (lx, ly + LR q)
-    const int tx = tid & 7, ty = tid >> 3;    // block rows 4tx.., columns TN ty..
+    const int tx = tid % TX, ty = tid / TX;   // block rows 4tx.., columns TN ty..
     const T Z = SrNum<T>::zero();
     const bool hasP = J + d < NB, hasM = I - d >= 0;
     const int kP = (J + d) * B, kM = (I - d) * B;
 #pragma unroll
-    for (int q = 0; q < 32 / LR; ++q) {
-        const int y = ly + LR * q;
+    for (int q = 0; q < B * B / NT; ++q) {
+        const int e = tid + NT * q, lx = e % B, y = e / B;   // element (lx, y) of each tile
         Ta[0][y][lx] = (hasP && r0 + lx < n && kP + y < n) ? TE[sr_idx(r0 + lx, kP + y, ld)] : Z;
         Tb[0][lx][y] = (hasP && kP + lx < n && c0 + y < n) ? TE[sr_idx(kP + lx, c0 + y, ld)] : Z;
         Ta[1][y][lx] = (hasM && r0 + lx < n && kM + y < n) ? TE[sr_idx(r0 + lx, kM + y, ld)] : Z;
@@ -260,7 +270,7 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
                             : Z;
         }
     __syncthreads();
-    tile_pair_products<T, TN, SA>(Ta, Tb, tx, ty, hasP, hasM, acc);
+    tile_pair_products<T, TN, SA, B>(Ta, Tb, tx, ty, hasP, hasM, acc);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -274,9 +284,9 @@ trisolve_update_kernel(int n, T *__restrict__ TE, int ld, int t, const uint32_t 
 }
 
 // ---- solve of the tiles of subdiagonal t ---------------------------------------
-// 1024 threads; thread (lane a, warp b) owns entry (a, b) of the tile.
-template <typename T, bool GROUP = false>
-__global__ void __launch_bounds__(1024)
+// B x B threads; thread a + B b owns entry (a, b) of the tile.
+template <typename T, bool GROUP = false, int B = kSolveTile>
+__global__ void __launch_bounds__(B * B)
 trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>::hp *__restrict__ dhp,
                      const double *__restrict__ dlo, int t, const uint32_t *__restrict__ plan, int *__restrict__ flags,
                      double cap,
@@ -285,7 +295,7 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
                      int ldacc = 0)
 {
     using Hp = typename SrNum<T>::hp;
-    constexpr int B = kSolveTile, S = B + 1;
+    constexpr int S = B + 1;
     const T Z = SrNum<T>::zero();
     uint32_t tile;
     if constexpr (GROUP) {
@@ -318,7 +328,7 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
     T (*Tj)[S] = sm[2];
     __shared__ Hp dI[B], dJ[B];
     __shared__ double dIl[B], dJl[B];   // low parts of a double-double diagonal (dlo given)
-    const int a = threadIdx.x & 31, b = threadIdx.x >> 5;
+    const int a = threadIdx.x % B, b = threadIdx.x / B;
     const bool own = a < nr && b < nc && (D > 0 || a > b);
 
     // 1. E plus the two products of subdiagonal t+1
@@ -368,8 +378,8 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
     __syncthreads();
 
     // 2. wavefront over the tile's subdiagonals. When subdiagonal w is final, a
-    // pending entry (a, b) adds T_II(a, b+w) X(b+w, b) (from lane b+w of its
-    // own warp) and -X(a, a-w) T_JJ(a-w, b) (from shared memory).
+    // pending entry (a, b) adds T_II(a, b+w) X(b+w, b) (from the lane of its own
+    // warp that owns (b+w, b)) and -X(a, a-w) T_JJ(a-w, b) (from shared memory).
     Ti[a][b] = (a <= b && a < nr && b < nr) ? TE[sr_idx(r0 + a, r0 + b, ld)] : Z;
     Tj[a][b] = (a <= b && a < nc && b < nc) ? TE[sr_idx(c0 + a, c0 + b, ld)] : Z;
     X[a][b] = Z;
@@ -389,8 +399,8 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
             X[a][b] = xv;
         }
         __syncthreads();
-        const int c = b + w;                         // (c, b): lane c of this warp
-        const T xcol = sr_shfl(xv, c & 31);
+        const int c = b + w;                         // (c, b): lane (c + B b) mod 32 of this warp
+        const T xcol = sr_shfl(xv, (c + B * b) & 31);
         if (own && a - b < w) {
             if (c < nr) acc = sr_fma(Ti[a][c], xcol, acc);
             const int c2 = a - w;                    // (a, c2), c2 < b
@@ -403,14 +413,16 @@ trisolve_leaf_kernel(int n, T *__restrict__ TE, int ld, const typename SrNum<T>:
 
 // The launch sequence on two streams: leaf kernels on `st`, update kernels on
 // `aux`, with a full dependency between consecutive steps (events ev0, ev1).
-// plan: device copy of trisolve_plan's tiles; offsets: its host offsets.
+// plan: device copy of trisolve_plan's tiles for the tile StepTile<T>::B;
+// offsets: its host offsets.
 template <typename T>
 inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEvent_t ev0, cudaEvent_t ev1, int n,
                                      T *TE, int ld, const typename SrNum<T>::hp *dhp, const double *dlo,
                                      int *flags, const uint32_t *plan, const std::vector<long long> &offsets,
                                      double cap = 0.0, T *accb = nullptr, int ldacc = 0)
 {
-    const int NB = (n + kSolveTile - 1) / kSolveTile;
+    constexpr int B = StepTile<T>::B;   // the plan is built for this tile
+    const int NB = (n + B - 1) / B;
     // accb (optional): the far products' sums, apart from E; cleared first
     cudaError_t e = accb ? cudaMemset2DAsync(accb, (size_t)ldacc * sizeof(T), 0, (size_t)n * sizeof(T), n, st)
                          : cudaSuccess;
@@ -420,10 +432,10 @@ inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEven
         const int l = NB - 1 - t;
         const long long nleaf = NB - t;
         const long long nupd = offsets[l + 1] - offsets[l] - nleaf;
-        trisolve_leaf_kernel<T><<<(unsigned)nleaf, 1024, 0, st>>>(n, TE, ld, dhp, dlo, t, plan + offsets[l], flags,
-                                                                 cap, nullptr, nullptr, accb, ldacc);
+        trisolve_leaf_kernel<T, false, B><<<(unsigned)nleaf, B * B, 0, st>>>(
+            n, TE, ld, dhp, dlo, t, plan + offsets[l], flags, cap, nullptr, nullptr, accb, ldacc);
         if (nupd > 0)
-            trisolve_update_kernel<T><<<(unsigned)nupd, UpdShape<T>::NT, 0, aux>>>(
+            trisolve_update_kernel<T, false, B><<<(unsigned)nupd, UpdShape<T, B>::NT, 0, aux>>>(
                 n, TE, ld, t, plan + offsets[l] + nleaf, nullptr, nullptr, accb, ldacc);
         e = cudaGetLastError();
         // both kernels of this step finish before either of the next starts
@@ -435,14 +447,16 @@ inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEven
     return e;
 }
 
-// The launches of a group plan (no double-double divisors): the same two-stream
-// sequence as trisolve_launches, steps t = nsteps-1 .. 0.
+// The launches of a group plan (no double-double divisors; the plan built for
+// StepTile<T>::B): the same two-stream sequence as trisolve_launches, steps
+// t = nsteps-1 .. 0.
 template <typename T>
 inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cudaEvent_t ev0, cudaEvent_t ev1,
                                            const SolveMat *mats, int *flags, const unsigned long long *plan,
                                            const std::vector<long long> &offsets, const std::vector<long long> &nleaf,
                                            double cap = 0.0)
 {
+    constexpr int B = StepTile<T>::B;   // the plan is built for this tile
     const int nsteps = (int)nleaf.size();
     cudaError_t e = cudaEventRecord(ev0, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev0, 0);
@@ -451,11 +465,11 @@ inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cu
         const long long nl = nleaf[l];
         const long long nupd = offsets[l + 1] - offsets[l] - nl;
         if (nl > 0)
-            trisolve_leaf_kernel<T, true><<<(unsigned)nl, 1024, 0, st>>>(0, nullptr, 0, nullptr, nullptr, t, nullptr,
-                                                                        flags, cap, mats, plan + offsets[l]);
+            trisolve_leaf_kernel<T, true, B><<<(unsigned)nl, B * B, 0, st>>>(0, nullptr, 0, nullptr, nullptr, t,
+                                                                            nullptr, flags, cap, mats, plan + offsets[l]);
         if (nupd > 0)
-            trisolve_update_kernel<T, true><<<(unsigned)nupd, UpdShape<T>::NT, 0, aux>>>(0, nullptr, 0, t, nullptr, mats,
-                                                                                    plan + offsets[l] + nl);
+            trisolve_update_kernel<T, true, B><<<(unsigned)nupd, UpdShape<T, B>::NT, 0, aux>>>(
+                0, nullptr, 0, t, nullptr, mats, plan + offsets[l] + nl);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
         if (e == cudaSuccess) e = cudaEventRecord(ev1, aux);
