@@ -654,9 +654,16 @@ def run_batched(args):
     stream = torch.cuda.current_stream()
     out = {}
     clk = None
-    # grouped launches (the measured path), the worker pool of streams, one matrix at a time
-    for key, mode, workers in (("grouped", 0, 1), ("streams", 1, args.batch_streams), ("serial", 1, 1)):
-        opt = B.default_options(hp_gemm=B.SR_HP_OZAKI_BF16, lp=B.SR_LP_FP32, batch_streams=workers,
+    # grouped launches (the measured path), the same with digit-form products, the
+    # worker pool of streams, one matrix at a time
+    hp = {"crt": B.SR_HP_OZAKI_CRT, "ozaki": B.SR_HP_OZAKI_BF16, "fp64": B.SR_HP_FP64}[args.hp]
+    runs = [("grouped", 0, 1, hp), ("streams", 1, args.batch_streams, hp), ("serial", 1, 1, hp)]
+    if hp == B.SR_HP_OZAKI_CRT and not args.measured_only:
+        runs.insert(1, ("grouped_digits", 0, 1, B.SR_HP_OZAKI_BF16))
+    if args.measured_only:
+        runs = runs[:1]
+    for key, mode, workers, hpk in runs:
+        opt = B.default_options(hp_gemm=hpk, lp=B.SR_LP_FP32, batch_streams=workers,
                                 batch_mode=mode, profile=1 if key == "grouped" else 0)
         st, h = B.schur_refine_create(nmax, opt, stream.cuda_stream)
         assert st == 0
@@ -693,9 +700,10 @@ def run_batched(args):
         if mma["ms"] > 0:
             achieved = mma["flops"] / (mma["ms"] * 1e-3) / 1e12
             peak, psrc = bf16_peak(clk, peaks)
+            kern = ("residue products (16 moduli), work-item form (tcgen05 kind::f16 bf16)"
+                    if hp == B.SR_HP_OZAKI_CRT else "ozaki slice products, work-item form (tcgen05 kind::f16 bf16)")
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "ozaki slice products, work-item form (tcgen05 kind::f16 bf16)",
-                    "peak_source": psrc,
+                    "traffic": None, "kernel": kern, "peak_source": psrc,
                     "share_of_step": mma["ms"] / (ms * args.steps)}
         cpu = None
         if not args.no_cpu_baseline:
@@ -714,11 +722,16 @@ def run_batched(args):
                 "data": "synthetic",
                 "config": {"workload": f"{len(ns)} real matrices, n log-uniform in [32,512] (sum n^3 = "
                                        f"{float(np.sum(ns.astype(float) ** 3)):.3g}), unit-step spectra, FP32 Qhat",
-                           "form": "grouped launches (every stage one launch for all live matrices)",
+                           "form": "grouped launches (every stage one launch for all live matrices), "
+                                   + {"crt": "residue-form FP64 products (16 moduli)",
+                                      "ozaki": "digit-form FP64 products (7 digits)",
+                                      "fp64": "native FP64 products"}[args.hp],
                            "status": st, "all_ok": all(x == 0 for x in stats), "mean_iters": float(np.mean(iters)),
-                           "worker_streams_ms": out["streams"][0], "worker_streams": args.batch_streams,
-                           "one_at_a_time_ms": out["serial"][0],
-                           "speedup_vs_one_at_a_time": out["serial"][0] / ms,
+                           "grouped_digit_form_ms": out["grouped_digits"][0] if "grouped_digits" in out else None,
+                           "worker_streams_ms": out["streams"][0] if "streams" in out else None,
+                           "worker_streams": args.batch_streams,
+                           "one_at_a_time_ms": out["serial"][0] if "serial" in out else None,
+                           "speedup_vs_one_at_a_time": out["serial"][0] / ms if "serial" in out else None,
                            "phase_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
                            "launches_per_step": int(sum(v["launches"] for v in prof.values()) / args.steps)},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk,

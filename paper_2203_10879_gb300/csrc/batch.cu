@@ -156,6 +156,7 @@ struct BatchWork {
     int *flow = nullptr;
     size_t flow_cap = 0;
     int flow_ctas = 0;
+    int crt = -1;              // the high-precision slots hold residues (1) or digits (0)
 };
 
 void sr_batch_free(BatchWork *bw)
@@ -180,10 +181,11 @@ void sr_batch_free(BatchWork *bw)
 
 bool sr_batch_supported(const sr_options &o)
 {
-    return o.dtype == SR_REAL && o.target == SR_TARGET_FP64 && o.hp_gemm == SR_HP_OZAKI_BF16 &&
+    const bool crt = o.hp_gemm == SR_HP_OZAKI_CRT;
+    return o.dtype == SR_REAL && o.target == SR_TARGET_FP64 && (o.hp_gemm == SR_HP_OZAKI_BF16 || crt) &&
            o.lp == SR_LP_FP32 && o.qhat_type == SR_QHAT_FP32 && !o.full_sigma && sr::kOzakiBuilt &&
-           (o.ozaki_slices <= 0 || o.ozaki_slices == kHp) && (o.lp_slices <= 0 || o.lp_slices == kLp) &&
-           !o.symmetric;
+           (o.ozaki_slices <= 0 || o.ozaki_slices == (crt ? sr::kCrtDefaultModuli : kHp)) &&
+           (o.lp_slices <= 0 || o.lp_slices == kLp) && !o.symmetric;
 }
 
 namespace {
@@ -203,7 +205,7 @@ struct DescPack {
 };
 
 sr_status ensure_capacity(BatchWork *bw, long long elems, int rows, int count, long long planes, int kmax,
-                          size_t npartial, size_t flow_words, int dev)
+                          size_t npartial, size_t flow_words, int dev, bool crt)
 {
     cudaError_t e = cudaSuccess;
     if (flow_words > bw->flow_cap) {
@@ -228,7 +230,7 @@ sr_status ensure_capacity(BatchWork *bw, long long elems, int rows, int count, l
         bw->flow_ctas = std::max(1, per_sm) * sms;
     }
     if (elems > bw->cap_elems || rows > bw->cap_rows || planes > bw->cap_planes || count > bw->cap_count ||
-        kmax > bw->cap_k) {
+        kmax > bw->cap_k || bw->crt != (crt ? 1 : 0)) {
         // grow everything together (the group's buffers are replaced wholesale)
         double **bufs[] = {&bw->Q0, &bw->Q1, &bw->AQ, &bw->Y, &bw->Delta, &bw->W, &bw->W2, &bw->YW};
         for (double **p : bufs) { cudaFree(*p); *p = nullptr; }
@@ -250,16 +252,22 @@ sr_status ensure_capacity(BatchWork *bw, long long elems, int rows, int count, l
         if (e == cudaSuccess) e = cudaMalloc((void **)&bw->norms, (size_t)C * kNorms * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc((void **)&bw->flags, (size_t)C * sizeof(int));
         // slots: rows of A, columns of Q, columns of A Q / Delta, rows of Q (FP64
-        // class); columns of W, Y, W^2 (FP32 class)
+        // class: digits, or residues modulo 16 moduli); columns of W, Y, W^2 (FP32 class)
         int caps[sr::kOzakiSlots] = {kHp, kHp, kHp, kHp, kLp, kLp, kLp, 0};
-        if (e == cudaSuccess) e = sr::ozaki_alloc_group(bw->oz, R + sr::kOzakiTileI, Kx, caps, P);
+        const unsigned hp_mask = (1u << sr::OZS_ROWS) | (1u << sr::OZS_COLS) | (1u << sr::OZS_X) |
+                                 (1u << sr::OZS_QROWS);
+        if (e == cudaSuccess)
+            e = sr::ozaki_alloc_group(bw->oz, R + sr::kOzakiTileI, Kx, caps, P, crt ? sr::kCrtDefaultModuli : 0,
+                                      crt ? hp_mask : 0u);
         if (e != cudaSuccess) {
             sr_set_last_cuda_error(e);
             cudaGetLastError();
             bw->cap_elems = bw->cap_rows = bw->cap_count = bw->cap_k = 0;
             bw->cap_planes = 0;
+            bw->crt = -1;
             return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
         }
+        bw->crt = crt ? 1 : 0;
         bw->cap_elems = E;
         bw->cap_rows = R;
         bw->cap_count = C;
@@ -343,11 +351,12 @@ Grids add_grids(DescPack &pk, const std::vector<int> &order, const std::vector<i
     return G;
 }
 
-long long item_flops(const std::vector<sr::MmaItem> &items, int s)
+// bf16 flops of a slice product: s (s + 1) / 2 digit pairs, or s residue products
+long long item_flops(const std::vector<sr::MmaItem> &items, int s, bool crt)
 {
     long long f = 0;
     for (const auto &it : items)
-        f += (long long)s * (s + 1) / 2 * 2LL * sr::kOzakiTileI * sr::kOzakiTileJ *
+        f += (crt ? (long long)s : (long long)s * (s + 1) / 2) * 2LL * sr::kOzakiTileI * sr::kOzakiTileJ *
              ((it.nch - 1) * sr::kOzakiKChunk + it.kbl * 64);
     return f;
 }
@@ -382,7 +391,19 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
     // published words of the dataflow solve: NB_b^2 per matrix
     size_t flow_words = 2;
     for (int b = 0; b < batch; ++b) flow_words += (size_t)((n[b] + 31) / 32) * (size_t)((n[b] + 31) / 32);
-    SR_TRY(ensure_capacity(bw, elems, rows, batch, planes, std::max(512, nmx), (size_t)t32_all, flow_words, h->dev));
+    const bool crt = h->opt.hp_gemm == SR_HP_OZAKI_CRT;
+    SR_TRY(ensure_capacity(bw, elems, rows, batch, planes, std::max(512, nmx), (size_t)t32_all, flow_words, h->dev,
+                           crt));
+    // FP64-class products: digits, or residues modulo 16 moduli with each matrix's
+    // fixed-point bits t from its order (as schur_refine_step on that matrix alone)
+    const int shp = crt ? kCrtDefaultModuli : kHp;
+    const long long pb = crt ? shp : 4LL * shp;   // plane bytes per entry
+    std::vector<int> tb(batch, 0);
+    if (crt)
+        for (int b = 0; b < batch; ++b) {
+            tb[b] = crt_bits(bw->oz.crt, n[b]);
+            if (tb[b] < 1 || tb[b] > 62) return SR_ERR_UNSUPPORTED;
+        }
 
     std::vector<int> cur(batch, 0);   // buffer holding the current Q: 0 = Q0, 1 = Q1
     std::vector<double> y_last(batch, NAN), prev(batch, INFINITY), anorm(batch, 1.0);
@@ -453,7 +474,7 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
     };
     auto product = [&](int rs, int cs, size_t o, const std::vector<MmaItem> &it, int s) {
         return ozaki_product_items(h, st, bw->oz, rs, cs, (const MmaItem *)P(o), (int)it.size(), s,
-                                   item_flops(it, s), h->dflags);
+                                   item_flops(it, s, bw->oz.slot[rs].crt != 0), h->dflags);
     };
 
     SR_CUDA_TRY(cudaMemsetAsync(bw->flags, 0, (size_t)batch * sizeof(int), st));
@@ -474,17 +495,17 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
             const long long o = off[b];
             ga[b] = GMat{o, nb, nb, dA[b], nullptr};
             gq[b] = GMat{o, nb, nb, dQhat[b], nullptr};
-            arows[b] = SplitMat{(const double *)dA[b], nb, nb, nb, row0[b]};
-            qcols[b] = SplitMat{bw->Q0 + o, nb, nb, nb, row0[b]};
-            qrows[b] = SplitMat{bw->Q0 + o, nb, nb, nb, row0[b]};
-            ycols[b] = SplitMat{bw->Y + o, nb, nb, nb, row0[b]};
-            cm[b] = CombMat{poff[b], r32(nb), nb, nb, row0[b], row0[b]};
+            arows[b] = SplitMat{(const double *)dA[b], nb, nb, nb, row0[b], tb[b]};
+            qcols[b] = SplitMat{bw->Q0 + o, nb, nb, nb, row0[b], tb[b]};
+            qrows[b] = SplitMat{bw->Q0 + o, nb, nb, nb, row0[b], tb[b]};
+            ycols[b] = SplitMat{bw->Y + o, nb, nb, nb, row0[b], tb[b]};
+            cm[b] = CombMat{poff[b], r32(nb), nb, nb, row0[b], row0[b], 2 * tb[b]};
             epy[b] = EpMinusI{bw->Y + o, nb};
             epu[b] = EpUpdate{bw->Q0 + o, nb, bw->Q1 + o, nb, -0.5};
         }
         std::vector<MmaItem> sym, full;
-        make_items(sym, act, n, row0, poff, kHp, true);
-        make_items(full, act, n, row0, poff, kHp, false);
+        make_items(sym, act, n, row0, poff, shp, true);
+        make_items(full, act, n, row0, poff, shp, false);
         const size_t o_ga = pk.add(ga), o_gq = pk.add(gq), o_ar = pk.add(arows), o_qc = pk.add(qcols),
                      o_qr = pk.add(qrows), o_yc = pk.add(ycols), o_cm = pk.add(cm), o_epy = pk.add(epy),
                      o_epu = pk.add(epu), o_sym = pk.add(sym), o_full = pk.add(full), o_map = pk.add(act);
@@ -496,22 +517,22 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
             SR_CUDA_TRY(cudaGetLastError());
         }
         SR_TRY(reduce(g, o_map, 2));
-        SR_TRY(split(OZS_ROWS, o_ar, g, OZ_ROWS, kHp, elems));
+        SR_TRY(split(OZS_ROWS, o_ar, g, OZ_ROWS, shp, elems));
         {
             SrPhase ph(h, SR_PROF_OTHER, 0, 12 * elems, 1);
             group_convert_kernel<<<g.t32, blk, 0, st>>>((const GMat *)P(o_gq), (const int *)P(g.o32), g.m, bw->Q0);
             SR_CUDA_TRY(cudaGetLastError());
         }
-        SR_TRY(split(OZS_COLS, o_qc, g, OZ_COLS, kHp, elems));
-        SR_TRY(product(OZS_COLS, OZS_COLS, o_sym, sym, kHp));
-        SR_TRY(combine(OZS_COLS, OZS_COLS, o_cm, (const EpMinusI *)P(o_epy), g, kHp, 1.0, true, bw->partial, elems,
-                       4LL * kHp + 8));
+        SR_TRY(split(OZS_COLS, o_qc, g, OZ_COLS, shp, elems));
+        SR_TRY(product(OZS_COLS, OZS_COLS, o_sym, sym, shp));
+        SR_TRY(combine(OZS_COLS, OZS_COLS, o_cm, (const EpMinusI *)P(o_epy), g, shp, 1.0, true, bw->partial, elems,
+                       pb + 8));
         SR_TRY(reduce(g, o_map, 1));
-        SR_TRY(split(OZS_QROWS, o_qr, g, OZ_ROWS, kHp, elems));
-        SR_TRY(split(OZS_X, o_yc, g, OZ_COLS, kHp, elems));
-        SR_TRY(product(OZS_QROWS, OZS_X, o_full, full, kHp));
-        SR_TRY(combine(OZS_QROWS, OZS_X, o_cm, (const EpUpdate *)P(o_epu), g, kHp, 1.0, false, nullptr, elems,
-                       4LL * kHp + 24));
+        SR_TRY(split(OZS_QROWS, o_qr, g, OZ_ROWS, shp, elems));
+        SR_TRY(split(OZS_X, o_yc, g, OZ_COLS, shp, elems));
+        SR_TRY(product(OZS_QROWS, OZS_X, o_full, full, shp));
+        SR_TRY(combine(OZS_QROWS, OZS_X, o_cm, (const EpUpdate *)P(o_epu), g, shp, 1.0, false, nullptr, elems,
+                       pb + 24));
         SR_TRY(sync_read());
         if (timed_out()) return SR_ERR_TIMEOUT;
         for (int b = 0; b < batch; ++b) {
@@ -536,26 +557,26 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
             for (int a = 0; a < m; ++a) {
                 const int b = act[a], nb = n[b];
                 const long long o = off[b];
-                qcols[a] = SplitMat{Qbuf[cur[b]] + o, nb, nb, nb, row0[b]};
-                aqcols[a] = SplitMat{bw->AQ + o, nb, nb, nb, row0[b]};
-                cm[a] = CombMat{poff[b], r32(nb), nb, nb, row0[b], row0[b]};
+                qcols[a] = SplitMat{Qbuf[cur[b]] + o, nb, nb, nb, row0[b], tb[b]};
+                aqcols[a] = SplitMat{bw->AQ + o, nb, nb, nb, row0[b], tb[b]};
+                cm[a] = CombMat{poff[b], r32(nb), nb, nb, row0[b], row0[b], 2 * tb[b]};
                 e_aq[a] = EpStore{bw->AQ + o, nb};
                 e_sp[a] = EpSplit<float>{bw->TE + o, nb, bw->diag + row0[b], nullptr, nb};
             }
             std::vector<MmaItem> full;
-            make_items(full, act, n, row0, poff, kHp, false);
+            make_items(full, act, n, row0, poff, shp, false);
             const size_t o_qc = pk.add(qcols), o_aqc = pk.add(aqcols), o_cm = pk.add(cm), o_eaq = pk.add(e_aq),
                          o_esp = pk.add(e_sp), o_full = pk.add(full), o_map = pk.add(act);
             const Grids g = add_grids(pk, act, n);
             SR_TRY(upload(pk));
-            SR_TRY(split(OZS_COLS, o_qc, g, OZ_COLS, kHp, el));
-            SR_TRY(product(OZS_ROWS, OZS_COLS, o_full, full, kHp));
-            SR_TRY(combine(OZS_ROWS, OZS_COLS, o_cm, (const EpStore *)P(o_eaq), g, kHp, 1.0, false, nullptr, el,
-                           4LL * kHp + 8));
-            SR_TRY(split(OZS_X, o_aqc, g, OZ_COLS, kHp, el));
-            SR_TRY(product(OZS_COLS, OZS_X, o_full, full, kHp));
-            SR_TRY(combine(OZS_COLS, OZS_X, o_cm, (const EpSplit<float> *)P(o_esp), g, kHp, 1.0, false, bw->partial,
-                           el, 4LL * kHp + 4));
+            SR_TRY(split(OZS_COLS, o_qc, g, OZ_COLS, shp, el));
+            SR_TRY(product(OZS_ROWS, OZS_COLS, o_full, full, shp));
+            SR_TRY(combine(OZS_ROWS, OZS_COLS, o_cm, (const EpStore *)P(o_eaq), g, shp, 1.0, false, nullptr, el,
+                           pb + 8));
+            SR_TRY(split(OZS_X, o_aqc, g, OZ_COLS, shp, el));
+            SR_TRY(product(OZS_COLS, OZS_X, o_full, full, shp));
+            SR_TRY(combine(OZS_COLS, OZS_X, o_cm, (const EpSplit<float> *)P(o_esp), g, shp, 1.0, false, bw->partial,
+                           el, pb + 4));
             SR_TRY(reduce(g, o_map, 0));
             SR_TRY(sync_read());
             if (timed_out()) {
@@ -602,12 +623,12 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
                 fwords += (long long)((nb + 31) / 32) * ((nb + 31) / 32);
                 orders[b] = nb;
                 ga[a] = GMat{o, nb, nb, nullptr, nullptr};
-                wcols[a] = SplitMat{bw->W + o, nb, nb, nb, row0[b]};
-                ycols[a] = SplitMat{bw->Y + o, nb, nb, nb, row0[b]};
-                w2cols[a] = SplitMat{bw->W2 + o, nb, nb, nb, row0[b]};
-                qrows[a] = SplitMat{Qc, nb, nb, nb, row0[b]};
-                dcols[a] = SplitMat{bw->Delta + o, nb, nb, nb, row0[b]};
-                cm[a] = CombMat{poff[b], r32(nb), nb, nb, row0[b], row0[b]};
+                wcols[a] = SplitMat{bw->W + o, nb, nb, nb, row0[b], tb[b]};
+                ycols[a] = SplitMat{bw->Y + o, nb, nb, nb, row0[b], tb[b]};
+                w2cols[a] = SplitMat{bw->W2 + o, nb, nb, nb, row0[b], tb[b]};
+                qrows[a] = SplitMat{Qc, nb, nb, nb, row0[b], tb[b]};
+                dcols[a] = SplitMat{bw->Delta + o, nb, nb, nb, row0[b], tb[b]};
+                cm[a] = CombMat{poff[b], r32(nb), nb, nb, row0[b], row0[b], 2 * tb[b]};
                 e_y[a] = EpMinusI{bw->Y + o, nb};
                 e_w2[a] = EpStore{bw->W2 + o, nb};
                 e_yw[a] = EpStore{bw->YW + o, nb};
@@ -625,8 +646,8 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
                 for (size_t l = 0; l < nleaf.size(); ++l)
                     fplan.insert(fplan.end(), plan.begin() + poffs[l], plan.begin() + poffs[l] + nleaf[l]);
             std::vector<MmaItem> full_hp, sym_hp, full_lp, sym_lp;
-            make_items(full_hp, act, n, row0, poff, kHp, false);
-            make_items(sym_hp, act, n, row0, poff, kHp, true);
+            make_items(full_hp, act, n, row0, poff, shp, false);
+            make_items(sym_hp, act, n, row0, poff, shp, true);
             make_items(full_lp, act, n, row0, poff, kLp, false);
             make_items(sym_lp, act, n, row0, poff, kLp, true);
             const size_t o_sm = pk.add(sm), o_pl = pk.add(plan), o_ga = pk.add(ga), o_wc = pk.add(wcols),
@@ -657,9 +678,9 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
                 }
             }
             // S5: Y = Q^T Q - I from Q's column digits (still in slot OZS_COLS), W = L - L^T
-            SR_TRY(product(OZS_COLS, OZS_COLS, o_sh, sym_hp, kHp));
-            SR_TRY(combine(OZS_COLS, OZS_COLS, o_cm, (const EpMinusI *)P(o_ey), g, kHp, 1.0, true, bw->partial, el,
-                           4LL * kHp + 8));
+            SR_TRY(product(OZS_COLS, OZS_COLS, o_sh, sym_hp, shp));
+            SR_TRY(combine(OZS_COLS, OZS_COLS, o_cm, (const EpMinusI *)P(o_ey), g, shp, 1.0, true, bw->partial, el,
+                           pb + 8));
             SR_TRY(reduce(g, o_map, 1));
             {
                 SrPhase ph(h, SR_PROF_OTHER, 0, 12 * el, 1);
@@ -681,11 +702,11 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
             SR_TRY(combine(OZS_W, OZS_W2, o_cm, (const EpDeltaD *)P(o_ed), g, kLp, -1.0, false, nullptr, el,
                            4LL * kLp + 40));
             // S8: Q_new = Q + 1/2 Q Delta
-            SR_TRY(split(OZS_QROWS, o_qr, g, OZ_ROWS, kHp, el));
-            SR_TRY(split(OZS_X, o_dc, g, OZ_COLS, kHp, el));
-            SR_TRY(product(OZS_QROWS, OZS_X, o_fh, full_hp, kHp));
-            SR_TRY(combine(OZS_QROWS, OZS_X, o_cm, (const EpUpdate *)P(o_eu), g, kHp, 1.0, false, nullptr, el,
-                           4LL * kHp + 24));
+            SR_TRY(split(OZS_QROWS, o_qr, g, OZ_ROWS, shp, el));
+            SR_TRY(split(OZS_X, o_dc, g, OZ_COLS, shp, el));
+            SR_TRY(product(OZS_QROWS, OZS_X, o_fh, full_hp, shp));
+            SR_TRY(combine(OZS_QROWS, OZS_X, o_cm, (const EpUpdate *)P(o_eu), g, shp, 1.0, false, nullptr, el,
+                           pb + 24));
             SR_TRY(sync_read());
         }
         if (timed_out()) {

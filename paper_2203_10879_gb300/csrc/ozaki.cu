@@ -433,10 +433,12 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     }
                 if (!ok) break;
                 const uint32_t bias = count * 0x4B400000u;
-                if (!ITEMS && args.crt) {
+                if (args.crt && (!ITEMS || jl < v.clim)) {
                     // the exact sum (|sum| <= 64 chunks * 2^22 = 2^28) reduced modulo m into bytes
+                    // (a work item's region rows come in multiples of 32: whole 16-byte stores)
                     const uint32_t m = (uint32_t)args.mods[l], off = args.off28[l];
                     const unsigned long long inv = args.inv40[l];
+                    const int rmax = ITEMS ? v.rlim - half * (BN / 2) : BN;
                     uint8_t *dst8 = reinterpret_cast<uint8_t *>(args.planes) + (size_t)l * args.pstride +
                                     (size_t)v.poff + (size_t)jl * v.ldp + (size_t)(half * (BN / 2));
 #pragma unroll
@@ -453,8 +455,10 @@ ozaki_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                             }
                             wd[b] = pk;
                         }
-                        *reinterpret_cast<uint4 *>(dst8 + c) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                        if (c < rmax) *reinterpret_cast<uint4 *>(dst8 + c) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
                     }
+                } else if (args.crt) {
+                    // a column beyond the item's region: nothing to store
                 } else if (!ITEMS || jl < v.clim) {
                     int32_t *dst = args.planes + (size_t)l * args.pstride + (size_t)v.poff + (size_t)jl * v.ldp +
                                    (size_t)(half * (BN / 2));
@@ -944,26 +948,28 @@ __device__ __forceinline__ void crt_pieces(double xh, double xl, int t, int e, i
     }
 }
 
-template <typename Tin, int LAYOUT, int NM, bool DD>
-__global__ void __launch_bounds__(256)
-ozaki_residues_fast_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, const double *__restrict__ Xl,
-                           int ld, int t, int Pmax, int Kmax, const unsigned long long *__restrict__ vmax,
-                           __nv_bfloat16 *__restrict__ out, int *__restrict__ exps)
+// block (bx, by): vectors 32 bx .., K stretch [KT by, KT (by + 1))
+template <typename Tin, int LAYOUT, int NM, bool DD, int KT>
+__device__ __forceinline__ void residues_fast_body(int bx, int by, int R, int K, int Kh, int Kp,
+                                                   const Tin *__restrict__ X, const double *__restrict__ Xl, int ld,
+                                                   int t, int Pmax, int Kmax,
+                                                   const unsigned long long *__restrict__ vmax,
+                                                   __nv_bfloat16 *__restrict__ out, int *__restrict__ exps)
 {
     constexpr int P = DD ? 8 : 4;
     __shared__ double th[32][33];
     __shared__ double tl[DD ? 32 : 1][33];
     __shared__ int sexp[32];
-    const int r0 = blockIdx.x * 32, kbeg = blockIdx.y * RES_KT;
+    const int r0 = bx * 32, kbeg = by * KT;
     if (threadIdx.x < 32) {
         const int r = r0 + threadIdx.x;
         const int e = (r < R) ? split_exponent(vmax[r]) : 0;
         sexp[threadIdx.x] = e;
-        if (blockIdx.y == 0) exps[r] = e;
+        if (by == 0) exps[r] = e;
     }
     const int v = threadIdx.x >> 3, g = threadIdx.x & 7;
     const size_t pstride = (size_t)Pmax * Kmax;
-    for (int k0 = kbeg; k0 < kbeg + RES_KT && k0 < Kp; k0 += 32) {
+    for (int k0 = kbeg; k0 < kbeg + KT && k0 < Kp; k0 += 32) {
         __syncthreads();
         split_load_tile<Tin, LAYOUT>(th, X, ld, R, K, Kh, r0, k0);
         if constexpr (DD) split_load_tile<double, LAYOUT>(tl, Xl, ld, R, K, INT_MAX, r0, k0);
@@ -989,6 +995,34 @@ ozaki_residues_fast_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__
             *reinterpret_cast<uint2 *>(o + (size_t)l * pstride) = make_uint2(w01, w23);
         }
     }
+}
+
+template <typename Tin, int LAYOUT, int NM, bool DD>
+__global__ void __launch_bounds__(256)
+ozaki_residues_fast_kernel(int R, int K, int Kh, int Kp, const Tin *__restrict__ X, const double *__restrict__ Xl,
+                           int ld, int t, int Pmax, int Kmax, const unsigned long long *__restrict__ vmax,
+                           __nv_bfloat16 *__restrict__ out, int *__restrict__ exps)
+{
+    residues_fast_body<Tin, LAYOUT, NM, DD, RES_KT>(blockIdx.x, blockIdx.y, R, K, Kh, Kp, X, Xl, ld, t, Pmax, Kmax,
+                                                    vmax, out, exps);
+}
+
+// Grouped residue split (FP64 vectors, the 16 moduli of FP64 products): the
+// flat grid of the grouped digit split (blocks of 32 vectors x 64 of K), each
+// matrix with its own fixed-point bits t.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256)
+ozaki_residues_group_kernel(const SplitMat *__restrict__ mats, const int *__restrict__ start, int m, int Pmax,
+                            int Kmax, const unsigned long long *__restrict__ vmax, __nv_bfloat16 *__restrict__ out,
+                            int *__restrict__ exps)
+{
+    const int a = group_find(start, m, blockIdx.x);
+    const SplitMat g = mats[a];
+    const int Kp = (g.K + 63) / 64 * 64;   // work items stop at the order rounded to 64
+    const int local = blockIdx.x - start[a], gx = (g.R + 31) / 32;
+    residues_fast_body<double, LAYOUT, kCrtDefaultModuli, false, DIGIT_KT>(
+        local % gx, local / gx, g.R, g.K, INT_MAX, Kp, g.X, nullptr, g.ld, g.t, Pmax, Kmax, vmax + g.row0,
+        out + (size_t)g.row0 * Kmax, exps + g.row0);
 }
 
 // Triple-double operands: x0 + x1 + x2 times 2^(t - e), each word rounded to the
@@ -1762,20 +1796,33 @@ sr_status ozaki_product(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, int 
     return SR_OK;
 }
 
-cudaError_t ozaki_alloc_group(OzakiWork &w, int rows, int kmax, const int *caps, long long plane_elems)
+cudaError_t ozaki_alloc_group(OzakiWork &w, int rows, int kmax, const int *caps, long long plane_elems,
+                              int crt_moduli, unsigned crt_mask)
 {
     w.nmax = kmax;
     w.cplx = false;
     w.Pmax = (rows + kOzakiTileI - 1) / kOzakiTileI * kOzakiTileI;
     w.Kmax = (kmax + kOzakiKChunk - 1) / kOzakiKChunk * kOzakiKChunk;
     w.levels = kOzakiMaxSlices;
-    for (int i = 0; i < kOzakiSlots; ++i) w.levels = std::max(w.levels, caps[i]);
+    for (int i = 0; i < kOzakiSlots; ++i)
+        if (!(crt_mask >> i & 1u) || crt_moduli <= 0) w.levels = std::max(w.levels, caps[i]);
     w.pstride_group = plane_elems;
-    cudaError_t e = cudaMalloc((void **)&w.planes, (size_t)w.levels * (size_t)plane_elems * sizeof(int32_t));
+    cudaError_t e = cudaSuccess;
+    if (crt_moduli > 0) {
+        // FP64 results (4 limbs); crt_moduli byte planes fill (crt_moduli + 3) / 4 level planes
+        if (!crt_build_table(crt_moduli, 4, w.crt)) return cudaErrorInvalidValue;
+        w.levels = std::max(w.levels, (crt_moduli + 3) / 4);
+        e = cudaMalloc((void **)&w.crt_dev, sizeof(CrtTable));
+        if (e == cudaSuccess) e = cudaMemcpy(w.crt_dev, &w.crt, sizeof(CrtTable), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMalloc((void **)&w.planes, (size_t)w.levels * (size_t)plane_elems * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&w.vmax, (size_t)w.Pmax * sizeof(unsigned long long));
     for (int i = 0; i < kOzakiSlots && e == cudaSuccess; ++i) {
         OzakiSlot &sl = w.slot[i];
         sl.cap = caps[i];
+        sl.crt = (crt_mask >> i & 1u) && crt_moduli > 0 ? 1 : 0;
+        if (sl.crt) sl.cap = crt_moduli;
         if (sl.cap <= 0) continue;
         const size_t bytes = (size_t)sl.cap * w.Pmax * w.Kmax * 2;
         e = cudaMalloc(&sl.dig, bytes);
@@ -1793,14 +1840,28 @@ sr_status ozaki_split_group(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, 
                             int layout, int s, long long bytes)
 {
     if (g.m <= 0) return SR_OK;
-    if (slot < 0 || slot >= kOzakiSlots || s < 1 || s > w.slot[slot].cap || s > kOzakiMaxSlices || g.maxK > w.Kmax)
+    if (slot < 0 || slot >= kOzakiSlots || s < 1 || s > w.slot[slot].cap || g.maxK > w.Kmax)
+        return SR_ERR_INVALID_ARG;
+    const bool crt = w.slot[slot].crt != 0;
+    if (crt ? (s != w.crt.N || s != kCrtDefaultModuli || w.crt.L != 4) : s > kOzakiMaxSlices)
         return SR_ERR_INVALID_ARG;
     SrPhase ph(h, SR_PROF_OZ_SPLIT, 0, bytes, 2);
     w.slot[slot].layout = layout;
+    w.slot[slot].t = 0;   // residue form: each matrix's t travels in its SplitMat
     __nv_bfloat16 *out = (__nv_bfloat16 *)w.slot[slot].dig;
     int *ex = w.slot[slot].exps;
     SR_CUDA_TRY(cudaMemsetAsync(w.vmax, 0, (size_t)w.Pmax * sizeof(unsigned long long), st));
-    if (layout == OZ_COLS) {
+    if (crt) {
+        if (layout == OZ_COLS) {
+            ozaki_absmax_group_kernel<OZ_COLS><<<g.total_max, 256, 0, st>>>(g.mats, g.start_max, g.m, w.vmax);
+            ozaki_residues_group_kernel<OZ_COLS><<<g.total_dig, 256, 0, st>>>(g.mats, g.start_dig, g.m, w.Pmax,
+                                                                              w.Kmax, w.vmax, out, ex);
+        } else {
+            ozaki_absmax_group_kernel<OZ_ROWS><<<g.total_max, 256, 0, st>>>(g.mats, g.start_max, g.m, w.vmax);
+            ozaki_residues_group_kernel<OZ_ROWS><<<g.total_dig, 256, 0, st>>>(g.mats, g.start_dig, g.m, w.Pmax,
+                                                                              w.Kmax, w.vmax, out, ex);
+        }
+    } else if (layout == OZ_COLS) {
         ozaki_absmax_group_kernel<OZ_COLS><<<g.total_max, 256, 0, st>>>(g.mats, g.start_max, g.m, w.vmax);
         ozaki_digits_group_kernel<OZ_COLS><<<g.total_dig, 256, 0, st>>>(g.mats, g.start_dig, g.m, s, w.Pmax, w.Kmax,
                                                                         w.vmax, out, ex);
@@ -1817,12 +1878,24 @@ sr_status ozaki_product_items(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w
                               const MmaItem *items, int nitems, int s, long long flops, int *flags)
 {
     if (nitems <= 0) return SR_OK;
-    if (s < 1 || s > w.slot[rows].cap || s > w.slot[cols].cap || s > w.levels) return SR_ERR_INVALID_ARG;
+    const bool crt = w.slot[rows].crt && w.slot[cols].crt;
+    if (w.slot[rows].crt != w.slot[cols].crt || (crt && s != w.crt.N)) return SR_ERR_INVALID_ARG;
+    if (s < 1 || s > w.slot[rows].cap || s > w.slot[cols].cap || (crt ? s > 4 * w.levels : s > w.levels))
+        return SR_ERR_INVALID_ARG;
     // every item's K is at most w.Kmax: level sums stay below 2^31 when s * chunks * 2^22 does
-    if ((long long)s * (w.Kmax / kOzakiKChunk) * (1LL << 22) >= (1LL << 31)) return SR_ERR_UNSUPPORTED;
+    // (a residue product: one product per level, below 2^28 for 64 chunks)
+    if (crt ? (w.Kmax / kOzakiKChunk) > 64 : (long long)s * (w.Kmax / kOzakiKChunk) * (1LL << 22) >= (1LL << 31))
+        return SR_ERR_UNSUPPORTED;
     SrPhase ph(h, SR_PROF_OZ_MMA, flops, 0, 1);
     MmaArgs a{};
     a.s = s;
+    a.crt = crt ? 1 : 0;
+    if (crt)
+        for (int l = 0; l < s; ++l) {
+            a.mods[l] = w.crt.m[l];
+            a.inv40[l] = w.crt.inv40[l];
+            a.off28[l] = w.crt.off28[l];
+        }
     a.nch = w.Kmax / kOzakiKChunk;
     a.Pmax = w.Pmax;
     a.planes = w.planes;

@@ -186,13 +186,17 @@ cudaError_t ozaki_alloc(OzakiWork &w, int nmax, const int *caps, bool cplx, int 
 // in each digit slot: matrix b's vectors are slot rows [row0_b, row0_b + R_b),
 // row0_b a multiple of 32; `rows` is the total (the slot's row stride Pmax).
 // Level planes are per-matrix regions at plane offsets chosen by the caller.
-cudaError_t ozaki_alloc_group(OzakiWork &w, int rows, int kmax, const int *caps, long long plane_elems);
+// crt_moduli > 0: the slots in crt_mask hold residues (FP64 results, 4 limbs),
+// whose byte planes share the level planes' buffer (plane stride plane_elems bytes)
+cudaError_t ozaki_alloc_group(OzakiWork &w, int rows, int kmax, const int *caps, long long plane_elems,
+                              int crt_moduli = 0, unsigned crt_mask = 0);
 
 // one matrix of a grouped split: vectors r < R of length K (layout as in
 // ozaki_split) go to slot rows row0 + r
 struct SplitMat {
     const double *X;
     int ld, R, K, row0;
+    int t = 0;   // residue form: fixed-point bits of the vectors
 };
 
 // one output tile of a slice product (a work item of the grouped launch)
@@ -211,6 +215,7 @@ struct MmaItem {
 struct CombMat {
     long long poff;
     int ldp, m, n, ra, rb;
+    int tsum = 0;   // residue form: t of the row side plus t of the column side
 };
 
 // The flat grids of a grouped split (device arrays): matrix a of the launch
@@ -685,26 +690,29 @@ crt_value(const uint8_t *__restrict__ planes, size_t off, size_t pstride, const 
 // mirrored block (coalesced along the planes' contiguous index) and turns it
 // in shared memory; entries below the diagonal of a diagonal block read the
 // mirrored position directly.
+template <bool CPLX, int L>
+using CrtCombineValue = std::conditional_t<CPLX, cd, std::conditional_t<L == 8, ddv, double>>;
+
+// The 32 x 32 output block (bx, by) of one product (planes: its region's
+// origin); returns the thread's sum of the epilogue's values. T is staged and
+// turned is the block's shared turning buffer.
 template <class EP, bool CPLX, int L, int NM>
-__global__ void __launch_bounds__(256)
-ozaki_crt_combine_kernel(int m, int n, const uint8_t *__restrict__ planes, int ldp, size_t pstride, size_t imoff,
-                         const int *__restrict__ ea, const int *__restrict__ fb, int tsum, double sign, int mirror,
-                         EP ep, double *partial, const CrtTable *__restrict__ tab)
+__device__ __forceinline__ double crt_combine_block(int bx, int by, int m, int n, const uint8_t *__restrict__ planes,
+                                                    int ldp, size_t pstride, size_t imoff, const int *__restrict__ ea,
+                                                    const int *__restrict__ fb, int tsum, double sign, int mirror,
+                                                    const EP &ep, const CrtRebuildSm &T,
+                                                    CrtCombineValue<CPLX, L> (&turned)[32][33])
 {
     static_assert(!(CPLX && L == 8), "complex products rebuild FP64 parts");
     using RV = std::conditional_t<L == 8, ddv, double>;
-    using VT = std::conditional_t<CPLX, cd, RV>;
-    __shared__ CrtRebuildSm T;
-    __shared__ VT turned[32][33];
-    crt_stage(T, tab, L);
-    __syncthreads();
+    using VT = CrtCombineValue<CPLX, L>;
     const int N = T.N;
     const bool negs = sign < 0;
     const int ig = threadIdx.x & 7, jl = threadIdx.x >> 3;
-    const bool below = mirror && blockIdx.x > blockIdx.y;
+    const bool below = mirror && bx > by;
     // rebuilt entries (ra + 4 ig + u, ca + jl) of the planes, u = 0..3
-    const int ra = (below ? blockIdx.y : blockIdx.x) * 32 + 4 * ig;
-    const int ca = (below ? blockIdx.x : blockIdx.y) * 32 + jl;
+    const int ra = (below ? by : bx) * 32 + 4 * ig;
+    const int ca = (below ? bx : by) * 32 + jl;
     const int rlim = below ? n : m, clim = below ? m : n;
     VT val[4];
     auto rebuild = [&](size_t base, int e2, RV (&out)[4]) {
@@ -782,7 +790,7 @@ ozaki_crt_combine_kernel(int m, int n, const uint8_t *__restrict__ planes, int l
 #pragma unroll
             for (int u = 0; u < 4; ++u) turned[jl][4 * ig + u] = val[u];
         __syncthreads();
-        const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+        const int i0 = bx * 32, j0 = by * 32;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int i = i0 + 4 * ig + u, j = j0 + jl;
@@ -809,11 +817,54 @@ ozaki_crt_combine_kernel(int m, int n, const uint8_t *__restrict__ planes, int l
             part += ep(i, j, v);
         }
     }
+    return part;
+}
+
+template <class EP, bool CPLX, int L, int NM>
+__global__ void __launch_bounds__(256)
+ozaki_crt_combine_kernel(int m, int n, const uint8_t *__restrict__ planes, int ldp, size_t pstride, size_t imoff,
+                         const int *__restrict__ ea, const int *__restrict__ fb, int tsum, double sign, int mirror,
+                         EP ep, double *partial, const CrtTable *__restrict__ tab)
+{
+    __shared__ CrtRebuildSm T;
+    __shared__ CrtCombineValue<CPLX, L> turned[32][33];
+    crt_stage(T, tab, L);
+    __syncthreads();
+    double part = crt_combine_block<EP, CPLX, L, NM>(blockIdx.x, blockIdx.y, m, n, planes, ldp, pstride, imoff, ea,
+                                                     fb, tsum, sign, mirror, ep, T, turned);
     if (partial) {
         part = sr_block_sum<256>(part);
         if (threadIdx.x == 0) partial[blockIdx.x + (size_t)gridDim.x * blockIdx.y] = part;
     }
 }
+
+// Grouped residue-form combine (FP64 results, NM moduli): one flat grid of
+// 32 x 32 output blocks over all matrices as ozaki_combine_group_kernel, each
+// matrix's planes a byte region at its poff (leading dimension ldp, a
+// multiple of 32) and its own tsum.
+template <class EP, int NM>
+__global__ void __launch_bounds__(256)
+ozaki_crt_combine_group_kernel(const uint8_t *__restrict__ planes, size_t pstride, const CombMat *__restrict__ mats,
+                               const EP *__restrict__ eps, const int *__restrict__ start, int cnt,
+                               const int *__restrict__ ea, const int *__restrict__ fb, double sign, int mirror,
+                               double *partial, const CrtTable *__restrict__ tab)
+{
+    __shared__ CrtRebuildSm T;
+    __shared__ CrtCombineValue<false, 4> turned[32][33];
+    crt_stage(T, tab, 4);
+    __syncthreads();
+    const int a = group_find(start, cnt, blockIdx.x);
+    const CombMat cm = mats[a];
+    const int local = blockIdx.x - start[a], gx = (cm.m + 31) / 32;
+    double part = crt_combine_block<EP, false, 4, NM>(local % gx, local / gx, cm.m, cm.n, planes + cm.poff, cm.ldp,
+                                                      pstride, 0, ea + cm.ra, fb + cm.rb, cm.tsum, sign, mirror,
+                                                      eps[a], T, turned);
+    if (partial) {
+        part = sr_block_sum<256>(part);
+        if (threadIdx.x == 0) partial[blockIdx.x] = part;
+    }
+}
+
 
 // Triple-double results (L = 12 limbs, the 48 moduli of the triple-double
 // operands): one entry per rebuild, so that the twelve 64-bit column sums
@@ -1202,6 +1253,17 @@ sr_status ozaki_combine_group(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w
 {
     if (cnt <= 0 || total <= 0) return SR_OK;
     SrPhase ph(h, SR_PROF_OZ_COMBINE, flops, bytes, 1);
+    if (w.slot[rows].crt || w.slot[cols].crt) {
+        // residue form: byte planes, 16 moduli (FP64 results)
+        if (!w.slot[rows].crt || !w.slot[cols].crt || s != w.crt.N || w.crt.N != kCrtDefaultModuli ||
+            w.crt.L != 4)
+            return SR_ERR_INVALID_ARG;
+        ozaki_crt_combine_group_kernel<EP, kCrtDefaultModuli><<<total, 256, 0, st>>>(
+            reinterpret_cast<const uint8_t *>(w.planes), (size_t)w.pstride_group, mats, eps, start, cnt,
+            w.slot[rows].exps, w.slot[cols].exps, sign, mirror ? 1 : 0, partial, w.crt_dev);
+        SR_CUDA_TRY(cudaGetLastError());
+        return SR_OK;
+    }
     ozaki_combine_group_kernel<EP><<<total, 256, 0, st>>>(s, w.planes, (size_t)w.pstride_group, mats, eps, start,
                                                           cnt, w.slot[rows].exps, w.slot[cols].exps, sign,
                                                           mirror ? 1 : 0, partial);

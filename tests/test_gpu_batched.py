@@ -42,7 +42,7 @@ def batch():
     return [inputs.batch_problem(i, n) for i, n in enumerate(ns)]
 
 
-@pytest.mark.parametrize("hp", [B.SR_HP_OZAKI_BF16, B.SR_HP_FP64])
+@pytest.mark.parametrize("hp", [B.SR_HP_OZAKI_BF16, B.SR_HP_OZAKI_CRT, B.SR_HP_FP64])
 def test_batched_matches_oracle(batch, hp):
     st, iters, stats, Qs = _run(batch, 4, hp_gemm=hp, lp=B.SR_LP_FP32)
     assert st == B.SR_OK and all(x == B.SR_OK for x in stats)
@@ -77,12 +77,15 @@ def _single(p, **kw):
         B.schur_refine_destroy(h)
 
 
+@pytest.mark.parametrize("hp", [B.SR_HP_OZAKI_BF16, B.SR_HP_OZAKI_CRT])
 @pytest.mark.parametrize("solve_mode", [1, 2])
-def test_grouped_launches_equal_single_steps(batch, solve_mode):
-    st, iters, stats, Qs = _run(batch, 8, mode=0, hp_gemm=B.SR_HP_OZAKI_BF16, solve_mode=solve_mode)
+def test_grouped_launches_equal_single_steps(batch, solve_mode, hp):
+    # the residue form: each matrix's residues, products and rebuild use the
+    # fixed-point bits t of its own order, as a single step on it does
+    st, iters, stats, Qs = _run(batch, 8, mode=0, hp_gemm=hp, solve_mode=solve_mode)
     assert st == B.SR_OK
     for p, Q, k, s in zip(batch, Qs, iters, stats):
-        s1, k1, Q1 = _single(p, hp_gemm=B.SR_HP_OZAKI_BF16, solve_mode=solve_mode)
+        s1, k1, Q1 = _single(p, hp_gemm=hp, solve_mode=solve_mode)
         assert (s, k) == (s1, k1), p.n
         if solve_mode == 2:
             assert np.array_equal(Q, Q1), p.n
@@ -93,15 +96,16 @@ def test_grouped_launches_equal_single_steps(batch, solve_mode):
             assert np.max(np.abs(Q - Q1)) <= 1e-13, p.n
 
 
-def test_grouped_launches_isolate_a_failing_matrix(batch):
+@pytest.mark.parametrize("hp", [B.SR_HP_OZAKI_BF16, B.SR_HP_OZAKI_CRT])
+def test_grouped_launches_isolate_a_failing_matrix(batch, hp):
     # the variance reading of the upper entries (std 1/sqrt(n)) on a packed
     # spectrum diverges (the analogue of Example 3); its neighbours must not care
     bad = inputs.jittered_real(200, upper_std=1.0 / np.sqrt(200))
     group = batch[:5] + [bad] + batch[5:9]
-    st, iters, stats, Qs = _run(group, 8, mode=0, hp_gemm=B.SR_HP_OZAKI_BF16)
+    st, iters, stats, Qs = _run(group, 8, mode=0, hp_gemm=hp)
     assert stats[5] in (B.SR_ERR_NONFINITE, B.SR_ERR_NOT_CONVERGED, B.SR_ERR_NONDISTINCT)
     assert st == stats[5]
-    _, _, _, Qok = _run(batch[:9], 8, mode=0, hp_gemm=B.SR_HP_OZAKI_BF16)
+    _, _, _, Qok = _run(batch[:9], 8, mode=0, hp_gemm=hp)
     for a, b, s in zip(Qs[:5] + Qs[6:], Qok, stats[:5] + stats[6:]):
         assert s == B.SR_OK
         assert np.array_equal(a, b)
@@ -140,17 +144,17 @@ def test_batched_rejects_bad_sizes():
         B.schur_refine_destroy(h)
 
 
-def test_full_batched_workload_certified():
+@pytest.mark.parametrize("hp", [B.SR_HP_OZAKI_BF16, B.SR_HP_OZAKI_CRT])
+def test_full_batched_workload_certified(hp):
     """The benchmarked group itself: all 1024 matrices of the batched workload in
-    one schur_refine_batched call with the bench's options. Every matrix's
+    one schur_refine_batched call with the bench's options (both product forms). Every matrix's
     residuals are certified in double-double on the device
     (schur_refine_residuals, <= 1e-14 sqrt(n)); that certifier is checked against
     the oracle's double-double residuals on 25 matrices, the largest among them."""
     import torch
     ns = [int(n) for n in inputs.batch_sizes(1024)]
     nmax = max(ns)
-    s, h = B.schur_refine_create(nmax, B.default_options(hp_gemm=B.SR_HP_OZAKI_BF16, lp=B.SR_LP_FP32,
-                                                         batch_streams=8), None)
+    s, h = B.schur_refine_create(nmax, B.default_options(hp_gemm=hp, lp=B.SR_LP_FP32, batch_streams=8), None)
     assert s == B.SR_OK
     try:
         problems = [inputs.batch_problem(i, n) for i, n in enumerate(ns)]
