@@ -637,7 +637,7 @@ sr_status sr_batch_refine(schur_refine_ctx *h, int batch, const int *nv, const v
             }
             std::vector<unsigned long long> plan;
             std::vector<long long> poffs, nleaf;
-            trisolve_plan_group(orders, plan, poffs, nleaf, StepTile<float>::B);
+            trisolve_plan_group(orders, plan, poffs, nleaf, kSolveTile);   // the dataflow form's tiles too
             // the dataflow solve's tickets: the plan's solved tiles, step by step
             // (every tile after the tiles it reads)
             const bool flow = h->opt.solve_mode == 1;   // the stepwise form unless asked

@@ -43,7 +43,9 @@ constexpr int kSolveTile = 32;
 // 2 FMA per SM per cycle, so a 32 x 32 FP64 tile (about 4000 FP64 warp
 // instructions) takes ~60-100 us per block step, a 16 x 16 one about 8 times
 // less for twice the steps. The update kernels' FP64 work is the same n^3/3
-// FMAs for either size and runs beside the leaves.
+// FMAs for either size and runs beside the leaves. (FP32 keeps 32: at n = 4096
+// its 16 x 16 form measured slower, 41.4 against 35.5 ms per refinement, the
+// update launches and step gaps outweighing the shorter leaves.)
 template <typename T> struct StepTile {
     static constexpr int B = SrNum<T>::kind == 1 ? 16 : kSolveTile;
 };
@@ -448,15 +450,14 @@ inline cudaError_t trisolve_launches(cudaStream_t st, cudaStream_t aux, cudaEven
 }
 
 // The launches of a group plan (no double-double divisors; the plan built for
-// StepTile<T>::B): the same two-stream sequence as trisolve_launches, steps
+// the tile B): the same two-stream sequence as trisolve_launches, steps
 // t = nsteps-1 .. 0.
-template <typename T>
+template <typename T, int B = kSolveTile>
 inline cudaError_t trisolve_launches_group(cudaStream_t st, cudaStream_t aux, cudaEvent_t ev0, cudaEvent_t ev1,
                                            const SolveMat *mats, int *flags, const unsigned long long *plan,
                                            const std::vector<long long> &offsets, const std::vector<long long> &nleaf,
                                            double cap = 0.0)
 {
-    constexpr int B = StepTile<T>::B;   // the plan is built for this tile
     const int nsteps = (int)nleaf.size();
     cudaError_t e = cudaEventRecord(ev0, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev0, 0);
