@@ -971,64 +971,152 @@ ozaki_crt_combine_td_kernel(int m, int n, const uint8_t *__restrict__ planes, in
     }
 }
 
+// ---- the column sums of a 12-limb rebuild on the tensor cores -------------------
+// acc[k] = sum_l R_l w_l[k] (R_l the residue bytes of one entry, w_l[k] the
+// 32-bit limbs of the rebuild weights) is, byte by byte, a product of the
+// entries' residues (an entries x moduli matrix) with the weights' bytes (a
+// moduli x 48 matrix): every factor is an integer below 256, exact in bf16,
+// and every column sum is below 48 * 255^2 < 2^22, exact in the FP32
+// accumulation of mma.sync. A warp forms the sums of 32 consecutive plane
+// rows as two m16n8k16 groups over NM / 16 steps of K and 6 tiles of 8 byte
+// positions. The C fragment of tile j holds byte positions 8 j + 2 tig (+ 1)
+// of rows g and g + 8 (g = lane / 4, tig = lane % 4): byte position p is byte
+// p % 4 of limb p / 4, so a lane and lane ^ 1 hold the two halves of limb
+// 2 j + tig / 2, and lane ^ 2 the limb of the other parity. After the
+// exchanges, lane (g, tig) holds the 12 sums of row crt_tc_entry(lane).
+__device__ __forceinline__ void sr_mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// the bf16 bits of an integer below 256 (exact: at most 8 significant bits)
+__device__ __forceinline__ uint32_t bf16_of_byte(uint32_t x) { return __float_as_uint((float)x) >> 16; }
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t lo, uint32_t hi)
+{
+    return bf16_of_byte(lo) | (bf16_of_byte(hi) << 16);
+}
+__device__ __forceinline__ int crt_tc_entry(int lane)
+{
+    const int tig = lane & 3;
+    return 16 * (tig & 1) + (lane >> 2) + 8 * (tig >> 1);
+}
+// B fragments: the weight bytes, rows k = 16 s + 2 tig (+1, +8, +9), column 8 j + g
+template <int NM>
+__device__ __forceinline__ void crt_weight_frags(const CrtRebuildSm &T, int lane, uint32_t (&bw)[NM / 16][6][2])
+{
+    const int g = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int s = 0; s < NM / 16; ++s)
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 16 * s + 2 * tig + 8 * h, pos = 8 * j + g;
+                const uint32_t b0 = (T.w[k][pos >> 2] >> (8 * (pos & 3))) & 255u;
+                const uint32_t b1 = (T.w[k + 1][pos >> 2] >> (8 * (pos & 3))) & 255u;
+                bw[s][j][h] = bf16_pair(b0, b1);
+            }
+}
+template <int NM>
+__device__ __forceinline__ void crt_sums_tc(const uint8_t *__restrict__ planes, size_t off, size_t pstride,
+                                            const uint32_t (&bw)[NM / 16][6][2], int lane, u64 (&acc)[12])
+{
+    const int g = lane >> 2, tig = lane & 3;
+    float c[2][6][4];
+#pragma unroll
+    for (int G = 0; G < 2; ++G)
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) c[G][j][x] = 0.f;
+#pragma unroll
+    for (int s = 0; s < NM / 16; ++s) {
+        const size_t k0 = (size_t)(16 * s + 2 * tig);
+#pragma unroll
+        for (int G = 0; G < 2; ++G) {
+            const uint8_t *p = planes + off + (size_t)(16 * G + g);   // row 16 G + g, modulus 0
+            uint32_t a[4];
+            a[0] = bf16_pair(p[k0 * pstride], p[(k0 + 1) * pstride]);
+            a[1] = bf16_pair(p[8 + k0 * pstride], p[8 + (k0 + 1) * pstride]);
+            a[2] = bf16_pair(p[(k0 + 8) * pstride], p[(k0 + 9) * pstride]);
+            a[3] = bf16_pair(p[8 + (k0 + 8) * pstride], p[8 + (k0 + 9) * pstride]);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) sr_mma_bf16(c[G][j], a, bw[s][j][0], bw[s][j][1]);
+        }
+    }
+    const bool bh = (tig & 1) != 0;   // this lane holds bytes 2, 3 (else 0, 1) of its limbs
+    const bool gm = bh, hm = (tig >> 1) != 0, odd = hm;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        u64 v[2][2];   // [group][row half]: limb 2 j + tig / 2
+#pragma unroll
+        for (int G = 0; G < 2; ++G)
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr) {
+                // two byte positions in 32 bits (below 2^22 + 2^30), the partner's two above them
+                const uint32_t own = __float2uint_rn(c[G][j][2 * hr]) + (__float2uint_rn(c[G][j][2 * hr + 1]) << 8);
+                const uint32_t oth = __shfl_xor_sync(0xffffffffu, own, 1);
+                const uint32_t lo = bh ? oth : own, hi = bh ? own : oth;
+                v[G][hr] = (u64)lo + ((u64)hi << 16);
+            }
+        // this lane's row (gm, hm): its limb of this parity is v[gm][hm]; lane ^ 2
+        // holds the other parity and sends it for row (gm, hm), as this lane sends
+        // v[gm][!hm] for the row of lane ^ 2
+        const u64 mine = gm ? (hm ? v[1][1] : v[1][0]) : (hm ? v[0][1] : v[0][0]);
+        const u64 send = gm ? (hm ? v[1][0] : v[1][1]) : (hm ? v[0][0] : v[0][1]);
+        const u64 got = __shfl_xor_sync(0xffffffffu, send, 2);
+        acc[2 * j] = odd ? got : mine;
+        acc[2 * j + 1] = odd ? mine : got;
+    }
+}
+
+// v = the 6 words mw shifted up by Q words and rr < 64 bits, in 12 words
+template <int Q>
+__device__ __forceinline__ void d6_place(const u64 (&mw)[6], int rr, u64 (&v)[12])
+{
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const u64 lo = (k - Q >= 0 && k - Q < 6) ? mw[k - Q >= 0 && k - Q < 6 ? k - Q : 0] : 0ull;
+        const u64 hi = (k - Q - 1 >= 0 && k - Q - 1 < 6) ? mw[k - Q - 1 >= 0 && k - Q - 1 < 6 ? k - Q - 1 : 0] : 0ull;
+        v[k] = rr ? (lo << rr) | (hi >> (64 - rr)) : lo;
+    }
+}
+
 // Six-double results: the product of operands held as two residue halves,
 // X = X_hi 2^t + X_lo for each vector, is HH 2^(2t) + (HL + LH) 2^t + LL. The
 // four integer products are the four plane sets (48 byte planes each) of one
-// entry; each is rebuilt into 12 limbs as for the triple-double form, the four
-// are summed exactly in a 768-bit two's complement integer, and its 512
-// leading bits are rounded once to six words. One entry per rebuild, 32 x 32
-// entries per block (no mirrored form: the Gram products are formed whole).
+// entry; each is rebuilt into 12 limbs (column sums on the tensor cores, by a
+// whole warp for its 32 rows), the four are summed exactly in a 768-bit two's
+// complement integer, and its 512 leading bits are rounded once to six words.
+// No mirrored form: the Gram products are formed whole.
 template <int NM>
-__device__ __forceinline__ d6v crt_value_d6(const uint8_t *__restrict__ planes, size_t off, size_t pstride,
-                                            size_t setstride, const CrtRebuildSm &T, int e1, int e2, int t,
-                                            bool negs)
+__device__ __forceinline__ d6v crt_value_d6_tc(const uint8_t *__restrict__ planes, size_t off, size_t pstride,
+                                               size_t setstride, const CrtRebuildSm &T,
+                                               const uint32_t (&bw)[NM / 16][6][2], int lane, int e1, int e2,
+                                               int t, bool negs)
 {
     constexpr int L = 12, NS = 12;   // limbs of one rebuild; 64-bit words of the sum
     d6v r;
-    const double nan = __longlong_as_double(0x7ff8000000000000LL);
-    if (e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite) {
-#pragma unroll
-        for (int k = 0; k < kD6Words; ++k) r.x[k] = nan;
-        return r;
-    }
     u64 S[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) S[k] = 0;
 #pragma unroll 1
     for (int set = 0; set < 4; ++set) {
         u64 acc[L];
-#pragma unroll
-        for (int k = 0; k < L; ++k) acc[k] = 0ull;
-        const size_t base = off + (size_t)set * setstride;
-#pragma unroll 4
-        for (int l = 0; l < NM; ++l) {
-            const uint32_t R = planes[base + (size_t)l * pstride];
-#pragma unroll
-            for (int k = 0; k < L; k += 4) {
-                const uint4 w4 = *reinterpret_cast<const uint4 *>(&T.w[l][k]);
-                acc[k] += (u64)R * w4.x;
-                acc[k + 1] += (u64)R * w4.y;
-                acc[k + 2] += (u64)R * w4.z;
-                acc[k + 3] += (u64)R * w4.w;
-            }
-        }
+        crt_sums_tc<NM>(planes + (size_t)set * setstride, off, pstride, bw, lane, acc);
         uint32_t mag[L];
         const bool ng = crt_reduce<L>(acc, T, mag) != negs;
-        // mag (6 words) shifted by 2t (HH), t (HL, LH) or 0 (LL) into the sum
-        const int sh = set == 0 ? 2 * t : (set == 3 ? 0 : t);
-        const int q = sh >> 6, rr = sh & 63;
+        // mag (6 words) shifted by 2t (HH), t (HL, LH) or 0 (LL) into the sum; for
+        // t in [160, 174] these are 5, 2 and 0 whole words and a bit shift rr
+        u64 mw[L / 2];
+#pragma unroll
+        for (int j = 0; j < L / 2; ++j) mw[j] = ((u64)mag[2 * j + 1] << 32) | mag[2 * j];
         u64 v[NS];
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-            u64 lo = 0, hi = 0;   // words k - q and k - q - 1 of mag
-#pragma unroll
-            for (int j = 0; j < L / 2; ++j) {
-                const u64 mj = ((u64)mag[2 * j + 1] << 32) | mag[2 * j];
-                if (j == k - q) lo = mj;
-                if (j == k - q - 1) hi = mj;
-            }
-            v[k] = rr ? (lo << rr) | (hi >> (64 - rr)) : lo;
-        }
+        if (set == 0) d6_place<5>(mw, (2 * t) & 63, v);
+        else if (set == 3) d6_place<0>(mw, 0, v);
+        else d6_place<2>(mw, t & 63, v);
         if (ng) mw_neg<NS>(v);
         mw_add<NS>(S, v);
     }
@@ -1043,28 +1131,41 @@ __device__ __forceinline__ d6v crt_value_d6(const uint8_t *__restrict__ planes, 
     for (int j = 0; j < 8; ++j) W[j] = mw_word<NS>(S, top - 7 + j);
     const int T2 = 2 * (2 * t - 2);   // the operands hold T = 2t - 2 bits each
     mw_round<kD6Words, 8>(W, neg, e1 + e2 - T2 - T.sigma + 64 * (top - 7), r.x);
+    if (e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite) {
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+        for (int k = 0; k < kD6Words; ++k) r.x[k] = nan;
+    }
     return r;
 }
 
+// 32 x 32 entries per block; warp w rebuilds rows blockIdx.x 32 .. + 31 of
+// columns w, w + 8, w + 16, w + 24 (lane: row crt_tc_entry(lane)); every
+// branch around the warp's tensor-core product is uniform over the warp.
 template <class EP, int NM>
 __global__ void __launch_bounds__(256)
 ozaki_crt_combine_d6_kernel(int m, int n, const uint8_t *__restrict__ planes, int ldp, size_t pstride,
                             size_t setstride, const int *__restrict__ ea, const int *__restrict__ fb, int t,
                             double sign, EP ep, double *partial, const CrtTable *__restrict__ tab)
 {
+    static_assert(NM % 16 == 0, "moduli in steps of 16");
     __shared__ CrtRebuildSm T;
     crt_stage(T, tab, 12);
     __syncthreads();
     const bool negs = sign < 0;
-    const int a = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    uint32_t bw[NM / 16][6][2];
+    crt_weight_frags<NM>(T, lane, bw);
+    const int i0 = blockIdx.x * 32, i = i0 + crt_tc_entry(lane);
+    const int e1 = i < m ? ea[i] : 0;
     double part = 0.0;
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
-        const int i = blockIdx.x * 32 + a, j = blockIdx.y * 32 + wv + 8 * q;
-        if (i >= m || j >= n) continue;
-        const d6v v = crt_value_d6<NM>(planes, (size_t)i + (size_t)j * ldp, pstride, setstride, T, ea[i], fb[j],
-                                       t, negs);
-        part += ep(i, j, v);
+        const int j = blockIdx.y * 32 + wv + 8 * q;
+        if (j >= n) break;   // uniform over the warp
+        const d6v v = crt_value_d6_tc<NM>(planes, (size_t)i0 + (size_t)j * ldp, pstride, setstride, T, bw, lane, e1,
+                                          fb[j], t, negs);
+        if (i < m) part += ep(i, j, v);
     }
     if (partial) {
         part = sr_block_sum<256>(part);
@@ -1080,8 +1181,9 @@ sr_status ozaki_combine_d6(schur_refine_ctx *h, cudaStream_t st, OzakiWork &w, i
                            double sign, EP ep, double *partial, int *blocks)
 {
     static_assert(ep_is_d6<EP>::value, "six-double epilogue");
+    // the rebuild places the partial products 5 and 2 words up: t in [160, 174]
     if (w.cplx || w.crt.L != 12 || w.crt.N != kCrtDefaultModuliTD || !w.slot[rows].crt || !w.slot[cols].crt ||
-        w.slot[rows].t != w.slot[cols].t)
+        w.slot[rows].t != w.slot[cols].t || w.slot[rows].t < 160 || w.slot[rows].t > 174)
         return SR_ERR_INVALID_ARG;
     const int s = w.crt.N;
     const dim3 grid((m + 31) / 32, (n + 31) / 32);
