@@ -866,111 +866,6 @@ ozaki_crt_combine_group_kernel(const uint8_t *__restrict__ planes, size_t pstrid
 }
 
 
-// Triple-double results (L = 12 limbs, the 48 moduli of the triple-double
-// operands): one entry per rebuild, so that the twelve 64-bit column sums
-// stay in registers; a block covers 32 x 32 entries, thread (lane a, warp w)
-// rebuilds rows a of columns w, w + 8, w + 16, w + 24. The rebuilt integer is
-// rounded to a triple-double from its 256 leading bits (the bits below them
-// lie far beyond the 159 kept). Mirrored blocks are turned in shared memory as
-// in ozaki_crt_combine_kernel.
-__device__ __forceinline__ tdv crt_to_td(const uint32_t (&mag)[12], bool neg, int x)
-{
-    int k = 7;   // leading limb of the 256-bit window (limbs k-7 .. k)
-#pragma unroll
-    for (int a = 11; a >= 8; --a)
-        if (k == 7 && mag[a] != 0) k = a;
-    u64 W[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        uint32_t lo = 0, hi = 0;
-#pragma unroll
-        for (int a = 0; a < 12; ++a) {
-            if (a == k - 7 + 2 * q) lo = mag[a];
-            if (a == k - 6 + 2 * q) hi = mag[a];
-        }
-        W[q] = ((u64)hi << 32) | lo;
-    }
-    return td_round_u256(W, neg, x + 32 * (k - 7));
-}
-
-template <int NM>
-__device__ __forceinline__ tdv crt_value_td(const uint8_t *__restrict__ planes, size_t off, size_t pstride,
-                                            const CrtRebuildSm &T, int e1, int e2, int tsum, bool negs)
-{
-    constexpr int L = 12;
-    const double nan = __longlong_as_double(0x7ff8000000000000LL);
-    if (e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite) return {nan, nan, nan};
-    u64 acc[L];
-#pragma unroll
-    for (int k = 0; k < L; ++k) acc[k] = 0ull;
-#pragma unroll 4
-    for (int l = 0; l < NM; ++l) {
-        const uint32_t R = planes[off + (size_t)l * pstride];
-#pragma unroll
-        for (int k = 0; k < L; k += 4) {
-            const uint4 w4 = *reinterpret_cast<const uint4 *>(&T.w[l][k]);
-            acc[k] += (u64)R * w4.x;
-            acc[k + 1] += (u64)R * w4.y;
-            acc[k + 2] += (u64)R * w4.z;
-            acc[k + 3] += (u64)R * w4.w;
-        }
-    }
-    uint32_t mag[L];
-    const bool ng = crt_reduce<L>(acc, T, mag) != negs;
-    return crt_to_td(mag, ng, e1 + e2 - tsum - T.sigma);
-}
-
-template <class EP, int NM>
-__global__ void __launch_bounds__(256)
-ozaki_crt_combine_td_kernel(int m, int n, const uint8_t *__restrict__ planes, int ldp, size_t pstride,
-                            const int *__restrict__ ea, const int *__restrict__ fb, int tsum, double sign, int mirror,
-                            EP ep, double *partial, const CrtTable *__restrict__ tab)
-{
-    __shared__ CrtRebuildSm T;
-    __shared__ tdv turned[32][33];
-    crt_stage(T, tab, 12);
-    __syncthreads();
-    const bool negs = sign < 0;
-    const int a = threadIdx.x & 31, wv = threadIdx.x >> 5;
-    const bool below = mirror && blockIdx.x > blockIdx.y;
-    const int rb = (below ? blockIdx.y : blockIdx.x) * 32, cb = (below ? blockIdx.x : blockIdx.y) * 32;
-    const int rlim = below ? n : m, clim = below ? m : n;
-    double part = 0.0;
-    if (below) {
-        // rebuild the mirrored block (rows along the planes' contiguous index), turn it
-#pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-            const int r = rb + a, c = cb + wv + 8 * q;
-            if (r < rlim && c < clim)
-                turned[wv + 8 * q][a] = crt_value_td<NM>(planes, (size_t)r + (size_t)c * ldp, pstride, T, ea[r],
-                                                         fb[c], tsum, negs);
-        }
-        __syncthreads();
-        const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
-#pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + a, j = j0 + wv + 8 * q;
-            if (i < m && j < n) part += ep(i, j, turned[a][wv + 8 * q]);
-        }
-    } else {
-#pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-            const int i = rb + a, j = cb + wv + 8 * q;
-            if (i >= m || j >= n) continue;
-            tdv v;
-            if (mirror && i > j)   // below the diagonal of a diagonal block: the mirrored entry
-                v = crt_value_td<NM>(planes, (size_t)j + (size_t)i * ldp, pstride, T, ea[j], fb[i], tsum, negs);
-            else
-                v = crt_value_td<NM>(planes, (size_t)i + (size_t)j * ldp, pstride, T, ea[i], fb[j], tsum, negs);
-            part += ep(i, j, v);
-        }
-    }
-    if (partial) {
-        part = sr_block_sum<256>(part);
-        if (threadIdx.x == 0) partial[blockIdx.x + (size_t)gridDim.x * blockIdx.y] = part;
-    }
-}
-
 // ---- the column sums of a 12-limb rebuild on the tensor cores -------------------
 // acc[k] = sum_l R_l w_l[k] (R_l the residue bytes of one entry, w_l[k] the
 // 32-bit limbs of the rebuild weights) is, byte by byte, a product of the
@@ -1069,6 +964,104 @@ __device__ __forceinline__ void crt_sums_tc(const uint8_t *__restrict__ planes, 
         const u64 got = __shfl_xor_sync(0xffffffffu, send, 2);
         acc[2 * j] = odd ? got : mine;
         acc[2 * j + 1] = odd ? mine : got;
+    }
+}
+
+// Triple-double results (L = 12 limbs, the 48 moduli of the triple-double
+// operands): the twelve column sums of an entry come from the warp's
+// tensor-core product (crt_sums_tc); a block covers 32 x 32 entries. The
+// rebuilt integer is rounded to a triple-double from its 256 leading bits (the
+// bits below them lie far beyond the 159 kept).
+__device__ __forceinline__ tdv crt_to_td(const uint32_t (&mag)[12], bool neg, int x)
+{
+    int k = 7;   // leading limb of the 256-bit window (limbs k-7 .. k)
+#pragma unroll
+    for (int a = 11; a >= 8; --a)
+        if (k == 7 && mag[a] != 0) k = a;
+    u64 W[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int a = 0; a < 12; ++a) {
+            if (a == k - 7 + 2 * q) lo = mag[a];
+            if (a == k - 6 + 2 * q) hi = mag[a];
+        }
+        W[q] = ((u64)hi << 32) | lo;
+    }
+    return td_round_u256(W, neg, x + 32 * (k - 7));
+}
+
+// this lane's entry of the warp's 32 plane rows at off (every lane of the warp
+// calls it together)
+template <int NM>
+__device__ __forceinline__ tdv crt_value_td_tc(const uint8_t *__restrict__ planes, size_t off, size_t pstride,
+                                               const CrtRebuildSm &T, const uint32_t (&bw)[NM / 16][6][2],
+                                               int lane, int e1, int e2, int tsum, bool negs)
+{
+    constexpr int L = 12;
+    u64 acc[L];
+    crt_sums_tc<NM>(planes, off, pstride, bw, lane, acc);
+    uint32_t mag[L];
+    const bool ng = crt_reduce<L>(acc, T, mag) != negs;
+    const tdv v = crt_to_td(mag, ng, e1 + e2 - tsum - T.sigma);
+    if (e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite) {
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        return {nan, nan, nan};
+    }
+    return v;
+}
+
+// Warp w rebuilds, for q = 0..3, 32 consecutive plane rows of column w + 8 q
+// of its block (lane: row crt_tc_entry(lane)); every branch around the warp's
+// tensor-core product is uniform over the warp. A mirrored block below the
+// diagonal rebuilds the block above it and turns it in shared memory; entries
+// below the diagonal of a diagonal block are read where they are: the product
+// tile holding a diagonal 32 x 32 block is always formed.
+template <class EP, int NM>
+__global__ void __launch_bounds__(256)
+ozaki_crt_combine_td_kernel(int m, int n, const uint8_t *__restrict__ planes, int ldp, size_t pstride,
+                            const int *__restrict__ ea, const int *__restrict__ fb, int tsum, double sign, int mirror,
+                            EP ep, double *partial, const CrtTable *__restrict__ tab)
+{
+    static_assert(NM % 16 == 0, "moduli in steps of 16");
+    __shared__ CrtRebuildSm T;
+    __shared__ tdv turned[32][33];
+    crt_stage(T, tab, 12);
+    __syncthreads();
+    const bool negs = sign < 0;
+    const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5, a = crt_tc_entry(lane);
+    uint32_t bw[NM / 16][6][2];
+    crt_weight_frags<NM>(T, lane, bw);
+    const bool below = mirror && blockIdx.x > blockIdx.y;
+    const int rb = (below ? blockIdx.y : blockIdx.x) * 32, cb = (below ? blockIdx.x : blockIdx.y) * 32;
+    const int rlim = below ? n : m, clim = below ? m : n;
+    const int r = rb + a;
+    const int e1 = r < rlim ? ea[r] : 0;
+    double part = 0.0;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+        const int c = cb + wv + 8 * q;
+        if (c >= clim) break;   // uniform over the warp
+        const tdv v = crt_value_td_tc<NM>(planes, (size_t)rb + (size_t)c * ldp, pstride, T, bw, lane, e1, fb[c],
+                                          tsum, negs);
+        if (r < rlim) {
+            if (below) turned[wv + 8 * q][a] = v;
+            else part += ep(r, c, v);
+        }
+    }
+    if (below) {
+        __syncthreads();
+        const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32, al = threadIdx.x & 31;
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + al, j = j0 + wv + 8 * q;
+            if (i < m && j < n) part += ep(i, j, turned[al][wv + 8 * q]);
+        }
+    }
+    if (partial) {
+        part = sr_block_sum<256>(part);
+        if (threadIdx.x == 0) partial[blockIdx.x + (size_t)gridDim.x * blockIdx.y] = part;
     }
 }
 
