@@ -690,6 +690,110 @@ crt_value(const uint8_t *__restrict__ planes, size_t off, size_t pstride, const 
 // mirrored block (coalesced along the planes' contiguous index) and turns it
 // in shared memory; entries below the diagonal of a diagonal block read the
 // mirrored position directly.
+// ---- the column sums of a rebuild on the tensor cores ---------------------------
+// acc[k] = sum_l R_l w_l[k] (R_l the residue bytes of one entry, w_l[k] the
+// L 32-bit limbs of the rebuild weights) is, byte by byte, a product of the
+// entries' residues (an entries x moduli matrix) with the weights' bytes (a
+// moduli x 4 L matrix): every factor is an integer below 256, exact in bf16,
+// and every column sum is below 64 * 255^2 < 2^22 for up to 64 moduli, exact
+// in the FP32 accumulation of mma.sync. A warp forms the sums of 32
+// consecutive plane rows as two m16n8k16 groups over NM / 16 steps of K and
+// L / 2 tiles of 8 byte positions. The C fragment of tile j holds byte
+// positions 8 j + 2 tig (+ 1) of rows g and g + 8 (g = lane / 4, tig =
+// lane % 4): byte position p is byte p % 4 of limb p / 4, so a lane and
+// lane ^ 1 hold the two halves of limb 2 j + tig / 2, and lane ^ 2 the limb of
+// the other parity. After the exchanges, lane (g, tig) holds the L sums of row
+// crt_tc_entry(lane).
+__device__ __forceinline__ void sr_mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// the bf16 bits of an integer below 256 (exact: at most 8 significant bits)
+__device__ __forceinline__ uint32_t bf16_of_byte(uint32_t x) { return __float_as_uint((float)x) >> 16; }
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t lo, uint32_t hi)
+{
+    return bf16_of_byte(lo) | (bf16_of_byte(hi) << 16);
+}
+__device__ __forceinline__ int crt_tc_entry(int lane)
+{
+    const int tig = lane & 3;
+    return 16 * (tig & 1) + (lane >> 2) + 8 * (tig >> 1);
+}
+// B fragments: the weight bytes, rows k = 16 s + 2 tig (+1, +8, +9), column 8 j + g
+template <int NM, int L = 12>
+__device__ __forceinline__ void crt_weight_frags(const CrtRebuildSm &T, int lane,
+                                                 uint32_t (&bw)[NM / 16][L / 2][2])
+{
+    const int g = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int s = 0; s < NM / 16; ++s)
+#pragma unroll
+        for (int j = 0; j < L / 2; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 16 * s + 2 * tig + 8 * h, pos = 8 * j + g;
+                const uint32_t b0 = (T.w[k][pos >> 2] >> (8 * (pos & 3))) & 255u;
+                const uint32_t b1 = (T.w[k + 1][pos >> 2] >> (8 * (pos & 3))) & 255u;
+                bw[s][j][h] = bf16_pair(b0, b1);
+            }
+}
+template <int NM, int L = 12>
+__device__ __forceinline__ void crt_sums_tc(const uint8_t *__restrict__ planes, size_t off, size_t pstride,
+                                            const uint32_t (&bw)[NM / 16][L / 2][2], int lane, u64 (&acc)[L])
+{
+    constexpr int NJ = L / 2;   // tiles of 8 byte positions (2 limbs each)
+    const int g = lane >> 2, tig = lane & 3;
+    float c[2][NJ][4];
+#pragma unroll
+    for (int G = 0; G < 2; ++G)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) c[G][j][x] = 0.f;
+#pragma unroll
+    for (int s = 0; s < NM / 16; ++s) {
+        const size_t k0 = (size_t)(16 * s + 2 * tig);
+#pragma unroll
+        for (int G = 0; G < 2; ++G) {
+            const uint8_t *p = planes + off + (size_t)(16 * G + g);   // row 16 G + g, modulus 0
+            uint32_t a[4];
+            a[0] = bf16_pair(p[k0 * pstride], p[(k0 + 1) * pstride]);
+            a[1] = bf16_pair(p[8 + k0 * pstride], p[8 + (k0 + 1) * pstride]);
+            a[2] = bf16_pair(p[(k0 + 8) * pstride], p[(k0 + 9) * pstride]);
+            a[3] = bf16_pair(p[8 + (k0 + 8) * pstride], p[8 + (k0 + 9) * pstride]);
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) sr_mma_bf16(c[G][j], a, bw[s][j][0], bw[s][j][1]);
+        }
+    }
+    const bool bh = (tig & 1) != 0;   // this lane holds bytes 2, 3 (else 0, 1) of its limbs
+    const bool gm = bh, hm = (tig >> 1) != 0, odd = hm;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        u64 v[2][2];   // [group][row half]: limb 2 j + tig / 2
+#pragma unroll
+        for (int G = 0; G < 2; ++G)
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr) {
+                // two byte positions in 32 bits (below 2^22 + 2^30), the partner's two above them
+                const uint32_t own = __float2uint_rn(c[G][j][2 * hr]) + (__float2uint_rn(c[G][j][2 * hr + 1]) << 8);
+                const uint32_t oth = __shfl_xor_sync(0xffffffffu, own, 1);
+                const uint32_t lo = bh ? oth : own, hi = bh ? own : oth;
+                v[G][hr] = (u64)lo + ((u64)hi << 16);
+            }
+        // this lane's row (gm, hm): its limb of this parity is v[gm][hm]; lane ^ 2
+        // holds the other parity and sends it for row (gm, hm), as this lane sends
+        // v[gm][!hm] for the row of lane ^ 2
+        const u64 mine = gm ? (hm ? v[1][1] : v[1][0]) : (hm ? v[0][1] : v[0][0]);
+        const u64 send = gm ? (hm ? v[1][0] : v[1][1]) : (hm ? v[0][0] : v[0][1]);
+        const u64 got = __shfl_xor_sync(0xffffffffu, send, 2);
+        acc[2 * j] = odd ? got : mine;
+        acc[2 * j + 1] = odd ? mine : got;
+    }
+}
+
 template <bool CPLX, int L>
 using CrtCombineValue = std::conditional_t<CPLX, cd, std::conditional_t<L == 8, ddv, double>>;
 
@@ -706,6 +810,52 @@ __device__ __forceinline__ double crt_combine_block(int bx, int by, int m, int n
     static_assert(!(CPLX && L == 8), "complex products rebuild FP64 parts");
     using RV = std::conditional_t<L == 8, ddv, double>;
     using VT = CrtCombineValue<CPLX, L>;
+    if constexpr (!CPLX && NM > 0 && NM % 16 == 0) {
+        // real products: the column sums on the tensor cores, a warp per 32 plane
+        // rows of a column (as ozaki_crt_combine_td_kernel; the rebuilt values are
+        // those of the scalar sums bit for bit)
+        const bool negs = sign < 0;
+        const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5, a = crt_tc_entry(lane);
+        uint32_t bw[NM / 16][L / 2][2];
+        crt_weight_frags<NM, L>(T, lane, bw);
+        const bool below = mirror && bx > by;
+        const int rb = (below ? by : bx) * 32, cb = (below ? bx : by) * 32;
+        const int rlim = below ? n : m, clim = below ? m : n;
+        const int r = rb + a;
+        const int e1 = r < rlim ? ea[r] : 0;
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        double part = 0.0;
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const int c = cb + wv + 8 * q;
+            if (c >= clim) break;   // uniform over the warp
+            const int e2 = fb[c];
+            u64 acc[L];
+            crt_sums_tc<NM, L>(planes, (size_t)rb + (size_t)c * ldp, pstride, bw, lane, acc);
+            uint32_t mag[L];
+            const bool ng = crt_reduce<L>(acc, T, mag) != negs;
+            RV v;
+            if constexpr (L == 8) v = crt_to_dd(mag, ng, e1 + e2 - tsum - T.sigma);
+            else v = crt_to_double(mag, ng, e1 + e2 - tsum - T.sigma);
+            if (e1 == kOzakiExpNonfinite || e2 == kOzakiExpNonfinite) {
+                if constexpr (L == 8) v = ddv{nan, nan}; else v = nan;
+            }
+            if (r < rlim) {
+                if (below) turned[wv + 8 * q][a] = v;
+                else part += ep(r, c, v);
+            }
+        }
+        if (below) {
+            __syncthreads();
+            const int i0 = bx * 32, j0 = by * 32, al = threadIdx.x & 31;
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + al, j = j0 + wv + 8 * q;
+                if (i < m && j < n) part += ep(i, j, turned[al][wv + 8 * q]);
+            }
+        }
+        return part;
+    } else {
     const int N = T.N;
     const bool negs = sign < 0;
     const int ig = threadIdx.x & 7, jl = threadIdx.x >> 3;
@@ -818,6 +968,7 @@ __device__ __forceinline__ double crt_combine_block(int bx, int by, int m, int n
         }
     }
     return part;
+    }
 }
 
 template <class EP, bool CPLX, int L, int NM>
@@ -865,107 +1016,6 @@ ozaki_crt_combine_group_kernel(const uint8_t *__restrict__ planes, size_t pstrid
     }
 }
 
-
-// ---- the column sums of a 12-limb rebuild on the tensor cores -------------------
-// acc[k] = sum_l R_l w_l[k] (R_l the residue bytes of one entry, w_l[k] the
-// 32-bit limbs of the rebuild weights) is, byte by byte, a product of the
-// entries' residues (an entries x moduli matrix) with the weights' bytes (a
-// moduli x 48 matrix): every factor is an integer below 256, exact in bf16,
-// and every column sum is below 48 * 255^2 < 2^22, exact in the FP32
-// accumulation of mma.sync. A warp forms the sums of 32 consecutive plane
-// rows as two m16n8k16 groups over NM / 16 steps of K and 6 tiles of 8 byte
-// positions. The C fragment of tile j holds byte positions 8 j + 2 tig (+ 1)
-// of rows g and g + 8 (g = lane / 4, tig = lane % 4): byte position p is byte
-// p % 4 of limb p / 4, so a lane and lane ^ 1 hold the two halves of limb
-// 2 j + tig / 2, and lane ^ 2 the limb of the other parity. After the
-// exchanges, lane (g, tig) holds the 12 sums of row crt_tc_entry(lane).
-__device__ __forceinline__ void sr_mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-// the bf16 bits of an integer below 256 (exact: at most 8 significant bits)
-__device__ __forceinline__ uint32_t bf16_of_byte(uint32_t x) { return __float_as_uint((float)x) >> 16; }
-__device__ __forceinline__ uint32_t bf16_pair(uint32_t lo, uint32_t hi)
-{
-    return bf16_of_byte(lo) | (bf16_of_byte(hi) << 16);
-}
-__device__ __forceinline__ int crt_tc_entry(int lane)
-{
-    const int tig = lane & 3;
-    return 16 * (tig & 1) + (lane >> 2) + 8 * (tig >> 1);
-}
-// B fragments: the weight bytes, rows k = 16 s + 2 tig (+1, +8, +9), column 8 j + g
-template <int NM>
-__device__ __forceinline__ void crt_weight_frags(const CrtRebuildSm &T, int lane, uint32_t (&bw)[NM / 16][6][2])
-{
-    const int g = lane >> 2, tig = lane & 3;
-#pragma unroll
-    for (int s = 0; s < NM / 16; ++s)
-#pragma unroll
-        for (int j = 0; j < 6; ++j)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = 16 * s + 2 * tig + 8 * h, pos = 8 * j + g;
-                const uint32_t b0 = (T.w[k][pos >> 2] >> (8 * (pos & 3))) & 255u;
-                const uint32_t b1 = (T.w[k + 1][pos >> 2] >> (8 * (pos & 3))) & 255u;
-                bw[s][j][h] = bf16_pair(b0, b1);
-            }
-}
-template <int NM>
-__device__ __forceinline__ void crt_sums_tc(const uint8_t *__restrict__ planes, size_t off, size_t pstride,
-                                            const uint32_t (&bw)[NM / 16][6][2], int lane, u64 (&acc)[12])
-{
-    const int g = lane >> 2, tig = lane & 3;
-    float c[2][6][4];
-#pragma unroll
-    for (int G = 0; G < 2; ++G)
-#pragma unroll
-        for (int j = 0; j < 6; ++j)
-#pragma unroll
-            for (int x = 0; x < 4; ++x) c[G][j][x] = 0.f;
-#pragma unroll
-    for (int s = 0; s < NM / 16; ++s) {
-        const size_t k0 = (size_t)(16 * s + 2 * tig);
-#pragma unroll
-        for (int G = 0; G < 2; ++G) {
-            const uint8_t *p = planes + off + (size_t)(16 * G + g);   // row 16 G + g, modulus 0
-            uint32_t a[4];
-            a[0] = bf16_pair(p[k0 * pstride], p[(k0 + 1) * pstride]);
-            a[1] = bf16_pair(p[8 + k0 * pstride], p[8 + (k0 + 1) * pstride]);
-            a[2] = bf16_pair(p[(k0 + 8) * pstride], p[(k0 + 9) * pstride]);
-            a[3] = bf16_pair(p[8 + (k0 + 8) * pstride], p[8 + (k0 + 9) * pstride]);
-#pragma unroll
-            for (int j = 0; j < 6; ++j) sr_mma_bf16(c[G][j], a, bw[s][j][0], bw[s][j][1]);
-        }
-    }
-    const bool bh = (tig & 1) != 0;   // this lane holds bytes 2, 3 (else 0, 1) of its limbs
-    const bool gm = bh, hm = (tig >> 1) != 0, odd = hm;
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        u64 v[2][2];   // [group][row half]: limb 2 j + tig / 2
-#pragma unroll
-        for (int G = 0; G < 2; ++G)
-#pragma unroll
-            for (int hr = 0; hr < 2; ++hr) {
-                // two byte positions in 32 bits (below 2^22 + 2^30), the partner's two above them
-                const uint32_t own = __float2uint_rn(c[G][j][2 * hr]) + (__float2uint_rn(c[G][j][2 * hr + 1]) << 8);
-                const uint32_t oth = __shfl_xor_sync(0xffffffffu, own, 1);
-                const uint32_t lo = bh ? oth : own, hi = bh ? own : oth;
-                v[G][hr] = (u64)lo + ((u64)hi << 16);
-            }
-        // this lane's row (gm, hm): its limb of this parity is v[gm][hm]; lane ^ 2
-        // holds the other parity and sends it for row (gm, hm), as this lane sends
-        // v[gm][!hm] for the row of lane ^ 2
-        const u64 mine = gm ? (hm ? v[1][1] : v[1][0]) : (hm ? v[0][1] : v[0][0]);
-        const u64 send = gm ? (hm ? v[1][0] : v[1][1]) : (hm ? v[0][0] : v[0][1]);
-        const u64 got = __shfl_xor_sync(0xffffffffu, send, 2);
-        acc[2 * j] = odd ? got : mine;
-        acc[2 * j + 1] = odd ? mine : got;
-    }
-}
 
 // Triple-double results (L = 12 limbs, the 48 moduli of the triple-double
 // operands): the twelve column sums of an entry come from the warp's
