@@ -115,8 +115,7 @@ __device__ __forceinline__ void mw_round(u64 (&W)[NW], bool neg, int xe, double 
         if (p < 0) {
             out[wd] = 0.0;
         } else if (p <= 52) {
-            const double v = scalbn((double)W[0], xe);   // exact: at most 53 bits
-            out[wd] = neg ? -v : v;
+            out[wd] = td_make(W[0], xe, neg);   // exact: at most 53 bits
             W[0] = 0;
         } else {
             const int s = p - 52;
@@ -124,8 +123,7 @@ __device__ __forceinline__ void mw_round(u64 (&W)[NW], bool neg, int xe, double 
             const bool half = (mw_bits64<NW>(W, s - 1) & 1ull) != 0;
             const bool rest = mw_any_below<NW>(W, s - 1);
             const bool up = half && (rest || (m & 1ull));
-            const double v = scalbn((double)(m + (up ? 1ull : 0ull)), s + xe);
-            out[wd] = neg ? -v : v;
+            out[wd] = td_make(m + (up ? 1ull : 0ull), s + xe, neg);   // m + 1 <= 2^53: exact
             mw_keep_low<NW>(W, s);
             if (up) {
                 mw_neg<NW>(W);

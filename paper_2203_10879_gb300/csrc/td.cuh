@@ -89,6 +89,23 @@ __device__ __forceinline__ void u256_neg(u64 (&W)[4])
     }
 }
 
+// (-1)^neg M 2^e as a double, M nonzero with at most 53 significant bits (the
+// value is exact). A normal result is assembled from its fields with integer
+// instructions (GB300's FP64 pipe is slow); one near either end of the
+// exponent range goes through scalbn.
+__device__ __forceinline__ double td_make(u64 M, int e, bool neg)
+{
+    const int top = 63 - __clzll((long long)M);   // M in [2^top, 2^(top + 1))
+    const int E = e + top + 1023;                  // biased exponent
+    if (E >= 1 && E <= 2046) {
+        const u64 mant = top >= 52 ? M >> (top - 52) : M << (52 - top);   // drops only zero bits
+        return __longlong_as_double(
+            (long long)(((u64)neg << 63) | ((u64)E << 52) | (mant & ((1ull << 52) - 1ull))));
+    }
+    const double v = scalbn((double)M, e);
+    return neg ? -v : v;
+}
+
 // (-1)^neg W 2^xe rounded to a triple-double (W is consumed)
 __device__ __forceinline__ tdv td_round_u256(u64 (&W)[4], bool neg, int xe)
 {
@@ -99,8 +116,7 @@ __device__ __forceinline__ tdv td_round_u256(u64 (&W)[4], bool neg, int xe)
         if (p < 0) {
             out[wd] = 0.0;
         } else if (p <= 52) {
-            const double v = scalbn((double)W[0], xe);   // exact: at most 53 bits
-            out[wd] = neg ? -v : v;
+            out[wd] = td_make(W[0], xe, neg);   // exact: at most 53 bits
             W[0] = 0;
         } else {
             const int s = p - 52;
@@ -108,8 +124,7 @@ __device__ __forceinline__ tdv td_round_u256(u64 (&W)[4], bool neg, int xe)
             const bool half = (u256_bits64(W, s - 1) & 1ull) != 0;   // bit s - 1
             const bool rest = u256_any_below(W, s - 1);
             const bool up = half && (rest || (m & 1ull));
-            const double v = scalbn((double)(m + (up ? 1ull : 0ull)), s + xe);   // m + 1 <= 2^53: exact
-            out[wd] = neg ? -v : v;
+            out[wd] = td_make(m + (up ? 1ull : 0ull), s + xe, neg);   // m + 1 <= 2^53: exact
             u256_keep_low(W, s);
             if (up) {
                 // what is left, 2^s - W, has the other sign
