@@ -683,13 +683,6 @@ crt_value(const uint8_t *__restrict__ planes, size_t off, size_t pstride, const 
     else return crt_to_double(mag, ng, e1 + e2 - tsum - T.sigma);
 }
 
-// C(i, j) = sign * (rebuilt product) with the epilogue ep, FP64 results
-// (L = 4) or double-double results (L = 8). Each thread takes 4 consecutive
-// rows of one column (one 32-bit load per residue plane); a block covers 32 x
-// 32 entries. With mirror, a block wholly below the diagonal rebuilds the
-// mirrored block (coalesced along the planes' contiguous index) and turns it
-// in shared memory; entries below the diagonal of a diagonal block read the
-// mirrored position directly.
 // ---- the column sums of a rebuild on the tensor cores ---------------------------
 // acc[k] = sum_l R_l w_l[k] (R_l the residue bytes of one entry, w_l[k] the
 // L 32-bit limbs of the rebuild weights) is, byte by byte, a product of the
@@ -797,9 +790,18 @@ __device__ __forceinline__ void crt_sums_tc(const uint8_t *__restrict__ planes, 
 template <bool CPLX, int L>
 using CrtCombineValue = std::conditional_t<CPLX, cd, std::conditional_t<L == 8, ddv, double>>;
 
-// The 32 x 32 output block (bx, by) of one product (planes: its region's
-// origin); returns the thread's sum of the epilogue's values. T is staged and
-// turned is the block's shared turning buffer.
+// C(i, j) = sign * (rebuilt product) with the epilogue ep, FP64 results
+// (L = 4) or double-double results (L = 8): the 32 x 32 output block (bx, by)
+// of one product (planes: its region's origin); returns the thread's sum of
+// the epilogue's values. T is staged and turned is the block's shared turning
+// buffer. Real products: each warp rebuilds 32 consecutive plane rows of four
+// columns with the column sums on the tensor cores; a block wholly below the
+// diagonal of a mirrored product rebuilds the block above it and turns it in
+// shared memory, and entries below the diagonal of a diagonal block are read
+// in place (the product tile holding a diagonal 32 x 32 block is always
+// formed). Complex products: each thread takes 4 consecutive rows of one
+// column (one 32-bit load per residue plane) with scalar sums; entries below
+// the diagonal of a diagonal block read the mirrored position.
 template <class EP, bool CPLX, int L, int NM>
 __device__ __forceinline__ double crt_combine_block(int bx, int by, int m, int n, const uint8_t *__restrict__ planes,
                                                     int ldp, size_t pstride, size_t imoff, const int *__restrict__ ea,
