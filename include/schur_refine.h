@@ -102,7 +102,7 @@ enum { SR_QHAT_FP32 = 0, SR_QHAT_FP64 = 1 };
 typedef struct {
     int dtype;        /* SR_REAL or SR_COMPLEX */
     int target;       /* SR_TARGET_FP64, SR_TARGET_DD, SR_TARGET_TD or SR_TARGET_D6 */
-    int hp_gemm;      /* SR_HP_FP64 or SR_HP_OZAKI_BF16 */
+    int hp_gemm;      /* SR_HP_FP64, SR_HP_OZAKI_BF16 or SR_HP_OZAKI_CRT */
     int lp;           /* SR_LP_FP32 (mixed form) or SR_LP_FP64 (all-FP64 form) */
     int qhat_type;    /* SR_QHAT_FP32 or SR_QHAT_FP64 */
     int full_sigma;   /* 1: keep W^2 Y + W^2 Y W in Sigma (eq. NSmerged);
@@ -130,9 +130,9 @@ typedef struct {
                          another on the handle's stream */
     int batch_mode;   /* schur_refine_batched: 0 (default) = grouped launches
                          where built (real data, FP64 target, emulated
-                         products with 7 digits, FP32 low precision and Qhat,
-                         truncated Sigma, dQhat given), else worker streams;
-                         1 = worker streams always */
+                         products with 7 digits or 16 moduli, FP32 low
+                         precision and Qhat, truncated Sigma, dQhat given),
+                         else worker streams; 1 = worker streams always */
     int tune;         /* work split of the emulated slice products (groups of
                          digit levels per output tile): 0 (default) = the
                          analytic makespan estimate; 1 = on the first product
@@ -266,10 +266,12 @@ sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, vo
  * Grouped launches (batch_mode 0 where built): all matrices advance pass by
  * pass together on the handle's stream, and every stage of a pass is one
  * launch for all matrices still iterating (per-matrix stop test, statuses and
- * pass counts as schur_refine_step; two synchronizations per pass). The
- * grouped workspace (about 60 bytes per matrix element plus 10 KiB per matrix
- * row of digits) is allocated on first use, grown when a later call needs
- * more, and kept by the handle.
+ * pass counts as schur_refine_step; two synchronizations per pass). With
+ * SR_HP_OZAKI_CRT each matrix's operands carry the fixed-point bits t of its
+ * own order, so its factors equal schur_refine_step's on it alone bit for bit
+ * (as with digits). The grouped workspace (about 60 bytes per matrix element
+ * plus 10 KiB per matrix row of digits, 24 KiB with residues) is allocated on
+ * first use, grown when a later call needs more, and kept by the handle.
  * Worker streams (otherwise): the matrices are distributed over batch_streams
  * workers (host threads), each with its own stream and workspace (created on
  * first use and kept by the handle), so the refinements of different matrices
