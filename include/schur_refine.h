@@ -270,8 +270,9 @@ sr_status schur_refine_step(schur_refine_t h, int n, const void *dA, int lda, vo
  * SR_HP_OZAKI_CRT each matrix's operands carry the fixed-point bits t of its
  * own order, so its factors equal schur_refine_step's on it alone bit for bit
  * (as with digits). The grouped workspace (about 60 bytes per matrix element
- * plus 10 KiB per matrix row of digits, 24 KiB with residues) is allocated on
- * first use, grown when a later call needs more, and kept by the handle.
+ * plus 10 KiB per matrix row of digits; the residue form keeps 16 planes per
+ * high-precision slot against 7 digits) is allocated on first use, grown when
+ * a later call needs more, and kept by the handle.
  * Worker streams (otherwise): the matrices are distributed over batch_streams
  * workers (host threads), each with its own stream and workspace (created on
  * first use and kept by the handle), so the refinements of different matrices
