@@ -314,9 +314,12 @@ def run_reference(args):
             else _workload_name(n_ref, cplx, sym, quasi))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "dd+f64" if dd else "f64+f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "dd+f64" if dd else (f"{args.workload}+f64" if mw else "f64+f32"),
+            "data": "synthetic",
             "config": {"workload": name, "n": n_ref,
-                       "form": "FP64->double-double (oracle)" if dd else "mixed FP32->FP64 (oracle)",
+                       "form": ("FP64->double-double (oracle)" if dd else
+                                f"FP64->{_MW_FORMS[mw][0]} (exact fixed-point oracle)" if mw else
+                                "mixed FP32->FP64 (oracle)"),
                        "note": f"measured at n = {n_ref}, not at the GPU line's n = {args.n} (a full oracle "
                                f"refinement at n = {args.n} per step does not fit the run)",
                        "status": st, "iters": it},
