@@ -69,3 +69,19 @@ def test_forty_eight_moduli_give_triple_double_operands():
     s, mods, w, Ms, sigma, t = B.schur_refine_crt_info(48, 12, 4096)
     assert s == B.SR_OK and t == 162 and prod(mods).bit_length() == 338
     assert B.schur_refine_crt_info(48, 12, 8192)[5] >= 159
+
+
+def test_six_double_halves_sit_at_fixed_word_offsets():
+    # the six-double rebuild places HH at 2t and HL + LH at t bits: 5 and 2 whole
+    # words plus a bit shift for t in [160, 174], the range the split and the
+    # rebuild accept; every inner length up to the workspace's limit lands there,
+    # and each half-product still rebuilds exactly (K 2^(2t) < M / 2)
+    for K in (1, 2, 64, 1000, 1024, 4096, 8192):
+        s, mods, w, Ms, sigma, t = B.schur_refine_crt_info(48, 12, K)
+        assert s == B.SR_OK
+        assert 160 <= t <= 174, (K, t)
+        assert (2 * t) >> 6 == 5 and t >> 6 == 2
+        M = 1
+        for m in mods:
+            M *= m
+        assert K * 2 ** (2 * t) < M // 2
